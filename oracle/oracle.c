@@ -1,0 +1,1087 @@
+/*
+ * CPU oracle for the interval branch-and-bound global minimiser.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, scalar restatement
+ * of the method for checking the CUDA library; only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may build or call it.  It shares
+ * no code, header or table with the CUDA path: it parses the objective's
+ * node array (the input format) with its own definitions below.
+ *
+ * What it follows (Zhang, Shan, Cagan, "Global optimization tailored for
+ * graphics processing units"):
+ *   - interval +, -, x, / : Eqs. 3-6 (section 2.1), with optimal outward
+ *     rounding of every endpoint (section 2.1): lower endpoints rounded toward
+ *     -inf, upper toward +inf, here by switching the FPU mode with fesetround.
+ *   - natural interval extension of f (section 2.1): each node of the
+ *     objective replaced by its interval operation.
+ *   - the iteration of section 3.1: sample (GUB update), remove suboptimal
+ *     regions (LB > GUB), partition, rule out by cut-off and by the
+ *     first-order (monotonicity) test, insert, stop; output GLB, GUB and the
+ *     remaining regions.
+ *   - uniform partition of the selected coordinates (Eqs. 10-11) and the
+ *     variable-cycling schedule (section 3.2).
+ * Where the paper leaves a choice open (reduction order, transcendental
+ * rounding, sample point, batching of the best-first selection) the oracle
+ * takes the readings written beside each function.
+ *
+ * Build: gcc -O1 -frounding-math -ffp-contract=off -fno-fast-math
+ *        -fno-math-errno -shared -fPIC oracle.c -lm
+ * No claim of speed is made; every directed operation is its own call.
+ */
+#include <fenv.h>
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* GCC does not implement the FENV_ACCESS pragma; -frounding-math is its
+ * equivalent and is required when building this file. */
+
+#define NOINL __attribute__((noinline))
+
+/* ------------------------------------------------------------------------ */
+/* Directed rounding, section 2.1 ("optimal outward rounding").              */
+/* Every helper switches the mode, performs one operation, and restores      */
+/* round-to-nearest so that libm calls elsewhere run in their default mode.  */
+/* ------------------------------------------------------------------------ */
+static NOINL double d_add(double a, double b, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile double r = a + b;
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static NOINL double d_sub(double a, double b, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile double r = a - b;
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static NOINL double d_mul(double a, double b, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile double r = a * b;
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static NOINL double d_div(double a, double b, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile double r = a / b;
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static NOINL double d_sqrt(double a, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile double r = __builtin_sqrt(a);
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static NOINL float f_add(float a, float b, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile float r = a + b;
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static NOINL float f_sub(float a, float b, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile float r = a - b;
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static NOINL float f_mul(float a, float b, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile float r = a * b;
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static NOINL float f_div(float a, float b, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile float r = a / b;
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static NOINL float f_sqrt(float a, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile float r = __builtin_sqrtf(a);
+    fesetround(FE_TONEAREST);
+    return r;
+}
+/* double -> float conversion rounded down (up = 0) or up (up = 1). */
+static NOINL float f_conv(double a, int up) {
+    fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    volatile float r = (float)a;
+    fesetround(FE_TONEAREST);
+    return r;
+}
+
+/* Precision-generic wrappers.  In single precision (p = 1) every value held
+ * in a double is a float value, so the (float) casts below are exact. */
+static double R_add(double a, double b, int p, int up) {
+    return p ? (double)f_add((float)a, (float)b, up) : d_add(a, b, up);
+}
+static double R_sub(double a, double b, int p, int up) {
+    return p ? (double)f_sub((float)a, (float)b, up) : d_sub(a, b, up);
+}
+static double R_mul(double a, double b, int p, int up) {
+    /* closed interval system: 0 * (+-inf) = 0 */
+    if (a == 0.0 || b == 0.0) return 0.0;
+    return p ? (double)f_mul((float)a, (float)b, up) : d_mul(a, b, up);
+}
+static double R_div(double a, double b, int p, int up) {
+    return p ? (double)f_div((float)a, (float)b, up) : d_div(a, b, up);
+}
+static double R_sqrt(double a, int p, int up) {
+    return p ? (double)f_sqrt((float)a, up) : d_sqrt(a, up);
+}
+/* Outward conversion of an FP64 number into the working precision. */
+static double R_in(double a, int p, int up) {
+    return p ? (double)f_conv(a, up) : a;
+}
+/* Move x by k units in the last place toward -inf (up = 0) or +inf. */
+static double R_step(double x, int k, int p, int up) {
+    for (int i = 0; i < k; i++) {
+        if (p) x = (double)nextafterf((float)x, up ? INFINITY : -INFINITY);
+        else   x = nextafter(x, up ? INFINITY : -INFINITY);
+    }
+    return x;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Intervals                                                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct { double lo, hi; } iv;
+
+static iv mk(double lo, double hi) { iv r = {lo, hi}; return r; }
+static iv entire(void) { return mk(-INFINITY, INFINITY); }
+
+/* Eq. 3 */
+static iv iv_add(iv x, iv y, int p) {
+    return mk(R_add(x.lo, y.lo, p, 0), R_add(x.hi, y.hi, p, 1));
+}
+/* Eq. 4 */
+static iv iv_sub(iv x, iv y, int p) {
+    return mk(R_sub(x.lo, y.hi, p, 0), R_sub(x.hi, y.lo, p, 1));
+}
+/* Eq. 5: min / max of the four endpoint products, each rounded outward. */
+static iv iv_mul(iv x, iv y, int p) {
+    double l1 = R_mul(x.lo, y.lo, p, 0), l2 = R_mul(x.lo, y.hi, p, 0);
+    double l3 = R_mul(x.hi, y.lo, p, 0), l4 = R_mul(x.hi, y.hi, p, 0);
+    double h1 = R_mul(x.lo, y.lo, p, 1), h2 = R_mul(x.lo, y.hi, p, 1);
+    double h3 = R_mul(x.hi, y.lo, p, 1), h4 = R_mul(x.hi, y.hi, p, 1);
+    return mk(fmin(fmin(l1, l2), fmin(l3, l4)), fmax(fmax(h1, h2), fmax(h3, h4)));
+}
+/* 1/[y] for Eq. 6.  Reading: when 0 lies in [y] the result is the whole
+ * real line (rigorous; the paper does not treat this case). */
+static iv iv_recip(iv y, int p) {
+    if (y.lo > 0.0 || y.hi < 0.0)
+        return mk(R_div(1.0, y.hi, p, 0), R_div(1.0, y.lo, p, 1));
+    return entire();
+}
+/* Eq. 6: [x]/[y] = [x] * (1/[y]). */
+static iv iv_div(iv x, iv y, int p) { return iv_mul(x, iv_recip(y, p), p); }
+
+static iv iv_neg(iv x) { return mk(-x.hi, -x.lo); }
+
+/* Square with the dependence of x*x removed (section 2.1 names the
+ * dependence problem; the paper does not define sqr itself). */
+static iv iv_sqr(iv x, int p) {
+    if (x.lo >= 0.0) return mk(R_mul(x.lo, x.lo, p, 0), R_mul(x.hi, x.hi, p, 1));
+    if (x.hi <= 0.0) return mk(R_mul(x.hi, x.hi, p, 0), R_mul(x.lo, x.lo, p, 1));
+    return mk(0.0, fmax(R_mul(x.lo, x.lo, p, 1), R_mul(x.hi, x.hi, p, 1)));
+}
+
+/* sqrt restricted to its domain x >= 0; IEEE sqrt is correctly rounded in
+ * each direction. */
+static iv iv_sqrt(iv x, int p) {
+    return mk(R_sqrt(fmax(x.lo, 0.0), p, 0), R_sqrt(fmax(x.hi, 0.0), p, 1));
+}
+
+/* Multiplication by a point constant c (exact FP64 in the problem data). */
+static iv iv_scale(iv x, double c, int p) {
+    if (p) {
+        iv cc = mk(R_in(c, 1, 0), R_in(c, 1, 1));
+        return iv_mul(x, cc, 1);
+    }
+    if (c == 0.0) return mk(0.0, 0.0);
+    if (c > 0.0) return mk(R_mul(x.lo, c, 0, 0), R_mul(x.hi, c, 0, 1));
+    return mk(R_mul(x.hi, c, 0, 0), R_mul(x.lo, c, 0, 1));
+}
+
+/* Transcendentals.  libm is called in round-to-nearest and the result is
+ * widened by K_WIDEN units in the last place in each direction: glibc
+ * documents at most 1 ulp of error for exp, sin and cos in both precisions,
+ * and one more ulp is added as margin.  The paper is silent on how it rounds
+ * transcendental functions (section 2.1 only defines outward rounding). */
+#define K_WIDEN 2
+
+static double PI_LO, PI_HI, E_LO, E_HI;      /* adjacent doubles around pi, e */
+
+static void init_constants(void) {
+    /* 0x400921FB54442D18 is the double nearest pi and lies below pi;
+       0x4005BF0A8B145769 is the double nearest e and lies below e. */
+    union { uint64_t u; double d; } v;
+    v.u = 0x400921FB54442D18ull; PI_LO = v.d; PI_HI = nextafter(PI_LO, INFINITY);
+    v.u = 0x4005BF0A8B145769ull; E_LO = v.d;  E_HI = nextafter(E_LO, INFINITY);
+}
+
+static iv const_pi(int p) { return mk(R_in(PI_LO, p, 0), R_in(PI_HI, p, 1)); }
+static iv const_e(int p) { return mk(R_in(E_LO, p, 0), R_in(E_HI, p, 1)); }
+
+static double lm_exp(double x, int p) { return p ? (double)expf((float)x) : exp(x); }
+static double lm_cos(double x, int p) { return p ? (double)cosf((float)x) : cos(x); }
+static double lm_sin(double x, int p) { return p ? (double)sinf((float)x) : sin(x); }
+
+static iv iv_exp(iv x, int p) {
+    double lo = R_step(lm_exp(x.lo, p), K_WIDEN, p, 0);
+    double hi = R_step(lm_exp(x.hi, p), K_WIDEN, p, 1);
+    if (lo < 0.0) lo = 0.0;
+    return mk(lo, hi);
+}
+
+static int is_even(double k) { return fmod(k, 2.0) == 0.0; }
+
+/* Interval cosine (cos_not_sin = 1) or sine.  Endpoint values widened as
+ * above; an extremum +-1 is included whenever a critical point may lie in
+ * [x] according to an outward enclosure of x/pi; wide or huge arguments
+ * give [-1, 1]. */
+static iv iv_trig(iv x, int p, int cos_not_sin) {
+    double big = p ? 1048576.0 : 1099511627776.0; /* 2^20 / 2^40 */
+    iv pi = const_pi(p);
+    double w = R_sub(x.hi, x.lo, p, 1);
+    double two_pi_lo = pi.lo * 2.0;
+    if (!(w < two_pi_lo) || !(fabs(x.lo) <= big) || !(fabs(x.hi) <= big))
+        return mk(-1.0, 1.0);
+    double va = cos_not_sin ? lm_cos(x.lo, p) : lm_sin(x.lo, p);
+    double vb = cos_not_sin ? lm_cos(x.hi, p) : lm_sin(x.hi, p);
+    double lo = fmin(R_step(va, K_WIDEN, p, 0), R_step(vb, K_WIDEN, p, 0));
+    double hi = fmax(R_step(va, K_WIDEN, p, 1), R_step(vb, K_WIDEN, p, 1));
+    /* enclosure [qlo, qhi] of {x/pi}: divide by the pi bound that makes the
+       quotient smaller (for qlo) or larger (for qhi) */
+    double qlo = R_div(x.lo, x.lo >= 0.0 ? pi.hi : pi.lo, p, 0);
+    double qhi = R_div(x.hi, x.hi >= 0.0 ? pi.lo : pi.hi, p, 1);
+    if (!cos_not_sin) {            /* sin extrema at (k + 1/2) pi */
+        qlo = R_sub(qlo, 0.5, p, 0);
+        qhi = R_sub(qhi, 0.5, p, 1);
+    }
+    double k0 = ceil(qlo), k1 = floor(qhi);
+    if (k0 <= k1) {
+        int has_even = is_even(k0) || k0 + 1.0 <= k1;
+        int has_odd = !is_even(k0) || k0 + 1.0 <= k1;
+        if (has_even) hi = 1.0;    /* cos(2k pi) = 1, sin((2k+1/2) pi) = 1 */
+        if (has_odd) lo = -1.0;
+    }
+    if (lo < -1.0) lo = -1.0;
+    if (hi > 1.0) hi = 1.0;
+    return mk(lo, hi);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Objective DAG (input format; 32-byte nodes)                               */
+/* ------------------------------------------------------------------------ */
+enum {
+    O_CONST = 0, O_PI = 1, O_EULER = 2, O_VAR = 3, O_IDX_VAR = 4, O_IDX_COEF = 5,
+    O_ADD = 6, O_SUB = 7, O_MUL = 8, O_DIV = 9, O_NEG = 10, O_SQR = 11,
+    O_SQRT = 12, O_EXP = 13, O_SIN = 14, O_COS = 15, O_SCALE = 16, O_ISUM = 17,
+    O_COUNT = 18
+};
+
+typedef struct { int32_t op, a, b, c, d, pad; double v; } onode;
+
+static int n_operands(int op) {
+    switch (op) {
+    case O_ADD: case O_SUB: case O_MUL: case O_DIV: return 2;
+    case O_NEG: case O_SQR: case O_SQRT: case O_EXP: case O_SIN: case O_COS:
+    case O_SCALE: return 1;
+    default: return 0;
+    }
+}
+
+typedef struct {
+    int n, nn, root, B, nb;
+    onode* nd;
+    int ntab;
+    double** tab;
+    int64_t* tlen;
+    double *l, *u;
+    /* structure derived from the DAG */
+    char* outer;          /* node reachable from root outside any template */
+    char* in_tmpl;        /* scratch for template membership */
+    int n_isum;           /* ISUM nodes on the outer side, ascending */
+    int* isum_node;
+    int** tmpl_nodes;     /* per ISUM: template nodes ascending */
+    int* tmpl_count;
+    int* off_min;         /* per ISUM: min / max IDX_VAR offset */
+    int* off_max;
+    int* has_var;         /* per ISUM: template contains IDX_VAR */
+    /* scratch */
+    iv *val, *adj, *tval, *tadj, *terms, *groups, *gsum, *dacc;
+    char* touched;
+    int max_terms;
+} oprob;
+
+static int isum_count(const onode* s) {
+    if (s->c <= s->b) return 0;
+    return (s->c - s->b + s->d - 1) / s->d;
+}
+
+/* mark template nodes reachable from r into mark[]; fail on VAR / ISUM */
+static int mark_template(const oprob* P, int r, char* mark) {
+    if (mark[r]) return 0;
+    mark[r] = 1;
+    const onode* q = &P->nd[r];
+    if (q->op == O_VAR || q->op == O_ISUM) return 1;
+    int k = n_operands(q->op);
+    if (k >= 1 && mark_template(P, q->a, mark)) return 1;
+    if (k >= 2 && mark_template(P, q->b, mark)) return 1;
+    return 0;
+}
+
+static int mark_outer(const oprob* P, int r) {
+    if (P->outer[r]) return 0;
+    P->outer[r] = 1;
+    const onode* q = &P->nd[r];
+    if (q->op == O_IDX_VAR || q->op == O_IDX_COEF) return 1;
+    if (q->op == O_ISUM) return 0;           /* template handled separately */
+    int k = n_operands(q->op);
+    if (k >= 1 && mark_outer(P, q->a)) return 1;
+    if (k >= 2 && mark_outer(P, q->b)) return 1;
+    return 0;
+}
+
+static void free_prob(oprob* P) {
+    if (!P) return;
+    if (P->tab) for (int t = 0; t < P->ntab; t++) free(P->tab[t]);
+    free(P->tab); free(P->tlen); free(P->nd); free(P->l); free(P->u);
+    free(P->outer); free(P->in_tmpl); free(P->isum_node);
+    if (P->tmpl_nodes) for (int k = 0; k < P->n_isum; k++) free(P->tmpl_nodes[k]);
+    free(P->tmpl_nodes); free(P->tmpl_count); free(P->off_min); free(P->off_max);
+    free(P->has_var);
+    free(P->val); free(P->adj); free(P->tval); free(P->tadj); free(P->terms);
+    free(P->groups); free(P->gsum); free(P->dacc); free(P->touched);
+    free(P);
+}
+
+/* Copies and validates the problem (Eqs. 1-2: objective and simple bounds;
+ * l < u finite).  Returns NULL on invalid input. */
+static oprob* make_prob(const void* nodes, int nn, int root, const double* const* tables,
+                        const int64_t* tlen, int ntab, int n, const double* l,
+                        const double* u, int B) {
+    init_constants();
+    if (nn < 1 || root < 0 || root >= nn || n < 1 || ntab < 0 || B < 1 || B > n) return NULL;
+    oprob* P = (oprob*)calloc(1, sizeof(oprob));
+    P->n = n; P->nn = nn; P->root = root; P->B = B; P->nb = (n + B - 1) / B;
+    P->nd = (onode*)malloc(sizeof(onode) * nn);
+    memcpy(P->nd, nodes, sizeof(onode) * nn);
+    P->ntab = ntab;
+    P->tab = (double**)calloc(ntab > 0 ? ntab : 1, sizeof(double*));
+    P->tlen = (int64_t*)calloc(ntab > 0 ? ntab : 1, sizeof(int64_t));
+    for (int t = 0; t < ntab; t++) {
+        if (tlen[t] < 0) { free_prob(P); return NULL; }
+        P->tlen[t] = tlen[t];
+        P->tab[t] = (double*)malloc(sizeof(double) * (tlen[t] > 0 ? tlen[t] : 1));
+        memcpy(P->tab[t], tables[t], sizeof(double) * tlen[t]);
+        for (int64_t i = 0; i < tlen[t]; i++)
+            if (!isfinite(P->tab[t][i])) { free_prob(P); return NULL; }
+    }
+    P->l = (double*)malloc(sizeof(double) * n);
+    P->u = (double*)malloc(sizeof(double) * n);
+    for (int j = 0; j < n; j++) {
+        P->l[j] = l[j]; P->u[j] = u[j];
+        if (!isfinite(l[j]) || !isfinite(u[j]) || !(l[j] < u[j]) || !isfinite(u[j] - l[j])) {
+            free_prob(P); return NULL;
+        }
+    }
+    /* node-level checks: op range, topological operands */
+    for (int v = 0; v < nn; v++) {
+        const onode* q = &P->nd[v];
+        if (q->op < 0 || q->op >= O_COUNT) { free_prob(P); return NULL; }
+        int k = n_operands(q->op);
+        if (k >= 1 && (q->a < 0 || q->a >= v)) { free_prob(P); return NULL; }
+        if (k >= 2 && (q->b < 0 || q->b >= v)) { free_prob(P); return NULL; }
+        if ((q->op == O_CONST || q->op == O_SCALE) && !isfinite(q->v)) { free_prob(P); return NULL; }
+        if (q->op == O_VAR && (q->a < 0 || q->a >= n)) { free_prob(P); return NULL; }
+        if (q->op == O_ISUM && (q->a < 0 || q->a >= v || q->d < 1)) { free_prob(P); return NULL; }
+    }
+    P->outer = (char*)calloc(nn, 1);
+    P->in_tmpl = (char*)calloc(nn, 1);
+    if (mark_outer(P, root)) { free_prob(P); return NULL; }
+    /* ISUM nodes and their templates */
+    P->isum_node = (int*)malloc(sizeof(int) * nn);
+    P->tmpl_nodes = (int**)calloc(nn, sizeof(int*));
+    P->tmpl_count = (int*)calloc(nn, sizeof(int));
+    P->off_min = (int*)calloc(nn, sizeof(int));
+    P->off_max = (int*)calloc(nn, sizeof(int));
+    P->has_var = (int*)calloc(nn, sizeof(int));
+    int max_terms = 1;
+    for (int v = 0; v < nn; v++) {
+        if (!P->outer[v] || P->nd[v].op != O_ISUM) continue;
+        int k = P->n_isum++;
+        P->isum_node[k] = v;
+        const onode* s = &P->nd[v];
+        memset(P->in_tmpl, 0, nn);
+        if (mark_template(P, s->a, P->in_tmpl)) { free_prob(P); return NULL; }
+        int cnt = 0;
+        for (int t = 0; t <= s->a; t++) cnt += P->in_tmpl[t];
+        P->tmpl_nodes[k] = (int*)malloc(sizeof(int) * cnt);
+        P->tmpl_count[k] = cnt;
+        cnt = 0;
+        int omin = 0, omax = 0, hv = 0;
+        for (int t = 0; t <= s->a; t++) {
+            if (!P->in_tmpl[t]) continue;
+            P->tmpl_nodes[k][cnt++] = t;
+            if (P->nd[t].op == O_IDX_VAR) {
+                int off = P->nd[t].b;
+                if (!hv) { omin = omax = off; hv = 1; }
+                if (off < omin) omin = off;
+                if (off > omax) omax = off;
+            }
+        }
+        P->off_min[k] = omin; P->off_max[k] = omax; P->has_var[k] = hv;
+        int count = isum_count(s);
+        if (count > max_terms) max_terms = count;
+        if (count > 0) {
+            int64_t ifirst = s->b, ilast = (int64_t)s->b + (int64_t)(count - 1) * s->d;
+            if (hv && (ifirst + omin < 0 || ilast + omax >= n)) { free_prob(P); return NULL; }
+            for (int t = 0; t < cnt; t++) {
+                const onode* q = &P->nd[P->tmpl_nodes[k][t]];
+                if (q->op == O_IDX_COEF) {
+                    if (q->a < 0 || q->a >= ntab) { free_prob(P); return NULL; }
+                    if (ifirst + q->b < 0 || ilast + q->b >= P->tlen[q->a]) { free_prob(P); return NULL; }
+                }
+            }
+        }
+    }
+    P->max_terms = max_terms;
+    P->val = (iv*)calloc(nn, sizeof(iv));
+    P->adj = (iv*)calloc(nn, sizeof(iv));
+    P->tval = (iv*)calloc(nn, sizeof(iv));
+    P->tadj = (iv*)calloc(nn, sizeof(iv));
+    P->terms = (iv*)calloc(max_terms, sizeof(iv));
+    P->groups = (iv*)calloc(max_terms, sizeof(iv));
+    P->gsum = (iv*)calloc(max_terms, sizeof(iv));
+    P->dacc = (iv*)calloc(B, sizeof(iv));
+    P->touched = (char*)calloc(B, 1);
+    return P;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Evaluation                                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct { const double *lo, *hi; } obox;
+
+/* one node's forward value; i = ISUM index (templates), vals = value array */
+static iv node_value(const oprob* P, int v, int i, obox X, int p, const iv* vals) {
+    const onode* q = &P->nd[v];
+    switch (q->op) {
+    case O_CONST: return mk(R_in(q->v, p, 0), R_in(q->v, p, 1));
+    case O_PI: return const_pi(p);
+    case O_EULER: return const_e(p);
+    case O_VAR: return mk(R_in(X.lo[q->a], p, 0), R_in(X.hi[q->a], p, 1));
+    case O_IDX_VAR: return mk(R_in(X.lo[i + q->b], p, 0), R_in(X.hi[i + q->b], p, 1));
+    case O_IDX_COEF: {
+        double c = P->tab[q->a][i + q->b];
+        return mk(R_in(c, p, 0), R_in(c, p, 1));
+    }
+    case O_ADD: return iv_add(vals[q->a], vals[q->b], p);
+    case O_SUB: return iv_sub(vals[q->a], vals[q->b], p);
+    case O_MUL: return iv_mul(vals[q->a], vals[q->b], p);
+    case O_DIV: return iv_div(vals[q->a], vals[q->b], p);
+    case O_NEG: return iv_neg(vals[q->a]);
+    case O_SQR: return iv_sqr(vals[q->a], p);
+    case O_SQRT: return iv_sqrt(vals[q->a], p);
+    case O_EXP: return iv_exp(vals[q->a], p);
+    case O_SIN: return iv_trig(vals[q->a], p, 0);
+    case O_COS: return iv_trig(vals[q->a], p, 1);
+    case O_SCALE: return iv_scale(vals[q->a], q->v, p);
+    default: return entire();
+    }
+}
+
+/* Reverse-mode step: adds node v's contributions to its operands' adjoints
+ * (first operand a, then b).  Because v runs from high to low index, each
+ * adjoint receives its consumers' contributions in descending consumer order,
+ * starting from [0, 0].  The derivative formulas are the natural interval
+ * extensions of d(op)/d(operand). */
+static void push_adjoint(const oprob* P, int v, int p, const iv* vals, iv* adj) {
+    const onode* q = &P->nd[v];
+    iv g = adj[v];
+    switch (q->op) {
+    case O_ADD:
+        adj[q->a] = iv_add(adj[q->a], g, p);
+        adj[q->b] = iv_add(adj[q->b], g, p);
+        break;
+    case O_SUB:
+        adj[q->a] = iv_add(adj[q->a], g, p);
+        adj[q->b] = iv_add(adj[q->b], iv_neg(g), p);
+        break;
+    case O_MUL:
+        adj[q->a] = iv_add(adj[q->a], iv_mul(g, vals[q->b], p), p);
+        adj[q->b] = iv_add(adj[q->b], iv_mul(g, vals[q->a], p), p);
+        break;
+    case O_DIV: {
+        iv rb = iv_recip(vals[q->b], p);
+        adj[q->a] = iv_add(adj[q->a], iv_mul(g, rb, p), p);
+        adj[q->b] = iv_add(adj[q->b], iv_mul(g, iv_neg(iv_mul(vals[v], rb, p)), p), p);
+        break;
+    }
+    case O_NEG:
+        adj[q->a] = iv_add(adj[q->a], iv_neg(g), p);
+        break;
+    case O_SQR:
+        adj[q->a] = iv_add(adj[q->a], iv_mul(g, iv_scale(vals[q->a], 2.0, p), p), p);
+        break;
+    case O_SQRT:
+        adj[q->a] = iv_add(adj[q->a], iv_mul(g, iv_scale(iv_recip(vals[v], p), 0.5, p), p), p);
+        break;
+    case O_EXP:
+        adj[q->a] = iv_add(adj[q->a], iv_mul(g, vals[v], p), p);
+        break;
+    case O_SIN:
+        adj[q->a] = iv_add(adj[q->a], iv_mul(g, iv_trig(vals[q->a], p, 1), p), p);
+        break;
+    case O_COS:
+        adj[q->a] = iv_add(adj[q->a], iv_mul(g, iv_neg(iv_trig(vals[q->a], p, 0)), p), p);
+        break;
+    case O_SCALE:
+        adj[q->a] = iv_add(adj[q->a], iv_scale(g, q->v, p), p);
+        break;
+    default:
+        break;
+    }
+}
+
+/* Pairwise reduction tree over a[0..m) in index order, in place:
+ * level s = 1, 2, 4, ...: a[i] += a[i + s] for i = 0, 2s, 4s, ... while
+ * i + s < m.  Reading: the paper does not fix a summation order; this one is
+ * fixed so that every implementation produces the same bits. */
+static iv tree_sum(iv* a, int m, int p) {
+    if (m == 0) return mk(0.0, 0.0);
+    for (int s = 1; s < m; s *= 2)
+        for (int i = 0; i + s < m; i += 2 * s) a[i] = iv_add(a[i], a[i + s], p);
+    return a[0];
+}
+
+/* Evaluates template k (ISUM node index isum_node[k]) for index i; values
+ * in P->tval, returns the root value. */
+static iv eval_term(oprob* P, int k, int i, obox X, int p) {
+    for (int t = 0; t < P->tmpl_count[k]; t++) {
+        int v = P->tmpl_nodes[k][t];
+        P->tval[v] = node_value(P, v, i, X, p, P->tval);
+    }
+    return P->tval[P->nd[P->isum_node[k]].a];
+}
+
+/* Block range [bmin, bmax] of the coordinates term i of ISUM k touches. */
+static void term_blocks(const oprob* P, int k, int i, int* bmin, int* bmax) {
+    if (!P->has_var[k]) { *bmin = *bmax = -1; return; }
+    *bmin = (i + P->off_min[k]) / P->B;
+    *bmax = (i + P->off_max[k]) / P->B;
+}
+
+/* ISUM value: terms in index order are grouped into maximal runs with the
+ * same touched-block range; each group is reduced by tree_sum, then the
+ * groups (in order) by tree_sum again. */
+static iv isum_value(oprob* P, int k, obox X, int p) {
+    const onode* s = &P->nd[P->isum_node[k]];
+    int cnt = isum_count(s);
+    if (cnt == 0) return mk(0.0, 0.0);
+    for (int q = 0; q < cnt; q++) P->terms[q] = eval_term(P, k, s->b + q * s->d, X, p);
+    int ng = 0, start = 0;
+    for (int q = 1; q <= cnt; q++) {
+        int b0, b1, c0, c1;
+        term_blocks(P, k, s->b + start * s->d, &b0, &b1);
+        int boundary = (q == cnt);
+        if (!boundary) {
+            term_blocks(P, k, s->b + q * s->d, &c0, &c1);
+            boundary = (c0 != b0 || c1 != b1);
+        }
+        if (boundary) {
+            for (int r = start; r < q; r++) P->groups[r - start] = P->terms[r];
+            P->gsum[ng++] = tree_sum(P->groups, q - start, p);
+            start = q;
+        }
+    }
+    return tree_sum(P->gsum, ng, p);
+}
+
+/* Forward pass of the outer expression; returns F(X). */
+static iv eval_outer(oprob* P, obox X, int p) {
+    int k = 0;
+    for (int v = 0; v < P->nn; v++) {
+        if (!P->outer[v]) continue;
+        if (P->nd[v].op == O_ISUM) {
+            while (P->isum_node[k] != v) k++;
+            P->val[v] = isum_value(P, k, X, p);
+        } else {
+            P->val[v] = node_value(P, v, -1, X, p, P->val);
+        }
+    }
+    return P->val[P->root];
+}
+
+/* Interval partials of f for the coordinates of block blk (section 3.1's
+ * first-order test needs [DLB_i, DUB_i]).  Reading: reverse-mode interval
+ * adjoints; for coordinate j the sum runs over the outer VAR(j) leaves
+ * (ascending node), then over the ISUM nodes (ascending) of
+ * adj(ISUM) * D_j, where D_j sums the template adjoints (seeded with [1,1])
+ * of the IDX_VAR leaves that hit x_j, in ascending term index and ascending
+ * leaf node.  Requires eval_outer(X) to have run.  G has B entries. */
+static void block_partials(oprob* P, obox X, int p, int blk, iv* G, int* width) {
+    int c0 = blk * P->B, c1 = c0 + P->B;
+    if (c1 > P->n) c1 = P->n;
+    *width = c1 - c0;
+    for (int v = 0; v < P->nn; v++) P->adj[v] = mk(0.0, 0.0);
+    P->adj[P->root] = mk(1.0, 1.0);
+    for (int v = P->nn - 1; v >= 0; v--) {
+        if (!P->outer[v] || P->nd[v].op == O_ISUM) continue;
+        push_adjoint(P, v, p, P->val, P->adj);
+    }
+    for (int j = c0; j < c1; j++) G[j - c0] = mk(0.0, 0.0);
+    for (int v = 0; v < P->nn; v++)
+        if (P->outer[v] && P->nd[v].op == O_VAR && P->nd[v].a >= c0 && P->nd[v].a < c1)
+            G[P->nd[v].a - c0] = iv_add(G[P->nd[v].a - c0], P->adj[v], p);
+    for (int k = 0; k < P->n_isum; k++) {
+        if (!P->has_var[k]) continue;
+        const onode* s = &P->nd[P->isum_node[k]];
+        int cnt = isum_count(s);
+        for (int j = c0; j < c1; j++) { P->dacc[j - c0] = mk(0.0, 0.0); P->touched[j - c0] = 0; }
+        for (int q = 0; q < cnt; q++) {
+            int i = s->b + q * s->d;
+            if (i + P->off_max[k] < c0 || i + P->off_min[k] >= c1) continue;
+            eval_term(P, k, i, X, p);
+            int troot = s->a;
+            for (int t = 0; t < P->tmpl_count[k]; t++) P->tadj[P->tmpl_nodes[k][t]] = mk(0.0, 0.0);
+            P->tadj[troot] = mk(1.0, 1.0);
+            for (int t = P->tmpl_count[k] - 1; t >= 0; t--)
+                push_adjoint(P, P->tmpl_nodes[k][t], p, P->tval, P->tadj);
+            for (int t = 0; t < P->tmpl_count[k]; t++) {
+                const onode* leaf = &P->nd[P->tmpl_nodes[k][t]];
+                if (leaf->op != O_IDX_VAR) continue;
+                int j = i + leaf->b;
+                if (j < c0 || j >= c1) continue;
+                P->dacc[j - c0] = iv_add(P->dacc[j - c0], P->tadj[P->tmpl_nodes[k][t]], p);
+                P->touched[j - c0] = 1;
+            }
+        }
+        for (int j = c0; j < c1; j++)
+            if (P->touched[j - c0])
+                G[j - c0] = iv_add(G[j - c0], iv_mul(P->adj[P->isum_node[k]], P->dacc[j - c0], p), p);
+    }
+}
+
+/* First-order test of section 3.1: the box is ruled out if some tested
+ * partial has DLB > 0 while its lower face is not on l, or DUB < 0 while
+ * its upper face is not on u.  Reading: the tested coordinates are those of
+ * the box's active cycling block. */
+static int mono_test(const oprob* P, obox X, int blk, const iv* G, int width) {
+    int c0 = blk * P->B;
+    for (int t = 0; t < width; t++) {
+        int j = c0 + t;
+        if (G[t].lo > 0.0 && X.lo[j] != P->l[j]) return 1;
+        if (G[t].hi < 0.0 && X.hi[j] != P->u[j]) return 1;
+    }
+    return 0;
+}
+
+/* Midpoint sample point (section 3.1 allows any sampling strategy; reading:
+ * one point per box, mid = RN(0.5 lo + 0.5 hi)). */
+static double midpoint(double lo, double hi) {
+    volatile double a = 0.5 * lo;
+    volatile double b = 0.5 * hi;
+    return a + b;
+}
+
+static double canon_lo(double x) {
+    if (isnan(x)) return -INFINITY;
+    if (x == 0.0) return 0.0;
+    return x;
+}
+
+static uint64_t order_key(double x) {
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported: problem handle, single-box evaluation, reduction-tree hook      */
+/* ------------------------------------------------------------------------ */
+void* oracle_create(const void* nodes, int nn, int root, const double* const* tables,
+                    const int64_t* tlen, int ntab, int n, const double* l, const double* u,
+                    int block) {
+    return make_prob(nodes, nn, root, tables, tlen, ntab, n, l, u, block);
+}
+
+void oracle_destroy(void* h) { free_prob((oprob*)h); }
+
+int oracle_n_blocks(void* h) { return ((oprob*)h)->nb; }
+
+/* Evaluates one box: F(X) (2 doubles), the midpoint sample F([m, m]) (2),
+ * the partials of block blk (2 * B doubles, unused tail left as is) and the
+ * monotonicity verdict.  p = 1 evaluates in single precision (the box is
+ * widened outward to floats first).  blk < 0 skips the partials. */
+int oracle_eval_box(void* h, const double* lo, const double* hi, int p, int blk,
+                    double* F, double* Fmid, double* G, int32_t* mono) {
+    oprob* P = (oprob*)h;
+    obox X = {lo, hi};
+    iv f = eval_outer(P, X, p);
+    F[0] = f.lo; F[1] = f.hi;
+    if (blk >= 0) {
+        iv* g = (iv*)malloc(sizeof(iv) * P->B);
+        int width = 0;
+        block_partials(P, X, p, blk, g, &width);
+        for (int t = 0; t < width; t++) { G[2 * t] = g[t].lo; G[2 * t + 1] = g[t].hi; }
+        *mono = mono_test(P, X, blk, g, width);
+        free(g);
+    }
+    double* m = (double*)malloc(sizeof(double) * P->n);
+    for (int j = 0; j < P->n; j++) m[j] = midpoint(lo[j], hi[j]);
+    obox M = {m, m};
+    iv fm = eval_outer(P, M, 0);
+    Fmid[0] = fm.lo; Fmid[1] = fm.hi;
+    free(m);
+    return 0;
+}
+
+/* Single interval operation, for pinning the arithmetic against an
+ * independent multiprecision library.  op uses the node codes; c is the
+ * SCALE factor. */
+int oracle_iv_op(int op, const double* x, const double* y, double c, int p, double* out) {
+    init_constants();
+    iv a = mk(x[0], x[1]), b = mk(y[0], y[1]), r;
+    switch (op) {
+    case O_ADD: r = iv_add(a, b, p); break;
+    case O_SUB: r = iv_sub(a, b, p); break;
+    case O_MUL: r = iv_mul(a, b, p); break;
+    case O_DIV: r = iv_div(a, b, p); break;
+    case O_NEG: r = iv_neg(a); break;
+    case O_SQR: r = iv_sqr(a, p); break;
+    case O_SQRT: r = iv_sqrt(a, p); break;
+    case O_EXP: r = iv_exp(a, p); break;
+    case O_SIN: r = iv_trig(a, p, 0); break;
+    case O_COS: r = iv_trig(a, p, 1); break;
+    case O_SCALE: r = iv_scale(a, c, p); break;
+    case O_PI: r = const_pi(p); break;
+    case O_EULER: r = const_e(p); break;
+    default: return 1;
+    }
+    out[0] = r.lo; out[1] = r.hi;
+    return 0;
+}
+
+int oracle_tree_sum(const double* lo, const double* hi, int m, int p, double* out) {
+    iv* a = (iv*)malloc(sizeof(iv) * (m > 0 ? m : 1));
+    for (int i = 0; i < m; i++) a[i] = mk(lo[i], hi[i]);
+    iv r = tree_sum(a, m, p);
+    out[0] = r.lo; out[1] = r.hi;
+    free(a);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Branch and bound (section 3.1 flowchart, section 3.2 variable cycling)    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double tol_f, tol_x;
+    int32_t split_m, split_d, fp32, pad;
+    int64_t max_gen, max_parents, cap;
+} oopts;
+
+typedef struct {
+    double glb, gub;
+    int64_t n_boxes;
+    double *box_lo, *box_hi, *box_flo;
+    int32_t* box_cyc;
+    int64_t generations, evals32, evals64, mids;
+    int32_t status, pad;
+    int64_t n_trace;
+    int64_t *tr_parents, *tr_children, *tr_kept32, *tr_kept, *tr_pool;
+    double* tr_gub;
+} oresult;
+
+enum { ST_OK = 0, ST_INVALID = 1, ST_CAPACITY = 3, ST_LIMIT = 4 };
+
+typedef struct {
+    double *lo, *hi;        /* n each */
+    double flo;
+    int32_t cyc, fin, blk;  /* cycling position, final flag, block split last */
+} entry;
+
+typedef struct { entry* e; int64_t len, cap; } elist;
+
+static void el_push(elist* L, entry x) {
+    if (L->len == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 64;
+        L->e = (entry*)realloc(L->e, sizeof(entry) * L->cap);
+    }
+    L->e[L->len++] = x;
+}
+static void ent_free(entry* x) { free(x->lo); free(x->hi); }
+
+static int cmp_u64(const void* a, const void* b) {
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static void trace_push(oresult* R, int64_t* cap, int64_t par, int64_t ch, int64_t k32,
+                       int64_t k, double gub, int64_t pool) {
+    if (R->n_trace == *cap) {
+        *cap = *cap ? 2 * *cap : 64;
+        R->tr_parents = (int64_t*)realloc(R->tr_parents, sizeof(int64_t) * *cap);
+        R->tr_children = (int64_t*)realloc(R->tr_children, sizeof(int64_t) * *cap);
+        R->tr_kept32 = (int64_t*)realloc(R->tr_kept32, sizeof(int64_t) * *cap);
+        R->tr_kept = (int64_t*)realloc(R->tr_kept, sizeof(int64_t) * *cap);
+        R->tr_pool = (int64_t*)realloc(R->tr_pool, sizeof(int64_t) * *cap);
+        R->tr_gub = (double*)realloc(R->tr_gub, sizeof(double) * *cap);
+    }
+    int64_t t = R->n_trace++;
+    R->tr_parents[t] = par; R->tr_children[t] = ch; R->tr_kept32[t] = k32;
+    R->tr_kept[t] = k; R->tr_gub[t] = gub; R->tr_pool[t] = pool;
+}
+
+/* Child r of a box: the d' coordinates starting at the cycling position are
+ * each cut into m equal pieces (Eqs. 10-11).  Reading for the rounding of
+ * Eqs. 10-11: boundary t of [lo, hi] is RN(lo + RN(RN(RN(hi - lo) / m) * t)),
+ * with boundary 0 = lo and boundary m = hi exactly, so the pieces cover the
+ * parent.  Digit k of r (base m) picks the piece of coordinate cyc + k. */
+static double split_bound(double lo, double hi, int m, int t) {
+    if (t == 0) return lo;
+    if (t == m) return hi;
+    volatile double w = hi - lo;
+    volatile double q = w / (double)m;
+    volatile double s = q * (double)t;
+    volatile double r = lo + s;
+    return r;
+}
+
+int oracle_solve(void* h, const oopts* opt, oresult* R) {
+    oprob* P = (oprob*)h;
+    memset(R, 0, sizeof(*R));
+    const int n = P->n, B = P->B, m = opt->split_m, d = opt->split_d, f32 = opt->fp32;
+    if (!(m == 2 || m == 4) || d < 1 || d > B || opt->max_parents < 1 || opt->cap < 1 ||
+        !(opt->tol_f >= 0.0)) {
+        R->status = ST_INVALID;
+        return ST_INVALID;
+    }
+    int64_t tcap = 0;
+    iv* G = (iv*)malloc(sizeof(iv) * B);
+    double* mid = (double*)malloc(sizeof(double) * n);
+
+    /* initialisation: the whole domain (section 3.1) */
+    elist pool = {0}, par = {0}, kids = {0}, keep = {0};
+    entry root;
+    root.lo = (double*)malloc(sizeof(double) * n);
+    root.hi = (double*)malloc(sizeof(double) * n);
+    memcpy(root.lo, P->l, sizeof(double) * n);
+    memcpy(root.hi, P->u, sizeof(double) * n);
+    obox X0 = {root.lo, root.hi};
+    iv f0 = eval_outer(P, X0, 0);
+    root.flo = canon_lo(f0.lo);
+    root.cyc = 0;
+    root.fin = 0;
+    for (int j = 0; j < n; j++) mid[j] = midpoint(root.lo[j], root.hi[j]);
+    obox M0 = {mid, mid};
+    double gub = eval_outer(P, M0, 0).hi;
+    if (isnan(gub)) gub = INFINITY;
+    R->evals64 = 1; R->mids = 1;
+    el_push(&pool, root);
+    int status = ST_OK;
+    int64_t gen = 0;
+
+    for (;;) {
+        /* remove suboptimal regions: LB > GUB (section 3.1) */
+        elist next = {0};
+        for (int64_t q = 0; q < pool.len; q++) {
+            if (pool.e[q].flo > gub) ent_free(&pool.e[q]);
+            else el_push(&next, pool.e[q]);
+        }
+        free(pool.e); pool = next;
+        double thr = d_sub(gub, opt->tol_f, 1);
+        int64_t n_act = 0;
+        for (int64_t q = 0; q < pool.len; q++)
+            if (pool.e[q].flo < thr && !pool.e[q].fin) n_act++;
+        if (n_act == 0) break;
+        if (gen >= opt->max_gen) { status = ST_LIMIT; break; }
+
+        /* best-first selection, batched: the max_parents active boxes with the
+           smallest lower bound; among equal lower bounds at the cut, the ones
+           placed last in the list (the most recently inserted) */
+        char* sel = (char*)calloc(pool.len, 1);
+        if (n_act <= opt->max_parents) {
+            for (int64_t q = 0; q < pool.len; q++)
+                sel[q] = pool.e[q].flo < thr && !pool.e[q].fin;
+        } else {
+            uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * n_act);
+            int64_t t = 0;
+            for (int64_t q = 0; q < pool.len; q++)
+                if (pool.e[q].flo < thr && !pool.e[q].fin) keys[t++] = order_key(pool.e[q].flo);
+            qsort(keys, n_act, sizeof(uint64_t), cmp_u64);
+            uint64_t T = keys[opt->max_parents - 1];
+            free(keys);
+            int64_t below = 0;
+            for (int64_t q = 0; q < pool.len; q++) {
+                int act = pool.e[q].flo < thr && !pool.e[q].fin;
+                if (act && order_key(pool.e[q].flo) < T) { sel[q] = 1; below++; }
+            }
+            int64_t need = opt->max_parents - below;
+            for (int64_t q = pool.len - 1; q >= 0 && need > 0; q--) {
+                int act = pool.e[q].flo < thr && !pool.e[q].fin;
+                if (act && order_key(pool.e[q].flo) == T) { sel[q] = 1; need--; }
+            }
+        }
+        par.len = 0;
+        next.e = NULL; next.len = next.cap = 0;
+        for (int64_t q = 0; q < pool.len; q++) {
+            if (sel[q]) el_push(&par, pool.e[q]);
+            else el_push(&next, pool.e[q]);
+        }
+        free(sel);
+        free(pool.e); pool = next;
+
+        /* partition each selected region (Eqs. 10-11, variable cycling) */
+        kids.len = 0;
+        for (int64_t q = 0; q < par.len; q++) {
+            const entry* pe = &par.e[q];
+            int c = pe->cyc, b = c / B;
+            int e = (b + 1) * B < n ? (b + 1) * B : n;
+            int dd = d < e - c ? d : e - c;
+            int64_t valid = 1;
+            for (int k = 0; k < dd; k++) valid *= m;
+            for (int64_t r = 0; r < valid; r++) {
+                entry ch;
+                ch.lo = (double*)malloc(sizeof(double) * n);
+                ch.hi = (double*)malloc(sizeof(double) * n);
+                memcpy(ch.lo, pe->lo, sizeof(double) * n);
+                memcpy(ch.hi, pe->hi, sizeof(double) * n);
+                int64_t rr = r;
+                for (int k = 0; k < dd; k++) {
+                    int dig = (int)(rr % m);
+                    rr /= m;
+                    int j = c + k;
+                    ch.lo[j] = split_bound(pe->lo[j], pe->hi[j], m, dig);
+                    ch.hi[j] = split_bound(pe->lo[j], pe->hi[j], m, dig + 1);
+                }
+                ch.cyc = (c + dd == n) ? 0 : c + dd;
+                ch.fin = 0;
+                ch.blk = b;
+                ch.flo = 0.0;
+                el_push(&kids, ch);
+            }
+        }
+
+        /* sample (GUB update) and rule out (cut-off and first-order test) */
+        double gub_prev = gub, gub_new = gub;
+        char* cand = (char*)malloc(kids.len ? kids.len : 1);
+        int64_t kept32 = kids.len;
+        if (f32) {
+            kept32 = 0;
+            for (int64_t q = 0; q < kids.len; q++) {
+                entry* ch = &kids.e[q];
+                obox X = {ch->lo, ch->hi};
+                iv f = eval_outer(P, X, 1);
+                int width;
+                block_partials(P, X, 1, ch->blk, G, &width);
+                int mono = mono_test(P, X, ch->blk, G, width);
+                cand[q] = !(f.lo > gub_prev) && !mono;
+                kept32 += cand[q];
+            }
+            R->evals32 += kids.len;
+        } else {
+            memset(cand, 1, kids.len);
+        }
+        for (int64_t q = 0; q < kids.len; q++) {
+            if (!cand[q]) continue;
+            entry* ch = &kids.e[q];
+            for (int j = 0; j < n; j++) mid[j] = midpoint(ch->lo[j], ch->hi[j]);
+            obox M = {mid, mid};
+            double fm = eval_outer(P, M, 0).hi;
+            if (fm < gub_new) gub_new = fm;
+            R->mids++;
+        }
+        keep.len = 0;
+        int64_t kept = 0;
+        for (int64_t q = 0; q < kids.len; q++) {
+            entry* ch = &kids.e[q];
+            int ok = 0;
+            if (cand[q]) {
+                obox X = {ch->lo, ch->hi};
+                iv f = eval_outer(P, X, 0);
+                R->evals64++;
+                int width;
+                block_partials(P, X, 0, ch->blk, G, &width);
+                int mono = mono_test(P, X, ch->blk, G, width);
+                ok = !(f.lo > gub_new) && !mono;
+                ch->flo = canon_lo(f.lo);
+            }
+            if (ok) {
+                int fin = 0;
+                if (opt->tol_x > 0.0) {
+                    fin = 1;
+                    for (int j = 0; j < n; j++)
+                        if (!(ch->hi[j] - ch->lo[j] < opt->tol_x)) { fin = 0; break; }
+                }
+                ch->fin = fin;
+                el_push(&keep, *ch);
+                kept++;
+            } else {
+                ent_free(ch);
+            }
+        }
+        free(cand);
+        /* capacity: boxes alive during the generation.  On overflow the
+           generation is abandoned: its children are dropped, its parents go
+           back to the end of the list, the samples' GUB is kept, and the
+           solve stops with the list still covering every unresolved region. */
+        if (pool.len + par.len + keep.len > opt->cap) {
+            for (int64_t q = 0; q < keep.len; q++) ent_free(&keep.e[q]);
+            keep.len = 0;
+            for (int64_t q = 0; q < par.len; q++) el_push(&pool, par.e[q]);
+            par.len = 0;
+            gub = gub_new;
+            status = ST_CAPACITY;
+            gen++;
+            trace_push(R, &tcap, 0, kids.len, kept32, kept, gub, pool.len);
+            break;
+        }
+        for (int64_t q = 0; q < par.len; q++) ent_free(&par.e[q]);
+        for (int64_t q = 0; q < keep.len; q++) el_push(&pool, keep.e[q]);
+        gub = gub_new;
+        gen++;
+        trace_push(R, &tcap, par.len, kids.len, kept32, kept, gub, pool.len);
+    }
+
+    /* output (section 3.1): regions with LB <= GUB, GLB = their smallest LB */
+    elist out = {0};
+    for (int64_t q = 0; q < pool.len; q++) {
+        if (pool.e[q].flo > gub) ent_free(&pool.e[q]);
+        else el_push(&out, pool.e[q]);
+    }
+    free(pool.e);
+    double glb = INFINITY;
+    for (int64_t q = 0; q < out.len; q++) if (out.e[q].flo < glb) glb = out.e[q].flo;
+    R->glb = glb;
+    R->gub = gub;
+    R->n_boxes = out.len;
+    R->box_lo = (double*)malloc(sizeof(double) * n * (out.len ? out.len : 1));
+    R->box_hi = (double*)malloc(sizeof(double) * n * (out.len ? out.len : 1));
+    R->box_flo = (double*)malloc(sizeof(double) * (out.len ? out.len : 1));
+    R->box_cyc = (int32_t*)malloc(sizeof(int32_t) * (out.len ? out.len : 1));
+    for (int64_t q = 0; q < out.len; q++) {
+        memcpy(R->box_lo + q * n, out.e[q].lo, sizeof(double) * n);
+        memcpy(R->box_hi + q * n, out.e[q].hi, sizeof(double) * n);
+        R->box_flo[q] = out.e[q].flo;
+        R->box_cyc[q] = out.e[q].cyc;
+        ent_free(&out.e[q]);
+    }
+    free(out.e); free(par.e); free(kids.e); free(keep.e);
+    free(G); free(mid);
+    R->generations = gen;
+    R->status = status;
+    return status;
+}
+
+void oracle_free_result(oresult* R) {
+    free(R->box_lo); free(R->box_hi); free(R->box_flo); free(R->box_cyc);
+    free(R->tr_parents); free(R->tr_children); free(R->tr_kept32); free(R->tr_kept);
+    free(R->tr_pool); free(R->tr_gub);
+    memset(R, 0, sizeof(*R));
+}

@@ -1,0 +1,237 @@
+"""Seeded synthetic minimisation problems with a planted global minimum.
+
+Every family is a sum of non-negative terms that vanish at a seeded point s,
+so min f = 0 is attained at x = s (the closed form that pins the solvers).
+Coefficients are drawn as FP64 from numpy's PCG64 generator; nothing here
+performs interval arithmetic or any step of the branch-and-bound method.
+
+Families (shapes follow the paper's benchmark families of SI Appendix A and D,
+shifted so the minimiser is planted):
+
+* ``sep_cos``  (C0): sum_i a_i (x_i-s_i)^2 + b_i (1 - cos(2 pi (x_i-s_i)))
+                     a~U[0.5,2], b~U[5,15], s~U[-2,2], box [-5.12,5.12]^n
+* ``chain``    (C1): sum_{i<n-1} alpha_i ((x_{i+1}-s_{i+1}) - (x_i-s_i)^2)^2
+                                 + beta_i (x_i-s_i)^2
+                     alpha~U[50,150], beta~U[0.5,2], s~U[-1,2], box [-5,10]^n
+* ``ackley``   (C2): -20 exp(-0.2 sqrt(mean((x-s)^2))) - exp(mean(cos(2 pi (x-s))))
+                     + 20 + e + sum_i gamma_i (x_i-s_i)^2
+                     gamma~U[0,0.01], s~U[-3,3], box [-32.768,32.768]^n
+* ``mixed``    (C3): sep_cos terms on even i (s~U[-2,2]) and chain terms on odd
+                     i (s~U[-1,2]; the alpha part only when i+1<n),
+                     box [-5.12,5.12]^n
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .dag import Dag
+
+
+@dataclass
+class Problem:
+    family: str
+    n: int
+    nodes: np.ndarray
+    root: int
+    tables: list
+    l: np.ndarray
+    u: np.ndarray
+    tol_f: float
+    block: int
+    s: np.ndarray
+    seed: int
+    meta: dict = field(default_factory=dict)
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _shifted(g: Dag, s_tab: int, off: int = 0) -> int:
+    """Template node for y = x[i+off] - s[i+off]."""
+    return g.sub(g.ivar(off), g.icoef(s_tab, off))
+
+
+def sep_cos(n: int = 2, seed: int = 0, tol_f: float = 1e-8, block: int | None = None) -> Problem:
+    r = _rng(seed)
+    a = r.uniform(0.5, 2.0, n)
+    b = r.uniform(5.0, 15.0, n)
+    s = r.uniform(-2.0, 2.0, n)
+    g = Dag()
+    ta, tb, ts = g.table(a), g.table(b), g.table(s)
+    y = _shifted(g, ts)
+    quad = g.mul(g.icoef(ta), g.sqr(y))
+    two_pi = g.scale(g.pi(), 2.0)
+    osc = g.mul(g.icoef(tb), g.sub(g.const(1.0), g.cos(g.mul(two_pi, y))))
+    term = g.add(quad, osc)
+    root = g.isum(term, 0, n, 1)
+    return Problem("sep_cos", n, g.nodes(), root, g.tables,
+                   np.full(n, -5.12), np.full(n, 5.12), tol_f,
+                   block if block else min(n, 10), s, seed)
+
+
+def chain(n: int = 100, seed: int = 0, tol_f: float = 1e-6, block: int | None = None) -> Problem:
+    if n < 2:
+        raise ValueError("chain needs n >= 2")
+    r = _rng(seed)
+    alpha = r.uniform(50.0, 150.0, n)
+    beta = r.uniform(0.5, 2.0, n)
+    s = r.uniform(-1.0, 2.0, n)
+    g = Dag()
+    tal, tbe, ts = g.table(alpha), g.table(beta), g.table(s)
+    y0 = _shifted(g, ts, 0)
+    y1 = _shifted(g, ts, 1)
+    sq0 = g.sqr(y0)
+    t_alpha = g.mul(g.icoef(tal), g.sqr(g.sub(y1, sq0)))
+    t_beta = g.mul(g.icoef(tbe), g.sqr(y0))
+    root = g.isum(g.add(t_alpha, t_beta), 0, n - 1, 1)
+    return Problem("chain", n, g.nodes(), root, g.tables,
+                   np.full(n, -5.0), np.full(n, 10.0), tol_f,
+                   block if block else min(n, 10), s, seed)
+
+
+def ackley(n: int = 1000, seed: int = 0, tol_f: float = 1e-6, block: int | None = None) -> Problem:
+    r = _rng(seed)
+    gamma = r.uniform(0.0, 0.01, n)
+    s = r.uniform(-3.0, 3.0, n)
+    g = Dag()
+    tg, ts = g.table(gamma), g.table(s)
+    # template 1: (x_i - s_i)^2
+    t1 = g.sqr(_shifted(g, ts))
+    s1 = g.isum(t1, 0, n, 1)
+    # template 2: cos(2 pi (x_i - s_i))
+    two_pi = g.scale(g.pi(), 2.0)
+    t2 = g.cos(g.mul(two_pi, _shifted(g, ts)))
+    s2 = g.isum(t2, 0, n, 1)
+    # template 3: gamma_i (x_i - s_i)^2
+    t3 = g.mul(g.icoef(tg), g.sqr(_shifted(g, ts)))
+    s3 = g.isum(t3, 0, n, 1)
+    nn = g.const(float(n))
+    a_part = g.scale(g.exp(g.scale(g.sqrt(g.div(s1, nn)), -0.2)), -20.0)
+    c_part = g.neg(g.exp(g.div(s2, nn)))
+    f = g.add(g.add(g.add(a_part, c_part), g.add(g.const(20.0), g.euler())), s3)
+    return Problem("ackley", n, g.nodes(), f, g.tables,
+                   np.full(n, -32.768), np.full(n, 32.768), tol_f,
+                   block if block else min(n, 10), s, seed)
+
+
+def mixed(n: int = 10000, seed: int = 0, tol_f: float = 1e-6, block: int | None = None) -> Problem:
+    if n < 2:
+        raise ValueError("mixed needs n >= 2")
+    r = _rng(seed)
+    even = np.arange(n) % 2 == 0
+    a = np.where(even, r.uniform(0.5, 2.0, n), 0.0)
+    b = np.where(even, r.uniform(5.0, 15.0, n), 0.0)
+    alpha = np.where(~even, r.uniform(50.0, 150.0, n), 0.0)
+    beta = np.where(~even, r.uniform(0.5, 2.0, n), 0.0)
+    s = np.where(even, r.uniform(-2.0, 2.0, n), r.uniform(-1.0, 2.0, n))
+    g = Dag()
+    ta, tb, tal, tbe, ts = (g.table(a), g.table(b), g.table(alpha),
+                            g.table(beta), g.table(s))
+    # even i: separable cosine term
+    y = _shifted(g, ts)
+    two_pi = g.scale(g.pi(), 2.0)
+    t_even = g.add(g.mul(g.icoef(ta), g.sqr(y)),
+                   g.mul(g.icoef(tb), g.sub(g.const(1.0), g.cos(g.mul(two_pi, y)))))
+    s_even = g.isum(t_even, 0, n, 2)
+    # odd i with i+1 < n: chain term
+    y0 = _shifted(g, ts, 0)
+    y1 = _shifted(g, ts, 1)
+    sq0 = g.sqr(y0)
+    t_odd = g.add(g.mul(g.icoef(tal), g.sqr(g.sub(y1, sq0))),
+                  g.mul(g.icoef(tbe), g.sqr(y0)))
+    last_odd = n - 1 if (n - 1) % 2 == 1 else n - 2
+    end_full = last_odd if last_odd + 1 >= n else last_odd + 2
+    f = s_even
+    if end_full > 1:
+        f = g.add(f, g.isum(t_odd, 1, end_full, 2))
+    if last_odd + 1 >= n:  # odd index n-1 has no successor: beta term only
+        t_tail = g.mul(g.icoef(tbe), g.sqr(_shifted(g, ts)))
+        f = g.add(f, g.isum(t_tail, last_odd, last_odd + 1, 1))
+    return Problem("mixed", n, g.nodes(), f, g.tables,
+                   np.full(n, -5.12), np.full(n, 5.12), tol_f,
+                   block if block else min(n, 100), s, seed)
+
+
+FAMILIES = {"sep_cos": sep_cos, "chain": chain, "ackley": ackley, "mixed": mixed}
+
+
+def make(family: str, **kw) -> Problem:
+    return FAMILIES[family](**kw)
+
+
+def random_boxes(p: Problem, count: int, seed: int, min_width: float = 1e-6,
+                 max_frac: float = 1.0, around_s: float = 0.0) -> tuple[np.ndarray, np.ndarray]:
+    """Seeded random sub-boxes of [l, u] (count x n, row-major).
+
+    Each coordinate interval has a log-uniform width between ``min_width`` and
+    ``max_frac`` of the domain width.  With ``around_s`` > 0 a fraction of the
+    boxes is placed so that it contains the planted point s.
+    """
+    r = _rng(seed)
+    n = p.n
+    span = p.u - p.l
+    lw = r.uniform(np.log(min_width), np.log(max_frac), (count, n))
+    w = np.minimum(np.exp(lw) * span, span)
+    lo = p.l + r.uniform(0.0, 1.0, (count, n)) * (span - w)
+    if around_s > 0.0:
+        pick = r.uniform(0.0, 1.0, count) < around_s
+        shift = r.uniform(0.0, 1.0, (count, n)) * w
+        lo_s = np.clip(p.s - shift, p.l, p.u - w)
+        lo = np.where(pick[:, None], lo_s, lo)
+    hi = np.minimum(lo + w, p.u)
+    lo = np.maximum(lo, p.l)
+    return np.ascontiguousarray(lo), np.ascontiguousarray(hi)
+
+
+def serving_stream(count: int = 512, seed: int = 0, rate: float = 20.0,
+                   n_min: int = 2, n_max: int = 2000, tol_f: float = 1e-6):
+    """Poisson request stream: (arrival time s, Problem) pairs.
+
+    n is log-uniform on [n_min, n_max]; the family is uniform over
+    sep_cos / chain / ackley; every request draws fresh coefficients.
+    """
+    r = _rng(seed)
+    gaps = r.exponential(1.0 / rate, count)
+    t = np.cumsum(gaps)
+    out = []
+    fams = ["sep_cos", "chain", "ackley"]
+    for k in range(count):
+        n = int(round(np.exp(r.uniform(np.log(n_min), np.log(n_max)))))
+        fam = fams[int(r.integers(0, 3))]
+        sub_seed = int(r.integers(0, 2**31 - 1))
+        if fam == "chain":
+            n = max(n, 2)
+        out.append((float(t[k]), make(fam, n=n, seed=sub_seed, tol_f=tol_f)))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Benchmark functions printed in the paper (SI Appendix A), unshifted.
+def paper_rastrigin(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S14-S15: 10n + sum_i (x_i^2 - 10 cos(2 pi x_i)), -5.5 <= x_i <= 6."""
+    g = Dag()
+    x = g.ivar(0)
+    two_pi = g.scale(g.pi(), 2.0)
+    term = g.sub(g.sqr(x), g.scale(g.cos(g.mul(two_pi, x)), 10.0))
+    root = g.add(g.const(10.0 * n), g.isum(term, 0, n, 1))
+    return Problem("paper_rastrigin", n, g.nodes(), root, g.tables,
+                   np.full(n, -5.5), np.full(n, 6.0), tol_f,
+                   block if block else min(n, 10), np.zeros(n), 0)
+
+
+def paper_breiman(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S5-S6: -0.1 sum_i cos(5 pi x_i) + sum_i x_i^2, -1 <= x_i <= 2."""
+    g = Dag()
+    x = g.ivar(0)
+    five_pi = g.scale(g.pi(), 5.0)
+    term = g.sub(g.sqr(x), g.scale(g.cos(g.mul(five_pi, x)), 0.1))
+    root = g.isum(term, 0, n, 1)
+    return Problem("paper_breiman", n, g.nodes(), root, g.tables,
+                   np.full(n, -1.0), np.full(n, 2.0), tol_f,
+                   block if block else min(n, 10), np.zeros(n), 0)
+
+
+FAMILIES.update(paper_rastrigin=paper_rastrigin, paper_breiman=paper_breiman)

@@ -1,0 +1,195 @@
+"""Pins of the oracle's box evaluation: F(X), the interval partials and the
+first-order test (section 3.1), against references that do not share its code.
+
+* the reduction tree against exact rational arithmetic with directed rounding;
+* F(X) for polynomial objectives bit-for-bit against mpmath's 53-bit interval
+  arithmetic in the same grouping and order;
+* containment (the rigour claim of section 2.1): for sampled points p in X,
+  f(p) computed at 60 digits lies in F(X) and each partial at p in G(X)_j;
+* the closed form: every family has f(s) = 0 at its planted point.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+pytest.importorskip("mpmath")
+import mpmath  # noqa: E402
+
+import oracle as O  # noqa: E402
+import synthetic as S  # noqa: E402
+import mp_ref  # noqa: E402
+
+
+def _rd(fr: Fraction) -> float:
+    x = float(fr)
+    if Fraction(x) > fr:
+        x = math.nextafter(x, -math.inf)
+    return x
+
+
+def _ru(fr: Fraction) -> float:
+    x = float(fr)
+    if Fraction(x) < fr:
+        x = math.nextafter(x, math.inf)
+    return x
+
+
+def _exact_tree(lo, hi):
+    a = [(float(l), float(h)) for l, h in zip(lo, hi)]
+    m = len(a)
+    s = 1
+    while s < m:
+        for i in range(0, m - s, 2 * s):
+            a[i] = (_rd(Fraction(a[i][0]) + Fraction(a[i + s][0])),
+                    _ru(Fraction(a[i][1]) + Fraction(a[i + s][1])))
+        s *= 2
+    return a[0] if m else (0.0, 0.0)
+
+
+def test_tree_sum_matches_exact_rational_rounding():
+    rng = np.random.default_rng(3)
+    for m in list(range(1, 40)) + [63, 64, 65, 100]:
+        mag = 10.0 ** rng.uniform(-8, 8, m)
+        lo = rng.uniform(-1, 1, m) * mag
+        hi = lo + np.abs(rng.uniform(0, 1, m)) * mag
+        assert O.tree_sum(lo, hi) == _exact_tree(lo, hi)
+
+
+def test_tree_sum_is_not_sequential():
+    # 1 + 3 * 2^-53: sequential rounding down keeps 1, the pairwise tree
+    # first adds the two small terms exactly
+    lo = np.array([1.0, 2.0**-53, 2.0**-53, 2.0**-53])
+    got = O.tree_sum(lo, lo)
+    seq = 1.0
+    for v in lo[1:]:
+        seq = _rd(Fraction(seq) + Fraction(v))
+    assert got == _exact_tree(lo, lo)
+    assert got[0] != seq
+
+
+@pytest.mark.parametrize("n,B", [(2, 2), (5, 3), (7, 3), (12, 5), (20, 10), (33, 10)])
+def test_polynomial_F_bit_exact_vs_mpmath(n, B):
+    p = S.chain(n=n, seed=n)
+    o = O.Oracle(p, block=B)
+    lo, hi = S.random_boxes(p, 40, seed=n + 100, around_s=0.5)
+    for k in range(len(lo)):
+        F, _, _, _ = o.eval_box(lo[k], hi[k])
+        assert tuple(F) == mp_ref.iv53_value(p, lo[k], hi[k], B)
+
+
+def test_polynomial_F_bit_exact_custom_dag():
+    # outer VAR leaves, a stride-2 sum, scaling and negation
+    g = S.Dag()
+    y = g.sub(g.ivar(0), g.ivar(1))
+    t = g.mul(g.icoef(g.table(np.linspace(0.5, 3.0, 9))), g.sqr(y))
+    s_even = g.isum(t, 0, 8, 2)
+    f = g.add(g.sub(s_even, g.scale(g.var(3), -1.5)), g.neg(g.mul(g.var(0), g.var(8))))
+    p = S.Problem("custom", 9, g.nodes(), f, g.tables, np.full(9, -2.0), np.full(9, 3.0),
+                  1e-6, 3, np.zeros(9), 0)
+    o = O.Oracle(p)
+    lo, hi = S.random_boxes(p, 60, seed=5)
+    for k in range(len(lo)):
+        F, _, _, _ = o.eval_box(lo[k], hi[k])
+        assert tuple(F) == mp_ref.iv53_value(p, lo[k], hi[k], 3)
+
+
+def _sample_points(rng, lo, hi, count):
+    t = rng.uniform(0, 1, (count, len(lo)))
+    t[0] = 0.0
+    t[1] = 1.0
+    return lo + t * (hi - lo)
+
+
+CASES = [("sep_cos", dict(n=3)), ("chain", dict(n=6)), ("ackley", dict(n=4)),
+         ("mixed", dict(n=7)), ("paper_rastrigin", dict(n=3)), ("paper_breiman", dict(n=3))]
+
+
+@pytest.mark.parametrize("f32", [False, True])
+@pytest.mark.parametrize("fam,kw", CASES)
+def test_containment_of_f_and_partials(fam, kw, f32):
+    p = S.make(fam, **kw)
+    B = max(1, min(p.n, 3))
+    o = O.Oracle(p, block=B)
+    rng = np.random.default_rng(17)
+    lo, hi = S.random_boxes(p, 12, seed=23, min_width=1e-5, around_s=0.4)
+    nb = (p.n + B - 1) // B
+    for k in range(len(lo)):
+        blk = k % nb
+        F, Fm, G, _ = o.eval_box(lo[k], hi[k], blk=blk, f32=f32)
+        for x in _sample_points(rng, lo[k], hi[k], 4):
+            fx = mp_ref.point_value(p, x)
+            assert F[0] <= fx <= F[1], (fam, k, F, fx)
+            for t in range(min(B, p.n - blk * B)):
+                j = blk * B + t
+                if fam == "ackley":
+                    r = math.sqrt(sum((x[q] - p.s[q]) ** 2 for q in range(p.n)))
+                    if r < 1e-6:
+                        continue           # derivative undefined at the minimiser
+                gx = mp_ref.point_grad(p, x, j)
+                assert G[t, 0] <= gx + mpmath.mpf(1e-30) and gx - mpmath.mpf(1e-30) <= G[t, 1], \
+                    (fam, k, j, G[t], gx)
+        # the midpoint sample is a point enclosure of f at RN(0.5 lo + 0.5 hi)
+        mid = 0.5 * lo[k] + 0.5 * hi[k]
+        fm = mp_ref.point_value(p, mid)
+        assert Fm[0] <= fm <= Fm[1]
+
+
+@pytest.mark.parametrize("fam,kw", CASES[:4])
+def test_planted_point_encloses_zero_tightly(fam, kw):
+    p = S.make(fam, **kw)
+    o = O.Oracle(p)
+    F, Fm, _, _ = o.eval_box(p.s, p.s)
+    assert F[0] <= 0.0 <= F[1]
+    assert F[1] - F[0] < 1e-12
+    assert mp_ref.point_value(p, p.s) == 0
+
+
+def test_point_box_partials_are_tight():
+    p = S.chain(n=8, seed=4)
+    o = O.Oracle(p, block=4)
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        x = rng.uniform(-1, 2, 8)
+        for blk in (0, 1):
+            _, _, G, _ = o.eval_box(x, x, blk=blk)
+            for t in range(4):
+                g = float(mp_ref.point_grad(p, x, blk * 4 + t))
+                assert G[t, 0] <= g <= G[t, 1]
+                assert G[t, 1] - G[t, 0] <= 1e-10 * max(1.0, abs(g))
+
+
+def test_monotonicity_rules_out_far_boxes_and_keeps_edges():
+    p = S.sep_cos(n=2, seed=1)
+    o = O.Oracle(p, block=2)
+    s = p.s
+    # a thin box right of s_0 in coordinate 0 (derivative > 0 there), s_1 inside
+    lo = np.array([s[0] + 1e-3, s[1] - 1e-4])
+    hi = np.array([s[0] + 1.1e-3, s[1] + 1e-4])
+    _, _, G, mono = o.eval_box(lo, hi, blk=0)
+    assert G[0, 0] > 0 and mono == 1
+    # the same box containing s in both coordinates is kept
+    lo2 = np.array([s[0] - 1e-4, s[1] - 1e-4])
+    hi2 = np.array([s[0] + 1e-4, s[1] + 1e-4])
+    assert o.eval_box(lo2, hi2, blk=0)[3] == 0
+    # a box whose lower face lies on l is exempt when DLB > 0 (edge of the domain)
+    g = S.Dag()
+    f = g.isum(g.sqr(g.ivar(0)), 0, 1, 1)      # f = x^2 on [1, 3]
+    q = S.Problem("edge", 1, g.nodes(), f, g.tables, np.array([1.0]), np.array([3.0]),
+                  1e-6, 1, np.array([1.0]), 0)
+    oq = O.Oracle(q)
+    assert oq.eval_box(np.array([1.0]), np.array([1.5]), blk=0)[3] == 0
+    assert oq.eval_box(np.array([1.5]), np.array([2.0]), blk=0)[3] == 1
+
+
+def test_invalid_problems_are_rejected():
+    p = S.chain(n=4)
+    bad = p.nodes.copy()
+    bad[2]["a"] = 7                          # SUB node referring forward
+    q = S.Problem("bad", 4, bad, p.root, p.tables, p.l, p.u, 1e-6, 2, p.s, 0)
+    with pytest.raises(ValueError):
+        O.Oracle(q)
+    q2 = S.Problem("bad", 4, p.nodes, p.root, p.tables, p.l, p.l, 1e-6, 2, p.s, 0)
+    with pytest.raises(ValueError):
+        O.Oracle(q2)                         # l < u violated

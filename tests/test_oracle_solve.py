@@ -1,0 +1,144 @@
+"""Pins of the oracle's branch and bound (section 3.1, variable cycling of
+section 3.2) against what the paper and the mathematics fix:
+
+* the paper's own iteration and region counts (Tables S4, S7, Table 1),
+  reproduced per cycling block in paper mode;
+* the planted minimum (closed form min f = 0 at s) and the enclosure width;
+* a separable problem against its 1-D sub-problems solved separately;
+* brute force on a grid for n <= 3;
+* the output regions always cover the planted minimiser, also when the solve
+  stops early on a capacity or generation limit.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_iterations.txt")
+
+
+def _golden_rows():
+    rows = []
+    for line in open(GOLDEN):
+        line = line.split("#")[0].strip()
+        if line:
+            fam, n, it, reg = line.split()
+            rows.append((fam, int(n), int(it), int(reg)))
+    return rows
+
+
+def _covers(res, x):
+    inside = np.all((res.box_lo <= x) & (x <= res.box_hi), axis=1)
+    return bool(inside.any())
+
+
+@pytest.mark.parametrize("fam", ["paper_rastrigin", "paper_breiman"])
+def test_paper_mode_iteration_counts(fam):
+    rows = [r for r in _golden_rows() if r[0] == fam]
+    per_block = {r[2] * 10 // r[1] for r in rows}
+    assert len(per_block) == 1            # the paper's rows scale as n/10
+    per_block = per_block.pop()
+    for n, B in ((5, 5), (10, 5)):
+        p = S.make(fam, n=n, block=B)
+        res = O.Oracle(p, block=B).solve(tol_f=0.0, tol_x=1e-4, split_m=4, split_d=B,
+                                         max_parents=1)
+        assert res.status == O.ST_OK
+        assert res.generations == (n // B) * per_block
+        assert len(res.box_flo) == 1 == rows[0][3]
+        assert np.all(res.box_hi - res.box_lo < 1e-4)
+        fstar = 0.0 if fam == "paper_rastrigin" else -0.1 * n   # SI Appendix A
+        assert res.glb <= fstar <= res.gub
+        assert _covers(res, np.zeros(n))
+
+
+CASES = [("sep_cos", dict(n=2), dict(split_m=2, split_d=1)),
+         ("sep_cos", dict(n=3, tol_f=1e-6), dict(split_m=4, split_d=3)),
+         ("chain", dict(n=6, block=3), dict(split_m=2, split_d=3)),
+         ("chain", dict(n=10, block=5), dict(split_m=2, split_d=5, max_parents=8)),
+         ("ackley", dict(n=3), dict(split_m=2, split_d=3)),
+         ("mixed", dict(n=6, block=3), dict(split_m=2, split_d=3))]
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("fam,kw,opt", CASES)
+def test_planted_minimum_enclosed(fam, kw, opt, fp32):
+    p = S.make(fam, seed=2, **kw)
+    res = O.Oracle(p).solve(fp32=fp32, **opt)
+    assert res.status == O.ST_OK
+    assert res.glb <= 0.0 <= res.gub
+    assert res.gub - res.glb <= p.tol_f
+    assert _covers(res, p.s)
+    assert np.all(res.box_flo <= res.gub)
+
+
+def test_separable_reduction():
+    p = S.sep_cos(n=2, seed=5, tol_f=1e-9)
+    res = O.Oracle(p).solve(split_m=2, split_d=1)
+    a, b, s = p.tables
+    lo_sum = hi_sum = 0.0
+    for j in range(2):
+        g = S.Dag()
+        ta, tb, ts = g.table(a[j:j + 1]), g.table(b[j:j + 1]), g.table(s[j:j + 1])
+        y = g.sub(g.ivar(0), g.icoef(ts))
+        term = g.add(g.mul(g.icoef(ta), g.sqr(y)),
+                     g.mul(g.icoef(tb), g.sub(g.const(1.0), g.cos(g.mul(g.scale(g.pi(), 2.0), y)))))
+        root = g.isum(term, 0, 1, 1)
+        q = S.Problem("1d", 1, g.nodes(), root, g.tables,
+                      p.l[j:j + 1], p.u[j:j + 1], 1e-9, 1, s[j:j + 1], 0)
+        r1 = O.Oracle(q).solve(split_m=2, split_d=1)
+        assert r1.glb <= 0.0 <= r1.gub
+        lo_sum += r1.glb
+        hi_sum += r1.gub
+    # both enclose the same minimum 0: the intervals must overlap
+    assert max(lo_sum, res.glb) <= min(hi_sum, res.gub) + 1e-15
+
+
+@pytest.mark.parametrize("fam,kw", [("sep_cos", dict(n=2)), ("chain", dict(n=3, block=3)),
+                                     ("ackley", dict(n=2)), ("paper_breiman", dict(n=2))])
+def test_brute_force_grid(fam, kw):
+    import itertools
+    import mp_ref
+    p = S.make(fam, **kw) if fam.startswith("paper") else S.make(fam, seed=3, **kw)
+    res = O.Oracle(p).solve(tol_f=1e-6, split_m=2, split_d=p.block)
+    G = 41 if p.n == 2 else 17
+    axes = [np.linspace(p.l[j], p.u[j], G) for j in range(p.n)]
+    pts = list(itertools.product(*axes)) + [tuple(p.s)]
+    vals = [float(mp_ref.point_value(p, x, dps=30)) for x in pts]
+    k = int(np.argmin(vals))
+    assert min(vals) >= res.glb                 # GLB is a lower bound of f
+    fstar = 0.0 if not fam.startswith("paper") else -0.1 * p.n
+    assert res.glb <= fstar <= res.gub
+    # every point with f below the final GUB lies in some output region
+    for x, v in zip(pts, vals):
+        if v < res.gub:
+            assert _covers(res, np.array(x)), (x, v)
+    assert vals[k] >= res.glb
+
+
+def test_determinism():
+    p = S.chain(n=8, seed=7, block=4)
+    a = O.Oracle(p).solve(split_m=2, split_d=2, max_parents=16)
+    b = O.Oracle(p).solve(split_m=2, split_d=2, max_parents=16)
+    assert a.glb == b.glb and a.gub == b.gub and a.generations == b.generations
+    assert np.array_equal(a.box_lo, b.box_lo) and np.array_equal(a.box_hi, b.box_hi)
+    assert np.array_equal(a.trace["gub"], b.trace["gub"])
+
+
+def test_capacity_and_limit_keep_a_valid_enclosure():
+    p = S.chain(n=8, seed=1, block=4)
+    r = O.Oracle(p).solve(split_m=2, split_d=4, cap=40)
+    assert r.status == O.ST_CAPACITY
+    assert r.glb <= 0.0 <= r.gub and _covers(r, p.s)
+    r = O.Oracle(p).solve(split_m=2, split_d=1, max_gen=5)
+    assert r.status == O.ST_LIMIT and r.generations == 5
+    assert r.glb <= 0.0 <= r.gub and _covers(r, p.s)
+
+
+def test_bad_options_rejected():
+    p = S.chain(n=4)
+    assert O.Oracle(p).solve(split_m=3).status == O.ST_INVALID
+    assert O.Oracle(p).solve(split_d=0).status == O.ST_INVALID
