@@ -1,0 +1,284 @@
+#!/usr/bin/env python3
+"""Benchmark: box evaluations per second of the GPU interval branch and bound.
+
+Workload (one "step" = one complete solve, every row of the hot path):
+  coupled quartic chain, n = 100, seed 0 (synthetic.chain): alpha~U[50,150],
+  beta~U[0.5,2], s~U[-1,2], box [-5,10]^100, min f = 0 at the planted s,
+  enclosure width target 1e-6, FP64, variable cycling over blocks of 10
+  coordinates, bisection of all 10 block coordinates per generation (1024
+  children per parent), up to 2^20 children per generation.
+
+value      box evaluations (F + interval gradient + first-order test, FP64 and
+           FP32 children) per second over the timed solves, problem and
+           coefficients resident on the device, device time from CUDA events
+           on the library's stream.
+e2e        the same metric through the public C ABI from host buffers:
+           gb_create_problem (DAG, tables and bounds copied host -> device),
+           gb_solve (boxes and trace copied device -> host), gb_destroy_problem.
+roofline   the FP64 evaluation kernel: directed-rounding FP64 operations of the
+           compiled program (static count per child and per midpoint sample)
+           per second, against the FP64 pipe rate of the chip at the sampled
+           SM clock (2 FP64 operations per SM per clock, 152 SMs).
+cpu_baseline / --impl reference
+           the CPU oracle (plain C, fesetround) on the host cores, one thread,
+           on a bounded sample of the same workload.
+
+Under torchrun (N > 1) every rank solves its own replica (seed = rank): the
+solves are independent, there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+FP64_OPS_PER_SM_CLK = 2.0    # GB300: 1.25 TFLOP/s FP64 (FMA = 2) at 2.07 GHz over 152 SMs
+SMS = 152
+WORKLOAD = dict(family="chain", n=100, block=10, split_m=2, split_d=10, max_children=1 << 20)
+WORKLOAD_NAME = ("chain n=100 (coupled quartic, planted min 0), FP64, B=10, bisect 10 coords/gen "
+                 "(1024 children/parent), <=2^20 children/gen, tol_f=1e-6")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb", choices=["gb", "reference"])
+    ap.add_argument("--max-children", type=int, default=WORKLOAD["max_children"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-gens", type=int, default=20, help="generations in the oracle sample")
+    return ap.parse_args()
+
+
+def _problem(seed=0):
+    return S.chain(n=WORKLOAD["n"], seed=seed)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def flush_l2(torch, dev, buf):
+    buf.add_(1.0)          # 512 MB written: larger than the 129 MB L2
+    torch.cuda.synchronize(dev)
+
+
+def cpu_baseline(gens):
+    """Oracle, one thread, first `gens` generations (4 parents each) of the workload."""
+    import oracle
+    p = _problem(0)
+    o = oracle.Oracle(p, block=WORKLOAD["block"])
+    t = time.perf_counter()
+    r = o.solve(split_m=WORKLOAD["split_m"], split_d=WORKLOAD["split_d"], max_parents=4, max_gen=gens)
+    dt = time.perf_counter() - t
+    evals = r.evals64 + r.evals32
+    return {"value": evals / dt, "unit": "box-evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {r.generations} generations of the workload with 4 parents per generation "
+                      f"({evals} box evaluations, {dt:.1f} s, 1 thread)"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    vals = []
+    for i in range(a.warmup):
+        cpu_baseline(1)
+    for i in range(a.steps):
+        vals.append(cpu_baseline(max(1, a.cpu_gens // 2)))
+    v = statistics.median([x["value"] for x in vals])
+    line = {"impl": "reference", "metric": "box-evals/s", "value": v, "unit": "box-evals/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[0]["sample"], "value": v},
+            "e2e": {"value": v, "unit": "box-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import paper_2507_01770_gb300 as gb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    gb.load()
+    p = _problem(seed=rank)
+    opts = dict(block=WORKLOAD["block"], split_m=WORKLOAD["split_m"], split_d=WORKLOAD["split_d"],
+                max_children=a.max_children, device=local)
+    solver = gb.Solver(p, **opts)
+    info = solver.info()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float64, device=dev)
+
+    for _ in range(a.warmup):
+        solver.solve(device_only=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    results = []
+    host_t = 0.0
+    for _ in range(a.steps):
+        flush_l2(torch, dev, flush)
+        t0 = time.perf_counter()
+        r = solver.solve(device_only=True)
+        host_t += time.perf_counter() - t0
+        results.append(r)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+
+    dev_ms = sum(r.device_ms for r in results)
+    evals = sum(r.box_evals_fp64 + r.box_evals_fp32 for r in results)
+    mids = sum(r.mid_evals for r in results)
+    launches = sum(r.kernel_launches for r in results)
+    e64_ms = sum(r.eval64_ms for r in results)
+    e64_n = sum(r.eval64_launches for r in results)
+    ok = all(r.status == 0 and r.fmin_lo <= 0.0 <= r.fmin_hi and r.fmin_hi - r.fmin_lo <= p.tol_f
+             for r in results)
+
+    # ---- end to end through the public API from host buffers -----------------
+    e2e_steps = max(1, min(3, a.steps))
+    h2d = p.nodes.nbytes + sum(t.nbytes for t in p.tables) + p.l.nbytes + p.u.nbytes
+    e2e_t, e2e_evals, d2h = 0.0, 0, 0
+    for _ in range(e2e_steps):
+        flush_l2(torch, dev, flush)
+        t0 = time.perf_counter()
+        h = gb.gb_create_problem(p.nodes, p.root, p.tables, p.n, p.l, p.u, p.tol_f,
+                                 gb.gb_default_options(**opts))
+        r = gb.gb_solve(h)
+        h.close()
+        e2e_t += time.perf_counter() - t0
+        e2e_evals += r.box_evals_fp64 + r.box_evals_fp32
+        d2h = r.n_boxes * (2 * p.n + 1) * 8 + r.generations * (48 + 256) + 256
+
+    if dist:
+        t = torch.tensor([dev_ms, e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([evals, e2e_evals], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        dev_ms, e2e_t = float(t[0]), float(t[1])
+        evals, e2e_evals = float(c[0]), float(c[1])
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    value = evals / (dev_ms * 1e-3)
+    sm_mhz = ck["sm_mhz"] if ck else 2070.0
+    ops = info["ops_eval"] * sum(r.box_evals_fp64 - 1 for r in results) + info["ops_mid"] * sum(
+        r.mid_evals - 1 for r in results)
+    achieved = ops / (e64_ms * 1e-3) / 1e12 if e64_ms > 0 else None
+    peak = FP64_OPS_PER_SM_CLK * SMS * sm_mhz * 1e6 / 1e12
+    try:
+        probe_ops, _ = gb.gb_measure_peak(local, 0)
+    except Exception:
+        probe_ops = None
+    line = {
+        "metric": "box-evals/s", "value": value, "unit": "box-evals/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": dev_ms / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "l2": "flushed between steps (512 MB write)",
+                   "solves_per_s": a.steps / (dev_ms * 1e-3), "generations_per_solve":
+                   results[-1].generations, "mid_evals_per_s": mids / (dev_ms * 1e-3),
+                   "all_enclosures_valid": ok, "enclosure": [results[-1].fmin_lo, results[-1].fmin_hi],
+                   "host_ms_per_step": 1e3 * host_t / a.steps, "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "e2e": {"value": e2e_evals / e2e_t, "unit": "box-evals/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "k_eval64", "ops": "FP64 directed-rounding operations",
+                     "peak_source": f"2 FP64 ops/SM/clk x 152 SMs x {sm_mhz:.0f} MHz (sampled median)",
+                     "avg_launch_ms": e64_ms / max(1, e64_n),
+                     "probe_measured_tops": probe_ops / 1e12 if probe_ops else None},
+        "clocks": ck,
+    }
+    if not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"] = cpu_baseline(a.cpu_gens)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * gb.h -- C ABI of the GB300 interval branch-and-bound global minimiser.
+ *
+ * The library encloses the global minimum of f(x) subject to l <= x <= u
+ * (the problem of Eqs. 1-2 of Zhang, Shan and Cagan, "Global optimization
+ * tailored for graphics processing units") with outward-rounded interval
+ * arithmetic on the GPU (section 2.1, Eqs. 3-6).  Each generation selects a
+ * batch of boxes with the smallest lower bounds (section 3.1, "select"),
+ * splits each on the coordinates of its variable-cycling block (section 3.2,
+ * Eqs. 7-11), samples f at every child's midpoint to lower the incumbent
+ * upper bound GUB (section 3.1, "sample"), evaluates F(X) and the interval
+ * gradient of every child, rules children out by the cut-off test
+ * (LB > GUB) and the first-order test (section 3.1, "partition and rule
+ * out"), and inserts the survivors into a pool kept in GPU memory.  The solve
+ * stops when every remaining box has a lower bound within tol_f of GUB.
+ *
+ * Conventions for every entry point:
+ *  - No call aborts, throws or exits; failures return a gb_status and
+ *    gb_last_error() describes the most recent failure on the calling thread.
+ *  - Pointers named h_* are host memory, d_* are device memory of the
+ *    problem's CUDA device; "stream" is a cudaStream_t (NULL = legacy
+ *    default stream).
+ *  - Inputs are copied at the call; the caller keeps ownership of them.
+ *  - Results returned in a gb_result are owned by the library until
+ *    gb_free_result().
+ *  - There is no CPU fallback: without a usable CUDA device the calls that
+ *    need one return GB_E_CUDA.
+ */
+#ifndef GB_H
+#define GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gb_status {
+    GB_OK = 0,
+    GB_E_INVALID = 1,   /* malformed problem, options or arguments */
+    GB_E_OOM = 2,       /* device or host allocation failed */
+    GB_E_CAPACITY = 3,  /* box pool full; the returned enclosure is still rigorous */
+    GB_E_LIMIT = 4,     /* generation limit reached; enclosure still rigorous */
+    GB_E_TIMEOUT = 5,   /* a bounded device wait gave up */
+    GB_E_CUDA = 6,      /* CUDA runtime error or no device */
+    GB_E_BUSY = 7       /* serving: request not finished / no slot free */
+} gb_status;
+
+/* ---------------------------------------------------------------------- */
+/* Objective: expression DAG (input format, 32-byte nodes)                 */
+/* ---------------------------------------------------------------------- */
+/* Node operators.  Nodes are topologically ordered (operand index < node
+ * index).  ISUM(a = template root, b = first, c = end, d = step) is the sum
+ * over i in {b, b+d, ...} < c of the template sub-DAG rooted at a, in which
+ * IDX_VAR(b = offset) stands for x[i+offset] and IDX_COEF(a = table,
+ * b = offset) for coef_tables[a][i+offset].  CONST(v) is the exact double v;
+ * PI and EULER are the constants pi and e, enclosed by adjacent doubles;
+ * SCALE(a, v) multiplies node a by the exact double v.  Template nodes may
+ * not use VAR or ISUM; outer nodes may not use IDX_VAR or IDX_COEF. */
+enum {
+    GB_OP_CONST = 0, GB_OP_PI = 1, GB_OP_EULER = 2, GB_OP_VAR = 3,
+    GB_OP_IDX_VAR = 4, GB_OP_IDX_COEF = 5, GB_OP_ADD = 6, GB_OP_SUB = 7,
+    GB_OP_MUL = 8, GB_OP_DIV = 9, GB_OP_NEG = 10, GB_OP_SQR = 11,
+    GB_OP_SQRT = 12, GB_OP_EXP = 13, GB_OP_SIN = 14, GB_OP_COS = 15,
+    GB_OP_SCALE = 16, GB_OP_ISUM = 17
+};
+
+typedef struct gb_node {
+    int32_t op;   /* GB_OP_* */
+    int32_t a;    /* operand 1 | VAR coordinate | IDX_COEF table | ISUM template root */
+    int32_t b;    /* operand 2 | IDX_VAR / IDX_COEF offset | ISUM first index */
+    int32_t c;    /* ISUM end index (exclusive) */
+    int32_t d;    /* ISUM step (>= 1) */
+    int32_t pad;  /* must be 0 */
+    double v;     /* CONST value | SCALE factor */
+} gb_node;
+
+/* ---------------------------------------------------------------------- */
+/* Options                                                                 */
+/* ---------------------------------------------------------------------- */
+typedef struct gb_options {
+    double tol_f;             /* target width of [fmin_lo, fmin_hi] (<= 0: use the tol argument) */
+    double tol_x;             /* a box narrower than tol_x in every coordinate is final (0 = off) */
+    int32_t block;            /* cycling block size B, section 3.2 (0: min(n, 10)) */
+    int32_t split_m;          /* pieces per split coordinate, 2 or 4 (0: 2) */
+    int32_t split_d;          /* coordinates split per generation, 1..B (0: B, capped so m^d <= 4096) */
+    int32_t fp32_prefilter;   /* 1: FP32 directed-rounding pass before FP64 */
+    int64_t max_generations;  /* 0: 10^9 */
+    int64_t max_children;     /* children evaluated per generation (0: 1 << 22) */
+    int64_t max_boxes;        /* pool capacity in boxes (0: from pool_bytes) */
+    size_t pool_bytes;        /* device memory budget for the pool (0: 4 GiB) */
+    int32_t device;           /* CUDA device ordinal */
+    int32_t pad;
+} gb_options;
+
+/* Fills *opt with the defaults documented above. */
+void gb_default_options(gb_options* opt);
+
+/* ---------------------------------------------------------------------- */
+/* Problems and solves                                                     */
+/* ---------------------------------------------------------------------- */
+typedef struct gb_problem gb_problem;
+
+/* Creates a problem: minimise node `root` of h_dag[0..n_nodes) over the box
+ * l <= x <= u (Eqs. 1-2; l < u finite, u - l finite), with coefficient
+ * tables h_tables[t][0..h_table_lens[t]).  tol is the enclosure width target
+ * (overridden by opt->tol_f when > 0).  opt may be NULL for the defaults.
+ * The DAG is compiled to device bytecode and copied to the device together
+ * with the tables.  Returns GB_E_INVALID for a malformed DAG or bounds,
+ * GB_E_CUDA without a device, GB_E_OOM on allocation failure.  *out is set
+ * only on GB_OK and must be released with gb_destroy_problem(). */
+gb_status gb_create_problem(const gb_node* h_dag, int32_t n_nodes, int32_t root,
+                            const double* const* h_tables, const int64_t* h_table_lens,
+                            int32_t n_tables, int32_t n, const double* l, const double* u,
+                            double tol, const gb_options* opt, gb_problem** out);
+
+/* Per-generation counters of a solve (one row per generation). */
+typedef struct gb_gen_stat {
+    int64_t parents;   /* boxes selected and split */
+    int64_t children;  /* children evaluated */
+    int64_t kept32;    /* children kept by the FP32 pass (= children without it) */
+    int64_t kept;      /* children inserted into the pool */
+    int64_t pool;      /* pool size after the generation */
+    double gub;        /* incumbent upper bound after the generation */
+} gb_gen_stat;
+
+typedef struct gb_result {
+    double fmin_lo, fmin_hi;  /* rigorous enclosure [GLB, GUB] of min f */
+    int64_t n_boxes;          /* boxes that may contain a global minimiser */
+    int32_t n;                /* problem dimension */
+    int32_t status;           /* gb_status of the solve */
+    double* box_lo;           /* n_boxes x n, row-major, host (NULL from gb_solve_device) */
+    double* box_hi;
+    double* box_flo;          /* lower bound of f on each box */
+    int64_t generations;
+    int64_t box_evals_fp32;   /* children evaluated in FP32 (F and gradient) */
+    int64_t box_evals_fp64;   /* children evaluated in FP64 (F and gradient) */
+    int64_t mid_evals;        /* FP64 midpoint samples */
+    double solve_ms;          /* wall time of the solve on the host clock */
+    double device_ms;         /* CUDA-event time from the first to the last launch */
+    double eval64_ms;         /* CUDA-event time inside the FP64 evaluation kernels */
+    double eval32_ms;         /* CUDA-event time inside the FP32 evaluation kernels */
+    int64_t eval64_launches;
+    int64_t eval32_launches;
+    int64_t kernel_launches;  /* kernels the library launched for this solve */
+    int64_t n_trace;
+    gb_gen_stat* trace;       /* n_trace rows, host */
+} gb_result;
+
+/* Solves the problem (blocking).  Copies the enclosure, the surviving boxes
+ * and the per-generation trace to host memory in *out.  On GB_E_CAPACITY or
+ * GB_E_LIMIT the enclosure and boxes returned are still rigorous.  The
+ * problem can be solved again; each solve starts from the whole domain. */
+gb_status gb_solve(gb_problem* prob, gb_result* out);
+
+/* Same solve, leaving the surviving boxes on the device (box_lo/box_hi/
+ * box_flo are NULL in *out).  Used to time the device path alone. */
+gb_status gb_solve_device(gb_problem* prob, gb_result* out);
+
+/* Releases the host arrays of a result (safe on a zeroed result). */
+void gb_free_result(gb_result* res);
+
+/* Releases the problem and all its device memory. */
+void gb_destroy_problem(gb_problem* prob);
+
+const char* gb_status_str(gb_status s);
+const char* gb_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Parity hook: evaluate given boxes from scratch                          */
+/* ---------------------------------------------------------------------- */
+/* For each of nbox boxes (d_lo, d_hi: nbox x n row-major, device) computes
+ * F(X) (d_F: nbox x 2), the FP64 midpoint sample F([m, m]) with
+ * m = RN(0.5 lo + 0.5 hi) (d_Fmid: nbox x 2), the interval partials of the
+ * coordinates of cycling block `block_index` (d_G: nbox x B x 2, tail of a
+ * short last block untouched) and the first-order verdict (d_mono: 1 if
+ * some tested partial excludes 0 away from the domain edge, section 3.1).
+ * fp32 = 1 evaluates F and G in FP32 directed rounding (the box widened
+ * outward to floats); Fmid is always FP64.  Runs on `stream`; no sync. */
+gb_status gb_eval_boxes(gb_problem* prob, const double* d_lo, const double* d_hi,
+                        int64_t nbox, int32_t block_index, int32_t fp32, double* d_F,
+                        double* d_Fmid, double* d_G, int32_t* d_mono, void* stream);
+
+/* Block size B, number of blocks and the static count of directed-rounding
+ * floating-point operations of one F+gradient child evaluation and one
+ * midpoint sample (FP64), as compiled. */
+gb_status gb_problem_info(const gb_problem* prob, int32_t* block, int32_t* n_blocks,
+                          int64_t* ops_eval, int64_t* ops_mid);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement helper (the paper has no counterpart)                        */
+/* ---------------------------------------------------------------------- */
+/* Throughput of directed-rounding arithmetic on `device`, for roofline
+ * denominators: which = 0 times FP64 __dadd_rd/__dmul_ru chains, which = 1
+ * the FP32 __fadd_rd/__fmul_ru forms.  Runs a register-resident kernel on
+ * all SMs and returns operations per second in *ops_per_s and the kernel's
+ * CUDA-event time in *ms.  Blocking. */
+gb_status gb_measure_peak(int32_t device, int32_t which, double* ops_per_s, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB_H */

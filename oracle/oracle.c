@@ -1032,6 +1032,7 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
            back to the end of the list, the samples' GUB is kept, and the
            solve stops with the list still covering every unresolved region. */
         if (pool.len + par.len + keep.len > opt->cap) {
+            int64_t npar = par.len;
             for (int64_t q = 0; q < keep.len; q++) ent_free(&keep.e[q]);
             keep.len = 0;
             for (int64_t q = 0; q < par.len; q++) el_push(&pool, par.e[q]);
@@ -1039,7 +1040,7 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
             gub = gub_new;
             status = ST_CAPACITY;
             gen++;
-            trace_push(R, &tcap, 0, kids.len, kept32, kept, gub, pool.len);
+            trace_push(R, &tcap, npar, kids.len, kept32, 0, gub, pool.len);
             break;
         }
         for (int64_t q = 0; q < par.len; q++) ent_free(&par.e[q]);

@@ -1,0 +1,514 @@
+// C ABI of the library (include/gb.h): problem creation, the generation loop
+// of the batched best-first branch and bound, result handling and the
+// per-box evaluation hook.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gb_internal.h"
+#include "gb_launch.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+gb_status fail(gb_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+gb_status cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? GB_E_OOM : GB_E_CUDA;
+}
+
+#define GB_CU(call)                                        \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+template <typename T>
+cudaError_t upload(T** dst, const T* src, size_t count, std::vector<void*>& owned) {
+    *dst = nullptr;
+    size_t bytes = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    if (e != cudaSuccess) return e;
+    owned.push_back(*dst);
+    if (count) e = cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
+    return e;
+}
+
+template <typename T>
+cudaError_t alloc(T** dst, size_t count, std::vector<void*>& owned) {
+    *dst = nullptr;
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) owned.push_back(*dst);
+    return e;
+}
+
+void float_bounds(double c, float* lo, float* hi) {
+    float f = (float)c;
+    *lo = ((double)f <= c) ? f : std::nextafter(f, -INFINITY);
+    *hi = ((double)f >= c) ? f : std::nextafter(f, INFINITY);
+}
+
+}  // namespace
+
+struct gb_problem {
+    int n = 0, device = 0;
+    gb_options opt{};
+    double tol_f = 0.0;
+    GbHostProg hp;
+    GbProg P{};
+    std::vector<void*> owned;      // device allocations
+    cudaStream_t stream = nullptr;
+    GbPool pool{};
+    GbEntries E[2]{};
+    GbParents par{};
+    GbChildren ch{};
+    GbScan sc{};
+    GbSplit sp{};
+    GbState* st = nullptr;         // device
+    GbState* st_host = nullptr;    // pinned host
+    unsigned* out_list = nullptr;
+    long long cap = 0, K = 0, Cmax = 0, fan = 0;
+    cudaEvent_t ev[6] = {};        // solve start/end, eval64 start/end, eval32 start/end
+};
+
+extern "C" {
+
+void gb_default_options(gb_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->split_m = 2;
+    o->max_generations = 1000000000LL;
+    o->max_children = 1LL << 22;
+    o->pool_bytes = (size_t)4 << 30;
+}
+
+const char* gb_status_str(gb_status s) {
+    switch (s) {
+    case GB_OK: return "ok";
+    case GB_E_INVALID: return "invalid argument";
+    case GB_E_OOM: return "out of memory";
+    case GB_E_CAPACITY: return "box pool capacity reached";
+    case GB_E_LIMIT: return "generation limit reached";
+    case GB_E_TIMEOUT: return "device wait timed out";
+    case GB_E_CUDA: return "CUDA error";
+    case GB_E_BUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+const char* gb_last_error(void) { return g_err.c_str(); }
+
+void gb_destroy_problem(gb_problem* p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    for (void* q : p->owned) cudaFree(q);
+    if (p->st_host) cudaFreeHost(p->st_host);
+    for (cudaEvent_t e : p->ev)
+        if (e) cudaEventDestroy(e);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, const double* const* tables,
+                            const int64_t* table_lens, int32_t n_tables, int32_t n, const double* l,
+                            const double* u, double tol, const gb_options* opt_in, gb_problem** out) {
+    if (!out) return fail(GB_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!dag || n_nodes < 1 || n < 1 || !l || !u || n_tables < 0 || (n_tables > 0 && (!tables || !table_lens)))
+        return fail(GB_E_INVALID, "missing DAG, bounds or tables");
+    gb_options opt;
+    gb_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.split_m == 0) opt.split_m = 2;
+    if (opt.max_generations <= 0) opt.max_generations = 1000000000LL;
+    if (opt.max_children <= 0) opt.max_children = 1LL << 22;
+    if (opt.pool_bytes == 0) opt.pool_bytes = (size_t)4 << 30;
+    if (opt.block <= 0) opt.block = n < 10 ? n : 10;
+    if (opt.block > n) return fail(GB_E_INVALID, "block size larger than n");
+    if (opt.split_m != 2 && opt.split_m != 4) return fail(GB_E_INVALID, "split_m must be 2 or 4");
+    const int mshift = opt.split_m == 2 ? 1 : 2;
+    if (opt.split_d <= 0) {
+        opt.split_d = opt.block;
+        while (opt.split_d > 1 && (opt.split_d * mshift > 12 || opt.split_d > GB_MAX_SPLIT_D)) opt.split_d--;
+    }
+    if (opt.split_d > opt.block || opt.split_d > GB_MAX_SPLIT_D || opt.split_d * mshift > 12)
+        return fail(GB_E_INVALID, "split_d must be <= block, <= 12 and give at most 4096 children");
+    double tol_f = opt.tol_f > 0.0 ? opt.tol_f : tol;
+    if (!(tol_f >= 0.0) || !std::isfinite(tol_f)) return fail(GB_E_INVALID, "tolerance must be finite and >= 0");
+    if (!(opt.tol_x >= 0.0)) return fail(GB_E_INVALID, "tol_x must be >= 0");
+    for (int j = 0; j < n; j++)
+        if (!std::isfinite(l[j]) || !std::isfinite(u[j]) || !(l[j] < u[j]) || !std::isfinite(u[j] - l[j]))
+            return fail(GB_E_INVALID, "bounds must be finite with l < u (coordinate " + std::to_string(j) + ")");
+    for (int t = 0; t < n_tables; t++) {
+        if (table_lens[t] < 0 || (table_lens[t] > 0 && !tables[t])) return fail(GB_E_INVALID, "bad table");
+        for (int64_t i = 0; i < table_lens[t]; i++)
+            if (!std::isfinite(tables[t][i])) return fail(GB_E_INVALID, "non-finite coefficient");
+    }
+
+    gb_problem* p = new gb_problem();
+    p->n = n;
+    p->opt = opt;
+    p->tol_f = tol_f;
+    p->device = opt.device;
+    std::string err = gb_compile(dag, n_nodes, root, table_lens, n_tables, n, opt.block, &p->hp);
+    if (!err.empty()) {
+        delete p;
+        return fail(GB_E_INVALID, err);
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= opt.device || opt.device < 0) {
+        delete p;
+        return fail(GB_E_CUDA, "no CUDA device available");
+    }
+    cudaError_t e = cudaSetDevice(opt.device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaSetDevice");
+    }
+    gb_status rc = GB_OK;
+    auto bad = [&](cudaError_t ee, const char* where) {
+        rc = cuda_fail(ee, where);
+        gb_destroy_problem(p);
+        return rc;
+    };
+
+    // ---- program and tables ----------------------------------------------
+    const GbHostProg& H = p->hp;
+    GbProg& P = p->P;
+    P.n = n;
+    P.B = H.B;
+    P.nb = H.nb;
+    P.n_sum = (int)H.sums.size();
+    P.n_groups = (int)H.groups.size();
+    P.n_outer = (int)H.outer.size();
+    P.outer_root = H.outer_root;
+    P.n_var_leaves = (int)H.var_leaves.size();
+    GbIns *d_outer, *d_tins;
+    GbSum* d_sums;
+    GbGroup* d_groups;
+    int2* d_dirty;
+    GbVarLeaf* d_leaves;
+    double *d_l, *d_u;
+    if ((e = upload(&d_outer, H.outer.data(), H.outer.size(), p->owned))) return bad(e, "upload program");
+    if ((e = upload(&d_tins, H.tins.data(), H.tins.size(), p->owned))) return bad(e, "upload program");
+    if ((e = upload(&d_sums, H.sums.data(), H.sums.size(), p->owned))) return bad(e, "upload program");
+    if ((e = upload(&d_groups, H.groups.data(), H.groups.size(), p->owned))) return bad(e, "upload program");
+    if ((e = upload(&d_dirty, H.dirty.data(), H.dirty.size(), p->owned))) return bad(e, "upload program");
+    if ((e = upload(&d_leaves, H.var_leaves.data(), H.var_leaves.size(), p->owned))) return bad(e, "upload program");
+    if ((e = upload(&d_l, l, (size_t)n, p->owned))) return bad(e, "upload bounds");
+    if ((e = upload(&d_u, u, (size_t)n, p->owned))) return bad(e, "upload bounds");
+    std::vector<const double*> t64(n_tables > 0 ? n_tables : 1, nullptr);
+    std::vector<const float2*> t32(n_tables > 0 ? n_tables : 1, nullptr);
+    for (int t = 0; t < n_tables; t++) {
+        double* d64;
+        float2* d32;
+        std::vector<float2> f(table_lens[t]);
+        for (int64_t i = 0; i < table_lens[t]; i++) float_bounds(tables[t][i], &f[i].x, &f[i].y);
+        if ((e = upload(&d64, tables[t], (size_t)table_lens[t], p->owned))) return bad(e, "upload tables");
+        if ((e = upload(&d32, f.data(), f.size(), p->owned))) return bad(e, "upload tables");
+        t64[t] = d64;
+        t32[t] = d32;
+    }
+    const double** d_t64;
+    const float2** d_t32;
+    if ((e = upload(&d_t64, t64.data(), t64.size(), p->owned))) return bad(e, "upload tables");
+    if ((e = upload(&d_t32, t32.data(), t32.size(), p->owned))) return bad(e, "upload tables");
+    P.outer = d_outer;
+    P.tins = d_tins;
+    P.sums = d_sums;
+    P.groups = d_groups;
+    P.dirty = d_dirty;
+    P.var_leaves = d_leaves;
+    P.tab64 = d_t64;
+    P.tab32 = d_t32;
+    P.l = d_l;
+    P.u = d_u;
+
+    // ---- solver buffers ------------------------------------------------------
+    const int m = opt.split_m, d = opt.split_d;
+    p->fan = 1LL << (d * mshift);
+    p->Cmax = (opt.max_children / p->fan) * p->fan;
+    if (p->Cmax < p->fan) p->Cmax = p->fan;
+    p->K = p->Cmax / p->fan;
+    p->sp = GbSplit{m, mshift, d, d * mshift, d};
+    const int fp32 = opt.fp32_prefilter ? 1 : 0;
+    const int NG = P.n_groups > 0 ? P.n_groups : 1;
+    size_t per_slot = (size_t)n * 16 + (fp32 ? (size_t)n * 8 : 0) + (size_t)NG * 32 + (fp32 ? (size_t)NG * 8 : 0) +
+                      4 + 2 * 16;
+    long long cap = opt.max_boxes > 0 ? opt.max_boxes : (long long)(opt.pool_bytes / per_slot);
+    if (cap < 1) return bad(cudaErrorMemoryAllocation, "pool budget below one box");
+    if (cap > (1LL << 31) - 1) cap = (1LL << 31) - 1;
+    p->cap = cap;
+    GbPool& pl = p->pool;
+    pl.n = n;
+    pl.NG = NG;
+    pl.fp32 = fp32;
+    if ((e = alloc(&pl.lo64, (size_t)cap * n, p->owned)) || (e = alloc(&pl.hi64, (size_t)cap * n, p->owned)) ||
+        (e = alloc(&pl.gsum, (size_t)cap * NG, p->owned)) || (e = alloc(&pl.gmid, (size_t)cap * NG, p->owned)) ||
+        (e = alloc(&pl.freel, (size_t)cap, p->owned)))
+        return bad(e, "allocate box pool");
+    if (fp32) {
+        if ((e = alloc(&pl.lo32, (size_t)cap * n, p->owned)) || (e = alloc(&pl.hi32, (size_t)cap * n, p->owned)) ||
+            (e = alloc(&pl.gsum32, (size_t)cap * NG, p->owned)))
+            return bad(e, "allocate box pool");
+    }
+    for (int b = 0; b < 2; b++)
+        if ((e = alloc(&p->E[b].flo, (size_t)cap, p->owned)) || (e = alloc(&p->E[b].slot, (size_t)cap, p->owned)) ||
+            (e = alloc(&p->E[b].cyc, (size_t)cap, p->owned)))
+            return bad(e, "allocate pool entries");
+    const size_t K = (size_t)p->K, bt = K * d * (m + 1);
+    if ((e = alloc(&p->par.slot, K, p->owned)) || (e = alloc(&p->par.cyc, K, p->owned)) ||
+        (e = alloc(&p->par.flo, K, p->owned)) || (e = alloc(&p->par.info, K, p->owned)) ||
+        (e = alloc(&p->par.bnd, bt, p->owned)) || (e = alloc(&p->par.bnd_rd, bt, p->owned)) ||
+        (e = alloc(&p->par.bnd_ru, bt, p->owned)))
+        return bad(e, "allocate parent buffers");
+    const size_t C = (size_t)p->Cmax;
+    if ((e = alloc(&p->ch.flo, C, p->owned)) || (e = alloc(&p->ch.flag, C, p->owned)) ||
+        (e = alloc(&p->ch.flag32, C, p->owned)) || (e = alloc(&p->ch.list32, C, p->owned)) ||
+        (e = alloc(&p->ch.surv, C, p->owned)))
+        return bad(e, "allocate child buffers");
+    long long items = cap > p->Cmax ? cap : p->Cmax;
+    p->sc.max_tiles = (int)((items + GB_TILE - 1) / GB_TILE) + 1;
+    if ((e = alloc(&p->sc.tile_cnt, (size_t)3 * p->sc.max_tiles, p->owned)) ||
+        (e = alloc(&p->sc.tile_off, (size_t)3 * p->sc.max_tiles, p->owned)) ||
+        (e = alloc(&p->sc.hist, (size_t)65536, p->owned)) || (e = alloc(&p->out_list, (size_t)cap, p->owned)) ||
+        (e = alloc(&p->st, 1, p->owned)))
+        return bad(e, "allocate scan buffers");
+    if ((e = cudaMemset(p->sc.hist, 0, 65536 * sizeof(unsigned)))) return bad(e, "cudaMemset");
+    if ((e = cudaMallocHost((void**)&p->st_host, sizeof(GbState)))) return bad(e, "cudaMallocHost");
+    if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking))) return bad(e, "cudaStreamCreate");
+    for (cudaEvent_t& ev : p->ev)
+        if ((e = cudaEventCreate(&ev))) return bad(e, "cudaEventCreate");
+    *out = p;
+    return GB_OK;
+}
+
+gb_status gb_problem_info(const gb_problem* p, int32_t* block, int32_t* n_blocks, int64_t* ops_eval,
+                          int64_t* ops_mid) {
+    if (!p) return fail(GB_E_INVALID, "NULL problem");
+    if (block) *block = p->hp.B;
+    if (n_blocks) *n_blocks = p->hp.nb;
+    if (ops_eval) *ops_eval = p->hp.ops_eval;
+    if (ops_mid) *ops_mid = p->hp.ops_mid;
+    return GB_OK;
+}
+
+void gb_free_result(gb_result* r) {
+    if (!r) return;
+    std::free(r->box_lo);
+    std::free(r->box_hi);
+    std::free(r->box_flo);
+    std::free(r->trace);
+    std::memset(r, 0, sizeof(*r));
+}
+
+static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
+    if (!p || !out) return fail(GB_E_INVALID, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    GB_CU(cudaSetDevice(p->device));
+    auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = gb_launches_so_far();
+    cudaStream_t s = p->stream;
+    GbState init{};
+    init.cap = p->cap;
+    GB_CU(cudaEventRecord(p->ev[0], s));
+    GB_CU(cudaMemcpyAsync(p->st, &init, sizeof(GbState), cudaMemcpyHostToDevice, s));
+    GB_CU(gb_launch_root_init(p->P, p->pool, p->E[0], p->st, s));
+    GB_CU(gb_launch_stats(p->E[0], 1, p->tol_f, p->st, s));
+    int cur = 0;
+    std::vector<gb_gen_stat> trace;
+    gb_status status = GB_OK;
+    long long last_par = 0, last_children = 0;
+    bool timed64 = false, timed32 = false;
+    double t64 = 0.0, t32 = 0.0;
+    long long n64 = 0, n32 = 0;
+    for (;;) {
+        GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
+        GB_CU(cudaStreamSynchronize(s));
+        GbState h = *p->st_host;
+        double gub = gb_key_value(h.gub_key);
+        float ms = 0.f;
+        if (timed64 && cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) t64 += ms, n64++;
+        if (timed32 && cudaEventElapsedTime(&ms, p->ev[4], p->ev[5]) == cudaSuccess) t32 += ms, n32++;
+        timed64 = timed32 = false;
+        if (h.gen > 0) {
+            gb_gen_stat g;
+            g.parents = last_par;
+            g.children = last_children;
+            g.kept32 = p->opt.fp32_prefilter ? h.kept32 : last_children;
+            g.kept = h.overflow ? 0 : h.kept;
+            g.pool = h.pool;
+            g.gub = gub;
+            if ((long long)trace.size() < h.gen) trace.push_back(g);
+        }
+        if (h.error) {
+            status = fail(GB_E_CUDA, "device-side selection error");
+            break;
+        }
+        if (h.overflow) {
+            status = GB_E_CAPACITY;
+            g_err = "box pool capacity reached";
+            break;
+        }
+        if (h.active == 0) break;
+        if (h.gen >= p->opt.max_generations) {
+            status = GB_E_LIMIT;
+            g_err = "generation limit reached";
+            break;
+        }
+        const long long count = h.pool;
+        const long long npar = h.active < p->K ? h.active : p->K;
+        const long long nch = npar * p->fan;
+        GB_CU(gb_launch_select(p->E[cur], count, h.active, p->K, gub, p->tol_f, p->st, p->sc, s));
+        GB_CU(gb_launch_partition(p->E[cur], count, gub, p->tol_f, p->E[1 - cur], p->par, p->pool, p->st, p->sc, s));
+        GB_CU(gb_launch_prep(p->P, p->pool, p->par, npar, p->sp, p->st, s));
+        if (p->opt.fp32_prefilter) {
+            GB_CU(cudaEventRecord(p->ev[4], s));
+            GB_CU(gb_launch_eval32(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, p->st, s));
+            GB_CU(cudaEventRecord(p->ev[5], s));
+            GB_CU(gb_launch_compact_children(p->ch, nch, 0, p->st, p->sc, s));
+            GB_CU(cudaEventRecord(p->ev[2], s));
+            GB_CU(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, true, p->st, s));
+            GB_CU(cudaEventRecord(p->ev[3], s));
+            timed32 = true;
+        } else {
+            GB_CU(cudaEventRecord(p->ev[2], s));
+            GB_CU(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, false, p->st, s));
+            GB_CU(cudaEventRecord(p->ev[3], s));
+        }
+        timed64 = true;
+        GB_CU(gb_launch_compact_children(p->ch, nch, 1, p->st, p->sc, s));
+        GB_CU(gb_launch_materialize(p->P, p->pool, p->par, p->ch, nch, p->sp, p->E[1 - cur], p->opt.tol_x, p->st, s));
+        GB_CU(gb_launch_finish(p->par, npar, p->pool, p->E[1 - cur], p->st, s));
+        cur = 1 - cur;
+        last_par = npar;
+        last_children = nch;
+        long long bound = count + nch;
+        GB_CU(gb_launch_stats(p->E[cur], bound < p->cap ? bound : p->cap, p->tol_f, p->st, s));
+    }
+    // ---- output: boxes with LB <= GUB, GLB -------------------------------------
+    GbState h = *p->st_host;
+    double gub = gb_key_value(h.gub_key);
+    unsigned long long ones = ~0ull;
+    GB_CU(cudaMemcpyAsync(&p->st->glb_key, &ones, sizeof(ones), cudaMemcpyHostToDevice, s));
+    GB_CU(gb_launch_output(p->E[cur], h.pool, p->pool, gub, p->out_list, nullptr, nullptr, nullptr, p->st, p->sc, s));
+    GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
+    GB_CU(cudaStreamSynchronize(s));
+    GbState hf = *p->st_host;
+    const long long nbox = hf.kept;
+    out->n = p->n;
+    out->n_boxes = nbox;
+    out->fmin_hi = gub;
+    out->fmin_lo = hf.glb_key == ~0ull ? -INFINITY : gb_key_value(hf.glb_key);
+    out->generations = hf.gen;
+    out->box_evals_fp32 = hf.evals32;
+    out->box_evals_fp64 = hf.evals64;
+    out->mid_evals = hf.mids;
+    out->eval64_ms = t64;
+    out->eval32_ms = t32;
+    out->eval64_launches = n64;
+    out->eval32_launches = n32;
+    if (copy_boxes && nbox > 0) {
+        size_t nb = (size_t)nbox * p->n;
+        double *d_lo = nullptr, *d_hi = nullptr, *d_flo = nullptr;
+        cudaError_t e1 = cudaMallocAsync((void**)&d_lo, nb * sizeof(double), s);
+        cudaError_t e2 = cudaMallocAsync((void**)&d_hi, nb * sizeof(double), s);
+        cudaError_t e3 = cudaMallocAsync((void**)&d_flo, (size_t)nbox * sizeof(double), s);
+        if (e1 || e2 || e3) return cuda_fail(e1 ? e1 : (e2 ? e2 : e3), "allocate output");
+        GB_CU(gb_launch_output(p->E[cur], h.pool, p->pool, gub, p->out_list, d_lo, d_hi, d_flo, p->st, p->sc, s));
+        out->box_lo = (double*)std::malloc(nb * sizeof(double));
+        out->box_hi = (double*)std::malloc(nb * sizeof(double));
+        out->box_flo = (double*)std::malloc((size_t)nbox * sizeof(double));
+        if (!out->box_lo || !out->box_hi || !out->box_flo) return fail(GB_E_OOM, "host allocation");
+        GB_CU(cudaMemcpyAsync(out->box_lo, d_lo, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GB_CU(cudaMemcpyAsync(out->box_hi, d_hi, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GB_CU(cudaMemcpyAsync(out->box_flo, d_flo, (size_t)nbox * sizeof(double), cudaMemcpyDeviceToHost, s));
+        cudaFreeAsync(d_lo, s);
+        cudaFreeAsync(d_hi, s);
+        cudaFreeAsync(d_flo, s);
+        GB_CU(cudaStreamSynchronize(s));
+    }
+    GB_CU(cudaEventRecord(p->ev[1], s));
+    GB_CU(cudaEventSynchronize(p->ev[1]));
+    {
+        float ms = 0.f;
+        GB_CU(cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
+        out->device_ms = ms;
+    }
+    out->kernel_launches = gb_launches_so_far() - launches0;
+    out->n_trace = (int64_t)trace.size();
+    if (!trace.empty()) {
+        out->trace = (gb_gen_stat*)std::malloc(trace.size() * sizeof(gb_gen_stat));
+        std::memcpy(out->trace, trace.data(), trace.size() * sizeof(gb_gen_stat));
+    }
+    out->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    out->status = status;
+    return status;
+}
+
+gb_status gb_solve(gb_problem* p, gb_result* out) { return solve_impl(p, out, true); }
+
+gb_status gb_solve_device(gb_problem* p, gb_result* out) { return solve_impl(p, out, false); }
+
+gb_status gb_eval_boxes(gb_problem* p, const double* d_lo, const double* d_hi, int64_t nbox, int32_t blk,
+                        int32_t fp32, double* d_F, double* d_Fmid, double* d_G, int32_t* d_mono, void* stream) {
+    if (!p) return fail(GB_E_INVALID, "NULL problem");
+    if (nbox < 0 || blk >= p->hp.nb || (nbox > 0 && (!d_lo || !d_hi || !d_F || !d_Fmid)) ||
+        (blk >= 0 && nbox > 0 && (!d_G || !d_mono)))
+        return fail(GB_E_INVALID, "bad arguments to gb_eval_boxes");
+    if (nbox == 0) return GB_OK;
+    GB_CU(cudaSetDevice(p->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    float* scratch = nullptr;
+    if (fp32) {
+        size_t cnt = (size_t)nbox * p->n * 2;
+        GB_CU(cudaMallocAsync((void**)&scratch, cnt * sizeof(float), s));
+    }
+    cudaError_t e = gb_launch_eval_boxes(p->P, d_lo, d_hi, scratch, nbox, blk, fp32, d_F, d_Fmid, d_G, d_mono, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gb_eval_boxes launch");
+    return GB_OK;
+}
+
+gb_status gb_measure_peak(int32_t device, int32_t which, double* ops_per_s, double* ms_out) {
+    if (!ops_per_s || (which != 0 && which != 1)) return fail(GB_E_INVALID, "bad arguments to gb_measure_peak");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(GB_E_CUDA, "no CUDA device available");
+    GB_CU(cudaSetDevice(device));
+    int sms = 0;
+    GB_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const int blocks = sms * 8, iters = which == 0 ? 20000 : 200000;
+    void* sink = nullptr;
+    GB_CU(cudaMalloc(&sink, 256 * sizeof(double)));
+    cudaEvent_t a, b;
+    GB_CU(cudaEventCreate(&a));
+    GB_CU(cudaEventCreate(&b));
+    GB_CU(gb_launch_peak(which, 100, blocks, sink, 0));   // warm-up
+    GB_CU(cudaEventRecord(a, 0));
+    GB_CU(gb_launch_peak(which, iters, blocks, sink, 0));
+    GB_CU(cudaEventRecord(b, 0));
+    GB_CU(cudaEventSynchronize(b));
+    float ms = 0.f;
+    GB_CU(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    double ops = 8.0 * iters * (double)blocks * 256.0;
+    *ops_per_s = ops / (ms * 1e-3);
+    if (ms_out) *ms_out = ms;
+    return GB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+// Expression-DAG -> device bytecode compiler.
+//
+// The objective arrives as the node array of include/gb.h.  The compiler
+//  1. validates it (operator codes, topological operands, coordinate and
+//     table ranges, finite constants);
+//  2. splits it into the outer expression (reachable from the root without
+//     entering a sum) and one template per ISUM node;
+//  3. emits straight-line bytecode with one register per node, in ascending
+//     node order, so that the reverse sweep (the interval gradient used by the
+//     first-order test of section 3.1) walks the same list backwards;
+//  4. groups the terms of every sum into maximal runs with the same range of
+//     touched cycling blocks (section 3.2 cycles the split over blocks of B
+//     coordinates) and records, for every block b, the run of groups whose
+//     terms touch it.  A box caches one partial sum per group; a child split
+//     in block b recomputes only those groups.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "gb_internal.h"
+
+namespace {
+
+// Outward conversion of an exact double to a float interval.
+void out_float(double c, float* lo, float* hi) {
+    float f = (float)c;
+    *lo = ((double)f <= c) ? f : std::nextafter(f, -INFINITY);
+    *hi = ((double)f >= c) ? f : std::nextafter(f, INFINITY);
+}
+
+int n_operands(int op) {
+    switch (op) {
+    case GB_OP_ADD: case GB_OP_SUB: case GB_OP_MUL: case GB_OP_DIV: return 2;
+    case GB_OP_NEG: case GB_OP_SQR: case GB_OP_SQRT: case GB_OP_EXP: case GB_OP_SIN:
+    case GB_OP_COS: case GB_OP_SCALE: return 1;
+    default: return 0;
+    }
+}
+
+uint8_t dev_op(int op) {
+    switch (op) {
+    case GB_OP_CONST: return D_CONST;
+    case GB_OP_PI: return D_PI;
+    case GB_OP_EULER: return D_EULER;
+    case GB_OP_VAR: return D_VAR;
+    case GB_OP_IDX_VAR: return D_IVAR;
+    case GB_OP_IDX_COEF: return D_COEF;
+    case GB_OP_ADD: return D_ADD;
+    case GB_OP_SUB: return D_SUB;
+    case GB_OP_MUL: return D_MUL;
+    case GB_OP_DIV: return D_DIV;
+    case GB_OP_NEG: return D_NEG;
+    case GB_OP_SQR: return D_SQR;
+    case GB_OP_SQRT: return D_SQRT;
+    case GB_OP_EXP: return D_EXP;
+    case GB_OP_SIN: return D_SIN;
+    case GB_OP_COS: return D_COS;
+    case GB_OP_SCALE: return D_SCALE;
+    default: return D_ISUMV;
+    }
+}
+
+// Directed-rounding floating-point operations of one instruction's forward
+// step (endpoint operations of the interval formula) and of its reverse step
+// (the adjoint products and the accumulation into each operand).
+int fwd_ops(uint8_t op) {
+    switch (op) {
+    case D_ADD: case D_SUB: case D_MUL: case D_SQR: case D_SCALE:
+    case D_SQRT: case D_EXP: case D_SIN: case D_COS: return 2;
+    case D_DIV: return 4;
+    default: return 0;
+    }
+}
+int rev_ops(uint8_t op) {
+    switch (op) {
+    case D_ADD: case D_SUB: return 4;               // two accumulations
+    case D_MUL: return 8;                           // two products, two accumulations
+    case D_DIV: return 12;
+    case D_NEG: return 2;
+    case D_SQR: case D_EXP: case D_SCALE: return 4; // product, accumulation
+    case D_SQRT: case D_SIN: case D_COS: return 6;
+    default: return 0;
+    }
+}
+
+struct Ctx {
+    const gb_node* nd;
+    int nn;
+    std::vector<char> outer, mark;
+};
+
+bool mark_outer(Ctx& c, int v, std::string& err) {
+    if (c.outer[v]) return true;
+    c.outer[v] = 1;
+    const gb_node& q = c.nd[v];
+    if (q.op == GB_OP_IDX_VAR || q.op == GB_OP_IDX_COEF) {
+        err = "IDX_VAR / IDX_COEF node " + std::to_string(v) + " used outside a sum template";
+        return false;
+    }
+    if (q.op == GB_OP_ISUM) return true;
+    int k = n_operands(q.op);
+    if (k >= 1 && !mark_outer(c, q.a, err)) return false;
+    if (k >= 2 && !mark_outer(c, q.b, err)) return false;
+    return true;
+}
+
+bool mark_template(Ctx& c, int v, std::string& err) {
+    if (c.mark[v]) return true;
+    c.mark[v] = 1;
+    const gb_node& q = c.nd[v];
+    if (q.op == GB_OP_VAR || q.op == GB_OP_ISUM) {
+        err = "VAR / ISUM node " + std::to_string(v) + " inside a sum template";
+        return false;
+    }
+    int k = n_operands(q.op);
+    if (k >= 1 && !mark_template(c, q.a, err)) return false;
+    if (k >= 2 && !mark_template(c, q.b, err)) return false;
+    return true;
+}
+
+}  // namespace
+
+std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_t* tlen,
+                       int32_t ntab, int32_t n, int32_t B, GbHostProg* P) {
+    if (nn < 1 || root < 0 || root >= nn) return "root outside the node array";
+    if (n < 1) return "dimension n must be >= 1";
+    if (B < 1 || B > n) return "block size must satisfy 1 <= B <= n";
+    if (ntab < 0) return "negative table count";
+    for (int v = 0; v < nn; v++) {
+        const gb_node& q = nd[v];
+        if (q.op < 0 || q.op > GB_OP_ISUM) return "unknown operator at node " + std::to_string(v);
+        if (q.pad != 0) return "nonzero pad at node " + std::to_string(v);
+        int k = n_operands(q.op);
+        if (k >= 1 && (q.a < 0 || q.a >= v)) return "operand not before node " + std::to_string(v);
+        if (k >= 2 && (q.b < 0 || q.b >= v)) return "operand not before node " + std::to_string(v);
+        if ((q.op == GB_OP_CONST || q.op == GB_OP_SCALE) && !std::isfinite(q.v))
+            return "non-finite constant at node " + std::to_string(v);
+        if (q.op == GB_OP_VAR && (q.a < 0 || q.a >= n)) return "VAR coordinate out of range";
+        if (q.op == GB_OP_ISUM && (q.a < 0 || q.a >= v || q.d < 1))
+            return "bad ISUM at node " + std::to_string(v);
+    }
+    Ctx c{nd, nn, std::vector<char>(nn, 0), std::vector<char>(nn, 0)};
+    std::string err;
+    if (!mark_outer(c, root, err)) return err;
+
+    P->n = n;
+    P->B = B;
+    P->nb = (n + B - 1) / B;
+    P->outer.clear(); P->tins.clear(); P->sums.clear(); P->groups.clear();
+    P->dirty.clear(); P->var_leaves.clear();
+
+    std::vector<int> oreg(nn, -1);
+    for (int v = 0; v < nn; v++)
+        if (c.outer[v]) oreg[v] = (int)(P->outer.size()), P->outer.push_back(GbIns{});
+    if ((int)P->outer.size() > GB_MAX_OREGS) return "outer expression exceeds the register limit";
+    P->outer_root = oreg[root];
+
+    for (int v = 0; v < nn; v++) {
+        if (!c.outer[v]) continue;
+        const gb_node& q = nd[v];
+        GbIns& I = P->outer[oreg[v]];
+        I = GbIns{};
+        I.op = dev_op(q.op);
+        I.dst = (uint8_t)oreg[v];
+        int k = n_operands(q.op);
+        if (k >= 1) I.a = (uint8_t)oreg[q.a];
+        if (k >= 2) I.b = (uint8_t)oreg[q.b];
+        I.c = q.v;
+        out_float(q.v, &I.clo32, &I.chi32);
+        if (q.op == GB_OP_VAR) {
+            I.aux = q.a;
+            P->var_leaves.push_back(GbVarLeaf{oreg[v], q.a});
+        }
+        if (q.op != GB_OP_ISUM) continue;
+
+        // ---- an ISUM node: its template -----------------------------------
+        int ks = (int)P->sums.size();
+        if (ks >= GB_MAX_ISUM) return "too many sums";
+        I.aux = ks;
+        std::fill(c.mark.begin(), c.mark.end(), 0);
+        if (!mark_template(c, q.a, err)) return err;
+        std::vector<int> treg(nn, -1);
+        GbSum S{};
+        S.ins0 = (int)P->tins.size();
+        int omin = 0, omax = 0, hv = 0, nleaf = 0;
+        for (int t = 0; t <= q.a; t++) {
+            if (!c.mark[t]) continue;
+            treg[t] = (int)P->tins.size() - S.ins0;
+            const gb_node& w = nd[t];
+            GbIns J{};
+            J.op = dev_op(w.op);
+            J.dst = (uint8_t)treg[t];
+            int kk = n_operands(w.op);
+            if (kk >= 1) J.a = (uint8_t)treg[w.a];
+            if (kk >= 2) J.b = (uint8_t)treg[w.b];
+            J.c = w.v;
+            out_float(w.v, &J.clo32, &J.chi32);
+            if (w.op == GB_OP_IDX_VAR) {
+                J.aux = w.b;
+                if (!hv) omin = omax = w.b, hv = 1;
+                omin = std::min(omin, w.b);
+                omax = std::max(omax, w.b);
+                nleaf++;
+            }
+            if (w.op == GB_OP_IDX_COEF) {
+                if (w.a < 0 || w.a >= ntab) return "IDX_COEF table out of range";
+                J.aux = w.a;
+                J.aux2 = w.b;
+            }
+            P->tins.push_back(J);
+        }
+        S.nins = (int)P->tins.size() - S.ins0;
+        if (S.nins > GB_MAX_TREGS) return "sum template exceeds the register limit";
+        if (treg[q.a] != S.nins - 1) return "internal: template root is not last";
+        S.first = q.b;
+        S.step = q.d;
+        S.count = q.c > q.b ? (q.c - q.b + q.d - 1) / q.d : 0;
+        if (S.count >= (1 << 20)) return "sum with 2^20 or more terms";  // reduction tree depth limit
+        S.off_min = omin;
+        S.off_max = omax;
+        S.has_var = hv;
+        S.nvar_leaves = nleaf;
+        S.outer_reg = oreg[v];
+        if (hv && omax - omin + 1 > GB_MAX_WIN) return "IDX_VAR offsets span too wide";
+        if (S.count > 0) {
+            int64_t i0 = S.first, i1 = (int64_t)S.first + (int64_t)(S.count - 1) * S.step;
+            if (hv && (i0 + omin < 0 || i1 + omax >= n)) return "IDX_VAR index out of range";
+            for (int t = S.ins0; t < S.ins0 + S.nins; t++) {
+                const GbIns& J = P->tins[t];
+                if (J.op != D_COEF) continue;
+                if (i0 + J.aux2 < 0 || i1 + J.aux2 >= tlen[J.aux]) return "IDX_COEF index out of range";
+            }
+        }
+        // groups: runs of terms with the same touched-block range
+        S.group0 = (int)P->groups.size();
+        for (int t = 0; t < S.count; t++) {
+            int i = S.first + t * S.step;
+            int b0 = hv ? (i + omin) / B : -1, b1 = hv ? (i + omax) / B : -1;
+            if (t == 0 || P->groups.back().bmin != b0 || P->groups.back().bmax != b1)
+                P->groups.push_back(GbGroup{t, 0, b0, b1});
+            P->groups.back().count++;
+        }
+        S.ngroups = (int)P->groups.size() - S.group0;
+        P->sums.push_back(S);
+    }
+    // dirty group ranges per block (local indices within each sum)
+    int ns = (int)P->sums.size();
+    P->dirty.assign((size_t)P->nb * ns, int2{0, 0});
+    for (int b = 0; b < P->nb; b++)
+        for (int k = 0; k < ns; k++) {
+            const GbSum& S = P->sums[k];
+            int g0 = -1, g1 = -1;
+            for (int g = 0; g < S.ngroups; g++) {
+                const GbGroup& G = P->groups[S.group0 + g];
+                if (G.bmin <= b && b <= G.bmax) {
+                    if (g0 < 0) g0 = g;
+                    g1 = g + 1;
+                }
+            }
+            if (g0 < 0) g0 = g1 = 0;
+            P->dirty[(size_t)b * ns + k] = int2{g0, g1};
+        }
+
+    // static directed-op counts, averaged over the blocks
+    int64_t tot_eval = 0, tot_mid = 0;
+    int64_t outer_f = 0, outer_r = 0;
+    for (auto& I : P->outer) outer_f += fwd_ops(I.op), outer_r += rev_ops(I.op);
+    for (int b = 0; b < P->nb; b++) {
+        int64_t ev = outer_f + outer_r, md = outer_f;
+        int c0 = b * B, c1 = std::min(n, c0 + B);
+        for (int k = 0; k < ns; k++) {
+            const GbSum& S = P->sums[k];
+            int64_t tf = 0, tr = 0;
+            for (int t = S.ins0; t < S.ins0 + S.nins; t++)
+                tf += fwd_ops(P->tins[t].op), tr += rev_ops(P->tins[t].op);
+            int2 dr = P->dirty[(size_t)b * ns + k];
+            int64_t dterms = 0;
+            for (int g = dr.x; g < dr.y; g++) dterms += P->groups[S.group0 + g].count;
+            int64_t tree = 2 * std::max(0, S.ngroups - 1) + 2 * std::max<int64_t>(0, dterms - (dr.y - dr.x));
+            ev += dterms * tf + tree;
+            md += dterms * tf + tree + 2 * dterms * S.nvar_leaves;  // midpoint of each loaded coordinate
+            if (!S.has_var) continue;
+            int64_t gterms = 0;
+            for (int t = 0; t < S.count; t++) {
+                int i = S.first + t * S.step;
+                if (i + S.off_max >= c0 && i + S.off_min < c1) gterms++;
+            }
+            ev += gterms * (tf + tr) + 2 * gterms * S.nvar_leaves + 2 * (c1 - c0);
+        }
+        tot_eval += ev;
+        tot_mid += md;
+    }
+    P->ops_eval = tot_eval / P->nb;
+    P->ops_mid = tot_mid / P->nb;
+    return "";
+}

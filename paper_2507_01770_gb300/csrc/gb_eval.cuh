@@ -1,0 +1,346 @@
+// Device evaluation of the compiled objective over one box (one thread).
+//
+//  * natural interval extension of f (section 2.1): the template bytecode of
+//    every sum and the outer bytecode are interpreted instruction by
+//    instruction with the outward-rounded operations of gb_interval.cuh;
+//  * sums are reduced in a fixed order: within a group of terms by a pairwise
+//    tree in term order, then over the groups by a pairwise tree in group
+//    order.  The tree is computed with a binary counter (level L holds the
+//    sum of 2^L consecutive items), which forms exactly the in-place pairwise
+//    tree a[i] += a[i + s], s = 1, 2, 4, ...;
+//  * a child of a cached parent recomputes only the groups that touch its
+//    split block and reuses the parent's cached group sums for the rest;
+//  * the interval partials of the active block's coordinates (the DLB/DUB of
+//    the first-order test, section 3.1) come from a reverse sweep over the
+//    outer bytecode and, per term, over the template bytecode seeded with
+//    [1, 1]; leaf adjoints are accumulated per coordinate in ascending term
+//    and leaf order, then multiplied by the sum's outer adjoint.
+#pragma once
+#include "gb_internal.h"
+#include "gb_interval.cuh"
+
+namespace gb {
+
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+    typedef iv64 I;
+    static __device__ __forceinline__ I coef(const GbProg& P, int t, int idx) {
+        double c = __ldg(P.tab64[t] + idx);
+        return I{c, c};
+    }
+    static __device__ __forceinline__ I cst(const GbIns& in) { return I{in.c, in.c}; }
+};
+template <> struct Prec<float> {
+    typedef iv32 I;
+    static __device__ __forceinline__ I coef(const GbProg& P, int t, int idx) {
+        float2 c = __ldg(P.tab32[t] + idx);
+        return I{c.x, c.y};
+    }
+    static __device__ __forceinline__ I cst(const GbIns& in) { return I{in.clo32, in.chi32}; }
+};
+
+// Coordinates of a box in precision T.  Coordinates [c0, c0 + dd) come from
+// a split table: piece `digit` of coordinate c0 + k spans
+// [blo[k * (m + 1) + digit], bhi[k * (m + 1) + digit + 1]]; the others from
+// the row (plo, phi).  dd = 0 views a plain box.
+template <typename T> struct View {
+    const T* plo;
+    const T* phi;
+    const T* blo;
+    const T* bhi;
+    int c0, dd, mshift, mstride;
+    unsigned r;
+    __device__ __forceinline__ typename Prec<T>::I get(int j) const {
+        unsigned k = (unsigned)(j - c0);
+        typename Prec<T>::I x;
+        if (k < (unsigned)dd) {
+            int dig = (r >> (k * mshift)) & ((1 << mshift) - 1);
+            x.lo = blo[k * mstride + dig];
+            x.hi = bhi[k * mstride + dig + 1];
+        } else {
+            x.lo = plo[j];
+            x.hi = phi[j];
+        }
+        return x;
+    }
+};
+
+// The FP64 midpoint sample point m = RN(0.5 lo + 0.5 hi) of each coordinate.
+struct MidView {
+    View<double> v;
+    __device__ __forceinline__ iv64 get(int j) const {
+        iv64 x = v.get(j);
+        double m = __dadd_rn(__dmul_rn(0.5, x.lo), __dmul_rn(0.5, x.hi));
+        return iv64{m, m};
+    }
+};
+
+// Binary-counter pairwise tree.
+template <typename I> struct Tree {
+    I lvl[20];
+    unsigned cnt;
+    __device__ __forceinline__ void init() { cnt = 0; }
+    __device__ __forceinline__ void push(I v) {
+        unsigned c = cnt;
+        int L = 0;
+        while (c & 1u) {
+            v = iadd(lvl[L], v);
+            c >>= 1;
+            L++;
+        }
+        lvl[L] = v;
+        cnt++;
+    }
+    __device__ __forceinline__ I result() const {
+        I r;
+        bool have = false;
+        for (int L = 0; L < 20; L++) {
+            if (!((cnt >> L) & 1u)) continue;
+            r = have ? iadd(lvl[L], r) : lvl[L];
+            have = true;
+        }
+        if (!have) { r.lo = 0; r.hi = 0; }
+        return r;
+    }
+};
+
+// Forward interpretation of one template for term index i; returns the root.
+template <typename T, typename V>
+__device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const GbSum& S, int i,
+                                                         const V& X, typename Prec<T>::I* R) {
+    typedef typename Prec<T>::I I;
+    const GbIns* ins = P.tins + S.ins0;
+    for (int t = 0; t < S.nins; t++) {
+        GbIns in = ins[t];
+        I v;
+        switch (in.op) {
+        case D_CONST: v = Prec<T>::cst(in); break;
+        case D_PI: v = pi_iv((T)0); break;
+        case D_EULER: v = e_iv((T)0); break;
+        case D_IVAR: v = X.get(i + in.aux); break;
+        case D_COEF: v = Prec<T>::coef(P, in.aux, i + in.aux2); break;
+        case D_ADD: v = iadd(R[in.a], R[in.b]); break;
+        case D_SUB: v = isub(R[in.a], R[in.b]); break;
+        case D_MUL: v = imul(R[in.a], R[in.b]); break;
+        case D_DIV: v = idiv(R[in.a], R[in.b]); break;
+        case D_NEG: v = ineg(R[in.a]); break;
+        case D_SQR: v = isqr(R[in.a]); break;
+        case D_SQRT: v = isqrt(R[in.a]); break;
+        case D_EXP: v = iexp(R[in.a]); break;
+        case D_SIN: v = itrig(R[in.a], false); break;
+        case D_COS: v = itrig(R[in.a], true); break;
+        case D_SCALE:
+            if (in.clo32 == in.chi32 || sizeof(T) == 8)
+                v = iscale(R[in.a], sizeof(T) == 8 ? (T)in.c : (T)in.clo32);
+            else
+                v = imul(R[in.a], mk<T>((T)in.clo32, (T)in.chi32));
+            break;
+        default: v.lo = 0; v.hi = 0; break;
+        }
+        R[t] = v;
+    }
+    return R[S.nins - 1];
+}
+
+// Reverse sweep over a bytecode list (forward values V, adjoints A already
+// seeded).  Node t pushes into its first, then its second operand; a node's
+// adjoint thus receives its consumers' contributions in descending order.
+template <typename T>
+__device__ __forceinline__ void reverse_sweep(const GbIns* ins, int nins, const typename Prec<T>::I* V,
+                                              typename Prec<T>::I* A) {
+    typedef typename Prec<T>::I I;
+    for (int t = nins - 1; t >= 0; t--) {
+        GbIns in = ins[t];
+        I g = A[t];
+        switch (in.op) {
+        case D_ADD:
+            A[in.a] = iadd(A[in.a], g);
+            A[in.b] = iadd(A[in.b], g);
+            break;
+        case D_SUB:
+            A[in.a] = iadd(A[in.a], g);
+            A[in.b] = iadd(A[in.b], ineg(g));
+            break;
+        case D_MUL: {
+            I va = V[in.a], vb = V[in.b];
+            A[in.a] = iadd(A[in.a], imul(g, vb));
+            A[in.b] = iadd(A[in.b], imul(g, va));
+            break;
+        }
+        case D_DIV: {
+            I rb = ircp(V[in.b]);
+            A[in.a] = iadd(A[in.a], imul(g, rb));
+            A[in.b] = iadd(A[in.b], imul(g, ineg(imul(V[t], rb))));
+            break;
+        }
+        case D_NEG: A[in.a] = iadd(A[in.a], ineg(g)); break;
+        case D_SQR: A[in.a] = iadd(A[in.a], imul(g, iscale(V[in.a], (T)2))); break;
+        case D_SQRT: A[in.a] = iadd(A[in.a], imul(g, iscale(ircp(V[t]), (T)0.5))); break;
+        case D_EXP: A[in.a] = iadd(A[in.a], imul(g, V[t])); break;
+        case D_SIN: A[in.a] = iadd(A[in.a], imul(g, itrig(V[in.a], true))); break;
+        case D_COS: A[in.a] = iadd(A[in.a], imul(g, ineg(itrig(V[in.a], false)))); break;
+        case D_SCALE:
+            if (in.clo32 == in.chi32 || sizeof(T) == 8)
+                A[in.a] = iadd(A[in.a], iscale(g, sizeof(T) == 8 ? (T)in.c : (T)in.clo32));
+            else
+                A[in.a] = iadd(A[in.a], imul(g, mk<T>((T)in.clo32, (T)in.chi32)));
+            break;
+        default: break;
+        }
+    }
+}
+
+// Sum of the terms of one group (local group g of sum S).
+template <typename T, typename V>
+__device__ __forceinline__ typename Prec<T>::I group_sum(const GbProg& P, const GbSum& S, int g, const V& X,
+                                                          typename Prec<T>::I* R) {
+    typedef typename Prec<T>::I I;
+    GbGroup G = P.groups[S.group0 + g];
+    Tree<I> tr;
+    tr.init();
+    for (int t = 0; t < G.count; t++) tr.push(term_fwd<T>(P, S, S.first + (G.t0 + t) * S.step, X, R));
+    return tr.result();
+}
+
+// Value of every sum: dirty groups recomputed, the others read from `cache`
+// (one interval per global group; NULL: recompute everything).
+template <typename T, typename V, typename C>
+__device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X, const C* cache,
+                                           typename Prec<T>::I* R, typename Prec<T>::I* sums) {
+    typedef typename Prec<T>::I I;
+    for (int k = 0; k < P.n_sum; k++) {
+        GbSum S = P.sums[k];
+        int2 dr = cache ? P.dirty[blk * P.n_sum + k] : make_int2(0, S.ngroups);
+        Tree<I> tr;
+        tr.init();
+        for (int g = 0; g < S.ngroups; g++) {
+            I v;
+            if (g >= dr.x && g < dr.y) {
+                v = group_sum<T>(P, S, g, X, R);
+            } else {
+                C c = cache[S.group0 + g];
+                v.lo = c.x;
+                v.hi = c.y;
+            }
+            tr.push(v);
+        }
+        sums[k] = tr.result();
+    }
+}
+
+// Outer forward pass; O receives all outer registers, returns F.
+template <typename T, typename V>
+__device__ __forceinline__ typename Prec<T>::I outer_fwd(const GbProg& P, const V& X,
+                                                          const typename Prec<T>::I* sums,
+                                                          typename Prec<T>::I* O) {
+    typedef typename Prec<T>::I I;
+    for (int t = 0; t < P.n_outer; t++) {
+        GbIns in = P.outer[t];
+        I v;
+        switch (in.op) {
+        case D_CONST: v = Prec<T>::cst(in); break;
+        case D_PI: v = pi_iv((T)0); break;
+        case D_EULER: v = e_iv((T)0); break;
+        case D_VAR: v = X.get(in.aux); break;
+        case D_ISUMV: v = sums[in.aux]; break;
+        case D_ADD: v = iadd(O[in.a], O[in.b]); break;
+        case D_SUB: v = isub(O[in.a], O[in.b]); break;
+        case D_MUL: v = imul(O[in.a], O[in.b]); break;
+        case D_DIV: v = idiv(O[in.a], O[in.b]); break;
+        case D_NEG: v = ineg(O[in.a]); break;
+        case D_SQR: v = isqr(O[in.a]); break;
+        case D_SQRT: v = isqrt(O[in.a]); break;
+        case D_EXP: v = iexp(O[in.a]); break;
+        case D_SIN: v = itrig(O[in.a], false); break;
+        case D_COS: v = itrig(O[in.a], true); break;
+        case D_SCALE:
+            if (in.clo32 == in.chi32 || sizeof(T) == 8)
+                v = iscale(O[in.a], sizeof(T) == 8 ? (T)in.c : (T)in.clo32);
+            else
+                v = imul(O[in.a], mk<T>((T)in.clo32, (T)in.chi32));
+            break;
+        default: v.lo = 0; v.hi = 0; break;
+        }
+        O[t] = v;
+    }
+    return O[P.outer_root];
+}
+
+// First-order test over the coordinates of block blk (section 3.1): returns
+// true if some partial excludes 0 with the corresponding face off the domain
+// edge.  X64 gives the FP64 box for the edge comparison.  G (optional)
+// receives the partials of the block.  Needs the outer registers O of the
+// forward pass.
+template <typename T, typename V>
+__device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X, const View<double>& X64,
+                                           const typename Prec<T>::I* O, typename Prec<T>::I* OA,
+                                           typename Prec<T>::I* R, typename Prec<T>::I* RA,
+                                           double* Gout) {
+    typedef typename Prec<T>::I I;
+    // outer adjoints
+    for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
+    OA[P.outer_root] = mk<T>((T)1, (T)1);
+    reverse_sweep<T>(P.outer, P.n_outer, O, OA);
+
+    const int c0 = blk * P.B;
+    const int c1 = min(P.n, c0 + P.B);
+    I W[GB_MAX_ISUM][GB_MAX_WIN];
+    unsigned touched[GB_MAX_ISUM];
+    int cur[GB_MAX_ISUM];
+    for (int k = 0; k < P.n_sum; k++) {
+        GbSum S = P.sums[k];
+        // first term whose touched range reaches c0
+        int need = c0 - S.off_max - S.first;
+        cur[k] = need <= 0 ? 0 : (need + S.step - 1) / S.step;
+        touched[k] = 0;
+        for (int w = 0; w < GB_MAX_WIN; w++) W[k][w] = mk<T>((T)0, (T)0);
+    }
+    bool mono = false;
+    for (int j = c0; j < c1; j++) {
+        I g = mk<T>((T)0, (T)0);
+        for (int v = 0; v < P.n_var_leaves; v++) {
+            GbVarLeaf L = P.var_leaves[v];
+            if (L.coord == j) g = iadd(g, OA[L.reg]);
+        }
+        for (int k = 0; k < P.n_sum; k++) {
+            GbSum S = P.sums[k];
+            if (!S.has_var) continue;
+            while (cur[k] < S.count && S.first + cur[k] * S.step + S.off_min <= j) {
+                int i = S.first + cur[k] * S.step;
+                term_fwd<T>(P, S, i, X, R);
+                for (int t = 0; t < S.nins; t++) RA[t] = mk<T>((T)0, (T)0);
+                RA[S.nins - 1] = mk<T>((T)1, (T)1);
+                const GbIns* ins = P.tins + S.ins0;
+                reverse_sweep<T>(ins, S.nins, R, RA);
+                for (int t = 0; t < S.nins; t++) {
+                    GbIns in = ins[t];
+                    if (in.op != D_IVAR) continue;
+                    int cc = i + in.aux;
+                    if (cc < c0 || cc >= c1) continue;
+                    int w = cc & (GB_MAX_WIN - 1);
+                    W[k][w] = iadd(W[k][w], RA[t]);
+                    touched[k] |= 1u << w;
+                }
+                cur[k]++;
+            }
+            int w = j & (GB_MAX_WIN - 1);
+            if (touched[k] & (1u << w)) {
+                g = iadd(g, imul(OA[S.outer_reg], W[k][w]));
+                W[k][w] = mk<T>((T)0, (T)0);
+                touched[k] &= ~(1u << w);
+            }
+        }
+        if (Gout) {
+            Gout[2 * (j - c0)] = (double)g.lo;
+            Gout[2 * (j - c0) + 1] = (double)g.hi;
+        }
+        iv64 x = X64.get(j);
+        if ((g.lo > (T)0 && x.lo != __ldg(P.l + j)) || (g.hi < (T)0 && x.hi != __ldg(P.u + j))) {
+            mono = true;
+            if (!Gout) break;
+        }
+    }
+    return mono;
+}
+
+}  // namespace gb

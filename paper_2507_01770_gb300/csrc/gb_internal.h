@@ -1,0 +1,141 @@
+// Internal data structures of the library: the compiled device program of an
+// objective and the device-side solver state.  Shared by the host compiler
+// (gb_compile.cpp) and the CUDA kernels; not part of the public ABI.
+#pragma once
+#include <stdint.h>
+#include <vector_types.h>
+
+#include "../../include/gb.h"
+
+#ifdef __CUDACC__
+#define GB_HD __host__ __device__
+#else
+#define GB_HD
+#endif
+
+// Limits of the bytecode interpreter (registers live in thread-local arrays).
+#define GB_MAX_TREGS 24   // nodes of one ISUM template
+#define GB_MAX_OREGS 32   // nodes of the outer expression
+#define GB_MAX_ISUM 6     // ISUM nodes per objective
+#define GB_MAX_WIN 4      // IDX_VAR offset span + 1 per template
+#define GB_MAX_SPLIT_D 12 // coordinates split per generation
+#define GB_MAX_FAN 4096   // children per parent (m^d)
+
+// Device opcodes of one instruction (registers are node slots).
+enum GbDevOp : uint8_t {
+    D_CONST = 0, D_PI, D_EULER, D_VAR, D_IVAR, D_COEF, D_ISUMV,
+    D_ADD, D_SUB, D_MUL, D_DIV, D_NEG, D_SQR, D_SQRT, D_EXP, D_SIN, D_COS, D_SCALE
+};
+
+struct GbIns {
+    uint8_t op;       // GbDevOp
+    uint8_t dst;      // destination register
+    uint8_t a, b;     // operand registers
+    int32_t aux;      // VAR coordinate | IVAR offset | COEF table | ISUMV slot
+    int32_t aux2;     // COEF offset
+    float clo32;      // c rounded down to float
+    float chi32;      // c rounded up to float
+    int32_t pad;
+    double c;         // CONST value | SCALE factor
+};  // 32 bytes
+
+// One ISUM node: its template bytecode and the grouping of its terms.
+// Terms are grouped into maximal runs with the same range of touched
+// cycling blocks; the cached partial sums of a box are kept per group.
+struct GbSum {
+    int32_t ins0, nins;      // template instructions [ins0, ins0 + nins)
+    int32_t first, step, count;  // index set {first + t * step : t < count}
+    int32_t off_min, off_max, has_var;
+    int32_t group0, ngroups; // global group ids [group0, group0 + ngroups)
+    int32_t outer_reg;       // outer register receiving the sum
+    int32_t nvar_leaves;     // IVAR instructions in the template
+};
+
+struct GbGroup {
+    int32_t t0, count;       // term ordinals [t0, t0 + count) of its ISUM
+    int32_t bmin, bmax;      // touched blocks (-1, -1 if the template has no IVAR)
+};
+
+// Outer VAR leaf: register and coordinate (for the gradient).
+struct GbVarLeaf { int32_t reg, coord; };
+
+// Program passed by value to kernels (pointers are device memory).
+struct GbProg {
+    int32_t n, B, nb;
+    int32_t n_sum, n_groups;         // ISUM nodes, total groups
+    int32_t n_outer, outer_root;     // outer instructions (register = index)
+    int32_t n_var_leaves;
+    const GbIns* outer;              // [n_outer]
+    const GbIns* tins;               // all template instructions
+    const GbSum* sums;               // [n_sum]
+    const GbGroup* groups;           // [n_groups]
+    const int2* dirty;               // [nb * n_sum]: dirty local group range per block
+    const GbVarLeaf* var_leaves;     // [n_var_leaves]
+    const double* const* tab64;      // [n_tables] table pointers
+    const float2* const* tab32;      // [n_tables] outward float pairs (lo, hi)
+    const double* l;                 // [n]
+    const double* u;                 // [n]
+};
+
+// Host-side compiled program (arrays in host memory before upload).
+#ifdef __cplusplus
+#include <string>
+#include <vector>
+struct GbHostProg {
+    int32_t n = 0, B = 0, nb = 0;
+    int32_t outer_root = 0;
+    std::vector<GbIns> outer, tins;
+    std::vector<GbSum> sums;
+    std::vector<GbGroup> groups;
+    std::vector<int2> dirty;
+    std::vector<GbVarLeaf> var_leaves;
+    int64_t ops_eval = 0, ops_mid = 0;   // static directed-op counts (see gb_compile.cpp)
+};
+// Compiles and validates a DAG; returns an empty string or an error message.
+std::string gb_compile(const gb_node* nodes, int32_t nn, int32_t root, const int64_t* tlen,
+                       int32_t ntab, int32_t n, int32_t B, GbHostProg* out);
+#endif
+
+// Order-preserving map of doubles to unsigned keys (for min reductions and
+// the best-first selection).
+GB_HD inline unsigned long long gb_order_key(double x) {
+    union { double d; unsigned long long u; } v;
+    v.d = x;
+    return (v.u >> 63) ? ~v.u : (v.u | 0x8000000000000000ull);
+}
+GB_HD inline double gb_key_value(unsigned long long k) {
+    union { double d; unsigned long long u; } v;
+    v.u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return v.d;
+}
+
+// Device-side solver state of one problem (one copy in device memory; the
+// host reads it back once per generation).
+struct GbState {
+    long long pool;             // entries in the current pool
+    long long nfree;            // slots on the free list
+    long long bump;             // next never-used slot
+    long long cap;              // slot capacity
+    long long active;           // active entries (F_lo < RU(GUB - tol_f), not final)
+    long long parents;          // parents selected this generation
+    long long drops;            // entries removed by the cut-off this generation
+    long long kept_old;         // entries carried over
+    long long children;         // children evaluated
+    long long kept32;           // children passing the FP32 pass
+    long long kept;             // children inserted
+    long long gen;              // generations completed
+    long long sel_below;        // selection: active entries with key < sel_T
+    long long sel_need;         // ties (key == sel_T) to take, the last ones in pool order
+    long long sel_ties;         // active entries with key == sel_T
+    long long radix_rank;       // radix select: remaining rank
+    long long n32;              // length of the FP32-survivor list
+    long long nfree_after_drop; // free-list size after the cut-off's frees
+    unsigned long long gub_key;     // incumbent upper bound (order key)
+    unsigned long long gub_new_key; // min over this generation's samples
+    unsigned long long sel_T;       // selection threshold key (~0: take all active)
+    unsigned long long radix_prefix;
+    unsigned long long glb_key;     // min lower bound over the pool (final pass)
+    int overflow;               // survivors do not fit: generation abandoned
+    int error;                  // device-side error code (bit flags)
+    long long evals32, evals64, mids;  // running counters
+};

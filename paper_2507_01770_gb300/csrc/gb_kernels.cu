@@ -1,0 +1,907 @@
+// Solver kernels: one generation of the batched best-first interval branch
+// and bound (section 3.1 flowchart; partition of Eqs. 7-11 with the variable
+// cycling of section 3.2), and the per-box evaluation used for parity.
+//
+// Generation, as launched by gb_api.cu:
+//   stats      active count over the pool (LB < RU(GUB - tol_f), not final)
+//   select     radix select of the K-th smallest LB key when active > K
+//   partition  stable 3-way split of the pool: cut off (LB > GUB, section 3.1
+//              "remove the suboptimal regions"), selected parents, kept
+//   prep       per parent: the m+1 piece boundaries of each split coordinate
+//   eval       per child: FP64 midpoint sample (GUB), F(X), first-order test;
+//              or FP32 pass, compaction, FP64 pass on the FP32 survivors
+//   compact    stable list of survivors (LB <= new GUB and not monotone)
+//   materialize survivors written into free slots with their group caches
+//   finish     parents' slots freed, counters rolled forward
+// All orderings are deterministic (no atomics decide an order).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gb_eval.cuh"
+#include "gb_launch.h"
+
+using namespace gb;
+
+namespace {
+
+__device__ __forceinline__ double canon_lo(double x) {
+    if (x != x) return -__longlong_as_double(0x7ff0000000000000LL);
+    if (x == 0.0) return 0.0;
+    return x;
+}
+
+__device__ __forceinline__ double thr_of(double gub, double tol_f) { return __dsub_ru(gub, tol_f); }
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive prefix of one flag per thread (item order = thread order)
+template <int NT>
+__device__ __forceinline__ int block_prefix(bool f, int* smem_warp, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned b = __ballot_sync(0xffffffffu, f);
+    int in_warp = __popc(b & ((1u << lane) - 1u));
+    if (lane == 0) smem_warp[wid] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int w = 0; w < NT / 32; w++) {
+            int c = smem_warp[w];
+            smem_warp[w] = acc;
+            acc += c;
+        }
+        smem_warp[NT / 32] = acc;
+    }
+    __syncthreads();
+    int r = smem_warp[wid] + in_warp;
+    *total = smem_warp[NT / 32];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Root box: the whole domain [l, u] (section 3.1 "initialization").
+__global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, GbState* st) {
+    const int n = P.n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double l = P.l[j], u = P.u[j];
+        pool.lo64[j] = l;
+        pool.hi64[j] = u;
+        if (pool.fp32) {
+            pool.lo32[j] = __double2float_rd(l);
+            pool.hi32[j] = __double2float_ru(u);
+        }
+    }
+    __syncthreads();
+    View<double> X{pool.lo64, pool.hi64, nullptr, nullptr, 0, 0, 1, 2, 0u};
+    MidView MX{X};
+    View<float> X32{pool.lo32, pool.hi32, nullptr, nullptr, 0, 0, 1, 2, 0u};
+    iv64 R[GB_MAX_TREGS];
+    iv32 R32[GB_MAX_TREGS];
+    for (int k = 0; k < P.n_sum; k++) {
+        GbSum S = P.sums[k];
+        for (int g = threadIdx.x; g < S.ngroups; g += blockDim.x) {
+            iv64 a = group_sum<double>(P, S, g, X, R);
+            iv64 b = group_sum<double>(P, S, g, MX, R);
+            pool.gsum[S.group0 + g] = make_double2(a.lo, a.hi);
+            pool.gmid[S.group0 + g] = make_double2(b.lo, b.hi);
+            if (pool.fp32) {
+                iv32 c = group_sum<float>(P, S, g, X32, R32);
+                pool.gsum32[S.group0 + g] = make_float2(c.lo, c.hi);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    iv64 sums[GB_MAX_ISUM], O[GB_MAX_OREGS];
+    sum_values<double>(P, 0, X, (const double2*)nullptr, R, sums);
+    iv64 F = outer_fwd<double>(P, X, sums, O);
+    sum_values<double>(P, 0, MX, (const double2*)nullptr, R, sums);
+    iv64 Fm = outer_fwd<double>(P, MX, sums, O);
+    double gub = Fm.hi;
+    if (gub != gub) gub = __longlong_as_double(0x7ff0000000000000LL);
+    E.flo[0] = canon_lo(F.lo);
+    E.slot[0] = 0;
+    E.cyc[0] = 0;
+    GbState s0 = {};
+    s0.pool = 1;
+    s0.nfree = 0;
+    s0.bump = 1;
+    s0.cap = st->cap;
+    s0.gub_key = gb_order_key(gub);
+    s0.gub_new_key = s0.gub_key;
+    s0.sel_T = ~0ull;
+    s0.evals64 = 1;
+    s0.mids = 1;
+    *st = s0;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_stats(GbEntries E, double tol_f, GbState* st) {
+    const long long count = st->pool;
+    const double thr = thr_of(gb_key_value(st->gub_key), tol_f);
+    long long c = 0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x) {
+        double f = E.flo[q];
+        c += (f < thr && !((unsigned)E.cyc[q] & GB_FINAL_BIT)) ? 1 : 0;
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd((unsigned long long*)&st->active, (unsigned long long)c);
+}
+
+// ---------------------------------------------------------------------------
+// Radix select (16-bit digits, 4 passes) of the K-th smallest active key.
+__global__ void k_radix_init(GbState* st, long long K) {
+    st->radix_prefix = 0;
+    st->radix_rank = K;
+    st->sel_below = 0;
+}
+
+__global__ void k_select_all(GbState* st) {
+    st->sel_T = ~0ull;
+    st->sel_below = st->active;
+    st->sel_need = 0;
+}
+
+__global__ void k_radix_hist(GbEntries E, long long count, double gub, double tol_f, int pass,
+                             const GbState* st, unsigned* hist) {
+    const double thr = thr_of(gub, tol_f);
+    const unsigned long long prefix = st->radix_prefix;
+    const int shift = 48 - 16 * pass;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x) {
+        double f = E.flo[q];
+        if (!(f < thr) || ((unsigned)E.cyc[q] & GB_FINAL_BIT)) continue;
+        unsigned long long key = gb_order_key(f);
+        if (pass > 0 && (key >> (shift + 16)) != prefix) continue;
+        atomicAdd(&hist[(key >> shift) & 0xffffu], 1u);
+    }
+}
+
+__global__ void k_radix_pick(int pass, GbState* st, unsigned* hist) {
+    __shared__ long long part[1025];
+    __shared__ int found;
+    const int t = threadIdx.x;    // 1024 threads x 64 bins
+    long long s = 0;
+    for (int b = 0; b < 64; b++) s += hist[t * 64 + b];
+    part[t] = s;
+    if (t == 0) found = -1;
+    __syncthreads();
+    if (t == 0) {
+        long long acc = 0;
+        for (int i = 0; i < 1024; i++) {
+            long long c = part[i];
+            part[i] = acc;
+            acc += c;
+        }
+        part[1024] = acc;
+    }
+    __syncthreads();
+    const long long rank = st->radix_rank;
+    if (part[t] < rank && rank <= part[t] + s) {
+        long long acc = part[t];
+        for (int b = 0; b < 64; b++) {
+            long long c = hist[t * 64 + b];
+            if (acc < rank && rank <= acc + c) {
+                st->radix_prefix = (st->radix_prefix << 16) | (unsigned long long)(t * 64 + b);
+                st->radix_rank = rank - acc;
+                st->sel_below += acc;
+                found = 1;
+                break;
+            }
+            acc += c;
+        }
+    }
+    __syncthreads();
+    for (int b = 0; b < 64; b++) hist[t * 64 + b] = 0;
+    if (t == 0 && pass == 3) {
+        st->sel_T = st->radix_prefix;
+        st->sel_need = st->radix_rank;
+        if (found < 0) st->error |= 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pool partition: class of entry q.
+struct PartFlags { bool drop, below, tie; };
+
+__device__ __forceinline__ PartFlags part_flags(const GbEntries& E, long long q, long long count, double gub,
+                                                double thr, unsigned long long T) {
+    PartFlags f{false, false, false};
+    if (q >= count) return f;
+    double v = E.flo[q];
+    if (v > gub) { f.drop = true; return f; }
+    bool act = v < thr && !((unsigned)E.cyc[q] & GB_FINAL_BIT);
+    if (!act) return f;
+    if (T == ~0ull) { f.below = true; return f; }
+    unsigned long long key = gb_order_key(v);
+    f.below = key < T;
+    f.tie = key == T;
+    return f;
+}
+
+constexpr int PT = 256;  // threads per partition / compaction block; tile = 4 rounds
+
+__global__ void k_part_count(GbEntries E, long long count, double gub, double tol_f, const GbState* st,
+                             int* tile_cnt, int max_tiles) {
+    __shared__ int sw[PT / 32 + 1];
+    const double thr = thr_of(gub, tol_f);
+    const unsigned long long T = st->sel_T;
+    const long long base = (long long)blockIdx.x * GB_TILE;
+    int cd = 0, cb = 0, ct = 0, tot;
+    for (int r = 0; r < GB_TILE / PT; r++) {
+        PartFlags f = part_flags(E, base + r * PT + threadIdx.x, count, gub, thr, T);
+        block_prefix<PT>(f.drop, sw, &tot); cd += tot;
+        block_prefix<PT>(f.below, sw, &tot); cb += tot;
+        block_prefix<PT>(f.tie, sw, &tot); ct += tot;
+    }
+    if (threadIdx.x == 0) {
+        tile_cnt[blockIdx.x] = cd;
+        tile_cnt[max_tiles + blockIdx.x] = cb;
+        tile_cnt[2 * max_tiles + blockIdx.x] = ct;
+    }
+}
+
+// Exclusive scan of up to 3 arrays of tile counts (one block of 1024
+// threads, each owning a contiguous run of tiles).
+// what: 0 = partition (3 arrays), 1 = FP32 list, 2 = survivors, 3 = output.
+__global__ void __launch_bounds__(1024) k_scan_tiles(int ntiles, int narr, const int* tile_cnt, int* tile_off,
+                                                     int max_tiles, int what, long long count, GbState* st) {
+    __shared__ long long part[1024];
+    __shared__ long long tot[3];
+    const int t = threadIdx.x;
+    const int per = (ntiles + 1023) / 1024;
+    for (int a = 0; a < narr; a++) {
+        const int* c = tile_cnt + a * max_tiles;
+        int* o = tile_off + a * max_tiles;
+        int i0 = t * per, i1 = min(ntiles, i0 + per);
+        long long s = 0;
+        for (int i = i0; i < i1; i++) s += c[i];
+        part[t] = s;
+        __syncthreads();
+        for (int d = 1; d < 1024; d <<= 1) {
+            long long v = t >= d ? part[t - d] : 0;
+            __syncthreads();
+            part[t] += v;
+            __syncthreads();
+        }
+        long long acc = part[t] - s;
+        for (int i = i0; i < i1; i++) {
+            o[i] = (int)acc;
+            acc += c[i];
+        }
+        if (t == 1023) tot[a] = part[1023];
+        __syncthreads();
+    }
+    if (t != 0) return;
+    if (what == 0) {
+        long long D = tot[0], Bl = tot[1], Ti = tot[2];
+        long long need = st->sel_T == ~0ull ? 0 : st->sel_need;
+        st->drops = D;
+        st->parents = Bl + need;
+        st->kept_old = count - D - (Bl + need);
+        st->nfree_after_drop = st->nfree + D;
+        st->sel_below = Bl;
+        st->sel_ties = Ti;
+    } else if (what == 1) {
+        st->n32 = tot[0];
+        st->kept32 = tot[0];
+    } else if (what == 2) {
+        long long S = tot[0];
+        st->kept = S;
+        long long room = st->nfree + (st->cap - st->bump);
+        st->overflow = S > room ? 1 : 0;
+    } else {
+        st->kept = tot[0];
+    }
+}
+
+__global__ void k_part_scatter(GbEntries E, long long count, double gub, double tol_f, const GbState* st,
+                               const int* tile_off, int max_tiles, GbEntries En, GbParents par,
+                               unsigned* freel) {
+    __shared__ int sw[PT / 32 + 1];
+    const double thr = thr_of(gub, tol_f);
+    const unsigned long long T = st->sel_T;
+    const long long need = (T == ~0ull) ? 0 : st->sel_need;
+    const long long Ti = st->sel_ties;
+    const long long nfree = st->nfree;
+    long long od = tile_off[blockIdx.x];
+    long long ob = tile_off[max_tiles + blockIdx.x];
+    long long ot = tile_off[2 * max_tiles + blockIdx.x];
+    const long long base = (long long)blockIdx.x * GB_TILE;
+    for (int r = 0; r < GB_TILE / PT; r++) {
+        long long q = base + r * PT + threadIdx.x;
+        PartFlags f = part_flags(E, q, count, gub, thr, T);
+        int td, tb, tt;
+        long long rd = od + block_prefix<PT>(f.drop, sw, &td);
+        long long rb = ob + block_prefix<PT>(f.below, sw, &tb);
+        long long rt = ot + block_prefix<PT>(f.tie, sw, &tt);
+        od += td; ob += tb; ot += tt;
+        if (q >= count) continue;
+        long long sel_before = rb + max(0LL, rt - (Ti - need));
+        bool sel = f.below || (f.tie && rt >= Ti - need);
+        if (f.drop) {
+            freel[nfree + rd] = E.slot[q];
+        } else if (sel) {
+            par.slot[sel_before] = E.slot[q];
+            par.cyc[sel_before] = E.cyc[q];
+            par.flo[sel_before] = E.flo[q];
+        } else {
+            long long kr = q - rd - sel_before;
+            En.flo[kr] = E.flo[q];
+            En.slot[kr] = E.slot[q];
+            En.cyc[kr] = E.cyc[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per parent: split coordinates and piece boundaries (Eqs. 10-11 with the
+// rounding reading: boundary t = RN(lo + RN(RN(RN(hi - lo) / m) * t)),
+// boundary 0 = lo, boundary m = hi).
+__global__ void k_prep(GbProg P, GbPool pool, GbParents par, long long npar, GbSplit sp, GbState* st) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p == 0) {
+        st->gub_new_key = st->gub_key;
+        st->nfree = st->nfree_after_drop;
+        st->kept = 0;
+        st->kept32 = 0;
+        st->n32 = 0;
+        st->overflow = 0;
+    }
+    if (p >= npar) return;
+    const int n = P.n, B = P.B;
+    int c = par.cyc[p] & 0x7fffffff;
+    int b = c / B;
+    int e = min((b + 1) * B, n);
+    int dd = min(sp.d, e - c);
+    int nxt = (c + dd == n) ? 0 : c + dd;
+    par.info[p] = make_int4(c, dd, b, nxt);
+    unsigned slot = par.slot[p];
+    const int ms = sp.m + 1;
+    for (int k = 0; k < dd; k++) {
+        int j = c + k;
+        double lo = pool.lo64[(size_t)slot * n + j], hi = pool.hi64[(size_t)slot * n + j];
+        double w = __dsub_rn(hi, lo);
+        double q = __ddiv_rn(w, (double)sp.m);
+        for (int t = 0; t <= sp.m; t++) {
+            double v = (t == 0) ? lo : (t == sp.m ? hi : __dadd_rn(lo, __dmul_rn(q, (double)t)));
+            size_t o = ((size_t)p * sp.dmax + k) * ms + t;
+            par.bnd[o] = v;
+            par.bnd_rd[o] = __double2float_rd(v);
+            par.bnd_ru[o] = __double2float_ru(v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+struct ChildCtx {
+    long long p;
+    unsigned r, slot;
+    int4 info;
+    bool valid;
+};
+
+__device__ __forceinline__ ChildCtx child_ctx(const GbParents& par, long long ci, const GbSplit& sp) {
+    ChildCtx c;
+    c.p = ci >> sp.flog2;
+    c.r = (unsigned)(ci & ((1LL << sp.flog2) - 1));
+    c.info = par.info[c.p];
+    c.slot = par.slot[c.p];
+    c.valid = c.r < (1u << (c.info.y * sp.mshift));
+    return c;
+}
+
+__device__ __forceinline__ View<double> view64(const GbPool& pool, const GbParents& par, const ChildCtx& c,
+                                               const GbSplit& sp) {
+    const double* b = par.bnd + (size_t)c.p * sp.dmax * (sp.m + 1);
+    return View<double>{pool.lo64 + (size_t)c.slot * pool.n, pool.hi64 + (size_t)c.slot * pool.n, b, b,
+                        c.info.x, c.info.y, sp.mshift, sp.m + 1, c.r};
+}
+__device__ __forceinline__ View<float> view32(const GbPool& pool, const GbParents& par, const ChildCtx& c,
+                                              const GbSplit& sp) {
+    size_t o = (size_t)c.p * sp.dmax * (sp.m + 1);
+    return View<float>{pool.lo32 + (size_t)c.slot * pool.n, pool.hi32 + (size_t)c.slot * pool.n,
+                       par.bnd_rd + o, par.bnd_ru + o, c.info.x, c.info.y, sp.mshift, sp.m + 1, c.r};
+}
+
+__device__ __forceinline__ void warp_min_gub(unsigned long long key, bool has, GbState* st) {
+    unsigned long long k = has ? key : ~0ull;
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long other = __shfl_down_sync(0xffffffffu, k, o);
+        k = other < k ? other : k;
+    }
+    if ((threadIdx.x & 31) == 0 && k != ~0ull) atomicMin(&st->gub_new_key, k);
+}
+
+// FP64 child evaluation: midpoint sample, F(X), first-order test.
+__device__ __forceinline__ void eval64_child(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                             const GbChildren& ch, long long ci, const GbSplit& sp,
+                                             double gub_prev, unsigned long long* gkey, bool* has_key) {
+    ChildCtx c = child_ctx(par, ci, sp);
+    if (!c.valid) {
+        ch.flag[ci] = 0;
+        ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
+        return;
+    }
+    View<double> X = view64(pool, par, c, sp);
+    MidView MX{X};
+    iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+    const int blk = c.info.z;
+    sum_values<double>(P, blk, MX, pool.gmid + (size_t)c.slot * pool.NG, R, sums);
+    iv64 Fm = outer_fwd<double>(P, MX, sums, O);
+    if (Fm.hi == Fm.hi) {
+        *gkey = gb_order_key(Fm.hi);
+        *has_key = true;
+    }
+    sum_values<double>(P, blk, X, pool.gsum + (size_t)c.slot * pool.NG, R, sums);
+    iv64 F = outer_fwd<double>(P, X, sums, O);
+    bool keep = !(F.lo > gub_prev);
+    if (keep) keep = !block_mono<double>(P, blk, X, X, O, OA, R, RA, (double*)nullptr);
+    ch.flo[ci] = canon_lo(F.lo);
+    ch.flag[ci] = keep ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents par, GbChildren ch,
+                                                long long nchildren, GbSplit sp, double gub_prev,
+                                                int from_list, GbState* st) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long lim = from_list ? st->n32 : nchildren;
+    unsigned long long key = ~0ull;
+    bool has = false;
+    bool valid = false;
+    if (idx < lim) {
+        long long ci = from_list ? (long long)ch.list32[idx] : idx;
+        eval64_child(P, pool, par, ch, ci, sp, gub_prev, &key, &has);
+        valid = has;
+    }
+    warp_min_gub(key, has, st);
+    unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
+    if ((threadIdx.x & 31) == 0 && nv) {
+        atomicAdd((unsigned long long*)&st->evals64, (unsigned long long)nv);
+        atomicAdd((unsigned long long*)&st->mids, (unsigned long long)nv);
+    }
+}
+
+// FP32 prefilter: F(X) and the first-order test in FP32 directed rounding,
+// cut-off against the GUB of the previous generation.
+__global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents par, GbChildren ch,
+                                                long long nchildren, GbSplit sp, double gub_prev,
+                                                GbState* st) {
+    long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool valid = false;
+    if (ci < nchildren) {
+        ChildCtx c = child_ctx(par, ci, sp);
+        ch.flag[ci] = 0;
+        ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
+        if (c.valid) {
+            valid = true;
+            View<float> X = view32(pool, par, c, sp);
+            View<double> X64 = view64(pool, par, c, sp);
+            iv32 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+            const int blk = c.info.z;
+            sum_values<float>(P, blk, X, pool.gsum32 + (size_t)c.slot * pool.NG, R, sums);
+            iv32 F = outer_fwd<float>(P, X, sums, O);
+            bool keep = !((double)F.lo > gub_prev);
+            if (keep) keep = !block_mono<float>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr);
+            ch.flag32[ci] = keep ? 1 : 0;
+        } else {
+            ch.flag32[ci] = 0;
+        }
+    }
+    unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
+    if ((threadIdx.x & 31) == 0 && nv) atomicAdd((unsigned long long*)&st->evals32, (unsigned long long)nv);
+}
+
+// ---------------------------------------------------------------------------
+// Stable compaction of child indices by a predicate (3 phases).
+__device__ __forceinline__ bool child_pred(const GbChildren& ch, long long i, long long n, int mode,
+                                           double gub_new) {
+    if (i >= n) return false;
+    if (mode == 0) return ch.flag32[i] != 0;
+    return ch.flag[i] != 0 && !(ch.flo[i] > gub_new);
+}
+
+__global__ void k_cc_count(GbChildren ch, long long n, int mode, const GbState* st, int* tile_cnt) {
+    __shared__ int sw[PT / 32 + 1];
+    const double gub_new = gb_key_value(st->gub_new_key);
+    const long long base = (long long)blockIdx.x * GB_TILE;
+    int acc = 0, tot;
+    for (int r = 0; r < GB_TILE / PT; r++) {
+        block_prefix<PT>(child_pred(ch, base + r * PT + threadIdx.x, n, mode, gub_new), sw, &tot);
+        acc += tot;
+    }
+    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = acc;
+}
+
+__global__ void k_cc_scatter(GbChildren ch, long long n, int mode, const GbState* st, const int* tile_off,
+                             unsigned* out) {
+    __shared__ int sw[PT / 32 + 1];
+    const double gub_new = gb_key_value(st->gub_new_key);
+    const long long base = (long long)blockIdx.x * GB_TILE;
+    long long o = tile_off[blockIdx.x];
+    for (int r = 0; r < GB_TILE / PT; r++) {
+        long long i = base + r * PT + threadIdx.x;
+        bool f = child_pred(ch, i, n, mode, gub_new);
+        int tot;
+        int rk = block_prefix<PT>(f, sw, &tot);
+        if (f) out[o + rk] = (unsigned)i;
+        o += tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Survivors into free slots: coordinates, FP32 shadow, group caches (dirty
+// groups recomputed, the rest copied from the parent), pool entry.
+__global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbParents par, GbChildren ch,
+                                                     GbSplit sp, GbEntries En, double tol_x, GbState* st) {
+    const int lane = threadIdx.x & 31;
+    const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (st->overflow) return;
+    if (s >= st->kept) return;
+    const long long nfree = st->nfree, bump = st->bump, kept_old = st->kept_old;
+    const long long ci = ch.surv[s];
+    ChildCtx c = child_ctx(par, ci, sp);
+    const unsigned ns = (s < nfree) ? pool.freel[nfree - 1 - s] : (unsigned)(bump + (s - nfree));
+    const int n = pool.n;
+    View<double> X = view64(pool, par, c, sp);
+    View<float> X32;
+    if (pool.fp32) X32 = view32(pool, par, c, sp);
+    bool narrow = true;
+    for (int j = lane; j < n; j += 32) {
+        iv64 x = X.get(j);
+        pool.lo64[(size_t)ns * n + j] = x.lo;
+        pool.hi64[(size_t)ns * n + j] = x.hi;
+        if (pool.fp32) {
+            iv32 y = X32.get(j);
+            pool.lo32[(size_t)ns * n + j] = y.lo;
+            pool.hi32[(size_t)ns * n + j] = y.hi;
+        }
+        if (!(__dsub_rn(x.hi, x.lo) < tol_x)) narrow = false;
+    }
+    narrow = __all_sync(0xffffffffu, narrow) && tol_x > 0.0;
+    const int blk = c.info.z;
+    MidView MX{X};
+    iv64 R[GB_MAX_TREGS];
+    iv32 R32[GB_MAX_TREGS];
+    int slot_k = 0;
+    for (int k = 0; k < P.n_sum; k++) {
+        GbSum S = P.sums[k];
+        int2 dr = P.dirty[blk * P.n_sum + k];
+        for (int g = lane; g < S.ngroups; g += 32) {
+            if (g >= dr.x && g < dr.y) continue;
+            size_t src = (size_t)c.slot * pool.NG + S.group0 + g, dst = (size_t)ns * pool.NG + S.group0 + g;
+            pool.gsum[dst] = pool.gsum[src];
+            pool.gmid[dst] = pool.gmid[src];
+            if (pool.fp32) pool.gsum32[dst] = pool.gsum32[src];
+        }
+        for (int g = dr.x; g < dr.y; g++, slot_k++) {
+            if ((slot_k & 31) != lane) continue;
+            size_t dst = (size_t)ns * pool.NG + S.group0 + g;
+            iv64 a = group_sum<double>(P, S, g, X, R);
+            iv64 b = group_sum<double>(P, S, g, MX, R);
+            pool.gsum[dst] = make_double2(a.lo, a.hi);
+            pool.gmid[dst] = make_double2(b.lo, b.hi);
+            if (pool.fp32) {
+                iv32 f = group_sum<float>(P, S, g, X32, R32);
+                pool.gsum32[dst] = make_float2(f.lo, f.hi);
+            }
+        }
+    }
+    if (lane == 0) {
+        long long e = kept_old + s;
+        En.flo[e] = ch.flo[ci];
+        En.slot[e] = ns;
+        En.cyc[e] = (int)((unsigned)c.info.w | (narrow ? GB_FINAL_BIT : 0u));
+    }
+}
+
+// Parents' slots back to the free list, or (on overflow) the parents back
+// into the pool after the carried-over entries.
+__global__ void k_free_parents(GbParents par, long long npar, GbPool pool, GbEntries En, GbState* st) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= npar) return;
+    if (st->overflow) {
+        long long e = st->kept_old + p;
+        En.flo[e] = par.flo[p];
+        En.slot[e] = par.slot[p];
+        En.cyc[e] = par.cyc[p];
+        return;
+    }
+    long long kept = st->kept, nfree = st->nfree;
+    long long base = kept < nfree ? nfree - kept : 0;
+    pool.freel[base + p] = par.slot[p];
+}
+
+__global__ void k_finish(long long npar, GbState* st) {
+    long long kept = st->kept, nfree = st->nfree;
+    if (st->overflow) {
+        st->pool = st->kept_old + npar;
+        st->kept = 0;
+    } else {
+        long long from_free = kept < nfree ? kept : nfree;
+        st->bump += kept - from_free;
+        st->nfree = nfree - from_free + npar;
+        st->pool = st->kept_old + kept;
+    }
+    st->gub_key = st->gub_new_key;
+    st->gen += 1;
+    st->active = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Output: entries with LB <= GUB (stable), gathered into rows; GLB = min LB.
+__global__ void k_out_count(GbEntries E, long long count, double gub, int* tile_cnt, GbState* st) {
+    __shared__ int sw[PT / 32 + 1];
+    const long long base = (long long)blockIdx.x * GB_TILE;
+    int acc = 0, tot;
+    unsigned long long kmin = ~0ull;
+    for (int r = 0; r < GB_TILE / PT; r++) {
+        long long q = base + r * PT + threadIdx.x;
+        bool f = q < count && !(E.flo[q] > gub);
+        if (f) {
+            unsigned long long k = gb_order_key(E.flo[q]);
+            kmin = k < kmin ? k : kmin;
+        }
+        block_prefix<PT>(f, sw, &tot);
+        acc += tot;
+    }
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long other = __shfl_down_sync(0xffffffffu, kmin, o);
+        kmin = other < kmin ? other : kmin;
+    }
+    if ((threadIdx.x & 31) == 0 && kmin != ~0ull) atomicMin(&st->glb_key, kmin);
+    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = acc;
+}
+
+__global__ void k_out_scatter(GbEntries E, long long count, double gub, const int* tile_off, unsigned* list) {
+    __shared__ int sw[PT / 32 + 1];
+    const long long base = (long long)blockIdx.x * GB_TILE;
+    long long o = tile_off[blockIdx.x];
+    for (int r = 0; r < GB_TILE / PT; r++) {
+        long long q = base + r * PT + threadIdx.x;
+        bool f = q < count && !(E.flo[q] > gub);
+        int tot;
+        int rk = block_prefix<PT>(f, sw, &tot);
+        if (f) list[o + rk] = (unsigned)q;
+        o += tot;
+    }
+}
+
+__global__ void k_out_gather(GbEntries E, const unsigned* list, const GbState* st, GbPool pool, double* out_lo,
+                             double* out_hi, double* out_flo) {
+    const int lane = threadIdx.x & 31;
+    const long long b = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (b >= st->kept) return;
+    unsigned q = list[b];
+    unsigned slot = E.slot[q];
+    const int n = pool.n;
+    for (int j = lane; j < n; j += 32) {
+        out_lo[(size_t)b * n + j] = pool.lo64[(size_t)slot * n + j];
+        out_hi[(size_t)b * n + j] = pool.hi64[(size_t)slot * n + j];
+    }
+    if (lane == 0) out_flo[b] = E.flo[q];
+}
+
+// ---------------------------------------------------------------------------
+// Parity hook: full evaluation of given boxes.
+__global__ void k_to_f32(const double* lo, const double* hi, float* lo32, float* hi32, long long count) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    lo32[i] = __double2float_rd(lo[i]);
+    hi32[i] = __double2float_ru(hi[i]);
+}
+
+__global__ void __launch_bounds__(128) k_eval_boxes(GbProg P, const double* lo, const double* hi,
+                                                    const float* lo32, const float* hi32, long long nbox,
+                                                    int blk, int fp32, double* Fo, double* Fmo, double* Go,
+                                                    int* mono) {
+    long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const int n = P.n;
+    View<double> X{lo + (size_t)b * n, hi + (size_t)b * n, nullptr, nullptr, 0, 0, 1, 2, 0u};
+    MidView MX{X};
+    iv64 R[GB_MAX_TREGS], O[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+    sum_values<double>(P, blk, MX, (const double2*)nullptr, R, sums);
+    iv64 Fm = outer_fwd<double>(P, MX, sums, O);
+    Fmo[2 * b] = Fm.lo;
+    Fmo[2 * b + 1] = Fm.hi;
+    if (!fp32) {
+        iv64 RA[GB_MAX_TREGS], OA[GB_MAX_OREGS];
+        sum_values<double>(P, blk, X, (const double2*)nullptr, R, sums);
+        iv64 F = outer_fwd<double>(P, X, sums, O);
+        Fo[2 * b] = F.lo;
+        Fo[2 * b + 1] = F.hi;
+        if (blk >= 0) {
+            bool m = block_mono<double>(P, blk, X, X, O, OA, R, RA, Go + (size_t)b * P.B * 2);
+            mono[b] = m ? 1 : 0;
+        }
+    } else {
+        View<float> X32{lo32 + (size_t)b * n, hi32 + (size_t)b * n, nullptr, nullptr, 0, 0, 1, 2, 0u};
+        iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS], O32[GB_MAX_OREGS], OA32[GB_MAX_OREGS], s32[GB_MAX_ISUM];
+        sum_values<float>(P, blk, X32, (const float2*)nullptr, R32, s32);
+        iv32 F = outer_fwd<float>(P, X32, s32, O32);
+        Fo[2 * b] = F.lo;
+        Fo[2 * b + 1] = F.hi;
+        if (blk >= 0) {
+            bool m = block_mono<float>(P, blk, X32, X, O32, OA32, R32, RA32, Go + (size_t)b * P.B * 2);
+            mono[b] = m ? 1 : 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Directed-rounding throughput probe: 8 independent chains per thread,
+// 4 additions rounded down and 4 multiplications rounded up per iteration.
+template <typename T>
+__global__ void __launch_bounds__(256) k_peak(int iters, T seed, T inc, T mul, T* sink) {
+    T a0 = seed + (T)threadIdx.x, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
+    T m0 = (T)1 + (T)threadIdx.x * (T)1e-7, m1 = m0, m2 = m0, m3 = m0;
+    for (int i = 0; i < iters; i++) {
+        a0 = add_rd(a0, inc); a1 = add_rd(a1, inc); a2 = add_rd(a2, inc); a3 = add_rd(a3, inc);
+        m0 = mul_ru(m0, mul); m1 = mul_ru(m1, mul); m2 = mul_ru(m2, mul); m3 = mul_ru(m3, mul);
+    }
+    T s = a0 + a1 + a2 + a3 + m0 + m1 + m2 + m3;
+    if (s == (T)-1) sink[threadIdx.x] = s;   // never taken; keeps the chains live
+}
+
+inline unsigned grid_for(long long items, int per_block) {
+    long long g = (items + per_block - 1) / per_block;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// ===========================================================================
+// launch wrappers (each adds the number of kernels it launched to the
+// calling thread's counter)
+thread_local long long gb_launch_count = 0;
+
+long long gb_launches_so_far() { return gb_launch_count; }
+cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, GbState* st,
+                                cudaStream_t s) {
+    gb_launch_count++;
+    k_root_init<<<1, 256, 0, s>>>(P, pool, E, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_stats(const GbEntries& E, long long max_count, double tol_f, GbState* st, cudaStream_t s) {
+    unsigned g = grid_for(max_count, 256);
+    if (g > 152 * 16) g = 152 * 16;
+    gb_launch_count++;
+    k_stats<<<g, 256, 0, s>>>(E, tol_f, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_select(const GbEntries& E, long long count, long long active, long long K, double gub,
+                             double tol_f, GbState* st, const GbScan& sc, cudaStream_t s) {
+    if (active <= K) {
+        gb_launch_count++;
+        k_select_all<<<1, 1, 0, s>>>(st);
+        return cudaGetLastError();
+    }
+    gb_launch_count++;
+    k_radix_init<<<1, 1, 0, s>>>(st, K);
+    unsigned g = grid_for(count, 256);
+    if (g > 152 * 16) g = 152 * 16;
+    for (int pass = 0; pass < 4; pass++) {
+        gb_launch_count++;
+        k_radix_hist<<<g, 256, 0, s>>>(E, count, gub, tol_f, pass, st, sc.hist);
+        gb_launch_count++;
+        k_radix_pick<<<1, 1024, 0, s>>>(pass, st, sc.hist);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_partition(const GbEntries& E, long long count, double gub, double tol_f,
+                                const GbEntries& E_new, const GbParents& par, const GbPool& pool, GbState* st,
+                                const GbScan& sc, cudaStream_t s) {
+    unsigned tiles = grid_for(count, GB_TILE);
+    if ((int)tiles > sc.max_tiles) return cudaErrorInvalidValue;
+    gb_launch_count++;
+    k_part_count<<<tiles, PT, 0, s>>>(E, count, gub, tol_f, st, sc.tile_cnt, sc.max_tiles);
+    gb_launch_count++;
+    k_scan_tiles<<<1, 1024, 0, s>>>(tiles, 3, sc.tile_cnt, sc.tile_off, sc.max_tiles, 0, count, st);
+    gb_launch_count++;
+    k_part_scatter<<<tiles, PT, 0, s>>>(E, count, gub, tol_f, st, sc.tile_off, sc.max_tiles, E_new, par,
+                                        pool.freel);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_prep(const GbProg& P, const GbPool& pool, const GbParents& par, long long npar,
+                           const GbSplit& sp, GbState* st, cudaStream_t s) {
+    gb_launch_count++;
+    k_prep<<<grid_for(npar, 128), 128, 0, s>>>(P, pool, par, npar, sp, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_eval64(const GbProg& P, const GbPool& pool, const GbParents& par, const GbChildren& ch,
+                             long long nchildren, const GbSplit& sp, double gub_prev, bool from_list,
+                             GbState* st, cudaStream_t s) {
+    gb_launch_count++;
+    k_eval64<<<grid_for(nchildren, 128), 128, 0, s>>>(P, pool, par, ch, nchildren, sp, gub_prev,
+                                                      from_list ? 1 : 0, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_eval32(const GbProg& P, const GbPool& pool, const GbParents& par, const GbChildren& ch,
+                             long long nchildren, const GbSplit& sp, double gub_prev, GbState* st,
+                             cudaStream_t s) {
+    gb_launch_count++;
+    k_eval32<<<grid_for(nchildren, 128), 128, 0, s>>>(P, pool, par, ch, nchildren, sp, gub_prev, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_compact_children(const GbChildren& ch, long long nchildren, int mode, GbState* st,
+                                       const GbScan& sc, cudaStream_t s) {
+    unsigned tiles = grid_for(nchildren, GB_TILE);
+    if ((int)tiles > sc.max_tiles) return cudaErrorInvalidValue;
+    gb_launch_count++;
+    k_cc_count<<<tiles, PT, 0, s>>>(ch, nchildren, mode, st, sc.tile_cnt);
+    gb_launch_count++;
+    k_scan_tiles<<<1, 1024, 0, s>>>(tiles, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, mode == 0 ? 1 : 2,
+                                  nchildren, st);
+    gb_launch_count++;
+    k_cc_scatter<<<tiles, PT, 0, s>>>(ch, nchildren, mode, st, sc.tile_off, mode == 0 ? ch.list32 : ch.surv);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_materialize(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                  const GbChildren& ch, long long nchildren, const GbSplit& sp,
+                                  const GbEntries& E_new, double tol_x, GbState* st, cudaStream_t s) {
+    gb_launch_count++;
+    k_materialize<<<grid_for(nchildren * 32, 128), 128, 0, s>>>(P, pool, par, ch, sp, E_new, tol_x, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_finish(const GbParents& par, long long npar, const GbPool& pool, const GbEntries& E_new,
+                             GbState* st, cudaStream_t s) {
+    gb_launch_count++;
+    k_free_parents<<<grid_for(npar, 256), 256, 0, s>>>(par, npar, pool, E_new, st);
+    gb_launch_count++;
+    k_finish<<<1, 1, 0, s>>>(npar, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_output(const GbEntries& E, long long count, const GbPool& pool, double gub, unsigned* list,
+                             double* out_lo, double* out_hi, double* out_flo, GbState* st, const GbScan& sc,
+                             cudaStream_t s) {
+    unsigned tiles = grid_for(count, GB_TILE);
+    if ((int)tiles > sc.max_tiles) return cudaErrorInvalidValue;
+    gb_launch_count++;
+    k_out_count<<<tiles, PT, 0, s>>>(E, count, gub, sc.tile_cnt, st);
+    gb_launch_count++;
+    k_scan_tiles<<<1, 1024, 0, s>>>(tiles, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 3, count, st);
+    gb_launch_count++;
+    k_out_scatter<<<tiles, PT, 0, s>>>(E, count, gub, sc.tile_off, list);
+    if (out_lo) {
+        gb_launch_count++;
+        k_out_gather<<<grid_for(count * 32, 128), 128, 0, s>>>(E, list, st, pool, out_lo, out_hi, out_flo);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_eval_boxes(const GbProg& P, const double* lo, const double* hi, float* scratch32,
+                                 long long nbox, int blk, int fp32, double* F, double* Fmid, double* G, int* mono,
+                                 cudaStream_t s) {
+    float* lo32 = nullptr;
+    float* hi32 = nullptr;
+    if (fp32) {
+        long long cnt = nbox * (long long)P.n;
+        lo32 = scratch32;
+        hi32 = scratch32 + cnt;
+        gb_launch_count++;
+        k_to_f32<<<grid_for(cnt, 256), 256, 0, s>>>(lo, hi, lo32, hi32, cnt);
+    }
+    gb_launch_count++;
+    k_eval_boxes<<<grid_for(nbox, 128), 128, 0, s>>>(P, lo, hi, lo32, hi32, nbox, blk, fp32, F, Fmid, G, mono);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_peak(int which, int iters, int blocks, void* sink, cudaStream_t s) {
+    gb_launch_count++;
+    if (which == 0)
+        k_peak<double><<<blocks, 256, 0, s>>>(iters, 1.0, 1e-300, 1.0000001, (double*)sink);
+    else
+        k_peak<float><<<blocks, 256, 0, s>>>(iters, 1.0f, 1e-30f, 1.0001f, (float*)sink);
+    return cudaGetLastError();
+}

@@ -1,0 +1,97 @@
+// Launch wrappers of the solver kernels (gb_kernels.cu), used by gb_api.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "gb_internal.h"
+
+#define GB_FINAL_BIT 0x80000000u
+
+// Box store: one slot per box, slot-major rows.
+struct GbPool {
+    double* lo64;     // [cap][n]
+    double* hi64;
+    float* lo32;      // [cap][n] outward float shadow (FP32 prefilter only)
+    float* hi32;
+    double2* gsum;    // [cap][NG] cached group sums of F (FP64)
+    double2* gmid;    // [cap][NG] cached group sums at the box midpoint (FP64)
+    float2* gsum32;   // [cap][NG] cached group sums of F (FP32 prefilter only)
+    unsigned* freel;  // [cap] free slots
+    int n, NG, fp32;
+};
+
+// Ordered list of pool entries (the best-first list; bit 31 of cyc = final).
+struct GbEntries {
+    double* flo;
+    unsigned* slot;
+    int* cyc;
+};
+
+struct GbParents {
+    unsigned* slot;
+    int* cyc;
+    double* flo;
+    int4* info;       // c0 (first split coordinate), dd (coordinates split), block, next cyc
+    double* bnd;      // [K][dmax][m+1] piece boundaries
+    float* bnd_rd;    // boundaries rounded down / up to float
+    float* bnd_ru;
+};
+
+struct GbChildren {
+    double* flo;
+    unsigned char* flag;
+    unsigned char* flag32;
+    unsigned* list32;
+    unsigned* surv;
+};
+
+struct GbSplit {
+    int m, mshift, d, flog2;   // pieces, log2(pieces), coordinates split, log2(fan-out)
+    int dmax;                  // boundary table stride (coordinates)
+};
+
+// scratch for the three-phase scans
+struct GbScan {
+    int* tile_cnt;     // [3][max_tiles]
+    int* tile_off;     // [3][max_tiles]
+    unsigned* hist;    // [65536] radix-select histogram
+    int max_tiles;
+};
+
+constexpr int GB_TILE = 1024;
+
+cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, GbState* st,
+                                cudaStream_t s);
+// Active count of the pool; count and GUB are read from the device state,
+// max_count bounds the grid.
+cudaError_t gb_launch_stats(const GbEntries& E, long long max_count, double tol_f, GbState* st, cudaStream_t s);
+cudaError_t gb_launch_select(const GbEntries& E, long long count, long long active, long long K,
+                             double gub, double tol_f, GbState* st, const GbScan& sc, cudaStream_t s);
+cudaError_t gb_launch_partition(const GbEntries& E, long long count, double gub, double tol_f,
+                                const GbEntries& E_new, const GbParents& par, const GbPool& pool,
+                                GbState* st, const GbScan& sc, cudaStream_t s);
+cudaError_t gb_launch_prep(const GbProg& P, const GbPool& pool, const GbParents& par, long long npar,
+                           const GbSplit& sp, GbState* st, cudaStream_t s);
+cudaError_t gb_launch_eval64(const GbProg& P, const GbPool& pool, const GbParents& par,
+                             const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
+                             bool from_list, GbState* st, cudaStream_t s);
+cudaError_t gb_launch_eval32(const GbProg& P, const GbPool& pool, const GbParents& par,
+                             const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
+                             GbState* st, cudaStream_t s);
+// mode 0: list of FP32 survivors (flag32); mode 1: final survivors
+// (flag && flo <= new GUB) with the capacity check.
+cudaError_t gb_launch_compact_children(const GbChildren& ch, long long nchildren, int mode, GbState* st,
+                                       const GbScan& sc, cudaStream_t s);
+cudaError_t gb_launch_materialize(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                  const GbChildren& ch, long long nchildren, const GbSplit& sp,
+                                  const GbEntries& E_new, double tol_x, GbState* st, cudaStream_t s);
+cudaError_t gb_launch_finish(const GbParents& par, long long npar, const GbPool& pool,
+                             const GbEntries& E_new, GbState* st, cudaStream_t s);
+// Final output: entries with flo <= GUB, in pool order, gathered into rows.
+cudaError_t gb_launch_output(const GbEntries& E, long long count, const GbPool& pool, double gub,
+                             unsigned* list, double* out_lo, double* out_hi, double* out_flo,
+                             GbState* st, const GbScan& sc, cudaStream_t s);
+cudaError_t gb_launch_eval_boxes(const GbProg& P, const double* lo, const double* hi, float* scratch32,
+                                 long long nbox, int blk, int fp32, double* F, double* Fmid, double* G,
+                                 int* mono, cudaStream_t s);
+cudaError_t gb_launch_peak(int which, int iters, int blocks, void* sink, cudaStream_t s);
+long long gb_launches_so_far();

@@ -1,0 +1,139 @@
+"""Per-box parity of the CUDA evaluation with the CPU oracle (runs on a GPU).
+
+For objectives built from +, -, x, square and scaling the FP64 and FP32
+results must be bit-identical: F(X), the FP64 midpoint sample, every interval
+partial of the tested block, and the first-order verdict.  With sin, cos, exp
+and sqrt both sides widen library results by their own documented error
+bounds, so the endpoints must agree within 4 * n ulps of the value's scale.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2507_01770_gb300 as gb  # noqa: E402
+
+
+def _gpu_eval(solver, lo, hi, blk, fp32):
+    dlo = torch.from_numpy(lo).cuda()
+    dhi = torch.from_numpy(hi).cuda()
+    F, Fm, G, mono = solver.eval_boxes(dlo, dhi, blk, fp32)
+    torch.cuda.synchronize()
+    return F.cpu().numpy(), Fm.cpu().numpy(), G.cpu().numpy(), mono.cpu().numpy()
+
+
+def _oracle_eval(orc, lo, hi, blk, fp32):
+    F, Fm, G, M = [], [], [], []
+    for k in range(len(lo)):
+        f, fm, g, m = orc.eval_box(lo[k], hi[k], blk=blk, f32=fp32)
+        F.append(f); Fm.append(fm); G.append(g); M.append(m)
+    return np.array(F), np.array(Fm), np.array(G), np.array(M)
+
+
+def _ulp(x):
+    return np.array([math.ulp(max(abs(v), 1e-300)) for v in np.ravel(x)]).reshape(np.shape(x))
+
+
+POLY = [("chain", dict(n=33, seed=3), 10), ("chain", dict(n=12, seed=4), 5),
+        ("chain", dict(n=2, seed=5), 2), ("chain", dict(n=100, seed=0), 10)]
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("fam,kw,B", POLY)
+def test_polynomial_bit_exact(fam, kw, B, fp32):
+    p = S.make(fam, **kw)
+    solver = gb.Solver(p, block=B)
+    orc = O.Oracle(p, block=B)
+    nb = (p.n + B - 1) // B
+    count = 160 if p.n <= 40 else 40
+    lo, hi = S.random_boxes(p, count, seed=11, around_s=0.5)
+    for blk in sorted({0, nb // 2, nb - 1}):
+        gF, gFm, gG, gM = _gpu_eval(solver, lo, hi, blk, fp32)
+        oF, oFm, oG, oM = _oracle_eval(orc, lo, hi, blk, fp32)
+        w = min(B, p.n - blk * B)
+        assert np.array_equal(gF, oF), (blk, np.argwhere(gF != oF)[:5])
+        assert np.array_equal(gFm, oFm)
+        assert np.array_equal(gG[:, :w], oG[:, :w]), (blk, np.argwhere(gG[:, :w] != oG[:, :w])[:5])
+        assert np.array_equal(gM, oM)
+    solver.close()
+
+
+def test_custom_dag_bit_exact():
+    g = S.Dag()
+    y = g.sub(g.ivar(0), g.ivar(1))
+    t = g.mul(g.icoef(g.table(np.linspace(0.5, 3.0, 9))), g.sqr(y))
+    s_even = g.isum(t, 0, 8, 2)
+    f = g.add(g.sub(s_even, g.scale(g.var(3), -1.5)), g.neg(g.mul(g.var(0), g.var(8))))
+    p = S.Problem("custom", 9, g.nodes(), f, g.tables, np.full(9, -2.0), np.full(9, 3.0),
+                  1e-6, 3, np.zeros(9), 0)
+    solver = gb.Solver(p, block=3)
+    orc = O.Oracle(p, block=3)
+    lo, hi = S.random_boxes(p, 200, seed=5)
+    for fp32 in (False, True):
+        for blk in range(3):
+            gF, gFm, gG, gM = _gpu_eval(solver, lo, hi, blk, fp32)
+            oF, oFm, oG, oM = _oracle_eval(orc, lo, hi, blk, fp32)
+            assert np.array_equal(gF, oF) and np.array_equal(gFm, oFm)
+            assert np.array_equal(gG, oG) and np.array_equal(gM, oM)
+
+
+TRANS = [("sep_cos", dict(n=2, seed=1), 2), ("sep_cos", dict(n=25, seed=2), 10),
+         ("ackley", dict(n=10, seed=3), 5), ("ackley", dict(n=1000, seed=0), 10),
+         ("mixed", dict(n=21, seed=4), 10), ("paper_rastrigin", dict(n=7), 7),
+         ("paper_breiman", dict(n=5), 5)]
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("fam,kw,B", TRANS)
+def test_transcendental_within_tolerance(fam, kw, B, fp32):
+    p = S.make(fam, **kw)
+    solver = gb.Solver(p, block=B)
+    orc = O.Oracle(p, block=B)
+    nb = (p.n + B - 1) // B
+    count = 120 if p.n <= 100 else 12
+    lo, hi = S.random_boxes(p, count, seed=13, min_width=1e-7, around_s=0.5)
+    ntol = 4 * p.n
+    for blk in sorted({0, nb - 1}):
+        gF, gFm, gG, gM = _gpu_eval(solver, lo, hi, blk, fp32)
+        oF, oFm, oG, oM = _oracle_eval(orc, lo, hi, blk, fp32)
+        scale = np.maximum(np.abs(oF).max(axis=1, keepdims=True), 1.0)
+        unit = _ulp(scale) if not fp32 else np.array([[float(np.spacing(np.float32(v)))] for v in scale[:, 0]])
+        assert np.all(np.abs(gF - oF) <= ntol * unit), np.abs(gF - oF).max()
+        # the FP64 midpoint samples agree within the same bound and contain
+        # each other's point value up to it
+        sm = np.maximum(np.abs(oFm).max(axis=1, keepdims=True), 1.0)
+        assert np.all(np.abs(gFm - oFm) <= ntol * _ulp(sm))
+        w = min(B, p.n - blk * B)
+        fin = np.isfinite(oG[:, :w])
+        assert np.array_equal(fin, np.isfinite(gG[:, :w]))
+        gs = np.where(fin, gG[:, :w], 0.0)
+        os_ = np.where(fin, oG[:, :w], 0.0)
+        gscale = np.maximum(np.abs(os_), 1.0)
+        gunit = _ulp(gscale) if not fp32 else np.vectorize(lambda v: float(np.spacing(np.float32(v))))(gscale)
+        assert np.all(np.abs(gs - os_) <= ntol * 16 * gunit), np.abs(gs - os_).max()
+        # verdicts may only differ where a partial is within tolerance of 0
+        for k in np.nonzero(gM != oM)[0]:
+            edge = np.min(np.abs(oG[k, :w]), axis=1)
+            assert np.min(edge) <= ntol * 16 * np.max(gunit[k])
+        assert np.mean(gM != oM) < 0.02
+    solver.close()
+
+
+def test_point_boxes_enclose_planted_zero():
+    for fam, kw in (("sep_cos", dict(n=3)), ("chain", dict(n=7)), ("ackley", dict(n=5)),
+                    ("mixed", dict(n=6))):
+        p = S.make(fam, **kw)
+        solver = gb.Solver(p)
+        lo = p.s[None, :].copy()
+        F, Fm, _, _ = _gpu_eval(solver, lo, lo.copy(), -1, False)
+        assert F[0, 0] <= 0.0 <= F[0, 1] and Fm[0, 0] <= 0.0 <= Fm[0, 1]
+        solver.close()

@@ -1,0 +1,137 @@
+"""Whole-run parity of the CUDA branch and bound with the CPU oracle (GPU).
+
+For polynomial objectives every generation must agree exactly: parents,
+children, survivors, pool size and the GUB sequence, and the final enclosure
+and box list bit for bit (same order).  With transcendental terms the two
+enclosures must overlap and each contain the planted minimum within the
+tolerance.  At the full size of the n = 100 chain workload the oracle cannot
+run the solve, so the result is checked by its properties and by re-evaluating
+a sample of the output boxes with the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2507_01770_gb300 as gb  # noqa: E402
+
+
+def _covers(lo, hi, x):
+    return bool(np.any(np.all((lo <= x) & (x <= hi), axis=1)))
+
+
+def _run_both(p, B, m, d, K, fp32=False, tol_x=0.0, tol_f=None, max_gen=10**9, cap=None):
+    tol = p.tol_f if tol_f is None else tol_f
+    opts = dict(block=B, split_m=m, split_d=d, max_children=K * m ** d, fp32_prefilter=int(fp32),
+                tol_x=tol_x, max_generations=max_gen)
+    if tol_f is not None:
+        opts["tol_f"] = tol_f if tol_f > 0 else 0.0
+    if cap is not None:
+        opts["max_boxes"] = cap
+    s = gb.Solver(p, **opts)
+    g = s.solve(raise_on_error=False)
+    s.close()
+    o = O.Oracle(p, block=B).solve(tol_f=tol, tol_x=tol_x, split_m=m, split_d=d, fp32=fp32,
+                                   max_parents=K, max_gen=max_gen, cap=cap if cap else 1 << 40)
+    return g, o
+
+
+def _assert_identical(g, o):
+    assert g.status == o.status
+    assert g.generations == o.generations
+    for k in ("parents", "children", "kept32", "kept", "pool"):
+        assert np.array_equal(g.trace[k], o.trace[k]), (k, g.trace[k][:20], o.trace[k][:20])
+    assert np.array_equal(g.trace["gub"], o.trace["gub"])
+    assert g.fmin_lo == o.glb and g.fmin_hi == o.gub
+    assert g.n_boxes == len(o.box_flo)
+    assert np.array_equal(g.box_lo, o.box_lo) and np.array_equal(g.box_hi, o.box_hi)
+    assert np.array_equal(g.box_flo, o.box_flo)
+
+
+@pytest.mark.parametrize("case", [
+    dict(n=10, B=5, m=2, d=5, K=64),          # radix selection with ties
+    dict(n=12, B=5, m=2, d=3, K=16),          # ragged last block, d not dividing B
+    dict(n=20, B=10, m=4, d=5, K=2),          # 4-way split
+    dict(n=10, B=10, m=2, d=10, K=4),         # 1024 children per parent
+    dict(n=6, B=3, m=2, d=1, K=1),            # single best-first selection
+])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_chain_run_parity(case, fp32):
+    p = S.chain(n=case["n"], seed=case["n"] + 1, block=case["B"])
+    g, o = _run_both(p, case["B"], case["m"], case["d"], case["K"], fp32=fp32)
+    _assert_identical(g, o)
+    assert g.fmin_lo <= 0.0 <= g.fmin_hi and g.fmin_hi - g.fmin_lo <= p.tol_f
+    assert _covers(g.box_lo, g.box_hi, p.s)
+
+
+def test_capacity_and_limit_parity():
+    p = S.chain(n=10, seed=2, block=5)
+    g, o = _run_both(p, 5, 2, 5, 64, cap=200)
+    assert g.status == gb.GB_E_CAPACITY
+    _assert_identical(g, o)
+    assert _covers(g.box_lo, g.box_hi, p.s) and g.fmin_lo <= 0.0 <= g.fmin_hi
+    g, o = _run_both(p, 5, 2, 1, 8, max_gen=7)
+    assert g.status == gb.GB_E_LIMIT and g.generations == 7
+    _assert_identical(g, o)
+
+
+def test_paper_mode_rastrigin_iterations():
+    p = S.paper_rastrigin(n=5, block=5)
+    g, o = _run_both(p, 5, 4, 5, 1, tol_x=1e-4, tol_f=0.0)
+    assert g.generations == o.generations == 9 and g.n_boxes == 1
+    assert g.fmin_lo <= 0.0 <= g.fmin_hi
+    assert np.array_equal(g.trace["kept"], o.trace["kept"])
+
+
+@pytest.mark.parametrize("fam,kw,B,m,d,K", [
+    ("sep_cos", dict(n=2), 2, 2, 1, 64),
+    ("sep_cos", dict(n=4, tol_f=1e-6), 4, 2, 4, 16),
+    ("ackley", dict(n=3), 3, 2, 3, 16),
+    ("mixed", dict(n=6), 3, 2, 3, 16),
+])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_transcendental_runs_overlap(fam, kw, B, m, d, K, fp32):
+    p = S.make(fam, seed=3, **kw)
+    g, o = _run_both(p, B, m, d, K, fp32=fp32)
+    assert g.status == o.status == 0
+    for r in ((g.fmin_lo, g.fmin_hi), (o.glb, o.gub)):
+        assert r[0] <= 0.0 <= r[1] and r[1] - r[0] <= p.tol_f
+    assert max(g.fmin_lo, o.glb) <= min(g.fmin_hi, o.gub)
+    assert _covers(g.box_lo, g.box_hi, p.s)
+
+
+def test_full_size_chain_n100():
+    """The n = 100 chain workload in the benchmark's configuration."""
+    p = S.chain(n=100, seed=0)
+    s = gb.Solver(p, block=10, split_m=2, split_d=10, max_children=1 << 20)
+    r = s.solve()
+    s.close()
+    assert r.status == 0
+    assert r.fmin_lo <= 0.0 <= r.fmin_hi and r.fmin_hi - r.fmin_lo <= 1e-6
+    assert _covers(r.box_lo, r.box_hi, p.s)
+    orc = O.Oracle(p, block=10)
+    pick = np.linspace(0, r.n_boxes - 1, min(r.n_boxes, 16)).astype(int)
+    for k in pick:
+        F, _, _, _ = orc.eval_box(r.box_lo[k], r.box_hi[k])
+        assert F[0] == r.box_flo[k] or (F[0] == 0.0 and r.box_flo[k] == 0.0)
+        assert not (F[0] > r.fmin_hi)
+    assert r.trace["parents"].sum() > 0 and r.box_evals_fp64 == r.mid_evals
+
+
+def test_solve_is_repeatable_and_device_only_matches():
+    p = S.chain(n=30, seed=5)
+    s = gb.Solver(p, block=10, split_m=2, split_d=10, max_children=1 << 16)
+    a = s.solve()
+    b = s.solve()
+    c = s.solve(device_only=True)
+    s.close()
+    assert a.fmin_lo == b.fmin_lo == c.fmin_lo and a.fmin_hi == b.fmin_hi == c.fmin_hi
+    assert np.array_equal(a.box_lo, b.box_lo) and c.box_lo is None and c.n_boxes == a.n_boxes
+    assert np.array_equal(a.trace["gub"], b.trace["gub"])
