@@ -84,12 +84,12 @@ typedef struct gb_options {
     double tol_x;             /* a box narrower than tol_x in every coordinate is final (0 = off) */
     int32_t block;            /* cycling block size B, section 3.2 (0: min(n, 10)) */
     int32_t split_m;          /* pieces per split coordinate, 2 or 4 (0: 2) */
-    int32_t split_d;          /* coordinates split per generation, 1..B (0: B, capped so m^d <= 4096) */
+    int32_t split_d;          /* coordinates split per generation, 1..B, m^d <= 2^20 (0: B, capped so m^d <= 4096) */
     int32_t fp32_prefilter;   /* 1: FP32 directed-rounding pass before FP64 */
     int64_t max_generations;  /* 0: 10^9 */
     int64_t max_children;     /* children evaluated per generation (0: 1 << 22) */
     int64_t max_boxes;        /* pool capacity in boxes (0: from pool_bytes) */
-    size_t pool_bytes;        /* device memory budget for the pool (0: 4 GiB) */
+    size_t pool_bytes;        /* device memory budget for the pool (0: 16 GiB) */
     int32_t device;           /* CUDA device ordinal */
     int32_t pad;
 } gb_options;

@@ -89,7 +89,7 @@ void gb_default_options(gb_options* o) {
     o->split_m = 2;
     o->max_generations = 1000000000LL;
     o->max_children = 1LL << 22;
-    o->pool_bytes = (size_t)4 << 30;
+    o->pool_bytes = (size_t)16 << 30;
 }
 
 const char* gb_status_str(gb_status s) {
@@ -133,7 +133,7 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     if (opt.split_m == 0) opt.split_m = 2;
     if (opt.max_generations <= 0) opt.max_generations = 1000000000LL;
     if (opt.max_children <= 0) opt.max_children = 1LL << 22;
-    if (opt.pool_bytes == 0) opt.pool_bytes = (size_t)4 << 30;
+    if (opt.pool_bytes == 0) opt.pool_bytes = (size_t)16 << 30;
     if (opt.block <= 0) opt.block = n < 10 ? n : 10;
     if (opt.block > n) return fail(GB_E_INVALID, "block size larger than n");
     if (opt.split_m != 2 && opt.split_m != 4) return fail(GB_E_INVALID, "split_m must be 2 or 4");
@@ -142,8 +142,8 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         opt.split_d = opt.block;
         while (opt.split_d > 1 && (opt.split_d * mshift > 12 || opt.split_d > GB_MAX_SPLIT_D)) opt.split_d--;
     }
-    if (opt.split_d > opt.block || opt.split_d > GB_MAX_SPLIT_D || opt.split_d * mshift > 12)
-        return fail(GB_E_INVALID, "split_d must be <= block, <= 12 and give at most 4096 children");
+    if (opt.split_d > opt.block || opt.split_d > GB_MAX_SPLIT_D || opt.split_d * mshift > GB_MAX_FAN_LOG2)
+        return fail(GB_E_INVALID, "split_d must be <= block, <= 20 and give at most 2^20 children per parent");
     double tol_f = opt.tol_f > 0.0 ? opt.tol_f : tol;
     if (!(tol_f >= 0.0) || !std::isfinite(tol_f)) return fail(GB_E_INVALID, "tolerance must be finite and >= 0");
     if (!(opt.tol_x >= 0.0)) return fail(GB_E_INVALID, "tol_x must be >= 0");
@@ -345,8 +345,8 @@ static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
         if (h.gen > 0) {
             gb_gen_stat g;
             g.parents = last_par;
-            g.children = last_children;
-            g.kept32 = p->opt.fp32_prefilter ? h.kept32 : last_children;
+            g.children = h.children;
+            g.kept32 = p->opt.fp32_prefilter ? h.kept32 : h.children;
             g.kept = h.overflow ? 0 : h.kept;
             g.pool = h.pool;
             g.gub = gub;

@@ -18,8 +18,8 @@
 #define GB_MAX_OREGS 32   // nodes of the outer expression
 #define GB_MAX_ISUM 6     // ISUM nodes per objective
 #define GB_MAX_WIN 4      // IDX_VAR offset span + 1 per template
-#define GB_MAX_SPLIT_D 12 // coordinates split per generation
-#define GB_MAX_FAN 4096   // children per parent (m^d)
+#define GB_MAX_SPLIT_D 20   // coordinates split per generation
+#define GB_MAX_FAN_LOG2 20  // children per parent (m^d) at most 2^20
 
 // Device opcodes of one instruction (registers are node slots).
 enum GbDevOp : uint8_t {

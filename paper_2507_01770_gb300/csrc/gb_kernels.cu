@@ -346,6 +346,7 @@ __global__ void k_prep(GbProg P, GbPool pool, GbParents par, long long npar, GbS
         st->kept = 0;
         st->kept32 = 0;
         st->n32 = 0;
+        st->children = 0;
         st->overflow = 0;
     }
     if (p >= npar) return;
@@ -414,14 +415,14 @@ __device__ __forceinline__ void warp_min_gub(unsigned long long key, bool has, G
 }
 
 // FP64 child evaluation: midpoint sample, F(X), first-order test.
-__device__ __forceinline__ void eval64_child(const GbProg& P, const GbPool& pool, const GbParents& par,
+__device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool, const GbParents& par,
                                              const GbChildren& ch, long long ci, const GbSplit& sp,
                                              double gub_prev, unsigned long long* gkey, bool* has_key) {
     ChildCtx c = child_ctx(par, ci, sp);
     if (!c.valid) {
         ch.flag[ci] = 0;
         ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
-        return;
+        return false;
     }
     View<double> X = view64(pool, par, c, sp);
     MidView MX{X};
@@ -439,6 +440,7 @@ __device__ __forceinline__ void eval64_child(const GbProg& P, const GbPool& pool
     if (keep) keep = !block_mono<double>(P, blk, X, X, O, OA, R, RA, (double*)nullptr);
     ch.flo[ci] = canon_lo(F.lo);
     ch.flag[ci] = keep ? 1 : 0;
+    return true;
 }
 
 __global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents par, GbChildren ch,
@@ -451,14 +453,14 @@ __global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents
     bool valid = false;
     if (idx < lim) {
         long long ci = from_list ? (long long)ch.list32[idx] : idx;
-        eval64_child(P, pool, par, ch, ci, sp, gub_prev, &key, &has);
-        valid = has;
+        valid = eval64_child(P, pool, par, ch, ci, sp, gub_prev, &key, &has);
     }
     warp_min_gub(key, has, st);
     unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
     if ((threadIdx.x & 31) == 0 && nv) {
         atomicAdd((unsigned long long*)&st->evals64, (unsigned long long)nv);
         atomicAdd((unsigned long long*)&st->mids, (unsigned long long)nv);
+        if (!from_list) atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
     }
 }
 
@@ -489,7 +491,10 @@ __global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents
         }
     }
     unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
-    if ((threadIdx.x & 31) == 0 && nv) atomicAdd((unsigned long long*)&st->evals32, (unsigned long long)nv);
+    if ((threadIdx.x & 31) == 0 && nv) {
+        atomicAdd((unsigned long long*)&st->evals32, (unsigned long long)nv);
+        atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -7,4 +7,4 @@ of the minimisation method.
 from .dag import Dag, NODE_DTYPE, OP_NAMES  # noqa: F401
 from . import dag  # noqa: F401
 from .families import (Problem, make, sep_cos, chain, ackley, mixed,  # noqa: F401
-                       random_boxes, serving_stream, FAMILIES)
+                       paper_rastrigin, paper_breiman, random_boxes, serving_stream, FAMILIES)

@@ -110,7 +110,7 @@ def test_transcendental_runs_overlap(fam, kw, B, m, d, K, fp32):
 def test_full_size_chain_n100():
     """The n = 100 chain workload in the benchmark's configuration."""
     p = S.chain(n=100, seed=0)
-    s = gb.Solver(p, block=10, split_m=2, split_d=10, max_children=1 << 20)
+    s = gb.Solver(p, block=10, split_m=2, split_d=10, max_children=16 << 10)
     r = s.solve()
     s.close()
     assert r.status == 0
