@@ -182,6 +182,26 @@ gb_status gb_eval_boxes(gb_problem* prob, const double* d_lo, const double* d_hi
                         int64_t nbox, int32_t block_index, int32_t fp32, double* d_F,
                         double* d_Fmid, double* d_G, int32_t* d_mono, void* stream);
 
+/* gb_eval_boxes without any device allocation, for callers that cannot
+ * allocate device memory while they run (for example a serving process that
+ * has already handed all free device memory to its own pool, or a
+ * latency-critical thread that must not wait on the device allocator).
+ * Same arguments and results as gb_eval_boxes.  The paper has no counterpart
+ * of this entry point.
+ *  - The FP32 copy of the boxes that fp32 = 1 needs is kept in a fixed array
+ *    inside the library instead of a per-call buffer: at most 2^20
+ *    coordinates (nbox * n <= 1048576) per call; larger calls return
+ *    GB_E_INVALID with a message.  The array (8 MiB) is held on every GPU
+ *    that loads the library until the process exits.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call shares the one array; each call writes the part it uses
+ *    before reading it, so no clearing is needed, but calls whose work
+ *    overlaps on the GPU (unordered streams or threads) race. */
+gb_status gb_eval_boxes_noalloc(gb_problem* prob, const double* d_lo, const double* d_hi,
+                                int64_t nbox, int32_t block_index, int32_t fp32, double* d_F,
+                                double* d_Fmid, double* d_G, int32_t* d_mono, void* stream);
+
 /* Block size B, number of blocks and the static count of directed-rounding
  * floating-point operations of one F+gradient child evaluation and one
  * midpoint sample (FP64), as compiled. */

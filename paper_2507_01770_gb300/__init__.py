@@ -63,7 +63,7 @@ class gb_result(ctypes.Structure):
 
 EXPORTS = ["gb_default_options", "gb_create_problem", "gb_solve", "gb_solve_device",
            "gb_free_result", "gb_destroy_problem", "gb_status_str", "gb_last_error",
-           "gb_eval_boxes", "gb_problem_info", "gb_measure_peak"]
+           "gb_eval_boxes", "gb_eval_boxes_noalloc", "gb_problem_info", "gb_measure_peak"]
 
 
 def library_path() -> str:
@@ -99,8 +99,9 @@ def load(build_if_missing: bool = True):
     L.gb_status_str.restype = ctypes.c_char_p
     L.gb_last_error.argtypes = []
     L.gb_last_error.restype = ctypes.c_char_p
-    L.gb_eval_boxes.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp]
-    L.gb_eval_boxes.restype = ctypes.c_int
+    for fn in ("gb_eval_boxes", "gb_eval_boxes_noalloc"):
+        getattr(L, fn).argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp]
+        getattr(L, fn).restype = ctypes.c_int
     L.gb_problem_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64)]
     L.gb_problem_info.restype = ctypes.c_int
@@ -234,13 +235,18 @@ def gb_problem_info(prob: _Problem) -> dict:
     return dict(block=b.value, n_blocks=nb.value, ops_eval=oe.value, ops_mid=om.value)
 
 
-def gb_eval_boxes(prob: _Problem, lo, hi, block_index: int = -1, fp32: bool = False):
+def gb_eval_boxes(prob: _Problem, lo, hi, block_index: int = -1, fp32: bool = False,
+                  noalloc: bool = False):
     """Per-box F, midpoint F, block partials and monotonicity verdict.
 
     lo, hi: torch CUDA float64 tensors (nbox x n).  Returns torch tensors
-    (F [nbox, 2], Fmid [nbox, 2], G [nbox, B, 2], mono [nbox])."""
+    (F [nbox, 2], Fmid [nbox, 2], G [nbox, B, 2], mono [nbox]).  With
+    noalloc=True the call goes to gb_eval_boxes_noalloc, which uses the
+    library's fixed scratch array instead of allocating (at most 2^20
+    coordinates per call)."""
     import torch
     L = load()
+    fn = L.gb_eval_boxes_noalloc if noalloc else L.gb_eval_boxes
     lo = lo.contiguous()
     hi = hi.contiguous()
     nbox = lo.shape[0]
@@ -251,7 +257,7 @@ def gb_eval_boxes(prob: _Problem, lo, hi, block_index: int = -1, fp32: bool = Fa
     G = torch.full((nbox, B, 2), float("nan"), dtype=torch.float64, device=dev)
     mono = torch.zeros(nbox, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
-    rc = L.gb_eval_boxes(prob.handle, lo.data_ptr(), hi.data_ptr(), nbox, int(block_index), int(fp32),
+    rc = fn(prob.handle, lo.data_ptr(), hi.data_ptr(), nbox, int(block_index), int(fp32),
                          F.data_ptr(), Fm.data_ptr(), G.data_ptr() if block_index >= 0 else None,
                          mono.data_ptr() if block_index >= 0 else None, stream)
     if rc != GB_OK:

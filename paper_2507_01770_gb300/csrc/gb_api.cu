@@ -481,6 +481,21 @@ gb_status gb_eval_boxes(gb_problem* p, const double* d_lo, const double* d_hi, i
     return GB_OK;
 }
 
+// Read-only view of a problem for the other translation units of the library
+// (not exported from the shared object).
+__attribute__((visibility("hidden"))) const GbProg* gb_internal_prog(const gb_problem* p, int* device, int* n, int* nb) {
+    if (!p) return nullptr;
+    *device = p->device;
+    *n = p->n;
+    *nb = p->hp.nb;
+    return &p->P;
+}
+
+// Sets the calling thread's gb_last_error() message (not exported).
+__attribute__((visibility("hidden"))) gb_status gb_internal_fail(gb_status s, const char* msg) {
+    return fail(s, msg);
+}
+
 gb_status gb_measure_peak(int32_t device, int32_t which, double* ops_per_s, double* ms_out) {
     if (!ops_per_s || (which != 0 && which != 1)) return fail(GB_E_INVALID, "bad arguments to gb_measure_peak");
     int ndev = 0;

@@ -95,3 +95,5 @@ cudaError_t gb_launch_eval_boxes(const GbProg& P, const double* lo, const double
                                  int* mono, cudaStream_t s);
 cudaError_t gb_launch_peak(int which, int iters, int blocks, void* sink, cudaStream_t s);
 long long gb_launches_so_far();
+extern "C" const GbProg* gb_internal_prog(const gb_problem* p, int* device, int* n, int* nb);
+extern "C" gb_status gb_internal_fail(gb_status s, const char* msg);
