@@ -144,6 +144,8 @@ typedef struct gb_result {
     int64_t eval64_launches;
     int64_t eval32_launches;
     int64_t kernel_launches;  /* kernels the library launched for this solve */
+    int64_t ops64;            /* directed-rounding FP64 operations executed by the FP64 evaluation kernels */
+    int64_t ops32;            /* directed-rounding FP32 operations executed by the FP32 evaluation kernels */
     int64_t n_trace;
     gb_gen_stat* trace;       /* n_trace rows, host */
 } gb_result;

@@ -57,7 +57,8 @@ class gb_result(ctypes.Structure):
                 ("solve_ms", ctypes.c_double), ("device_ms", ctypes.c_double),
                 ("eval64_ms", ctypes.c_double), ("eval32_ms", ctypes.c_double),
                 ("eval64_launches", ctypes.c_int64), ("eval32_launches", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("n_trace", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("ops64", ctypes.c_int64),
+                ("ops32", ctypes.c_int64), ("n_trace", ctypes.c_int64),
                 ("trace", ctypes.POINTER(gb_gen_stat))]
 
 
@@ -186,6 +187,8 @@ class Result:
     eval64_launches: int
     eval32_launches: int
     kernel_launches: int
+    ops64: int
+    ops32: int
     trace: dict
 
 
@@ -210,7 +213,7 @@ def _result(r: gb_result, n: int) -> Result:
                   hi.reshape(nb, n) if hi is not None else None,
                   arr(r.box_flo, nb), r.generations, r.box_evals_fp32, r.box_evals_fp64,
                   r.mid_evals, r.solve_ms, r.device_ms, r.eval64_ms, r.eval32_ms,
-                  r.eval64_launches, r.eval32_launches, r.kernel_launches, tr)
+                  r.eval64_launches, r.eval32_launches, r.kernel_launches, r.ops64, r.ops32, tr)
 
 
 def gb_solve(prob: _Problem, device_only: bool = False, raise_on_error: bool = True) -> Result:

@@ -447,6 +447,8 @@ static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
         out->device_ms = ms;
     }
     out->kernel_launches = gb_launches_so_far() - launches0;
+    out->ops64 = (int64_t)hf.ops64;
+    out->ops32 = (int64_t)hf.ops32;
     out->n_trace = (int64_t)trace.size();
     if (!trace.empty()) {
         out->trace = (gb_gen_stat*)std::malloc(trace.size() * sizeof(gb_gen_stat));

@@ -168,6 +168,7 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
         if (k >= 2) I.b = (uint8_t)oreg[q.b];
         I.c = q.v;
         out_float(q.v, &I.clo32, &I.chi32);
+        I.pad = fwd_ops(I.op) | (rev_ops(I.op) << 8);
         if (q.op == GB_OP_VAR) {
             I.aux = q.a;
             P->var_leaves.push_back(GbVarLeaf{oreg[v], q.a});
@@ -196,6 +197,7 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
             if (kk >= 2) J.b = (uint8_t)treg[w.b];
             J.c = w.v;
             out_float(w.v, &J.clo32, &J.chi32);
+            J.pad = fwd_ops(J.op) | (rev_ops(J.op) << 8);
             if (w.op == GB_OP_IDX_VAR) {
                 J.aux = w.b;
                 if (!hv) omin = omax = w.b, hv = 1;

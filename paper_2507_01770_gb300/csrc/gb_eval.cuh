@@ -107,11 +107,12 @@ template <typename I> struct Tree {
 // Forward interpretation of one template for term index i; returns the root.
 template <typename T, typename V>
 __device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const GbSum& S, int i,
-                                                         const V& X, typename Prec<T>::I* R) {
+                                                         const V& X, typename Prec<T>::I* R, int& ops) {
     typedef typename Prec<T>::I I;
     const GbIns* ins = P.tins + S.ins0;
     for (int t = 0; t < S.nins; t++) {
         GbIns in = ins[t];
+        ops += in.pad & 0xff;
         I v;
         switch (in.op) {
         case D_CONST: v = Prec<T>::cst(in); break;
@@ -147,10 +148,11 @@ __device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const G
 // adjoint thus receives its consumers' contributions in descending order.
 template <typename T>
 __device__ __forceinline__ void reverse_sweep(const GbIns* ins, int nins, const typename Prec<T>::I* V,
-                                              typename Prec<T>::I* A) {
+                                              typename Prec<T>::I* A, int& ops) {
     typedef typename Prec<T>::I I;
     for (int t = nins - 1; t >= 0; t--) {
         GbIns in = ins[t];
+        ops += (in.pad >> 8) & 0xff;
         I g = A[t];
         switch (in.op) {
         case D_ADD:
@@ -193,12 +195,13 @@ __device__ __forceinline__ void reverse_sweep(const GbIns* ins, int nins, const 
 // Sum of the terms of one group (local group g of sum S).
 template <typename T, typename V>
 __device__ __forceinline__ typename Prec<T>::I group_sum(const GbProg& P, const GbSum& S, int g, const V& X,
-                                                          typename Prec<T>::I* R) {
+                                                          typename Prec<T>::I* R, int& ops) {
     typedef typename Prec<T>::I I;
     GbGroup G = P.groups[S.group0 + g];
     Tree<I> tr;
     tr.init();
-    for (int t = 0; t < G.count; t++) tr.push(term_fwd<T>(P, S, S.first + (G.t0 + t) * S.step, X, R));
+    for (int t = 0; t < G.count; t++) tr.push(term_fwd<T>(P, S, S.first + (G.t0 + t) * S.step, X, R, ops));
+    ops += 2 * (G.count > 0 ? G.count - 1 : 0);
     return tr.result();
 }
 
@@ -206,7 +209,7 @@ __device__ __forceinline__ typename Prec<T>::I group_sum(const GbProg& P, const 
 // (one interval per global group; NULL: recompute everything).
 template <typename T, typename V, typename C>
 __device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X, const C* cache,
-                                           typename Prec<T>::I* R, typename Prec<T>::I* sums) {
+                                           typename Prec<T>::I* R, typename Prec<T>::I* sums, int& ops) {
     typedef typename Prec<T>::I I;
     for (int k = 0; k < P.n_sum; k++) {
         GbSum S = P.sums[k];
@@ -216,7 +219,7 @@ __device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X,
         for (int g = 0; g < S.ngroups; g++) {
             I v;
             if (g >= dr.x && g < dr.y) {
-                v = group_sum<T>(P, S, g, X, R);
+                v = group_sum<T>(P, S, g, X, R, ops);
             } else {
                 C c = cache[S.group0 + g];
                 v.lo = c.x;
@@ -224,6 +227,7 @@ __device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X,
             }
             tr.push(v);
         }
+        ops += 2 * (S.ngroups > 0 ? S.ngroups - 1 : 0);
         sums[k] = tr.result();
     }
 }
@@ -232,10 +236,11 @@ __device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X,
 template <typename T, typename V>
 __device__ __forceinline__ typename Prec<T>::I outer_fwd(const GbProg& P, const V& X,
                                                           const typename Prec<T>::I* sums,
-                                                          typename Prec<T>::I* O) {
+                                                          typename Prec<T>::I* O, int& ops) {
     typedef typename Prec<T>::I I;
     for (int t = 0; t < P.n_outer; t++) {
         GbIns in = P.outer[t];
+        ops += in.pad & 0xff;
         I v;
         switch (in.op) {
         case D_CONST: v = Prec<T>::cst(in); break;
@@ -275,12 +280,12 @@ template <typename T, typename V>
 __device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X, const View<double>& X64,
                                            const typename Prec<T>::I* O, typename Prec<T>::I* OA,
                                            typename Prec<T>::I* R, typename Prec<T>::I* RA,
-                                           double* Gout) {
+                                           double* Gout, int& ops) {
     typedef typename Prec<T>::I I;
     // outer adjoints
     for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
     OA[P.outer_root] = mk<T>((T)1, (T)1);
-    reverse_sweep<T>(P.outer, P.n_outer, O, OA);
+    reverse_sweep<T>(P.outer, P.n_outer, O, OA, ops);
 
     const int c0 = blk * P.B;
     const int c1 = min(P.n, c0 + P.B);
@@ -300,18 +305,18 @@ __device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X,
         I g = mk<T>((T)0, (T)0);
         for (int v = 0; v < P.n_var_leaves; v++) {
             GbVarLeaf L = P.var_leaves[v];
-            if (L.coord == j) g = iadd(g, OA[L.reg]);
+            if (L.coord == j) g = iadd(g, OA[L.reg]), ops += 2;
         }
         for (int k = 0; k < P.n_sum; k++) {
             GbSum S = P.sums[k];
             if (!S.has_var) continue;
             while (cur[k] < S.count && S.first + cur[k] * S.step + S.off_min <= j) {
                 int i = S.first + cur[k] * S.step;
-                term_fwd<T>(P, S, i, X, R);
+                term_fwd<T>(P, S, i, X, R, ops);
                 for (int t = 0; t < S.nins; t++) RA[t] = mk<T>((T)0, (T)0);
                 RA[S.nins - 1] = mk<T>((T)1, (T)1);
                 const GbIns* ins = P.tins + S.ins0;
-                reverse_sweep<T>(ins, S.nins, R, RA);
+                reverse_sweep<T>(ins, S.nins, R, RA, ops);
                 for (int t = 0; t < S.nins; t++) {
                     GbIns in = ins[t];
                     if (in.op != D_IVAR) continue;
@@ -319,6 +324,7 @@ __device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X,
                     if (cc < c0 || cc >= c1) continue;
                     int w = cc & (GB_MAX_WIN - 1);
                     W[k][w] = iadd(W[k][w], RA[t]);
+                    ops += 2;
                     touched[k] |= 1u << w;
                 }
                 cur[k]++;
@@ -326,6 +332,7 @@ __device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X,
             int w = j & (GB_MAX_WIN - 1);
             if (touched[k] & (1u << w)) {
                 g = iadd(g, imul(OA[S.outer_reg], W[k][w]));
+                ops += 4;
                 W[k][w] = mk<T>((T)0, (T)0);
                 touched[k] &= ~(1u << w);
             }

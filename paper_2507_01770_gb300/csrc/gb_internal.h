@@ -35,7 +35,7 @@ struct GbIns {
     int32_t aux2;     // COEF offset
     float clo32;      // c rounded down to float
     float chi32;      // c rounded up to float
-    int32_t pad;
+    int32_t pad;      // directed-op cost: forward (bits 0-7), reverse (bits 8-15)
     double c;         // CONST value | SCALE factor
 };  // 32 bytes
 
@@ -138,4 +138,5 @@ struct GbState {
     int overflow;               // survivors do not fit: generation abandoned
     int error;                  // device-side error code (bit flags)
     long long evals32, evals64, mids;  // running counters
+    unsigned long long ops64, ops32;   // directed-rounding operations executed by the eval kernels
 };

@@ -76,15 +76,16 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, GbState* st) {
     View<float> X32{pool.lo32, pool.hi32, nullptr, nullptr, 0, 0, 1, 2, 0u};
     iv64 R[GB_MAX_TREGS];
     iv32 R32[GB_MAX_TREGS];
+    int ops = 0;
     for (int k = 0; k < P.n_sum; k++) {
         GbSum S = P.sums[k];
         for (int g = threadIdx.x; g < S.ngroups; g += blockDim.x) {
-            iv64 a = group_sum<double>(P, S, g, X, R);
-            iv64 b = group_sum<double>(P, S, g, MX, R);
+            iv64 a = group_sum<double>(P, S, g, X, R, ops);
+            iv64 b = group_sum<double>(P, S, g, MX, R, ops);
             pool.gsum[S.group0 + g] = make_double2(a.lo, a.hi);
             pool.gmid[S.group0 + g] = make_double2(b.lo, b.hi);
             if (pool.fp32) {
-                iv32 c = group_sum<float>(P, S, g, X32, R32);
+                iv32 c = group_sum<float>(P, S, g, X32, R32, ops);
                 pool.gsum32[S.group0 + g] = make_float2(c.lo, c.hi);
             }
         }
@@ -92,10 +93,10 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, GbState* st) {
     __syncthreads();
     if (threadIdx.x != 0) return;
     iv64 sums[GB_MAX_ISUM], O[GB_MAX_OREGS];
-    sum_values<double>(P, 0, X, (const double2*)nullptr, R, sums);
-    iv64 F = outer_fwd<double>(P, X, sums, O);
-    sum_values<double>(P, 0, MX, (const double2*)nullptr, R, sums);
-    iv64 Fm = outer_fwd<double>(P, MX, sums, O);
+    sum_values<double>(P, 0, X, (const double2*)nullptr, R, sums, ops);
+    iv64 F = outer_fwd<double>(P, X, sums, O, ops);
+    sum_values<double>(P, 0, MX, (const double2*)nullptr, R, sums, ops);
+    iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
     double gub = Fm.hi;
     if (gub != gub) gub = __longlong_as_double(0x7ff0000000000000LL);
     E.flo[0] = canon_lo(F.lo);
@@ -414,10 +415,17 @@ __device__ __forceinline__ void warp_min_gub(unsigned long long key, bool has, G
     if ((threadIdx.x & 31) == 0 && k != ~0ull) atomicMin(&st->gub_new_key, k);
 }
 
+__device__ __forceinline__ void warp_add_ops(int ops, unsigned long long* dst) {
+    unsigned long long v = (unsigned long long)ops;
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
 // FP64 child evaluation: midpoint sample, F(X), first-order test.
 __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool, const GbParents& par,
                                              const GbChildren& ch, long long ci, const GbSplit& sp,
-                                             double gub_prev, unsigned long long* gkey, bool* has_key) {
+                                             double gub_prev, unsigned long long* gkey, bool* has_key,
+                                             int& ops) {
     ChildCtx c = child_ctx(par, ci, sp);
     if (!c.valid) {
         ch.flag[ci] = 0;
@@ -428,16 +436,16 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
     MidView MX{X};
     iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
     const int blk = c.info.z;
-    sum_values<double>(P, blk, MX, pool.gmid + (size_t)c.slot * pool.NG, R, sums);
-    iv64 Fm = outer_fwd<double>(P, MX, sums, O);
+    sum_values<double>(P, blk, MX, pool.gmid + (size_t)c.slot * pool.NG, R, sums, ops);
+    iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
     if (Fm.hi == Fm.hi) {
         *gkey = gb_order_key(Fm.hi);
         *has_key = true;
     }
-    sum_values<double>(P, blk, X, pool.gsum + (size_t)c.slot * pool.NG, R, sums);
-    iv64 F = outer_fwd<double>(P, X, sums, O);
+    sum_values<double>(P, blk, X, pool.gsum + (size_t)c.slot * pool.NG, R, sums, ops);
+    iv64 F = outer_fwd<double>(P, X, sums, O, ops);
     bool keep = !(F.lo > gub_prev);
-    if (keep) keep = !block_mono<double>(P, blk, X, X, O, OA, R, RA, (double*)nullptr);
+    if (keep) keep = !block_mono<double>(P, blk, X, X, O, OA, R, RA, (double*)nullptr, ops);
     ch.flo[ci] = canon_lo(F.lo);
     ch.flag[ci] = keep ? 1 : 0;
     return true;
@@ -451,11 +459,13 @@ __global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents
     unsigned long long key = ~0ull;
     bool has = false;
     bool valid = false;
+    int ops = 0;
     if (idx < lim) {
         long long ci = from_list ? (long long)ch.list32[idx] : idx;
-        valid = eval64_child(P, pool, par, ch, ci, sp, gub_prev, &key, &has);
+        valid = eval64_child(P, pool, par, ch, ci, sp, gub_prev, &key, &has, ops);
     }
     warp_min_gub(key, has, st);
+    warp_add_ops(ops, &st->ops64);
     unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
     if ((threadIdx.x & 31) == 0 && nv) {
         atomicAdd((unsigned long long*)&st->evals64, (unsigned long long)nv);
@@ -471,6 +481,7 @@ __global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents
                                                 GbState* st) {
     long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     bool valid = false;
+    int ops = 0;
     if (ci < nchildren) {
         ChildCtx c = child_ctx(par, ci, sp);
         ch.flag[ci] = 0;
@@ -481,15 +492,16 @@ __global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents
             View<double> X64 = view64(pool, par, c, sp);
             iv32 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
             const int blk = c.info.z;
-            sum_values<float>(P, blk, X, pool.gsum32 + (size_t)c.slot * pool.NG, R, sums);
-            iv32 F = outer_fwd<float>(P, X, sums, O);
+            sum_values<float>(P, blk, X, pool.gsum32 + (size_t)c.slot * pool.NG, R, sums, ops);
+            iv32 F = outer_fwd<float>(P, X, sums, O, ops);
             bool keep = !((double)F.lo > gub_prev);
-            if (keep) keep = !block_mono<float>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr);
+            if (keep) keep = !block_mono<float>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr, ops);
             ch.flag32[ci] = keep ? 1 : 0;
         } else {
             ch.flag32[ci] = 0;
         }
     }
+    warp_add_ops(ops, &st->ops32);
     unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
     if ((threadIdx.x & 31) == 0 && nv) {
         atomicAdd((unsigned long long*)&st->evals32, (unsigned long long)nv);
@@ -568,7 +580,7 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
     MidView MX{X};
     iv64 R[GB_MAX_TREGS];
     iv32 R32[GB_MAX_TREGS];
-    int slot_k = 0;
+    int slot_k = 0, ops = 0;
     for (int k = 0; k < P.n_sum; k++) {
         GbSum S = P.sums[k];
         int2 dr = P.dirty[blk * P.n_sum + k];
@@ -582,12 +594,12 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
         for (int g = dr.x; g < dr.y; g++, slot_k++) {
             if ((slot_k & 31) != lane) continue;
             size_t dst = (size_t)ns * pool.NG + S.group0 + g;
-            iv64 a = group_sum<double>(P, S, g, X, R);
-            iv64 b = group_sum<double>(P, S, g, MX, R);
+            iv64 a = group_sum<double>(P, S, g, X, R, ops);
+            iv64 b = group_sum<double>(P, S, g, MX, R, ops);
             pool.gsum[dst] = make_double2(a.lo, a.hi);
             pool.gmid[dst] = make_double2(b.lo, b.hi);
             if (pool.fp32) {
-                iv32 f = group_sum<float>(P, S, g, X32, R32);
+                iv32 f = group_sum<float>(P, S, g, X32, R32, ops);
                 pool.gsum32[dst] = make_float2(f.lo, f.hi);
             }
         }
@@ -706,29 +718,30 @@ __global__ void __launch_bounds__(128) k_eval_boxes(GbProg P, const double* lo, 
     View<double> X{lo + (size_t)b * n, hi + (size_t)b * n, nullptr, nullptr, 0, 0, 1, 2, 0u};
     MidView MX{X};
     iv64 R[GB_MAX_TREGS], O[GB_MAX_OREGS], sums[GB_MAX_ISUM];
-    sum_values<double>(P, blk, MX, (const double2*)nullptr, R, sums);
-    iv64 Fm = outer_fwd<double>(P, MX, sums, O);
+    int ops = 0;
+    sum_values<double>(P, blk, MX, (const double2*)nullptr, R, sums, ops);
+    iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
     Fmo[2 * b] = Fm.lo;
     Fmo[2 * b + 1] = Fm.hi;
     if (!fp32) {
         iv64 RA[GB_MAX_TREGS], OA[GB_MAX_OREGS];
-        sum_values<double>(P, blk, X, (const double2*)nullptr, R, sums);
-        iv64 F = outer_fwd<double>(P, X, sums, O);
+        sum_values<double>(P, blk, X, (const double2*)nullptr, R, sums, ops);
+        iv64 F = outer_fwd<double>(P, X, sums, O, ops);
         Fo[2 * b] = F.lo;
         Fo[2 * b + 1] = F.hi;
         if (blk >= 0) {
-            bool m = block_mono<double>(P, blk, X, X, O, OA, R, RA, Go + (size_t)b * P.B * 2);
+            bool m = block_mono<double>(P, blk, X, X, O, OA, R, RA, Go + (size_t)b * P.B * 2, ops);
             mono[b] = m ? 1 : 0;
         }
     } else {
         View<float> X32{lo32 + (size_t)b * n, hi32 + (size_t)b * n, nullptr, nullptr, 0, 0, 1, 2, 0u};
         iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS], O32[GB_MAX_OREGS], OA32[GB_MAX_OREGS], s32[GB_MAX_ISUM];
-        sum_values<float>(P, blk, X32, (const float2*)nullptr, R32, s32);
-        iv32 F = outer_fwd<float>(P, X32, s32, O32);
+        sum_values<float>(P, blk, X32, (const float2*)nullptr, R32, s32, ops);
+        iv32 F = outer_fwd<float>(P, X32, s32, O32, ops);
         Fo[2 * b] = F.lo;
         Fo[2 * b + 1] = F.hi;
         if (blk >= 0) {
-            bool m = block_mono<float>(P, blk, X32, X, O32, OA32, R32, RA32, Go + (size_t)b * P.B * 2);
+            bool m = block_mono<float>(P, blk, X32, X, O32, OA32, R32, RA32, Go + (size_t)b * P.B * 2, ops);
             mono[b] = m ? 1 : 0;
         }
     }
