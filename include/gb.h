@@ -146,6 +146,8 @@ typedef struct gb_result {
     int64_t kernel_launches;  /* kernels the library launched for this solve */
     int64_t ops64;            /* directed-rounding FP64 operations executed by the FP64 evaluation kernels */
     int64_t ops32;            /* directed-rounding FP32 operations executed by the FP32 evaluation kernels */
+    double queue_ms;          /* serving: submit -> admission (host clock); 0 for gb_solve */
+    double latency_ms;        /* serving: submit -> result ready (host clock); 0 for gb_solve */
     int64_t n_trace;
     gb_gen_stat* trace;       /* n_trace rows, host */
 } gb_result;
@@ -168,6 +170,43 @@ void gb_destroy_problem(gb_problem* prob);
 
 const char* gb_status_str(gb_status s);
 const char* gb_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of many problems on one GPU                */
+/* ---------------------------------------------------------------------- */
+/* A server runs independent minimisation requests concurrently on one GPU
+ * (the paper solves one problem at a time; this is the serving form of the
+ * same method).  Requests are admitted in arrival order while the device
+ * memory they reserve (opt->pool_bytes, or budget / max_active when 0) fits
+ * the budget and fewer than max_active are running; each admitted request
+ * runs its generations on its own stream, and the server advances whichever
+ * request's previous generation has finished, so the requests' kernels
+ * overlap on the device.  Finished requests free their memory and slot for
+ * the queued ones.  A request's result does not depend on the others. */
+typedef struct gb_server gb_server;
+
+/* Starts a server (and its worker thread) on `device`.  pool_budget_bytes
+ * bounds the device memory reserved by running requests.  Returns
+ * GB_E_INVALID for a zero budget or max_active < 1, GB_E_CUDA without the
+ * device. */
+gb_status gb_server_create(size_t pool_budget_bytes, int32_t device, int32_t max_active, gb_server** out);
+
+/* Queues a request (same arguments as gb_create_problem; everything is
+ * copied) and returns at once with its id.  Never blocks on the GPU.
+ * GB_E_BUSY if the server is shutting down. */
+gb_status gb_submit(gb_server* srv, const gb_node* h_dag, int32_t n_nodes, int32_t root,
+                    const double* const* h_tables, const int64_t* h_table_lens, int32_t n_tables,
+                    int32_t n, const double* l, const double* u, double tol, const gb_options* opt,
+                    uint64_t* request_id);
+
+/* GB_E_BUSY while the request is queued or running.  Once it has finished,
+ * fills *out (host arrays owned by the caller from then on: release with
+ * gb_free_result; queue_ms / latency_ms set), forgets the id and returns the
+ * solve's status.  GB_E_INVALID for an unknown id. */
+gb_status gb_poll(gb_server* srv, uint64_t request_id, gb_result* out);
+
+/* Stops the worker, releases running requests and unclaimed results. */
+gb_status gb_server_destroy(gb_server* srv);
 
 /* ---------------------------------------------------------------------- */
 /* Parity hook: evaluate given boxes from scratch                          */

@@ -58,13 +58,15 @@ class gb_result(ctypes.Structure):
                 ("eval64_ms", ctypes.c_double), ("eval32_ms", ctypes.c_double),
                 ("eval64_launches", ctypes.c_int64), ("eval32_launches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ops64", ctypes.c_int64),
-                ("ops32", ctypes.c_int64), ("n_trace", ctypes.c_int64),
+                ("ops32", ctypes.c_int64), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("n_trace", ctypes.c_int64),
                 ("trace", ctypes.POINTER(gb_gen_stat))]
 
 
 EXPORTS = ["gb_default_options", "gb_create_problem", "gb_solve", "gb_solve_device",
            "gb_free_result", "gb_destroy_problem", "gb_status_str", "gb_last_error",
-           "gb_eval_boxes", "gb_eval_boxes_noalloc", "gb_problem_info", "gb_measure_peak"]
+           "gb_eval_boxes", "gb_eval_boxes_noalloc", "gb_problem_info", "gb_measure_peak",
+           "gb_server_create", "gb_submit", "gb_poll", "gb_server_destroy"]
 
 
 def library_path() -> str:
@@ -108,6 +110,15 @@ def load(build_if_missing: bool = True):
     L.gb_problem_info.restype = ctypes.c_int
     L.gb_measure_peak.argtypes = [i32, i32, _PD, _PD]
     L.gb_measure_peak.restype = ctypes.c_int
+    L.gb_server_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)]
+    L.gb_server_create.restype = ctypes.c_int
+    L.gb_submit.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_PD), ctypes.POINTER(i64), i32, i32, _PD, _PD,
+                            ctypes.c_double, ctypes.POINTER(gb_options), ctypes.POINTER(ctypes.c_uint64)]
+    L.gb_submit.restype = ctypes.c_int
+    L.gb_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(gb_result)]
+    L.gb_poll.restype = ctypes.c_int
+    L.gb_server_destroy.argtypes = [vp]
+    L.gb_server_destroy.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -189,6 +200,8 @@ class Result:
     kernel_launches: int
     ops64: int
     ops32: int
+    queue_ms: float
+    latency_ms: float
     trace: dict
 
 
@@ -213,7 +226,8 @@ def _result(r: gb_result, n: int) -> Result:
                   hi.reshape(nb, n) if hi is not None else None,
                   arr(r.box_flo, nb), r.generations, r.box_evals_fp32, r.box_evals_fp64,
                   r.mid_evals, r.solve_ms, r.device_ms, r.eval64_ms, r.eval32_ms,
-                  r.eval64_launches, r.eval32_launches, r.kernel_launches, r.ops64, r.ops32, tr)
+                  r.eval64_launches, r.eval32_launches, r.kernel_launches, r.ops64, r.ops32,
+                  r.queue_ms, r.latency_ms, tr)
 
 
 def gb_solve(prob: _Problem, device_only: bool = False, raise_on_error: bool = True) -> Result:
@@ -302,3 +316,60 @@ class Solver:
 
     def close(self):
         self.h.close()
+
+
+class Server:
+    """Binding of the gb_server_* calls (continuous batching on one GPU)."""
+
+    def __init__(self, pool_budget_bytes: int, device: int = 0, max_active: int = 16):
+        h = ctypes.c_void_p()
+        rc = load().gb_server_create(int(pool_budget_bytes), int(device), int(max_active), ctypes.byref(h))
+        if rc != GB_OK:
+            raise GbError(rc, gb_last_error())
+        self.h = h
+        self._n = {}
+
+    def submit(self, problem, options: gb_options | None = None) -> int:
+        """Queue a problem description (nodes, root, tables, n, l, u, tol_f)."""
+        nodes = np.ascontiguousarray(problem.nodes)
+        tabs = [np.ascontiguousarray(t, dtype=np.float64) for t in problem.tables]
+        ptrs = (_PD * max(1, len(tabs)))(*[t.ctypes.data_as(_PD) for t in tabs])
+        lens = (ctypes.c_int64 * max(1, len(tabs)))(*[len(t) for t in tabs])
+        l = np.ascontiguousarray(problem.l, dtype=np.float64)
+        u = np.ascontiguousarray(problem.u, dtype=np.float64)
+        rid = ctypes.c_uint64()
+        rc = load().gb_submit(self.h, nodes.ctypes.data, len(nodes), int(problem.root), ptrs, lens, len(tabs),
+                              int(problem.n), l.ctypes.data_as(_PD), u.ctypes.data_as(_PD),
+                              float(problem.tol_f), ctypes.byref(options) if options is not None else None,
+                              ctypes.byref(rid))
+        if rc != GB_OK:
+            raise GbError(rc, gb_last_error())
+        self._n[rid.value] = int(problem.n)
+        return rid.value
+
+    def poll(self, rid: int):
+        """None while running; the Result once finished."""
+        L = load()
+        r = gb_result()
+        rc = L.gb_poll(self.h, ctypes.c_uint64(rid), ctypes.byref(r))
+        if rc == GB_E_BUSY:
+            return None
+        n = self._n.pop(rid, None)
+        try:
+            res = _result(r, n) if n is not None else None
+        finally:
+            L.gb_free_result(ctypes.byref(r))
+        if rc not in (GB_OK, GB_E_CAPACITY, GB_E_LIMIT):
+            raise GbError(rc, gb_last_error())
+        return res
+
+    def close(self):
+        if self.h:
+            load().gb_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -33,22 +33,37 @@ gb_status cuda_fail(cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
+// Device allocations of a problem are stream-ordered (cudaMallocAsync on the
+// problem's stream, freed with cudaFreeAsync): creating and destroying
+// problems never synchronises the whole device, which matters when a server
+// creates and retires problems while others run.
+struct DevAlloc {
+    std::vector<void*>* owned;
+    size_t* bytes;
+    cudaStream_t s;
+};
+
 template <typename T>
-cudaError_t upload(T** dst, const T* src, size_t count, std::vector<void*>& owned) {
+cudaError_t upload(T** dst, const T* src, size_t count, DevAlloc& a) {
     *dst = nullptr;
     size_t bytes = sizeof(T) * (count ? count : 1);
-    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    cudaError_t e = cudaMallocAsync((void**)dst, bytes, a.s);
     if (e != cudaSuccess) return e;
-    owned.push_back(*dst);
-    if (count) e = cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
+    a.owned->push_back(*dst);
+    *a.bytes += bytes;
+    if (count) e = cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, a.s);
     return e;
 }
 
 template <typename T>
-cudaError_t alloc(T** dst, size_t count, std::vector<void*>& owned) {
+cudaError_t alloc(T** dst, size_t count, DevAlloc& a) {
     *dst = nullptr;
-    cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (count ? count : 1));
-    if (e == cudaSuccess) owned.push_back(*dst);
+    size_t bytes = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMallocAsync((void**)dst, bytes, a.s);
+    if (e == cudaSuccess) {
+        a.owned->push_back(*dst);
+        *a.bytes += bytes;
+    }
     return e;
 }
 
@@ -59,6 +74,18 @@ void float_bounds(double c, float* lo, float* hi) {
 }
 
 }  // namespace
+
+struct SolveRun {
+    bool active = false, loop_done = false;
+    int cur = 0;
+    std::vector<gb_gen_stat> trace;
+    long long last_par = 0, launches = 0;
+    bool timed64 = false, timed32 = false;
+    double t64 = 0.0, t32 = 0.0;
+    long long n64 = 0, n32 = 0;
+    gb_status status = GB_OK;
+    std::chrono::steady_clock::time_point t0;
+};
 
 struct gb_problem {
     int n = 0, device = 0;
@@ -79,6 +106,9 @@ struct gb_problem {
     unsigned* out_list = nullptr;
     long long cap = 0, K = 0, Cmax = 0, fan = 0;
     cudaEvent_t ev[6] = {};        // solve start/end, eval64 start/end, eval32 start/end
+    cudaEvent_t ev_state = nullptr; // the state record of the last generation has reached the host
+    SolveRun run;
+    size_t device_bytes = 0;       // device memory held by the problem
 };
 
 extern "C" {
@@ -111,11 +141,16 @@ const char* gb_last_error(void) { return g_err.c_str(); }
 void gb_destroy_problem(gb_problem* p) {
     if (!p) return;
     cudaSetDevice(p->device);
-    if (p->stream) cudaStreamSynchronize(p->stream);
-    for (void* q : p->owned) cudaFree(q);
+    if (p->stream) {
+        for (void* q : p->owned) cudaFreeAsync(q, p->stream);
+        cudaStreamSynchronize(p->stream);
+    } else {
+        for (void* q : p->owned) cudaFree(q);
+    }
     if (p->st_host) cudaFreeHost(p->st_host);
     for (cudaEvent_t e : p->ev)
         if (e) cudaEventDestroy(e);
+    if (p->ev_state) cudaEventDestroy(p->ev_state);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -182,6 +217,8 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         gb_destroy_problem(p);
         return rc;
     };
+    if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking))) return bad(e, "cudaStreamCreate");
+    DevAlloc A{&p->owned, &p->device_bytes, p->stream};
 
     // ---- program and tables ----------------------------------------------
     const GbHostProg& H = p->hp;
@@ -200,30 +237,31 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     int2* d_dirty;
     GbVarLeaf* d_leaves;
     double *d_l, *d_u;
-    if ((e = upload(&d_outer, H.outer.data(), H.outer.size(), p->owned))) return bad(e, "upload program");
-    if ((e = upload(&d_tins, H.tins.data(), H.tins.size(), p->owned))) return bad(e, "upload program");
-    if ((e = upload(&d_sums, H.sums.data(), H.sums.size(), p->owned))) return bad(e, "upload program");
-    if ((e = upload(&d_groups, H.groups.data(), H.groups.size(), p->owned))) return bad(e, "upload program");
-    if ((e = upload(&d_dirty, H.dirty.data(), H.dirty.size(), p->owned))) return bad(e, "upload program");
-    if ((e = upload(&d_leaves, H.var_leaves.data(), H.var_leaves.size(), p->owned))) return bad(e, "upload program");
-    if ((e = upload(&d_l, l, (size_t)n, p->owned))) return bad(e, "upload bounds");
-    if ((e = upload(&d_u, u, (size_t)n, p->owned))) return bad(e, "upload bounds");
-    std::vector<const double*> t64(n_tables > 0 ? n_tables : 1, nullptr);
+    if ((e = upload(&d_outer, H.outer.data(), H.outer.size(), A))) return bad(e, "upload program");
+    if ((e = upload(&d_tins, H.tins.data(), H.tins.size(), A))) return bad(e, "upload program");
+    if ((e = upload(&d_sums, H.sums.data(), H.sums.size(), A))) return bad(e, "upload program");
+    if ((e = upload(&d_groups, H.groups.data(), H.groups.size(), A))) return bad(e, "upload program");
+    if ((e = upload(&d_dirty, H.dirty.data(), H.dirty.size(), A))) return bad(e, "upload program");
+    if ((e = upload(&d_leaves, H.var_leaves.data(), H.var_leaves.size(), A))) return bad(e, "upload program");
+    if ((e = upload(&d_l, l, (size_t)n, A))) return bad(e, "upload bounds");
+    if ((e = upload(&d_u, u, (size_t)n, A))) return bad(e, "upload bounds");
+    std::vector<const double*> t64(n_tables > 0 ? n_tables : 1, nullptr);  // kept until the final sync
     std::vector<const float2*> t32(n_tables > 0 ? n_tables : 1, nullptr);
     for (int t = 0; t < n_tables; t++) {
         double* d64;
         float2* d32;
         std::vector<float2> f(table_lens[t]);
         for (int64_t i = 0; i < table_lens[t]; i++) float_bounds(tables[t][i], &f[i].x, &f[i].y);
-        if ((e = upload(&d64, tables[t], (size_t)table_lens[t], p->owned))) return bad(e, "upload tables");
-        if ((e = upload(&d32, f.data(), f.size(), p->owned))) return bad(e, "upload tables");
+        if ((e = upload(&d64, tables[t], (size_t)table_lens[t], A))) return bad(e, "upload tables");
+        if ((e = upload(&d32, f.data(), f.size(), A))) return bad(e, "upload tables");
+        if ((e = cudaStreamSynchronize(p->stream))) return bad(e, "upload tables");   // f is released below
         t64[t] = d64;
         t32[t] = d32;
     }
     const double** d_t64;
     const float2** d_t32;
-    if ((e = upload(&d_t64, t64.data(), t64.size(), p->owned))) return bad(e, "upload tables");
-    if ((e = upload(&d_t32, t32.data(), t32.size(), p->owned))) return bad(e, "upload tables");
+    if ((e = upload(&d_t64, t64.data(), t64.size(), A))) return bad(e, "upload tables");
+    if ((e = upload(&d_t32, t32.data(), t32.size(), A))) return bad(e, "upload tables");
     P.outer = d_outer;
     P.tins = d_tins;
     P.sums = d_sums;
@@ -254,42 +292,43 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     pl.n = n;
     pl.NG = NG;
     pl.fp32 = fp32;
-    if ((e = alloc(&pl.lo64, (size_t)cap * n, p->owned)) || (e = alloc(&pl.hi64, (size_t)cap * n, p->owned)) ||
-        (e = alloc(&pl.gsum, (size_t)cap * NG, p->owned)) || (e = alloc(&pl.gmid, (size_t)cap * NG, p->owned)) ||
-        (e = alloc(&pl.freel, (size_t)cap, p->owned)))
+    if ((e = alloc(&pl.lo64, (size_t)cap * n, A)) || (e = alloc(&pl.hi64, (size_t)cap * n, A)) ||
+        (e = alloc(&pl.gsum, (size_t)cap * NG, A)) || (e = alloc(&pl.gmid, (size_t)cap * NG, A)) ||
+        (e = alloc(&pl.freel, (size_t)cap, A)))
         return bad(e, "allocate box pool");
     if (fp32) {
-        if ((e = alloc(&pl.lo32, (size_t)cap * n, p->owned)) || (e = alloc(&pl.hi32, (size_t)cap * n, p->owned)) ||
-            (e = alloc(&pl.gsum32, (size_t)cap * NG, p->owned)))
+        if ((e = alloc(&pl.lo32, (size_t)cap * n, A)) || (e = alloc(&pl.hi32, (size_t)cap * n, A)) ||
+            (e = alloc(&pl.gsum32, (size_t)cap * NG, A)))
             return bad(e, "allocate box pool");
     }
     for (int b = 0; b < 2; b++)
-        if ((e = alloc(&p->E[b].flo, (size_t)cap, p->owned)) || (e = alloc(&p->E[b].slot, (size_t)cap, p->owned)) ||
-            (e = alloc(&p->E[b].cyc, (size_t)cap, p->owned)))
+        if ((e = alloc(&p->E[b].flo, (size_t)cap, A)) || (e = alloc(&p->E[b].slot, (size_t)cap, A)) ||
+            (e = alloc(&p->E[b].cyc, (size_t)cap, A)))
             return bad(e, "allocate pool entries");
     const size_t K = (size_t)p->K, bt = K * d * (m + 1);
-    if ((e = alloc(&p->par.slot, K, p->owned)) || (e = alloc(&p->par.cyc, K, p->owned)) ||
-        (e = alloc(&p->par.flo, K, p->owned)) || (e = alloc(&p->par.info, K, p->owned)) ||
-        (e = alloc(&p->par.bnd, bt, p->owned)) || (e = alloc(&p->par.bnd_rd, bt, p->owned)) ||
-        (e = alloc(&p->par.bnd_ru, bt, p->owned)))
+    if ((e = alloc(&p->par.slot, K, A)) || (e = alloc(&p->par.cyc, K, A)) ||
+        (e = alloc(&p->par.flo, K, A)) || (e = alloc(&p->par.info, K, A)) ||
+        (e = alloc(&p->par.bnd, bt, A)) || (e = alloc(&p->par.bnd_rd, bt, A)) ||
+        (e = alloc(&p->par.bnd_ru, bt, A)))
         return bad(e, "allocate parent buffers");
     const size_t C = (size_t)p->Cmax;
-    if ((e = alloc(&p->ch.flo, C, p->owned)) || (e = alloc(&p->ch.flag, C, p->owned)) ||
-        (e = alloc(&p->ch.flag32, C, p->owned)) || (e = alloc(&p->ch.list32, C, p->owned)) ||
-        (e = alloc(&p->ch.surv, C, p->owned)))
+    if ((e = alloc(&p->ch.flo, C, A)) || (e = alloc(&p->ch.flag, C, A)) ||
+        (e = alloc(&p->ch.flag32, C, A)) || (e = alloc(&p->ch.list32, C, A)) ||
+        (e = alloc(&p->ch.surv, C, A)))
         return bad(e, "allocate child buffers");
     long long items = cap > p->Cmax ? cap : p->Cmax;
     p->sc.max_tiles = (int)((items + GB_TILE - 1) / GB_TILE) + 1;
-    if ((e = alloc(&p->sc.tile_cnt, (size_t)3 * p->sc.max_tiles, p->owned)) ||
-        (e = alloc(&p->sc.tile_off, (size_t)3 * p->sc.max_tiles, p->owned)) ||
-        (e = alloc(&p->sc.hist, (size_t)65536, p->owned)) || (e = alloc(&p->out_list, (size_t)cap, p->owned)) ||
-        (e = alloc(&p->st, 1, p->owned)))
+    if ((e = alloc(&p->sc.tile_cnt, (size_t)3 * p->sc.max_tiles, A)) ||
+        (e = alloc(&p->sc.tile_off, (size_t)3 * p->sc.max_tiles, A)) ||
+        (e = alloc(&p->sc.hist, (size_t)65536, A)) || (e = alloc(&p->out_list, (size_t)cap, A)) ||
+        (e = alloc(&p->st, 1, A)))
         return bad(e, "allocate scan buffers");
-    if ((e = cudaMemset(p->sc.hist, 0, 65536 * sizeof(unsigned)))) return bad(e, "cudaMemset");
+    if ((e = cudaMemsetAsync(p->sc.hist, 0, 65536 * sizeof(unsigned), p->stream))) return bad(e, "cudaMemset");
     if ((e = cudaMallocHost((void**)&p->st_host, sizeof(GbState)))) return bad(e, "cudaMallocHost");
-    if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking))) return bad(e, "cudaStreamCreate");
     for (cudaEvent_t& ev : p->ev)
         if ((e = cudaEventCreate(&ev))) return bad(e, "cudaEventCreate");
+    if ((e = cudaEventCreateWithFlags(&p->ev_state, cudaEventDisableTiming))) return bad(e, "cudaEventCreate");
+    if ((e = cudaStreamSynchronize(p->stream))) return bad(e, "upload");   // host sources may now go away
     *out = p;
     return GB_OK;
 }
@@ -313,12 +352,18 @@ void gb_free_result(gb_result* r) {
     std::memset(r, 0, sizeof(*r));
 }
 
-static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
-    if (!p || !out) return fail(GB_E_INVALID, "NULL argument");
-    std::memset(out, 0, sizeof(*out));
+// ---------------------------------------------------------------------------
+// A solve as a resumable state machine: solve_begin enqueues the root box,
+// each solve_advance reads the state record of the previous generation (when
+// its asynchronous copy has landed) and enqueues the next generation,
+// solve_finish gathers the output.  gb_solve runs the three blocking; the
+// serving loop interleaves many problems without blocking on any of them.
+__attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
+    SolveRun& R = p->run;
+    R = SolveRun{};
+    R.t0 = std::chrono::steady_clock::now();
     GB_CU(cudaSetDevice(p->device));
-    auto t0 = std::chrono::steady_clock::now();
-    const long long launches0 = gb_launches_so_far();
+    const long long l0 = gb_launches_so_far();
     cudaStream_t s = p->stream;
     GbState init{};
     init.cap = p->cap;
@@ -326,79 +371,100 @@ static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
     GB_CU(cudaMemcpyAsync(p->st, &init, sizeof(GbState), cudaMemcpyHostToDevice, s));
     GB_CU(gb_launch_root_init(p->P, p->pool, p->E[0], p->st, s));
     GB_CU(gb_launch_stats(p->E[0], 1, p->tol_f, p->st, s));
-    int cur = 0;
-    std::vector<gb_gen_stat> trace;
-    gb_status status = GB_OK;
-    long long last_par = 0, last_children = 0;
-    bool timed64 = false, timed32 = false;
-    double t64 = 0.0, t32 = 0.0;
-    long long n64 = 0, n32 = 0;
-    for (;;) {
-        GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
-        GB_CU(cudaStreamSynchronize(s));
-        GbState h = *p->st_host;
-        double gub = gb_key_value(h.gub_key);
-        float ms = 0.f;
-        if (timed64 && cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) t64 += ms, n64++;
-        if (timed32 && cudaEventElapsedTime(&ms, p->ev[4], p->ev[5]) == cudaSuccess) t32 += ms, n32++;
-        timed64 = timed32 = false;
-        if (h.gen > 0) {
-            gb_gen_stat g;
-            g.parents = last_par;
-            g.children = h.children;
-            g.kept32 = p->opt.fp32_prefilter ? h.kept32 : h.children;
-            g.kept = h.overflow ? 0 : h.kept;
-            g.pool = h.pool;
-            g.gub = gub;
-            if ((long long)trace.size() < h.gen) trace.push_back(g);
-        }
-        if (h.error) {
-            status = fail(GB_E_CUDA, "device-side selection error");
-            break;
-        }
-        if (h.overflow) {
-            status = GB_E_CAPACITY;
-            g_err = "box pool capacity reached";
-            break;
-        }
-        if (h.active == 0) break;
-        if (h.gen >= p->opt.max_generations) {
-            status = GB_E_LIMIT;
-            g_err = "generation limit reached";
-            break;
-        }
-        const long long count = h.pool;
-        const long long npar = h.active < p->K ? h.active : p->K;
-        const long long nch = npar * p->fan;
-        GB_CU(gb_launch_select(p->E[cur], count, h.active, p->K, gub, p->tol_f, p->st, p->sc, s));
-        GB_CU(gb_launch_partition(p->E[cur], count, gub, p->tol_f, p->E[1 - cur], p->par, p->pool, p->st, p->sc, s));
-        GB_CU(gb_launch_prep(p->P, p->pool, p->par, npar, p->sp, p->st, s));
-        if (p->opt.fp32_prefilter) {
-            GB_CU(cudaEventRecord(p->ev[4], s));
-            GB_CU(gb_launch_eval32(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, p->st, s));
-            GB_CU(cudaEventRecord(p->ev[5], s));
-            GB_CU(gb_launch_compact_children(p->ch, nch, 0, p->st, p->sc, s));
-            GB_CU(cudaEventRecord(p->ev[2], s));
-            GB_CU(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, true, p->st, s));
-            GB_CU(cudaEventRecord(p->ev[3], s));
-            timed32 = true;
-        } else {
-            GB_CU(cudaEventRecord(p->ev[2], s));
-            GB_CU(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, false, p->st, s));
-            GB_CU(cudaEventRecord(p->ev[3], s));
-        }
-        timed64 = true;
-        GB_CU(gb_launch_compact_children(p->ch, nch, 1, p->st, p->sc, s));
-        GB_CU(gb_launch_materialize(p->P, p->pool, p->par, p->ch, nch, p->sp, p->E[1 - cur], p->opt.tol_x, p->st, s));
-        GB_CU(gb_launch_finish(p->par, npar, p->pool, p->E[1 - cur], p->st, s));
-        cur = 1 - cur;
-        last_par = npar;
-        last_children = nch;
-        long long bound = count + nch;
-        GB_CU(gb_launch_stats(p->E[cur], bound < p->cap ? bound : p->cap, p->tol_f, p->st, s));
+    GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
+    GB_CU(cudaEventRecord(p->ev_state, s));
+    R.launches += gb_launches_so_far() - l0;
+    R.active = true;
+    return GB_OK;
+}
+
+// Returns 1 when the generation loop has ended (R.status holds the outcome),
+// 0 when another generation was enqueued or (non-blocking) the previous one
+// has not finished yet.
+__attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool block) {
+    SolveRun& R = p->run;
+    if (R.loop_done) return 1;
+    auto stop = [&](gb_status st) {
+        R.status = st;
+        R.loop_done = true;
+        return 1;
+    };
+    cudaError_t q = block ? cudaEventSynchronize(p->ev_state) : cudaEventQuery(p->ev_state);
+    if (q == cudaErrorNotReady) return 0;
+    if (q != cudaSuccess) return stop(cuda_fail(q, "generation"));
+    cudaSetDevice(p->device);
+    cudaStream_t s = p->stream;
+    const GbState h = *p->st_host;
+    const double gub = gb_key_value(h.gub_key);
+    float ms = 0.f;
+    if (R.timed64 && cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) R.t64 += ms, R.n64++;
+    if (R.timed32 && cudaEventElapsedTime(&ms, p->ev[4], p->ev[5]) == cudaSuccess) R.t32 += ms, R.n32++;
+    R.timed64 = R.timed32 = false;
+    if (h.gen > 0 && (long long)R.trace.size() < h.gen) {
+        gb_gen_stat g;
+        g.parents = R.last_par;
+        g.children = h.children;
+        g.kept32 = p->opt.fp32_prefilter ? h.kept32 : h.children;
+        g.kept = h.overflow ? 0 : h.kept;
+        g.pool = h.pool;
+        g.gub = gub;
+        R.trace.push_back(g);
     }
-    // ---- output: boxes with LB <= GUB, GLB -------------------------------------
+    if (h.error) return stop(fail(GB_E_CUDA, "device-side selection error"));
+    if (h.overflow) return stop(fail(GB_E_CAPACITY, "box pool capacity reached"));
+    if (h.active == 0) return stop(GB_OK);
+    if (h.gen >= p->opt.max_generations) return stop(fail(GB_E_LIMIT, "generation limit reached"));
+    const long long l0 = gb_launches_so_far();
+    const int cur = R.cur;
+    const long long count = h.pool;
+    const long long npar = h.active < p->K ? h.active : p->K;
+    const long long nch = npar * p->fan;
+    cudaError_t e = cudaSuccess;
+#define GB_ST(call)                                 \
+    do {                                            \
+        if ((e = (call)) != cudaSuccess) return stop(cuda_fail(e, #call)); \
+    } while (0)
+    GB_ST(gb_launch_select(p->E[cur], count, h.active, p->K, gub, p->tol_f, p->st, p->sc, s));
+    GB_ST(gb_launch_partition(p->E[cur], count, gub, p->tol_f, p->E[1 - cur], p->par, p->pool, p->st, p->sc, s));
+    GB_ST(gb_launch_prep(p->P, p->pool, p->par, npar, p->sp, p->st, s));
+    if (p->opt.fp32_prefilter) {
+        GB_ST(cudaEventRecord(p->ev[4], s));
+        GB_ST(gb_launch_eval32(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, p->st, s));
+        GB_ST(cudaEventRecord(p->ev[5], s));
+        GB_ST(gb_launch_compact_children(p->ch, nch, 0, p->st, p->sc, s));
+        GB_ST(cudaEventRecord(p->ev[2], s));
+        GB_ST(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, true, p->st, s));
+        GB_ST(cudaEventRecord(p->ev[3], s));
+        R.timed32 = true;
+    } else {
+        GB_ST(cudaEventRecord(p->ev[2], s));
+        GB_ST(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, false, p->st, s));
+        GB_ST(cudaEventRecord(p->ev[3], s));
+    }
+    R.timed64 = true;
+    GB_ST(gb_launch_compact_children(p->ch, nch, 1, p->st, p->sc, s));
+    GB_ST(gb_launch_materialize(p->P, p->pool, p->par, p->ch, nch, p->sp, p->E[1 - cur], p->opt.tol_x, p->st, s));
+    GB_ST(gb_launch_finish(p->par, npar, p->pool, p->E[1 - cur], p->st, s));
+    R.cur = 1 - cur;
+    R.last_par = npar;
+    long long bound = count + nch;
+    GB_ST(gb_launch_stats(p->E[R.cur], bound < p->cap ? bound : p->cap, p->tol_f, p->st, s));
+    GB_ST(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
+    GB_ST(cudaEventRecord(p->ev_state, s));
+#undef GB_ST
+    R.launches += gb_launches_so_far() - l0;
+    return 0;
+}
+
+__attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_result* out, bool copy_boxes) {
+    SolveRun& R = p->run;
+    std::memset(out, 0, sizeof(*out));
+    GB_CU(cudaSetDevice(p->device));
+    const long long l0 = gb_launches_so_far();
+    cudaStream_t s = p->stream;
+    GB_CU(cudaStreamSynchronize(s));
     GbState h = *p->st_host;
+    const int cur = R.cur;
     double gub = gb_key_value(h.gub_key);
     unsigned long long ones = ~0ull;
     GB_CU(cudaMemcpyAsync(&p->st->glb_key, &ones, sizeof(ones), cudaMemcpyHostToDevice, s));
@@ -415,10 +481,10 @@ static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
     out->box_evals_fp32 = hf.evals32;
     out->box_evals_fp64 = hf.evals64;
     out->mid_evals = hf.mids;
-    out->eval64_ms = t64;
-    out->eval32_ms = t32;
-    out->eval64_launches = n64;
-    out->eval32_launches = n32;
+    out->eval64_ms = R.t64;
+    out->eval32_ms = R.t32;
+    out->eval64_launches = R.n64;
+    out->eval32_launches = R.n32;
     if (copy_boxes && nbox > 0) {
         size_t nb = (size_t)nbox * p->n;
         double *d_lo = nullptr, *d_hi = nullptr, *d_flo = nullptr;
@@ -446,17 +512,30 @@ static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
         GB_CU(cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
         out->device_ms = ms;
     }
-    out->kernel_launches = gb_launches_so_far() - launches0;
+    R.launches += gb_launches_so_far() - l0;
+    out->kernel_launches = R.launches;
     out->ops64 = (int64_t)hf.ops64;
     out->ops32 = (int64_t)hf.ops32;
-    out->n_trace = (int64_t)trace.size();
-    if (!trace.empty()) {
-        out->trace = (gb_gen_stat*)std::malloc(trace.size() * sizeof(gb_gen_stat));
-        std::memcpy(out->trace, trace.data(), trace.size() * sizeof(gb_gen_stat));
+    out->n_trace = (int64_t)R.trace.size();
+    if (!R.trace.empty()) {
+        out->trace = (gb_gen_stat*)std::malloc(R.trace.size() * sizeof(gb_gen_stat));
+        std::memcpy(out->trace, R.trace.data(), R.trace.size() * sizeof(gb_gen_stat));
     }
-    out->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    out->status = status;
-    return status;
+    out->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - R.t0).count();
+    out->status = R.status;
+    R.active = false;
+    return R.status;
+}
+
+static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
+    if (!p || !out) return fail(GB_E_INVALID, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    gb_status st = solve_begin(p);
+    if (st != GB_OK) return st;
+    while (!solve_advance(p, true)) {
+    }
+    gb_status fin = solve_finish(p, out, copy_boxes);
+    return fin;
 }
 
 gb_status gb_solve(gb_problem* p, gb_result* out) { return solve_impl(p, out, true); }
@@ -485,6 +564,10 @@ gb_status gb_eval_boxes(gb_problem* p, const double* d_lo, const double* d_hi, i
 
 // Read-only view of a problem for the other translation units of the library
 // (not exported from the shared object).
+__attribute__((visibility("hidden"))) size_t gb_internal_device_bytes(const gb_problem* p) {
+    return p ? p->device_bytes : 0;
+}
+
 __attribute__((visibility("hidden"))) const GbProg* gb_internal_prog(const gb_problem* p, int* device, int* n, int* nb) {
     if (!p) return nullptr;
     *device = p->device;

@@ -143,6 +143,31 @@ __global__ void k_select_all(GbState* st) {
     st->sel_need = 0;
 }
 
+// K = 1: the threshold is the smallest active key (the partition then takes
+// the most recently inserted box among those with that key).
+__global__ void k_min_init(GbState* st) {
+    st->sel_T = ~0ull - 1;   // replaced by the minimum below (there is at least one active box)
+    st->sel_below = 0;
+    st->sel_need = 1;
+}
+
+__global__ void k_min_key(GbEntries E, long long count, double gub, double tol_f, GbState* st) {
+    const double thr = thr_of(gub, tol_f);
+    unsigned long long kmin = ~0ull;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x) {
+        double f = E.flo[q];
+        if (!(f < thr) || ((unsigned)E.cyc[q] & GB_FINAL_BIT)) continue;
+        unsigned long long k = gb_order_key(f);
+        kmin = k < kmin ? k : kmin;
+    }
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long other = __shfl_down_sync(0xffffffffu, kmin, o);
+        kmin = other < kmin ? other : kmin;
+    }
+    if ((threadIdx.x & 31) == 0 && kmin != ~0ull) atomicMin(&st->sel_T, kmin);
+}
+
 __global__ void k_radix_hist(GbEntries E, long long count, double gub, double tol_f, int pass,
                              const GbState* st, unsigned* hist) {
     const double thr = thr_of(gub, tol_f);
@@ -158,46 +183,56 @@ __global__ void k_radix_hist(GbEntries E, long long count, double gub, double to
     }
 }
 
-__global__ void k_radix_pick(int pass, GbState* st, unsigned* hist) {
-    __shared__ long long part[1025];
-    __shared__ int found;
-    const int t = threadIdx.x;    // 1024 threads x 64 bins
+// One block of 1024 threads (32 warps, each owning 2048 consecutive bins):
+// coalesced warp totals, a scan over the 32 totals, then the owning warp
+// walks its chunk 32 bins at a time.  Clears the histogram for the next pass.
+__global__ void __launch_bounds__(1024) k_radix_pick(int pass, GbState* st, unsigned* hist) {
+    __shared__ long long wtot[32];
+    __shared__ long long wpre[33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned* h = hist + w * 2048;
     long long s = 0;
-    for (int b = 0; b < 64; b++) s += hist[t * 64 + b];
-    part[t] = s;
-    if (t == 0) found = -1;
+    for (int k = 0; k < 64; k++) s += h[k * 32 + lane];
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) wtot[w] = s;
     __syncthreads();
-    if (t == 0) {
+    if (threadIdx.x == 0) {
         long long acc = 0;
-        for (int i = 0; i < 1024; i++) {
-            long long c = part[i];
-            part[i] = acc;
-            acc += c;
+        for (int i = 0; i < 32; i++) {
+            wpre[i] = acc;
+            acc += wtot[i];
         }
-        part[1024] = acc;
+        wpre[32] = acc;
     }
     __syncthreads();
     const long long rank = st->radix_rank;
-    if (part[t] < rank && rank <= part[t] + s) {
-        long long acc = part[t];
-        for (int b = 0; b < 64; b++) {
-            long long c = hist[t * 64 + b];
-            if (acc < rank && rank <= acc + c) {
-                st->radix_prefix = (st->radix_prefix << 16) | (unsigned long long)(t * 64 + b);
-                st->radix_rank = rank - acc;
-                st->sel_below += acc;
-                found = 1;
-                break;
+    if (wpre[w] < rank && rank <= wpre[w] + wtot[w]) {
+        long long acc = wpre[w];
+        for (int k = 0; k < 64; k++) {
+            long long c = h[k * 32 + lane];
+            long long inc = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                long long v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
             }
-            acc += c;
+            long long before = acc + inc - c;   // bins before this lane's bin
+            bool hit = before < rank && rank <= before + c;
+            unsigned b = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                st->radix_prefix = (st->radix_prefix << 16) | (unsigned long long)(w * 2048 + k * 32 + lane);
+                st->radix_rank = rank - before;
+                st->sel_below += before;
+            }
+            if (b) break;
+            acc += __shfl_sync(0xffffffffu, inc, 31);
         }
     }
     __syncthreads();
-    for (int b = 0; b < 64; b++) hist[t * 64 + b] = 0;
-    if (t == 0 && pass == 3) {
+    for (int k = 0; k < 64; k++) hist[w * 2048 + k * 32 + lane] = 0;
+    if (threadIdx.x == 0 && pass == 3) {
         st->sel_T = st->radix_prefix;
         st->sel_need = st->radix_rank;
-        if (found < 0) st->error |= 1;
+        if (wpre[32] < rank) st->error |= 1;
     }
 }
 
@@ -454,23 +489,27 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
 __global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents par, GbChildren ch,
                                                 long long nchildren, GbSplit sp, double gub_prev,
                                                 int from_list, GbState* st) {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long lim = from_list ? st->n32 : nchildren;
-    unsigned long long key = ~0ull;
-    bool has = false;
-    bool valid = false;
-    int ops = 0;
-    if (idx < lim) {
-        long long ci = from_list ? (long long)ch.list32[idx] : idx;
-        valid = eval64_child(P, pool, par, ch, ci, sp, gub_prev, &key, &has, ops);
-    }
-    warp_min_gub(key, has, st);
-    warp_add_ops(ops, &st->ops64);
-    unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
-    if ((threadIdx.x & 31) == 0 && nv) {
-        atomicAdd((unsigned long long*)&st->evals64, (unsigned long long)nv);
-        atomicAdd((unsigned long long*)&st->mids, (unsigned long long)nv);
-        if (!from_list) atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+    const long long lim = from_list ? st->n32 : nchildren;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // warp-uniform loop: every lane of a warp runs the same iterations
+    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < lim; base += stride) {
+        long long idx = base + (threadIdx.x & 31);
+        unsigned long long key = ~0ull;
+        bool has = false;
+        bool valid = false;
+        int ops = 0;
+        if (idx < lim) {
+            long long ci = from_list ? (long long)ch.list32[idx] : idx;
+            valid = eval64_child(P, pool, par, ch, ci, sp, gub_prev, &key, &has, ops);
+        }
+        warp_min_gub(key, has, st);
+        warp_add_ops(ops, &st->ops64);
+        unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
+        if ((threadIdx.x & 31) == 0 && nv) {
+            atomicAdd((unsigned long long*)&st->evals64, (unsigned long long)nv);
+            atomicAdd((unsigned long long*)&st->mids, (unsigned long long)nv);
+            if (!from_list) atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+        }
     }
 }
 
@@ -549,12 +588,9 @@ __global__ void k_cc_scatter(GbChildren ch, long long n, int mode, const GbState
 // ---------------------------------------------------------------------------
 // Survivors into free slots: coordinates, FP32 shadow, group caches (dirty
 // groups recomputed, the rest copied from the parent), pool entry.
-__global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbParents par, GbChildren ch,
-                                                     GbSplit sp, GbEntries En, double tol_x, GbState* st) {
-    const int lane = threadIdx.x & 31;
-    const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    if (st->overflow) return;
-    if (s >= st->kept) return;
+__device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                                const GbChildren& ch, const GbSplit& sp, const GbEntries& En,
+                                                double tol_x, const GbState* st, long long s, int lane) {
     const long long nfree = st->nfree, bump = st->bump, kept_old = st->kept_old;
     const long long ci = ch.surv[s];
     ChildCtx c = child_ctx(par, ci, sp);
@@ -610,6 +646,16 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
         En.slot[e] = ns;
         En.cyc[e] = (int)((unsigned)c.info.w | (narrow ? GB_FINAL_BIT : 0u));
     }
+}
+
+__global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbParents par, GbChildren ch,
+                                                     GbSplit sp, GbEntries En, double tol_x, GbState* st) {
+    const int lane = threadIdx.x & 31;
+    if (st->overflow) return;
+    const long long kept = st->kept;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < kept; s += nwarps)
+        materialize_one(P, pool, par, ch, sp, En, tol_x, st, s, lane);
 }
 
 // Parents' slots back to the free list, or (on overflow) the parents back
@@ -797,6 +843,15 @@ cudaError_t gb_launch_select(const GbEntries& E, long long count, long long acti
         k_select_all<<<1, 1, 0, s>>>(st);
         return cudaGetLastError();
     }
+    if (K == 1) {
+        unsigned g1 = grid_for(count, 256);
+        if (g1 > 152 * 8) g1 = 152 * 8;
+        gb_launch_count++;
+        k_min_init<<<1, 1, 0, s>>>(st);
+        gb_launch_count++;
+        k_min_key<<<g1, 256, 0, s>>>(E, count, gub, tol_f, st);
+        return cudaGetLastError();
+    }
     gb_launch_count++;
     k_radix_init<<<1, 1, 0, s>>>(st, K);
     unsigned g = grid_for(count, 256);
@@ -836,8 +891,9 @@ cudaError_t gb_launch_eval64(const GbProg& P, const GbPool& pool, const GbParent
                              long long nchildren, const GbSplit& sp, double gub_prev, bool from_list,
                              GbState* st, cudaStream_t s) {
     gb_launch_count++;
-    k_eval64<<<grid_for(nchildren, 128), 128, 0, s>>>(P, pool, par, ch, nchildren, sp, gub_prev,
-                                                      from_list ? 1 : 0, st);
+    unsigned g = grid_for(nchildren, 128);
+    if (from_list && g > 152 * 16) g = 152 * 16;
+    k_eval64<<<g, 128, 0, s>>>(P, pool, par, ch, nchildren, sp, gub_prev, from_list ? 1 : 0, st);
     return cudaGetLastError();
 }
 
@@ -867,7 +923,9 @@ cudaError_t gb_launch_materialize(const GbProg& P, const GbPool& pool, const GbP
                                   const GbChildren& ch, long long nchildren, const GbSplit& sp,
                                   const GbEntries& E_new, double tol_x, GbState* st, cudaStream_t s) {
     gb_launch_count++;
-    k_materialize<<<grid_for(nchildren * 32, 128), 128, 0, s>>>(P, pool, par, ch, sp, E_new, tol_x, st);
+    unsigned g = grid_for(nchildren * 32, 128);
+    if (g > 152 * 16) g = 152 * 16;
+    k_materialize<<<g, 128, 0, s>>>(P, pool, par, ch, sp, E_new, tol_x, st);
     return cudaGetLastError();
 }
 

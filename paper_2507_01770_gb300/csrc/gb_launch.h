@@ -97,3 +97,8 @@ cudaError_t gb_launch_peak(int which, int iters, int blocks, void* sink, cudaStr
 long long gb_launches_so_far();
 extern "C" const GbProg* gb_internal_prog(const gb_problem* p, int* device, int* n, int* nb);
 extern "C" gb_status gb_internal_fail(gb_status s, const char* msg);
+// resumable solve (gb_api.cu), used by the serving loop (gb_server.cpp)
+extern "C" gb_status solve_begin(gb_problem* p);
+extern "C" int solve_advance(gb_problem* p, bool block);
+extern "C" gb_status solve_finish(gb_problem* p, gb_result* out, bool copy_boxes);
+extern "C" size_t gb_internal_device_bytes(const gb_problem* p);
