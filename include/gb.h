@@ -91,7 +91,8 @@ typedef struct gb_options {
     int64_t max_boxes;        /* pool capacity in boxes (0: from pool_bytes) */
     size_t pool_bytes;        /* device memory budget for the pool (0: 16 GiB) */
     int32_t device;           /* CUDA device ordinal */
-    int32_t pad;
+    int32_t eval_mode;        /* child evaluation: 0 auto (term tables when m^d >= 16 and they fit),
+                                 1 bytecode interpreter, 2 term tables when they fit; results are identical */
 } gb_options;
 
 /* Fills *opt with the defaults documented above. */

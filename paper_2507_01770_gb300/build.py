@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgb.so")
-SOURCES = ["gb_kernels.cu", "gb_api.cu", "gb_compile.cpp", "gb_noalloc.cu", "gb_server.cpp"]
-HEADERS = ["gb_internal.h", "gb_interval.cuh", "gb_eval.cuh", "gb_launch.h"]
+SOURCES = ["gb_kernels.cu", "gb_kernels_tab.cu", "gb_api.cu", "gb_compile.cpp", "gb_noalloc.cu", "gb_server.cpp"]
+HEADERS = ["gb_internal.h", "gb_interval.cuh", "gb_eval.cuh", "gb_launch.h", "gb_child.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fno-fast-math"]

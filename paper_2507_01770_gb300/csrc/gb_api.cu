@@ -101,6 +101,8 @@ struct gb_problem {
     GbChildren ch{};
     GbScan sc{};
     GbSplit sp{};
+    GbTabs tabs{};
+    bool use_tabs = false;
     GbState* st = nullptr;         // device
     GbState* st_host = nullptr;    // pinned host
     unsigned* out_list = nullptr;
@@ -316,6 +318,50 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         (e = alloc(&p->ch.flag32, C, A)) || (e = alloc(&p->ch.list32, C, A)) ||
         (e = alloc(&p->ch.surv, C, A)))
         return bad(e, "allocate child buffers");
+    // per-parent term tables
+    if (opt.eval_mode != 1) {
+        gb_build_tables(&p->hp, m, d);
+        const bool want = opt.eval_mode == 2 || p->fan >= 16;
+        if (p->hp.tab_ok && want) {
+            const GbHostProg& Hh = p->hp;
+            int32_t* d_spc;
+            GbSplitPos* d_sps;
+            GbDTerm* d_dt;
+            int2* d_jk;
+            GbContrib* d_cb;
+            if ((e = upload(&d_spc, Hh.sp_of_cyc.data(), Hh.sp_of_cyc.size(), A)) ||
+                (e = upload(&d_sps, Hh.sps.data(), Hh.sps.size(), A)) ||
+                (e = upload(&d_dt, Hh.dterms.data(), Hh.dterms.size(), A)) ||
+                (e = upload(&d_jk, Hh.jk.data(), Hh.jk.size(), A)) ||
+                (e = upload(&d_cb, Hh.contribs.data(), Hh.contribs.size(), A)))
+                return bad(e, "upload table layouts");
+            P.tab_ok = 1;
+            P.m = Hh.m;
+            P.mshift = Hh.mshift;
+            P.max_rows = Hh.max_rows;
+            P.max_leaves = Hh.max_leaves > 0 ? Hh.max_leaves : 1;
+            P.tree_nodes = Hh.tree_nodes > 0 ? Hh.tree_nodes : 1;
+            P.max_dterm = Hh.max_dterm;
+            P.sp_of_cyc = d_spc;
+            P.sps = d_sps;
+            P.dterms = d_dt;
+            P.jk = d_jk;
+            P.contribs = d_cb;
+            GbTabs& T = p->tabs;
+            T.max_rows = P.max_rows > 0 ? P.max_rows : 1;
+            T.max_leaves = P.max_leaves;
+            T.tree_nodes = P.tree_nodes;
+            const size_t rows = K * (size_t)T.max_rows, nodes = K * (size_t)T.tree_nodes;
+            if ((e = alloc(&T.tv64, rows, A)) || (e = alloc(&T.tm64, rows, A)) ||
+                (e = alloc(&T.tl64, rows * T.max_leaves, A)) || (e = alloc(&T.nf64, nodes, A)) ||
+                (e = alloc(&T.nm64, nodes, A)))
+                return bad(e, "allocate term tables");
+            if (fp32 && ((e = alloc(&T.tv32, rows, A)) || (e = alloc(&T.tl32, rows * T.max_leaves, A)) ||
+                         (e = alloc(&T.nf32, nodes, A))))
+                return bad(e, "allocate term tables");
+            p->use_tabs = true;
+        }
+    }
     long long items = cap > p->Cmax ? cap : p->Cmax;
     p->sc.max_tiles = (int)((items + GB_TILE - 1) / GB_TILE) + 1;
     if ((e = alloc(&p->sc.tile_cnt, (size_t)3 * p->sc.max_tiles, A)) ||
@@ -363,7 +409,7 @@ __attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
     R = SolveRun{};
     R.t0 = std::chrono::steady_clock::now();
     GB_CU(cudaSetDevice(p->device));
-    const long long l0 = gb_launches_so_far();
+    const long long l0 = (gb_launches_so_far() + gb_tab_launches_so_far());
     cudaStream_t s = p->stream;
     GbState init{};
     init.cap = p->cap;
@@ -373,7 +419,7 @@ __attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
     GB_CU(gb_launch_stats(p->E[0], 1, p->tol_f, p->st, s));
     GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
     GB_CU(cudaEventRecord(p->ev_state, s));
-    R.launches += gb_launches_so_far() - l0;
+    R.launches += (gb_launches_so_far() + gb_tab_launches_so_far()) - l0;
     R.active = true;
     return GB_OK;
 }
@@ -414,7 +460,7 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
     if (h.overflow) return stop(fail(GB_E_CAPACITY, "box pool capacity reached"));
     if (h.active == 0) return stop(GB_OK);
     if (h.gen >= p->opt.max_generations) return stop(fail(GB_E_LIMIT, "generation limit reached"));
-    const long long l0 = gb_launches_so_far();
+    const long long l0 = (gb_launches_so_far() + gb_tab_launches_so_far());
     const int cur = R.cur;
     const long long count = h.pool;
     const long long npar = h.active < p->K ? h.active : p->K;
@@ -427,18 +473,23 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
     GB_ST(gb_launch_select(p->E[cur], count, h.active, p->K, gub, p->tol_f, p->st, p->sc, s));
     GB_ST(gb_launch_partition(p->E[cur], count, gub, p->tol_f, p->E[1 - cur], p->par, p->pool, p->st, p->sc, s));
     GB_ST(gb_launch_prep(p->P, p->pool, p->par, npar, p->sp, p->st, s));
+    const bool tab = p->use_tabs;
+    if (tab) GB_ST(gb_launch_ptab(p->P, p->pool, p->par, p->tabs, npar, p->sp, s));
     if (p->opt.fp32_prefilter) {
         GB_ST(cudaEventRecord(p->ev[4], s));
-        GB_ST(gb_launch_eval32(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, p->st, s));
+        if (tab) GB_ST(gb_launch_eval32_tab(p->P, p->pool, p->par, p->tabs, p->ch, nch, p->sp, gub, p->st, s));
+        else GB_ST(gb_launch_eval32(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, p->st, s));
         GB_ST(cudaEventRecord(p->ev[5], s));
         GB_ST(gb_launch_compact_children(p->ch, nch, 0, p->st, p->sc, s));
         GB_ST(cudaEventRecord(p->ev[2], s));
-        GB_ST(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, true, p->st, s));
+        if (tab) GB_ST(gb_launch_eval64_tab(p->P, p->pool, p->par, p->tabs, p->ch, nch, p->sp, gub, true, p->st, s));
+        else GB_ST(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, true, p->st, s));
         GB_ST(cudaEventRecord(p->ev[3], s));
         R.timed32 = true;
     } else {
         GB_ST(cudaEventRecord(p->ev[2], s));
-        GB_ST(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, false, p->st, s));
+        if (tab) GB_ST(gb_launch_eval64_tab(p->P, p->pool, p->par, p->tabs, p->ch, nch, p->sp, gub, false, p->st, s));
+        else GB_ST(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, false, p->st, s));
         GB_ST(cudaEventRecord(p->ev[3], s));
     }
     R.timed64 = true;
@@ -452,7 +503,7 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
     GB_ST(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
     GB_ST(cudaEventRecord(p->ev_state, s));
 #undef GB_ST
-    R.launches += gb_launches_so_far() - l0;
+    R.launches += (gb_launches_so_far() + gb_tab_launches_so_far()) - l0;
     return 0;
 }
 
@@ -460,7 +511,7 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
     SolveRun& R = p->run;
     std::memset(out, 0, sizeof(*out));
     GB_CU(cudaSetDevice(p->device));
-    const long long l0 = gb_launches_so_far();
+    const long long l0 = (gb_launches_so_far() + gb_tab_launches_so_far());
     cudaStream_t s = p->stream;
     GB_CU(cudaStreamSynchronize(s));
     GbState h = *p->st_host;
@@ -512,7 +563,7 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
         GB_CU(cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
         out->device_ms = ms;
     }
-    R.launches += gb_launches_so_far() - l0;
+    R.launches += (gb_launches_so_far() + gb_tab_launches_so_far()) - l0;
     out->kernel_launches = R.launches;
     out->ops64 = (int64_t)hf.ops64;
     out->ops32 = (int64_t)hf.ops32;

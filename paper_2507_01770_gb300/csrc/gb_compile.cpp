@@ -297,3 +297,100 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
     P->ops_mid = tot_mid / P->nb;
     return "";
 }
+
+// Per-split-position layouts of the per-parent term tables (see GbSplitPos).
+void gb_build_tables(GbHostProg* P, int m, int d) {
+    P->tab_ok = 0;
+    P->m = m;
+    P->mshift = m == 2 ? 1 : 2;
+    P->sp_of_cyc.assign(P->n, -1);
+    P->sps.clear();
+    P->dterms.clear();
+    P->jk.clear();
+    P->contribs.clear();
+    P->max_rows = P->max_dterm = 0;
+    const int n = P->n, B = P->B, ns = (int)P->sums.size();
+    int node = 0, max_leaves = 0;
+    for (GbSum& S : P->sums) {
+        S.node0 = node;
+        int cnt = 0;
+        for (int mL = S.ngroups; mL > 0; mL = (mL + 1) / 2) {
+            cnt += mL;
+            if (mL == 1) break;
+        }
+        S.nnodes = cnt;
+        node += cnt;
+        max_leaves = std::max(max_leaves, S.nvar_leaves);
+    }
+    P->tree_nodes = node;
+    P->max_leaves = max_leaves;
+    for (int b = 0; b < P->nb; b++) {
+        const int bs = b * B, be = std::min(n, bs + B);
+        for (int c = bs; c < be; c += d) {
+            const int dd = std::min(d, be - c);
+            GbSplitPos sp{};
+            sp.c0 = c;
+            sp.dd = dd;
+            sp.block = b;
+            sp.dterm0 = (int)P->dterms.size();
+            sp.jk0 = (int)P->jk.size();
+            int rows = 0;
+            for (int k = 0; k < ns; k++) {
+                const GbSum& S = P->sums[k];
+                int2 dr = P->dirty[(size_t)b * ns + k];
+                if (dr.y - dr.x > GB_TAB_MAX_DIRTY) return;
+                for (int g = dr.x; g < dr.y; g++) {
+                    const GbGroup& G = P->groups[S.group0 + g];
+                    for (int t = G.t0; t < G.t0 + G.count; t++) {
+                        const int i = S.first + t * S.step;
+                        int w = 0, a = 0;
+                        if (S.has_var) {
+                            a = std::max(i + S.off_min, c);
+                            const int z = std::min(i + S.off_max, c + dd - 1);
+                            w = a <= z ? z - a + 1 : 0;
+                        }
+                        GbDTerm D{};
+                        D.sum = (int16_t)k;
+                        D.w = (int16_t)w;
+                        D.dshift = (int16_t)(w ? (a - c) * P->mshift : 0);
+                        D.group = (int16_t)g;
+                        D.term = t;
+                        D.row = rows;
+                        rows += 1 << (w * P->mshift);
+                        P->dterms.push_back(D);
+                    }
+                }
+            }
+            sp.ndterm = (int)P->dterms.size() - sp.dterm0;
+            sp.tab_entries = rows;
+            if (rows > GB_TAB_MAX_ROWS) return;
+            P->max_rows = std::max(P->max_rows, rows);
+            P->max_dterm = std::max(P->max_dterm, sp.ndterm);
+            // gradient contributions of every block coordinate, per sum, in
+            // ascending term and ascending leaf order
+            for (int j = bs; j < be; j++) {
+                for (int k = 0; k < ns; k++) {
+                    const GbSum& S = P->sums[k];
+                    const int start = (int)P->contribs.size();
+                    if (S.has_var) {
+                        for (int q = 0; q < sp.ndterm; q++) {
+                            const GbDTerm& D = P->dterms[sp.dterm0 + q];
+                            if (D.sum != k) continue;
+                            const int i = S.first + D.term * S.step;
+                            int leaf = 0;
+                            for (int t = S.ins0; t < S.ins0 + S.nins; t++) {
+                                if (P->tins[t].op != D_IVAR) continue;
+                                if (i + P->tins[t].aux == j) P->contribs.push_back(GbContrib{q, leaf});
+                                leaf++;
+                            }
+                        }
+                    }
+                    P->jk.push_back(int2{start, (int)P->contribs.size()});
+                }
+            }
+            P->sp_of_cyc[c] = (int)P->sps.size();
+            P->sps.push_back(sp);
+        }
+    }
+    P->tab_ok = 1;
+}

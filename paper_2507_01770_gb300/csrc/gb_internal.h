@@ -19,6 +19,8 @@
 #define GB_MAX_ISUM 6     // ISUM nodes per objective
 #define GB_MAX_WIN 4      // IDX_VAR offset span + 1 per template
 #define GB_MAX_SPLIT_D 20   // coordinates split per generation
+#define GB_TAB_MAX_DIRTY 8  // dirty groups per sum for the table path
+#define GB_TAB_MAX_ROWS 4096 // table rows per parent for the table path
 #define GB_MAX_FAN_LOG2 20  // children per parent (m^d) at most 2^20
 
 // Device opcodes of one instruction (registers are node slots).
@@ -49,12 +51,36 @@ struct GbSum {
     int32_t group0, ngroups; // global group ids [group0, group0 + ngroups)
     int32_t outer_reg;       // outer register receiving the sum
     int32_t nvar_leaves;     // IVAR instructions in the template
+    int32_t node0;           // first node of its group tree in a parent's node array
+    int32_t nnodes;          // nodes of the group tree (all levels)
 };
 
 struct GbGroup {
     int32_t t0, count;       // term ordinals [t0, t0 + count) of its ISUM
     int32_t bmin, bmax;      // touched blocks (-1, -1 if the template has no IVAR)
 };
+
+// ---- per-parent term tables ------------------------------------------------
+// A child of a box differs from it only in the pieces of the split
+// coordinates [c0, c0 + dd).  A term that touches w of them takes at most
+// m^w values over all the children, so per parent the value, the midpoint
+// value and the leaf adjoints of every dirty term are tabulated once per
+// digit combination, and a child assembles its sums from the tables.
+// Layouts depend only on the split position (c0, dd), fixed at creation.
+struct GbSplitPos {
+    int32_t c0, dd, block;
+    int32_t dterm0, ndterm;   // dirty terms [dterm0, dterm0 + ndterm)
+    int32_t tab_entries;      // combinations over all dirty terms (table rows)
+    int32_t jk0;              // (coordinate of the block, sum) ranges start
+    int32_t pad;
+};
+struct GbDTerm {
+    int16_t sum, w;           // sum index, number of split coordinates touched
+    int16_t dshift, group;    // bit shift of its first digit in the child index, local group
+    int32_t term;             // term ordinal within the sum
+    int32_t row;              // first table row of the term (m^w rows)
+};
+struct GbContrib { int32_t dterm, leaf; };   // a leaf adjoint feeding one coordinate
 
 // Outer VAR leaf: register and coordinate (for the gradient).
 struct GbVarLeaf { int32_t reg, coord; };
@@ -75,6 +101,13 @@ struct GbProg {
     const float2* const* tab32;      // [n_tables] outward float pairs (lo, hi)
     const double* l;                 // [n]
     const double* u;                 // [n]
+    // per-parent term tables (null when not built)
+    int32_t tab_ok, m, mshift, max_rows, max_leaves, tree_nodes, max_dterm;
+    const int32_t* sp_of_cyc;        // [n] split position of a cycling position (-1: unreachable)
+    const GbSplitPos* sps;
+    const GbDTerm* dterms;
+    const int2* jk;                  // [(c1 - c0) * n_sum] per split position: contribution ranges
+    const GbContrib* contribs;
 };
 
 // Host-side compiled program (arrays in host memory before upload).
@@ -90,7 +123,17 @@ struct GbHostProg {
     std::vector<int2> dirty;
     std::vector<GbVarLeaf> var_leaves;
     int64_t ops_eval = 0, ops_mid = 0;   // static directed-op counts (see gb_compile.cpp)
+    // per-parent term tables
+    int32_t tab_ok = 0, m = 2, mshift = 1, max_rows = 0, max_leaves = 0, tree_nodes = 0, max_dterm = 0;
+    std::vector<int32_t> sp_of_cyc;
+    std::vector<GbSplitPos> sps;
+    std::vector<GbDTerm> dterms;
+    std::vector<int2> jk;
+    std::vector<GbContrib> contribs;
 };
+// Builds the per-split-position table layouts for pieces m and split width d;
+// leaves tab_ok = 0 when a layout exceeds the table limits.
+void gb_build_tables(GbHostProg* P, int m, int d);
 // Compiles and validates a DAG; returns an empty string or an error message.
 std::string gb_compile(const gb_node* nodes, int32_t nn, int32_t root, const int64_t* tlen,
                        int32_t ntab, int32_t n, int32_t B, GbHostProg* out);

@@ -1,0 +1,376 @@
+// Child evaluation from per-parent term tables.
+//
+// The paper computes each child's bounds from its parent and its index
+// (Eqs. 7-11, the SPSD style of section 3.2).  Carried one step further: a
+// term that touches w of the split coordinates takes at most m^w values over
+// all children of a parent, so k_ptab tabulates, once per parent, the value,
+// the midpoint value and the leaf adjoints of every dirty term for each digit
+// combination, together with the group-sum trees of the parent's cached sums.
+// A child then reads its terms from the tables, rebuilds only the path of the
+// group tree above its dirty groups, and runs the outer expression and the
+// first-order test.  Every value is computed by the same operations in the
+// same order as the interpreter kernels, so the results are bit-identical.
+#include <cuda_runtime.h>
+
+#include "gb_child.cuh"
+
+using namespace gb;
+
+namespace {
+
+thread_local long long g_tab_launches = 0;
+
+template <typename T> struct TabPrec;
+template <> struct TabPrec<double> {
+    typedef iv64 I;
+    static __device__ __forceinline__ I tv(const GbTabs& T, size_t i) { double2 v = T.tv64[i]; return I{v.x, v.y}; }
+    static __device__ __forceinline__ I tl(const GbTabs& T, size_t i) { double2 v = T.tl64[i]; return I{v.x, v.y}; }
+    static __device__ __forceinline__ I node(const GbTabs& T, size_t i) { double2 v = T.nf64[i]; return I{v.x, v.y}; }
+};
+template <> struct TabPrec<float> {
+    typedef iv32 I;
+    static __device__ __forceinline__ I tv(const GbTabs& T, size_t i) { float2 v = T.tv32[i]; return I{v.x, v.y}; }
+    static __device__ __forceinline__ I tl(const GbTabs& T, size_t i) { float2 v = T.tl32[i]; return I{v.x, v.y}; }
+    static __device__ __forceinline__ I node(const GbTabs& T, size_t i) { float2 v = T.nf32[i]; return I{v.x, v.y}; }
+};
+
+__device__ __forceinline__ iv64 mid_tv(const GbTabs& T, size_t i) { double2 v = T.tm64[i]; return iv64{v.x, v.y}; }
+__device__ __forceinline__ iv64 mid_node(const GbTabs& T, size_t i) { double2 v = T.nm64[i]; return iv64{v.x, v.y}; }
+
+// ---------------------------------------------------------------------------
+// k_ptab: one block per parent.  Rows: (dirty term, digit combination).
+__global__ void __launch_bounds__(128) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp) {
+    const long long p = blockIdx.x;
+    const int4 info = par.info[p];
+    const unsigned slot = par.slot[p];
+    const GbSplitPos SP = P.sps[P.sp_of_cyc[info.x]];
+    const size_t o = (size_t)p * sp.dmax * (sp.m + 1);
+    const double* b64 = par.bnd + o;
+    iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS];
+    iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS];
+    int ops = 0;
+    for (int row = threadIdx.x; row < SP.tab_entries; row += blockDim.x) {
+        // the dirty term owning this row (rows are contiguous per term)
+        int lo = 0, hi = SP.ndterm - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (P.dterms[SP.dterm0 + mid].row <= row) lo = mid; else hi = mid - 1;
+        }
+        const GbDTerm D = P.dterms[SP.dterm0 + lo];
+        const unsigned combo = (unsigned)(row - D.row);
+        const unsigned r = combo << D.dshift;   // a child index with these digits
+        const GbSum S = P.sums[D.sum];
+        const int i = S.first + D.term * S.step;
+        View<double> X{pool.lo64 + (size_t)slot * pool.n, pool.hi64 + (size_t)slot * pool.n, b64, b64,
+                       info.x, info.y, sp.mshift, sp.m + 1, r};
+        MidView MX{X};
+        const size_t orow = (size_t)p * T.max_rows + row;
+        iv64 v = term_fwd<double>(P, S, i, X, R, ops);
+        T.tv64[orow] = make_double2(v.lo, v.hi);
+        iv64 vm = term_fwd<double>(P, S, i, MX, R, ops);
+        T.tm64[orow] = make_double2(vm.lo, vm.hi);
+        term_fwd<double>(P, S, i, X, R, ops);
+        for (int t = 0; t < S.nins; t++) RA[t] = iv64{0.0, 0.0};
+        RA[S.nins - 1] = iv64{1.0, 1.0};
+        reverse_sweep<double>(P.tins + S.ins0, S.nins, R, RA, ops);
+        int leaf = 0;
+        for (int t = 0; t < S.nins; t++) {
+            if (P.tins[S.ins0 + t].op != D_IVAR) continue;
+            T.tl64[orow * T.max_leaves + leaf] = make_double2(RA[t].lo, RA[t].hi);
+            leaf++;
+        }
+        if (pool.fp32) {
+            View<float> X32{pool.lo32 + (size_t)slot * pool.n, pool.hi32 + (size_t)slot * pool.n,
+                            par.bnd_rd + o, par.bnd_ru + o, info.x, info.y, sp.mshift, sp.m + 1, r};
+            iv32 f = term_fwd<float>(P, S, i, X32, R32, ops);
+            T.tv32[orow] = make_float2(f.lo, f.hi);
+            for (int t = 0; t < S.nins; t++) RA32[t] = iv32{0.f, 0.f};
+            RA32[S.nins - 1] = iv32{1.f, 1.f};
+            reverse_sweep<float>(P.tins + S.ins0, S.nins, R32, RA32, ops);
+            leaf = 0;
+            for (int t = 0; t < S.nins; t++) {
+                if (P.tins[S.ins0 + t].op != D_IVAR) continue;
+                T.tl32[orow * T.max_leaves + leaf] = make_float2(RA32[t].lo, RA32[t].hi);
+                leaf++;
+            }
+        }
+    }
+    // group trees of the parent's cached sums (level-major, pairwise)
+    const int kinds = pool.fp32 ? 3 : 2;
+    for (int job = threadIdx.x; job < P.n_sum * kinds; job += blockDim.x) {
+        const int k = job % P.n_sum, kind = job / P.n_sum;
+        const GbSum S = P.sums[k];
+        const size_t nb = (size_t)p * T.tree_nodes + S.node0;
+        const size_t cb = (size_t)slot * pool.NG + S.group0;
+        for (int g = 0; g < S.ngroups; g++) {
+            if (kind == 0) T.nf64[nb + g] = pool.gsum[cb + g];
+            else if (kind == 1) T.nm64[nb + g] = pool.gmid[cb + g];
+            else T.nf32[nb + g] = pool.gsum32[cb + g];
+        }
+        int off = 0;
+        for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
+            const int mN = (mL + 1) / 2;
+            for (int q = 0; q < mN; q++) {
+                const size_t a = nb + off + 2 * q, c = nb + off + mL + q;
+                if (kind == 2) {
+                    float2 x = T.nf32[a];
+                    iv32 v{x.x, x.y};
+                    if (2 * q + 1 < mL) {
+                        float2 y = T.nf32[a + 1];
+                        v = iadd(v, iv32{y.x, y.y});
+                    }
+                    T.nf32[c] = make_float2(v.lo, v.hi);
+                } else {
+                    double2* arr = kind == 0 ? T.nf64 : T.nm64;
+                    double2 x = arr[a];
+                    iv64 v{x.x, x.y};
+                    if (2 * q + 1 < mL) {
+                        double2 y = arr[a + 1];
+                        v = iadd(v, iv64{y.x, y.y});
+                    }
+                    arr[c] = make_double2(v.lo, v.hi);
+                }
+            }
+            off += mL;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sum k of a child: dirty group leaves from the tables, then the path of the
+// pairwise tree above them with the parent's nodes for the clean siblings.
+template <typename T, bool MID>
+__device__ __forceinline__ typename TabPrec<T>::I tab_sum(const GbProg& P, const GbTabs& Tb, long long p,
+                                                          const GbSplitPos& SP, int k, int blk, unsigned r,
+                                                          int& dt, int& ops) {
+    typedef typename TabPrec<T>::I I;
+    const GbSum S = P.sums[k];
+    const int2 dr = P.dirty[blk * P.n_sum + k];
+    const size_t rowbase = (size_t)p * Tb.max_rows;
+    const size_t nb = (size_t)p * Tb.tree_nodes + S.node0;
+    I cur[GB_TAB_MAX_DIRTY], tmp[GB_TAB_MAX_DIRTY];
+    for (int g = dr.x; g < dr.y; g++) {
+        Tree<I> tr;
+        tr.init();
+        int cnt = 0;
+        while (dt < SP.dterm0 + SP.ndterm) {
+            const GbDTerm D = P.dterms[dt];
+            if (D.sum != k || D.group != g) break;
+            const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
+            I v;
+            if (MID) {
+                iv64 m = mid_tv(Tb, rowbase + D.row + combo);
+                v.lo = m.lo;
+                v.hi = m.hi;
+            } else {
+                v = TabPrec<T>::tv(Tb, rowbase + D.row + combo);
+            }
+            tr.push(v);
+            cnt++;
+            dt++;
+        }
+        ops += 2 * (cnt > 0 ? cnt - 1 : 0);
+        cur[g - dr.x] = tr.result();
+    }
+    if (S.ngroups == 0) {
+        I z;
+        z.lo = 0;
+        z.hi = 0;
+        return z;
+    }
+    int lo = dr.x, hi = dr.y, off = 0;
+    auto node = [&](size_t i) -> I {
+        if (MID) {
+            iv64 m = mid_node(Tb, nb + i);
+            I v;
+            v.lo = m.lo;
+            v.hi = m.hi;
+            return v;
+        }
+        return TabPrec<T>::node(Tb, nb + i);
+    };
+    if (lo >= hi) return node(S.nnodes - 1);   // no dirty group: the parent's root
+    for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
+        const int nlo = lo >> 1, nhi = ((hi - 1) >> 1) + 1;
+        for (int q = nlo; q < nhi; q++) {
+            const int a = 2 * q;
+            I left = (a >= lo && a < hi) ? cur[a - lo] : node(off + a);
+            I v = left;
+            if (a + 1 < mL) {
+                I right = (a + 1 >= lo && a + 1 < hi) ? cur[a + 1 - lo] : node(off + a + 1);
+                v = iadd(left, right);
+                ops += 2;
+            }
+            tmp[q - nlo] = v;
+        }
+        for (int q = 0; q < nhi - nlo; q++) cur[q] = tmp[q];
+        lo = nlo;
+        hi = nhi;
+        off += mL;
+    }
+    return cur[0];
+}
+
+// First-order test from the tables (same accumulation order as block_mono).
+template <typename T>
+__device__ __forceinline__ bool tab_mono(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
+                                         int blk, unsigned r, const View<double>& X64,
+                                         const typename TabPrec<T>::I* O, typename TabPrec<T>::I* OA, int& ops) {
+    typedef typename TabPrec<T>::I I;
+    for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
+    OA[P.outer_root] = mk<T>((T)1, (T)1);
+    reverse_sweep<T>(P.outer, P.n_outer, O, OA, ops);
+    const int c0 = blk * P.B, c1 = min(P.n, c0 + P.B);
+    const size_t rowbase = (size_t)p * Tb.max_rows;
+    for (int j = c0; j < c1; j++) {
+        I g = mk<T>((T)0, (T)0);
+        for (int v = 0; v < P.n_var_leaves; v++) {
+            GbVarLeaf L = P.var_leaves[v];
+            if (L.coord == j) g = iadd(g, OA[L.reg]), ops += 2;
+        }
+        for (int k = 0; k < P.n_sum; k++) {
+            const int2 rg = P.jk[SP.jk0 + (j - c0) * P.n_sum + k];
+            if (rg.x == rg.y) continue;
+            I Dk = mk<T>((T)0, (T)0);
+            for (int q = rg.x; q < rg.y; q++) {
+                const GbContrib C = P.contribs[q];
+                const GbDTerm D = P.dterms[SP.dterm0 + C.dterm];
+                const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
+                Dk = iadd(Dk, TabPrec<T>::tl(Tb, (rowbase + D.row + combo) * Tb.max_leaves + C.leaf));
+                ops += 2;
+            }
+            g = iadd(g, imul(OA[P.sums[k].outer_reg], Dk));
+            ops += 4;
+        }
+        iv64 x = X64.get(j);
+        if ((g.lo > (T)0 && x.lo != __ldg(P.l + j)) || (g.hi < (T)0 && x.hi != __ldg(P.u + j))) return true;
+    }
+    return false;
+}
+
+// FP64 child: midpoint sample, F(X), first-order test.
+__device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                                 const GbTabs& Tb, const GbChildren& ch, long long ci,
+                                                 const GbSplit& sp, double gub_prev, unsigned long long* gkey,
+                                                 bool* has_key, int& ops) {
+    ChildCtx c = child_ctx(par, ci, sp);
+    if (!c.valid) {
+        ch.flag[ci] = 0;
+        ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
+        return false;
+    }
+    const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
+    const int blk = c.info.z;
+    View<double> X = view64(pool, par, c, sp);
+    MidView MX{X};
+    iv64 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+    int dt = SP.dterm0;
+    for (int k = 0; k < P.n_sum; k++) sums[k] = tab_sum<double, true>(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
+    iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
+    if (Fm.hi == Fm.hi) {
+        *gkey = gb_order_key(Fm.hi);
+        *has_key = true;
+    }
+    dt = SP.dterm0;
+    for (int k = 0; k < P.n_sum; k++) sums[k] = tab_sum<double, false>(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
+    iv64 F = outer_fwd<double>(P, X, sums, O, ops);
+    bool keep = !(F.lo > gub_prev);
+    if (keep) keep = !tab_mono<double>(P, Tb, c.p, SP, blk, c.r, X, O, OA, ops);
+    ch.flo[ci] = canon_lo(F.lo);
+    ch.flag[ci] = keep ? 1 : 0;
+    return true;
+}
+
+__global__ void __launch_bounds__(128) k_eval64_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+                                                    GbChildren ch, long long nchildren, GbSplit sp,
+                                                    double gub_prev, int from_list, GbState* st) {
+    const long long lim = from_list ? st->n32 : nchildren;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < lim; base += stride) {
+        long long idx = base + (threadIdx.x & 31);
+        unsigned long long key = ~0ull;
+        bool has = false, valid = false;
+        int ops = 0;
+        if (idx < lim) {
+            long long ci = from_list ? (long long)ch.list32[idx] : idx;
+            valid = eval64_tab_child(P, pool, par, Tb, ch, ci, sp, gub_prev, &key, &has, ops);
+        }
+        warp_min_gub(key, has, st);
+        warp_add_ops(ops, &st->ops64);
+        unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
+        if ((threadIdx.x & 31) == 0 && nv) {
+            atomicAdd((unsigned long long*)&st->evals64, (unsigned long long)nv);
+            atomicAdd((unsigned long long*)&st->mids, (unsigned long long)nv);
+            if (!from_list) atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_eval32_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+                                                    GbChildren ch, long long nchildren, GbSplit sp,
+                                                    double gub_prev, GbState* st) {
+    long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool valid = false;
+    int ops = 0;
+    if (ci < nchildren) {
+        ChildCtx c = child_ctx(par, ci, sp);
+        ch.flag[ci] = 0;
+        ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
+        if (c.valid) {
+            valid = true;
+            const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
+            const int blk = c.info.z;
+            View<float> X = view32(pool, par, c, sp);
+            View<double> X64 = view64(pool, par, c, sp);
+            iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+            int dt = SP.dterm0;
+            for (int k = 0; k < P.n_sum; k++) sums[k] = tab_sum<float, false>(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
+            iv32 F = outer_fwd<float>(P, X, sums, O, ops);
+            bool keep = !((double)F.lo > gub_prev);
+            if (keep) keep = !tab_mono<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, ops);
+            ch.flag32[ci] = keep ? 1 : 0;
+        } else {
+            ch.flag32[ci] = 0;
+        }
+    }
+    warp_add_ops(ops, &st->ops32);
+    unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
+    if ((threadIdx.x & 31) == 0 && nv) {
+        atomicAdd((unsigned long long*)&st->evals32, (unsigned long long)nv);
+        atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+    }
+}
+
+unsigned grid_for(long long items, int per_block) {
+    long long g = (items + per_block - 1) / per_block;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+long long gb_tab_launches_so_far() { return g_tab_launches; }
+
+cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                           long long npar, const GbSplit& sp, cudaStream_t s) {
+    g_tab_launches++;
+    k_ptab<<<(unsigned)npar, 128, 0, s>>>(P, pool, par, T, sp);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                                 const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
+                                 bool from_list, GbState* st, cudaStream_t s) {
+    unsigned g = grid_for(nchildren, 128);
+    if (from_list && g > 152 * 16) g = 152 * 16;
+    g_tab_launches++;
+    k_eval64_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, nchildren, sp, gub_prev, from_list ? 1 : 0, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                                 const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
+                                 GbState* st, cudaStream_t s) {
+    g_tab_launches++;
+    k_eval32_tab<<<grid_for(nchildren, 128), 128, 0, s>>>(P, pool, par, T, ch, nchildren, sp, gub_prev, st);
+    return cudaGetLastError();
+}

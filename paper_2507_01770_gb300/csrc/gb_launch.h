@@ -49,6 +49,20 @@ struct GbSplit {
     int dmax;                  // boundary table stride (coordinates)
 };
 
+// Per-parent term tables (rows indexed by parent * max_rows + row) and the
+// parent's group-sum trees (nodes indexed by parent * tree_nodes + node).
+struct GbTabs {
+    double2* tv64;    // term value over the box
+    double2* tm64;    // term value at the box midpoint
+    double2* tl64;    // leaf adjoints, max_leaves per row
+    float2* tv32;     // FP32 term value (FP32 prefilter only)
+    float2* tl32;     // FP32 leaf adjoints
+    double2* nf64;    // group tree of the parent's cached sums: F
+    double2* nm64;    // midpoint
+    float2* nf32;     // FP32
+    int max_rows, max_leaves, tree_nodes;
+};
+
 // scratch for the three-phase scans
 struct GbScan {
     int* tile_cnt;     // [3][max_tiles]
@@ -102,3 +116,13 @@ extern "C" gb_status solve_begin(gb_problem* p);
 extern "C" int solve_advance(gb_problem* p, bool block);
 extern "C" gb_status solve_finish(gb_problem* p, gb_result* out, bool copy_boxes);
 extern "C" size_t gb_internal_device_bytes(const gb_problem* p);
+// per-parent term tables (gb_kernels_tab.cu)
+cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                           long long npar, const GbSplit& sp, cudaStream_t s);
+cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                                 const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
+                                 bool from_list, GbState* st, cudaStream_t s);
+cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                                 const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
+                                 GbState* st, cudaStream_t s);
+long long gb_tab_launches_so_far();

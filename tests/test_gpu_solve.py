@@ -135,3 +135,31 @@ def test_solve_is_repeatable_and_device_only_matches():
     assert a.fmin_lo == b.fmin_lo == c.fmin_lo and a.fmin_hi == b.fmin_hi == c.fmin_hi
     assert np.array_equal(a.box_lo, b.box_lo) and c.box_lo is None and c.n_boxes == a.n_boxes
     assert np.array_equal(a.trace["gub"], b.trace["gub"])
+
+
+@pytest.mark.parametrize("fam,kw,opt", [
+    ("chain", dict(n=12, seed=3), dict(block=6, split_m=2, split_d=3, max_children=8 * 8)),
+    ("chain", dict(n=20, seed=4), dict(block=10, split_m=4, split_d=5, max_children=2 * 1024)),
+    ("sep_cos", dict(n=4, seed=5, tol_f=1e-6), dict(block=4, split_m=2, split_d=4, max_children=16 * 16)),
+    ("ackley", dict(n=8, seed=6), dict(block=4, split_m=2, split_d=4, max_children=16 * 16, fp32_prefilter=1)),
+    ("mixed", dict(n=10, seed=7), dict(block=5, split_m=2, split_d=5, max_children=16 * 32)),
+])
+def test_table_path_identical_to_interpreter(fam, kw, opt):
+    """The per-parent term tables change how a child is assembled, never its
+    bits: both paths must give the same run; for polynomials also the oracle's."""
+    p = S.make(fam, **kw)
+    runs = []
+    for mode in (1, 2):
+        s = gb.Solver(p, eval_mode=mode, **opt)
+        runs.append(s.solve())
+        s.close()
+    a, b = runs
+    assert a.status == b.status == 0
+    assert a.fmin_lo == b.fmin_lo and a.fmin_hi == b.fmin_hi
+    assert np.array_equal(a.box_lo, b.box_lo) and np.array_equal(a.box_hi, b.box_hi)
+    for k in ("parents", "children", "kept32", "kept", "pool", "gub"):
+        assert np.array_equal(a.trace[k], b.trace[k]), k
+    if fam == "chain":
+        o = O.Oracle(p, block=opt["block"]).solve(split_m=opt["split_m"], split_d=opt["split_d"],
+                                                  max_parents=opt["max_children"] // opt["split_m"] ** opt["split_d"])
+        _assert_identical(b, o)
