@@ -203,6 +203,9 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         delete p;
         return fail(GB_E_INVALID, err);
     }
+    // term-table layouts also set each sum's tree offsets: build them before
+    // the program is uploaded
+    if (opt.eval_mode != 1) gb_build_tables(&p->hp, opt.split_m, opt.split_d);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= opt.device || opt.device < 0) {
         delete p;
@@ -320,7 +323,6 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         return bad(e, "allocate child buffers");
     // per-parent term tables
     if (opt.eval_mode != 1) {
-        gb_build_tables(&p->hp, m, d);
         const bool want = opt.eval_mode == 2 || p->fan >= 16;
         if (p->hp.tab_ok && want) {
             const GbHostProg& Hh = p->hp;

@@ -43,7 +43,9 @@ __global__ void __launch_bounds__(128) k_ptab(GbProg P, GbPool pool, GbParents p
     const long long p = blockIdx.x;
     const int4 info = par.info[p];
     const unsigned slot = par.slot[p];
-    const GbSplitPos SP = P.sps[P.sp_of_cyc[info.x]];
+    const int spi = P.sp_of_cyc[info.x];
+    if (spi < 0) return;
+    const GbSplitPos SP = P.sps[spi];
     const size_t o = (size_t)p * sp.dmax * (sp.m + 1);
     const double* b64 = par.bnd + o;
     iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS];
@@ -172,7 +174,7 @@ __device__ __forceinline__ typename TabPrec<T>::I tab_sum(const GbProg& P, const
         ops += 2 * (cnt > 0 ? cnt - 1 : 0);
         cur[g - dr.x] = tr.result();
     }
-    if (S.ngroups == 0) {
+    if (S.ngroups == 0 || S.nnodes <= 0) {
         I z;
         z.lo = 0;
         z.hi = 0;
@@ -254,12 +256,13 @@ __device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& 
                                                  const GbSplit& sp, double gub_prev, unsigned long long* gkey,
                                                  bool* has_key, int& ops) {
     ChildCtx c = child_ctx(par, ci, sp);
-    if (!c.valid) {
+    const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
+    if (spi < 0) {   // invalid child (or, defensively, a split position without a layout)
         ch.flag[ci] = 0;
         ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
         return false;
     }
-    const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
+    const GbSplitPos SP = P.sps[spi];
     const int blk = c.info.z;
     View<double> X = view64(pool, par, c, sp);
     MidView MX{X};
@@ -316,9 +319,10 @@ __global__ void __launch_bounds__(128) k_eval32_tab(GbProg P, GbPool pool, GbPar
         ChildCtx c = child_ctx(par, ci, sp);
         ch.flag[ci] = 0;
         ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
-        if (c.valid) {
+        const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
+        if (spi >= 0) {
             valid = true;
-            const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
+            const GbSplitPos SP = P.sps[spi];
             const int blk = c.info.z;
             View<float> X = view32(pool, par, c, sp);
             View<double> X64 = view64(pool, par, c, sp);
