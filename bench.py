@@ -177,63 +177,88 @@ def _serving_opts(gb, p, fp32):
 
 
 def run_serving(a):
-    """Poisson stream of minimisation requests served with continuous
-    batching (FP32 prefilter + FP64), against the same problems solved one
-    at a time in FP64 on the same GPU."""
-    import torch
+    """Stream of minimisation requests served with continuous batching
+    (FP32 prefilter + FP64) against the same problems solved one at a time in
+    FP64 on the same GPU.
+
+    Phase 1: Poisson arrivals, served: per-request latency (submit -> result).
+    Phase 2: the same problems one at a time (FP64): service times; the FIFO
+             queue under the same arrival times gives its latencies.
+    Phase 3: saturation -- every request submitted at once -- for the served
+             capacity (solves/s), against the sum of the one-at-a-time times.
+    """
     import paper_2507_01770_gb300 as gb
     gb.load()
     stream = S.serving_stream(count=a.requests, seed=0, rate=20.0, n_min=2, n_max=a.n_max, tol_f=1e-6)
-    # warm-up: one small request of each family
-    srv = gb.Server(pool_budget_bytes=150 << 30, device=0, max_active=32)
-    for _, p in stream[:3]:
-        rid = srv.submit(p, _serving_opts(gb, p, True))
-        while srv.poll(rid) is None:
-            time.sleep(0.001)
-    t_start = time.perf_counter()
-    pending = {}
-    done = {}
-    k = 0
-    while len(done) < len(stream):
-        now = time.perf_counter() - t_start
-        while k < len(stream) and stream[k][0] <= now:
-            p = stream[k][1]
-            pending[srv.submit(p, _serving_opts(gb, p, True))] = k
-            k += 1
-        for rid in list(pending):
-            r = srv.poll(rid)
-            if r is not None:
-                done[pending.pop(rid)] = (r, time.perf_counter() - t_start)
-        time.sleep(0.0005)
-    makespan = max(t for _, t in done.values()) - stream[0][0]
-    srv.close()
-    lat = np.array([done[i][0].latency_ms for i in range(len(stream))])
-    ok = all(done[i][0].status == 0 and done[i][0].fmin_lo <= 0.0 <= done[i][0].fmin_hi
-             and done[i][0].fmin_hi - done[i][0].fmin_lo <= 1e-6 for i in range(len(stream)))
-    # one at a time, FP64 only, same problems
-    t0 = time.perf_counter()
-    seq_ok = True
+    arrivals = np.array([t for t, _ in stream]) - stream[0][0]
+
+    def serve(times):
+        srv = gb.Server(pool_budget_bytes=150 << 30, device=0, max_active=32)
+        for _, p in stream[:3]:                       # warm-up
+            rid = srv.submit(p, _serving_opts(gb, p, True))
+            while srv.poll(rid) is None:
+                time.sleep(0.0005)
+        t0 = time.perf_counter()
+        pending, done, k = {}, {}, 0
+        while len(done) < len(stream):
+            now = time.perf_counter() - t0
+            while k < len(stream) and times[k] <= now:
+                p = stream[k][1]
+                pending[srv.submit(p, _serving_opts(gb, p, True))] = k
+                k += 1
+            for rid in list(pending):
+                r = srv.poll(rid)
+                if r is not None:
+                    done[pending.pop(rid)] = (r, time.perf_counter() - t0)
+            time.sleep(0.0002)
+        srv.close()
+        return done
+
+    live = serve(arrivals)
+    lat = np.array([live[i][0].latency_ms for i in range(len(stream))])
+    makespan = max(t for _, t in live.values())
+    ok = all(live[i][0].status == 0 and live[i][0].fmin_lo <= 0.0 <= live[i][0].fmin_hi
+             and live[i][0].fmin_hi - live[i][0].fmin_lo <= 1e-6 for i in range(len(stream)))
+    # one at a time, FP64 only
+    service, seq_ok = [], True
     for _, p in stream:
-        s = gb.Solver(p, **{f: getattr(_serving_opts(gb, p, False), f)
-                            for f in ("block", "split_m", "split_d", "max_children", "pool_bytes")})
-        r = s.solve(device_only=True)
+        o = _serving_opts(gb, p, False)
+        s = gb.Solver(p, **{f: getattr(o, f) for f in ("block", "split_m", "split_d", "max_children",
+                                                        "pool_bytes")})
+        t0 = time.perf_counter()
+        r = s.solve()
+        service.append(time.perf_counter() - t0)
         seq_ok &= r.status == 0 and r.fmin_lo <= 0.0 <= r.fmin_hi
         s.close()
-    seq_t = time.perf_counter() - t0
+    finish, fifo_lat = 0.0, []
+    for t, sv in zip(arrivals, service):
+        finish = max(finish, t) + sv
+        fifo_lat.append(1e3 * (finish - t))
+    fifo_lat = np.array(fifo_lat)
+    # saturation
+    sat = serve(np.zeros(len(stream)))
+    sat_t = max(t for _, t in sat.values())
     fams = {}
     for _, p in stream:
         fams[p.family] = fams.get(p.family, 0) + 1
-    line = {"metric": "served solves/s", "value": len(stream) / makespan, "unit": "solves/s",
-            "n_gpus": 1, "steps": 1, "warmup": 3, "ms_per_step": 1e3 * makespan,
+    line = {"metric": "served solves/s", "value": len(stream) / sat_t, "unit": "solves/s",
+            "n_gpus": 1, "steps": 1, "warmup": 3, "ms_per_step": 1e3 * sat_t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"serving stream: {len(stream)} requests, Poisson arrivals 20/s, "
-                                   f"n log-uniform [2, {a.n_max}], families {fams}, tol_f=1e-6, "
-                                   "FP32 prefilter + FP64, 150 GB budget, 32 slots, 4 GB per request",
-                       "p50_latency_ms": float(np.percentile(lat, 50)),
-                       "p99_latency_ms": float(np.percentile(lat, 99)),
-                       "sequential_fp64_solves_per_s": len(stream) / seq_t,
-                       "speedup_vs_sequential_fp64": (len(stream) / makespan) / (len(stream) / seq_t),
+            "config": {"workload": f"serving stream: {len(stream)} requests, n log-uniform [2, {a.n_max}], "
+                                   f"families {fams}, tol_f=1e-6, FP32 prefilter + FP64, "
+                                   "150 GB budget, 32 slots, 4 GB per request",
+                       "value_is": "capacity: all requests submitted at once, solves per second",
+                       "sequential_fp64_solves_per_s": len(stream) / sum(service),
+                       "speedup_vs_sequential_fp64": (len(stream) / sat_t) / (len(stream) / sum(service)),
+                       "poisson_20_per_s": {
+                           "served_p50_ms": float(np.percentile(lat, 50)),
+                           "served_p99_ms": float(np.percentile(lat, 99)),
+                           "served_solves_per_s": len(stream) / makespan,
+                           "one_at_a_time_fp64_p50_ms": float(np.percentile(fifo_lat, 50)),
+                           "one_at_a_time_fp64_p99_ms": float(np.percentile(fifo_lat, 99)),
+                           "one_at_a_time_fp64_solves_per_s": len(stream) / (arrivals[-1] + 0.0 +
+                                                                             max(0.0, finish - arrivals[-1]))},
                        "all_enclosures_valid": bool(ok and seq_ok),
                        "note": "n range reduced from the named [2, 2000]: dense box rows of the "
                                "n > 200 Ackley requests exceed the per-request pool"}}
@@ -351,8 +376,9 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "kernel": "k_eval64", "ops": "FP64 directed-rounding operations executed by the "
-                                                  "interpreted program (counted in the kernel)",
+                     "kernel": "k_eval64_tab", "ops": "FP64 directed-rounding operations executed by the "
+                                                      "child kernel (counted in the kernel; the per-parent "
+                                                      "term tables of k_ptab are not included)",
                      "ops_per_eval": ops64 / max(1, sum(r.box_evals_fp64 - 1 for r in results)),
                      "static_ops_per_eval": info["ops_eval"] + info["ops_mid"],
                      "peak_source": f"2 FP64 ops/SM/clk x 152 SMs x {sm_mhz:.0f} MHz (sampled median)",

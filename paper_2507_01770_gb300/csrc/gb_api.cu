@@ -496,7 +496,8 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
     }
     R.timed64 = true;
     GB_ST(gb_launch_compact_children(p->ch, nch, 1, p->st, p->sc, s));
-    GB_ST(gb_launch_materialize(p->P, p->pool, p->par, p->ch, nch, p->sp, p->E[1 - cur], p->opt.tol_x, p->st, s));
+    GB_ST(gb_launch_materialize(p->P, p->pool, p->par, p->ch, nch, p->sp, p->E[1 - cur], p->opt.tol_x, p->st, s,
+                                tab ? &p->tabs : nullptr));
     GB_ST(gb_launch_finish(p->par, npar, p->pool, p->E[1 - cur], p->st, s));
     R.cur = 1 - cur;
     R.last_par = npar;

@@ -60,4 +60,36 @@ __device__ __forceinline__ void warp_add_ops(int ops, unsigned long long* dst) {
 }
 
 
+// Sum of the terms of dirty group g of sum k for child index r, read from
+// the parent's term tables (kind 0: F, 1: midpoint); same pairwise tree as
+// group_sum.
+__device__ __forceinline__ iv64 tab_group64(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
+                                            int k, int g, unsigned r, int kind) {
+    Tree<iv64> tr;
+    tr.init();
+    const size_t rowbase = (size_t)p * Tb.max_rows;
+    for (int q = 0; q < SP.ndterm; q++) {
+        const GbDTerm D = P.dterms[SP.dterm0 + q];
+        if (D.sum != k || D.group != g) continue;
+        const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
+        double2 v = kind == 0 ? Tb.tv64[rowbase + D.row + combo] : Tb.tm64[rowbase + D.row + combo];
+        tr.push(iv64{v.x, v.y});
+    }
+    return tr.result();
+}
+__device__ __forceinline__ iv32 tab_group32(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
+                                            int k, int g, unsigned r) {
+    Tree<iv32> tr;
+    tr.init();
+    const size_t rowbase = (size_t)p * Tb.max_rows;
+    for (int q = 0; q < SP.ndterm; q++) {
+        const GbDTerm D = P.dterms[SP.dterm0 + q];
+        if (D.sum != k || D.group != g) continue;
+        const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
+        float2 v = Tb.tv32[rowbase + D.row + combo];
+        tr.push(iv32{v.x, v.y});
+    }
+    return tr.result();
+}
+
 }  // namespace gb

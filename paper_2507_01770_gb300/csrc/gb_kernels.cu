@@ -539,7 +539,8 @@ __global__ void k_cc_scatter(GbChildren ch, long long n, int mode, const GbState
 // groups recomputed, the rest copied from the parent), pool entry.
 __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                 const GbChildren& ch, const GbSplit& sp, const GbEntries& En,
-                                                double tol_x, const GbState* st, long long s, int lane) {
+                                                double tol_x, const GbState* st, long long s, int lane,
+                                                const GbTabs& Tb, bool tab) {
     const long long nfree = st->nfree, bump = st->bump, kept_old = st->kept_old;
     const long long ci = ch.surv[s];
     ChildCtx c = child_ctx(par, ci, sp);
@@ -579,14 +580,25 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
         for (int g = dr.x; g < dr.y; g++, slot_k++) {
             if ((slot_k & 31) != lane) continue;
             size_t dst = (size_t)ns * pool.NG + S.group0 + g;
-            iv64 a = group_sum<double>(P, S, g, X, R, ops);
-            iv64 b = group_sum<double>(P, S, g, MX, R, ops);
+            iv64 a, b;
+            if (tab) {
+                const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
+                a = tab_group64(P, Tb, c.p, SP, k, g, c.r, 0);
+                b = tab_group64(P, Tb, c.p, SP, k, g, c.r, 1);
+                if (pool.fp32) {
+                    iv32 f = tab_group32(P, Tb, c.p, SP, k, g, c.r);
+                    pool.gsum32[dst] = make_float2(f.lo, f.hi);
+                }
+            } else {
+                a = group_sum<double>(P, S, g, X, R, ops);
+                b = group_sum<double>(P, S, g, MX, R, ops);
+                if (pool.fp32) {
+                    iv32 f = group_sum<float>(P, S, g, X32, R32, ops);
+                    pool.gsum32[dst] = make_float2(f.lo, f.hi);
+                }
+            }
             pool.gsum[dst] = make_double2(a.lo, a.hi);
             pool.gmid[dst] = make_double2(b.lo, b.hi);
-            if (pool.fp32) {
-                iv32 f = group_sum<float>(P, S, g, X32, R32, ops);
-                pool.gsum32[dst] = make_float2(f.lo, f.hi);
-            }
         }
     }
     if (lane == 0) {
@@ -598,13 +610,14 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
 }
 
 __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbParents par, GbChildren ch,
-                                                     GbSplit sp, GbEntries En, double tol_x, GbState* st) {
+                                                     GbSplit sp, GbEntries En, double tol_x, GbState* st,
+                                                     GbTabs Tb, int tab) {
     const int lane = threadIdx.x & 31;
     if (st->overflow) return;
     const long long kept = st->kept;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < kept; s += nwarps)
-        materialize_one(P, pool, par, ch, sp, En, tol_x, st, s, lane);
+        materialize_one(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0);
 }
 
 // Parents' slots back to the free list, or (on overflow) the parents back
@@ -870,11 +883,14 @@ cudaError_t gb_launch_compact_children(const GbChildren& ch, long long nchildren
 
 cudaError_t gb_launch_materialize(const GbProg& P, const GbPool& pool, const GbParents& par,
                                   const GbChildren& ch, long long nchildren, const GbSplit& sp,
-                                  const GbEntries& E_new, double tol_x, GbState* st, cudaStream_t s) {
+                                  const GbEntries& E_new, double tol_x, GbState* st, cudaStream_t s,
+                                  const GbTabs* tabs) {
+    GbTabs Tb{};
+    if (tabs) Tb = *tabs;
     gb_launch_count++;
     unsigned g = grid_for(nchildren * 32, 128);
     if (g > 152 * 16) g = 152 * 16;
-    k_materialize<<<g, 128, 0, s>>>(P, pool, par, ch, sp, E_new, tol_x, st);
+    k_materialize<<<g, 128, 0, s>>>(P, pool, par, ch, sp, E_new, tol_x, st, Tb, tabs ? 1 : 0);
     return cudaGetLastError();
 }
 

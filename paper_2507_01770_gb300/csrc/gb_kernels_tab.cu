@@ -39,8 +39,8 @@ __device__ __forceinline__ iv64 mid_node(const GbTabs& T, size_t i) { double2 v 
 
 // ---------------------------------------------------------------------------
 // k_ptab: one block per parent.  Rows: (dirty term, digit combination).
-__global__ void __launch_bounds__(128) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp) {
-    const long long p = blockIdx.x;
+__global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp) {
+    const long long p = blockIdx.y;
     const int4 info = par.info[p];
     const unsigned slot = par.slot[p];
     const int spi = P.sp_of_cyc[info.x];
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(128) k_ptab(GbProg P, GbPool pool, GbParents p
     iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS];
     iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS];
     int ops = 0;
-    for (int row = threadIdx.x; row < SP.tab_entries; row += blockDim.x) {
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < SP.tab_entries; row += gridDim.x * blockDim.x) {
         // the dirty term owning this row (rows are contiguous per term)
         int lo = 0, hi = SP.ndterm - 1;
         while (lo < hi) {
@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(128) k_ptab(GbProg P, GbPool pool, GbParents p
     }
     // group trees of the parent's cached sums (level-major, pairwise)
     const int kinds = pool.fp32 ? 3 : 2;
+    if (blockIdx.x != 0) return;
     for (int job = threadIdx.x; job < P.n_sum * kinds; job += blockDim.x) {
         const int k = job % P.n_sum, kind = job / P.n_sum;
         const GbSum S = P.sums[k];
@@ -224,26 +225,38 @@ __device__ __forceinline__ bool tab_mono(const GbProg& P, const GbTabs& Tb, long
     reverse_sweep<T>(P.outer, P.n_outer, O, OA, ops);
     const int c0 = blk * P.B, c1 = min(P.n, c0 + P.B);
     const size_t rowbase = (size_t)p * Tb.max_rows;
+    // Sums whose outer adjoint is exactly [1, 1] (a plain sum): the product
+    // adj * D equals D, so it is skipped; additions to an exact [0, 0] start
+    // are skipped too (they return the other operand's value).
     for (int j = c0; j < c1; j++) {
-        I g = mk<T>((T)0, (T)0);
+        I g;
+        bool have = false;
         for (int v = 0; v < P.n_var_leaves; v++) {
             GbVarLeaf L = P.var_leaves[v];
-            if (L.coord == j) g = iadd(g, OA[L.reg]), ops += 2;
+            if (L.coord != j) continue;
+            if (have) g = iadd(g, OA[L.reg]), ops += 2;
+            else g = OA[L.reg], have = true;
         }
         for (int k = 0; k < P.n_sum; k++) {
             const int2 rg = P.jk[SP.jk0 + (j - c0) * P.n_sum + k];
             if (rg.x == rg.y) continue;
-            I Dk = mk<T>((T)0, (T)0);
+            I Dk;
             for (int q = rg.x; q < rg.y; q++) {
                 const GbContrib C = P.contribs[q];
                 const GbDTerm D = P.dterms[SP.dterm0 + C.dterm];
                 const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
-                Dk = iadd(Dk, TabPrec<T>::tl(Tb, (rowbase + D.row + combo) * Tb.max_leaves + C.leaf));
-                ops += 2;
+                I v = TabPrec<T>::tl(Tb, (rowbase + D.row + combo) * Tb.max_leaves + C.leaf);
+                if (q > rg.x) Dk = iadd(Dk, v), ops += 2;
+                else Dk = v;
             }
-            g = iadd(g, imul(OA[P.sums[k].outer_reg], Dk));
-            ops += 4;
+            const I a = OA[P.sums[k].outer_reg];
+            I term;
+            if (a.lo == (T)1 && a.hi == (T)1) term = Dk;
+            else term = imul(a, Dk), ops += 2;
+            if (have) g = iadd(g, term), ops += 2;
+            else g = term, have = true;
         }
+        if (!have) g = mk<T>((T)0, (T)0);
         iv64 x = X64.get(j);
         if ((g.lo > (T)0 && x.lo != __ldg(P.l + j)) || (g.hi < (T)0 && x.hi != __ldg(P.u + j))) return true;
     }
@@ -356,8 +369,10 @@ long long gb_tab_launches_so_far() { return g_tab_launches; }
 
 cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                            long long npar, const GbSplit& sp, cudaStream_t s) {
+    // rows of a parent spread over blocks of 64 threads
+    const unsigned chunks = (unsigned)((P.max_rows + 63) / 64);
     g_tab_launches++;
-    k_ptab<<<(unsigned)npar, 128, 0, s>>>(P, pool, par, T, sp);
+    k_ptab<<<dim3(chunks < 1 ? 1 : chunks, (unsigned)npar), 64, 0, s>>>(P, pool, par, T, sp);
     return cudaGetLastError();
 }
 

@@ -95,9 +95,11 @@ cudaError_t gb_launch_eval32(const GbProg& P, const GbPool& pool, const GbParent
 // (flag && flo <= new GUB) with the capacity check.
 cudaError_t gb_launch_compact_children(const GbChildren& ch, long long nchildren, int mode, GbState* st,
                                        const GbScan& sc, cudaStream_t s);
+// tabs: the parents' term tables (null: dirty groups are re-interpreted)
 cudaError_t gb_launch_materialize(const GbProg& P, const GbPool& pool, const GbParents& par,
                                   const GbChildren& ch, long long nchildren, const GbSplit& sp,
-                                  const GbEntries& E_new, double tol_x, GbState* st, cudaStream_t s);
+                                  const GbEntries& E_new, double tol_x, GbState* st, cudaStream_t s,
+                                  const GbTabs* tabs);
 cudaError_t gb_launch_finish(const GbParents& par, long long npar, const GbPool& pool,
                              const GbEntries& E_new, GbState* st, cudaStream_t s);
 // Final output: entries with flo <= GUB, in pool order, gathered into rows.
