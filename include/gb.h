@@ -93,6 +93,10 @@ typedef struct gb_options {
     int32_t device;           /* CUDA device ordinal */
     int32_t eval_mode;        /* child evaluation: 0 auto (term tables when m^d >= 16 and they fit),
                                  1 bytecode interpreter, 2 term tables when they fit; results are identical */
+    int32_t gens_per_sync;    /* <= 1: the host reads the state after every generation (per-kernel timing);
+                                 G > 1: generations run as replays of a captured CUDA graph, G between
+                                 state reads (the search is the same) */
+    int32_t pad;
 } gb_options;
 
 /* Fills *opt with the defaults documented above. */

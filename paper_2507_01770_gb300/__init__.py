@@ -36,7 +36,8 @@ class gb_options(ctypes.Structure):
                 ("split_d", ctypes.c_int32), ("fp32_prefilter", ctypes.c_int32),
                 ("max_generations", ctypes.c_int64), ("max_children", ctypes.c_int64),
                 ("max_boxes", ctypes.c_int64), ("pool_bytes", ctypes.c_size_t),
-                ("device", ctypes.c_int32), ("eval_mode", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("eval_mode", ctypes.c_int32),
+                ("gens_per_sync", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class gb_gen_stat(ctypes.Structure):

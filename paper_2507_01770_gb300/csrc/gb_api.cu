@@ -110,6 +110,10 @@ struct gb_problem {
     cudaEvent_t ev[6] = {};        // solve start/end, eval64 start/end, eval32 start/end
     cudaEvent_t ev_state = nullptr; // the state record of the last generation has reached the host
     SolveRun run;
+    GbGenConst G{};
+    gb_gen_stat* trace_dev = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // one generation, pool buffers 0->1 and 1->0
+    long long graph_kernels = 0;
     size_t device_bytes = 0;       // device memory held by the problem
 };
 
@@ -153,6 +157,8 @@ void gb_destroy_problem(gb_problem* p) {
     for (cudaEvent_t e : p->ev)
         if (e) cudaEventDestroy(e);
     if (p->ev_state) cudaEventDestroy(p->ev_state);
+    for (cudaGraphExec_t g : p->gexec)
+        if (g) cudaGraphExecDestroy(g);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -364,6 +370,15 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             p->use_tabs = true;
         }
     }
+    p->G.K = p->K;
+    p->G.flog2 = d * mshift;
+    p->G.fp32 = fp32;
+    p->G.max_gen = opt.max_generations;
+    p->G.tol_f = tol_f;
+    p->G.tol_x = opt.tol_x;
+    p->G.trace_cap = opt.max_generations < (1LL << 20) ? opt.max_generations : (1LL << 20);
+    if ((e = alloc(&p->trace_dev, (size_t)p->G.trace_cap, A))) return bad(e, "allocate trace");
+    p->G.trace = p->trace_dev;
     long long items = cap > p->Cmax ? cap : p->Cmax;
     p->sc.max_tiles = (int)((items + GB_TILE - 1) / GB_TILE) + 1;
     if ((e = alloc(&p->sc.tile_cnt, (size_t)3 * p->sc.max_tiles, A)) ||
@@ -411,24 +426,48 @@ __attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
     R = SolveRun{};
     R.t0 = std::chrono::steady_clock::now();
     GB_CU(cudaSetDevice(p->device));
-    const long long l0 = (gb_launches_so_far() + gb_tab_launches_so_far());
+    const long long l0 = gb_launches_so_far();
     cudaStream_t s = p->stream;
     GbState init{};
     init.cap = p->cap;
     GB_CU(cudaEventRecord(p->ev[0], s));
     GB_CU(cudaMemcpyAsync(p->st, &init, sizeof(GbState), cudaMemcpyHostToDevice, s));
     GB_CU(gb_launch_root_init(p->P, p->pool, p->E[0], p->st, s));
-    GB_CU(gb_launch_stats(p->E[0], 1, p->tol_f, p->st, s));
+    GB_CU(gb_launch_stats(p->E[0], p->G, 1, p->st, s));
     GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
     GB_CU(cudaEventRecord(p->ev_state, s));
-    R.launches += (gb_launches_so_far() + gb_tab_launches_so_far()) - l0;
+    R.launches += gb_launches_so_far() - l0;
     R.active = true;
     return GB_OK;
 }
 
+// Captures one generation per pool-buffer parity as a CUDA graph (once per
+// problem; every argument of a generation is fixed, sizes come from the
+// device state).
+static cudaError_t capture_graphs(gb_problem* p) {
+    cudaStream_t s = p->stream;
+    for (int par = 0; par < 2; par++) {
+        if (p->gexec[par]) continue;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        long long nl = 0;
+        e = gb_launch_generation(p->P, p->pool, p->E[par], p->E[1 - par], p->par, p->ch, p->sp, p->sc,
+                                 p->use_tabs ? &p->tabs : nullptr, p->G, p->cap, p->Cmax, p->st, s, nullptr, &nl);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess) return e;
+        if (e2 != cudaSuccess) return e2;
+        e = cudaGraphInstantiate(&p->gexec[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        p->graph_kernels = nl;
+    }
+    return cudaSuccess;
+}
+
 // Returns 1 when the generation loop has ended (R.status holds the outcome),
-// 0 when another generation was enqueued or (non-blocking) the previous one
-// has not finished yet.
+// 0 when more generations were enqueued or (non-blocking) the previous ones
+// have not finished yet.
 __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool block) {
     SolveRun& R = p->run;
     if (R.loop_done) return 1;
@@ -443,70 +482,37 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
     cudaSetDevice(p->device);
     cudaStream_t s = p->stream;
     const GbState h = *p->st_host;
-    const double gub = gb_key_value(h.gub_key);
     float ms = 0.f;
     if (R.timed64 && cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) R.t64 += ms, R.n64++;
     if (R.timed32 && cudaEventElapsedTime(&ms, p->ev[4], p->ev[5]) == cudaSuccess) R.t32 += ms, R.n32++;
     R.timed64 = R.timed32 = false;
-    if (h.gen > 0 && (long long)R.trace.size() < h.gen) {
-        gb_gen_stat g;
-        g.parents = R.last_par;
-        g.children = h.children;
-        g.kept32 = p->opt.fp32_prefilter ? h.kept32 : h.children;
-        g.kept = h.overflow ? 0 : h.kept;
-        g.pool = h.pool;
-        g.gub = gub;
-        R.trace.push_back(g);
-    }
     if (h.error) return stop(fail(GB_E_CUDA, "device-side selection error"));
     if (h.overflow) return stop(fail(GB_E_CAPACITY, "box pool capacity reached"));
     if (h.active == 0) return stop(GB_OK);
-    if (h.gen >= p->opt.max_generations) return stop(fail(GB_E_LIMIT, "generation limit reached"));
-    const long long l0 = (gb_launches_so_far() + gb_tab_launches_so_far());
-    const int cur = R.cur;
-    const long long count = h.pool;
-    const long long npar = h.active < p->K ? h.active : p->K;
-    const long long nch = npar * p->fan;
+    if (h.halt || h.gen >= p->opt.max_generations) return stop(fail(GB_E_LIMIT, "generation limit reached"));
+    const long long l0 = gb_launches_so_far();
+    const int cur = (int)(h.gen & 1);   // every completed generation swaps the pool buffers
     cudaError_t e = cudaSuccess;
-#define GB_ST(call)                                 \
-    do {                                            \
-        if ((e = (call)) != cudaSuccess) return stop(cuda_fail(e, #call)); \
-    } while (0)
-    GB_ST(gb_launch_select(p->E[cur], count, h.active, p->K, gub, p->tol_f, p->st, p->sc, s));
-    GB_ST(gb_launch_partition(p->E[cur], count, gub, p->tol_f, p->E[1 - cur], p->par, p->pool, p->st, p->sc, s));
-    GB_ST(gb_launch_prep(p->P, p->pool, p->par, npar, p->sp, p->st, s));
-    const bool tab = p->use_tabs;
-    if (tab) GB_ST(gb_launch_ptab(p->P, p->pool, p->par, p->tabs, npar, p->sp, s));
-    if (p->opt.fp32_prefilter) {
-        GB_ST(cudaEventRecord(p->ev[4], s));
-        if (tab) GB_ST(gb_launch_eval32_tab(p->P, p->pool, p->par, p->tabs, p->ch, nch, p->sp, gub, p->st, s));
-        else GB_ST(gb_launch_eval32(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, p->st, s));
-        GB_ST(cudaEventRecord(p->ev[5], s));
-        GB_ST(gb_launch_compact_children(p->ch, nch, 0, p->st, p->sc, s));
-        GB_ST(cudaEventRecord(p->ev[2], s));
-        if (tab) GB_ST(gb_launch_eval64_tab(p->P, p->pool, p->par, p->tabs, p->ch, nch, p->sp, gub, true, p->st, s));
-        else GB_ST(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, true, p->st, s));
-        GB_ST(cudaEventRecord(p->ev[3], s));
-        R.timed32 = true;
+    const int G = p->opt.gens_per_sync;
+    if (G > 1) {
+        if ((e = capture_graphs(p)) != cudaSuccess) return stop(cuda_fail(e, "graph capture"));
+        for (int k = 0; k < G; k++) {
+            if ((e = cudaGraphLaunch(p->gexec[(cur + k) & 1], s)) != cudaSuccess)
+                return stop(cuda_fail(e, "cudaGraphLaunch"));
+            R.launches += p->graph_kernels;
+        }
     } else {
-        GB_ST(cudaEventRecord(p->ev[2], s));
-        if (tab) GB_ST(gb_launch_eval64_tab(p->P, p->pool, p->par, p->tabs, p->ch, nch, p->sp, gub, false, p->st, s));
-        else GB_ST(gb_launch_eval64(p->P, p->pool, p->par, p->ch, nch, p->sp, gub, false, p->st, s));
-        GB_ST(cudaEventRecord(p->ev[3], s));
+        long long nl = 0;
+        e = gb_launch_generation(p->P, p->pool, p->E[cur], p->E[1 - cur], p->par, p->ch, p->sp, p->sc,
+                                 p->use_tabs ? &p->tabs : nullptr, p->G, p->cap, p->Cmax, p->st, s, &p->ev[2], &nl);
+        if (e != cudaSuccess) return stop(cuda_fail(e, "generation launch"));
+        R.timed64 = true;
+        R.timed32 = p->opt.fp32_prefilter != 0;
+        R.launches += gb_launches_so_far() - l0;
     }
-    R.timed64 = true;
-    GB_ST(gb_launch_compact_children(p->ch, nch, 1, p->st, p->sc, s));
-    GB_ST(gb_launch_materialize(p->P, p->pool, p->par, p->ch, nch, p->sp, p->E[1 - cur], p->opt.tol_x, p->st, s,
-                                tab ? &p->tabs : nullptr));
-    GB_ST(gb_launch_finish(p->par, npar, p->pool, p->E[1 - cur], p->st, s));
-    R.cur = 1 - cur;
-    R.last_par = npar;
-    long long bound = count + nch;
-    GB_ST(gb_launch_stats(p->E[R.cur], bound < p->cap ? bound : p->cap, p->tol_f, p->st, s));
-    GB_ST(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
-    GB_ST(cudaEventRecord(p->ev_state, s));
-#undef GB_ST
-    R.launches += (gb_launches_so_far() + gb_tab_launches_so_far()) - l0;
+    if ((e = cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return stop(cuda_fail(e, "state readback"));
+    if ((e = cudaEventRecord(p->ev_state, s)) != cudaSuccess) return stop(cuda_fail(e, "event"));
     return 0;
 }
 
@@ -514,11 +520,11 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
     SolveRun& R = p->run;
     std::memset(out, 0, sizeof(*out));
     GB_CU(cudaSetDevice(p->device));
-    const long long l0 = (gb_launches_so_far() + gb_tab_launches_so_far());
+    const long long l0 = gb_launches_so_far();
     cudaStream_t s = p->stream;
     GB_CU(cudaStreamSynchronize(s));
     GbState h = *p->st_host;
-    const int cur = R.cur;
+    const int cur = (int)(h.gen & 1);
     double gub = gb_key_value(h.gub_key);
     unsigned long long ones = ~0ull;
     GB_CU(cudaMemcpyAsync(&p->st->glb_key, &ones, sizeof(ones), cudaMemcpyHostToDevice, s));
@@ -566,14 +572,16 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
         GB_CU(cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
         out->device_ms = ms;
     }
-    R.launches += (gb_launches_so_far() + gb_tab_launches_so_far()) - l0;
+    R.launches += gb_launches_so_far() - l0;
     out->kernel_launches = R.launches;
     out->ops64 = (int64_t)hf.ops64;
     out->ops32 = (int64_t)hf.ops32;
-    out->n_trace = (int64_t)R.trace.size();
-    if (!R.trace.empty()) {
-        out->trace = (gb_gen_stat*)std::malloc(R.trace.size() * sizeof(gb_gen_stat));
-        std::memcpy(out->trace, R.trace.data(), R.trace.size() * sizeof(gb_gen_stat));
+    const long long nt = hf.gen < p->G.trace_cap ? hf.gen : p->G.trace_cap;
+    out->n_trace = nt;
+    if (nt > 0) {
+        out->trace = (gb_gen_stat*)std::malloc((size_t)nt * sizeof(gb_gen_stat));
+        if (!out->trace) return fail(GB_E_OOM, "host allocation");
+        GB_CU(cudaMemcpy(out->trace, p->trace_dev, (size_t)nt * sizeof(gb_gen_stat), cudaMemcpyDeviceToHost));
     }
     out->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - R.t0).count();
     out->status = R.status;

@@ -180,6 +180,9 @@ struct GbState {
     unsigned long long glb_key;     // min lower bound over the pool (final pass)
     int overflow;               // survivors do not fit: generation abandoned
     int error;                  // device-side error code (bit flags)
+    int halt;                   // set at the start of a generation that must not run
+    int sel_mode;               // selection: 0 all active, 1 minimum key (K = 1), 2 radix select
+    long long nch;              // children of this generation (parents * fan-out)
     long long evals32, evals64, mids;  // running counters
     unsigned long long ops64, ops32;   // directed-rounding operations executed by the eval kernels
 };

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "gb_child.cuh"
 #include "gb_eval.cuh"
 #include "gb_launch.h"
@@ -111,9 +113,18 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, GbState* st) {
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_stats(GbEntries E, double tol_f, GbState* st) {
+// Every kernel of a generation reads its sizes (pool size, parents, children)
+// and the incumbent GUB from the device state, so the launch sequence of a
+// generation is fixed and can be replayed from a CUDA graph; a generation that
+// must not run (no active box, limit reached, overflow, error) is skipped by
+// every kernel through st->halt.
+
+__device__ __forceinline__ double gub_of(const GbState* st) { return gb_key_value(st->gub_key); }
+
+__global__ void k_stats(GbEntries E, GbGenConst G, GbState* st) {
+    if (st->halt) return;
     const long long count = st->pool;
-    const double thr = thr_of(gb_key_value(st->gub_key), tol_f);
+    const double thr = thr_of(gub_of(st), G.tol_f);
     long long c = 0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
          q += (long long)gridDim.x * blockDim.x) {
@@ -124,30 +135,39 @@ __global__ void k_stats(GbEntries E, double tol_f, GbState* st) {
     if ((threadIdx.x & 31) == 0 && c) atomicAdd((unsigned long long*)&st->active, (unsigned long long)c);
 }
 
-// ---------------------------------------------------------------------------
-// Radix select (16-bit digits, 4 passes) of the K-th smallest active key.
-__global__ void k_radix_init(GbState* st, long long K) {
-    st->radix_prefix = 0;
-    st->radix_rank = K;
-    st->sel_below = 0;
-}
-
-__global__ void k_select_all(GbState* st) {
-    st->sel_T = ~0ull;
-    st->sel_below = st->active;
-    st->sel_need = 0;
+// Start of a generation: stop if nothing is active or a limit was reached;
+// otherwise choose the selection (all active boxes if at most K, the minimum
+// key when K = 1, else a radix select of the K-th smallest key).
+__global__ void k_gen_begin(GbGenConst G, GbState* st) {
+    if (st->halt) return;
+    if (st->active == 0 || st->gen >= G.max_gen || st->overflow || st->error) {
+        st->halt = 1;
+        return;
+    }
+    if (st->active <= G.K) {
+        st->sel_mode = 0;
+        st->sel_T = ~0ull;
+        st->sel_below = st->active;
+        st->sel_need = 0;
+    } else if (G.K == 1) {
+        st->sel_mode = 1;
+        st->sel_T = ~0ull - 1;   // replaced by the minimum active key
+        st->sel_below = 0;
+        st->sel_need = 1;
+    } else {
+        st->sel_mode = 2;
+        st->radix_prefix = 0;
+        st->radix_rank = G.K;
+        st->sel_below = 0;
+    }
 }
 
 // K = 1: the threshold is the smallest active key (the partition then takes
 // the most recently inserted box among those with that key).
-__global__ void k_min_init(GbState* st) {
-    st->sel_T = ~0ull - 1;   // replaced by the minimum below (there is at least one active box)
-    st->sel_below = 0;
-    st->sel_need = 1;
-}
-
-__global__ void k_min_key(GbEntries E, long long count, double gub, double tol_f, GbState* st) {
-    const double thr = thr_of(gub, tol_f);
+__global__ void k_min_key(GbEntries E, GbGenConst G, GbState* st) {
+    if (st->halt || st->sel_mode != 1) return;
+    const long long count = st->pool;
+    const double thr = thr_of(gub_of(st), G.tol_f);
     unsigned long long kmin = ~0ull;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
          q += (long long)gridDim.x * blockDim.x) {
@@ -163,9 +183,11 @@ __global__ void k_min_key(GbEntries E, long long count, double gub, double tol_f
     if ((threadIdx.x & 31) == 0 && kmin != ~0ull) atomicMin(&st->sel_T, kmin);
 }
 
-__global__ void k_radix_hist(GbEntries E, long long count, double gub, double tol_f, int pass,
-                             const GbState* st, unsigned* hist) {
-    const double thr = thr_of(gub, tol_f);
+// Radix select (16-bit digits, 4 passes) of the K-th smallest active key.
+__global__ void k_radix_hist(GbEntries E, GbGenConst G, int pass, const GbState* st, unsigned* hist) {
+    if (st->halt || st->sel_mode != 2) return;
+    const long long count = st->pool;
+    const double thr = thr_of(gub_of(st), G.tol_f);
     const unsigned long long prefix = st->radix_prefix;
     const int shift = 48 - 16 * pass;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
@@ -182,6 +204,7 @@ __global__ void k_radix_hist(GbEntries E, long long count, double gub, double to
 // coalesced warp totals, a scan over the 32 totals, then the owning warp
 // walks its chunk 32 bins at a time.  Clears the histogram for the next pass.
 __global__ void __launch_bounds__(1024) k_radix_pick(int pass, GbState* st, unsigned* hist) {
+    if (st->halt || st->sel_mode != 2) return;
     __shared__ long long wtot[32];
     __shared__ long long wpre[33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -252,33 +275,44 @@ __device__ __forceinline__ PartFlags part_flags(const GbEntries& E, long long q,
 
 constexpr int PT = 256;  // threads per partition / compaction block; tile = 4 rounds
 
-__global__ void k_part_count(GbEntries E, long long count, double gub, double tol_f, const GbState* st,
-                             int* tile_cnt, int max_tiles) {
+__device__ __forceinline__ long long ntiles_of(long long items) { return (items + GB_TILE - 1) / GB_TILE; }
+
+__global__ void k_part_count(GbEntries E, GbGenConst G, const GbState* st, int* tile_cnt, int max_tiles) {
+    if (st->halt) return;
     __shared__ int sw[PT / 32 + 1];
-    const double thr = thr_of(gub, tol_f);
+    const long long count = st->pool;
+    const double gub = gub_of(st);
+    const double thr = thr_of(gub, G.tol_f);
     const unsigned long long T = st->sel_T;
-    const long long base = (long long)blockIdx.x * GB_TILE;
-    int cd = 0, cb = 0, ct = 0, tot;
-    for (int r = 0; r < GB_TILE / PT; r++) {
-        PartFlags f = part_flags(E, base + r * PT + threadIdx.x, count, gub, thr, T);
-        block_prefix<PT>(f.drop, sw, &tot); cd += tot;
-        block_prefix<PT>(f.below, sw, &tot); cb += tot;
-        block_prefix<PT>(f.tie, sw, &tot); ct += tot;
-    }
-    if (threadIdx.x == 0) {
-        tile_cnt[blockIdx.x] = cd;
-        tile_cnt[max_tiles + blockIdx.x] = cb;
-        tile_cnt[2 * max_tiles + blockIdx.x] = ct;
+    const long long nt = ntiles_of(count);
+    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        const long long base = tile * GB_TILE;
+        int cd = 0, cb = 0, ct = 0, tot;
+        for (int r = 0; r < GB_TILE / PT; r++) {
+            PartFlags f = part_flags(E, base + r * PT + threadIdx.x, count, gub, thr, T);
+            block_prefix<PT>(f.drop, sw, &tot); cd += tot;
+            block_prefix<PT>(f.below, sw, &tot); cb += tot;
+            block_prefix<PT>(f.tie, sw, &tot); ct += tot;
+        }
+        if (threadIdx.x == 0) {
+            tile_cnt[tile] = cd;
+            tile_cnt[max_tiles + tile] = cb;
+            tile_cnt[2 * max_tiles + tile] = ct;
+        }
     }
 }
 
 // Exclusive scan of up to 3 arrays of tile counts (one block of 1024
 // threads, each owning a contiguous run of tiles).
-// what: 0 = partition (3 arrays), 1 = FP32 list, 2 = survivors, 3 = output.
-__global__ void __launch_bounds__(1024) k_scan_tiles(int ntiles, int narr, const int* tile_cnt, int* tile_off,
-                                                     int max_tiles, int what, long long count, GbState* st) {
+// what: 0 = partition (3 arrays, items = pool), 1 = FP32 list and 2 =
+// survivors (items = children of the generation), 3 = output (items = count).
+__global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_cnt, int* tile_off, int max_tiles,
+                                                     int what, long long out_count, GbGenConst G, GbState* st) {
+    if (what != 3 && st->halt) return;
     __shared__ long long part[1024];
     __shared__ long long tot[3];
+    const long long items = what == 0 ? st->pool : (what == 3 ? out_count : st->nch);
+    const int ntiles = (int)ntiles_of(items);
     const int t = threadIdx.x;
     const int per = (ntiles + 1023) / 1024;
     for (int a = 0; a < narr; a++) {
@@ -309,7 +343,8 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int ntiles, int narr, const
         long long need = st->sel_T == ~0ull ? 0 : st->sel_need;
         st->drops = D;
         st->parents = Bl + need;
-        st->kept_old = count - D - (Bl + need);
+        st->nch = (Bl + need) << G.flog2;
+        st->kept_old = items - D - (Bl + need);
         st->nfree_after_drop = st->nfree + D;
         st->sel_below = Bl;
         st->sel_ties = Ti;
@@ -326,41 +361,46 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int ntiles, int narr, const
     }
 }
 
-__global__ void k_part_scatter(GbEntries E, long long count, double gub, double tol_f, const GbState* st,
-                               const int* tile_off, int max_tiles, GbEntries En, GbParents par,
-                               unsigned* freel) {
+__global__ void k_part_scatter(GbEntries E, GbGenConst G, const GbState* st, const int* tile_off, int max_tiles,
+                               GbEntries En, GbParents par, unsigned* freel) {
+    if (st->halt) return;
     __shared__ int sw[PT / 32 + 1];
-    const double thr = thr_of(gub, tol_f);
+    const long long count = st->pool;
+    const double gub = gub_of(st);
+    const double thr = thr_of(gub, G.tol_f);
     const unsigned long long T = st->sel_T;
     const long long need = (T == ~0ull) ? 0 : st->sel_need;
     const long long Ti = st->sel_ties;
     const long long nfree = st->nfree;
-    long long od = tile_off[blockIdx.x];
-    long long ob = tile_off[max_tiles + blockIdx.x];
-    long long ot = tile_off[2 * max_tiles + blockIdx.x];
-    const long long base = (long long)blockIdx.x * GB_TILE;
-    for (int r = 0; r < GB_TILE / PT; r++) {
-        long long q = base + r * PT + threadIdx.x;
-        PartFlags f = part_flags(E, q, count, gub, thr, T);
-        int td, tb, tt;
-        long long rd = od + block_prefix<PT>(f.drop, sw, &td);
-        long long rb = ob + block_prefix<PT>(f.below, sw, &tb);
-        long long rt = ot + block_prefix<PT>(f.tie, sw, &tt);
-        od += td; ob += tb; ot += tt;
-        if (q >= count) continue;
-        long long sel_before = rb + max(0LL, rt - (Ti - need));
-        bool sel = f.below || (f.tie && rt >= Ti - need);
-        if (f.drop) {
-            freel[nfree + rd] = E.slot[q];
-        } else if (sel) {
-            par.slot[sel_before] = E.slot[q];
-            par.cyc[sel_before] = E.cyc[q];
-            par.flo[sel_before] = E.flo[q];
-        } else {
-            long long kr = q - rd - sel_before;
-            En.flo[kr] = E.flo[q];
-            En.slot[kr] = E.slot[q];
-            En.cyc[kr] = E.cyc[q];
+    const long long nt = ntiles_of(count);
+    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        long long od = tile_off[tile];
+        long long ob = tile_off[max_tiles + tile];
+        long long ot = tile_off[2 * max_tiles + tile];
+        const long long base = tile * GB_TILE;
+        for (int r = 0; r < GB_TILE / PT; r++) {
+            long long q = base + r * PT + threadIdx.x;
+            PartFlags f = part_flags(E, q, count, gub, thr, T);
+            int td, tb, tt;
+            long long rd = od + block_prefix<PT>(f.drop, sw, &td);
+            long long rb = ob + block_prefix<PT>(f.below, sw, &tb);
+            long long rt = ot + block_prefix<PT>(f.tie, sw, &tt);
+            od += td; ob += tb; ot += tt;
+            if (q >= count) continue;
+            long long sel_before = rb + max(0LL, rt - (Ti - need));
+            bool sel = f.below || (f.tie && rt >= Ti - need);
+            if (f.drop) {
+                freel[nfree + rd] = E.slot[q];
+            } else if (sel) {
+                par.slot[sel_before] = E.slot[q];
+                par.cyc[sel_before] = E.cyc[q];
+                par.flo[sel_before] = E.flo[q];
+            } else {
+                long long kr = q - rd - sel_before;
+                En.flo[kr] = E.flo[q];
+                En.slot[kr] = E.slot[q];
+                En.cyc[kr] = E.cyc[q];
+            }
         }
     }
 }
@@ -369,7 +409,8 @@ __global__ void k_part_scatter(GbEntries E, long long count, double gub, double 
 // Per parent: split coordinates and piece boundaries (Eqs. 10-11 with the
 // rounding reading: boundary t = RN(lo + RN(RN(RN(hi - lo) / m) * t)),
 // boundary 0 = lo, boundary m = hi).
-__global__ void k_prep(GbProg P, GbPool pool, GbParents par, long long npar, GbSplit sp, GbState* st) {
+__global__ void k_prep(GbProg P, GbPool pool, GbParents par, GbSplit sp, GbState* st) {
+    if (st->halt) return;
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p == 0) {
         st->gub_new_key = st->gub_key;
@@ -380,6 +421,7 @@ __global__ void k_prep(GbProg P, GbPool pool, GbParents par, long long npar, GbS
         st->children = 0;
         st->overflow = 0;
     }
+    const long long npar = st->parents;
     if (p >= npar) return;
     const int n = P.n, B = P.B;
     int c = par.cyc[p] & 0x7fffffff;
@@ -435,10 +477,11 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
     return true;
 }
 
-__global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents par, GbChildren ch,
-                                                long long nchildren, GbSplit sp, double gub_prev,
+__global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents par, GbChildren ch, GbSplit sp,
                                                 int from_list, GbState* st) {
-    const long long lim = from_list ? st->n32 : nchildren;
+    if (st->halt) return;
+    const long long lim = from_list ? st->n32 : st->nch;
+    const double gub_prev = gub_of(st);
     const long long stride = (long long)gridDim.x * blockDim.x;
     // warp-uniform loop: every lane of a warp runs the same iterations
     for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < lim; base += stride) {
@@ -464,36 +507,41 @@ __global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents
 
 // FP32 prefilter: F(X) and the first-order test in FP32 directed rounding,
 // cut-off against the GUB of the previous generation.
-__global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents par, GbChildren ch,
-                                                long long nchildren, GbSplit sp, double gub_prev,
+__global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents par, GbChildren ch, GbSplit sp,
                                                 GbState* st) {
-    long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    bool valid = false;
-    int ops = 0;
-    if (ci < nchildren) {
-        ChildCtx c = child_ctx(par, ci, sp);
-        ch.flag[ci] = 0;
-        ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
-        if (c.valid) {
-            valid = true;
-            View<float> X = view32(pool, par, c, sp);
-            View<double> X64 = view64(pool, par, c, sp);
-            iv32 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
-            const int blk = c.info.z;
-            sum_values<float>(P, blk, X, pool.gsum32 + (size_t)c.slot * pool.NG, R, sums, ops);
-            iv32 F = outer_fwd<float>(P, X, sums, O, ops);
-            bool keep = !((double)F.lo > gub_prev);
-            if (keep) keep = !block_mono<float>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr, ops);
-            ch.flag32[ci] = keep ? 1 : 0;
-        } else {
-            ch.flag32[ci] = 0;
+    if (st->halt) return;
+    const long long lim = st->nch;
+    const double gub_prev = gub_of(st);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < lim; base += stride) {
+        long long ci = base + (threadIdx.x & 31);
+        bool valid = false;
+        int ops = 0;
+        if (ci < lim) {
+            ChildCtx c = child_ctx(par, ci, sp);
+            ch.flag[ci] = 0;
+            ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
+            if (c.valid) {
+                valid = true;
+                View<float> X = view32(pool, par, c, sp);
+                View<double> X64 = view64(pool, par, c, sp);
+                iv32 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+                const int blk = c.info.z;
+                sum_values<float>(P, blk, X, pool.gsum32 + (size_t)c.slot * pool.NG, R, sums, ops);
+                iv32 F = outer_fwd<float>(P, X, sums, O, ops);
+                bool keep = !((double)F.lo > gub_prev);
+                if (keep) keep = !block_mono<float>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr, ops);
+                ch.flag32[ci] = keep ? 1 : 0;
+            } else {
+                ch.flag32[ci] = 0;
+            }
         }
-    }
-    warp_add_ops(ops, &st->ops32);
-    unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
-    if ((threadIdx.x & 31) == 0 && nv) {
-        atomicAdd((unsigned long long*)&st->evals32, (unsigned long long)nv);
-        atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+        warp_add_ops(ops, &st->ops32);
+        unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
+        if ((threadIdx.x & 31) == 0 && nv) {
+            atomicAdd((unsigned long long*)&st->evals32, (unsigned long long)nv);
+            atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+        }
     }
 }
 
@@ -506,31 +554,40 @@ __device__ __forceinline__ bool child_pred(const GbChildren& ch, long long i, lo
     return ch.flag[i] != 0 && !(ch.flo[i] > gub_new);
 }
 
-__global__ void k_cc_count(GbChildren ch, long long n, int mode, const GbState* st, int* tile_cnt) {
+__global__ void k_cc_count(GbChildren ch, int mode, const GbState* st, int* tile_cnt) {
+    if (st->halt) return;
     __shared__ int sw[PT / 32 + 1];
+    const long long n = st->nch;
     const double gub_new = gb_key_value(st->gub_new_key);
-    const long long base = (long long)blockIdx.x * GB_TILE;
-    int acc = 0, tot;
-    for (int r = 0; r < GB_TILE / PT; r++) {
-        block_prefix<PT>(child_pred(ch, base + r * PT + threadIdx.x, n, mode, gub_new), sw, &tot);
-        acc += tot;
+    const long long nt = ntiles_of(n);
+    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        const long long base = tile * GB_TILE;
+        int acc = 0, tot;
+        for (int r = 0; r < GB_TILE / PT; r++) {
+            block_prefix<PT>(child_pred(ch, base + r * PT + threadIdx.x, n, mode, gub_new), sw, &tot);
+            acc += tot;
+        }
+        if (threadIdx.x == 0) tile_cnt[tile] = acc;
     }
-    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = acc;
 }
 
-__global__ void k_cc_scatter(GbChildren ch, long long n, int mode, const GbState* st, const int* tile_off,
-                             unsigned* out) {
+__global__ void k_cc_scatter(GbChildren ch, int mode, const GbState* st, const int* tile_off, unsigned* out) {
+    if (st->halt) return;
     __shared__ int sw[PT / 32 + 1];
+    const long long n = st->nch;
     const double gub_new = gb_key_value(st->gub_new_key);
-    const long long base = (long long)blockIdx.x * GB_TILE;
-    long long o = tile_off[blockIdx.x];
-    for (int r = 0; r < GB_TILE / PT; r++) {
-        long long i = base + r * PT + threadIdx.x;
-        bool f = child_pred(ch, i, n, mode, gub_new);
-        int tot;
-        int rk = block_prefix<PT>(f, sw, &tot);
-        if (f) out[o + rk] = (unsigned)i;
-        o += tot;
+    const long long nt = ntiles_of(n);
+    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        const long long base = tile * GB_TILE;
+        long long o = tile_off[tile];
+        for (int r = 0; r < GB_TILE / PT; r++) {
+            long long i = base + r * PT + threadIdx.x;
+            bool f = child_pred(ch, i, n, mode, gub_new);
+            int tot;
+            int rk = block_prefix<PT>(f, sw, &tot);
+            if (f) out[o + rk] = (unsigned)i;
+            o += tot;
+        }
     }
 }
 
@@ -613,7 +670,7 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
                                                      GbSplit sp, GbEntries En, double tol_x, GbState* st,
                                                      GbTabs Tb, int tab) {
     const int lane = threadIdx.x & 31;
-    if (st->overflow) return;
+    if (st->halt || st->overflow) return;
     const long long kept = st->kept;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < kept; s += nwarps)
@@ -622,22 +679,27 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
 
 // Parents' slots back to the free list, or (on overflow) the parents back
 // into the pool after the carried-over entries.
-__global__ void k_free_parents(GbParents par, long long npar, GbPool pool, GbEntries En, GbState* st) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= npar) return;
-    if (st->overflow) {
-        long long e = st->kept_old + p;
-        En.flo[e] = par.flo[p];
-        En.slot[e] = par.slot[p];
-        En.cyc[e] = par.cyc[p];
-        return;
+__global__ void k_free_parents(GbParents par, GbPool pool, GbEntries En, GbState* st) {
+    if (st->halt) return;
+    const long long npar = st->parents;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npar;
+         p += (long long)gridDim.x * blockDim.x) {
+        if (st->overflow) {
+            long long e = st->kept_old + p;
+            En.flo[e] = par.flo[p];
+            En.slot[e] = par.slot[p];
+            En.cyc[e] = par.cyc[p];
+            continue;
+        }
+        long long kept = st->kept, nfree = st->nfree;
+        long long base = kept < nfree ? nfree - kept : 0;
+        pool.freel[base + p] = par.slot[p];
     }
-    long long kept = st->kept, nfree = st->nfree;
-    long long base = kept < nfree ? nfree - kept : 0;
-    pool.freel[base + p] = par.slot[p];
 }
 
-__global__ void k_finish(long long npar, GbState* st) {
+__global__ void k_finish(GbGenConst G, GbState* st) {
+    if (st->halt) return;
+    const long long npar = st->parents;
     long long kept = st->kept, nfree = st->nfree;
     if (st->overflow) {
         st->pool = st->kept_old + npar;
@@ -649,6 +711,16 @@ __global__ void k_finish(long long npar, GbState* st) {
         st->pool = st->kept_old + kept;
     }
     st->gub_key = st->gub_new_key;
+    if (G.trace && st->gen < G.trace_cap) {
+        gb_gen_stat row;
+        row.parents = npar;
+        row.children = st->children;
+        row.kept32 = G.fp32 ? st->kept32 : st->children;
+        row.kept = st->overflow ? 0 : st->kept;
+        row.pool = st->pool;
+        row.gub = gb_key_value(st->gub_key);
+        G.trace[st->gen] = row;
+    }
     st->gen += 1;
     st->active = 0;
 }
@@ -790,116 +862,86 @@ cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEnt
     return cudaGetLastError();
 }
 
-cudaError_t gb_launch_stats(const GbEntries& E, long long max_count, double tol_f, GbState* st, cudaStream_t s) {
-    unsigned g = grid_for(max_count, 256);
-    if (g > 152 * 16) g = 152 * 16;
+cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, GbState* st, cudaStream_t s) {
+    unsigned g = grid_for(cap, 256);
+    if (g > 152 * 8) g = 152 * 8;
     gb_launch_count++;
-    k_stats<<<g, 256, 0, s>>>(E, tol_f, st);
+    k_stats<<<g, 256, 0, s>>>(E, G, st);
     return cudaGetLastError();
 }
 
-cudaError_t gb_launch_select(const GbEntries& E, long long count, long long active, long long K, double gub,
-                             double tol_f, GbState* st, const GbScan& sc, cudaStream_t s) {
-    if (active <= K) {
+cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEntries& E, const GbEntries& E_new,
+                                 const GbParents& par, const GbChildren& ch, const GbSplit& sp, const GbScan& sc,
+                                 const GbTabs* tabs, const GbGenConst& G, long long cap, long long Cmax,
+                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch) {
+    long long n0 = gb_launch_count;
+    cudaError_t e;
+    const unsigned gpool = (unsigned)std::min<long long>(grid_for(cap, 256), 152 * 8);
+    const unsigned gtile_pool = (unsigned)std::min<long long>(grid_for(cap, GB_TILE), 152 * 8);
+    const unsigned gtile_ch = (unsigned)std::min<long long>(grid_for(Cmax, GB_TILE), 152 * 8);
+    const unsigned gch = (unsigned)std::min<long long>(grid_for(Cmax, 128), 152 * 32);
+    gb_launch_count++;
+    k_gen_begin<<<1, 1, 0, s>>>(G, st);
+    if (G.K == 1) {
         gb_launch_count++;
-        k_select_all<<<1, 1, 0, s>>>(st);
-        return cudaGetLastError();
+        k_min_key<<<gpool, 256, 0, s>>>(E, G, st);
+    } else {
+        for (int pass = 0; pass < 4; pass++) {
+            gb_launch_count += 2;
+            k_radix_hist<<<gpool, 256, 0, s>>>(E, G, pass, st, sc.hist);
+            k_radix_pick<<<1, 1024, 0, s>>>(pass, st, sc.hist);
+        }
     }
-    if (K == 1) {
-        unsigned g1 = grid_for(count, 256);
-        if (g1 > 152 * 8) g1 = 152 * 8;
+    gb_launch_count += 3;
+    k_part_count<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_cnt, sc.max_tiles);
+    k_scan_tiles<<<1, 1024, 0, s>>>(3, sc.tile_cnt, sc.tile_off, sc.max_tiles, 0, 0, G, st);
+    k_part_scatter<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_off, sc.max_tiles, E_new, par, pool.freel);
+    gb_launch_count++;
+    k_prep<<<grid_for(G.K, 128), 128, 0, s>>>(P, pool, par, sp, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (tabs) {
         gb_launch_count++;
-        k_min_init<<<1, 1, 0, s>>>(st);
-        gb_launch_count++;
-        k_min_key<<<g1, 256, 0, s>>>(E, count, gub, tol_f, st);
-        return cudaGetLastError();
+        if ((e = gb_launch_ptab(P, pool, par, *tabs, G.K, sp, st, s)) != cudaSuccess) return e;
     }
-    gb_launch_count++;
-    k_radix_init<<<1, 1, 0, s>>>(st, K);
-    unsigned g = grid_for(count, 256);
-    if (g > 152 * 16) g = 152 * 16;
-    for (int pass = 0; pass < 4; pass++) {
-        gb_launch_count++;
-        k_radix_hist<<<g, 256, 0, s>>>(E, count, gub, tol_f, pass, st, sc.hist);
-        gb_launch_count++;
-        k_radix_pick<<<1, 1024, 0, s>>>(pass, st, sc.hist);
+    if (G.fp32) {
+        if (ev) cudaEventRecord(ev[2], s);
+        if (tabs) {
+            gb_launch_count++;
+            if ((e = gb_launch_eval32_tab(P, pool, par, *tabs, ch, Cmax, sp, st, s)) != cudaSuccess) return e;
+        } else {
+            gb_launch_count++;
+            k_eval32<<<gch, 128, 0, s>>>(P, pool, par, ch, sp, st);
+        }
+        if (ev) cudaEventRecord(ev[3], s);
+        gb_launch_count += 3;
+        k_cc_count<<<gtile_ch, PT, 0, s>>>(ch, 0, st, sc.tile_cnt);
+        k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 1, 0, G, st);
+        k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 0, st, sc.tile_off, ch.list32);
     }
-    return cudaGetLastError();
-}
-
-cudaError_t gb_launch_partition(const GbEntries& E, long long count, double gub, double tol_f,
-                                const GbEntries& E_new, const GbParents& par, const GbPool& pool, GbState* st,
-                                const GbScan& sc, cudaStream_t s) {
-    unsigned tiles = grid_for(count, GB_TILE);
-    if ((int)tiles > sc.max_tiles) return cudaErrorInvalidValue;
-    gb_launch_count++;
-    k_part_count<<<tiles, PT, 0, s>>>(E, count, gub, tol_f, st, sc.tile_cnt, sc.max_tiles);
-    gb_launch_count++;
-    k_scan_tiles<<<1, 1024, 0, s>>>(tiles, 3, sc.tile_cnt, sc.tile_off, sc.max_tiles, 0, count, st);
-    gb_launch_count++;
-    k_part_scatter<<<tiles, PT, 0, s>>>(E, count, gub, tol_f, st, sc.tile_off, sc.max_tiles, E_new, par,
-                                        pool.freel);
-    return cudaGetLastError();
-}
-
-cudaError_t gb_launch_prep(const GbProg& P, const GbPool& pool, const GbParents& par, long long npar,
-                           const GbSplit& sp, GbState* st, cudaStream_t s) {
-    gb_launch_count++;
-    k_prep<<<grid_for(npar, 128), 128, 0, s>>>(P, pool, par, npar, sp, st);
-    return cudaGetLastError();
-}
-
-cudaError_t gb_launch_eval64(const GbProg& P, const GbPool& pool, const GbParents& par, const GbChildren& ch,
-                             long long nchildren, const GbSplit& sp, double gub_prev, bool from_list,
-                             GbState* st, cudaStream_t s) {
-    gb_launch_count++;
-    unsigned g = grid_for(nchildren, 128);
-    if (from_list && g > 152 * 16) g = 152 * 16;
-    k_eval64<<<g, 128, 0, s>>>(P, pool, par, ch, nchildren, sp, gub_prev, from_list ? 1 : 0, st);
-    return cudaGetLastError();
-}
-
-cudaError_t gb_launch_eval32(const GbProg& P, const GbPool& pool, const GbParents& par, const GbChildren& ch,
-                             long long nchildren, const GbSplit& sp, double gub_prev, GbState* st,
-                             cudaStream_t s) {
-    gb_launch_count++;
-    k_eval32<<<grid_for(nchildren, 128), 128, 0, s>>>(P, pool, par, ch, nchildren, sp, gub_prev, st);
-    return cudaGetLastError();
-}
-
-cudaError_t gb_launch_compact_children(const GbChildren& ch, long long nchildren, int mode, GbState* st,
-                                       const GbScan& sc, cudaStream_t s) {
-    unsigned tiles = grid_for(nchildren, GB_TILE);
-    if ((int)tiles > sc.max_tiles) return cudaErrorInvalidValue;
-    gb_launch_count++;
-    k_cc_count<<<tiles, PT, 0, s>>>(ch, nchildren, mode, st, sc.tile_cnt);
-    gb_launch_count++;
-    k_scan_tiles<<<1, 1024, 0, s>>>(tiles, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, mode == 0 ? 1 : 2,
-                                  nchildren, st);
-    gb_launch_count++;
-    k_cc_scatter<<<tiles, PT, 0, s>>>(ch, nchildren, mode, st, sc.tile_off, mode == 0 ? ch.list32 : ch.surv);
-    return cudaGetLastError();
-}
-
-cudaError_t gb_launch_materialize(const GbProg& P, const GbPool& pool, const GbParents& par,
-                                  const GbChildren& ch, long long nchildren, const GbSplit& sp,
-                                  const GbEntries& E_new, double tol_x, GbState* st, cudaStream_t s,
-                                  const GbTabs* tabs) {
+    if (ev) cudaEventRecord(ev[0], s);
+    if (tabs) {
+        gb_launch_count++;
+        if ((e = gb_launch_eval64_tab(P, pool, par, *tabs, ch, Cmax, sp, G.fp32 != 0, st, s)) != cudaSuccess)
+            return e;
+    } else {
+        gb_launch_count++;
+        k_eval64<<<gch, 128, 0, s>>>(P, pool, par, ch, sp, G.fp32, st);
+    }
+    if (ev) cudaEventRecord(ev[1], s);
+    gb_launch_count += 3;
+    k_cc_count<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_cnt);
+    k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 2, 0, G, st);
+    k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_off, ch.surv);
     GbTabs Tb{};
     if (tabs) Tb = *tabs;
     gb_launch_count++;
-    unsigned g = grid_for(nchildren * 32, 128);
-    if (g > 152 * 16) g = 152 * 16;
-    k_materialize<<<g, 128, 0, s>>>(P, pool, par, ch, sp, E_new, tol_x, st, Tb, tabs ? 1 : 0);
-    return cudaGetLastError();
-}
-
-cudaError_t gb_launch_finish(const GbParents& par, long long npar, const GbPool& pool, const GbEntries& E_new,
-                             GbState* st, cudaStream_t s) {
-    gb_launch_count++;
-    k_free_parents<<<grid_for(npar, 256), 256, 0, s>>>(par, npar, pool, E_new, st);
-    gb_launch_count++;
-    k_finish<<<1, 1, 0, s>>>(npar, st);
+    k_materialize<<<(unsigned)std::min<long long>(grid_for(Cmax * 32, 128), 152 * 16), 128, 0, s>>>(
+        P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, tabs ? 1 : 0);
+    gb_launch_count += 2;
+    k_free_parents<<<grid_for(G.K, 256), 256, 0, s>>>(par, pool, E_new, st);
+    k_finish<<<1, 1, 0, s>>>(G, st);
+    if ((e = gb_launch_stats(E_new, G, cap, st, s)) != cudaSuccess) return e;
+    if (nlaunch) *nlaunch = gb_launch_count - n0;
     return cudaGetLastError();
 }
 
@@ -911,7 +953,7 @@ cudaError_t gb_launch_output(const GbEntries& E, long long count, const GbPool& 
     gb_launch_count++;
     k_out_count<<<tiles, PT, 0, s>>>(E, count, gub, sc.tile_cnt, st);
     gb_launch_count++;
-    k_scan_tiles<<<1, 1024, 0, s>>>(tiles, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 3, count, st);
+    k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 3, count, GbGenConst{}, st);
     gb_launch_count++;
     k_out_scatter<<<tiles, PT, 0, s>>>(E, count, gub, sc.tile_off, list);
     if (out_lo) {

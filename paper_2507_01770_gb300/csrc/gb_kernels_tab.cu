@@ -18,8 +18,6 @@ using namespace gb;
 
 namespace {
 
-thread_local long long g_tab_launches = 0;
-
 template <typename T> struct TabPrec;
 template <> struct TabPrec<double> {
     typedef iv64 I;
@@ -39,8 +37,11 @@ __device__ __forceinline__ iv64 mid_node(const GbTabs& T, size_t i) { double2 v 
 
 // ---------------------------------------------------------------------------
 // k_ptab: one block per parent.  Rows: (dirty term, digit combination).
-__global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp) {
+__global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp,
+                                             const GbState* st) {
+    if (st->halt) return;
     const long long p = blockIdx.y;
+    if (p >= st->parents) return;
     const int4 info = par.info[p];
     const unsigned slot = par.slot[p];
     const int spi = P.sp_of_cyc[info.x];
@@ -298,9 +299,10 @@ __device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& 
 }
 
 __global__ void __launch_bounds__(128) k_eval64_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
-                                                    GbChildren ch, long long nchildren, GbSplit sp,
-                                                    double gub_prev, int from_list, GbState* st) {
-    const long long lim = from_list ? st->n32 : nchildren;
+                                                    GbChildren ch, GbSplit sp, int from_list, GbState* st) {
+    if (st->halt) return;
+    const long long lim = from_list ? st->n32 : st->nch;
+    const double gub_prev = gb_key_value(st->gub_key);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < lim; base += stride) {
         long long idx = base + (threadIdx.x & 31);
@@ -323,38 +325,44 @@ __global__ void __launch_bounds__(128) k_eval64_tab(GbProg P, GbPool pool, GbPar
 }
 
 __global__ void __launch_bounds__(128) k_eval32_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
-                                                    GbChildren ch, long long nchildren, GbSplit sp,
-                                                    double gub_prev, GbState* st) {
-    long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    bool valid = false;
-    int ops = 0;
-    if (ci < nchildren) {
-        ChildCtx c = child_ctx(par, ci, sp);
-        ch.flag[ci] = 0;
-        ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
-        const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
-        if (spi >= 0) {
-            valid = true;
-            const GbSplitPos SP = P.sps[spi];
-            const int blk = c.info.z;
-            View<float> X = view32(pool, par, c, sp);
-            View<double> X64 = view64(pool, par, c, sp);
-            iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
-            int dt = SP.dterm0;
-            for (int k = 0; k < P.n_sum; k++) sums[k] = tab_sum<float, false>(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
-            iv32 F = outer_fwd<float>(P, X, sums, O, ops);
-            bool keep = !((double)F.lo > gub_prev);
-            if (keep) keep = !tab_mono<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, ops);
-            ch.flag32[ci] = keep ? 1 : 0;
-        } else {
-            ch.flag32[ci] = 0;
+                                                    GbChildren ch, GbSplit sp, GbState* st) {
+    if (st->halt) return;
+    const long long lim = st->nch;
+    const double gub_prev = gb_key_value(st->gub_key);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < lim; base += stride) {
+        long long ci = base + (threadIdx.x & 31);
+        bool valid = false;
+        int ops = 0;
+        if (ci < lim) {
+            ChildCtx c = child_ctx(par, ci, sp);
+            ch.flag[ci] = 0;
+            ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
+            const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
+            if (spi >= 0) {
+                valid = true;
+                const GbSplitPos SP = P.sps[spi];
+                const int blk = c.info.z;
+                View<float> X = view32(pool, par, c, sp);
+                View<double> X64 = view64(pool, par, c, sp);
+                iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+                int dt = SP.dterm0;
+                for (int k = 0; k < P.n_sum; k++)
+                    sums[k] = tab_sum<float, false>(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
+                iv32 F = outer_fwd<float>(P, X, sums, O, ops);
+                bool keep = !((double)F.lo > gub_prev);
+                if (keep) keep = !tab_mono<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, ops);
+                ch.flag32[ci] = keep ? 1 : 0;
+            } else {
+                ch.flag32[ci] = 0;
+            }
         }
-    }
-    warp_add_ops(ops, &st->ops32);
-    unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
-    if ((threadIdx.x & 31) == 0 && nv) {
-        atomicAdd((unsigned long long*)&st->evals32, (unsigned long long)nv);
-        atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+        warp_add_ops(ops, &st->ops32);
+        unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
+        if ((threadIdx.x & 31) == 0 && nv) {
+            atomicAdd((unsigned long long*)&st->evals32, (unsigned long long)nv);
+            atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+        }
     }
 }
 
@@ -365,31 +373,28 @@ unsigned grid_for(long long items, int per_block) {
 
 }  // namespace
 
-long long gb_tab_launches_so_far() { return g_tab_launches; }
-
 cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                           long long npar, const GbSplit& sp, cudaStream_t s) {
+                           long long K, const GbSplit& sp, GbState* st, cudaStream_t s) {
     // rows of a parent spread over blocks of 64 threads
     const unsigned chunks = (unsigned)((P.max_rows + 63) / 64);
-    g_tab_launches++;
-    k_ptab<<<dim3(chunks < 1 ? 1 : chunks, (unsigned)npar), 64, 0, s>>>(P, pool, par, T, sp);
+    k_ptab<<<dim3(chunks < 1 ? 1 : chunks, (unsigned)K), 64, 0, s>>>(P, pool, par, T, sp, st);
     return cudaGetLastError();
 }
 
 cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                                 const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
-                                 bool from_list, GbState* st, cudaStream_t s) {
-    unsigned g = grid_for(nchildren, 128);
-    if (from_list && g > 152 * 16) g = 152 * 16;
-    g_tab_launches++;
-    k_eval64_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, nchildren, sp, gub_prev, from_list ? 1 : 0, st);
+                                 const GbChildren& ch, long long Cmax, const GbSplit& sp, bool from_list,
+                                 GbState* st, cudaStream_t s) {
+    unsigned g = grid_for(Cmax, 128);
+    if (g > 152 * 32) g = 152 * 32;
+    k_eval64_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
     return cudaGetLastError();
 }
 
 cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                                 const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
-                                 GbState* st, cudaStream_t s) {
-    g_tab_launches++;
-    k_eval32_tab<<<grid_for(nchildren, 128), 128, 0, s>>>(P, pool, par, T, ch, nchildren, sp, gub_prev, st);
+                                 const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
+                                 cudaStream_t s) {
+    unsigned g = grid_for(Cmax, 128);
+    if (g > 152 * 32) g = 152 * 32;
+    k_eval32_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);
     return cudaGetLastError();
 }

@@ -73,35 +73,34 @@ struct GbScan {
 
 constexpr int GB_TILE = 1024;
 
+// Constants of a problem's generations (kernel arguments that never change,
+// so a generation's launches can be captured once and replayed).
+struct GbGenConst {
+    long long K;            // parents per generation
+    int flog2;              // log2 of the fan-out
+    int fp32;               // FP32 prefilter on
+    long long max_gen;
+    double tol_f, tol_x;
+    gb_gen_stat* trace;     // device rows, one per generation
+    long long trace_cap;
+};
+
 cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, GbState* st,
                                 cudaStream_t s);
 // Active count of the pool; count and GUB are read from the device state,
 // max_count bounds the grid.
-cudaError_t gb_launch_stats(const GbEntries& E, long long max_count, double tol_f, GbState* st, cudaStream_t s);
-cudaError_t gb_launch_select(const GbEntries& E, long long count, long long active, long long K,
-                             double gub, double tol_f, GbState* st, const GbScan& sc, cudaStream_t s);
-cudaError_t gb_launch_partition(const GbEntries& E, long long count, double gub, double tol_f,
-                                const GbEntries& E_new, const GbParents& par, const GbPool& pool,
-                                GbState* st, const GbScan& sc, cudaStream_t s);
-cudaError_t gb_launch_prep(const GbProg& P, const GbPool& pool, const GbParents& par, long long npar,
-                           const GbSplit& sp, GbState* st, cudaStream_t s);
-cudaError_t gb_launch_eval64(const GbProg& P, const GbPool& pool, const GbParents& par,
-                             const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
-                             bool from_list, GbState* st, cudaStream_t s);
-cudaError_t gb_launch_eval32(const GbProg& P, const GbPool& pool, const GbParents& par,
-                             const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
-                             GbState* st, cudaStream_t s);
-// mode 0: list of FP32 survivors (flag32); mode 1: final survivors
-// (flag && flo <= new GUB) with the capacity check.
-cudaError_t gb_launch_compact_children(const GbChildren& ch, long long nchildren, int mode, GbState* st,
-                                       const GbScan& sc, cudaStream_t s);
-// tabs: the parents' term tables (null: dirty groups are re-interpreted)
-cudaError_t gb_launch_materialize(const GbProg& P, const GbPool& pool, const GbParents& par,
-                                  const GbChildren& ch, long long nchildren, const GbSplit& sp,
-                                  const GbEntries& E_new, double tol_x, GbState* st, cudaStream_t s,
-                                  const GbTabs* tabs);
-cudaError_t gb_launch_finish(const GbParents& par, long long npar, const GbPool& pool,
-                             const GbEntries& E_new, GbState* st, cudaStream_t s);
+// Active count of the pool (read from the device state) for the next generation.
+cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, GbState* st, cudaStream_t s);
+// One generation: select, partition, prepare parents, (term tables), evaluate
+// children (FP32 pass, compaction, FP64 pass), compact survivors,
+// materialise, free parents, finish, and the active count of the new pool.
+// Every size is read from the device state.  ev (4 events or null) brackets
+// the FP64 and FP32 evaluation kernels.  Returns the kernels launched in
+// *nlaunch.
+cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEntries& E, const GbEntries& E_new,
+                                 const GbParents& par, const GbChildren& ch, const GbSplit& sp, const GbScan& sc,
+                                 const GbTabs* tabs, const GbGenConst& G, long long cap, long long Cmax,
+                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch);
 // Final output: entries with flo <= GUB, in pool order, gathered into rows.
 cudaError_t gb_launch_output(const GbEntries& E, long long count, const GbPool& pool, double gub,
                              unsigned* list, double* out_lo, double* out_hi, double* out_flo,
@@ -118,13 +117,12 @@ extern "C" gb_status solve_begin(gb_problem* p);
 extern "C" int solve_advance(gb_problem* p, bool block);
 extern "C" gb_status solve_finish(gb_problem* p, gb_result* out, bool copy_boxes);
 extern "C" size_t gb_internal_device_bytes(const gb_problem* p);
-// per-parent term tables (gb_kernels_tab.cu)
+// per-parent term tables (gb_kernels_tab.cu); sizes read from the device state
 cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                           long long npar, const GbSplit& sp, cudaStream_t s);
+                           long long K, const GbSplit& sp, GbState* st, cudaStream_t s);
 cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                                 const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
-                                 bool from_list, GbState* st, cudaStream_t s);
-cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                                 const GbChildren& ch, long long nchildren, const GbSplit& sp, double gub_prev,
+                                 const GbChildren& ch, long long Cmax, const GbSplit& sp, bool from_list,
                                  GbState* st, cudaStream_t s);
-long long gb_tab_launches_so_far();
+cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                                 const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
+                                 cudaStream_t s);

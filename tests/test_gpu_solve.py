@@ -163,3 +163,41 @@ def test_table_path_identical_to_interpreter(fam, kw, opt):
         o = O.Oracle(p, block=opt["block"]).solve(split_m=opt["split_m"], split_d=opt["split_d"],
                                                   max_parents=opt["max_children"] // opt["split_m"] ** opt["split_d"])
         _assert_identical(b, o)
+
+
+@pytest.mark.parametrize("fam,kw,opt", [
+    ("chain", dict(n=10, seed=2, block=5), dict(block=5, split_m=2, split_d=5, max_children=64 * 32)),
+    ("chain", dict(n=20, seed=4), dict(block=10, split_m=4, split_d=5, max_children=1024)),
+    ("ackley", dict(n=12, seed=6), dict(block=6, split_m=2, split_d=6, max_children=4 * 64, fp32_prefilter=1)),
+    ("sep_cos", dict(n=2, seed=1), dict(block=2, split_m=2, split_d=1, max_children=64 * 2, eval_mode=1)),
+])
+def test_graph_replays_identical_to_per_generation_loop(fam, kw, opt):
+    """Generations replayed from captured CUDA graphs (several per state
+    read) run the same search as one host-synchronised generation at a time."""
+    p = S.make(fam, **kw)
+    runs = []
+    for g in (1, 7):
+        s = gb.Solver(p, gens_per_sync=g, **opt)
+        runs.append(s.solve())
+        runs.append(s.solve())      # the captured graphs are reused
+        s.close()
+    a = runs[0]
+    for b in runs[1:]:
+        assert b.status == a.status == 0
+        assert b.fmin_lo == a.fmin_lo and b.fmin_hi == a.fmin_hi and b.generations == a.generations
+        assert np.array_equal(a.box_lo, b.box_lo) and np.array_equal(a.box_hi, b.box_hi)
+        for k in ("parents", "children", "kept32", "kept", "pool", "gub"):
+            assert np.array_equal(a.trace[k], b.trace[k]), k
+
+
+def test_graph_mode_limit_and_capacity():
+    p = S.chain(n=10, seed=2, block=5)
+    for g in (1, 4):
+        s = gb.Solver(p, block=5, split_m=2, split_d=1, max_children=8 * 2, max_generations=7, gens_per_sync=g)
+        r = s.solve(raise_on_error=False)
+        s.close()
+        assert r.status == gb.GB_E_LIMIT and r.generations == 7 and len(r.trace["gub"]) == 7
+        s = gb.Solver(p, block=5, split_m=2, split_d=5, max_children=64 * 32, max_boxes=200, gens_per_sync=g)
+        r = s.solve(raise_on_error=False)
+        s.close()
+        assert r.status == gb.GB_E_CAPACITY and r.fmin_lo <= 0.0 <= r.fmin_hi
