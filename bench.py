@@ -173,7 +173,7 @@ def run_reference(a):
 def _serving_opts(gb, p, fp32):
     B = min(p.n, 10)
     return gb.gb_default_options(block=B, split_m=2, split_d=B, max_children=4 << 10,
-                                 fp32_prefilter=int(fp32), pool_bytes=4 << 30)
+                                 fp32_prefilter=int(fp32), pool_bytes=4 << 30, gens_per_sync=4)
 
 
 def run_serving(a):
@@ -224,7 +224,7 @@ def run_serving(a):
     for _, p in stream:
         o = _serving_opts(gb, p, False)
         s = gb.Solver(p, **{f: getattr(o, f) for f in ("block", "split_m", "split_d", "max_children",
-                                                        "pool_bytes")})
+                                                        "pool_bytes", "gens_per_sync")})
         t0 = time.perf_counter()
         r = s.solve()
         service.append(time.perf_counter() - t0)
