@@ -96,7 +96,13 @@ typedef struct gb_options {
     int32_t gens_per_sync;    /* <= 1: the host reads the state after every generation (per-kernel timing);
                                  G > 1: generations run as replays of a captured CUDA graph, G between
                                  state reads (the search is the same) */
+    int32_t pool_mode;        /* box storage (section 3.3): 0 auto (block records when n >= 1000 and a
+                                 child replaces at most a quarter of the blocks), 1 one dense row of n
+                                 coordinates per box, 2 block records shared between a box and its
+                                 children; results are identical */
     int32_t pad;
+    int64_t max_records;      /* block records: record capacity (0: 4 * nrec * boxes + blocks, nrec = blocks
+                                 a child replaces); unreferenced records are collected when new ones do not fit */
 } gb_options;
 
 /* Fills *opt with the defaults documented above. */
@@ -153,6 +159,9 @@ typedef struct gb_result {
     int64_t ops32;            /* directed-rounding FP32 operations executed by the FP32 evaluation kernels */
     double queue_ms;          /* serving: submit -> admission (host clock); 0 for gb_solve */
     double latency_ms;        /* serving: submit -> result ready (host clock); 0 for gb_solve */
+    int32_t pool_mode;        /* box storage used: 1 dense rows, 2 block records */
+    int32_t pad;
+    int64_t record_gcs;       /* block records: collections run */
     int64_t n_trace;
     gb_gen_stat* trace;       /* n_trace rows, host */
 } gb_result;

@@ -37,7 +37,8 @@ class gb_options(ctypes.Structure):
                 ("max_generations", ctypes.c_int64), ("max_children", ctypes.c_int64),
                 ("max_boxes", ctypes.c_int64), ("pool_bytes", ctypes.c_size_t),
                 ("device", ctypes.c_int32), ("eval_mode", ctypes.c_int32),
-                ("gens_per_sync", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("gens_per_sync", ctypes.c_int32), ("pool_mode", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("max_records", ctypes.c_int64)]
 
 
 class gb_gen_stat(ctypes.Structure):
@@ -60,7 +61,8 @@ class gb_result(ctypes.Structure):
                 ("eval64_launches", ctypes.c_int64), ("eval32_launches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ops64", ctypes.c_int64),
                 ("ops32", ctypes.c_int64), ("queue_ms", ctypes.c_double),
-                ("latency_ms", ctypes.c_double), ("n_trace", ctypes.c_int64),
+                ("latency_ms", ctypes.c_double), ("pool_mode", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("record_gcs", ctypes.c_int64), ("n_trace", ctypes.c_int64),
                 ("trace", ctypes.POINTER(gb_gen_stat))]
 
 
@@ -203,6 +205,8 @@ class Result:
     ops32: int
     queue_ms: float
     latency_ms: float
+    pool_mode: int
+    record_gcs: int
     trace: dict
 
 
@@ -228,7 +232,7 @@ def _result(r: gb_result, n: int) -> Result:
                   arr(r.box_flo, nb), r.generations, r.box_evals_fp32, r.box_evals_fp64,
                   r.mid_evals, r.solve_ms, r.device_ms, r.eval64_ms, r.eval32_ms,
                   r.eval64_launches, r.eval32_launches, r.kernel_launches, r.ops64, r.ops32,
-                  r.queue_ms, r.latency_ms, tr)
+                  r.queue_ms, r.latency_ms, r.pool_mode, r.record_gcs, tr)
 
 
 def gb_solve(prob: _Problem, device_only: bool = False, raise_on_error: bool = True) -> Result:

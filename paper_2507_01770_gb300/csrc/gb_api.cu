@@ -179,6 +179,8 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     if (opt.pool_bytes == 0) opt.pool_bytes = (size_t)16 << 30;
     if (opt.block <= 0) opt.block = n < 10 ? n : 10;
     if (opt.block > n) return fail(GB_E_INVALID, "block size larger than n");
+    if (opt.pool_mode < 0 || opt.pool_mode > 2) return fail(GB_E_INVALID, "pool_mode must be 0, 1 or 2");
+    if (opt.max_records < 0) return fail(GB_E_INVALID, "max_records must be >= 0");
     if (opt.split_m != 2 && opt.split_m != 4) return fail(GB_E_INVALID, "split_m must be 2 or 4");
     const int mshift = opt.split_m == 2 ? 1 : 2;
     if (opt.split_d <= 0) {
@@ -283,6 +285,16 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     P.tab32 = d_t32;
     P.l = d_l;
     P.u = d_u;
+    int2* d_gown;
+    int32_t* d_owned;
+    if ((e = upload(&d_gown, H.gown.data(), H.gown.size(), A)) ||
+        (e = upload(&d_owned, H.owned.data(), H.owned.size(), A)))
+        return bad(e, "upload group ownership");
+    P.GPB = H.GPB;
+    P.span = H.span;
+    P.nrec = std::min(H.nb, H.span + 1);
+    P.gown = d_gown;
+    P.owned = d_owned;
 
     // ---- solver buffers ------------------------------------------------------
     const int m = opt.split_m, d = opt.split_d;
@@ -293,25 +305,58 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     p->sp = GbSplit{m, mshift, d, d * mshift, d};
     const int fp32 = opt.fp32_prefilter ? 1 : 0;
     const int NG = P.n_groups > 0 ? P.n_groups : 1;
-    size_t per_slot = (size_t)n * 16 + (fp32 ? (size_t)n * 8 : 0) + (size_t)NG * 32 + (fp32 ? (size_t)NG * 8 : 0) +
-                      4 + 2 * 16;
-    long long cap = opt.max_boxes > 0 ? opt.max_boxes : (long long)(opt.pool_bytes / per_slot);
-    if (cap < 1) return bad(cudaErrorMemoryAllocation, "pool budget below one box");
-    if (cap > (1LL << 31) - 1) cap = (1LL << 31) - 1;
-    p->cap = cap;
     GbPool& pl = p->pool;
     pl.n = n;
     pl.NG = NG;
     pl.fp32 = fp32;
-    if ((e = alloc(&pl.lo64, (size_t)cap * n, A)) || (e = alloc(&pl.hi64, (size_t)cap * n, A)) ||
-        (e = alloc(&pl.gsum, (size_t)cap * NG, A)) || (e = alloc(&pl.gmid, (size_t)cap * NG, A)) ||
-        (e = alloc(&pl.freel, (size_t)cap, A)))
-        return bad(e, "allocate box pool");
-    if (fp32) {
-        if ((e = alloc(&pl.lo32, (size_t)cap * n, A)) || (e = alloc(&pl.hi32, (size_t)cap * n, A)) ||
-            (e = alloc(&pl.gsum32, (size_t)cap * NG, A)))
+    // box storage: dense rows, or block records when a child replaces few of
+    // the blocks (a record holds B coordinates and the cached sums of the
+    // groups its block owns; records per box budgeted at 4 * nrec)
+    const int nrec = std::min(H.nb, H.span + 1);
+    const bool recs = opt.pool_mode == 2 || (opt.pool_mode == 0 && n >= 1000 && 4 * nrec <= H.nb);
+    long long cap = 0;
+    if (recs) {
+        const size_t per_slot = (size_t)H.nb * 4 + 4 + 4 + 2 * 16;
+        const size_t per_rec = (size_t)opt.block * (16 + (fp32 ? 8 : 0)) + (size_t)H.GPB * (32 + (fp32 ? 8 : 0)) + 4 + 2;
+        const long long rho = 4LL * nrec;
+        cap = opt.max_boxes > 0 ? opt.max_boxes : (long long)(opt.pool_bytes / (per_slot + rho * per_rec));
+        if (cap < 1) return bad(cudaErrorMemoryAllocation, "pool budget below one box");
+        if (cap > (1LL << 31) - 1) cap = (1LL << 31) - 1;
+        long long R = opt.max_records > 0 ? opt.max_records : cap * rho + H.nb;
+        if (R > (1LL << 32) - 64) R = (1LL << 32) - 64;
+        if (R < H.nb) return bad(cudaErrorMemoryAllocation, "record capacity below the root box's blocks");
+        pl.recs = 1;
+        pl.nb = H.nb;
+        pl.B = opt.block;
+        pl.GPB = H.GPB;
+        pl.nrec = nrec;
+        pl.R = R;
+        const size_t RB = (size_t)R * opt.block, RG = (size_t)R * H.GPB;
+        if ((e = alloc(&pl.rid, (size_t)cap * H.nb, A)) || (e = alloc(&pl.swide, (size_t)cap, A)) ||
+            (e = alloc(&pl.freel, (size_t)cap, A)) || (e = alloc(&pl.rlo, RB, A)) || (e = alloc(&pl.rhi, RB, A)) ||
+            (e = alloc(&pl.rgsum, RG, A)) || (e = alloc(&pl.rgmid, RG, A)) || (e = alloc(&pl.rfree, (size_t)R, A)) ||
+            (e = alloc(&pl.rwide, (size_t)R, A)) || (e = alloc(&pl.rmark, (size_t)(R / 32 + 1), A)))
+            return bad(e, "allocate block records");
+        if (fp32 && ((e = alloc(&pl.rlo32, RB, A)) || (e = alloc(&pl.rhi32, RB, A)) ||
+                     (e = alloc(&pl.rgsum32, RG, A))))
+            return bad(e, "allocate block records");
+    } else {
+        size_t per_slot = (size_t)n * 16 + (fp32 ? (size_t)n * 8 : 0) + (size_t)NG * 32 + (fp32 ? (size_t)NG * 8 : 0) +
+                          4 + 2 * 16;
+        cap = opt.max_boxes > 0 ? opt.max_boxes : (long long)(opt.pool_bytes / per_slot);
+        if (cap < 1) return bad(cudaErrorMemoryAllocation, "pool budget below one box");
+        if (cap > (1LL << 31) - 1) cap = (1LL << 31) - 1;
+        if ((e = alloc(&pl.lo64, (size_t)cap * n, A)) || (e = alloc(&pl.hi64, (size_t)cap * n, A)) ||
+            (e = alloc(&pl.gsum, (size_t)cap * NG, A)) || (e = alloc(&pl.gmid, (size_t)cap * NG, A)) ||
+            (e = alloc(&pl.freel, (size_t)cap, A)))
             return bad(e, "allocate box pool");
+        if (fp32) {
+            if ((e = alloc(&pl.lo32, (size_t)cap * n, A)) || (e = alloc(&pl.hi32, (size_t)cap * n, A)) ||
+                (e = alloc(&pl.gsum32, (size_t)cap * NG, A)))
+                return bad(e, "allocate box pool");
+        }
     }
+    p->cap = cap;
     for (int b = 0; b < 2; b++)
         if ((e = alloc(&p->E[b].flo, (size_t)cap, A)) || (e = alloc(&p->E[b].slot, (size_t)cap, A)) ||
             (e = alloc(&p->E[b].cyc, (size_t)cap, A)))
@@ -377,9 +422,11 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     p->G.tol_f = tol_f;
     p->G.tol_x = opt.tol_x;
     p->G.trace_cap = opt.max_generations < (1LL << 20) ? opt.max_generations : (1LL << 20);
+    p->G.nrec = pl.recs ? pl.nrec : 0;
+    p->G.R = pl.recs ? pl.R : 0;
     if ((e = alloc(&p->trace_dev, (size_t)p->G.trace_cap, A))) return bad(e, "allocate trace");
     p->G.trace = p->trace_dev;
-    long long items = cap > p->Cmax ? cap : p->Cmax;
+    long long items = std::max(std::max(cap, p->Cmax), pl.recs ? pl.R : 0LL);
     p->sc.max_tiles = (int)((items + GB_TILE - 1) / GB_TILE) + 1;
     if ((e = alloc(&p->sc.tile_cnt, (size_t)3 * p->sc.max_tiles, A)) ||
         (e = alloc(&p->sc.tile_off, (size_t)3 * p->sc.max_tiles, A)) ||
@@ -432,7 +479,7 @@ __attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
     init.cap = p->cap;
     GB_CU(cudaEventRecord(p->ev[0], s));
     GB_CU(cudaMemcpyAsync(p->st, &init, sizeof(GbState), cudaMemcpyHostToDevice, s));
-    GB_CU(gb_launch_root_init(p->P, p->pool, p->E[0], p->st, s));
+    GB_CU(gb_launch_root_init(p->P, p->pool, p->E[0], p->G.tol_x, p->st, s));
     GB_CU(gb_launch_stats(p->E[0], p->G, 1, p->st, s));
     GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
     GB_CU(cudaEventRecord(p->ev_state, s));
@@ -487,7 +534,9 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
     if (R.timed32 && cudaEventElapsedTime(&ms, p->ev[4], p->ev[5]) == cudaSuccess) R.t32 += ms, R.n32++;
     R.timed64 = R.timed32 = false;
     if (h.error) return stop(fail(GB_E_CUDA, "device-side selection error"));
-    if (h.overflow) return stop(fail(GB_E_CAPACITY, "box pool capacity reached"));
+    if (h.overflow)
+        return stop(fail(GB_E_CAPACITY, p->pool.recs ? "box pool or block record capacity reached"
+                                                      : "box pool capacity reached"));
     if (h.active == 0) return stop(GB_OK);
     if (h.halt || h.gen >= p->opt.max_generations) return stop(fail(GB_E_LIMIT, "generation limit reached"));
     const long long l0 = gb_launches_so_far();
@@ -576,6 +625,8 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
     out->kernel_launches = R.launches;
     out->ops64 = (int64_t)hf.ops64;
     out->ops32 = (int64_t)hf.ops32;
+    out->pool_mode = p->pool.recs ? 2 : 1;
+    out->record_gcs = (int64_t)hf.rec_gc;
     const long long nt = hf.gen < p->G.trace_cap ? hf.gen : p->G.trace_cap;
     out->n_trace = nt;
     if (nt > 0) {

@@ -31,17 +31,78 @@ __device__ __forceinline__ ChildCtx child_ctx(const GbParents& par, long long ci
     return c;
 }
 
+// A stored box (no split coordinates) or, with split tables, a child of it.
+__device__ __forceinline__ View<double> box_view64(const GbPool& pool, unsigned slot) {
+    View<double> v{};
+    v.dd = 0;
+    v.mshift = 1;
+    v.mstride = 2;
+    if (pool.recs) {
+        v.plo = pool.rlo;
+        v.phi = pool.rhi;
+        v.rid = pool.rid + (size_t)slot * pool.nb;
+        v.B = pool.B;
+    } else {
+        v.plo = pool.lo64 + (size_t)slot * pool.n;
+        v.phi = pool.hi64 + (size_t)slot * pool.n;
+    }
+    return v;
+}
+__device__ __forceinline__ View<float> box_view32(const GbPool& pool, unsigned slot) {
+    View<float> v{};
+    v.dd = 0;
+    v.mshift = 1;
+    v.mstride = 2;
+    if (pool.recs) {
+        v.plo = pool.rlo32;
+        v.phi = pool.rhi32;
+        v.rid = pool.rid + (size_t)slot * pool.nb;
+        v.B = pool.B;
+    } else {
+        v.plo = pool.lo32 + (size_t)slot * pool.n;
+        v.phi = pool.hi32 + (size_t)slot * pool.n;
+    }
+    return v;
+}
+
 __device__ __forceinline__ View<double> view64(const GbPool& pool, const GbParents& par, const ChildCtx& c,
                                                const GbSplit& sp) {
+    View<double> v = box_view64(pool, c.slot);
     const double* b = par.bnd + (size_t)c.p * sp.dmax * (sp.m + 1);
-    return View<double>{pool.lo64 + (size_t)c.slot * pool.n, pool.hi64 + (size_t)c.slot * pool.n, b, b,
-                        c.info.x, c.info.y, sp.mshift, sp.m + 1, c.r};
+    v.blo = b;
+    v.bhi = b;
+    v.c0 = c.info.x;
+    v.dd = c.info.y;
+    v.mshift = sp.mshift;
+    v.mstride = sp.m + 1;
+    v.r = c.r;
+    return v;
 }
 __device__ __forceinline__ View<float> view32(const GbPool& pool, const GbParents& par, const ChildCtx& c,
                                               const GbSplit& sp) {
+    View<float> v = box_view32(pool, c.slot);
     size_t o = (size_t)c.p * sp.dmax * (sp.m + 1);
-    return View<float>{pool.lo32 + (size_t)c.slot * pool.n, pool.hi32 + (size_t)c.slot * pool.n,
-                       par.bnd_rd + o, par.bnd_ru + o, c.info.x, c.info.y, sp.mshift, sp.m + 1, c.r};
+    v.blo = par.bnd_rd + o;
+    v.bhi = par.bnd_ru + o;
+    v.c0 = c.info.x;
+    v.dd = c.info.y;
+    v.mshift = sp.mshift;
+    v.mstride = sp.m + 1;
+    v.r = c.r;
+    return v;
+}
+
+// Cached group sums of a stored box: which 0 = F, 1 = midpoint.
+__device__ __forceinline__ CacheRef<double2> cache64(const GbPool& pool, const GbProg& P, unsigned slot, int which) {
+    if (pool.recs)
+        return CacheRef<double2>{which ? pool.rgmid : pool.rgsum, pool.rid + (size_t)slot * pool.nb, P.gown,
+                                 pool.GPB};
+    return CacheRef<double2>{(which ? pool.gmid : pool.gsum) + (size_t)slot * pool.NG, nullptr, nullptr, 0};
+}
+__device__ __forceinline__ CacheRef<float2> cache32(const GbPool& pool, const GbProg& P, unsigned slot) {
+    if (pool.recs)
+        return CacheRef<float2>{pool.rgsum32, pool.rid + (size_t)slot * pool.nb, P.gown, pool.GPB};
+    return CacheRef<float2>{pool.gsum32 + (size_t)slot * pool.NG, nullptr, nullptr, 0};
 }
 
 __device__ __forceinline__ void warp_min_gub(unsigned long long key, bool has, GbState* st) {

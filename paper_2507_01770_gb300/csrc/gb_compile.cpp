@@ -264,6 +264,24 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
             P->dirty[(size_t)b * ns + k] = int2{g0, g1};
         }
 
+    // group ownership for the block-record pool
+    {
+        const int NG = (int)P->groups.size();
+        P->gown.assign(NG, int2{0, 0});
+        std::vector<int> cnt(P->nb, 0);
+        P->span = 0;
+        for (int g = 0; g < NG; g++) {
+            const GbGroup& G = P->groups[g];
+            const int ob = G.bmin < 0 ? 0 : G.bmin;
+            if (G.bmin >= 0) P->span = std::max(P->span, G.bmax - G.bmin);
+            P->gown[g] = int2{ob, cnt[ob]++};
+        }
+        P->GPB = 1;
+        for (int b = 0; b < P->nb; b++) P->GPB = std::max(P->GPB, cnt[b]);
+        P->owned.assign((size_t)P->nb * P->GPB, -1);
+        for (int g = 0; g < NG; g++) P->owned[(size_t)P->gown[g].x * P->GPB + P->gown[g].y] = g;
+    }
+
     // static directed-op counts, averaged over the blocks
     int64_t tot_eval = 0, tot_mid = 0;
     int64_t outer_f = 0, outer_r = 0;

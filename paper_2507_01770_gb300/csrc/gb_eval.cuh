@@ -50,6 +50,10 @@ template <typename T> struct View {
     const T* bhi;
     int c0, dd, mshift, mstride;
     unsigned r;
+    // block records: plo/phi are the record stores and rid the box's record
+    // ids (coordinate j in record rid[j / B] at j % B); null for a dense row
+    const unsigned* rid = nullptr;
+    int B = 1;
     __device__ __forceinline__ typename Prec<T>::I get(int j) const {
         unsigned k = (unsigned)(j - c0);
         typename Prec<T>::I x;
@@ -57,11 +61,32 @@ template <typename T> struct View {
             int dig = (r >> (k * mshift)) & ((1 << mshift) - 1);
             x.lo = blo[k * mstride + dig];
             x.hi = bhi[k * mstride + dig + 1];
+        } else if (rid) {
+            const int b = j / B;
+            const size_t o = (size_t)rid[b] * B + (j - b * B);
+            x.lo = plo[o];
+            x.hi = phi[o];
         } else {
             x.lo = plo[j];
             x.hi = phi[j];
         }
         return x;
+    }
+};
+
+// Cached group sums of one box: a dense row (rid == null) or the box's block
+// records (group g in record rid[gown[g].x] at index gown[g].y).
+template <typename C> struct CacheRef {
+    const C* base;
+    const unsigned* rid;
+    const int2* gown;
+    int GPB;
+    __device__ __forceinline__ C operator[](int g) const {
+        if (rid) {
+            const int2 o = gown[g];
+            return base[(size_t)rid[o.x] * GPB + o.y];
+        }
+        return base[g];
     }
 };
 
@@ -208,7 +233,7 @@ __device__ __forceinline__ typename Prec<T>::I group_sum(const GbProg& P, const 
 // Value of every sum: dirty groups recomputed, the others read from `cache`
 // (one interval per global group; NULL: recompute everything).
 template <typename T, typename V, typename C>
-__device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X, const C* cache,
+__device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X, const CacheRef<C>* cache,
                                            typename Prec<T>::I* R, typename Prec<T>::I* sums, int& ops) {
     typedef typename Prec<T>::I I;
     for (int k = 0; k < P.n_sum; k++) {
@@ -221,7 +246,7 @@ __device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X,
             if (g >= dr.x && g < dr.y) {
                 v = group_sum<T>(P, S, g, X, R, ops);
             } else {
-                C c = cache[S.group0 + g];
+                C c = (*cache)[S.group0 + g];
                 v.lo = c.x;
                 v.hi = c.y;
             }

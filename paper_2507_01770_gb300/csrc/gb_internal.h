@@ -101,6 +101,10 @@ struct GbProg {
     const float2* const* tab32;      // [n_tables] outward float pairs (lo, hi)
     const double* l;                 // [n]
     const double* u;                 // [n]
+    // block records (pool mode 2): group -> (owner block, index in its record)
+    int32_t GPB, span, nrec;         // groups per record, max block span of a group, records per child
+    const int2* gown;                // [n_groups]
+    const int32_t* owned;            // [nb * GPB] global groups owned by each block (-1: none)
     // per-parent term tables (null when not built)
     int32_t tab_ok, m, mshift, max_rows, max_leaves, tree_nodes, max_dterm;
     const int32_t* sp_of_cyc;        // [n] split position of a cycling position (-1: unreachable)
@@ -123,6 +127,10 @@ struct GbHostProg {
     std::vector<int2> dirty;
     std::vector<GbVarLeaf> var_leaves;
     int64_t ops_eval = 0, ops_mid = 0;   // static directed-op counts (see gb_compile.cpp)
+    // block records: group ownership (a group lives in the record of its lowest touched block)
+    int32_t GPB = 1, span = 0;
+    std::vector<int2> gown;
+    std::vector<int32_t> owned;
     // per-parent term tables
     int32_t tab_ok = 0, m = 2, mshift = 1, max_rows = 0, max_leaves = 0, tree_nodes = 0, max_dterm = 0;
     std::vector<int32_t> sp_of_cyc;
@@ -183,6 +191,10 @@ struct GbState {
     int halt;                   // set at the start of a generation that must not run
     int sel_mode;               // selection: 0 all active, 1 minimum key (K = 1), 2 radix select
     long long nch;              // children of this generation (parents * fan-out)
+    long long rec_nfree, rec_bump;     // block records: free list size, next never-used record
+    long long rec_gc;                  // block records: collections run
+    int gc;                            // block records: collect before this generation's inserts
+    int pad_;
     long long evals32, evals64, mids;  // running counters
     unsigned long long ops64, ops32;   // directed-rounding operations executed by the eval kernels
 };

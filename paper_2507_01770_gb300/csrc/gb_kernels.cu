@@ -56,43 +56,60 @@ __device__ __forceinline__ int block_prefix(bool f, int* smem_warp, int* total) 
 
 // ---------------------------------------------------------------------------
 // Root box: the whole domain [l, u] (section 3.1 "initialization").
-__global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, GbState* st) {
+__global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, GbState* st) {
     const int n = P.n;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         double l = P.l[j], u = P.u[j];
-        pool.lo64[j] = l;
-        pool.hi64[j] = u;
+        // dense: slot 0's row; records: record b = j / B holds block b
+        pool.recs ? (pool.rlo[j] = l) : (pool.lo64[j] = l);
+        pool.recs ? (pool.rhi[j] = u) : (pool.hi64[j] = u);
         if (pool.fp32) {
-            pool.lo32[j] = __double2float_rd(l);
-            pool.hi32[j] = __double2float_ru(u);
+            float l32 = __double2float_rd(l), u32 = __double2float_ru(u);
+            pool.recs ? (pool.rlo32[j] = l32) : (pool.lo32[j] = l32);
+            pool.recs ? (pool.rhi32[j] = u32) : (pool.hi32[j] = u32);
         }
     }
+    if (pool.recs)
+        for (int b = threadIdx.x; b < pool.nb; b += blockDim.x) {
+            pool.rid[b] = (unsigned)b;
+            bool wide = false;
+            for (int j = b * pool.B; j < min(n, (b + 1) * pool.B); j++)
+                if (!(__dsub_rn(P.u[j], P.l[j]) < tol_x)) wide = true;
+            pool.rwide[b] = wide ? 1 : 0;
+        }
     __syncthreads();
-    View<double> X{pool.lo64, pool.hi64, nullptr, nullptr, 0, 0, 1, 2, 0u};
+    if (pool.recs && threadIdx.x == 0) {
+        int w = 0;
+        for (int b = 0; b < pool.nb; b++) w += pool.rwide[b];
+        pool.swide[0] = w;
+    }
+    View<double> X = box_view64(pool, 0);
     MidView MX{X};
-    View<float> X32{pool.lo32, pool.hi32, nullptr, nullptr, 0, 0, 1, 2, 0u};
+    View<float> X32 = box_view32(pool, 0);
     iv64 R[GB_MAX_TREGS];
     iv32 R32[GB_MAX_TREGS];
     int ops = 0;
     for (int k = 0; k < P.n_sum; k++) {
         GbSum S = P.sums[k];
         for (int g = threadIdx.x; g < S.ngroups; g += blockDim.x) {
+            const int gg = S.group0 + g;
+            const size_t at = pool.recs ? (size_t)P.gown[gg].x * pool.GPB + P.gown[gg].y : (size_t)gg;
             iv64 a = group_sum<double>(P, S, g, X, R, ops);
             iv64 b = group_sum<double>(P, S, g, MX, R, ops);
-            pool.gsum[S.group0 + g] = make_double2(a.lo, a.hi);
-            pool.gmid[S.group0 + g] = make_double2(b.lo, b.hi);
+            (pool.recs ? pool.rgsum : pool.gsum)[at] = make_double2(a.lo, a.hi);
+            (pool.recs ? pool.rgmid : pool.gmid)[at] = make_double2(b.lo, b.hi);
             if (pool.fp32) {
                 iv32 c = group_sum<float>(P, S, g, X32, R32, ops);
-                pool.gsum32[S.group0 + g] = make_float2(c.lo, c.hi);
+                (pool.recs ? pool.rgsum32 : pool.gsum32)[at] = make_float2(c.lo, c.hi);
             }
         }
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
     iv64 sums[GB_MAX_ISUM], O[GB_MAX_OREGS];
-    sum_values<double>(P, 0, X, (const double2*)nullptr, R, sums, ops);
+    sum_values<double>(P, 0, X, (const CacheRef<double2>*)nullptr, R, sums, ops);
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
-    sum_values<double>(P, 0, MX, (const double2*)nullptr, R, sums, ops);
+    sum_values<double>(P, 0, MX, (const CacheRef<double2>*)nullptr, R, sums, ops);
     iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
     double gub = Fm.hi;
     if (gub != gub) gub = __longlong_as_double(0x7ff0000000000000LL);
@@ -109,6 +126,7 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, GbState* st) {
     s0.sel_T = ~0ull;
     s0.evals64 = 1;
     s0.mids = 1;
+    s0.rec_bump = pool.recs ? pool.nb : 0;
     *st = s0;
 }
 
@@ -305,13 +323,15 @@ __global__ void k_part_count(GbEntries E, GbGenConst G, const GbState* st, int* 
 // Exclusive scan of up to 3 arrays of tile counts (one block of 1024
 // threads, each owning a contiguous run of tiles).
 // what: 0 = partition (3 arrays, items = pool), 1 = FP32 list and 2 =
-// survivors (items = children of the generation), 3 = output (items = count).
+// survivors (items = children of the generation), 3 = output (items = count),
+// 4 = free block records (items = records ever used).
 __global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_cnt, int* tile_off, int max_tiles,
                                                      int what, long long out_count, GbGenConst G, GbState* st) {
     if (what != 3 && st->halt) return;
+    if (what == 4 && !st->gc) return;
     __shared__ long long part[1024];
     __shared__ long long tot[3];
-    const long long items = what == 0 ? st->pool : (what == 3 ? out_count : st->nch);
+    const long long items = what == 0 ? st->pool : what == 3 ? out_count : what == 4 ? st->rec_bump : st->nch;
     const int ntiles = (int)ntiles_of(items);
     const int t = threadIdx.x;
     const int per = (ntiles + 1023) / 1024;
@@ -356,6 +376,12 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_c
         st->kept = S;
         long long room = st->nfree + (st->cap - st->bump);
         st->overflow = S > room ? 1 : 0;
+        // block records: collect unreferenced records first if the new ones do not fit
+        st->gc = (!st->overflow && G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
+    } else if (what == 4) {
+        st->rec_nfree = tot[0];
+        st->rec_gc += 1;
+        if (st->kept * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) st->overflow = 1;
     } else {
         st->kept = tot[0];
     }
@@ -432,9 +458,11 @@ __global__ void k_prep(GbProg P, GbPool pool, GbParents par, GbSplit sp, GbState
     par.info[p] = make_int4(c, dd, b, nxt);
     unsigned slot = par.slot[p];
     const int ms = sp.m + 1;
+    const View<double> PX = box_view64(pool, slot);
     for (int k = 0; k < dd; k++) {
         int j = c + k;
-        double lo = pool.lo64[(size_t)slot * n + j], hi = pool.hi64[(size_t)slot * n + j];
+        const iv64 pj = PX.get(j);
+        double lo = pj.lo, hi = pj.hi;
         double w = __dsub_rn(hi, lo);
         double q = __ddiv_rn(w, (double)sp.m);
         for (int t = 0; t <= sp.m; t++) {
@@ -462,13 +490,14 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
     MidView MX{X};
     iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
     const int blk = c.info.z;
-    sum_values<double>(P, blk, MX, pool.gmid + (size_t)c.slot * pool.NG, R, sums, ops);
+    const CacheRef<double2> cm = cache64(pool, P, c.slot, 1), cf = cache64(pool, P, c.slot, 0);
+    sum_values<double>(P, blk, MX, &cm, R, sums, ops);
     iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
     if (Fm.hi == Fm.hi) {
         *gkey = gb_order_key(Fm.hi);
         *has_key = true;
     }
-    sum_values<double>(P, blk, X, pool.gsum + (size_t)c.slot * pool.NG, R, sums, ops);
+    sum_values<double>(P, blk, X, &cf, R, sums, ops);
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
     bool keep = !(F.lo > gub_prev);
     if (keep) keep = !block_mono<double>(P, blk, X, X, O, OA, R, RA, (double*)nullptr, ops);
@@ -527,7 +556,8 @@ __global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents
                 View<double> X64 = view64(pool, par, c, sp);
                 iv32 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
                 const int blk = c.info.z;
-                sum_values<float>(P, blk, X, pool.gsum32 + (size_t)c.slot * pool.NG, R, sums, ops);
+                const CacheRef<float2> c32 = cache32(pool, P, c.slot);
+                sum_values<float>(P, blk, X, &c32, R, sums, ops);
                 iv32 F = outer_fwd<float>(P, X, sums, O, ops);
                 bool keep = !((double)F.lo > gub_prev);
                 if (keep) keep = !block_mono<float>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr, ops);
@@ -666,6 +696,174 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
     }
 }
 
+// ---------------------------------------------------------------------------
+// Block records: a box's row names one record per block, and a child shares
+// all but the records of the blocks it changes with its parent, so a record
+// is referenced by many boxes and is freed by a mark-and-sweep collection,
+// run only when the new records of a generation do not fit: mark the records
+// named by the boxes still alive (entries carried over and this generation's
+// parents), then list the unmarked ones in ascending order as the free list.
+__global__ void k_gc_clear(GbPool pool, const GbState* st) {
+    if (st->halt || !st->gc) return;
+    const long long words = (st->rec_bump + 31) >> 5;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < words;
+         w += (long long)gridDim.x * blockDim.x)
+        pool.rmark[w] = 0u;
+}
+
+__global__ void k_gc_mark(GbPool pool, GbEntries En, GbParents par, const GbState* st) {
+    if (st->halt || !st->gc) return;
+    const long long nbox = st->kept_old + st->parents, nb = pool.nb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nbox * nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long q = i / nb, b = i - q * nb;
+        const unsigned slot = q < st->kept_old ? En.slot[q] : par.slot[q - st->kept_old];
+        const unsigned id = pool.rid[(size_t)slot * nb + b];
+        atomicOr(pool.rmark + (id >> 5), 1u << (id & 31));
+    }
+}
+
+__device__ __forceinline__ bool rec_free(const GbPool& pool, long long id, long long used) {
+    return id < used && !((pool.rmark[id >> 5] >> (id & 31)) & 1u);
+}
+
+__global__ void k_gc_count(GbPool pool, const GbState* st, int* tile_cnt) {
+    if (st->halt || !st->gc) return;
+    __shared__ int sw[PT / 32 + 1];
+    const long long used = st->rec_bump, nt = ntiles_of(used);
+    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        int acc = 0, tot;
+        for (int r = 0; r < GB_TILE / PT; r++) {
+            block_prefix<PT>(rec_free(pool, tile * GB_TILE + r * PT + threadIdx.x, used), sw, &tot);
+            acc += tot;
+        }
+        if (threadIdx.x == 0) tile_cnt[tile] = acc;
+    }
+}
+
+__global__ void k_gc_scatter(GbPool pool, const GbState* st, const int* tile_off) {
+    if (st->halt || !st->gc) return;
+    __shared__ int sw[PT / 32 + 1];
+    const long long used = st->rec_bump, nt = ntiles_of(used);
+    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        long long o = tile_off[tile];
+        for (int r = 0; r < GB_TILE / PT; r++) {
+            const long long id = tile * GB_TILE + r * PT + threadIdx.x;
+            const bool f = rec_free(pool, id, used);
+            int tot;
+            const int rk = block_prefix<PT>(f, sw, &tot);
+            if (f) pool.rfree[o + rk] = (unsigned)id;
+            o += tot;
+        }
+    }
+}
+
+// Block records: survivor s takes new records s * nrec + t (t = 0 .. nrec-1,
+// from the free list, then never-used ones) for blocks blk - t, the blocks
+// whose owned groups can touch the split block blk; its row is its parent's
+// with those entries replaced.  A new record holds the child's coordinates of
+// its block and the cached sums of the groups it owns (groups of the dirty
+// ranges recomputed, the others copied from the parent's record).
+__device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                                const GbChildren& ch, const GbSplit& sp, const GbEntries& En,
+                                                double tol_x, const GbState* st, long long s, int lane,
+                                                const GbTabs& Tb, bool tab) {
+    const long long nfree = st->nfree, bump = st->bump, kept_old = st->kept_old;
+    const long long rnf = st->rec_nfree, rbump = st->rec_bump;
+    const long long ci = ch.surv[s];
+    const ChildCtx c = child_ctx(par, ci, sp);
+    const unsigned ns = (s < nfree) ? pool.freel[nfree - 1 - s] : (unsigned)(bump + (s - nfree));
+    const int n = pool.n, nb = pool.nb, B = pool.B, GPB = pool.GPB, nrec = pool.nrec;
+    const int blk = c.info.z;
+    const unsigned* prow = pool.rid + (size_t)c.slot * nb;
+    unsigned* crow = pool.rid + (size_t)ns * nb;
+    for (int b = lane; b < nb; b += 32) {
+        const int t = blk - b;
+        unsigned id = prow[b];
+        if (t >= 0 && t < nrec) {
+            const long long q = s * nrec + t;
+            id = q < rnf ? pool.rfree[rnf - 1 - q] : (unsigned)(rbump + (q - rnf));
+        }
+        crow[b] = id;
+    }
+    __syncwarp();
+    const View<double> X = view64(pool, par, c, sp);
+    View<float> X32;
+    if (pool.fp32) X32 = view32(pool, par, c, sp);
+    int wide_delta = 0;
+    for (int t = 0; t < nrec && blk - t >= 0; t++) {
+        const int b = blk - t, j0 = b * B, j1 = min(n, j0 + B);
+        const size_t o = (size_t)crow[b] * B;
+        bool wide = false;
+        for (int j = j0 + lane; j < j1; j += 32) {
+            const iv64 x = X.get(j);
+            pool.rlo[o + (j - j0)] = x.lo;
+            pool.rhi[o + (j - j0)] = x.hi;
+            if (pool.fp32) {
+                const iv32 y = X32.get(j);
+                pool.rlo32[o + (j - j0)] = y.lo;
+                pool.rhi32[o + (j - j0)] = y.hi;
+            }
+            if (!(__dsub_rn(x.hi, x.lo) < tol_x)) wide = true;
+        }
+        wide = __any_sync(0xffffffffu, wide);
+        if (lane == 0) {
+            pool.rwide[crow[b]] = wide ? 1 : 0;
+            wide_delta += (wide ? 1 : 0) - (int)pool.rwide[prow[b]];
+        }
+    }
+    const MidView MX{X};
+    iv64 R[GB_MAX_TREGS];
+    iv32 R32[GB_MAX_TREGS];
+    int ops = 0;
+    for (int it = lane; it < nrec * GPB; it += 32) {
+        const int t = it / GPB, o = it - t * GPB, b = blk - t;
+        if (b < 0) continue;
+        const int g = P.owned[(size_t)b * GPB + o];
+        if (g < 0) continue;
+        int k = 0;
+        while (k + 1 < P.n_sum && P.sums[k + 1].group0 <= g) k++;
+        const GbSum S = P.sums[k];
+        const int gl = g - S.group0;
+        const int2 dr = P.dirty[blk * P.n_sum + k];
+        const size_t dst = (size_t)crow[b] * GPB + o, src = (size_t)prow[b] * GPB + o;
+        if (gl < dr.x || gl >= dr.y) {
+            pool.rgsum[dst] = pool.rgsum[src];
+            pool.rgmid[dst] = pool.rgmid[src];
+            if (pool.fp32) pool.rgsum32[dst] = pool.rgsum32[src];
+            continue;
+        }
+        iv64 a, m;
+        if (tab) {
+            const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
+            a = tab_group64(P, Tb, c.p, SP, k, gl, c.r, 0);
+            m = tab_group64(P, Tb, c.p, SP, k, gl, c.r, 1);
+            if (pool.fp32) {
+                const iv32 f = tab_group32(P, Tb, c.p, SP, k, gl, c.r);
+                pool.rgsum32[dst] = make_float2(f.lo, f.hi);
+            }
+        } else {
+            a = group_sum<double>(P, S, gl, X, R, ops);
+            m = group_sum<double>(P, S, gl, MX, R, ops);
+            if (pool.fp32) {
+                const iv32 f = group_sum<float>(P, S, gl, X32, R32, ops);
+                pool.rgsum32[dst] = make_float2(f.lo, f.hi);
+            }
+        }
+        pool.rgsum[dst] = make_double2(a.lo, a.hi);
+        pool.rgmid[dst] = make_double2(m.lo, m.hi);
+    }
+    if (lane == 0) {
+        const int w = pool.swide[c.slot] + wide_delta;
+        pool.swide[ns] = w;
+        const bool narrow = tol_x > 0.0 && w == 0;
+        const long long e = kept_old + s;
+        En.flo[e] = ch.flo[ci];
+        En.slot[e] = ns;
+        En.cyc[e] = (int)((unsigned)c.info.w | (narrow ? GB_FINAL_BIT : 0u));
+    }
+}
+
 __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbParents par, GbChildren ch,
                                                      GbSplit sp, GbEntries En, double tol_x, GbState* st,
                                                      GbTabs Tb, int tab) {
@@ -673,8 +871,12 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
     if (st->halt || st->overflow) return;
     const long long kept = st->kept;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < kept; s += nwarps)
-        materialize_one(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0);
+    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < kept; s += nwarps) {
+        if (pool.recs)
+            materialize_rec(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0);
+        else
+            materialize_one(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0);
+    }
 }
 
 // Parents' slots back to the free list, or (on overflow) the parents back
@@ -707,6 +909,12 @@ __global__ void k_finish(GbGenConst G, GbState* st) {
     } else {
         long long from_free = kept < nfree ? kept : nfree;
         st->bump += kept - from_free;
+        if (G.nrec) {
+            const long long used = kept * G.nrec, rf = st->rec_nfree;
+            const long long r_from_free = used < rf ? used : rf;
+            st->rec_nfree = rf - r_from_free;
+            st->rec_bump += used - r_from_free;
+        }
         st->nfree = nfree - from_free + npar;
         st->pool = st->kept_old + kept;
     }
@@ -723,6 +931,7 @@ __global__ void k_finish(GbGenConst G, GbState* st) {
     }
     st->gen += 1;
     st->active = 0;
+    st->gc = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -772,9 +981,11 @@ __global__ void k_out_gather(GbEntries E, const unsigned* list, const GbState* s
     unsigned q = list[b];
     unsigned slot = E.slot[q];
     const int n = pool.n;
+    const View<double> X = box_view64(pool, slot);
     for (int j = lane; j < n; j += 32) {
-        out_lo[(size_t)b * n + j] = pool.lo64[(size_t)slot * n + j];
-        out_hi[(size_t)b * n + j] = pool.hi64[(size_t)slot * n + j];
+        const iv64 x = X.get(j);
+        out_lo[(size_t)b * n + j] = x.lo;
+        out_hi[(size_t)b * n + j] = x.hi;
     }
     if (lane == 0) out_flo[b] = E.flo[q];
 }
@@ -799,13 +1010,13 @@ __global__ void __launch_bounds__(128) k_eval_boxes(GbProg P, const double* lo, 
     MidView MX{X};
     iv64 R[GB_MAX_TREGS], O[GB_MAX_OREGS], sums[GB_MAX_ISUM];
     int ops = 0;
-    sum_values<double>(P, blk, MX, (const double2*)nullptr, R, sums, ops);
+    sum_values<double>(P, blk, MX, (const CacheRef<double2>*)nullptr, R, sums, ops);
     iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
     Fmo[2 * b] = Fm.lo;
     Fmo[2 * b + 1] = Fm.hi;
     if (!fp32) {
         iv64 RA[GB_MAX_TREGS], OA[GB_MAX_OREGS];
-        sum_values<double>(P, blk, X, (const double2*)nullptr, R, sums, ops);
+        sum_values<double>(P, blk, X, (const CacheRef<double2>*)nullptr, R, sums, ops);
         iv64 F = outer_fwd<double>(P, X, sums, O, ops);
         Fo[2 * b] = F.lo;
         Fo[2 * b + 1] = F.hi;
@@ -816,7 +1027,7 @@ __global__ void __launch_bounds__(128) k_eval_boxes(GbProg P, const double* lo, 
     } else {
         View<float> X32{lo32 + (size_t)b * n, hi32 + (size_t)b * n, nullptr, nullptr, 0, 0, 1, 2, 0u};
         iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS], O32[GB_MAX_OREGS], OA32[GB_MAX_OREGS], s32[GB_MAX_ISUM];
-        sum_values<float>(P, blk, X32, (const float2*)nullptr, R32, s32, ops);
+        sum_values<float>(P, blk, X32, (const CacheRef<float2>*)nullptr, R32, s32, ops);
         iv32 F = outer_fwd<float>(P, X32, s32, O32, ops);
         Fo[2 * b] = F.lo;
         Fo[2 * b + 1] = F.hi;
@@ -855,10 +1066,10 @@ inline unsigned grid_for(long long items, int per_block) {
 thread_local long long gb_launch_count = 0;
 
 long long gb_launches_so_far() { return gb_launch_count; }
-cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, GbState* st,
-                                cudaStream_t s) {
+cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, double tol_x,
+                                GbState* st, cudaStream_t s) {
     gb_launch_count++;
-    k_root_init<<<1, 256, 0, s>>>(P, pool, E, st);
+    k_root_init<<<1, 256, 0, s>>>(P, pool, E, tol_x, st);
     return cudaGetLastError();
 }
 
@@ -932,6 +1143,15 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     k_cc_count<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_cnt);
     k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 2, 0, G, st);
     k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_off, ch.surv);
+    if (pool.recs) {
+        const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), 152 * 8);
+        gb_launch_count += 5;
+        k_gc_clear<<<152 * 4, 256, 0, s>>>(pool, st);
+        k_gc_mark<<<152 * 8, 256, 0, s>>>(pool, E_new, par, st);
+        k_gc_count<<<grec, PT, 0, s>>>(pool, st, sc.tile_cnt);
+        k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0, G, st);
+        k_gc_scatter<<<grec, PT, 0, s>>>(pool, st, sc.tile_off);
+    }
     GbTabs Tb{};
     if (tabs) Tb = *tabs;
     gb_launch_count++;

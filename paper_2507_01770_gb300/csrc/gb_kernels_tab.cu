@@ -64,8 +64,14 @@ __global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents pa
         const unsigned r = combo << D.dshift;   // a child index with these digits
         const GbSum S = P.sums[D.sum];
         const int i = S.first + D.term * S.step;
-        View<double> X{pool.lo64 + (size_t)slot * pool.n, pool.hi64 + (size_t)slot * pool.n, b64, b64,
-                       info.x, info.y, sp.mshift, sp.m + 1, r};
+        View<double> X = box_view64(pool, slot);
+        X.blo = b64;
+        X.bhi = b64;
+        X.c0 = info.x;
+        X.dd = info.y;
+        X.mshift = sp.mshift;
+        X.mstride = sp.m + 1;
+        X.r = r;
         MidView MX{X};
         const size_t orow = (size_t)p * T.max_rows + row;
         iv64 v = term_fwd<double>(P, S, i, X, R, ops);
@@ -83,8 +89,14 @@ __global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents pa
             leaf++;
         }
         if (pool.fp32) {
-            View<float> X32{pool.lo32 + (size_t)slot * pool.n, pool.hi32 + (size_t)slot * pool.n,
-                            par.bnd_rd + o, par.bnd_ru + o, info.x, info.y, sp.mshift, sp.m + 1, r};
+            View<float> X32 = box_view32(pool, slot);
+            X32.blo = par.bnd_rd + o;
+            X32.bhi = par.bnd_ru + o;
+            X32.c0 = info.x;
+            X32.dd = info.y;
+            X32.mshift = sp.mshift;
+            X32.mstride = sp.m + 1;
+            X32.r = r;
             iv32 f = term_fwd<float>(P, S, i, X32, R32, ops);
             T.tv32[orow] = make_float2(f.lo, f.hi);
             for (int t = 0; t < S.nins; t++) RA32[t] = iv32{0.f, 0.f};
@@ -105,11 +117,12 @@ __global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents pa
         const int k = job % P.n_sum, kind = job / P.n_sum;
         const GbSum S = P.sums[k];
         const size_t nb = (size_t)p * T.tree_nodes + S.node0;
-        const size_t cb = (size_t)slot * pool.NG + S.group0;
+        const CacheRef<double2> cf = cache64(pool, P, slot, 0), cm = cache64(pool, P, slot, 1);
+        const CacheRef<float2> c32 = cache32(pool, P, slot);
         for (int g = 0; g < S.ngroups; g++) {
-            if (kind == 0) T.nf64[nb + g] = pool.gsum[cb + g];
-            else if (kind == 1) T.nm64[nb + g] = pool.gmid[cb + g];
-            else T.nf32[nb + g] = pool.gsum32[cb + g];
+            if (kind == 0) T.nf64[nb + g] = cf[S.group0 + g];
+            else if (kind == 1) T.nm64[nb + g] = cm[S.group0 + g];
+            else T.nf32[nb + g] = c32[S.group0 + g];
         }
         int off = 0;
         for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {

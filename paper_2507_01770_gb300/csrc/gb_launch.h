@@ -17,6 +17,23 @@ struct GbPool {
     float2* gsum32;   // [cap][NG] cached group sums of F (FP32 prefilter only)
     unsigned* freel;  // [cap] free slots
     int n, NG, fp32;
+    // block-record mode (recs = 1): a box is a row of nb record ids; record q
+    // holds block coordinates [q*B, q*B + B) and the cached sums of the groups
+    // its block owns [q*GPB, q*GPB + GPB).  lo64..gsum32 above are unused.
+    int recs, nb, B, GPB, nrec;
+    unsigned* rid;    // [cap][nb]
+    double* rlo;      // [R][B]
+    double* rhi;
+    float* rlo32;     // [R][B] (FP32 prefilter only)
+    float* rhi32;
+    double2* rgsum;   // [R][GPB]
+    double2* rgmid;
+    float2* rgsum32;
+    unsigned* rfree;  // [R] free records
+    unsigned* rmark;  // [R / 32 + 1] mark bits of the record collector
+    unsigned char* rwide;  // [R] 1: some coordinate of the record is at least tol_x wide
+    int* swide;       // [cap] records of the box with rwide = 1 (0: the box is final)
+    long long R;      // record capacity
 };
 
 // Ordered list of pool entries (the best-first list; bit 31 of cyc = final).
@@ -83,10 +100,12 @@ struct GbGenConst {
     double tol_f, tol_x;
     gb_gen_stat* trace;     // device rows, one per generation
     long long trace_cap;
+    int nrec;               // block records: new records per child (0: dense rows)
+    long long R;            // block records: capacity
 };
 
-cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, GbState* st,
-                                cudaStream_t s);
+cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, double tol_x,
+                                GbState* st, cudaStream_t s);
 // Active count of the pool; count and GUB are read from the device state,
 // max_count bounds the grid.
 // Active count of the pool (read from the device state) for the next generation.
