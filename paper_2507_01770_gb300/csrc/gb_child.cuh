@@ -121,36 +121,59 @@ __device__ __forceinline__ void warp_add_ops(int ops, unsigned long long* dst) {
 }
 
 
-// Sum of the terms of dirty group g of sum k for child index r, read from
-// the parent's term tables (kind 0: F, 1: midpoint); same pairwise tree as
-// group_sum.
-__device__ __forceinline__ iv64 tab_group64(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
-                                            int k, int g, unsigned r, int kind) {
-    Tree<iv64> tr;
-    tr.init();
-    const size_t rowbase = (size_t)p * Tb.max_rows;
-    for (int q = 0; q < SP.ndterm; q++) {
-        const GbDTerm D = P.dterms[SP.dterm0 + q];
-        if (D.sum != k || D.group != g) continue;
-        const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
-        double2 v = kind == 0 ? Tb.tv64[rowbase + D.row + combo] : Tb.tm64[rowbase + D.row + combo];
-        tr.push(iv64{v.x, v.y});
-    }
-    return tr.result();
+// ---- warp-cooperative pieces (one child per warp) ---------------------------
+template <typename I> __device__ __forceinline__ I shfl_iv(I v, int src) {
+    v.lo = __shfl_sync(0xffffffffu, v.lo, src);
+    v.hi = __shfl_sync(0xffffffffu, v.hi, src);
+    return v;
 }
-__device__ __forceinline__ iv32 tab_group32(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
-                                            int k, int g, unsigned r) {
-    Tree<iv32> tr;
-    tr.init();
-    const size_t rowbase = (size_t)p * Tb.max_rows;
-    for (int q = 0; q < SP.ndterm; q++) {
-        const GbDTerm D = P.dterms[SP.dterm0 + q];
-        if (D.sum != k || D.group != g) continue;
-        const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
-        float2 v = Tb.tv32[rowbase + D.row + combo];
-        tr.push(iv32{v.x, v.y});
+
+// In-place pairwise tree a[i] += a[i + s] (s = 1, 2, ..., 16) over the values
+// of lanes [0, r): the same tree the binary counter forms over r items.
+// Returns the result on every lane.
+template <typename I> __device__ __forceinline__ I warp_tree(I v, int r, int lane) {
+    for (int s = 1; s < 32; s <<= 1) {
+        I o;
+        o.lo = __shfl_down_sync(0xffffffffu, v.lo, s);
+        o.hi = __shfl_down_sync(0xffffffffu, v.hi, s);
+        if ((lane & (2 * s - 1)) == 0 && lane + s < r) v = iadd(v, o);
     }
-    return tr.result();
+    return shfl_iv(v, 0);
+}
+
+// Table values of dirty group g of sum k for child digits r, NV tables at a
+// time (load(D, combo, v) fills v[0..NV)), starting at dirty term dt (the
+// terms of a split position are ordered by sum, group and term, so those of
+// (k, g) are the run starting at dt).  The pairwise tree over the run is the
+// in-place tree within each aligned chunk of 32 terms (warp_tree) followed by
+// the same tree over the chunk sums (binary counter), i.e. the tree
+// group_sum forms.  dt advances past the run; cnt = its length.
+// Every lane returns the same values.
+template <typename I, int NV, typename L>
+__device__ __forceinline__ void warp_group(const GbProg& P, const GbSplitPos& SP, int k, int g, unsigned r,
+                                           int& dt, int lane, L load, I* out, int& cnt) {
+    Tree<I> tr[NV];
+    for (int t = 0; t < NV; t++) tr[t].init();
+    cnt = 0;
+    const int end = SP.dterm0 + SP.ndterm;
+    for (;;) {
+        const int i = dt + lane;
+        bool mem = false;
+        I v[NV];
+        for (int t = 0; t < NV; t++) v[t].lo = v[t].hi = 0;
+        if (i < end) {
+            const GbDTerm D = P.dterms[i];
+            mem = D.sum == k && D.group == g;
+            if (mem) load(D, (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u), v);
+        }
+        const int rr = __popc(__ballot_sync(0xffffffffu, mem));
+        if (rr == 0) break;
+        for (int t = 0; t < NV; t++) tr[t].push(warp_tree(v[t], rr, lane));
+        cnt += rr;
+        dt += rr;
+        if (rr < 32) break;
+    }
+    for (int t = 0; t < NV; t++) out[t] = tr[t].result();
 }
 
 }  // namespace gb

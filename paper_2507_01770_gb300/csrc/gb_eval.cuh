@@ -238,7 +238,8 @@ __device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X,
     typedef typename Prec<T>::I I;
     for (int k = 0; k < P.n_sum; k++) {
         GbSum S = P.sums[k];
-        int2 dr = cache ? P.dirty[blk * P.n_sum + k] : make_int2(0, S.ngroups);
+        // with a cache: the dirty groups of block blk recomputed (blk < 0: none)
+        int2 dr = cache ? (blk >= 0 ? P.dirty[blk * P.n_sum + k] : make_int2(0, 0)) : make_int2(0, S.ngroups);
         Tree<I> tr;
         tr.init();
         for (int g = 0; g < S.ngroups; g++) {

@@ -106,10 +106,13 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
+    // F and the midpoint sample from the group sums just cached (the same
+    // group values and tree as a full evaluation)
     iv64 sums[GB_MAX_ISUM], O[GB_MAX_OREGS];
-    sum_values<double>(P, 0, X, (const CacheRef<double2>*)nullptr, R, sums, ops);
+    const CacheRef<double2> cf = cache64(pool, P, 0, 0), cm = cache64(pool, P, 0, 1);
+    sum_values<double>(P, -1, X, &cf, R, sums, ops);
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
-    sum_values<double>(P, 0, MX, (const CacheRef<double2>*)nullptr, R, sums, ops);
+    sum_values<double>(P, -1, MX, &cm, R, sums, ops);
     iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
     double gub = Fm.hi;
     if (gub != gub) gub = __longlong_as_double(0x7ff0000000000000LL);
@@ -621,16 +624,60 @@ __global__ void k_cc_scatter(GbChildren ch, int mode, const GbState* st, const i
     }
 }
 
+// Table path of the materialisation: the dirty group values of a survivor
+// (F, midpoint, FP32), one warp walking the dirty terms of its split position
+// (warp_group), staged in shared memory at [k * GB_TAB_MAX_DIRTY + g - dr.x].
+constexpr int GB_SHG = GB_MAX_ISUM * GB_TAB_MAX_DIRTY;
+__device__ __forceinline__ void tab_dirty_groups(const GbProg& P, const GbPool& pool, const GbTabs& Tb,
+                                                 const ChildCtx& c, int lane, double2* shF, double2* shM,
+                                                 float2* sh32) {
+    const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
+    const int blk = c.info.z;
+    const size_t rowbase = (size_t)c.p * Tb.max_rows;
+    int dtA = SP.dterm0, dtB = SP.dterm0;
+    for (int k = 0; k < P.n_sum; k++) {
+        const int2 dr = P.dirty[blk * P.n_sum + k];
+        for (int g = dr.x; g < dr.y; g++) {
+            iv64 v2[2];
+            int cnt;
+            warp_group<iv64, 2>(P, SP, k, g, c.r, dtA, lane,
+                                [&](const GbDTerm& D, unsigned combo, iv64* v) {
+                                    const double2 a = Tb.tv64[rowbase + D.row + combo];
+                                    const double2 b = Tb.tm64[rowbase + D.row + combo];
+                                    v[0] = iv64{a.x, a.y};
+                                    v[1] = iv64{b.x, b.y};
+                                }, v2, cnt);
+            const int at = k * GB_TAB_MAX_DIRTY + (g - dr.x);
+            if (lane == 0) {
+                shF[at] = make_double2(v2[0].lo, v2[0].hi);
+                shM[at] = make_double2(v2[1].lo, v2[1].hi);
+            }
+            if (pool.fp32) {
+                iv32 f;
+                warp_group<iv32, 1>(P, SP, k, g, c.r, dtB, lane,
+                                    [&](const GbDTerm& D, unsigned combo, iv32* v) {
+                                        const float2 a = Tb.tv32[rowbase + D.row + combo];
+                                        v[0] = iv32{a.x, a.y};
+                                    }, &f, cnt);
+                if (lane == 0) sh32[at] = make_float2(f.lo, f.hi);
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // Survivors into free slots: coordinates, FP32 shadow, group caches (dirty
 // groups recomputed, the rest copied from the parent), pool entry.
 __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                 const GbChildren& ch, const GbSplit& sp, const GbEntries& En,
                                                 double tol_x, const GbState* st, long long s, int lane,
-                                                const GbTabs& Tb, bool tab) {
+                                                const GbTabs& Tb, bool tab, double2* shF, double2* shM,
+                                                float2* sh32) {
     const long long nfree = st->nfree, bump = st->bump, kept_old = st->kept_old;
     const long long ci = ch.surv[s];
     ChildCtx c = child_ctx(par, ci, sp);
+    if (tab) tab_dirty_groups(P, pool, Tb, c, lane, shF, shM, sh32);
     const unsigned ns = (s < nfree) ? pool.freel[nfree - 1 - s] : (unsigned)(bump + (s - nfree));
     const int n = pool.n;
     View<double> X = view64(pool, par, c, sp);
@@ -669,13 +716,10 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
             size_t dst = (size_t)ns * pool.NG + S.group0 + g;
             iv64 a, b;
             if (tab) {
-                const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
-                a = tab_group64(P, Tb, c.p, SP, k, g, c.r, 0);
-                b = tab_group64(P, Tb, c.p, SP, k, g, c.r, 1);
-                if (pool.fp32) {
-                    iv32 f = tab_group32(P, Tb, c.p, SP, k, g, c.r);
-                    pool.gsum32[dst] = make_float2(f.lo, f.hi);
-                }
+                const int at = k * GB_TAB_MAX_DIRTY + (g - dr.x);
+                a = iv64{shF[at].x, shF[at].y};
+                b = iv64{shM[at].x, shM[at].y};
+                if (pool.fp32) pool.gsum32[dst] = sh32[at];
             } else {
                 a = group_sum<double>(P, S, g, X, R, ops);
                 b = group_sum<double>(P, S, g, MX, R, ops);
@@ -767,11 +811,13 @@ __global__ void k_gc_scatter(GbPool pool, const GbState* st, const int* tile_off
 __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                 const GbChildren& ch, const GbSplit& sp, const GbEntries& En,
                                                 double tol_x, const GbState* st, long long s, int lane,
-                                                const GbTabs& Tb, bool tab) {
+                                                const GbTabs& Tb, bool tab, double2* shF, double2* shM,
+                                                float2* sh32) {
     const long long nfree = st->nfree, bump = st->bump, kept_old = st->kept_old;
     const long long rnf = st->rec_nfree, rbump = st->rec_bump;
     const long long ci = ch.surv[s];
     const ChildCtx c = child_ctx(par, ci, sp);
+    if (tab) tab_dirty_groups(P, pool, Tb, c, lane, shF, shM, sh32);
     const unsigned ns = (s < nfree) ? pool.freel[nfree - 1 - s] : (unsigned)(bump + (s - nfree));
     const int n = pool.n, nb = pool.nb, B = pool.B, GPB = pool.GPB, nrec = pool.nrec;
     const int blk = c.info.z;
@@ -835,13 +881,10 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
         }
         iv64 a, m;
         if (tab) {
-            const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
-            a = tab_group64(P, Tb, c.p, SP, k, gl, c.r, 0);
-            m = tab_group64(P, Tb, c.p, SP, k, gl, c.r, 1);
-            if (pool.fp32) {
-                const iv32 f = tab_group32(P, Tb, c.p, SP, k, gl, c.r);
-                pool.rgsum32[dst] = make_float2(f.lo, f.hi);
-            }
+            const int at = k * GB_TAB_MAX_DIRTY + (gl - dr.x);
+            a = iv64{shF[at].x, shF[at].y};
+            m = iv64{shM[at].x, shM[at].y};
+            if (pool.fp32) pool.rgsum32[dst] = sh32[at];
         } else {
             a = group_sum<double>(P, S, gl, X, R, ops);
             m = group_sum<double>(P, S, gl, MX, R, ops);
@@ -867,15 +910,18 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
 __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbParents par, GbChildren ch,
                                                      GbSplit sp, GbEntries En, double tol_x, GbState* st,
                                                      GbTabs Tb, int tab) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ double2 shF[4][GB_SHG], shM[4][GB_SHG];
+    __shared__ float2 sh32[4][GB_SHG];
     if (st->halt || st->overflow) return;
     const long long kept = st->kept;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < kept; s += nwarps) {
         if (pool.recs)
-            materialize_rec(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0);
+            materialize_rec(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0, shF[w], shM[w], sh32[w]);
         else
-            materialize_one(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0);
+            materialize_one(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0, shF[w], shM[w], sh32[w]);
+        __syncwarp();
     }
 }
 

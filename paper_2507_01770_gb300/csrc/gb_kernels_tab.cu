@@ -110,24 +110,26 @@ __global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents pa
             }
         }
     }
-    // group trees of the parent's cached sums (level-major, pairwise)
+    // group trees of the parent's cached sums (level-major, pairwise): one
+    // block, the nodes of a level in parallel, a barrier between levels
     const int kinds = pool.fp32 ? 3 : 2;
     if (blockIdx.x != 0) return;
-    for (int job = threadIdx.x; job < P.n_sum * kinds; job += blockDim.x) {
+    const CacheRef<double2> cf = cache64(pool, P, slot, 0), cm = cache64(pool, P, slot, 1);
+    const CacheRef<float2> c32 = cache32(pool, P, slot);
+    for (int job = 0; job < P.n_sum * kinds; job++) {
         const int k = job % P.n_sum, kind = job / P.n_sum;
         const GbSum S = P.sums[k];
         const size_t nb = (size_t)p * T.tree_nodes + S.node0;
-        const CacheRef<double2> cf = cache64(pool, P, slot, 0), cm = cache64(pool, P, slot, 1);
-        const CacheRef<float2> c32 = cache32(pool, P, slot);
-        for (int g = 0; g < S.ngroups; g++) {
+        for (int g = threadIdx.x; g < S.ngroups; g += blockDim.x) {
             if (kind == 0) T.nf64[nb + g] = cf[S.group0 + g];
             else if (kind == 1) T.nm64[nb + g] = cm[S.group0 + g];
             else T.nf32[nb + g] = c32[S.group0 + g];
         }
+        __syncthreads();
         int off = 0;
         for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
             const int mN = (mL + 1) / 2;
-            for (int q = 0; q < mN; q++) {
+            for (int q = threadIdx.x; q < mN; q += blockDim.x) {
                 const size_t a = nb + off + 2 * q, c = nb + off + mL + q;
                 if (kind == 2) {
                     float2 x = T.nf32[a];
@@ -148,12 +150,48 @@ __global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents pa
                     arr[c] = make_double2(v.lo, v.hi);
                 }
             }
+            __syncthreads();
             off += mL;
         }
     }
 }
 
 // ---------------------------------------------------------------------------
+// Path of sum k's pairwise group tree above its dirty groups [dr.x, dr.y)
+// (values cur[0 .. dr.y - dr.x)), with the parent's tree nodes (node(i),
+// level-major) for the clean siblings; returns the sum.
+template <typename I, typename N>
+__device__ __forceinline__ I tab_path(const GbSum& S, int2 dr, I* cur, N node, int& ops) {
+    I tmp[GB_TAB_MAX_DIRTY];
+    if (S.ngroups == 0 || S.nnodes <= 0) {
+        I z;
+        z.lo = 0;
+        z.hi = 0;
+        return z;
+    }
+    int lo = dr.x, hi = dr.y, off = 0;
+    if (lo >= hi) return node(S.nnodes - 1);   // no dirty group: the parent's root
+    for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
+        const int nlo = lo >> 1, nhi = ((hi - 1) >> 1) + 1;
+        for (int q = nlo; q < nhi; q++) {
+            const int a = 2 * q;
+            I left = (a >= lo && a < hi) ? cur[a - lo] : node(off + a);
+            I v = left;
+            if (a + 1 < mL) {
+                I right = (a + 1 >= lo && a + 1 < hi) ? cur[a + 1 - lo] : node(off + a + 1);
+                v = iadd(left, right);
+                ops += 2;
+            }
+            tmp[q - nlo] = v;
+        }
+        for (int q = 0; q < nhi - nlo; q++) cur[q] = tmp[q];
+        lo = nlo;
+        hi = nhi;
+        off += mL;
+    }
+    return cur[0];
+}
+
 // Sum k of a child: dirty group leaves from the tables, then the path of the
 // pairwise tree above them with the parent's nodes for the clean siblings.
 template <typename T, bool MID>
@@ -165,7 +203,7 @@ __device__ __forceinline__ typename TabPrec<T>::I tab_sum(const GbProg& P, const
     const int2 dr = P.dirty[blk * P.n_sum + k];
     const size_t rowbase = (size_t)p * Tb.max_rows;
     const size_t nb = (size_t)p * Tb.tree_nodes + S.node0;
-    I cur[GB_TAB_MAX_DIRTY], tmp[GB_TAB_MAX_DIRTY];
+    I cur[GB_TAB_MAX_DIRTY];
     for (int g = dr.x; g < dr.y; g++) {
         Tree<I> tr;
         tr.init();
@@ -189,14 +227,7 @@ __device__ __forceinline__ typename TabPrec<T>::I tab_sum(const GbProg& P, const
         ops += 2 * (cnt > 0 ? cnt - 1 : 0);
         cur[g - dr.x] = tr.result();
     }
-    if (S.ngroups == 0 || S.nnodes <= 0) {
-        I z;
-        z.lo = 0;
-        z.hi = 0;
-        return z;
-    }
-    int lo = dr.x, hi = dr.y, off = 0;
-    auto node = [&](size_t i) -> I {
+    return tab_path(S, dr, cur, [&](int i) -> I {
         if (MID) {
             iv64 m = mid_node(Tb, nb + i);
             I v;
@@ -205,27 +236,7 @@ __device__ __forceinline__ typename TabPrec<T>::I tab_sum(const GbProg& P, const
             return v;
         }
         return TabPrec<T>::node(Tb, nb + i);
-    };
-    if (lo >= hi) return node(S.nnodes - 1);   // no dirty group: the parent's root
-    for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
-        const int nlo = lo >> 1, nhi = ((hi - 1) >> 1) + 1;
-        for (int q = nlo; q < nhi; q++) {
-            const int a = 2 * q;
-            I left = (a >= lo && a < hi) ? cur[a - lo] : node(off + a);
-            I v = left;
-            if (a + 1 < mL) {
-                I right = (a + 1 >= lo && a + 1 < hi) ? cur[a + 1 - lo] : node(off + a + 1);
-                v = iadd(left, right);
-                ops += 2;
-            }
-            tmp[q - nlo] = v;
-        }
-        for (int q = 0; q < nhi - nlo; q++) cur[q] = tmp[q];
-        lo = nlo;
-        hi = nhi;
-        off += mL;
-    }
-    return cur[0];
+    }, ops);
 }
 
 // First-order test from the tables (same accumulation order as block_mono).
@@ -379,6 +390,202 @@ __global__ void __launch_bounds__(128) k_eval32_tab(GbProg P, GbPool pool, GbPar
     }
 }
 
+// ---------------------------------------------------------------------------
+// One child per warp (generations with few children): the lanes share the
+// dirty terms of each group (warp_group) and the coordinates of the
+// first-order test; the group-tree paths and the outer expression are
+// computed by every lane alike.  Same operations in the same order as the
+// per-thread kernels, so the results are identical.  Operation counts: the
+// work every lane repeats is counted once (lane 0), the shared work per lane.
+
+// First-order test, coordinates of the block spread over the lanes.
+template <typename T>
+__device__ __forceinline__ bool tab_mono_w(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
+                                           int blk, unsigned r, const View<double>& X64,
+                                           const typename TabPrec<T>::I* O, typename TabPrec<T>::I* OA,
+                                           int& red, int& par, int lane) {
+    typedef typename TabPrec<T>::I I;
+    for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
+    OA[P.outer_root] = mk<T>((T)1, (T)1);
+    reverse_sweep<T>(P.outer, P.n_outer, O, OA, red);
+    const int c0 = blk * P.B, c1 = min(P.n, c0 + P.B);
+    const size_t rowbase = (size_t)p * Tb.max_rows;
+    bool hit = false;
+    for (int j = c0 + lane; j < c1 && !hit; j += 32) {
+        I g;
+        bool have = false;
+        for (int v = 0; v < P.n_var_leaves; v++) {
+            GbVarLeaf L = P.var_leaves[v];
+            if (L.coord != j) continue;
+            if (have) g = iadd(g, OA[L.reg]), par += 2;
+            else g = OA[L.reg], have = true;
+        }
+        for (int k = 0; k < P.n_sum; k++) {
+            const int2 rg = P.jk[SP.jk0 + (j - c0) * P.n_sum + k];
+            if (rg.x == rg.y) continue;
+            I Dk;
+            for (int q = rg.x; q < rg.y; q++) {
+                const GbContrib C = P.contribs[q];
+                const GbDTerm D = P.dterms[SP.dterm0 + C.dterm];
+                const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
+                I v = TabPrec<T>::tl(Tb, (rowbase + D.row + combo) * Tb.max_leaves + C.leaf);
+                if (q > rg.x) Dk = iadd(Dk, v), par += 2;
+                else Dk = v;
+            }
+            const I a = OA[P.sums[k].outer_reg];
+            I term;
+            if (a.lo == (T)1 && a.hi == (T)1) term = Dk;
+            else term = imul(a, Dk), par += 2;
+            if (have) g = iadd(g, term), par += 2;
+            else g = term, have = true;
+        }
+        if (!have) g = mk<T>((T)0, (T)0);
+        iv64 x = X64.get(j);
+        if ((g.lo > (T)0 && x.lo != __ldg(P.l + j)) || (g.hi < (T)0 && x.hi != __ldg(P.u + j))) hit = true;
+    }
+    return __any_sync(0xffffffffu, hit);
+}
+
+__device__ __forceinline__ bool eval64_tab_child_w(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                                   const GbTabs& Tb, const GbChildren& ch, long long ci,
+                                                   const GbSplit& sp, double gub_prev, unsigned long long* gkey,
+                                                   bool* has_key, int& red, int& pops, int lane) {
+    const ChildCtx c = child_ctx(par, ci, sp);
+    const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
+    if (spi < 0) {
+        if (lane == 0) {
+            ch.flag[ci] = 0;
+            ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
+        }
+        return false;
+    }
+    const GbSplitPos SP = P.sps[spi];
+    const int blk = c.info.z;
+    const View<double> X = view64(pool, par, c, sp);
+    const MidView MX{X};
+    const size_t rowbase = (size_t)c.p * Tb.max_rows, nbase = (size_t)c.p * Tb.tree_nodes;
+    iv64 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];
+    int dt = SP.dterm0;
+    for (int k = 0; k < P.n_sum; k++) {
+        const GbSum S = P.sums[k];
+        const int2 dr = P.dirty[blk * P.n_sum + k];
+        iv64 curF[GB_TAB_MAX_DIRTY], curM[GB_TAB_MAX_DIRTY];
+        for (int g = dr.x; g < dr.y; g++) {
+            iv64 v2[2];
+            int cnt;
+            warp_group<iv64, 2>(P, SP, k, g, c.r, dt, lane,
+                                [&](const GbDTerm& D, unsigned combo, iv64* v) {
+                                    const double2 a = Tb.tv64[rowbase + D.row + combo];
+                                    const double2 b = Tb.tm64[rowbase + D.row + combo];
+                                    v[0] = iv64{a.x, a.y};
+                                    v[1] = iv64{b.x, b.y};
+                                }, v2, cnt);
+            curF[g - dr.x] = v2[0];
+            curM[g - dr.x] = v2[1];
+            red += 4 * (cnt > 0 ? cnt - 1 : 0);
+        }
+        const size_t nb = nbase + S.node0;
+        sums[k] = tab_path(S, dr, curF, [&](int i) { return TabPrec<double>::node(Tb, nb + i); }, red);
+        msums[k] = tab_path(S, dr, curM, [&](int i) { return mid_node(Tb, nb + i); }, red);
+    }
+    const iv64 Fm = outer_fwd<double>(P, MX, msums, O, red);
+    if (Fm.hi == Fm.hi) {
+        *gkey = gb_order_key(Fm.hi);
+        *has_key = true;
+    }
+    const iv64 F = outer_fwd<double>(P, X, sums, O, red);
+    bool keep = !(F.lo > gub_prev);
+    if (keep) keep = !tab_mono_w<double>(P, Tb, c.p, SP, blk, c.r, X, O, OA, red, pops, lane);
+    if (lane == 0) {
+        ch.flo[ci] = canon_lo(F.lo);
+        ch.flag[ci] = keep ? 1 : 0;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(128) k_eval64_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+                                                     GbChildren ch, GbSplit sp, int from_list, GbState* st) {
+    if (st->halt) return;
+    const long long lim = from_list ? st->n32 : st->nch;
+    const double gub_prev = gb_key_value(st->gub_key);
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long key = ~0ull;
+    bool has = false;
+    int red = 0, pops = 0;
+    unsigned long long nv = 0;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < lim; w += nw) {
+        const long long ci = from_list ? (long long)ch.list32[w] : w;
+        unsigned long long k2 = ~0ull;
+        bool h2 = false;
+        if (eval64_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, &k2, &h2, red, pops, lane)) nv++;
+        if (h2 && k2 < key) key = k2, has = true;
+    }
+    warp_min_gub(key, has, st);
+    warp_add_ops((lane == 0 ? red : 0) + pops, &st->ops64);
+    if (lane == 0 && nv) {
+        atomicAdd((unsigned long long*)&st->evals64, nv);
+        atomicAdd((unsigned long long*)&st->mids, nv);
+        if (!from_list) atomicAdd((unsigned long long*)&st->children, nv);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_eval32_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+                                                     GbChildren ch, GbSplit sp, GbState* st) {
+    if (st->halt) return;
+    const long long lim = st->nch;
+    const double gub_prev = gb_key_value(st->gub_key);
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    int red = 0, pops = 0;
+    unsigned long long nv = 0;
+    for (long long ci = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; ci < lim; ci += nw) {
+        const ChildCtx c = child_ctx(par, ci, sp);
+        const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
+        if (lane == 0) {
+            ch.flag[ci] = 0;
+            ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
+        }
+        if (spi < 0) {
+            if (lane == 0) ch.flag32[ci] = 0;
+            continue;
+        }
+        nv++;
+        const GbSplitPos SP = P.sps[spi];
+        const int blk = c.info.z;
+        const View<float> X = view32(pool, par, c, sp);
+        const View<double> X64 = view64(pool, par, c, sp);
+        const size_t rowbase = (size_t)c.p * Tb.max_rows, nbase = (size_t)c.p * Tb.tree_nodes;
+        iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+        int dt = SP.dterm0;
+        for (int k = 0; k < P.n_sum; k++) {
+            const GbSum S = P.sums[k];
+            const int2 dr = P.dirty[blk * P.n_sum + k];
+            iv32 cur[GB_TAB_MAX_DIRTY];
+            for (int g = dr.x; g < dr.y; g++) {
+                int cnt;
+                warp_group<iv32, 1>(P, SP, k, g, c.r, dt, lane,
+                                    [&](const GbDTerm& D, unsigned combo, iv32* v) {
+                                        const float2 a = Tb.tv32[rowbase + D.row + combo];
+                                        v[0] = iv32{a.x, a.y};
+                                    }, cur + (g - dr.x), cnt);
+                red += 2 * (cnt > 0 ? cnt - 1 : 0);
+            }
+            const size_t nb = nbase + S.node0;
+            sums[k] = tab_path(S, dr, cur, [&](int i) { return TabPrec<float>::node(Tb, nb + i); }, red);
+        }
+        const iv32 F = outer_fwd<float>(P, X, sums, O, red);
+        bool keep = !((double)F.lo > gub_prev);
+        if (keep) keep = !tab_mono_w<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, red, pops, lane);
+        if (lane == 0) ch.flag32[ci] = keep ? 1 : 0;
+    }
+    warp_add_ops((lane == 0 ? red : 0) + pops, &st->ops32);
+    if (lane == 0 && nv) {
+        atomicAdd((unsigned long long*)&st->evals32, nv);
+        atomicAdd((unsigned long long*)&st->children, nv);
+    }
+}
+
 unsigned grid_for(long long items, int per_block) {
     long long g = (items + per_block - 1) / per_block;
     return (unsigned)(g < 1 ? 1 : g);
@@ -397,6 +604,12 @@ cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents&
 cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                  const GbChildren& ch, long long Cmax, const GbSplit& sp, bool from_list,
                                  GbState* st, cudaStream_t s) {
+    if (gb_warp_per_child(Cmax)) {
+        unsigned g = grid_for(Cmax * 32, 128);
+        if (g > 152 * 32) g = 152 * 32;
+        k_eval64_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
+        return cudaGetLastError();
+    }
     unsigned g = grid_for(Cmax, 128);
     if (g > 152 * 32) g = 152 * 32;
     k_eval64_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
@@ -406,6 +619,12 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
 cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                  const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
                                  cudaStream_t s) {
+    if (gb_warp_per_child(Cmax)) {
+        unsigned g = grid_for(Cmax * 32, 128);
+        if (g > 152 * 32) g = 152 * 32;
+        k_eval32_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);
+        return cudaGetLastError();
+    }
     unsigned g = grid_for(Cmax, 128);
     if (g > 152 * 32) g = 152 * 32;
     k_eval32_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);

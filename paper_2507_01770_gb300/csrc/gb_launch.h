@@ -104,6 +104,11 @@ struct GbGenConst {
     long long R;            // block records: capacity
 };
 
+// Child kernels run one child per warp when a generation has few children
+// (fewer than 2^16: one child per thread would leave most of the 152 SMs
+// idle), else one child per thread.
+inline bool gb_warp_per_child(long long Cmax) { return Cmax < (1LL << 16); }
+
 cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, double tol_x,
                                 GbState* st, cudaStream_t s);
 // Active count of the pool; count and GUB are read from the device state,
