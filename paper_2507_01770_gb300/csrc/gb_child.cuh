@@ -8,8 +8,9 @@
 namespace gb {
 
 __device__ __forceinline__ double canon_lo(double x) {
-    if (x != x) return -__longlong_as_double(0x7ff0000000000000LL);
-    if (x == 0.0) return 0.0;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    if ((b & 0x7fffffffffffffffULL) > 0x7ff0000000000000ULL) return -__longlong_as_double(0x7ff0000000000000LL);
+    if ((b << 1) == 0) return 0.0;
     return x;
 }
 

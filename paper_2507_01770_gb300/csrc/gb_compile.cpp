@@ -398,7 +398,9 @@ void gb_build_tables(GbHostProg* P, int m, int d) {
                             int leaf = 0;
                             for (int t = S.ins0; t < S.ins0 + S.nins; t++) {
                                 if (P->tins[t].op != D_IVAR) continue;
-                                if (i + P->tins[t].aux == j) P->contribs.push_back(GbContrib{q, leaf});
+                                if (i + P->tins[t].aux == j)
+                                    P->contribs.push_back(GbContrib{q, leaf, D.row * max_leaves + leaf, D.dshift,
+                                                                    (uint16_t)((1u << (D.w * P->mshift)) - 1u)});
                                 leaf++;
                             }
                         }

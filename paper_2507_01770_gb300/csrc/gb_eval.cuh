@@ -118,16 +118,43 @@ template <typename I> struct Tree {
     }
     __device__ __forceinline__ I result() const {
         I r;
-        bool have = false;
-        for (int L = 0; L < 20; L++) {
-            if (!((cnt >> L) & 1u)) continue;
-            r = have ? iadd(lvl[L], r) : lvl[L];
-            have = true;
-        }
-        if (!have) { r.lo = 0; r.hi = 0; }
+        if (!cnt) { r.lo = 0; r.hi = 0; return r; }
+        // levels present in ascending order (the set bits of cnt)
+        unsigned c = cnt;
+        r = lvl[__ffs(c) - 1];
+        for (c &= c - 1; c; c &= c - 1) r = iadd(lvl[__ffs(c) - 1], r);
         return r;
     }
 };
+
+// Division, square root and the transcendentals, kept out of line: the
+// interpreter loops below stay small in the instruction cache, and these
+// operations cost far more than a call.
+template <typename I> __device__ __noinline__ I slow_fwd(int op, I a, I b) {
+    switch (op) {
+    case D_DIV: return idiv(a, b);
+    case D_SQRT: return isqrt(a);
+    case D_EXP: return iexp(a);
+    case D_SIN: return itrig(a, false);
+    default: return itrig(a, true);   // D_COS
+    }
+}
+// Adjoint contributions of node v = op(a, b) with adjoint g: *da to operand
+// a (and *db to b for a division).
+template <typename I> __device__ __noinline__ void slow_rev(int op, I g, I va, I vb, I vt, I* da, I* db) {
+    typedef decltype(g.lo) T;
+    switch (op) {
+    case D_DIV: {
+        I rb = ircp(vb);
+        *da = imul(g, rb);
+        *db = imul(g, ineg(imul(vt, rb)));
+        break;
+    }
+    case D_SQRT: *da = imul(g, iscale(ircp(vt), (T)0.5)); break;
+    case D_SIN: *da = imul(g, itrig(va, true)); break;
+    default: *da = imul(g, ineg(itrig(va, false))); break;   // D_COS
+    }
+}
 
 // Forward interpretation of one template for term index i; returns the root.
 template <typename T, typename V>
@@ -148,13 +175,13 @@ __device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const G
         case D_ADD: v = iadd(R[in.a], R[in.b]); break;
         case D_SUB: v = isub(R[in.a], R[in.b]); break;
         case D_MUL: v = imul(R[in.a], R[in.b]); break;
-        case D_DIV: v = idiv(R[in.a], R[in.b]); break;
         case D_NEG: v = ineg(R[in.a]); break;
         case D_SQR: v = isqr(R[in.a]); break;
-        case D_SQRT: v = isqrt(R[in.a]); break;
-        case D_EXP: v = iexp(R[in.a]); break;
-        case D_SIN: v = itrig(R[in.a], false); break;
-        case D_COS: v = itrig(R[in.a], true); break;
+        case D_DIV: v = slow_fwd(in.op, R[in.a], R[in.b]); break;
+        case D_SQRT:
+        case D_EXP:
+        case D_SIN:
+        case D_COS: v = slow_fwd(in.op, R[in.a], R[in.a]); break;
         case D_SCALE:
             if (in.clo32 == in.chi32 || sizeof(T) == 8)
                 v = iscale(R[in.a], sizeof(T) == 8 ? (T)in.c : (T)in.clo32);
@@ -195,17 +222,23 @@ __device__ __forceinline__ void reverse_sweep(const GbIns* ins, int nins, const 
             break;
         }
         case D_DIV: {
-            I rb = ircp(V[in.b]);
-            A[in.a] = iadd(A[in.a], imul(g, rb));
-            A[in.b] = iadd(A[in.b], imul(g, ineg(imul(V[t], rb))));
+            I da, db;
+            slow_rev(in.op, g, V[in.a], V[in.b], V[t], &da, &db);
+            A[in.a] = iadd(A[in.a], da);
+            A[in.b] = iadd(A[in.b], db);
             break;
         }
         case D_NEG: A[in.a] = iadd(A[in.a], ineg(g)); break;
         case D_SQR: A[in.a] = iadd(A[in.a], imul(g, iscale(V[in.a], (T)2))); break;
-        case D_SQRT: A[in.a] = iadd(A[in.a], imul(g, iscale(ircp(V[t]), (T)0.5))); break;
         case D_EXP: A[in.a] = iadd(A[in.a], imul(g, V[t])); break;
-        case D_SIN: A[in.a] = iadd(A[in.a], imul(g, itrig(V[in.a], true))); break;
-        case D_COS: A[in.a] = iadd(A[in.a], imul(g, ineg(itrig(V[in.a], false)))); break;
+        case D_SQRT:
+        case D_SIN:
+        case D_COS: {
+            I da, db;
+            slow_rev(in.op, g, V[in.a], V[in.a], V[t], &da, &db);
+            A[in.a] = iadd(A[in.a], da);
+            break;
+        }
         case D_SCALE:
             if (in.clo32 == in.chi32 || sizeof(T) == 8)
                 A[in.a] = iadd(A[in.a], iscale(g, sizeof(T) == 8 ? (T)in.c : (T)in.clo32));
@@ -277,13 +310,13 @@ __device__ __forceinline__ typename Prec<T>::I outer_fwd(const GbProg& P, const 
         case D_ADD: v = iadd(O[in.a], O[in.b]); break;
         case D_SUB: v = isub(O[in.a], O[in.b]); break;
         case D_MUL: v = imul(O[in.a], O[in.b]); break;
-        case D_DIV: v = idiv(O[in.a], O[in.b]); break;
         case D_NEG: v = ineg(O[in.a]); break;
         case D_SQR: v = isqr(O[in.a]); break;
-        case D_SQRT: v = isqrt(O[in.a]); break;
-        case D_EXP: v = iexp(O[in.a]); break;
-        case D_SIN: v = itrig(O[in.a], false); break;
-        case D_COS: v = itrig(O[in.a], true); break;
+        case D_DIV:
+        case D_SQRT:
+        case D_EXP:
+        case D_SIN:
+        case D_COS: v = slow_fwd(in.op, O[in.a], O[in.b]); break;
         case D_SCALE:
             if (in.clo32 == in.chi32 || sizeof(T) == 8)
                 v = iscale(O[in.a], sizeof(T) == 8 ? (T)in.c : (T)in.clo32);
@@ -368,7 +401,8 @@ __device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X,
             Gout[2 * (j - c0) + 1] = (double)g.hi;
         }
         iv64 x = X64.get(j);
-        if ((g.lo > (T)0 && x.lo != __ldg(P.l + j)) || (g.hi < (T)0 && x.hi != __ldg(P.u + j))) {
+        if ((gt_zero(g.lo) && !same_value(x.lo, __ldg(P.l + j))) ||
+            (lt_zero(g.hi) && !same_value(x.hi, __ldg(P.u + j)))) {
             mono = true;
             if (!Gout) break;
         }

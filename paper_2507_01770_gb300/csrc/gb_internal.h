@@ -80,7 +80,15 @@ struct GbDTerm {
     int32_t term;             // term ordinal within the sum
     int32_t row;              // first table row of the term (m^w rows)
 };
-struct GbContrib { int32_t dterm, leaf; };   // a leaf adjoint feeding one coordinate
+// A leaf adjoint feeding one coordinate: dirty term, leaf, and its table
+// address (row * max_leaves + leaf; the child's digits select
+// base + ((r >> dshift) & mask) * max_leaves).
+struct GbContrib {
+    int32_t dterm, leaf;
+    int32_t base;
+    int16_t dshift;
+    uint16_t mask;
+};
 
 // Outer VAR leaf: register and coordinate (for the gradient).
 struct GbVarLeaf { int32_t reg, coord; };

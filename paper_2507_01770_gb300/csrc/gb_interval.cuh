@@ -69,6 +69,31 @@ __device__ __forceinline__ unsigned long long magkey(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
 }
 __device__ __forceinline__ unsigned magkey(float x) { return absbits(x); }
+// IEEE comparisons with zero and equality on the integer pipe (the FP64 pipe
+// is kept for the directed arithmetic): false for NaN, +0 == -0.
+__device__ __forceinline__ bool gt_zero(double x) {
+    long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool lt_zero(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return b > 0x8000000000000000ULL && b <= 0xfff0000000000000ULL;
+}
+__device__ __forceinline__ bool same_value(double x, double y) {
+    unsigned long long a = (unsigned long long)__double_as_longlong(x), b = (unsigned long long)__double_as_longlong(y);
+    return (a == b && (a & 0x7fffffffffffffffULL) <= 0x7ff0000000000000ULL) || ((a | b) << 1) == 0;
+}
+__device__ __forceinline__ bool is_one(double x) { return __double_as_longlong(x) == 0x3ff0000000000000LL; }
+__device__ __forceinline__ bool gt_zero(float x) {
+    int b = __float_as_int(x);
+    return b > 0 && b <= 0x7f800000;
+}
+__device__ __forceinline__ bool lt_zero(float x) {
+    unsigned b = (unsigned)__float_as_int(x);
+    return b > 0x80000000u && b <= 0xff800000u;
+}
+__device__ __forceinline__ bool is_one(float x) { return __float_as_int(x) == 0x3f800000; }
+
 __device__ __forceinline__ bool any_inf(double a, double b, double c, double d) {
     unsigned m = max(max(absbits(a), absbits(b)), max(absbits(c), absbits(d)));
     return m >= 0x7ff00000u;

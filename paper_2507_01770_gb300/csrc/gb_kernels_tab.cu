@@ -16,23 +16,34 @@
 
 using namespace gb;
 
+// Resident blocks of 128 threads per SM the one-child-per-thread kernels are
+// compiled for (register budget 65536 / (128 * GB_TAB_MINB) per thread).
+#ifndef GB_TAB_MINB
+#define GB_TAB_MINB 6
+#endif
+// Blocks per SM of their grid (each thread loops over children).
+#ifndef GB_TAB_GRID
+#define GB_TAB_GRID 32
+#endif
+
 namespace {
 
 template <typename T> struct TabPrec;
 template <> struct TabPrec<double> {
     typedef iv64 I;
+    typedef double2 P2;
     static __device__ __forceinline__ I tv(const GbTabs& T, size_t i) { double2 v = T.tv64[i]; return I{v.x, v.y}; }
     static __device__ __forceinline__ I tl(const GbTabs& T, size_t i) { double2 v = T.tl64[i]; return I{v.x, v.y}; }
     static __device__ __forceinline__ I node(const GbTabs& T, size_t i) { double2 v = T.nf64[i]; return I{v.x, v.y}; }
 };
 template <> struct TabPrec<float> {
     typedef iv32 I;
+    typedef float2 P2;
     static __device__ __forceinline__ I tv(const GbTabs& T, size_t i) { float2 v = T.tv32[i]; return I{v.x, v.y}; }
     static __device__ __forceinline__ I tl(const GbTabs& T, size_t i) { float2 v = T.tl32[i]; return I{v.x, v.y}; }
     static __device__ __forceinline__ I node(const GbTabs& T, size_t i) { float2 v = T.nf32[i]; return I{v.x, v.y}; }
 };
 
-__device__ __forceinline__ iv64 mid_tv(const GbTabs& T, size_t i) { double2 v = T.tm64[i]; return iv64{v.x, v.y}; }
 __device__ __forceinline__ iv64 mid_node(const GbTabs& T, size_t i) { double2 v = T.nm64[i]; return iv64{v.x, v.y}; }
 
 // ---------------------------------------------------------------------------
@@ -192,54 +203,162 @@ __device__ __forceinline__ I tab_path(const GbSum& S, int2 dr, I* cur, N node, i
     return cur[0];
 }
 
-// Sum k of a child: dirty group leaves from the tables, then the path of the
-// pairwise tree above them with the parent's nodes for the clean siblings.
-template <typename T, bool MID>
-__device__ __forceinline__ typename TabPrec<T>::I tab_sum(const GbProg& P, const GbTabs& Tb, long long p,
-                                                          const GbSplitPos& SP, int k, int blk, unsigned r,
-                                                          int& dt, int& ops) {
-    typedef typename TabPrec<T>::I I;
-    const GbSum S = P.sums[k];
-    const int2 dr = P.dirty[blk * P.n_sum + k];
-    const size_t rowbase = (size_t)p * Tb.max_rows;
-    const size_t nb = (size_t)p * Tb.tree_nodes + S.node0;
-    I cur[GB_TAB_MAX_DIRTY];
-    for (int g = dr.x; g < dr.y; g++) {
-        Tree<I> tr;
-        tr.init();
-        int cnt = 0;
-        while (dt < SP.dterm0 + SP.ndterm) {
+// Pairwise tree over the terms of one dirty group, two tables at once (F and
+// midpoint): the in-place tree within aligned chunks of 4 terms in registers,
+// then the binary counter over the chunk sums (the same tree as pushing
+// every term, see warp_group).
+template <typename I, typename L>
+__device__ __forceinline__ void group_pair(const GbProg& P, int k, int g, int& dt, int dend, L load, I& outA,
+                                           I& outB, int& cnt) {
+    Tree<I> ta, tb;
+    ta.init();
+    tb.init();
+    cnt = 0;
+    int chunks = 0;
+    I a0, a1, a2, a3, b0, b1, b2, b3;
+    for (;;) {
+        int r = 0;
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            if (dt >= dend) break;
             const GbDTerm D = P.dterms[dt];
             if (D.sum != k || D.group != g) break;
-            const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
-            I v;
-            if (MID) {
-                iv64 m = mid_tv(Tb, rowbase + D.row + combo);
-                v.lo = m.lo;
-                v.hi = m.hi;
-            } else {
-                v = TabPrec<T>::tv(Tb, rowbase + D.row + combo);
-            }
-            tr.push(v);
+            I x, y;
+            load(D, x, y);
+            if (t == 0) a0 = x, b0 = y;
+            else if (t == 1) a1 = x, b1 = y;
+            else if (t == 2) a2 = x, b2 = y;
+            else a3 = x, b3 = y;
+            r++;
+            dt++;
+        }
+        if (r == 0) break;
+        // in-place tree over r <= 4 items: s = 1 then s = 2
+        if (r > 1) a0 = iadd(a0, a1), b0 = iadd(b0, b1);
+        if (r > 3) a2 = iadd(a2, a3), b2 = iadd(b2, b3);
+        if (r > 2) a0 = iadd(a0, a2), b0 = iadd(b0, b2);
+        cnt += r;
+        if (chunks == 0 && r < 4) {   // the whole group in one chunk
+            outA = a0;
+            outB = b0;
+            return;
+        }
+        ta.push(a0);
+        tb.push(b0);
+        chunks++;
+        if (r < 4) break;
+    }
+    if (cnt == 0) {
+        outA.lo = outA.hi = 0;
+        outB.lo = outB.hi = 0;
+        return;
+    }
+    outA = ta.result();
+    outB = tb.result();
+}
+
+// Sum k of a child (FP32 tables): dirty group leaves from the tables, then
+// the path of the pairwise tree above them with the parent's nodes for the
+// clean siblings.
+__device__ __forceinline__ iv32 tab_sum32(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
+                                          int k, int blk, unsigned r, int& dt, int& ops) {
+    const GbSum S = P.sums[k];
+    const int2 dr = P.dirty[blk * P.n_sum + k];
+    const float2* tv = Tb.tv32 + (size_t)p * Tb.max_rows;
+    const float2* nfk = Tb.nf32 + (size_t)p * Tb.tree_nodes + S.node0;
+    const int dend = SP.dterm0 + SP.ndterm;
+    iv32 cur[GB_TAB_MAX_DIRTY];
+    for (int g = dr.x; g < dr.y; g++) {
+        Tree<iv32> tr;
+        tr.init();
+        int cnt = 0;
+        while (dt < dend) {
+            const GbDTerm D = P.dterms[dt];
+            if (D.sum != k || D.group != g) break;
+            const float2 v = tv[D.row + (int)((r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u))];
+            tr.push(iv32{v.x, v.y});
             cnt++;
             dt++;
         }
         ops += 2 * (cnt > 0 ? cnt - 1 : 0);
         cur[g - dr.x] = tr.result();
     }
-    return tab_path(S, dr, cur, [&](int i) -> I {
-        if (MID) {
-            iv64 m = mid_node(Tb, nb + i);
-            I v;
-            v.lo = m.lo;
-            v.hi = m.hi;
-            return v;
-        }
-        return TabPrec<T>::node(Tb, nb + i);
-    }, ops);
+    return tab_path(S, dr, cur, [&](int i) { const float2 v = nfk[i]; return iv32{v.x, v.y}; }, ops);
 }
 
 // First-order test from the tables (same accumulation order as block_mono).
+template <typename T>
+__device__ __forceinline__ const typename TabPrec<T>::P2* leaf_tab(const GbTabs& Tb, long long p);
+template <>
+__device__ __forceinline__ const double2* leaf_tab<double>(const GbTabs& Tb, long long p) {
+    return Tb.tl64 + (size_t)p * Tb.max_rows * Tb.max_leaves;
+}
+template <>
+__device__ __forceinline__ const float2* leaf_tab<float>(const GbTabs& Tb, long long p) {
+    return Tb.tl32 + (size_t)p * Tb.max_rows * Tb.max_leaves;
+}
+
+// Interval partial of coordinate j (c0 = block start) from the outer leaves
+// and the tabulated leaf adjoints; `unit` marks sums whose outer adjoint is
+// exactly [1, 1] (a plain sum: the product adj * D equals D and is skipped);
+// additions to an exact [0, 0] start are skipped too (they return the other
+// operand's value).
+template <typename T>
+__device__ __forceinline__ typename TabPrec<T>::I tab_partial(const GbProg& P, const GbTabs& Tb,
+                                                              const typename TabPrec<T>::P2* tl,
+                                                              const GbSplitPos& SP, int j, int c0, unsigned r,
+                                                              const typename TabPrec<T>::I* OA, unsigned unit,
+                                                              int& ops) {
+    typedef typename TabPrec<T>::I I;
+    I g;
+    bool have = false;
+    for (int v = 0; v < P.n_var_leaves; v++) {
+        GbVarLeaf L = P.var_leaves[v];
+        if (L.coord != j) continue;
+        if (have) g = iadd(g, OA[L.reg]), ops += 2;
+        else g = OA[L.reg], have = true;
+    }
+    for (int k = 0; k < P.n_sum; k++) {
+        const int2 rg = P.jk[SP.jk0 + (j - c0) * P.n_sum + k];
+        if (rg.x == rg.y) continue;
+        I Dk;
+        for (int q = rg.x; q < rg.y; q++) {
+            const GbContrib C = P.contribs[q];
+            const unsigned combo = (r >> C.dshift) & C.mask;
+            const typename TabPrec<T>::P2 e = tl[C.base + (int)combo * Tb.max_leaves];
+            const I v = mk<T>(e.x, e.y);
+            if (q > rg.x) Dk = iadd(Dk, v), ops += 2;
+            else Dk = v;
+        }
+        I term;
+        if ((unit >> k) & 1u) term = Dk;
+        else term = imul(OA[P.sums[k].outer_reg], Dk), ops += 2;
+        if (have) g = iadd(g, term), ops += 2;
+        else g = term, have = true;
+    }
+    if (!have) g = mk<T>((T)0, (T)0);
+    return g;
+}
+
+// Sums whose outer adjoint is exactly [1, 1].
+template <typename I>
+__device__ __forceinline__ unsigned unit_sums(const GbProg& P, const I* OA) {
+    unsigned unit = 0;
+    for (int k = 0; k < P.n_sum; k++) {
+        const I a = OA[P.sums[k].outer_reg];
+        if (is_one(a.lo) && is_one(a.hi)) unit |= 1u << k;
+    }
+    return unit;
+}
+
+// The first-order test discards the box when a partial has a fixed sign and
+// the box does not touch the bound the sign points to.
+__device__ __forceinline__ bool mono_hit(const GbProg& P, const View<double>& X64, int j, bool pos, bool neg) {
+    if (!pos && !neg) return false;
+    const iv64 x = X64.get(j);
+    return (pos && !same_value(x.lo, __ldg(P.l + j))) || (neg && !same_value(x.hi, __ldg(P.u + j)));
+}
+
 template <typename T>
 __device__ __forceinline__ bool tab_mono(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
                                          int blk, unsigned r, const View<double>& X64,
@@ -249,43 +368,46 @@ __device__ __forceinline__ bool tab_mono(const GbProg& P, const GbTabs& Tb, long
     OA[P.outer_root] = mk<T>((T)1, (T)1);
     reverse_sweep<T>(P.outer, P.n_outer, O, OA, ops);
     const int c0 = blk * P.B, c1 = min(P.n, c0 + P.B);
-    const size_t rowbase = (size_t)p * Tb.max_rows;
-    // Sums whose outer adjoint is exactly [1, 1] (a plain sum): the product
-    // adj * D equals D, so it is skipped; additions to an exact [0, 0] start
-    // are skipped too (they return the other operand's value).
+    const typename TabPrec<T>::P2* tl = leaf_tab<T>(Tb, p);
+    const unsigned unit = unit_sums(P, OA);
     for (int j = c0; j < c1; j++) {
-        I g;
-        bool have = false;
-        for (int v = 0; v < P.n_var_leaves; v++) {
-            GbVarLeaf L = P.var_leaves[v];
-            if (L.coord != j) continue;
-            if (have) g = iadd(g, OA[L.reg]), ops += 2;
-            else g = OA[L.reg], have = true;
-        }
-        for (int k = 0; k < P.n_sum; k++) {
-            const int2 rg = P.jk[SP.jk0 + (j - c0) * P.n_sum + k];
-            if (rg.x == rg.y) continue;
-            I Dk;
-            for (int q = rg.x; q < rg.y; q++) {
-                const GbContrib C = P.contribs[q];
-                const GbDTerm D = P.dterms[SP.dterm0 + C.dterm];
-                const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
-                I v = TabPrec<T>::tl(Tb, (rowbase + D.row + combo) * Tb.max_leaves + C.leaf);
-                if (q > rg.x) Dk = iadd(Dk, v), ops += 2;
-                else Dk = v;
-            }
-            const I a = OA[P.sums[k].outer_reg];
-            I term;
-            if (a.lo == (T)1 && a.hi == (T)1) term = Dk;
-            else term = imul(a, Dk), ops += 2;
-            if (have) g = iadd(g, term), ops += 2;
-            else g = term, have = true;
-        }
-        if (!have) g = mk<T>((T)0, (T)0);
-        iv64 x = X64.get(j);
-        if ((g.lo > (T)0 && x.lo != __ldg(P.l + j)) || (g.hi < (T)0 && x.hi != __ldg(P.u + j))) return true;
+        const I g = tab_partial<T>(P, Tb, tl, SP, j, c0, r, OA, unit, ops);
+        if (mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi))) return true;
     }
     return false;
+}
+
+// F and midpoint sums of a child in one walk over the dirty terms.
+__device__ __forceinline__ void tab_sums64(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
+                                           int blk, unsigned r, iv64* sums, iv64* msums, int& ops) {
+    const double2* tv = Tb.tv64 + (size_t)p * Tb.max_rows;
+    const double2* tm = Tb.tm64 + (size_t)p * Tb.max_rows;
+    const double2* nf = Tb.nf64 + (size_t)p * Tb.tree_nodes;
+    const double2* nm = Tb.nm64 + (size_t)p * Tb.tree_nodes;
+    int dt = SP.dterm0;
+    const int dend = SP.dterm0 + SP.ndterm;
+    auto load = [&](const GbDTerm& D, iv64& x, iv64& y) {
+        const int at = D.row + (int)((r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u));
+        const double2 a = tv[at], b = tm[at];
+        x = iv64{a.x, a.y};
+        y = iv64{b.x, b.y};
+    };
+    for (int k = 0; k < P.n_sum; k++) {
+        const GbSum S = P.sums[k];
+        const int2 dr = P.dirty[blk * P.n_sum + k];
+        const double2* nfk = nf + S.node0;
+        const double2* nmk = nm + S.node0;
+        auto nodeF = [&](int i) { const double2 v = nfk[i]; return iv64{v.x, v.y}; };
+        auto nodeM = [&](int i) { const double2 v = nmk[i]; return iv64{v.x, v.y}; };
+        iv64 curF[GB_TAB_MAX_DIRTY], curM[GB_TAB_MAX_DIRTY];
+        for (int g = dr.x; g < dr.y; g++) {
+            int cnt;
+            group_pair(P, k, g, dt, dend, load, curF[g - dr.x], curM[g - dr.x], cnt);
+            ops += 4 * (cnt > 0 ? cnt - 1 : 0);
+        }
+        sums[k] = tab_path(S, dr, curF, nodeF, ops);
+        msums[k] = tab_path(S, dr, curM, nodeM, ops);
+    }
 }
 
 // FP64 child: midpoint sample, F(X), first-order test.
@@ -304,16 +426,13 @@ __device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& 
     const int blk = c.info.z;
     View<double> X = view64(pool, par, c, sp);
     MidView MX{X};
-    iv64 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
-    int dt = SP.dterm0;
-    for (int k = 0; k < P.n_sum; k++) sums[k] = tab_sum<double, true>(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
-    iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
+    iv64 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];
+    tab_sums64(P, Tb, c.p, SP, blk, c.r, sums, msums, ops);
+    iv64 Fm = outer_fwd<double>(P, MX, msums, O, ops);
     if (Fm.hi == Fm.hi) {
         *gkey = gb_order_key(Fm.hi);
         *has_key = true;
     }
-    dt = SP.dterm0;
-    for (int k = 0; k < P.n_sum; k++) sums[k] = tab_sum<double, false>(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
     bool keep = !(F.lo > gub_prev);
     if (keep) keep = !tab_mono<double>(P, Tb, c.p, SP, blk, c.r, X, O, OA, ops);
@@ -322,7 +441,7 @@ __device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& 
     return true;
 }
 
-__global__ void __launch_bounds__(128) k_eval64_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+__global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval64_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
                                                     GbChildren ch, GbSplit sp, int from_list, GbState* st) {
     if (st->halt) return;
     const long long lim = from_list ? st->n32 : st->nch;
@@ -348,7 +467,7 @@ __global__ void __launch_bounds__(128) k_eval64_tab(GbProg P, GbPool pool, GbPar
     }
 }
 
-__global__ void __launch_bounds__(128) k_eval32_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+__global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval32_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
                                                     GbChildren ch, GbSplit sp, GbState* st) {
     if (st->halt) return;
     const long long lim = st->nch;
@@ -372,7 +491,7 @@ __global__ void __launch_bounds__(128) k_eval32_tab(GbProg P, GbPool pool, GbPar
                 iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
                 int dt = SP.dterm0;
                 for (int k = 0; k < P.n_sum; k++)
-                    sums[k] = tab_sum<float, false>(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
+                    sums[k] = tab_sum32(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
                 iv32 F = outer_fwd<float>(P, X, sums, O, ops);
                 bool keep = !((double)F.lo > gub_prev);
                 if (keep) keep = !tab_mono<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, ops);
@@ -409,39 +528,12 @@ __device__ __forceinline__ bool tab_mono_w(const GbProg& P, const GbTabs& Tb, lo
     OA[P.outer_root] = mk<T>((T)1, (T)1);
     reverse_sweep<T>(P.outer, P.n_outer, O, OA, red);
     const int c0 = blk * P.B, c1 = min(P.n, c0 + P.B);
-    const size_t rowbase = (size_t)p * Tb.max_rows;
+    const typename TabPrec<T>::P2* tl = leaf_tab<T>(Tb, p);
+    const unsigned unit = unit_sums(P, OA);
     bool hit = false;
     for (int j = c0 + lane; j < c1 && !hit; j += 32) {
-        I g;
-        bool have = false;
-        for (int v = 0; v < P.n_var_leaves; v++) {
-            GbVarLeaf L = P.var_leaves[v];
-            if (L.coord != j) continue;
-            if (have) g = iadd(g, OA[L.reg]), par += 2;
-            else g = OA[L.reg], have = true;
-        }
-        for (int k = 0; k < P.n_sum; k++) {
-            const int2 rg = P.jk[SP.jk0 + (j - c0) * P.n_sum + k];
-            if (rg.x == rg.y) continue;
-            I Dk;
-            for (int q = rg.x; q < rg.y; q++) {
-                const GbContrib C = P.contribs[q];
-                const GbDTerm D = P.dterms[SP.dterm0 + C.dterm];
-                const unsigned combo = (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u);
-                I v = TabPrec<T>::tl(Tb, (rowbase + D.row + combo) * Tb.max_leaves + C.leaf);
-                if (q > rg.x) Dk = iadd(Dk, v), par += 2;
-                else Dk = v;
-            }
-            const I a = OA[P.sums[k].outer_reg];
-            I term;
-            if (a.lo == (T)1 && a.hi == (T)1) term = Dk;
-            else term = imul(a, Dk), par += 2;
-            if (have) g = iadd(g, term), par += 2;
-            else g = term, have = true;
-        }
-        if (!have) g = mk<T>((T)0, (T)0);
-        iv64 x = X64.get(j);
-        if ((g.lo > (T)0 && x.lo != __ldg(P.l + j)) || (g.hi < (T)0 && x.hi != __ldg(P.u + j))) hit = true;
+        const I g = tab_partial<T>(P, Tb, tl, SP, j, c0, r, OA, unit, par);
+        hit = mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi));
     }
     return __any_sync(0xffffffffu, hit);
 }
@@ -611,7 +703,7 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
         return cudaGetLastError();
     }
     unsigned g = grid_for(Cmax, 128);
-    if (g > 152 * 32) g = 152 * 32;
+    if (g > 152 * GB_TAB_GRID) g = 152 * GB_TAB_GRID;
     k_eval64_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
     return cudaGetLastError();
 }
@@ -626,7 +718,7 @@ cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbPa
         return cudaGetLastError();
     }
     unsigned g = grid_for(Cmax, 128);
-    if (g > 152 * 32) g = 152 * 32;
+    if (g > 152 * GB_TAB_GRID) g = 152 * GB_TAB_GRID;
     k_eval32_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);
     return cudaGetLastError();
 }
