@@ -92,7 +92,10 @@ typedef struct gb_options {
     size_t pool_bytes;        /* device memory budget for the pool (0: 16 GiB) */
     int32_t device;           /* CUDA device ordinal */
     int32_t eval_mode;        /* child evaluation: 0 auto (term tables when m^d >= 16 and they fit),
-                                 1 bytecode interpreter, 2 term tables when they fit; results are identical */
+                                 1 bytecode interpreter, 2 term tables when they fit (one child per warp
+                                 when a generation has fewer than 2^16 children, else per thread),
+                                 3 / 4 term tables with one child per thread / per warp; results are
+                                 identical */
     int32_t gens_per_sync;    /* <= 1: the host reads the state after every generation (per-kernel timing);
                                  G > 1: generations run as replays of a captured CUDA graph, G between
                                  state reads (the search is the same) */

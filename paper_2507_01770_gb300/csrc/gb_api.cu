@@ -180,6 +180,7 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     if (opt.block <= 0) opt.block = n < 10 ? n : 10;
     if (opt.block > n) return fail(GB_E_INVALID, "block size larger than n");
     if (opt.pool_mode < 0 || opt.pool_mode > 2) return fail(GB_E_INVALID, "pool_mode must be 0, 1 or 2");
+    if (opt.eval_mode < 0 || opt.eval_mode > 4) return fail(GB_E_INVALID, "eval_mode must be 0 .. 4");
     if (opt.max_records < 0) return fail(GB_E_INVALID, "max_records must be >= 0");
     if (opt.split_m != 2 && opt.split_m != 4) return fail(GB_E_INVALID, "split_m must be 2 or 4");
     const int mshift = opt.split_m == 2 ? 1 : 2;
@@ -374,7 +375,7 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         return bad(e, "allocate child buffers");
     // per-parent term tables
     if (opt.eval_mode != 1) {
-        const bool want = opt.eval_mode == 2 || p->fan >= 16;
+        const bool want = opt.eval_mode >= 2 || p->fan >= 16;
         if (p->hp.tab_ok && want) {
             const GbHostProg& Hh = p->hp;
             int32_t* d_spc;
@@ -412,6 +413,7 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             if (fp32 && ((e = alloc(&T.tv32, rows, A)) || (e = alloc(&T.tl32, rows * T.max_leaves, A)) ||
                          (e = alloc(&T.nf32, nodes, A))))
                 return bad(e, "allocate term tables");
+            T.warp = opt.eval_mode == 4 ? 1 : opt.eval_mode == 3 ? 0 : (gb_warp_per_child(p->Cmax) ? 1 : 0);
             p->use_tabs = true;
         }
     }

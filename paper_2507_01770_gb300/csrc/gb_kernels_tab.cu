@@ -696,7 +696,7 @@ cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents&
 cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                  const GbChildren& ch, long long Cmax, const GbSplit& sp, bool from_list,
                                  GbState* st, cudaStream_t s) {
-    if (gb_warp_per_child(Cmax)) {
+    if (T.warp) {
         unsigned g = grid_for(Cmax * 32, 128);
         if (g > 152 * 32) g = 152 * 32;
         k_eval64_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
@@ -711,7 +711,7 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
 cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                  const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
                                  cudaStream_t s) {
-    if (gb_warp_per_child(Cmax)) {
+    if (T.warp) {
         unsigned g = grid_for(Cmax * 32, 128);
         if (g > 152 * 32) g = 152 * 32;
         k_eval32_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);

@@ -78,6 +78,7 @@ struct GbTabs {
     double2* nm64;    // midpoint
     float2* nf32;     // FP32
     int max_rows, max_leaves, tree_nodes;
+    int warp;         // child kernels: 1 one child per warp, 0 one child per thread
 };
 
 // scratch for the three-phase scans
@@ -106,7 +107,7 @@ struct GbGenConst {
 
 // Child kernels run one child per warp when a generation has few children
 // (fewer than 2^16: one child per thread would leave most of the 152 SMs
-// idle), else one child per thread.
+// idle), else one child per thread (eval_mode 3 / 4 force either).
 inline bool gb_warp_per_child(long long Cmax) { return Cmax < (1LL << 16); }
 
 cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, double tol_x,

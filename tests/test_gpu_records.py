@@ -57,7 +57,7 @@ CASES = [
 
 @pytest.mark.parametrize("name,p,o", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("fp32", [0, 1])
-@pytest.mark.parametrize("eval_mode", [1, 2])
+@pytest.mark.parametrize("eval_mode", [1, 3, 4])
 def test_records_identical_to_dense(name, p, o, fp32, eval_mode):
     o = dict(o, fp32_prefilter=fp32, eval_mode=eval_mode, max_generations=3000)
     d = _solve(p, pool_mode=1, **o)

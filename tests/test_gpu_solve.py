@@ -149,16 +149,21 @@ def test_table_path_identical_to_interpreter(fam, kw, opt):
     bits: both paths must give the same run; for polynomials also the oracle's."""
     p = S.make(fam, **kw)
     runs = []
-    for mode in (1, 2):
+    # 1 interpreter, 2 tables (automatic kernel choice), 3 tables with one
+    # child per thread, 4 tables with one child per warp
+    for mode in (1, 2, 3, 4):
         s = gb.Solver(p, eval_mode=mode, **opt)
         runs.append(s.solve())
         s.close()
-    a, b = runs
-    assert a.status == b.status == 0
-    assert a.fmin_lo == b.fmin_lo and a.fmin_hi == b.fmin_hi
-    assert np.array_equal(a.box_lo, b.box_lo) and np.array_equal(a.box_hi, b.box_hi)
-    for k in ("parents", "children", "kept32", "kept", "pool", "gub"):
-        assert np.array_equal(a.trace[k], b.trace[k]), k
+    a = runs[0]
+    for b in runs[1:]:
+        assert a.status == b.status == 0
+        assert a.fmin_lo == b.fmin_lo and a.fmin_hi == b.fmin_hi
+        assert np.array_equal(a.box_lo, b.box_lo) and np.array_equal(a.box_hi, b.box_hi)
+        for k in ("parents", "children", "kept32", "kept", "pool", "gub"):
+            assert np.array_equal(a.trace[k], b.trace[k]), k
+        assert a.box_evals_fp64 == b.box_evals_fp64 and a.mid_evals == b.mid_evals
+    b = runs[2]
     if fam == "chain":
         o = O.Oracle(p, block=opt["block"]).solve(split_m=opt["split_m"], split_d=opt["split_d"],
                                                   max_parents=opt["max_children"] // opt["split_m"] ** opt["split_d"])
