@@ -1,13 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark: box evaluations per second of the GPU interval branch and bound.
 
-Workload (one "step" = one complete solve, every row of the hot path):
+Workloads (one "step" = one complete solve, every row of the hot path):
+
+chain100 (default)
   coupled quartic chain, n = 100, seed 0 (synthetic.chain): alpha~U[50,150],
   beta~U[0.5,2], s~U[-1,2], box [-5,10]^100, min f = 0 at the planted s,
   enclosure width target 1e-6, FP64, variable cycling over blocks of 10
   coordinates with the paper's partition: the 10 coordinates of the block cut
   into 4 pieces each (4^10 = 1,048,576 children), one selected box per
   generation (best-first).
+ackley1000
+  shifted Ackley-type family, n = 1000, box [-32.768, 32.768]^1000, width
+  1e-6, FP32 prefilter + FP64, blocks of 10, 2^10 children of 4 boxes per
+  generation, 16 generations per host synchronisation (CUDA graphs).
+mixed10k
+  n = 10,000: separable cosine terms on even i, chain terms on odd i, box
+  [-5.12, 5.12]^n, width 1e-6, FP32 prefilter + FP64, blocks of 100, 2^10
+  children of one box per generation, block-record box pool.
+serving
+  512 requests, Poisson arrivals (20/s), n log-uniform on [2, 2000], family
+  uniform over sep_cos / chain / ackley, width 1e-6, 150 GB pool budget:
+  served solves/s and p50/p99 latency against one-at-a-time FP64 solves.
 
 value      box evaluations (F + interval gradient + first-order test, FP64 and
            FP32 children) per second over the timed solves, problem and
@@ -16,11 +30,14 @@ value      box evaluations (F + interval gradient + first-order test, FP64 and
 e2e        the same metric through the public C ABI from host buffers:
            gb_create_problem (DAG, tables and bounds copied host -> device),
            gb_solve (boxes and trace copied device -> host), gb_destroy_problem.
-roofline   the FP64 evaluation kernel: directed-rounding FP64 operations that the
-           interpreted program executes (counted in the kernel: the static
-           per-instruction costs of every instruction it runs) per second of
-           the kernel's CUDA-event time, against the FP64 pipe rate of the chip
-           at the sampled SM clock (2 FP64 operations per SM per clock, 152 SMs).
+roofline   the child evaluation kernel with the larger share of time (FP64 or
+           FP32): directed-rounding operations it executes (counted in the
+           kernel: the static per-instruction costs of every instruction it
+           runs) per second of its CUDA-event time, against the pipe rate of
+           the chip at the sampled SM clock (FP64: 2 operations per SM per
+           clock; FP32: 128), 152 SMs.  Workloads that replay generations from
+           CUDA graphs time the kernels on one extra solve with a host
+           synchronisation per generation (per-kernel events).
 cpu_baseline / --impl reference
            the CPU oracle (plain C, fesetround) on the host cores, one thread,
            on a bounded sample of the same workload.
@@ -46,10 +63,24 @@ sys.path.insert(0, ROOT)
 import synthetic as S  # noqa: E402
 
 FP64_OPS_PER_SM_CLK = 2.0    # GB300: 1.25 TFLOP/s FP64 (FMA = 2) at 2.07 GHz over 152 SMs
+FP32_OPS_PER_SM_CLK = 128.0  # 128 FP32 lanes per SM (directed add / mul at full rate)
 SMS = 152
-WORKLOAD = dict(family="chain", n=100, block=10, split_m=4, split_d=10, max_children=1 << 20)
-WORKLOAD_NAME = ("chain n=100 (coupled quartic, planted min 0), FP64, B=10, 4-way split of the 10 block "
-                 "coordinates (4^10 children) of 1 best box per generation, tol_f=1e-6")
+WORKLOADS = {
+    "chain100": dict(family="chain", n=100, block=10, split_m=4, split_d=10, max_children=1 << 20, fp32=0,
+                     gens_per_sync=0, pool_gb=16.0, cpu_parents=4, cpu_split_d=10, cpu_gens=20,
+                     name="chain n=100 (coupled quartic, planted min 0), FP64, B=10, 4-way split of the 10 "
+                          "block coordinates (4^10 children) of 1 best box per generation, tol_f=1e-6"),
+    "ackley1000": dict(family="ackley", n=1000, block=10, split_m=2, split_d=10, max_children=4 << 10, fp32=1,
+                       gens_per_sync=16, pool_gb=32.0, cpu_parents=4, cpu_split_d=10, cpu_gens=6,
+                       name="ackley n=1000 (exp/sqrt/cos mean form + quadratic, planted min 0), FP32 "
+                            "prefilter + FP64, B=10, 2-way split of 10 coordinates of 4 boxes per generation, "
+                            "tol_f=1e-6"),
+    "mixed10k": dict(family="mixed", n=10000, block=100, split_m=2, split_d=10, max_children=1 << 10, fp32=1,
+                     gens_per_sync=16, pool_gb=64.0, cpu_parents=1, cpu_split_d=10, cpu_gens=2,
+                     name="mixed n=10000 (separable cosine terms on even i, chain terms on odd i, planted min 0), "
+                          "FP32 prefilter + FP64, B=100, 2-way split of 10 coordinates of 1 best box per "
+                          "generation, block-record pool, tol_f=1e-6"),
+}
 
 
 def _args():
@@ -58,20 +89,24 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb", choices=["gb", "reference"])
-    ap.add_argument("--max-children", type=int, default=WORKLOAD["max_children"])
+    ap.add_argument("--workload", default="chain100", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--max-children", type=int, default=0, help="children per generation (0: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-gens", type=int, default=20, help="generations in the oracle sample")
-    ap.add_argument("--pool-gb", type=float, default=16.0, help="device memory for the box pool")
+    ap.add_argument("--cpu-gens", type=int, default=0, help="generations in the oracle sample (0: the workload's)")
+    ap.add_argument("--pool-gb", type=float, default=0.0, help="device memory for the box pool (0: the workload's)")
     ap.add_argument("--max-gens", type=int, default=0, help="stop each solve after this many generations")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="chain100", choices=["chain100", "serving"])
-    ap.add_argument("--requests", type=int, default=128)
-    ap.add_argument("--n-max", type=int, default=200)
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--n-max", type=int, default=2000)
     return ap.parse_args()
 
 
-def _problem(seed=0):
-    return S.chain(n=WORKLOAD["n"], seed=seed)
+def _workload(a):
+    return WORKLOADS[a.workload if a.workload in WORKLOADS else "chain100"]
+
+
+def _problem(w, seed=0):
+    return S.make(w["family"], n=w["n"], seed=seed)
 
 
 class ClockSampler:
@@ -131,22 +166,25 @@ def flush_l2(torch, dev, buf):
     torch.cuda.synchronize(dev)
 
 
-def cpu_baseline(gens):
+def cpu_baseline(w, gens):
     """Oracle, one thread, on the workload's problem: the first `gens`
-    generations with 2^10 children per parent and 4 parents per generation.
-    Every child costs what a child of the timed workload costs (same block,
-    same terms re-evaluated, same first-order test); only the batching
-    differs, which keeps the sample to seconds."""
+    generations with 2^d children per parent (d = the workload's split
+    width) and the workload's FP32 setting.  Every child costs what a child
+    of the timed workload costs (same block, same terms re-evaluated, same
+    first-order test); only the batching differs, which keeps the sample to
+    seconds."""
     import oracle
-    p = _problem(0)
-    o = oracle.Oracle(p, block=WORKLOAD["block"])
+    p = _problem(w, 0)
+    o = oracle.Oracle(p, block=w["block"])
     t = time.perf_counter()
-    r = o.solve(split_m=2, split_d=WORKLOAD["split_d"], max_parents=4, max_gen=gens)
+    r = o.solve(split_m=2, split_d=w["cpu_split_d"], max_parents=w["cpu_parents"], max_gen=gens,
+                fp32=bool(w["fp32"]))
     dt = time.perf_counter() - t
     evals = r.evals64 + r.evals32
     return {"value": evals / dt, "unit": "box-evals/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {r.generations} generations of the n=100 chain solve, 4 parents x 1024 "
-                      f"children per generation ({evals} box evaluations, {dt:.1f} s, 1 thread)"}
+            "sample": f"first {r.generations} generations of the {w['family']} n={w['n']} solve, "
+                      f"{w['cpu_parents']} parents x {2 ** w['cpu_split_d']} children per generation "
+                      f"({evals} box evaluations, {dt:.1f} s, 1 thread)"}
 
 
 def run_reference(a):
@@ -155,24 +193,30 @@ def run_reference(a):
         return
     import oracle
     oracle.build()
+    w = _workload(a)
+    gens = a.cpu_gens or w["cpu_gens"]
     vals = []
     for i in range(a.warmup):
-        cpu_baseline(1)
+        cpu_baseline(w, 1)
     for i in range(a.steps):
-        vals.append(cpu_baseline(max(1, a.cpu_gens // 2)))
+        vals.append(cpu_baseline(w, max(1, gens // 2)))
     v = statistics.median([x["value"] for x in vals])
     line = {"impl": "reference", "metric": "box-evals/s", "value": v, "unit": "box-evals/s",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": None,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if w["fp32"] else "f64",
+            "data": "synthetic", "config": {"workload": w["name"]},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[0]["sample"], "value": v},
             "e2e": {"value": v, "unit": "box-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def _serving_opts(gb, p, fp32):
+    """One best box per generation (2^B children, B = min(n, 10)): the dive
+    keeps each request's pool small and its generations short; the GPU is
+    filled by the concurrent requests."""
     B = min(p.n, 10)
-    return gb.gb_default_options(block=B, split_m=2, split_d=B, max_children=4 << 10,
+    return gb.gb_default_options(block=B, split_m=2, split_d=B, max_children=1 << 10,
                                  fp32_prefilter=int(fp32), pool_bytes=4 << 30, gens_per_sync=4)
 
 
@@ -247,7 +291,8 @@ def run_serving(a):
             "data": "synthetic",
             "config": {"workload": f"serving stream: {len(stream)} requests, n log-uniform [2, {a.n_max}], "
                                    f"families {fams}, tol_f=1e-6, FP32 prefilter + FP64, "
-                                   "150 GB budget, 32 slots, 4 GB per request",
+                                   "150 GB budget, 32 slots, 4 GB per request, one best box "
+                                   "per generation",
                        "value_is": "capacity: all requests submitted at once, solves per second",
                        "sequential_fp64_solves_per_s": len(stream) / sum(service),
                        "speedup_vs_sequential_fp64": (len(stream) / sat_t) / (len(stream) / sum(service)),
@@ -259,9 +304,7 @@ def run_serving(a):
                            "one_at_a_time_fp64_p99_ms": float(np.percentile(fifo_lat, 99)),
                            "one_at_a_time_fp64_solves_per_s": len(stream) / (arrivals[-1] + 0.0 +
                                                                              max(0.0, finish - arrivals[-1]))},
-                       "all_enclosures_valid": bool(ok and seq_ok),
-                       "note": "n range reduced from the named [2, 2000]: dense box rows of the "
-                               "n > 200 Ackley requests exceed the per-request pool"}}
+                       "all_enclosures_valid": bool(ok and seq_ok)}}
     print(json.dumps(line), flush=True)
 
 
@@ -287,9 +330,12 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     gb.load()
-    p = _problem(seed=rank)
-    opts = dict(block=WORKLOAD["block"], split_m=WORKLOAD["split_m"], split_d=WORKLOAD["split_d"],
-                max_children=a.max_children, device=local, pool_bytes=int(a.pool_gb * (1 << 30)))
+    w = _workload(a)
+    p = _problem(w, seed=rank)
+    opts = dict(block=w["block"], split_m=w["split_m"], split_d=w["split_d"],
+                max_children=a.max_children or w["max_children"], fp32_prefilter=w["fp32"],
+                gens_per_sync=w["gens_per_sync"], device=local,
+                pool_bytes=int((a.pool_gb or w["pool_gb"]) * (1 << 30)))
     if a.max_gens > 0:
         opts["max_generations"] = a.max_gens
     solver = gb.Solver(p, **opts)
@@ -320,11 +366,26 @@ def main():
     evals = sum(r.box_evals_fp64 + r.box_evals_fp32 for r in results)
     mids = sum(r.mid_evals for r in results)
     launches = sum(r.kernel_launches for r in results)
-    e64_ms = sum(r.eval64_ms for r in results)
-    e64_n = sum(r.eval64_launches for r in results)
     ok = all(r.status == 0 and r.fmin_lo <= 0.0 <= r.fmin_hi and r.fmin_hi - r.fmin_lo <= p.tol_f
              for r in results)
-    ops64 = sum(r.ops64 for r in results)
+
+    # ---- per-kernel event times of the child evaluation ---------------------
+    # (graph replays carry no per-kernel events: one extra solve with a host
+    # synchronisation per generation times the kernels)
+    prof = results
+    if w["gens_per_sync"] > 1:
+        psolver = gb.Solver(p, **dict(opts, gens_per_sync=1))
+        prof = [psolver.solve(device_only=True)]
+        psolver.close()
+    e64_ms = sum(r.eval64_ms for r in prof)
+    e32_ms = sum(r.eval32_ms for r in prof)
+    use32 = e32_ms > e64_ms
+    k_ms = e32_ms if use32 else e64_ms
+    k_ops = sum((r.ops32 if use32 else r.ops64) for r in prof)
+    k_n = sum((r.eval32_launches if use32 else r.eval64_launches) for r in prof)
+    k_evals = sum((r.box_evals_fp32 if use32 else r.box_evals_fp64 - 1) for r in prof)
+    warp = opts["max_children"] < (1 << 16)
+    kname = ("k_eval32_tab" if use32 else "k_eval64_tab") + ("w" if warp else "")
 
     # ---- end to end through the public API from host buffers -----------------
     e2e_steps = 0 if a.no_e2e else max(1, min(3, a.steps))
@@ -355,20 +416,24 @@ def main():
 
     value = evals / (dev_ms * 1e-3)
     sm_mhz = ck["sm_mhz"] if ck else 2070.0
-    achieved = ops64 / (e64_ms * 1e-3) / 1e12 if e64_ms > 0 else None
-    peak = FP64_OPS_PER_SM_CLK * SMS * sm_mhz * 1e6 / 1e12
+    achieved = k_ops / (k_ms * 1e-3) / 1e12 if k_ms > 0 else None
+    peak = (FP32_OPS_PER_SM_CLK if use32 else FP64_OPS_PER_SM_CLK) * SMS * sm_mhz * 1e6 / 1e12
     try:
-        probe_ops, _ = gb.gb_measure_peak(local, 0)
+        probe_ops, _ = gb.gb_measure_peak(local, 1 if use32 else 0)
     except Exception:
         probe_ops = None
     line = {
         "metric": "box-evals/s", "value": value, "unit": "box-evals/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dev_ms / a.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "l2": "flushed between steps (512 MB write)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if w["fp32"] else "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "l2": "flushed between steps (512 MB write)",
                    "solves_per_s": a.steps / (dev_ms * 1e-3), "generations_per_solve":
                    results[-1].generations, "mid_evals_per_s": mids / (dev_ms * 1e-3),
+                   "fp32_evals_per_solve": results[-1].box_evals_fp32,
+                   "fp64_evals_per_solve": results[-1].box_evals_fp64,
+                   "pool": "block records" if results[-1].pool_mode == 2 else "dense rows",
+                   "peak_pool_boxes": int(results[-1].trace["pool"].max()) if len(results[-1].trace["pool"]) else 1,
                    "all_enclosures_valid": ok, "enclosure": [results[-1].fmin_lo, results[-1].fmin_hi],
                    "host_ms_per_step": 1e3 * host_t / a.steps, "parallelism": "replicas" if world > 1 else "1 GPU"},
         "e2e": ({"value": e2e_evals / e2e_t, "unit": "box-evals/s", "h2d_bytes_per_step": int(h2d),
@@ -376,20 +441,23 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "kernel": "k_eval64_tab", "ops": "FP64 directed-rounding operations executed by the "
-                                                      "child kernel (counted in the kernel; the per-parent "
-                                                      "term tables of k_ptab are not included)",
-                     "ops_per_eval": ops64 / max(1, sum(r.box_evals_fp64 - 1 for r in results)),
+                     "kernel": kname, "ops": ("FP32" if use32 else "FP64") + " directed-rounding operations "
+                                             "executed by the child kernel (counted in the kernel; the "
+                                             "per-parent term tables of k_ptab are not included)",
+                     "ops_per_eval": k_ops / max(1, k_evals),
                      "static_ops_per_eval": info["ops_eval"] + info["ops_mid"],
-                     "peak_source": f"2 FP64 ops/SM/clk x 152 SMs x {sm_mhz:.0f} MHz (sampled median)",
-                     "avg_launch_ms": e64_ms / max(1, e64_n),
+                     "peak_source": f"{FP32_OPS_PER_SM_CLK if use32 else FP64_OPS_PER_SM_CLK:.0f} "
+                                    f"{'FP32' if use32 else 'FP64'} ops/SM/clk x 152 SMs x {sm_mhz:.0f} MHz "
+                                    "(sampled median)",
+                     "timed_on": "the timed solves" if prof is results else "one extra solve, per-generation sync",
+                     "avg_launch_ms": k_ms / max(1, k_n),
                      "probe_measured_tops": probe_ops / 1e12 if probe_ops else None},
         "clocks": ck,
     }
     if not a.no_cpu_baseline:
         import oracle
         oracle.build()
-        line["cpu_baseline"] = cpu_baseline(a.cpu_gens)
+        line["cpu_baseline"] = cpu_baseline(w, a.cpu_gens or w["cpu_gens"])
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

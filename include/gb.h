@@ -99,7 +99,7 @@ typedef struct gb_options {
     int32_t gens_per_sync;    /* <= 1: the host reads the state after every generation (per-kernel timing);
                                  G > 1: generations run as replays of a captured CUDA graph, G between
                                  state reads (the search is the same) */
-    int32_t pool_mode;        /* box storage (section 3.3): 0 auto (block records when n >= 1000 and a
+    int32_t pool_mode;        /* box storage (section 3.3): 0 auto (block records when n >= 128 and a
                                  child replaces at most a quarter of the blocks), 1 one dense row of n
                                  coordinates per box, 2 block records shared between a box and its
                                  children; results are identical */

@@ -310,11 +310,11 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     pl.n = n;
     pl.NG = NG;
     pl.fp32 = fp32;
-    // box storage: dense rows, or block records when a child replaces few of
-    // the blocks (a record holds B coordinates and the cached sums of the
+    // box storage: dense rows, or block records when n >= 128 and a child
+    // replaces few of the blocks (a record holds B coordinates and the cached sums of the
     // groups its block owns; records per box budgeted at 4 * nrec)
     const int nrec = std::min(H.nb, H.span + 1);
-    const bool recs = opt.pool_mode == 2 || (opt.pool_mode == 0 && n >= 1000 && 4 * nrec <= H.nb);
+    const bool recs = opt.pool_mode == 2 || (opt.pool_mode == 0 && n >= 128 && 4 * nrec <= H.nb);
     long long cap = 0;
     if (recs) {
         const size_t per_slot = (size_t)H.nb * 4 + 4 + 4 + 2 * 16;
