@@ -12,7 +12,7 @@ chain100 (default)
   generation (best-first).
 ackley1000
   shifted Ackley-type family, n = 1000, box [-32.768, 32.768]^1000, width
-  1e-6, FP32 prefilter + FP64, blocks of 10, 2^10 children of 4 boxes per
+  1e-6, FP32 prefilter + FP64, blocks of 10, 2^10 children of one box per
   generation, 16 generations per host synchronisation (CUDA graphs).
 mixed10k
   n = 10,000: separable cosine terms on even i, chain terms on odd i, box
@@ -70,10 +70,10 @@ WORKLOADS = {
                      gens_per_sync=0, pool_gb=16.0, cpu_parents=4, cpu_split_d=10, cpu_gens=20,
                      name="chain n=100 (coupled quartic, planted min 0), FP64, B=10, 4-way split of the 10 "
                           "block coordinates (4^10 children) of 1 best box per generation, tol_f=1e-6"),
-    "ackley1000": dict(family="ackley", n=1000, block=10, split_m=2, split_d=10, max_children=4 << 10, fp32=1,
-                       gens_per_sync=16, pool_gb=32.0, cpu_parents=4, cpu_split_d=10, cpu_gens=6,
+    "ackley1000": dict(family="ackley", n=1000, block=10, split_m=2, split_d=10, max_children=1 << 10, fp32=1,
+                       gens_per_sync=16, pool_gb=32.0, cpu_parents=1, cpu_split_d=10, cpu_gens=12,
                        name="ackley n=1000 (exp/sqrt/cos mean form + quadratic, planted min 0), FP32 "
-                            "prefilter + FP64, B=10, 2-way split of 10 coordinates of 4 boxes per generation, "
+                            "prefilter + FP64, B=10, 2-way split of 10 coordinates of 1 best box per generation, "
                             "tol_f=1e-6"),
     "mixed10k": dict(family="mixed", n=10000, block=100, split_m=2, split_d=10, max_children=1 << 10, fp32=1,
                      gens_per_sync=16, pool_gb=64.0, cpu_parents=1, cpu_split_d=10, cpu_gens=2,

@@ -202,7 +202,8 @@ struct GbState {
     long long rec_nfree, rec_bump;     // block records: free list size, next never-used record
     long long rec_gc;                  // block records: collections run
     int gc;                            // block records: collect before this generation's inserts
-    int pad_;
+    unsigned stats_done;               // blocks of k_stats finished (the last one starts the generation)
+    unsigned long long min_key;        // smallest active key (K = 1 selection)
     long long evals32, evals64, mids;  // running counters
     unsigned long long ops64, ops32;   // directed-rounding operations executed by the eval kernels
 };

@@ -127,6 +127,7 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
     s0.gub_key = gb_order_key(gub);
     s0.gub_new_key = s0.gub_key;
     s0.sel_T = ~0ull;
+    s0.min_key = ~0ull;
     s0.evals64 = 1;
     s0.mids = 1;
     s0.rec_bump = pool.recs ? pool.nb : 0;
@@ -142,37 +143,66 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
 
 __device__ __forceinline__ double gub_of(const GbState* st) { return gb_key_value(st->gub_key); }
 
-__global__ void k_stats(GbEntries E, GbGenConst G, GbState* st) {
+// Pool statistics at the end of a generation (and after the root): the
+// number of active entries and, for K = 1, the smallest active key.  The last
+// block to finish then starts the next generation: it stops the solve if
+// nothing is active or a limit was reached, otherwise it chooses the
+// selection (all active boxes if at most K; the minimum key when K = 1; else
+// a radix select of the K-th smallest key).
+__global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbState* st) {
     if (st->halt) return;
+    __shared__ unsigned long long s_c[8], s_k[8];
+    __shared__ bool s_last;
     const long long count = st->pool;
     const double thr = thr_of(gub_of(st), G.tol_f);
     long long c = 0;
+    unsigned long long kmin = ~0ull;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
          q += (long long)gridDim.x * blockDim.x) {
-        double f = E.flo[q];
-        c += (f < thr && !((unsigned)E.cyc[q] & GB_FINAL_BIT)) ? 1 : 0;
+        const double f = E.flo[q];
+        if (f < thr && !((unsigned)E.cyc[q] & GB_FINAL_BIT)) {
+            c++;
+            const unsigned long long k = gb_order_key(f);
+            kmin = k < kmin ? k : kmin;
+        }
     }
-    for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd((unsigned long long*)&st->active, (unsigned long long)c);
-}
-
-// Start of a generation: stop if nothing is active or a limit was reached;
-// otherwise choose the selection (all active boxes if at most K, the minimum
-// key when K = 1, else a radix select of the K-th smallest key).
-__global__ void k_gen_begin(GbGenConst G, GbState* st) {
-    if (st->halt) return;
-    if (st->active == 0 || st->gen >= G.max_gen || st->overflow || st->error) {
+    for (int o = 16; o; o >>= 1) {
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        const unsigned long long other = __shfl_down_sync(0xffffffffu, kmin, o);
+        kmin = other < kmin ? other : kmin;
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) s_c[w] = (unsigned long long)c, s_k[w] = kmin;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tc = 0, tk = ~0ull;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) tc += s_c[i], tk = s_k[i] < tk ? s_k[i] : tk;
+        if (tc) atomicAdd((unsigned long long*)&st->active, tc);
+        if (tk != ~0ull) atomicMin(&st->min_key, tk);
+        __threadfence();
+        s_last = atomicAdd(&st->stats_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    // last block: start of the next generation
+    __threadfence();
+    st->stats_done = 0;
+    const long long active = (long long)atomicAdd((unsigned long long*)&st->active, 0ull);
+    const unsigned long long mk = atomicMin(&st->min_key, ~0ull);
+    if (active == 0 || st->gen >= G.max_gen || st->overflow || st->error) {
         st->halt = 1;
         return;
     }
-    if (st->active <= G.K) {
+    if (active <= G.K) {
         st->sel_mode = 0;
         st->sel_T = ~0ull;
-        st->sel_below = st->active;
+        st->sel_below = active;
         st->sel_need = 0;
     } else if (G.K == 1) {
+        // the smallest active key (the partition then takes the most recently
+        // inserted box among those with that key)
         st->sel_mode = 1;
-        st->sel_T = ~0ull - 1;   // replaced by the minimum active key
+        st->sel_T = mk;
         st->sel_below = 0;
         st->sel_need = 1;
     } else {
@@ -181,27 +211,6 @@ __global__ void k_gen_begin(GbGenConst G, GbState* st) {
         st->radix_rank = G.K;
         st->sel_below = 0;
     }
-}
-
-// K = 1: the threshold is the smallest active key (the partition then takes
-// the most recently inserted box among those with that key).
-__global__ void k_min_key(GbEntries E, GbGenConst G, GbState* st) {
-    if (st->halt || st->sel_mode != 1) return;
-    const long long count = st->pool;
-    const double thr = thr_of(gub_of(st), G.tol_f);
-    unsigned long long kmin = ~0ull;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
-         q += (long long)gridDim.x * blockDim.x) {
-        double f = E.flo[q];
-        if (!(f < thr) || ((unsigned)E.cyc[q] & GB_FINAL_BIT)) continue;
-        unsigned long long k = gb_order_key(f);
-        kmin = k < kmin ? k : kmin;
-    }
-    for (int o = 16; o; o >>= 1) {
-        unsigned long long other = __shfl_down_sync(0xffffffffu, kmin, o);
-        kmin = other < kmin ? other : kmin;
-    }
-    if ((threadIdx.x & 31) == 0 && kmin != ~0ull) atomicMin(&st->sel_T, kmin);
 }
 
 // Radix select (16-bit digits, 4 passes) of the K-th smallest active key.
@@ -927,11 +936,10 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
 
 // Parents' slots back to the free list, or (on overflow) the parents back
 // into the pool after the carried-over entries.
-__global__ void k_free_parents(GbParents par, GbPool pool, GbEntries En, GbState* st) {
-    if (st->halt) return;
+__device__ __forceinline__ void free_parents(const GbParents& par, const GbPool& pool, const GbEntries& En,
+                                             const GbState* st, long long p0, long long step) {
     const long long npar = st->parents;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npar;
-         p += (long long)gridDim.x * blockDim.x) {
+    for (long long p = p0; p < npar; p += step) {
         if (st->overflow) {
             long long e = st->kept_old + p;
             En.flo[e] = par.flo[p];
@@ -945,8 +953,21 @@ __global__ void k_free_parents(GbParents par, GbPool pool, GbEntries En, GbState
     }
 }
 
-__global__ void k_finish(GbGenConst G, GbState* st) {
+__global__ void k_free_parents(GbParents par, GbPool pool, GbEntries En, GbState* st) {
     if (st->halt) return;
+    free_parents(par, pool, En, st, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                 (long long)gridDim.x * blockDim.x);
+}
+
+// End of a generation: pool size, free list, record counters, GUB, trace row.
+// With fused = 1 (one block) the block first frees the parents itself.
+__global__ void k_finish(GbGenConst G, GbParents par, GbPool pool, GbEntries En, int fused, GbState* st) {
+    if (st->halt) return;
+    if (fused) {
+        free_parents(par, pool, En, st, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
     const long long npar = st->parents;
     long long kept = st->kept, nfree = st->nfree;
     if (st->overflow) {
@@ -977,6 +998,7 @@ __global__ void k_finish(GbGenConst G, GbState* st) {
     }
     st->gen += 1;
     st->active = 0;
+    st->min_key = ~0ull;
     st->gc = 0;
 }
 
@@ -1137,12 +1159,8 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     const unsigned gtile_pool = (unsigned)std::min<long long>(grid_for(cap, GB_TILE), 152 * 8);
     const unsigned gtile_ch = (unsigned)std::min<long long>(grid_for(Cmax, GB_TILE), 152 * 8);
     const unsigned gch = (unsigned)std::min<long long>(grid_for(Cmax, 128), 152 * 32);
-    gb_launch_count++;
-    k_gen_begin<<<1, 1, 0, s>>>(G, st);
-    if (G.K == 1) {
-        gb_launch_count++;
-        k_min_key<<<gpool, 256, 0, s>>>(E, G, st);
-    } else {
+    // (the selection mode and the K = 1 threshold were set by the last k_stats)
+    if (G.K > 1) {
         for (int pass = 0; pass < 4; pass++) {
             gb_launch_count += 2;
             k_radix_hist<<<gpool, 256, 0, s>>>(E, G, pass, st, sc.hist);
@@ -1203,9 +1221,14 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     gb_launch_count++;
     k_materialize<<<(unsigned)std::min<long long>(grid_for(Cmax * 32, 128), 152 * 16), 128, 0, s>>>(
         P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, tabs ? 1 : 0);
-    gb_launch_count += 2;
-    k_free_parents<<<grid_for(G.K, 256), 256, 0, s>>>(par, pool, E_new, st);
-    k_finish<<<1, 1, 0, s>>>(G, st);
+    if (G.K <= 4096) {   // few parents: freed by the finishing block itself
+        gb_launch_count++;
+        k_finish<<<1, 256, 0, s>>>(G, par, pool, E_new, 1, st);
+    } else {
+        gb_launch_count += 2;
+        k_free_parents<<<grid_for(G.K, 256), 256, 0, s>>>(par, pool, E_new, st);
+        k_finish<<<1, 1, 0, s>>>(G, par, pool, E_new, 0, st);
+    }
     if ((e = gb_launch_stats(E_new, G, cap, st, s)) != cudaSuccess) return e;
     if (nlaunch) *nlaunch = gb_launch_count - n0;
     return cudaGetLastError();

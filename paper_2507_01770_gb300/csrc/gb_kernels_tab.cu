@@ -47,9 +47,18 @@ template <> struct TabPrec<float> {
 __device__ __forceinline__ iv64 mid_node(const GbTabs& T, size_t i) { double2 v = T.nm64[i]; return iv64{v.x, v.y}; }
 
 // ---------------------------------------------------------------------------
-// k_ptab: one block per parent.  Rows: (dirty term, digit combination).
-__global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp,
-                                             const GbState* st) {
+// k_ptab: per parent (blockIdx.y).  Blocks x < row_blocks: one table row part
+// per thread -- rows are (dirty term, digit combination) and each row has up
+// to four independent parts: 0 the FP64 value, 1 the midpoint value, 2 the
+// FP64 leaf adjoints, 3 the FP32 value and leaf adjoints.  Blocks x >=
+// row_blocks: one group tree of the parent's cached sums each (sum k, kind:
+// F, midpoint, FP32), level by level.
+constexpr int PTAB_T = 64;
+
+__device__ __forceinline__ int ptab_parts(const GbPool& pool) { return pool.fp32 ? 4 : 3; }
+
+__global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp,
+                                                 int row_blocks, const GbState* st) {
     if (st->halt) return;
     const long long p = blockIdx.y;
     if (p >= st->parents) return;
@@ -57,80 +66,16 @@ __global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents pa
     const unsigned slot = par.slot[p];
     const int spi = P.sp_of_cyc[info.x];
     if (spi < 0) return;
-    const GbSplitPos SP = P.sps[spi];
-    const size_t o = (size_t)p * sp.dmax * (sp.m + 1);
-    const double* b64 = par.bnd + o;
-    iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS];
-    iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS];
-    int ops = 0;
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < SP.tab_entries; row += gridDim.x * blockDim.x) {
-        // the dirty term owning this row (rows are contiguous per term)
-        int lo = 0, hi = SP.ndterm - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (P.dterms[SP.dterm0 + mid].row <= row) lo = mid; else hi = mid - 1;
-        }
-        const GbDTerm D = P.dterms[SP.dterm0 + lo];
-        const unsigned combo = (unsigned)(row - D.row);
-        const unsigned r = combo << D.dshift;   // a child index with these digits
-        const GbSum S = P.sums[D.sum];
-        const int i = S.first + D.term * S.step;
-        View<double> X = box_view64(pool, slot);
-        X.blo = b64;
-        X.bhi = b64;
-        X.c0 = info.x;
-        X.dd = info.y;
-        X.mshift = sp.mshift;
-        X.mstride = sp.m + 1;
-        X.r = r;
-        MidView MX{X};
-        const size_t orow = (size_t)p * T.max_rows + row;
-        iv64 v = term_fwd<double>(P, S, i, X, R, ops);
-        T.tv64[orow] = make_double2(v.lo, v.hi);
-        iv64 vm = term_fwd<double>(P, S, i, MX, R, ops);
-        T.tm64[orow] = make_double2(vm.lo, vm.hi);
-        term_fwd<double>(P, S, i, X, R, ops);
-        for (int t = 0; t < S.nins; t++) RA[t] = iv64{0.0, 0.0};
-        RA[S.nins - 1] = iv64{1.0, 1.0};
-        reverse_sweep<double>(P.tins + S.ins0, S.nins, R, RA, ops);
-        int leaf = 0;
-        for (int t = 0; t < S.nins; t++) {
-            if (P.tins[S.ins0 + t].op != D_IVAR) continue;
-            T.tl64[orow * T.max_leaves + leaf] = make_double2(RA[t].lo, RA[t].hi);
-            leaf++;
-        }
-        if (pool.fp32) {
-            View<float> X32 = box_view32(pool, slot);
-            X32.blo = par.bnd_rd + o;
-            X32.bhi = par.bnd_ru + o;
-            X32.c0 = info.x;
-            X32.dd = info.y;
-            X32.mshift = sp.mshift;
-            X32.mstride = sp.m + 1;
-            X32.r = r;
-            iv32 f = term_fwd<float>(P, S, i, X32, R32, ops);
-            T.tv32[orow] = make_float2(f.lo, f.hi);
-            for (int t = 0; t < S.nins; t++) RA32[t] = iv32{0.f, 0.f};
-            RA32[S.nins - 1] = iv32{1.f, 1.f};
-            reverse_sweep<float>(P.tins + S.ins0, S.nins, R32, RA32, ops);
-            leaf = 0;
-            for (int t = 0; t < S.nins; t++) {
-                if (P.tins[S.ins0 + t].op != D_IVAR) continue;
-                T.tl32[orow * T.max_leaves + leaf] = make_float2(RA32[t].lo, RA32[t].hi);
-                leaf++;
-            }
-        }
-    }
-    // group trees of the parent's cached sums (level-major, pairwise): one
-    // block, the nodes of a level in parallel, a barrier between levels
-    const int kinds = pool.fp32 ? 3 : 2;
-    if (blockIdx.x != 0) return;
-    const CacheRef<double2> cf = cache64(pool, P, slot, 0), cm = cache64(pool, P, slot, 1);
-    const CacheRef<float2> c32 = cache32(pool, P, slot);
-    for (int job = 0; job < P.n_sum * kinds; job++) {
+    if ((int)blockIdx.x >= row_blocks) {
+        // group tree job (k, kind)
+        const int kinds = pool.fp32 ? 3 : 2;
+        const int job = blockIdx.x - row_blocks;
+        if (job >= P.n_sum * kinds) return;
         const int k = job % P.n_sum, kind = job / P.n_sum;
         const GbSum S = P.sums[k];
         const size_t nb = (size_t)p * T.tree_nodes + S.node0;
+        const CacheRef<double2> cf = cache64(pool, P, slot, 0), cm = cache64(pool, P, slot, 1);
+        const CacheRef<float2> c32 = cache32(pool, P, slot);
         for (int g = threadIdx.x; g < S.ngroups; g += blockDim.x) {
             if (kind == 0) T.nf64[nb + g] = cf[S.group0 + g];
             else if (kind == 1) T.nm64[nb + g] = cm[S.group0 + g];
@@ -163,6 +108,77 @@ __global__ void __launch_bounds__(64) k_ptab(GbProg P, GbPool pool, GbParents pa
             }
             __syncthreads();
             off += mL;
+        }
+        return;
+    }
+    const GbSplitPos SP = P.sps[spi];
+    const size_t o = (size_t)p * sp.dmax * (sp.m + 1);
+    const int parts = ptab_parts(pool);
+    int ops = 0;
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < SP.tab_entries * parts;
+         item += row_blocks * blockDim.x) {
+        const int row = item / parts, part = item - row * parts;
+        // the dirty term owning this row (rows are contiguous per term)
+        int lo = 0, hi = SP.ndterm - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (P.dterms[SP.dterm0 + mid].row <= row) lo = mid; else hi = mid - 1;
+        }
+        const GbDTerm D = P.dterms[SP.dterm0 + lo];
+        const unsigned r = (unsigned)(row - D.row) << D.dshift;   // a child index with these digits
+        const GbSum S = P.sums[D.sum];
+        const int i = S.first + D.term * S.step;
+        const size_t orow = (size_t)p * T.max_rows + row;
+        if (part < 3) {
+            iv64 R[GB_MAX_TREGS];
+            View<double> X = box_view64(pool, slot);
+            X.blo = par.bnd + o;
+            X.bhi = par.bnd + o;
+            X.c0 = info.x;
+            X.dd = info.y;
+            X.mshift = sp.mshift;
+            X.mstride = sp.m + 1;
+            X.r = r;
+            if (part == 0) {
+                const iv64 v = term_fwd<double>(P, S, i, X, R, ops);
+                T.tv64[orow] = make_double2(v.lo, v.hi);
+            } else if (part == 1) {
+                const iv64 v = term_fwd<double>(P, S, i, MidView{X}, R, ops);
+                T.tm64[orow] = make_double2(v.lo, v.hi);
+            } else {
+                iv64 RA[GB_MAX_TREGS];
+                term_fwd<double>(P, S, i, X, R, ops);
+                for (int t = 0; t < S.nins; t++) RA[t] = iv64{0.0, 0.0};
+                RA[S.nins - 1] = iv64{1.0, 1.0};
+                reverse_sweep<double>(P.tins + S.ins0, S.nins, R, RA, ops);
+                int leaf = 0;
+                for (int t = 0; t < S.nins; t++) {
+                    if (P.tins[S.ins0 + t].op != D_IVAR) continue;
+                    T.tl64[orow * T.max_leaves + leaf] = make_double2(RA[t].lo, RA[t].hi);
+                    leaf++;
+                }
+            }
+        } else {
+            iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS];
+            View<float> X32 = box_view32(pool, slot);
+            X32.blo = par.bnd_rd + o;
+            X32.bhi = par.bnd_ru + o;
+            X32.c0 = info.x;
+            X32.dd = info.y;
+            X32.mshift = sp.mshift;
+            X32.mstride = sp.m + 1;
+            X32.r = r;
+            const iv32 f = term_fwd<float>(P, S, i, X32, R32, ops);
+            T.tv32[orow] = make_float2(f.lo, f.hi);
+            for (int t = 0; t < S.nins; t++) RA32[t] = iv32{0.f, 0.f};
+            RA32[S.nins - 1] = iv32{1.f, 1.f};
+            reverse_sweep<float>(P.tins + S.ins0, S.nins, R32, RA32, ops);
+            int leaf = 0;
+            for (int t = 0; t < S.nins; t++) {
+                if (P.tins[S.ins0 + t].op != D_IVAR) continue;
+                T.tl32[orow * T.max_leaves + leaf] = make_float2(RA32[t].lo, RA32[t].hi);
+                leaf++;
+            }
         }
     }
 }
@@ -687,9 +703,13 @@ unsigned grid_for(long long items, int per_block) {
 
 cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                            long long K, const GbSplit& sp, GbState* st, cudaStream_t s) {
-    // rows of a parent spread over blocks of 64 threads
-    const unsigned chunks = (unsigned)((P.max_rows + 63) / 64);
-    k_ptab<<<dim3(chunks < 1 ? 1 : chunks, (unsigned)K), 64, 0, s>>>(P, pool, par, T, sp, st);
+    // row parts of a parent spread over blocks of PTAB_T threads, then one
+    // block per group tree
+    const int parts = pool.fp32 ? 4 : 3, kinds = pool.fp32 ? 3 : 2;
+    int row_blocks = (P.max_rows * parts + PTAB_T - 1) / PTAB_T;
+    if (row_blocks < 1) row_blocks = 1;
+    k_ptab<<<dim3((unsigned)(row_blocks + P.n_sum * kinds), (unsigned)K), PTAB_T, 0, s>>>(P, pool, par, T, sp,
+                                                                                          row_blocks, st);
     return cudaGetLastError();
 }
 
