@@ -385,7 +385,10 @@ def main():
     k_n = sum((r.eval32_launches if use32 else r.eval64_launches) for r in prof)
     k_evals = sum((r.box_evals_fp32 if use32 else r.box_evals_fp64 - 1) for r in prof)
     warp = opts["max_children"] < (1 << 16)
-    kname = ("k_eval32_tab" if use32 else "k_eval64_tab") + ("w" if warp else "")
+    if w["fp32"] and warp:   # FP32 prefilter and FP64 evaluation in one warp-per-child kernel
+        kname = "k_eval3264_tabw (FP64 operations over the fused kernel's time)"
+    else:
+        kname = ("k_eval32_tab" if use32 else "k_eval64_tab") + ("w" if warp else "")
 
     # ---- end to end through the public API from host buffers -----------------
     e2e_steps = 0 if a.no_e2e else max(1, min(3, a.steps))

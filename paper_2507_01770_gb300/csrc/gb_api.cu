@@ -115,6 +115,7 @@ struct gb_problem {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // one generation, pool buffers 0->1 and 1->0
     long long graph_kernels = 0;
     size_t device_bytes = 0;       // device memory held by the problem
+    bool marks_used = false;       // a solve stamped record marks (cleared before the next one)
 };
 
 extern "C" {
@@ -318,7 +319,7 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     long long cap = 0;
     if (recs) {
         const size_t per_slot = (size_t)H.nb * 4 + 4 + 4 + 2 * 16;
-        const size_t per_rec = (size_t)opt.block * (16 + (fp32 ? 8 : 0)) + (size_t)H.GPB * (32 + (fp32 ? 8 : 0)) + 4 + 2;
+        const size_t per_rec = (size_t)opt.block * (16 + (fp32 ? 8 : 0)) + (size_t)H.GPB * (32 + (fp32 ? 8 : 0)) + 4 + 1 + 4;
         const long long rho = 4LL * nrec;
         cap = opt.max_boxes > 0 ? opt.max_boxes : (long long)(opt.pool_bytes / (per_slot + rho * per_rec));
         if (cap < 1) return bad(cudaErrorMemoryAllocation, "pool budget below one box");
@@ -336,11 +337,13 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         if ((e = alloc(&pl.rid, (size_t)cap * H.nb, A)) || (e = alloc(&pl.swide, (size_t)cap, A)) ||
             (e = alloc(&pl.freel, (size_t)cap, A)) || (e = alloc(&pl.rlo, RB, A)) || (e = alloc(&pl.rhi, RB, A)) ||
             (e = alloc(&pl.rgsum, RG, A)) || (e = alloc(&pl.rgmid, RG, A)) || (e = alloc(&pl.rfree, (size_t)R, A)) ||
-            (e = alloc(&pl.rwide, (size_t)R, A)) || (e = alloc(&pl.rmark, (size_t)(R / 32 + 1), A)))
+            (e = alloc(&pl.rwide, (size_t)R, A)) || (e = alloc(&pl.rmark, (size_t)R, A)))
             return bad(e, "allocate block records");
         if (fp32 && ((e = alloc(&pl.rlo32, RB, A)) || (e = alloc(&pl.rhi32, RB, A)) ||
                      (e = alloc(&pl.rgsum32, RG, A))))
             return bad(e, "allocate block records");
+        if ((e = cudaMemsetAsync(pl.rmark, 0, sizeof(unsigned) * (size_t)R, p->stream)))
+            return bad(e, "cudaMemset");
     } else {
         size_t per_slot = (size_t)n * 16 + (fp32 ? (size_t)n * 8 : 0) + (size_t)NG * 32 + (fp32 ? (size_t)NG * 8 : 0) +
                           4 + 2 * 16;
@@ -481,6 +484,10 @@ __attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
     init.cap = p->cap;
     GB_CU(cudaEventRecord(p->ev[0], s));
     GB_CU(cudaMemcpyAsync(p->st, &init, sizeof(GbState), cudaMemcpyHostToDevice, s));
+    if (p->pool.recs && p->marks_used) {   // collection numbers restart at 1 in every solve
+        GB_CU(cudaMemsetAsync(p->pool.rmark, 0, sizeof(unsigned) * (size_t)p->pool.R, s));
+        p->marks_used = false;
+    }
     GB_CU(gb_launch_root_init(p->P, p->pool, p->E[0], p->G.tol_x, p->st, s));
     GB_CU(gb_launch_stats(p->E[0], p->G, 1, p->st, s));
     GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
@@ -629,6 +636,7 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
     out->ops32 = (int64_t)hf.ops32;
     out->pool_mode = p->pool.recs ? 2 : 1;
     out->record_gcs = (int64_t)hf.rec_gc;
+    if (hf.rec_gc > 0) p->marks_used = true;
     const long long nt = hf.gen < p->G.trace_cap ? hf.gen : p->G.trace_cap;
     out->n_trace = nt;
     if (nt > 0) {

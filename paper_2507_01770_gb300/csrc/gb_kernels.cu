@@ -332,6 +332,15 @@ __global__ void k_part_count(GbEntries E, GbGenConst G, const GbState* st, int* 
     }
 }
 
+// Survivor count S of the generation: overflow if the slots cannot take
+// them; with block records, a collection first if their new records do not fit.
+__device__ __forceinline__ void set_survivors(const GbGenConst& G, GbState* st, long long S) {
+    st->kept = S;
+    const long long room = st->nfree + (st->cap - st->bump);
+    st->overflow = S > room ? 1 : 0;
+    st->gc = (!st->overflow && G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
+}
+
 // Exclusive scan of up to 3 arrays of tile counts (one block of 1024
 // threads, each owning a contiguous run of tiles).
 // what: 0 = partition (3 arrays, items = pool), 1 = FP32 list and 2 =
@@ -384,15 +393,9 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_c
         st->n32 = tot[0];
         st->kept32 = tot[0];
     } else if (what == 2) {
-        long long S = tot[0];
-        st->kept = S;
-        long long room = st->nfree + (st->cap - st->bump);
-        st->overflow = S > room ? 1 : 0;
-        // block records: collect unreferenced records first if the new ones do not fit
-        st->gc = (!st->overflow && G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
+        set_survivors(G, st, tot[0]);
     } else if (what == 4) {
         st->rec_nfree = tot[0];
-        st->rec_gc += 1;
         if (st->kept * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) st->overflow = 1;
     } else {
         st->kept = tot[0];
@@ -749,21 +752,33 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
     }
 }
 
+// Survivor list of a generation with at most 2^16 children: one block
+// does the count, the scan and the scatter.
+__global__ void __launch_bounds__(1024) k_cc_small(GbChildren ch, GbGenConst G, GbState* st) {
+    if (st->halt) return;
+    __shared__ int sw[1024 / 32 + 1];
+    const long long n = st->nch;
+    const double gub_new = gb_key_value(st->gub_new_key);
+    long long o = 0;
+    for (long long base = 0; base < n; base += 1024) {
+        const long long i = base + threadIdx.x;
+        const bool f = child_pred(ch, i, n, 1, gub_new);
+        int tot;
+        const int rk = block_prefix<1024>(f, sw, &tot);
+        if (f) ch.surv[o + rk] = (unsigned)i;
+        o += tot;
+    }
+    if (threadIdx.x == 0) set_survivors(G, st, o);
+}
+
 // ---------------------------------------------------------------------------
 // Block records: a box's row names one record per block, and a child shares
 // all but the records of the blocks it changes with its parent, so a record
 // is referenced by many boxes and is freed by a mark-and-sweep collection,
-// run only when the new records of a generation do not fit: mark the records
+// run only when the new records of a generation do not fit: stamp the records
 // named by the boxes still alive (entries carried over and this generation's
-// parents), then list the unmarked ones in ascending order as the free list.
-__global__ void k_gc_clear(GbPool pool, const GbState* st) {
-    if (st->halt || !st->gc) return;
-    const long long words = (st->rec_bump + 31) >> 5;
-    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < words;
-         w += (long long)gridDim.x * blockDim.x)
-        pool.rmark[w] = 0u;
-}
-
+// parents) with the collection's number, then list the unstamped ones in
+// ascending order as the free list.
 __global__ void k_gc_mark(GbPool pool, GbEntries En, GbParents par, const GbState* st) {
     if (st->halt || !st->gc) return;
     const long long nbox = st->kept_old + st->parents, nb = pool.nb;
@@ -771,23 +786,23 @@ __global__ void k_gc_mark(GbPool pool, GbEntries En, GbParents par, const GbStat
          i += (long long)gridDim.x * blockDim.x) {
         const long long q = i / nb, b = i - q * nb;
         const unsigned slot = q < st->kept_old ? En.slot[q] : par.slot[q - st->kept_old];
-        const unsigned id = pool.rid[(size_t)slot * nb + b];
-        atomicOr(pool.rmark + (id >> 5), 1u << (id & 31));
+        pool.rmark[pool.rid[(size_t)slot * nb + b]] = (unsigned)(st->rec_gc + 1);
     }
 }
 
-__device__ __forceinline__ bool rec_free(const GbPool& pool, long long id, long long used) {
-    return id < used && !((pool.rmark[id >> 5] >> (id & 31)) & 1u);
+__device__ __forceinline__ bool rec_free(const GbPool& pool, long long id, long long used, unsigned epoch) {
+    return id < used && pool.rmark[id] != epoch;
 }
 
 __global__ void k_gc_count(GbPool pool, const GbState* st, int* tile_cnt) {
     if (st->halt || !st->gc) return;
     __shared__ int sw[PT / 32 + 1];
     const long long used = st->rec_bump, nt = ntiles_of(used);
+    const unsigned epoch = (unsigned)(st->rec_gc + 1);
     for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         int acc = 0, tot;
         for (int r = 0; r < GB_TILE / PT; r++) {
-            block_prefix<PT>(rec_free(pool, tile * GB_TILE + r * PT + threadIdx.x, used), sw, &tot);
+            block_prefix<PT>(rec_free(pool, tile * GB_TILE + r * PT + threadIdx.x, used, epoch), sw, &tot);
             acc += tot;
         }
         if (threadIdx.x == 0) tile_cnt[tile] = acc;
@@ -798,11 +813,12 @@ __global__ void k_gc_scatter(GbPool pool, const GbState* st, const int* tile_off
     if (st->halt || !st->gc) return;
     __shared__ int sw[PT / 32 + 1];
     const long long used = st->rec_bump, nt = ntiles_of(used);
+    const unsigned epoch = (unsigned)(st->rec_gc + 1);
     for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         long long o = tile_off[tile];
         for (int r = 0; r < GB_TILE / PT; r++) {
             const long long id = tile * GB_TILE + r * PT + threadIdx.x;
-            const bool f = rec_free(pool, id, used);
+            const bool f = rec_free(pool, id, used, epoch);
             int tot;
             const int rk = block_prefix<PT>(f, sw, &tot);
             if (f) pool.rfree[o + rk] = (unsigned)id;
@@ -999,6 +1015,7 @@ __global__ void k_finish(GbGenConst G, GbParents par, GbPool pool, GbEntries En,
     st->gen += 1;
     st->active = 0;
     st->min_key = ~0ull;
+    if (st->gc) st->rec_gc += 1;
     st->gc = 0;
 }
 
@@ -1178,39 +1195,52 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
         gb_launch_count++;
         if ((e = gb_launch_ptab(P, pool, par, *tabs, G.K, sp, st, s)) != cudaSuccess) return e;
     }
-    if (G.fp32) {
-        if (ev) cudaEventRecord(ev[2], s);
+    const bool fused = G.fp32 && tabs && tabs->warp;
+    if (fused) {
+        // FP32 prefilter and FP64 evaluation in one warp-per-child kernel
+        if (ev) cudaEventRecord(ev[2], s), cudaEventRecord(ev[3], s), cudaEventRecord(ev[0], s);
+        gb_launch_count++;
+        if ((e = gb_launch_eval3264_tabw(P, pool, par, *tabs, ch, Cmax, sp, st, s)) != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[1], s);
+    } else {
+        if (G.fp32) {
+            if (ev) cudaEventRecord(ev[2], s);
+            if (tabs) {
+                gb_launch_count++;
+                if ((e = gb_launch_eval32_tab(P, pool, par, *tabs, ch, Cmax, sp, st, s)) != cudaSuccess) return e;
+            } else {
+                gb_launch_count++;
+                k_eval32<<<gch, 128, 0, s>>>(P, pool, par, ch, sp, st);
+            }
+            if (ev) cudaEventRecord(ev[3], s);
+            gb_launch_count += 3;
+            k_cc_count<<<gtile_ch, PT, 0, s>>>(ch, 0, st, sc.tile_cnt);
+            k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 1, 0, G, st);
+            k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 0, st, sc.tile_off, ch.list32);
+        }
+        if (ev) cudaEventRecord(ev[0], s);
         if (tabs) {
             gb_launch_count++;
-            if ((e = gb_launch_eval32_tab(P, pool, par, *tabs, ch, Cmax, sp, st, s)) != cudaSuccess) return e;
+            if ((e = gb_launch_eval64_tab(P, pool, par, *tabs, ch, Cmax, sp, G.fp32 != 0, st, s)) != cudaSuccess)
+                return e;
         } else {
             gb_launch_count++;
-            k_eval32<<<gch, 128, 0, s>>>(P, pool, par, ch, sp, st);
+            k_eval64<<<gch, 128, 0, s>>>(P, pool, par, ch, sp, G.fp32, st);
         }
-        if (ev) cudaEventRecord(ev[3], s);
-        gb_launch_count += 3;
-        k_cc_count<<<gtile_ch, PT, 0, s>>>(ch, 0, st, sc.tile_cnt);
-        k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 1, 0, G, st);
-        k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 0, st, sc.tile_off, ch.list32);
+        if (ev) cudaEventRecord(ev[1], s);
     }
-    if (ev) cudaEventRecord(ev[0], s);
-    if (tabs) {
+    if (Cmax <= (1LL << 16)) {
         gb_launch_count++;
-        if ((e = gb_launch_eval64_tab(P, pool, par, *tabs, ch, Cmax, sp, G.fp32 != 0, st, s)) != cudaSuccess)
-            return e;
+        k_cc_small<<<1, 1024, 0, s>>>(ch, G, st);
     } else {
-        gb_launch_count++;
-        k_eval64<<<gch, 128, 0, s>>>(P, pool, par, ch, sp, G.fp32, st);
+        gb_launch_count += 3;
+        k_cc_count<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_cnt);
+        k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 2, 0, G, st);
+        k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_off, ch.surv);
     }
-    if (ev) cudaEventRecord(ev[1], s);
-    gb_launch_count += 3;
-    k_cc_count<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_cnt);
-    k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 2, 0, G, st);
-    k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_off, ch.surv);
     if (pool.recs) {
         const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), 152 * 8);
-        gb_launch_count += 5;
-        k_gc_clear<<<152 * 4, 256, 0, s>>>(pool, st);
+        gb_launch_count += 4;
         k_gc_mark<<<152 * 8, 256, 0, s>>>(pool, E_new, par, st);
         k_gc_count<<<grec, PT, 0, s>>>(pool, st, sc.tile_cnt);
         k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0, G, st);

@@ -638,6 +638,52 @@ __global__ void __launch_bounds__(128) k_eval64_tabw(GbProg P, GbPool pool, GbPa
     }
 }
 
+// FP32 pass of one child by a warp: writes flag32 (and resets the FP64 flag
+// and LB); returns -1 for an invalid child, else whether the child passed.
+__device__ __forceinline__ int eval32_tab_child_w(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                                  const GbTabs& Tb, const GbChildren& ch, long long ci,
+                                                  const GbSplit& sp, double gub_prev, int& red, int& pops,
+                                                  int lane) {
+    const ChildCtx c = child_ctx(par, ci, sp);
+    const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
+    if (lane == 0) {
+        ch.flag[ci] = 0;
+        ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
+    }
+    if (spi < 0) {
+        if (lane == 0) ch.flag32[ci] = 0;
+        return -1;
+    }
+    const GbSplitPos SP = P.sps[spi];
+    const int blk = c.info.z;
+    const View<float> X = view32(pool, par, c, sp);
+    const View<double> X64 = view64(pool, par, c, sp);
+    const size_t rowbase = (size_t)c.p * Tb.max_rows, nbase = (size_t)c.p * Tb.tree_nodes;
+    iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+    int dt = SP.dterm0;
+    for (int k = 0; k < P.n_sum; k++) {
+        const GbSum S = P.sums[k];
+        const int2 dr = P.dirty[blk * P.n_sum + k];
+        iv32 cur[GB_TAB_MAX_DIRTY];
+        for (int g = dr.x; g < dr.y; g++) {
+            int cnt;
+            warp_group<iv32, 1>(P, SP, k, g, c.r, dt, lane,
+                                [&](const GbDTerm& D, unsigned combo, iv32* v) {
+                                    const float2 a = Tb.tv32[rowbase + D.row + combo];
+                                    v[0] = iv32{a.x, a.y};
+                                }, cur + (g - dr.x), cnt);
+            red += 2 * (cnt > 0 ? cnt - 1 : 0);
+        }
+        const size_t nb = nbase + S.node0;
+        sums[k] = tab_path(S, dr, cur, [&](int i) { return TabPrec<float>::node(Tb, nb + i); }, red);
+    }
+    const iv32 F = outer_fwd<float>(P, X, sums, O, red);
+    bool keep = !((double)F.lo > gub_prev);
+    if (keep) keep = !tab_mono_w<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, red, pops, lane);
+    if (lane == 0) ch.flag32[ci] = keep ? 1 : 0;
+    return keep ? 1 : 0;
+}
+
 __global__ void __launch_bounds__(128) k_eval32_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
                                                      GbChildren ch, GbSplit sp, GbState* st) {
     if (st->halt) return;
@@ -647,50 +693,52 @@ __global__ void __launch_bounds__(128) k_eval32_tabw(GbProg P, GbPool pool, GbPa
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     int red = 0, pops = 0;
     unsigned long long nv = 0;
-    for (long long ci = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; ci < lim; ci += nw) {
-        const ChildCtx c = child_ctx(par, ci, sp);
-        const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
-        if (lane == 0) {
-            ch.flag[ci] = 0;
-            ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
-        }
-        if (spi < 0) {
-            if (lane == 0) ch.flag32[ci] = 0;
-            continue;
-        }
-        nv++;
-        const GbSplitPos SP = P.sps[spi];
-        const int blk = c.info.z;
-        const View<float> X = view32(pool, par, c, sp);
-        const View<double> X64 = view64(pool, par, c, sp);
-        const size_t rowbase = (size_t)c.p * Tb.max_rows, nbase = (size_t)c.p * Tb.tree_nodes;
-        iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
-        int dt = SP.dterm0;
-        for (int k = 0; k < P.n_sum; k++) {
-            const GbSum S = P.sums[k];
-            const int2 dr = P.dirty[blk * P.n_sum + k];
-            iv32 cur[GB_TAB_MAX_DIRTY];
-            for (int g = dr.x; g < dr.y; g++) {
-                int cnt;
-                warp_group<iv32, 1>(P, SP, k, g, c.r, dt, lane,
-                                    [&](const GbDTerm& D, unsigned combo, iv32* v) {
-                                        const float2 a = Tb.tv32[rowbase + D.row + combo];
-                                        v[0] = iv32{a.x, a.y};
-                                    }, cur + (g - dr.x), cnt);
-                red += 2 * (cnt > 0 ? cnt - 1 : 0);
-            }
-            const size_t nb = nbase + S.node0;
-            sums[k] = tab_path(S, dr, cur, [&](int i) { return TabPrec<float>::node(Tb, nb + i); }, red);
-        }
-        const iv32 F = outer_fwd<float>(P, X, sums, O, red);
-        bool keep = !((double)F.lo > gub_prev);
-        if (keep) keep = !tab_mono_w<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, red, pops, lane);
-        if (lane == 0) ch.flag32[ci] = keep ? 1 : 0;
-    }
+    for (long long ci = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; ci < lim; ci += nw)
+        if (eval32_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, red, pops, lane) >= 0) nv++;
     warp_add_ops((lane == 0 ? red : 0) + pops, &st->ops32);
     if (lane == 0 && nv) {
         atomicAdd((unsigned long long*)&st->evals32, nv);
         atomicAdd((unsigned long long*)&st->children, nv);
+    }
+}
+
+// FP32 prefilter and FP64 evaluation in one pass, one child per warp: a warp
+// whose child passes the FP32 test evaluates it in FP64 at once (the same
+// children, the same previous GUB and the same operations as the FP32 kernel,
+// the survivor list and the FP64 kernel in sequence, without the list).
+__global__ void __launch_bounds__(128) k_eval3264_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+                                                       GbChildren ch, GbSplit sp, GbState* st) {
+    if (st->halt) return;
+    const long long lim = st->nch;
+    const double gub_prev = gb_key_value(st->gub_key);
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    int red32 = 0, pops32 = 0, red64 = 0, pops64 = 0;
+    unsigned long long nv = 0, n32 = 0, key = ~0ull;
+    bool has = false;
+    for (long long ci = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; ci < lim; ci += nw) {
+        const int v = eval32_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, red32, pops32, lane);
+        if (v < 0) continue;
+        nv++;
+        if (v == 0) continue;
+        n32++;
+        unsigned long long k2 = ~0ull;
+        bool h2 = false;
+        eval64_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, &k2, &h2, red64, pops64, lane);
+        if (h2 && k2 < key) key = k2, has = true;
+    }
+    warp_min_gub(key, has, st);
+    warp_add_ops((lane == 0 ? red32 : 0) + pops32, &st->ops32);
+    warp_add_ops((lane == 0 ? red64 : 0) + pops64, &st->ops64);
+    if (lane == 0 && nv) {
+        atomicAdd((unsigned long long*)&st->evals32, nv);
+        atomicAdd((unsigned long long*)&st->children, nv);
+    }
+    if (lane == 0 && n32) {
+        atomicAdd((unsigned long long*)&st->evals64, n32);
+        atomicAdd((unsigned long long*)&st->mids, n32);
+        atomicAdd((unsigned long long*)&st->kept32, n32);
+        atomicAdd((unsigned long long*)&st->n32, n32);
     }
 }
 
@@ -725,6 +773,15 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
     unsigned g = grid_for(Cmax, 128);
     if (g > 152 * GB_TAB_GRID) g = 152 * GB_TAB_GRID;
     k_eval64_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                                    const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
+                                    cudaStream_t s) {
+    unsigned g = grid_for(Cmax * 32, 128);
+    if (g > 152 * 32) g = 152 * 32;
+    k_eval3264_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);
     return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ struct GbPool {
     double2* rgmid;
     float2* rgsum32;
     unsigned* rfree;  // [R] free records
-    unsigned* rmark;  // [R / 32 + 1] mark bits of the record collector
+    unsigned* rmark;  // [R] collection number that last found the record referenced
     unsigned char* rwide;  // [R] 1: some coordinate of the record is at least tol_x wide
     int* swide;       // [cap] records of the box with rwide = 1 (0: the box is final)
     long long R;      // record capacity
@@ -148,6 +148,10 @@ cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents&
 cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                  const GbChildren& ch, long long Cmax, const GbSplit& sp, bool from_list,
                                  GbState* st, cudaStream_t s);
+// FP32 prefilter + FP64 evaluation fused, one child per warp (tables).
+cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                                    const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
+                                    cudaStream_t s);
 cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                  const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
                                  cudaStream_t s);
