@@ -246,6 +246,7 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     P.n_outer = (int)H.outer.size();
     P.outer_root = H.outer_root;
     P.n_var_leaves = (int)H.var_leaves.size();
+    P.outer_sum = (H.outer.size() == 1 && H.outer[0].op == D_ISUMV && H.outer_root == 0) ? 1 : 0;
     GbIns *d_outer, *d_tins;
     GbSum* d_sums;
     GbGroup* d_groups;
@@ -386,7 +387,9 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             GbDTerm* d_dt;
             int2* d_jk;
             GbContrib* d_cb;
-            if ((e = upload(&d_spc, Hh.sp_of_cyc.data(), Hh.sp_of_cyc.size(), A)) ||
+            GbJkD* d_jkd;
+            if ((e = upload(&d_jkd, Hh.jkd.data(), Hh.jkd.size(), A)) ||
+                (e = upload(&d_spc, Hh.sp_of_cyc.data(), Hh.sp_of_cyc.size(), A)) ||
                 (e = upload(&d_sps, Hh.sps.data(), Hh.sps.size(), A)) ||
                 (e = upload(&d_dt, Hh.dterms.data(), Hh.dterms.size(), A)) ||
                 (e = upload(&d_jk, Hh.jk.data(), Hh.jk.size(), A)) ||
@@ -404,11 +407,17 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             P.dterms = d_dt;
             P.jk = d_jk;
             P.contribs = d_cb;
+            P.jkd = d_jkd;
+            P.max_drows = Hh.max_drows > 0 ? Hh.max_drows : 1;
             GbTabs& T = p->tabs;
             T.max_rows = P.max_rows > 0 ? P.max_rows : 1;
             T.max_leaves = P.max_leaves;
             T.tree_nodes = P.tree_nodes;
+            T.max_drows = P.max_drows;
             const size_t rows = K * (size_t)T.max_rows, nodes = K * (size_t)T.tree_nodes;
+            if ((e = alloc(&T.td64, K * (size_t)T.max_drows, A)) ||
+                (fp32 && (e = alloc(&T.td32, K * (size_t)T.max_drows, A))))
+                return bad(e, "allocate partial tables");
             if ((e = alloc(&T.tv64, rows, A)) || (e = alloc(&T.tm64, rows, A)) ||
                 (e = alloc(&T.tl64, rows * T.max_leaves, A)) || (e = alloc(&T.nf64, nodes, A)) ||
                 (e = alloc(&T.nm64, nodes, A)))

@@ -326,6 +326,8 @@ void gb_build_tables(GbHostProg* P, int m, int d) {
     P->dterms.clear();
     P->jk.clear();
     P->contribs.clear();
+    P->jkd.clear();
+    P->max_drows = 0;
     P->max_rows = P->max_dterm = 0;
     const int n = P->n, B = P->B, ns = (int)P->sums.size();
     int node = 0, max_leaves = 0;
@@ -405,9 +407,31 @@ void gb_build_tables(GbHostProg* P, int m, int d) {
                             }
                         }
                     }
-                    P->jk.push_back(int2{start, (int)P->contribs.size()});
+                    const int end = (int)P->contribs.size();
+                    P->jk.push_back(int2{start, end});
+                    // digit bits the contributions depend on
+                    GbJkD J{0, -1, 0};
+                    if (end > start) {
+                        int lo = 1 << 30, hi = 0;
+                        for (int q = start; q < end; q++) {
+                            const GbContrib& C = P->contribs[q];
+                            const int nb = __builtin_popcount((unsigned)C.mask);
+                            if (nb == 0) continue;
+                            lo = std::min(lo, (int)C.dshift);
+                            hi = std::max(hi, (int)C.dshift + nb);
+                        }
+                        if (lo > hi) lo = hi = 0;   // no contribution touches a split coordinate
+                        if (hi - lo <= GB_TAB_DBITS) {
+                            J.base = sp.drows;
+                            J.shift = (int16_t)lo;
+                            J.mask = (uint16_t)((1u << (hi - lo)) - 1u);
+                            sp.drows += 1 << (hi - lo);
+                        }
+                    }
+                    P->jkd.push_back(J);
                 }
             }
+            P->max_drows = std::max(P->max_drows, sp.drows);
             P->sp_of_cyc[c] = (int)P->sps.size();
             P->sps.push_back(sp);
         }

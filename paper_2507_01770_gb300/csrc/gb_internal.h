@@ -72,7 +72,7 @@ struct GbSplitPos {
     int32_t dterm0, ndterm;   // dirty terms [dterm0, dterm0 + ndterm)
     int32_t tab_entries;      // combinations over all dirty terms (table rows)
     int32_t jk0;              // (coordinate of the block, sum) ranges start
-    int32_t pad;
+    int32_t drows;            // rows of the per-parent partial tables
 };
 struct GbDTerm {
     int16_t sum, w;           // sum index, number of split coordinates touched
@@ -87,6 +87,16 @@ struct GbContrib {
     int32_t dterm, leaf;
     int32_t base;
     int16_t dshift;
+    uint16_t mask;
+};
+// Per (coordinate of the block, sum): the sum over its contributions of the
+// leaf adjoints depends only on the child's digit bits [shift, shift + bits)
+// (bits <= GB_TAB_DBITS); such sums are tabulated per parent at rows
+// base + ((r >> shift) & mask).  shift < 0: not tabulated.
+#define GB_TAB_DBITS 6
+struct GbJkD {
+    int32_t base;
+    int16_t shift;
     uint16_t mask;
 };
 
@@ -120,6 +130,9 @@ struct GbProg {
     const GbDTerm* dterms;
     const int2* jk;                  // [(c1 - c0) * n_sum] per split position: contribution ranges
     const GbContrib* contribs;
+    const GbJkD* jkd;                // parallel to jk: partial-table rows
+    int32_t max_drows;
+    int32_t outer_sum;               // 1: the outer expression is one sum (F = that sum, adjoint [1, 1])
 };
 
 // Host-side compiled program (arrays in host memory before upload).
@@ -146,6 +159,8 @@ struct GbHostProg {
     std::vector<GbDTerm> dterms;
     std::vector<int2> jk;
     std::vector<GbContrib> contribs;
+    std::vector<GbJkD> jkd;
+    int32_t max_drows = 0;
 };
 // Builds the per-split-position table layouts for pieces m and split width d;
 // leaves tab_ok = 0 when a layout exceeds the table limits.

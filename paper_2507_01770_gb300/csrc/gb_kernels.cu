@@ -1194,6 +1194,8 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     if (tabs) {
         gb_launch_count++;
         if ((e = gb_launch_ptab(P, pool, par, *tabs, G.K, sp, st, s)) != cudaSuccess) return e;
+        gb_launch_count++;
+        if ((e = gb_launch_ptab_d(P, pool, par, *tabs, G.K, P.B, st, s)) != cudaSuccess) return e;
     }
     const bool fused = G.fp32 && tabs && tabs->warp;
     if (fused) {

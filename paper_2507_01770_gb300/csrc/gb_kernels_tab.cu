@@ -184,6 +184,49 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
 }
 
 // ---------------------------------------------------------------------------
+// k_ptab_d: per parent (blockIdx.y), the partial tables: for each (coordinate
+// of the block, sum) tabulated by the layout and each digit combination of
+// its bits, the serial sum of the leaf adjoints of its contributions (the
+// order tab_partial uses), FP64 and FP32.  Runs after k_ptab.
+__global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents par, GbTabs T,
+                                                const GbState* st) {
+    if (st->halt) return;
+    const long long p = blockIdx.y;
+    if (p >= st->parents) return;
+    const int4 info = par.info[p];
+    const int spi = P.sp_of_cyc[info.x];
+    if (spi < 0) return;
+    const GbSplitPos SP = P.sps[spi];
+    const int c0 = info.z * P.B, c1 = min(P.n, c0 + P.B);
+    const int nent = (c1 - c0) * P.n_sum;
+    const double2* tl = T.tl64 + (size_t)p * T.max_rows * T.max_leaves;
+    const float2* tl32 = pool.fp32 ? T.tl32 + (size_t)p * T.max_rows * T.max_leaves : nullptr;
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < (nent << GB_TAB_DBITS);
+         item += gridDim.x * blockDim.x) {
+        const int e = item >> GB_TAB_DBITS, c = item & ((1 << GB_TAB_DBITS) - 1);
+        const GbJkD J = P.jkd[SP.jk0 + e];
+        if (J.shift < 0 || c > (int)J.mask) continue;
+        const int2 rg = P.jk[SP.jk0 + e];
+        const unsigned r = (unsigned)c << J.shift;
+        iv64 D{0.0, 0.0};
+        iv32 D32{0.f, 0.f};
+        for (int q = rg.x; q < rg.y; q++) {
+            const GbContrib C = P.contribs[q];
+            const int at = C.base + (int)((r >> C.dshift) & C.mask) * T.max_leaves;
+            const double2 v = tl[at];
+            D = q > rg.x ? iadd(D, iv64{v.x, v.y}) : iv64{v.x, v.y};
+            if (tl32) {
+                const float2 v32 = tl32[at];
+                D32 = q > rg.x ? iadd(D32, iv32{v32.x, v32.y}) : iv32{v32.x, v32.y};
+            }
+        }
+        const size_t o = (size_t)p * T.max_drows + J.base + c;
+        T.td64[o] = make_double2(D.lo, D.hi);
+        if (tl32) T.td32[o] = make_float2(D32.lo, D32.hi);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Path of sum k's pairwise group tree above its dirty groups [dr.x, dr.y)
 // (values cur[0 .. dr.y - dr.x)), with the parent's tree nodes (node(i),
 // level-major) for the clean siblings; returns the sum.
@@ -314,6 +357,25 @@ __device__ __forceinline__ const float2* leaf_tab<float>(const GbTabs& Tb, long 
     return Tb.tl32 + (size_t)p * Tb.max_rows * Tb.max_leaves;
 }
 
+template <typename T>
+__device__ __forceinline__ const typename TabPrec<T>::P2* part_tab(const GbTabs& Tb, long long p);
+template <>
+__device__ __forceinline__ const double2* part_tab<double>(const GbTabs& Tb, long long p) {
+    return Tb.td64 + (size_t)p * Tb.max_drows;
+}
+template <>
+__device__ __forceinline__ const float2* part_tab<float>(const GbTabs& Tb, long long p) {
+    return Tb.td32 + (size_t)p * Tb.max_drows;
+}
+
+// Value of the outer expression (F from the sums).
+template <typename T, typename V>
+__device__ __forceinline__ typename TabPrec<T>::I outer_value(const GbProg& P, const V& X,
+                                                              const typename TabPrec<T>::I* sums,
+                                                              typename TabPrec<T>::I* O, int& ops) {
+    return P.outer_sum ? sums[0] : outer_fwd<T>(P, X, sums, O, ops);
+}
+
 // Interval partial of coordinate j (c0 = block start) from the outer leaves
 // and the tabulated leaf adjoints; `unit` marks sums whose outer adjoint is
 // exactly [1, 1] (a plain sum: the product adj * D equals D and is skipped);
@@ -322,6 +384,7 @@ __device__ __forceinline__ const float2* leaf_tab<float>(const GbTabs& Tb, long 
 template <typename T>
 __device__ __forceinline__ typename TabPrec<T>::I tab_partial(const GbProg& P, const GbTabs& Tb,
                                                               const typename TabPrec<T>::P2* tl,
+                                                              const typename TabPrec<T>::P2* td,
                                                               const GbSplitPos& SP, int j, int c0, unsigned r,
                                                               const typename TabPrec<T>::I* OA, unsigned unit,
                                                               int& ops) {
@@ -335,16 +398,23 @@ __device__ __forceinline__ typename TabPrec<T>::I tab_partial(const GbProg& P, c
         else g = OA[L.reg], have = true;
     }
     for (int k = 0; k < P.n_sum; k++) {
-        const int2 rg = P.jk[SP.jk0 + (j - c0) * P.n_sum + k];
+        const int at = SP.jk0 + (j - c0) * P.n_sum + k;
+        const int2 rg = P.jk[at];
         if (rg.x == rg.y) continue;
         I Dk;
-        for (int q = rg.x; q < rg.y; q++) {
-            const GbContrib C = P.contribs[q];
-            const unsigned combo = (r >> C.dshift) & C.mask;
-            const typename TabPrec<T>::P2 e = tl[C.base + (int)combo * Tb.max_leaves];
-            const I v = mk<T>(e.x, e.y);
-            if (q > rg.x) Dk = iadd(Dk, v), ops += 2;
-            else Dk = v;
+        const GbJkD J = P.jkd[at];
+        if (J.shift >= 0) {   // tabulated per parent (k_ptab_d)
+            const typename TabPrec<T>::P2 e = td[J.base + (int)((r >> J.shift) & J.mask)];
+            Dk = mk<T>(e.x, e.y);
+        } else {
+            for (int q = rg.x; q < rg.y; q++) {
+                const GbContrib C = P.contribs[q];
+                const unsigned combo = (r >> C.dshift) & C.mask;
+                const typename TabPrec<T>::P2 e = tl[C.base + (int)combo * Tb.max_leaves];
+                const I v = mk<T>(e.x, e.y);
+                if (q > rg.x) Dk = iadd(Dk, v), ops += 2;
+                else Dk = v;
+            }
         }
         I term;
         if ((unit >> k) & 1u) term = Dk;
@@ -380,14 +450,18 @@ __device__ __forceinline__ bool tab_mono(const GbProg& P, const GbTabs& Tb, long
                                          int blk, unsigned r, const View<double>& X64,
                                          const typename TabPrec<T>::I* O, typename TabPrec<T>::I* OA, int& ops) {
     typedef typename TabPrec<T>::I I;
-    for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
-    OA[P.outer_root] = mk<T>((T)1, (T)1);
-    reverse_sweep<T>(P.outer, P.n_outer, O, OA, ops);
+    unsigned unit = 1u;   // a single outer sum: its adjoint is [1, 1]
+    if (!P.outer_sum) {
+        for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
+        OA[P.outer_root] = mk<T>((T)1, (T)1);
+        reverse_sweep<T>(P.outer, P.n_outer, O, OA, ops);
+        unit = unit_sums(P, OA);
+    }
     const int c0 = blk * P.B, c1 = min(P.n, c0 + P.B);
     const typename TabPrec<T>::P2* tl = leaf_tab<T>(Tb, p);
-    const unsigned unit = unit_sums(P, OA);
+    const typename TabPrec<T>::P2* td = part_tab<T>(Tb, p);
     for (int j = c0; j < c1; j++) {
-        const I g = tab_partial<T>(P, Tb, tl, SP, j, c0, r, OA, unit, ops);
+        const I g = tab_partial<T>(P, Tb, tl, td, SP, j, c0, r, OA, unit, ops);
         if (mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi))) return true;
     }
     return false;
@@ -444,12 +518,12 @@ __device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& 
     MidView MX{X};
     iv64 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];
     tab_sums64(P, Tb, c.p, SP, blk, c.r, sums, msums, ops);
-    iv64 Fm = outer_fwd<double>(P, MX, msums, O, ops);
+    iv64 Fm = outer_value<double>(P, MX, msums, O, ops);
     if (Fm.hi == Fm.hi) {
         *gkey = gb_order_key(Fm.hi);
         *has_key = true;
     }
-    iv64 F = outer_fwd<double>(P, X, sums, O, ops);
+    iv64 F = outer_value<double>(P, X, sums, O, ops);
     bool keep = !(F.lo > gub_prev);
     if (keep) keep = !tab_mono<double>(P, Tb, c.p, SP, blk, c.r, X, O, OA, ops);
     ch.flo[ci] = canon_lo(F.lo);
@@ -508,7 +582,7 @@ __global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval32_tab(GbProg P, GbPoo
                 int dt = SP.dterm0;
                 for (int k = 0; k < P.n_sum; k++)
                     sums[k] = tab_sum32(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
-                iv32 F = outer_fwd<float>(P, X, sums, O, ops);
+                iv32 F = outer_value<float>(P, X, sums, O, ops);
                 bool keep = !((double)F.lo > gub_prev);
                 if (keep) keep = !tab_mono<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, ops);
                 ch.flag32[ci] = keep ? 1 : 0;
@@ -540,15 +614,19 @@ __device__ __forceinline__ bool tab_mono_w(const GbProg& P, const GbTabs& Tb, lo
                                            const typename TabPrec<T>::I* O, typename TabPrec<T>::I* OA,
                                            int& red, int& par, int lane) {
     typedef typename TabPrec<T>::I I;
-    for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
-    OA[P.outer_root] = mk<T>((T)1, (T)1);
-    reverse_sweep<T>(P.outer, P.n_outer, O, OA, red);
+    unsigned unit = 1u;   // a single outer sum: its adjoint is [1, 1]
+    if (!P.outer_sum) {
+        for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
+        OA[P.outer_root] = mk<T>((T)1, (T)1);
+        reverse_sweep<T>(P.outer, P.n_outer, O, OA, red);
+        unit = unit_sums(P, OA);
+    }
     const int c0 = blk * P.B, c1 = min(P.n, c0 + P.B);
     const typename TabPrec<T>::P2* tl = leaf_tab<T>(Tb, p);
-    const unsigned unit = unit_sums(P, OA);
+    const typename TabPrec<T>::P2* td = part_tab<T>(Tb, p);
     bool hit = false;
     for (int j = c0 + lane; j < c1 && !hit; j += 32) {
-        const I g = tab_partial<T>(P, Tb, tl, SP, j, c0, r, OA, unit, par);
+        const I g = tab_partial<T>(P, Tb, tl, td, SP, j, c0, r, OA, unit, par);
         hit = mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi));
     }
     return __any_sync(0xffffffffu, hit);
@@ -596,12 +674,12 @@ __device__ __forceinline__ bool eval64_tab_child_w(const GbProg& P, const GbPool
         sums[k] = tab_path(S, dr, curF, [&](int i) { return TabPrec<double>::node(Tb, nb + i); }, red);
         msums[k] = tab_path(S, dr, curM, [&](int i) { return mid_node(Tb, nb + i); }, red);
     }
-    const iv64 Fm = outer_fwd<double>(P, MX, msums, O, red);
+    const iv64 Fm = outer_value<double>(P, MX, msums, O, red);
     if (Fm.hi == Fm.hi) {
         *gkey = gb_order_key(Fm.hi);
         *has_key = true;
     }
-    const iv64 F = outer_fwd<double>(P, X, sums, O, red);
+    const iv64 F = outer_value<double>(P, X, sums, O, red);
     bool keep = !(F.lo > gub_prev);
     if (keep) keep = !tab_mono_w<double>(P, Tb, c.p, SP, blk, c.r, X, O, OA, red, pops, lane);
     if (lane == 0) {
@@ -677,7 +755,7 @@ __device__ __forceinline__ int eval32_tab_child_w(const GbProg& P, const GbPool&
         const size_t nb = nbase + S.node0;
         sums[k] = tab_path(S, dr, cur, [&](int i) { return TabPrec<float>::node(Tb, nb + i); }, red);
     }
-    const iv32 F = outer_fwd<float>(P, X, sums, O, red);
+    const iv32 F = outer_value<float>(P, X, sums, O, red);
     bool keep = !((double)F.lo > gub_prev);
     if (keep) keep = !tab_mono_w<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, red, pops, lane);
     if (lane == 0) ch.flag32[ci] = keep ? 1 : 0;
@@ -773,6 +851,13 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
     unsigned g = grid_for(Cmax, 128);
     if (g > 152 * GB_TAB_GRID) g = 152 * GB_TAB_GRID;
     k_eval64_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                             long long K, int B, GbState* st, cudaStream_t s) {
+    const int items = B * P.n_sum << GB_TAB_DBITS;
+    k_ptab_d<<<dim3((unsigned)grid_for(items, 128), (unsigned)K), 128, 0, s>>>(P, pool, par, T, st);
     return cudaGetLastError();
 }
 

@@ -77,7 +77,9 @@ struct GbTabs {
     double2* nf64;    // group tree of the parent's cached sums: F
     double2* nm64;    // midpoint
     float2* nf32;     // FP32
-    int max_rows, max_leaves, tree_nodes;
+    double2* td64;    // per (coordinate, sum) sums of leaf adjoints by digit combination
+    float2* td32;     // FP32
+    int max_rows, max_leaves, tree_nodes, max_drows;
     int warp;         // child kernels: 1 one child per warp, 0 one child per thread
 };
 
@@ -149,6 +151,9 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
                                  const GbChildren& ch, long long Cmax, const GbSplit& sp, bool from_list,
                                  GbState* st, cudaStream_t s);
 // FP32 prefilter + FP64 evaluation fused, one child per warp (tables).
+// Partial tables of every parent (after gb_launch_ptab).
+cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                             long long K, int B, GbState* st, cudaStream_t s);
 cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                     const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
                                     cudaStream_t s);
