@@ -112,7 +112,7 @@ struct gb_problem {
     SolveRun run;
     GbGenConst G{};
     gb_gen_stat* trace_dev = nullptr;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // one generation, pool buffers 0->1 and 1->0
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // gens_per_sync generations starting on pool buffer 0 / 1
     long long graph_kernels = 0;
     size_t device_bytes = 0;       // device memory held by the problem
     bool marks_used = false;       // a solve stamped record marks (cleared before the next one)
@@ -506,21 +506,33 @@ __attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
     return GB_OK;
 }
 
-// Captures one generation per pool-buffer parity as a CUDA graph (once per
-// problem; every argument of a generation is fixed, sizes come from the
-// device state).
+// Captures gens_per_sync consecutive generations as one CUDA graph per
+// starting pool buffer (once per problem; every argument of a generation is
+// fixed, sizes come from the device state, and a generation that must not
+// run is skipped by all its kernels), so the host launches one graph per
+// state read.
 static cudaError_t capture_graphs(gb_problem* p) {
     cudaStream_t s = p->stream;
+    const int G = p->opt.gens_per_sync;
     for (int par = 0; par < 2; par++) {
         if (p->gexec[par]) continue;
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
         long long nl = 0;
-        e = gb_launch_generation(p->P, p->pool, p->E[par], p->E[1 - par], p->par, p->ch, p->sp, p->sc,
-                                 p->use_tabs ? &p->tabs : nullptr, p->G, p->cap, p->Cmax, p->st, s, nullptr, &nl);
+        for (int k = 0; k < G && e == cudaSuccess; k++) {
+            const int b = (par + k) & 1;
+            long long n1 = 0;
+            e = gb_launch_generation(p->P, p->pool, p->E[b], p->E[1 - b], p->par, p->ch, p->sp, p->sc,
+                                     p->use_tabs ? &p->tabs : nullptr, p->G, p->cap, p->Cmax, p->st, s, nullptr,
+                                     &n1);
+            nl += n1;
+        }
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return e;
+        }
         if (e2 != cudaSuccess) return e2;
         e = cudaGraphInstantiate(&p->gexec[par], g, 0);
         cudaGraphDestroy(g);
@@ -563,11 +575,8 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
     const int G = p->opt.gens_per_sync;
     if (G > 1) {
         if ((e = capture_graphs(p)) != cudaSuccess) return stop(cuda_fail(e, "graph capture"));
-        for (int k = 0; k < G; k++) {
-            if ((e = cudaGraphLaunch(p->gexec[(cur + k) & 1], s)) != cudaSuccess)
-                return stop(cuda_fail(e, "cudaGraphLaunch"));
-            R.launches += p->graph_kernels;
-        }
+        if ((e = cudaGraphLaunch(p->gexec[cur], s)) != cudaSuccess) return stop(cuda_fail(e, "cudaGraphLaunch"));
+        R.launches += p->graph_kernels;
     } else {
         long long nl = 0;
         e = gb_launch_generation(p->P, p->pool, p->E[cur], p->E[1 - cur], p->par, p->ch, p->sp, p->sc,
