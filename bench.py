@@ -101,6 +101,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--n-max", type=int, default=2000)
+    ap.add_argument("--autotune", action="store_true",
+                    help="serving: tune fan-out / parents / kernel shape per family and n range first")
     return ap.parse_args()
 
 
@@ -223,6 +225,34 @@ def _serving_opts(gb, p, fp32):
                                  fp32_prefilter=int(fp32), pool_bytes=4 << 30, gens_per_sync=4)
 
 
+N_BUCKETS = (8, 32, 128, 512, 1 << 30)
+
+
+def _bucket(p):
+    return p.family, next(i for i, b in enumerate(N_BUCKETS) if p.n < b)
+
+
+def _bucket_name(key):
+    fam, i = key
+    lo = N_BUCKETS[i - 1] if i else 2
+    return f"{fam} n>={lo}" if i == len(N_BUCKETS) - 1 else f"{fam} {lo}<=n<{N_BUCKETS[i]}"
+
+
+def _tune_serving(gb, stream, budget_ms=1500.0):
+    """gb_autotune on the first request of every (family, n range) bucket."""
+    tuned, t0 = {}, time.perf_counter()
+    for _, p in stream:
+        key = _bucket(p)
+        if key in tuned:
+            continue
+        best, ms = gb.gb_autotune(p, budget_ms=budget_ms, base=_serving_opts(gb, p, True))
+        fan = best.split_m ** best.split_d
+        # relative to the block, so that it applies to every n of the bucket
+        tuned[key] = (dict(split_m=best.split_m, half_block=best.split_d < best.block,
+                           parents=best.max_children // fan, eval_mode=best.eval_mode), ms)
+    return tuned, time.perf_counter() - t0
+
+
 def run_serving(a):
     """Stream of minimisation requests served with continuous batching
     (FP32 prefilter + FP64) against the same problems solved one at a time in
@@ -238,6 +268,20 @@ def run_serving(a):
     gb.load()
     stream = S.serving_stream(count=a.requests, seed=0, rate=20.0, n_min=2, n_max=a.n_max, tol_f=1e-6)
     arrivals = np.array([t for t, _ in stream]) - stream[0][0]
+    tuned, tune_s = _tune_serving(gb, stream) if a.autotune else ({}, 0.0)
+
+    def served_opts(p):
+        o = _serving_opts(gb, p, True)
+        t = tuned.get(_bucket(p))
+        if t:
+            t = t[0]
+            o.split_m = t["split_m"]
+            o.split_d = (o.block + 1) // 2 if t["half_block"] else o.block
+            if o.split_m == 4 and o.split_d > 10:
+                o.split_d = 10
+            o.max_children = t["parents"] * t["split_m"] ** o.split_d
+            o.eval_mode = t["eval_mode"]
+        return o
 
     def serve(times):
         srv = gb.Server(pool_budget_bytes=150 << 30, device=0, max_active=32)
@@ -251,7 +295,7 @@ def run_serving(a):
             now = time.perf_counter() - t0
             while k < len(stream) and times[k] <= now:
                 p = stream[k][1]
-                pending[srv.submit(p, _serving_opts(gb, p, True))] = k
+                pending[srv.submit(p, served_opts(p))] = k
                 k += 1
             for rid in list(pending):
                 r = srv.poll(rid)
@@ -307,7 +351,10 @@ def run_serving(a):
                            "one_at_a_time_fp64_p99_ms": float(np.percentile(fifo_lat, 99)),
                            "one_at_a_time_fp64_solves_per_s": len(stream) / (arrivals[-1] + 0.0 +
                                                                              max(0.0, finish - arrivals[-1]))},
-                       "all_enclosures_valid": bool(ok and seq_ok)}}
+                       "all_enclosures_valid": bool(ok and seq_ok),
+                       "autotune": ({_bucket_name(k): dict(v[0], solve_ms=v[1])
+                                     for k, v in tuned.items()} if tuned else None),
+                       "autotune_s": tune_s}}
     print(json.dumps(line), flush=True)
 
 

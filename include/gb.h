@@ -276,6 +276,26 @@ gb_status gb_problem_info(const gb_problem* prob, int32_t* block, int32_t* n_blo
  * CUDA-event time in *ms.  Blocking. */
 gb_status gb_measure_peak(int32_t device, int32_t which, double* ops_per_s, double* ms);
 
+/* ---------------------------------------------------------------------- */
+/* Autotuner of the batching layer (the paper fixes m = 4, d = 10, §4)      */
+/* ---------------------------------------------------------------------- */
+/* Times complete solves of the problem (arguments as in gb_create_problem)
+ * under candidate settings of the bisection fan-out (split_m in {2, 4},
+ * split_d in {B, ceil(B/2)} with m^d <= 2^20), the parents per generation
+ * (max_children = 1 or 4 times m^d) and the child-kernel shape (eval_mode 3:
+ * one child per thread, 4: one child per warp, when term tables are used),
+ * starting from *base (NULL: defaults; its block, tolerances, precision,
+ * pool and device are kept), and writes the fastest setting to *best and its
+ * solve time (ms, host clock, second of two solves) to *best_ms.  Every
+ * candidate is a rigorous solve; only the time differs.  Candidates ending
+ * with GB_E_CAPACITY or GB_E_LIMIT are skipped; candidates are tried while
+ * the elapsed time is below budget_ms (at least one is always tried).
+ * Returns GB_E_LIMIT if no candidate completed.  Blocking; allocates and
+ * frees one problem per candidate. */
+gb_status gb_autotune(const gb_node* dag, int32_t n_nodes, int32_t root, const double* const* tables,
+                      const int64_t* table_lens, int32_t n_tables, int32_t n, const double* l, const double* u,
+                      double tol, const gb_options* base, double budget_ms, gb_options* best, double* best_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,7 +69,7 @@ class gb_result(ctypes.Structure):
 EXPORTS = ["gb_default_options", "gb_create_problem", "gb_solve", "gb_solve_device",
            "gb_free_result", "gb_destroy_problem", "gb_status_str", "gb_last_error",
            "gb_eval_boxes", "gb_eval_boxes_noalloc", "gb_problem_info", "gb_measure_peak",
-           "gb_server_create", "gb_submit", "gb_poll", "gb_server_destroy"]
+           "gb_server_create", "gb_submit", "gb_poll", "gb_server_destroy", "gb_autotune"]
 
 
 def library_path() -> str:
@@ -88,6 +88,10 @@ def load(build_if_missing: bool = True):
         raise ImportError(f"CUDA library not built: {path}")
     L = ctypes.CDLL(path)
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.gb_autotune.argtypes = [vp, i32, i32, ctypes.POINTER(_PD), ctypes.POINTER(i64), i32, i32, _PD, _PD,
+                              ctypes.c_double, ctypes.POINTER(gb_options), ctypes.c_double,
+                              ctypes.POINTER(gb_options), ctypes.POINTER(ctypes.c_double)]
+    L.gb_autotune.restype = ctypes.c_int
     L.gb_default_options.argtypes = [ctypes.POINTER(gb_options)]
     L.gb_default_options.restype = None
     L.gb_create_problem.argtypes = [vp, i32, i32, ctypes.POINTER(_PD), ctypes.POINTER(i64), i32, i32,
@@ -179,6 +183,27 @@ def gb_create_problem(nodes: np.ndarray, root: int, tables, n: int, l, u, tol: f
     if rc != GB_OK:
         raise GbError(rc, gb_last_error())
     return _Problem(h, int(n))
+
+
+def gb_autotune(problem, budget_ms: float = 2000.0, base: gb_options | None = None) -> tuple[gb_options, float]:
+    """Fastest fan-out / parents-per-generation / child-kernel setting for a
+    problem description (nodes, root, tables, n, l, u, tol_f), by timing
+    complete solves; returns (options, solve ms)."""
+    L = load()
+    nodes = np.ascontiguousarray(problem.nodes)
+    tabs = [np.ascontiguousarray(t, dtype=np.float64) for t in problem.tables]
+    ptrs = (_PD * max(1, len(tabs)))(*[t.ctypes.data_as(_PD) for t in tabs])
+    lens = (ctypes.c_int64 * max(1, len(tabs)))(*[len(t) for t in tabs])
+    l = np.ascontiguousarray(problem.l, dtype=np.float64)
+    u = np.ascontiguousarray(problem.u, dtype=np.float64)
+    best, ms = gb_options(), ctypes.c_double()
+    rc = L.gb_autotune(nodes.ctypes.data, len(nodes), int(problem.root), ptrs, lens, len(tabs), int(problem.n),
+                       l.ctypes.data_as(_PD), u.ctypes.data_as(_PD), float(problem.tol_f),
+                       ctypes.byref(base) if base is not None else None, float(budget_ms), ctypes.byref(best),
+                       ctypes.byref(ms))
+    if rc != GB_OK:
+        raise GbError(rc, gb_last_error())
+    return best, ms.value
 
 
 @dataclass

@@ -1,6 +1,6 @@
 """In-tree build of the CUDA library (libgb.so) for sm_103a.
 
-The three translation units are compiled in parallel with nvcc and linked
+The translation units are compiled in parallel with nvcc and linked
 into ``paper_2507_01770_gb300/_build/libgb.so``.  Device code is compiled
 without fast math and with FMA contraction disabled: the directed-rounding
 intrinsics carry their own rounding, and the round-to-nearest steps of the
@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgb.so")
-SOURCES = ["gb_kernels.cu", "gb_kernels_tab.cu", "gb_api.cu", "gb_compile.cpp", "gb_noalloc.cu", "gb_server.cpp"]
+SOURCES = ["gb_kernels.cu", "gb_kernels_tab.cu", "gb_api.cu", "gb_compile.cpp", "gb_noalloc.cu", "gb_server.cpp",
+           "gb_tune.cpp"]
 HEADERS = ["gb_internal.h", "gb_interval.cuh", "gb_eval.cuh", "gb_launch.h", "gb_child.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",

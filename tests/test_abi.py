@@ -75,6 +75,14 @@ def test_invalid_problems_rejected_without_gpu():
     assert "outside a sum" in str(e.value)
 
 
+def test_autotune_rejects_invalid_problems_without_gpu():
+    p = S.chain(n=6)
+    bad = S.Problem("bad", 6, p.nodes, p.root, p.tables, p.u, p.l, 1e-6, 3, p.s, 0)   # l > u
+    with pytest.raises(gb.GbError) as e:
+        gb.gb_autotune(bad, budget_ms=10.0)
+    assert e.value.status == gb.GB_E_INVALID
+
+
 def test_status_strings():
     assert gb.gb_status_str(gb.GB_OK) == "ok"
     assert gb.gb_status_str(gb.GB_E_CAPACITY) == "box pool capacity reached"
