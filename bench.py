@@ -358,6 +358,16 @@ def run_serving(a):
     print(json.dumps(line), flush=True)
 
 
+def reduce_ranks(torch, dist, device, dev_ms, e2e_t, evals, e2e_evals):
+    """Replicas: the job time is the slowest rank's (max), the work is every
+    rank's (sum); the whole-job value is sum / max."""
+    t = torch.tensor([dev_ms, e2e_t], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([evals, e2e_evals], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(c[0]), float(c[1])
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -456,12 +466,7 @@ def main():
         d2h = r.n_boxes * (2 * p.n + 1) * 8 + r.generations * (48 + 256) + 256
 
     if dist:
-        t = torch.tensor([dev_ms, e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([evals, e2e_evals], dtype=torch.float64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        dev_ms, e2e_t = float(t[0]), float(t[1])
-        evals, e2e_evals = float(c[0]), float(c[1])
+        dev_ms, e2e_t, evals, e2e_evals = reduce_ranks(torch, dist, dev, dev_ms, e2e_t, evals, e2e_evals)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
