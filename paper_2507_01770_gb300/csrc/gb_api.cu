@@ -215,7 +215,19 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     }
     // term-table layouts also set each sum's tree offsets: build them before
     // the program is uploaded
-    if (opt.eval_mode != 1) gb_build_tables(&p->hp, opt.split_m, opt.split_d);
+    if (opt.eval_mode != 1) {
+        // segment tables are per parent: the widest segments whose tables for
+        // all parents of a generation fit max(64 MiB, pool budget / 8)
+        const int msh = opt.split_m == 2 ? 1 : 2;
+        const long long fan = 1LL << (opt.split_d * msh);
+        const long long K = std::max(1LL, (long long)opt.max_children / fan);
+        const double budget = std::max(64.0 * (1 << 20), (double)opt.pool_bytes / 8.0);
+        const double per_row = opt.fp32_prefilter ? 40.0 : 32.0;
+        for (int sbits = GB_TAB_SBITS; sbits >= 0; sbits--) {
+            gb_build_tables(&p->hp, opt.split_m, opt.split_d, sbits);
+            if (!p->hp.tab_ok || (double)K * p->hp.max_srows * per_row <= budget) break;
+        }
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= opt.device || opt.device < 0) {
         delete p;
@@ -388,7 +400,9 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             int2* d_jk;
             GbContrib* d_cb;
             GbJkD* d_jkd;
+            GbSeg* d_segs;
             if ((e = upload(&d_jkd, Hh.jkd.data(), Hh.jkd.size(), A)) ||
+                (e = upload(&d_segs, Hh.segs.data(), Hh.segs.size(), A)) ||
                 (e = upload(&d_spc, Hh.sp_of_cyc.data(), Hh.sp_of_cyc.size(), A)) ||
                 (e = upload(&d_sps, Hh.sps.data(), Hh.sps.size(), A)) ||
                 (e = upload(&d_dt, Hh.dterms.data(), Hh.dterms.size(), A)) ||
@@ -409,11 +423,18 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             P.contribs = d_cb;
             P.jkd = d_jkd;
             P.max_drows = Hh.max_drows > 0 ? Hh.max_drows : 1;
+            P.segs = d_segs;
+            P.max_srows = Hh.max_srows > 0 ? Hh.max_srows : 1;
+            P.max_nseg = Hh.max_nseg;
             GbTabs& T = p->tabs;
             T.max_rows = P.max_rows > 0 ? P.max_rows : 1;
             T.max_leaves = P.max_leaves;
             T.tree_nodes = P.tree_nodes;
             T.max_drows = P.max_drows;
+            T.max_srows = P.max_srows;
+            if ((e = alloc(&T.ts64, K * (size_t)T.max_srows, A)) || (e = alloc(&T.tsm64, K * (size_t)T.max_srows, A)) ||
+                (fp32 && (e = alloc(&T.ts32, K * (size_t)T.max_srows, A))))
+                return bad(e, "allocate segment tables");
             const size_t rows = K * (size_t)T.max_rows, nodes = K * (size_t)T.tree_nodes;
             if ((e = alloc(&T.td64, K * (size_t)T.max_drows, A)) ||
                 (fp32 && (e = alloc(&T.td32, K * (size_t)T.max_drows, A))))

@@ -129,49 +129,44 @@ template <typename I> __device__ __forceinline__ I shfl_iv(I v, int src) {
     return v;
 }
 
-// In-place pairwise tree a[i] += a[i + s] (s = 1, 2, ..., 16) over the values
-// of lanes [0, r): the same tree the binary counter forms over r items.
-// Returns the result on every lane.
-template <typename I> __device__ __forceinline__ I warp_tree(I v, int r, int lane) {
-    for (int s = 1; s < 32; s <<= 1) {
-        I o;
-        o.lo = __shfl_down_sync(0xffffffffu, v.lo, s);
-        o.hi = __shfl_down_sync(0xffffffffu, v.hi, s);
-        if ((lane & (2 * s - 1)) == 0 && lane + s < r) v = iadd(v, o);
-    }
-    return shfl_iv(v, 0);
-}
-
-// Table values of dirty group g of sum k for child digits r, NV tables at a
-// time (load(D, combo, v) fills v[0..NV)), starting at dirty term dt (the
-// terms of a split position are ordered by sum, group and term, so those of
-// (k, g) are the run starting at dt).  The pairwise tree over the run is the
-// in-place tree within each aligned chunk of 32 terms (warp_tree) followed by
-// the same tree over the chunk sums (binary counter), i.e. the tree
-// group_sum forms.  dt advances past the run; cnt = its length.
-// Every lane returns the same values.
+// Value of dirty group g of sum k for child digits r, NV tables at a time,
+// from the group's term-tree segments starting at segment sg (the segments
+// of a split position are ordered by sum, group and term, so those of
+// (k, g) are the run starting at sg).  The lanes read one segment each
+// (load(G, row, v) fills v[0..NV) from the term row or the segment row);
+// the values are then pushed in order into the binary counter at each
+// segment's level, which forms the group's pairwise tree (Tree::push_level).
+// sg advances past the run; nseg = its length.  Every lane returns the same
+// values.
 template <typename I, int NV, typename L>
 __device__ __forceinline__ void warp_group(const GbProg& P, const GbSplitPos& SP, int k, int g, unsigned r,
-                                           int& dt, int lane, L load, I* out, int& cnt) {
+                                           int& sg, int lane, L load, I* out, int& nseg) {
     Tree<I> tr[NV];
     for (int t = 0; t < NV; t++) tr[t].init();
-    cnt = 0;
-    const int end = SP.dterm0 + SP.ndterm;
+    nseg = 0;
+    const int send = SP.seg0 + SP.nseg;
     for (;;) {
-        const int i = dt + lane;
+        const int i = sg + lane;
         bool mem = false;
+        int lev = 0;
         I v[NV];
         for (int t = 0; t < NV; t++) v[t].lo = v[t].hi = 0;
-        if (i < end) {
-            const GbDTerm D = P.dterms[i];
-            mem = D.sum == k && D.group == g;
-            if (mem) load(D, (r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u), v);
+        if (i < send) {
+            const GbSeg G = P.segs[i];
+            mem = G.sum == k && G.group == g;
+            if (mem) {
+                lev = G.level;
+                load(G, G.base + (int)((r >> G.shift) & G.mask), v);
+            }
         }
         const int rr = __popc(__ballot_sync(0xffffffffu, mem));
         if (rr == 0) break;
-        for (int t = 0; t < NV; t++) tr[t].push(warp_tree(v[t], rr, lane));
-        cnt += rr;
-        dt += rr;
+        for (int j = 0; j < rr; j++) {
+            const int lj = __shfl_sync(0xffffffffu, lev, j);
+            for (int t = 0; t < NV; t++) tr[t].push_level(shfl_iv(v[t], j), lj);
+        }
+        nseg += rr;
+        sg += rr;
         if (rr < 32) break;
     }
     for (int t = 0; t < NV; t++) out[t] = tr[t].result();

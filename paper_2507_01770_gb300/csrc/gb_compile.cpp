@@ -317,7 +317,7 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
 }
 
 // Per-split-position layouts of the per-parent term tables (see GbSplitPos).
-void gb_build_tables(GbHostProg* P, int m, int d) {
+void gb_build_tables(GbHostProg* P, int m, int d, int sbits) {
     P->tab_ok = 0;
     P->m = m;
     P->mshift = m == 2 ? 1 : 2;
@@ -328,6 +328,9 @@ void gb_build_tables(GbHostProg* P, int m, int d) {
     P->contribs.clear();
     P->jkd.clear();
     P->max_drows = 0;
+    P->segs.clear();
+    P->max_srows = 0;
+    P->max_nseg = 0;
     P->max_rows = P->max_dterm = 0;
     const int n = P->n, B = P->B, ns = (int)P->sums.size();
     int node = 0, max_leaves = 0;
@@ -383,6 +386,59 @@ void gb_build_tables(GbHostProg* P, int m, int d) {
             }
             sp.ndterm = (int)P->dterms.size() - sp.dterm0;
             sp.tab_entries = rows;
+            // segments of each dirty group's term tree: greedily the largest
+            // aligned block of 2^L terms whose digit bits fit GB_TAB_SBITS
+            sp.seg0 = (int)P->segs.size();
+            for (int q0 = 0; q0 < sp.ndterm;) {
+                const GbDTerm& D0 = P->dterms[sp.dterm0 + q0];
+                int cnt = 0;
+                while (q0 + cnt < sp.ndterm && P->dterms[sp.dterm0 + q0 + cnt].sum == D0.sum &&
+                       P->dterms[sp.dterm0 + q0 + cnt].group == D0.group)
+                    cnt++;
+                auto bits_of = [&](int t0, int len, int* lo_out) {
+                    int lo = 1 << 30, hi = 0;
+                    for (int t = t0; t < t0 + len; t++) {
+                        const GbDTerm& D = P->dterms[sp.dterm0 + q0 + t];
+                        if (D.w == 0) continue;
+                        lo = std::min(lo, (int)D.dshift);
+                        hi = std::max(hi, (int)D.dshift + D.w * P->mshift);
+                    }
+                    if (lo > hi) lo = hi = 0;
+                    *lo_out = lo;
+                    return hi - lo;
+                };
+                for (int t = 0; t < cnt;) {
+                    int L = 0, lo = 0;
+                    while (t % (2 << L) == 0 && t + (2 << L) <= cnt) {
+                        const int b = bits_of(t, 2 << L, &lo);
+                        if (b > sbits || b + L + 1 > GB_TAB_SCOST) break;
+                        L++;
+                    }
+                    const GbDTerm& D = P->dterms[sp.dterm0 + q0 + t];
+                    GbSeg g{};
+                    g.dterm = q0 + t;
+                    g.sum = (int8_t)D.sum;
+                    g.group = D.group;
+                    g.level = (int8_t)L;
+                    if (L == 0) {
+                        g.base = D.row;
+                        g.shift = D.dshift;
+                        g.mask = (uint16_t)((1u << (D.w * P->mshift)) - 1u);
+                    } else {
+                        const int b = bits_of(t, 1 << L, &lo);
+                        g.base = sp.srows;
+                        g.shift = (int16_t)lo;
+                        g.mask = (uint16_t)((1u << b) - 1u);
+                        sp.srows += 1 << b;
+                    }
+                    P->segs.push_back(g);
+                    t += 1 << L;
+                }
+                q0 += cnt;
+            }
+            sp.nseg = (int)P->segs.size() - sp.seg0;
+            P->max_srows = std::max(P->max_srows, sp.srows);
+            P->max_nseg = std::max(P->max_nseg, sp.nseg);
             if (rows > GB_TAB_MAX_ROWS) return;
             P->max_rows = std::max(P->max_rows, rows);
             P->max_dterm = std::max(P->max_dterm, sp.ndterm);

@@ -116,6 +116,20 @@ template <typename I> struct Tree {
         lvl[L] = v;
         cnt++;
     }
+    // Push the sum of an aligned block of 2^L items (cnt a multiple of 2^L):
+    // the same levels as pushing the block's items one by one, when v is
+    // the block's own in-place pairwise sum.
+    __device__ __forceinline__ void push_level(I v, int L) {
+        unsigned c = cnt >> L;
+        int lev = L;
+        while (c & 1u) {
+            v = iadd(lvl[lev], v);
+            c >>= 1;
+            lev++;
+        }
+        lvl[lev] = v;
+        cnt += 1u << L;
+    }
     __device__ __forceinline__ I result() const {
         I r;
         if (!cnt) { r.lo = 0; r.hi = 0; return r; }

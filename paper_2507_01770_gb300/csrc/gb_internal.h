@@ -73,6 +73,27 @@ struct GbSplitPos {
     int32_t tab_entries;      // combinations over all dirty terms (table rows)
     int32_t jk0;              // (coordinate of the block, sum) ranges start
     int32_t drows;            // rows of the per-parent partial tables
+    int32_t seg0, nseg;       // segments [seg0, seg0 + nseg) of the dirty groups' term trees
+    int32_t srows;            // rows of the per-parent segment tables
+    int32_t pad;
+};
+// A segment of a dirty group's term tree: the aligned block of 2^level terms
+// starting at dirty term dterm (relative to the split position's dterm0),
+// whose in-place pairwise sum depends only on the child's digit bits
+// [shift, shift + bits) (bits <= GB_TAB_SBITS).  level 0: a single term,
+// read from its term row `base`; level >= 1: tabulated per parent at segment
+// row base + ((r >> shift) & mask).  A group's segments cover its terms in
+// order, so pushing each segment's value into the binary counter at its
+// level gives the group's pairwise tree.
+#define GB_TAB_SBITS 10
+#define GB_TAB_SCOST 14   // a segment's table costs 2^(bits + level) additions per parent: at most 2^14
+struct GbSeg {
+    int32_t base;
+    int32_t dterm;
+    int16_t shift;
+    uint16_t mask;
+    int8_t sum, level;
+    int16_t group;
 };
 struct GbDTerm {
     int16_t sum, w;           // sum index, number of split coordinates touched
@@ -132,6 +153,8 @@ struct GbProg {
     const GbContrib* contribs;
     const GbJkD* jkd;                // parallel to jk: partial-table rows
     int32_t max_drows;
+    const GbSeg* segs;               // term-tree segments of every split position
+    int32_t max_srows, max_nseg;
     int32_t outer_sum;               // 1: the outer expression is one sum (F = that sum, adjoint [1, 1])
 };
 
@@ -161,10 +184,13 @@ struct GbHostProg {
     std::vector<GbContrib> contribs;
     std::vector<GbJkD> jkd;
     int32_t max_drows = 0;
+    std::vector<GbSeg> segs;
+    int32_t max_srows = 0, max_nseg = 0;
 };
 // Builds the per-split-position table layouts for pieces m and split width d;
 // leaves tab_ok = 0 when a layout exceeds the table limits.
-void gb_build_tables(GbHostProg* P, int m, int d);
+// sbits: largest digit-bit count of a tabulated term-tree segment (<= GB_TAB_SBITS).
+void gb_build_tables(GbHostProg* P, int m, int d, int sbits = GB_TAB_SBITS);
 // Compiles and validates a DAG; returns an empty string or an error message.
 std::string gb_compile(const gb_node* nodes, int32_t nn, int32_t root, const int64_t* tlen,
                        int32_t ntab, int32_t n, int32_t B, GbHostProg* out);

@@ -637,25 +637,26 @@ __global__ void k_cc_scatter(GbChildren ch, int mode, const GbState* st, const i
 }
 
 // Table path of the materialisation: the dirty group values of a survivor
-// (F, midpoint, FP32), one warp walking the dirty terms of its split position
-// (warp_group), staged in shared memory at [k * GB_TAB_MAX_DIRTY + g - dr.x].
+// (F, midpoint, FP32), one warp walking the term-tree segments of its split
+// position (warp_group), staged in shared memory at [k * GB_TAB_MAX_DIRTY +
+// g - dr.x].
 constexpr int GB_SHG = GB_MAX_ISUM * GB_TAB_MAX_DIRTY;
 __device__ __forceinline__ void tab_dirty_groups(const GbProg& P, const GbPool& pool, const GbTabs& Tb,
                                                  const ChildCtx& c, int lane, double2* shF, double2* shM,
                                                  float2* sh32) {
     const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
     const int blk = c.info.z;
-    const size_t rowbase = (size_t)c.p * Tb.max_rows;
-    int dtA = SP.dterm0, dtB = SP.dterm0;
+    const size_t rowbase = (size_t)c.p * Tb.max_rows, sbase = (size_t)c.p * Tb.max_srows;
+    int dtA = SP.seg0, dtB = SP.seg0;
     for (int k = 0; k < P.n_sum; k++) {
         const int2 dr = P.dirty[blk * P.n_sum + k];
         for (int g = dr.x; g < dr.y; g++) {
             iv64 v2[2];
             int cnt;
             warp_group<iv64, 2>(P, SP, k, g, c.r, dtA, lane,
-                                [&](const GbDTerm& D, unsigned combo, iv64* v) {
-                                    const double2 a = Tb.tv64[rowbase + D.row + combo];
-                                    const double2 b = Tb.tm64[rowbase + D.row + combo];
+                                [&](const GbSeg& G, int at, iv64* v) {
+                                    const double2 a = G.level ? Tb.ts64[sbase + at] : Tb.tv64[rowbase + at];
+                                    const double2 b = G.level ? Tb.tsm64[sbase + at] : Tb.tm64[rowbase + at];
                                     v[0] = iv64{a.x, a.y};
                                     v[1] = iv64{b.x, b.y};
                                 }, v2, cnt);
@@ -667,8 +668,8 @@ __device__ __forceinline__ void tab_dirty_groups(const GbProg& P, const GbPool& 
             if (pool.fp32) {
                 iv32 f;
                 warp_group<iv32, 1>(P, SP, k, g, c.r, dtB, lane,
-                                    [&](const GbDTerm& D, unsigned combo, iv32* v) {
-                                        const float2 a = Tb.tv32[rowbase + D.row + combo];
+                                    [&](const GbSeg& G, int at, iv32* v) {
+                                        const float2 a = G.level ? Tb.ts32[sbase + at] : Tb.tv32[rowbase + at];
                                         v[0] = iv32{a.x, a.y};
                                     }, &f, cnt);
                 if (lane == 0) sh32[at] = make_float2(f.lo, f.hi);

@@ -19,7 +19,7 @@ using namespace gb;
 // Resident blocks of 128 threads per SM the one-child-per-thread kernels are
 // compiled for (register budget 65536 / (128 * GB_TAB_MINB) per thread).
 #ifndef GB_TAB_MINB
-#define GB_TAB_MINB 6
+#define GB_TAB_MINB 7
 #endif
 // Blocks per SM of their grid (each thread loops over children).
 #ifndef GB_TAB_GRID
@@ -184,10 +184,13 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
 }
 
 // ---------------------------------------------------------------------------
-// k_ptab_d: per parent (blockIdx.y), the partial tables: for each (coordinate
-// of the block, sum) tabulated by the layout and each digit combination of
-// its bits, the serial sum of the leaf adjoints of its contributions (the
-// order tab_partial uses), FP64 and FP32.  Runs after k_ptab.
+// k_ptab_d: per parent (blockIdx.y), from the term rows of k_ptab (runs
+// after it): (1) the partial tables: for each (coordinate of the block, sum)
+// tabulated by the layout and each digit combination of its bits, the serial
+// sum of the leaf adjoints of its contributions (the order tab_partial uses);
+// (2) the segment tables: for each term-tree segment of level >= 1 and each
+// combination of its digit bits, the in-place pairwise sum of its terms (F,
+// midpoint, FP32).
 __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents par, GbTabs T,
                                                 const GbState* st) {
     if (st->halt) return;
@@ -201,8 +204,41 @@ __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents
     const int nent = (c1 - c0) * P.n_sum;
     const double2* tl = T.tl64 + (size_t)p * T.max_rows * T.max_leaves;
     const float2* tl32 = pool.fp32 ? T.tl32 + (size_t)p * T.max_rows * T.max_leaves : nullptr;
-    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < (nent << GB_TAB_DBITS);
+    const int nd_items = nent << GB_TAB_DBITS;
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nd_items + (SP.nseg << GB_TAB_SBITS);
          item += gridDim.x * blockDim.x) {
+        if (item >= nd_items) {   // segment table entry
+            const int si = (item - nd_items) >> GB_TAB_SBITS, c = (item - nd_items) & ((1 << GB_TAB_SBITS) - 1);
+            const GbSeg G = P.segs[SP.seg0 + si];
+            if (G.level == 0 || c > (int)G.mask) continue;
+            const unsigned r = (unsigned)c << G.shift;
+            const size_t rb = (size_t)p * T.max_rows;
+            Tree<iv64> tf, tm;
+            Tree<iv32> t32;
+            tf.init();
+            tm.init();
+            t32.init();
+            for (int t = 0; t < (1 << G.level); t++) {
+                const GbDTerm D = P.dterms[SP.dterm0 + G.dterm + t];
+                const size_t at = rb + D.row + ((r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u));
+                const double2 a = T.tv64[at], b = T.tm64[at];
+                tf.push(iv64{a.x, a.y});
+                tm.push(iv64{b.x, b.y});
+                if (tl32) {
+                    const float2 f = T.tv32[at];
+                    t32.push(iv32{f.x, f.y});
+                }
+            }
+            const size_t o = (size_t)p * T.max_srows + G.base + c;
+            const iv64 vf = tf.result(), vm = tm.result();
+            T.ts64[o] = make_double2(vf.lo, vf.hi);
+            T.tsm64[o] = make_double2(vm.lo, vm.hi);
+            if (tl32) {
+                const iv32 v32 = t32.result();
+                T.ts32[o] = make_float2(v32.lo, v32.hi);
+            }
+            continue;
+        }
         const int e = item >> GB_TAB_DBITS, c = item & ((1 << GB_TAB_DBITS) - 1);
         const GbJkD J = P.jkd[SP.jk0 + e];
         if (J.shift < 0 || c > (int)J.mask) continue;
@@ -262,84 +298,32 @@ __device__ __forceinline__ I tab_path(const GbSum& S, int2 dr, I* cur, N node, i
     return cur[0];
 }
 
-// Pairwise tree over the terms of one dirty group, two tables at once (F and
-// midpoint): the in-place tree within aligned chunks of 4 terms in registers,
-// then the binary counter over the chunk sums (the same tree as pushing
-// every term, see warp_group).
-template <typename I, typename L>
-__device__ __forceinline__ void group_pair(const GbProg& P, int k, int g, int& dt, int dend, L load, I& outA,
-                                           I& outB, int& cnt) {
-    Tree<I> ta, tb;
-    ta.init();
-    tb.init();
-    cnt = 0;
-    int chunks = 0;
-    I a0, a1, a2, a3, b0, b1, b2, b3;
-    for (;;) {
-        int r = 0;
-#pragma unroll
-        for (int t = 0; t < 4; t++) {
-            if (dt >= dend) break;
-            const GbDTerm D = P.dterms[dt];
-            if (D.sum != k || D.group != g) break;
-            I x, y;
-            load(D, x, y);
-            if (t == 0) a0 = x, b0 = y;
-            else if (t == 1) a1 = x, b1 = y;
-            else if (t == 2) a2 = x, b2 = y;
-            else a3 = x, b3 = y;
-            r++;
-            dt++;
-        }
-        if (r == 0) break;
-        // in-place tree over r <= 4 items: s = 1 then s = 2
-        if (r > 1) a0 = iadd(a0, a1), b0 = iadd(b0, b1);
-        if (r > 3) a2 = iadd(a2, a3), b2 = iadd(b2, b3);
-        if (r > 2) a0 = iadd(a0, a2), b0 = iadd(b0, b2);
-        cnt += r;
-        if (chunks == 0 && r < 4) {   // the whole group in one chunk
-            outA = a0;
-            outB = b0;
-            return;
-        }
-        ta.push(a0);
-        tb.push(b0);
-        chunks++;
-        if (r < 4) break;
-    }
-    if (cnt == 0) {
-        outA.lo = outA.hi = 0;
-        outB.lo = outB.hi = 0;
-        return;
-    }
-    outA = ta.result();
-    outB = tb.result();
-}
-
-// Sum k of a child (FP32 tables): dirty group leaves from the tables, then
-// the path of the pairwise tree above them with the parent's nodes for the
-// clean siblings.
+// Sum k of a child (FP32 tables): dirty group values from the term-tree
+// segments, then the path of the pairwise group tree above them with the
+// parent's nodes for the clean siblings.
 __device__ __forceinline__ iv32 tab_sum32(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
-                                          int k, int blk, unsigned r, int& dt, int& ops) {
+                                          int k, int blk, unsigned r, int& sg, int& ops) {
     const GbSum S = P.sums[k];
     const int2 dr = P.dirty[blk * P.n_sum + k];
     const float2* tv = Tb.tv32 + (size_t)p * Tb.max_rows;
+    const float2* ts = Tb.ts32 + (size_t)p * Tb.max_srows;
     const float2* nfk = Tb.nf32 + (size_t)p * Tb.tree_nodes + S.node0;
-    const int dend = SP.dterm0 + SP.ndterm;
+    const int send = SP.seg0 + SP.nseg;
     iv32 cur[GB_TAB_MAX_DIRTY];
     for (int g = dr.x; g < dr.y; g++) {
         Tree<iv32> tr;
         tr.init();
-        int cnt = 0;
-        while (dt < dend) {
-            const GbDTerm D = P.dterms[dt];
-            if (D.sum != k || D.group != g) break;
-            const float2 v = tv[D.row + (int)((r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u))];
-            tr.push(iv32{v.x, v.y});
-            cnt++;
-            dt++;
+        int ns = 0;
+        while (sg < send) {
+            const GbSeg G = P.segs[sg];
+            if (G.sum != k || G.group != g) break;
+            const int at = G.base + (int)((r >> G.shift) & G.mask);
+            const float2 v = G.level ? ts[at] : tv[at];
+            tr.push_level(iv32{v.x, v.y}, G.level);
+            ns++;
+            sg++;
         }
-        ops += 2 * (cnt > 0 ? cnt - 1 : 0);
+        ops += 2 * (ns > 0 ? ns - 1 : 0);
         cur[g - dr.x] = tr.result();
     }
     return tab_path(S, dr, cur, [&](int i) { const float2 v = nfk[i]; return iv32{v.x, v.y}; }, ops);
@@ -467,34 +451,44 @@ __device__ __forceinline__ bool tab_mono(const GbProg& P, const GbTabs& Tb, long
     return false;
 }
 
-// F and midpoint sums of a child in one walk over the dirty terms.
+// F and midpoint sums of a child in one walk over the term-tree segments.
 __device__ __forceinline__ void tab_sums64(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
                                            int blk, unsigned r, iv64* sums, iv64* msums, int& ops) {
     const double2* tv = Tb.tv64 + (size_t)p * Tb.max_rows;
     const double2* tm = Tb.tm64 + (size_t)p * Tb.max_rows;
+    const double2* ts = Tb.ts64 + (size_t)p * Tb.max_srows;
+    const double2* tsm = Tb.tsm64 + (size_t)p * Tb.max_srows;
     const double2* nf = Tb.nf64 + (size_t)p * Tb.tree_nodes;
     const double2* nm = Tb.nm64 + (size_t)p * Tb.tree_nodes;
-    int dt = SP.dterm0;
-    const int dend = SP.dterm0 + SP.ndterm;
-    auto load = [&](const GbDTerm& D, iv64& x, iv64& y) {
-        const int at = D.row + (int)((r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u));
-        const double2 a = tv[at], b = tm[at];
-        x = iv64{a.x, a.y};
-        y = iv64{b.x, b.y};
-    };
+    int sg = SP.seg0;
+    const int send = SP.seg0 + SP.nseg;
     for (int k = 0; k < P.n_sum; k++) {
         const GbSum S = P.sums[k];
         const int2 dr = P.dirty[blk * P.n_sum + k];
+        iv64 curF[GB_TAB_MAX_DIRTY], curM[GB_TAB_MAX_DIRTY];
+        for (int g = dr.x; g < dr.y; g++) {
+            Tree<iv64> tf, tmid;
+            tf.init();
+            tmid.init();
+            int ns = 0;
+            while (sg < send) {
+                const GbSeg G = P.segs[sg];
+                if (G.sum != k || G.group != g) break;
+                const int at = G.base + (int)((r >> G.shift) & G.mask);
+                const double2 a = G.level ? ts[at] : tv[at], b = G.level ? tsm[at] : tm[at];
+                tf.push_level(iv64{a.x, a.y}, G.level);
+                tmid.push_level(iv64{b.x, b.y}, G.level);
+                ns++;
+                sg++;
+            }
+            ops += 4 * (ns > 0 ? ns - 1 : 0);
+            curF[g - dr.x] = tf.result();
+            curM[g - dr.x] = tmid.result();
+        }
         const double2* nfk = nf + S.node0;
         const double2* nmk = nm + S.node0;
         auto nodeF = [&](int i) { const double2 v = nfk[i]; return iv64{v.x, v.y}; };
         auto nodeM = [&](int i) { const double2 v = nmk[i]; return iv64{v.x, v.y}; };
-        iv64 curF[GB_TAB_MAX_DIRTY], curM[GB_TAB_MAX_DIRTY];
-        for (int g = dr.x; g < dr.y; g++) {
-            int cnt;
-            group_pair(P, k, g, dt, dend, load, curF[g - dr.x], curM[g - dr.x], cnt);
-            ops += 4 * (cnt > 0 ? cnt - 1 : 0);
-        }
         sums[k] = tab_path(S, dr, curF, nodeF, ops);
         msums[k] = tab_path(S, dr, curM, nodeM, ops);
     }
@@ -579,9 +573,9 @@ __global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval32_tab(GbProg P, GbPoo
                 View<float> X = view32(pool, par, c, sp);
                 View<double> X64 = view64(pool, par, c, sp);
                 iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
-                int dt = SP.dterm0;
+                int sg = SP.seg0;
                 for (int k = 0; k < P.n_sum; k++)
-                    sums[k] = tab_sum32(P, Tb, c.p, SP, k, blk, c.r, dt, ops);
+                    sums[k] = tab_sum32(P, Tb, c.p, SP, k, blk, c.r, sg, ops);
                 iv32 F = outer_value<float>(P, X, sums, O, ops);
                 bool keep = !((double)F.lo > gub_prev);
                 if (keep) keep = !tab_mono<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, ops);
@@ -650,8 +644,9 @@ __device__ __forceinline__ bool eval64_tab_child_w(const GbProg& P, const GbPool
     const View<double> X = view64(pool, par, c, sp);
     const MidView MX{X};
     const size_t rowbase = (size_t)c.p * Tb.max_rows, nbase = (size_t)c.p * Tb.tree_nodes;
+    const size_t sbase = (size_t)c.p * Tb.max_srows;
     iv64 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];
-    int dt = SP.dterm0;
+    int dt = SP.seg0;
     for (int k = 0; k < P.n_sum; k++) {
         const GbSum S = P.sums[k];
         const int2 dr = P.dirty[blk * P.n_sum + k];
@@ -660,9 +655,9 @@ __device__ __forceinline__ bool eval64_tab_child_w(const GbProg& P, const GbPool
             iv64 v2[2];
             int cnt;
             warp_group<iv64, 2>(P, SP, k, g, c.r, dt, lane,
-                                [&](const GbDTerm& D, unsigned combo, iv64* v) {
-                                    const double2 a = Tb.tv64[rowbase + D.row + combo];
-                                    const double2 b = Tb.tm64[rowbase + D.row + combo];
+                                [&](const GbSeg& G, int at, iv64* v) {
+                                    const double2 a = G.level ? Tb.ts64[sbase + at] : Tb.tv64[rowbase + at];
+                                    const double2 b = G.level ? Tb.tsm64[sbase + at] : Tb.tm64[rowbase + at];
                                     v[0] = iv64{a.x, a.y};
                                     v[1] = iv64{b.x, b.y};
                                 }, v2, cnt);
@@ -737,8 +732,9 @@ __device__ __forceinline__ int eval32_tab_child_w(const GbProg& P, const GbPool&
     const View<float> X = view32(pool, par, c, sp);
     const View<double> X64 = view64(pool, par, c, sp);
     const size_t rowbase = (size_t)c.p * Tb.max_rows, nbase = (size_t)c.p * Tb.tree_nodes;
+    const size_t sbase = (size_t)c.p * Tb.max_srows;
     iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
-    int dt = SP.dterm0;
+    int dt = SP.seg0;
     for (int k = 0; k < P.n_sum; k++) {
         const GbSum S = P.sums[k];
         const int2 dr = P.dirty[blk * P.n_sum + k];
@@ -746,8 +742,8 @@ __device__ __forceinline__ int eval32_tab_child_w(const GbProg& P, const GbPool&
         for (int g = dr.x; g < dr.y; g++) {
             int cnt;
             warp_group<iv32, 1>(P, SP, k, g, c.r, dt, lane,
-                                [&](const GbDTerm& D, unsigned combo, iv32* v) {
-                                    const float2 a = Tb.tv32[rowbase + D.row + combo];
+                                [&](const GbSeg& G, int at, iv32* v) {
+                                    const float2 a = G.level ? Tb.ts32[sbase + at] : Tb.tv32[rowbase + at];
                                     v[0] = iv32{a.x, a.y};
                                 }, cur + (g - dr.x), cnt);
             red += 2 * (cnt > 0 ? cnt - 1 : 0);
@@ -856,7 +852,7 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
 
 cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                              long long K, int B, GbState* st, cudaStream_t s) {
-    const int items = B * P.n_sum << GB_TAB_DBITS;
+    const int items = (B * P.n_sum << GB_TAB_DBITS) + (P.max_nseg << GB_TAB_SBITS);
     k_ptab_d<<<dim3((unsigned)grid_for(items, 128), (unsigned)K), 128, 0, s>>>(P, pool, par, T, st);
     return cudaGetLastError();
 }

@@ -79,7 +79,10 @@ struct GbTabs {
     float2* nf32;     // FP32
     double2* td64;    // per (coordinate, sum) sums of leaf adjoints by digit combination
     float2* td32;     // FP32
-    int max_rows, max_leaves, tree_nodes, max_drows;
+    double2* ts64;    // term-tree segment sums by digit combination: F
+    double2* tsm64;   // midpoint
+    float2* ts32;     // FP32
+    int max_rows, max_leaves, tree_nodes, max_drows, max_srows;
     int warp;         // child kernels: 1 one child per warp, 0 one child per thread
 };
 
