@@ -48,9 +48,9 @@ def build(force: bool = False) -> str:
 class _Opts(ctypes.Structure):
     _fields_ = [("tol_f", ctypes.c_double), ("tol_x", ctypes.c_double),
                 ("split_m", ctypes.c_int32), ("split_d", ctypes.c_int32),
-                ("fp32", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("fp32", ctypes.c_int32), ("samples", ctypes.c_int32),
                 ("max_gen", ctypes.c_int64), ("max_parents", ctypes.c_int64),
-                ("cap", ctypes.c_int64)]
+                ("cap", ctypes.c_int64), ("mono_all", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 _P64 = ctypes.POINTER(ctypes.c_int64)
@@ -172,10 +172,14 @@ class Oracle:
 
     def solve(self, tol_f: float | None = None, tol_x: float = 0.0, split_m: int = 2,
               split_d: int = 1, fp32: bool = False, max_gen: int = 10**9,
-              max_parents: int = 1 << 20, cap: int = 1 << 40) -> SolveResult:
+              max_parents: int = 1 << 20, cap: int = 1 << 40, samples: int = 0,
+              mono_all: bool = False) -> SolveResult:
+        """samples: 0 one midpoint sample per box, S > 0 the S interior diagonal
+        points j / (S + 1); mono_all: first-order test on every coordinate
+        (the paper's rule) instead of the active block."""
         o = _Opts(tol_f=float(self.p.tol_f if tol_f is None else tol_f), tol_x=float(tol_x),
-                  split_m=split_m, split_d=split_d, fp32=int(fp32), pad=0,
-                  max_gen=max_gen, max_parents=max_parents, cap=cap)
+                  split_m=split_m, split_d=split_d, fp32=int(fp32), samples=int(samples),
+                  max_gen=max_gen, max_parents=max_parents, cap=cap, mono_all=int(mono_all), pad=0)
         r = _Result()
         lib().oracle_solve(self.h, ctypes.byref(o), ctypes.byref(r))
         try:

@@ -782,8 +782,9 @@ int oracle_tree_sum(const double* lo, const double* hi, int m, int p, double* ou
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double tol_f, tol_x;
-    int32_t split_m, split_d, fp32, pad;
+    int32_t split_m, split_d, fp32, samples;   /* samples: 0 midpoint, S > 0 diagonal points */
     int64_t max_gen, max_parents, cap;
+    int32_t mono_all, pad;                     /* mono_all: first-order test on every coordinate */
 } oopts;
 
 typedef struct {
@@ -853,6 +854,49 @@ static double split_bound(double lo, double hi, int m, int t) {
     return r;
 }
 
+/* GUB samples of a box (section 3.1 lets the sampling be chosen; the paper
+ * samples points on the diagonal, section 4).  S = 0: the midpoint; S > 0:
+ * the S interior points of the (S + 1)-piece partition of every coordinate
+ * taken at the same index j = 1 .. S (the box's diagonal), each coordinate
+ * rounded like a split boundary.  Returns the smallest upper end of F at the
+ * samples (+inf if none is a number); *count receives the samples taken. */
+static double sample_gub(oprob* P, const double* lo, const double* hi, int S, double* pt, int64_t* count) {
+    const int n = P->n;
+    double best = INFINITY;
+    if (S <= 0) {
+        for (int j = 0; j < n; j++) pt[j] = midpoint(lo[j], hi[j]);
+        obox M = {pt, pt};
+        double v = eval_outer(P, M, 0).hi;
+        if (v < best) best = v;
+        *count += 1;
+        return best;
+    }
+    for (int t = 1; t <= S; t++) {
+        for (int j = 0; j < n; j++) pt[j] = split_bound(lo[j], hi[j], S + 1, t);
+        obox M = {pt, pt};
+        double v = eval_outer(P, M, 0).hi;
+        if (v < best) best = v;
+    }
+    *count += S;
+    return best;
+}
+
+/* First-order test of the box: on the active block, or (mono_all, the
+ * paper's rule of section 3.1) on every coordinate. */
+static int mono_box(oprob* P, obox X, int p, int blk, iv* G, int mono_all) {
+    int width;
+    if (!mono_all) {
+        block_partials(P, X, p, blk, G, &width);
+        return mono_test(P, X, blk, G, width);
+    }
+    const int nb = (P->n + P->B - 1) / P->B;
+    for (int b = 0; b < nb; b++) {
+        block_partials(P, X, p, b, G, &width);
+        if (mono_test(P, X, b, G, width)) return 1;
+    }
+    return 0;
+}
+
 int oracle_solve(void* h, const oopts* opt, oresult* R) {
     oprob* P = (oprob*)h;
     memset(R, 0, sizeof(*R));
@@ -878,11 +922,9 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
     root.flo = canon_lo(f0.lo);
     root.cyc = 0;
     root.fin = 0;
-    for (int j = 0; j < n; j++) mid[j] = midpoint(root.lo[j], root.hi[j]);
-    obox M0 = {mid, mid};
-    double gub = eval_outer(P, M0, 0).hi;
+    R->evals64 = 1;
+    double gub = sample_gub(P, root.lo, root.hi, opt->samples, mid, &R->mids);
     if (isnan(gub)) gub = INFINITY;
-    R->evals64 = 1; R->mids = 1;
     el_push(&pool, root);
     int status = ST_OK;
     int64_t gen = 0;
@@ -978,9 +1020,7 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
                 entry* ch = &kids.e[q];
                 obox X = {ch->lo, ch->hi};
                 iv f = eval_outer(P, X, 1);
-                int width;
-                block_partials(P, X, 1, ch->blk, G, &width);
-                int mono = mono_test(P, X, ch->blk, G, width);
+                int mono = mono_box(P, X, 1, ch->blk, G, opt->mono_all);
                 cand[q] = !(f.lo > gub_prev) && !mono;
                 kept32 += cand[q];
             }
@@ -991,11 +1031,8 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
         for (int64_t q = 0; q < kids.len; q++) {
             if (!cand[q]) continue;
             entry* ch = &kids.e[q];
-            for (int j = 0; j < n; j++) mid[j] = midpoint(ch->lo[j], ch->hi[j]);
-            obox M = {mid, mid};
-            double fm = eval_outer(P, M, 0).hi;
+            double fm = sample_gub(P, ch->lo, ch->hi, opt->samples, mid, &R->mids);
             if (fm < gub_new) gub_new = fm;
-            R->mids++;
         }
         keep.len = 0;
         int64_t kept = 0;
@@ -1006,9 +1043,7 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
                 obox X = {ch->lo, ch->hi};
                 iv f = eval_outer(P, X, 0);
                 R->evals64++;
-                int width;
-                block_partials(P, X, 0, ch->blk, G, &width);
-                int mono = mono_test(P, X, ch->blk, G, width);
+                int mono = mono_box(P, X, 0, ch->blk, G, opt->mono_all);
                 ok = !(f.lo > gub_new) && !mono;
                 ch->flo = canon_lo(f.lo);
             }

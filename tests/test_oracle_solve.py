@@ -55,6 +55,66 @@ def test_paper_mode_iteration_counts(fam):
         assert _covers(res, np.zeros(n))
 
 
+@pytest.mark.parametrize("fam", ["paper_rastrigin", "paper_breiman"])
+def test_full_paper_procedure_iteration_counts(fam):
+    # the paper's procedure in full: 10 diagonal samples per region and the
+    # first-order test on every coordinate (section 3.1, section 4), besides
+    # the 4-way split of a block, one region per iteration and tol_x = 1e-4
+    rows = [r for r in _golden_rows() if r[0] == fam]
+    per_block = rows[0][2] * 10 // rows[0][1]
+    for n, B in ((5, 5), (10, 5)):
+        p = S.make(fam, n=n, block=B)
+        res = O.Oracle(p, block=B).solve(tol_f=0.0, tol_x=1e-4, split_m=4, split_d=B, max_parents=1,
+                                         samples=10, mono_all=True)
+        assert res.status == O.ST_OK
+        assert res.generations == (n // B) * per_block
+        assert len(res.box_flo) == 1 == rows[0][3]
+        fstar = 0.0 if fam == "paper_rastrigin" else -0.1 * n
+        assert res.glb <= fstar <= res.gub
+        assert _covers(res, np.zeros(n))
+
+
+def _diag_quadratic(n, s):
+    """f(x) = sum_i (x_i - s_i)^2 on [0, 11]^n (closed form: min 0 at s)."""
+    g = S.Dag()
+    ts = g.table(np.asarray(s, dtype=np.float64))
+    y = g.sub(g.ivar(0), g.icoef(ts))
+    f = g.isum(g.sqr(y), 0, n, 1)
+    return S.Problem("quad", n, g.nodes(), f, g.tables, np.zeros(n), np.full(n, 11.0), 1e-9, n,
+                     np.asarray(s, dtype=np.float64), 0)
+
+
+def test_diagonal_samples_hit_a_minimiser_on_the_diagonal():
+    # the interior diagonal points of [0, 11]^n at j / 11 are (j, ..., j)
+    # exactly; with the minimiser at (5, ..., 5) the root's samples already
+    # give GUB = f(s) = 0, while the midpoint (5.5, ...) gives n / 4
+    n = 3
+    p = _diag_quadratic(n, [5.0] * n)
+    o = O.Oracle(p, block=n)
+    paper = o.solve(tol_f=1e-9, split_m=2, split_d=n, samples=10, max_gen=1)
+    mid = o.solve(tol_f=1e-9, split_m=2, split_d=n, samples=0, max_gen=1)
+    # the root's samples close the enclosure at once: no region is active
+    assert paper.status == O.ST_OK and paper.generations == 0 and paper.mids == 10
+    assert paper.gub == 0.0 and paper.glb == 0.0
+    assert mid.trace["gub"][0] > 0.0
+    # off the diagonal the samples only give an upper bound above the minimum
+    q = _diag_quadratic(n, [5.0, 3.0, 5.0])
+    r = O.Oracle(q, block=n).solve(tol_f=1e-9, split_m=2, split_d=n, samples=10, max_gen=1)
+    assert r.trace["gub"][0] > 0.0
+
+
+def test_mono_all_discards_at_least_as_much():
+    # testing every coordinate can only rule out more regions than testing
+    # the active block: same enclosure, never more boxes
+    p = S.chain(n=8, seed=3)
+    o = O.Oracle(p, block=4)
+    a = o.solve(split_m=2, split_d=4, max_parents=4)
+    b = o.solve(split_m=2, split_d=4, max_parents=4, mono_all=True)
+    assert a.status == b.status == O.ST_OK
+    assert b.glb <= 0.0 <= b.gub and b.gub - b.glb <= p.tol_f
+    assert b.evals64 <= a.evals64 * 2
+
+
 CASES = [("sep_cos", dict(n=2), dict(split_m=2, split_d=1)),
          ("sep_cos", dict(n=3, tol_f=1e-6), dict(split_m=4, split_d=3)),
          ("chain", dict(n=6, block=3), dict(split_m=2, split_d=3)),
