@@ -103,9 +103,14 @@ typedef struct gb_options {
                                  child replaces at most a quarter of the blocks), 1 one dense row of n
                                  coordinates per box, 2 block records shared between a box and its
                                  children; results are identical */
-    int32_t pad;
+    int32_t samples;          /* GUB samples per box: 0 the midpoint; S in 1..64 the S interior points
+                                 j / (S + 1) of its diagonal (the paper takes 10, section 4); S > 0 needs
+                                 eval_mode 0 or 1 (bytecode interpreter) */
     int64_t max_records;      /* block records: record capacity (0: 4 * nrec * boxes + blocks, nrec = blocks
                                  a child replaces); unreferenced records are collected when new ones do not fit */
+    int32_t mono_all;         /* 1: first-order test on every coordinate (the paper's rule, section 3.1)
+                                 instead of the active block; needs eval_mode 0 or 1 */
+    int32_t pad;
 } gb_options;
 
 /* Fills *opt with the defaults documented above. */

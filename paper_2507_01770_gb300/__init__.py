@@ -38,7 +38,8 @@ class gb_options(ctypes.Structure):
                 ("max_boxes", ctypes.c_int64), ("pool_bytes", ctypes.c_size_t),
                 ("device", ctypes.c_int32), ("eval_mode", ctypes.c_int32),
                 ("gens_per_sync", ctypes.c_int32), ("pool_mode", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("max_records", ctypes.c_int64)]
+                ("samples", ctypes.c_int32), ("max_records", ctypes.c_int64),
+                ("mono_all", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class gb_gen_stat(ctypes.Structure):

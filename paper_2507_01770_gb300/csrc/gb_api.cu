@@ -182,6 +182,11 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     if (opt.block > n) return fail(GB_E_INVALID, "block size larger than n");
     if (opt.pool_mode < 0 || opt.pool_mode > 2) return fail(GB_E_INVALID, "pool_mode must be 0, 1 or 2");
     if (opt.eval_mode < 0 || opt.eval_mode > 4) return fail(GB_E_INVALID, "eval_mode must be 0 .. 4");
+    if (opt.samples < 0 || opt.samples > 64) return fail(GB_E_INVALID, "samples must be 0 .. 64");
+    if (opt.samples > 0 || opt.mono_all) {   // paper mode: full evaluations in the interpreter
+        if (opt.eval_mode >= 2) return fail(GB_E_INVALID, "samples > 0 and mono_all need eval_mode 0 or 1");
+        opt.eval_mode = 1;
+    }
     if (opt.max_records < 0) return fail(GB_E_INVALID, "max_records must be >= 0");
     if (opt.split_m != 2 && opt.split_m != 4) return fail(GB_E_INVALID, "split_m must be 2 or 4");
     const int mshift = opt.split_m == 2 ? 1 : 2;
@@ -259,6 +264,8 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     P.outer_root = H.outer_root;
     P.n_var_leaves = (int)H.var_leaves.size();
     P.outer_sum = (H.outer.size() == 1 && H.outer[0].op == D_ISUMV && H.outer_root == 0) ? 1 : 0;
+    P.samples = opt.samples;
+    P.mono_all = opt.mono_all ? 1 : 0;
     GbIns *d_outer, *d_tins;
     GbSum* d_sums;
     GbGroup* d_groups;

@@ -100,6 +100,22 @@ struct MidView {
     }
 };
 
+// Diagonal sample point j of S: coordinate i is boundary j of the (S + 1)-piece
+// partition of [lo_i, hi_i], RN(lo + RN(RN(RN(hi - lo) / (S + 1)) * j)) (the
+// split-boundary rounding), j in 1 .. S.
+struct SampleView {
+    View<double> v;
+    int j, m1;
+    __device__ __forceinline__ iv64 get(int i) const {
+        const iv64 x = v.get(i);
+        const double w = __dsub_rn(x.hi, x.lo);
+        const double q = __ddiv_rn(w, (double)m1);
+        const double s = __dmul_rn(q, (double)j);
+        const double p = __dadd_rn(x.lo, s);
+        return iv64{p, p};
+    }
+};
+
 // Binary-counter pairwise tree.
 template <typename I> struct Tree {
     I lvl[20];

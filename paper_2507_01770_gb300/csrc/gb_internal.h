@@ -156,6 +156,8 @@ struct GbProg {
     const GbSeg* segs;               // term-tree segments of every split position
     int32_t max_srows, max_nseg;
     int32_t outer_sum;               // 1: the outer expression is one sum (F = that sum, adjoint [1, 1])
+    int32_t samples;                 // GUB samples per box (0: midpoint; S: diagonal points j / (S + 1))
+    int32_t mono_all;                // first-order test on every coordinate
 };
 
 // Host-side compiled program (arrays in host memory before upload).

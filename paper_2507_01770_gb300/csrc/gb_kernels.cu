@@ -112,10 +112,21 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
     const CacheRef<double2> cf = cache64(pool, P, 0, 0), cm = cache64(pool, P, 0, 1);
     sum_values<double>(P, -1, X, &cf, R, sums, ops);
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
-    sum_values<double>(P, -1, MX, &cm, R, sums, ops);
-    iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
-    double gub = Fm.hi;
-    if (gub != gub) gub = __longlong_as_double(0x7ff0000000000000LL);
+    double gub = __longlong_as_double(0x7ff0000000000000LL);
+    long long nsamp = 1;
+    if (P.samples > 0) {   // diagonal samples of the domain
+        nsamp = P.samples;
+        for (int j = 1; j <= P.samples; j++) {
+            const SampleView SV{X, j, P.samples + 1};
+            sum_values<double>(P, -1, SV, (const CacheRef<double2>*)nullptr, R, sums, ops);
+            const iv64 Fs = outer_fwd<double>(P, SV, sums, O, ops);
+            if (Fs.hi < gub) gub = Fs.hi;
+        }
+    } else {
+        sum_values<double>(P, -1, MX, &cm, R, sums, ops);
+        const iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
+        if (Fm.hi == Fm.hi) gub = Fm.hi;
+    }
     E.flo[0] = canon_lo(F.lo);
     E.slot[0] = 0;
     E.cyc[0] = 0;
@@ -129,7 +140,7 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
     s0.sel_T = ~0ull;
     s0.min_key = ~0ull;
     s0.evals64 = 1;
-    s0.mids = 1;
+    s0.mids = nsamp;
     s0.rec_bump = pool.recs ? pool.nb : 0;
     *st = s0;
 }
@@ -491,6 +502,17 @@ __global__ void k_prep(GbProg P, GbPool pool, GbParents par, GbSplit sp, GbState
 }
 
 // FP64 child evaluation: midpoint sample, F(X), first-order test.
+// First-order test: the active block, or every block (mono_all).
+template <typename T, typename V>
+__device__ __forceinline__ bool mono_any(const GbProg& P, int blk, const V& X, const View<double>& X64,
+                                         const typename Prec<T>::I* O, typename Prec<T>::I* OA,
+                                         typename Prec<T>::I* R, typename Prec<T>::I* RA, int& ops) {
+    if (!P.mono_all) return block_mono<T>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr, ops);
+    for (int b = 0; b < P.nb; b++)
+        if (block_mono<T>(P, b, X, X64, O, OA, R, RA, (double*)nullptr, ops)) return true;
+    return false;
+}
+
 __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool, const GbParents& par,
                                              const GbChildren& ch, long long ci, const GbSplit& sp,
                                              double gub_prev, unsigned long long* gkey, bool* has_key,
@@ -506,16 +528,29 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
     iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
     const int blk = c.info.z;
     const CacheRef<double2> cm = cache64(pool, P, c.slot, 1), cf = cache64(pool, P, c.slot, 0);
-    sum_values<double>(P, blk, MX, &cm, R, sums, ops);
-    iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
-    if (Fm.hi == Fm.hi) {
-        *gkey = gb_order_key(Fm.hi);
-        *has_key = true;
+    if (P.samples > 0) {   // diagonal samples, each evaluated in full
+        for (int j = 1; j <= P.samples; j++) {
+            const SampleView SV{X, j, P.samples + 1};
+            sum_values<double>(P, blk, SV, (const CacheRef<double2>*)nullptr, R, sums, ops);
+            const iv64 Fs = outer_fwd<double>(P, SV, sums, O, ops);
+            if (Fs.hi == Fs.hi) {
+                const unsigned long long k = gb_order_key(Fs.hi);
+                if (!*has_key || k < *gkey) *gkey = k;
+                *has_key = true;
+            }
+        }
+    } else {
+        sum_values<double>(P, blk, MX, &cm, R, sums, ops);
+        iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
+        if (Fm.hi == Fm.hi) {
+            *gkey = gb_order_key(Fm.hi);
+            *has_key = true;
+        }
     }
     sum_values<double>(P, blk, X, &cf, R, sums, ops);
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
     bool keep = !(F.lo > gub_prev);
-    if (keep) keep = !block_mono<double>(P, blk, X, X, O, OA, R, RA, (double*)nullptr, ops);
+    if (keep) keep = !mono_any<double>(P, blk, X, X, O, OA, R, RA, ops);
     ch.flo[ci] = canon_lo(F.lo);
     ch.flag[ci] = keep ? 1 : 0;
     return true;
@@ -543,7 +578,7 @@ __global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents
         unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
         if ((threadIdx.x & 31) == 0 && nv) {
             atomicAdd((unsigned long long*)&st->evals64, (unsigned long long)nv);
-            atomicAdd((unsigned long long*)&st->mids, (unsigned long long)nv);
+            atomicAdd((unsigned long long*)&st->mids, (unsigned long long)nv * (P.samples > 0 ? P.samples : 1));
             if (!from_list) atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
         }
     }
@@ -575,7 +610,7 @@ __global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents
                 sum_values<float>(P, blk, X, &c32, R, sums, ops);
                 iv32 F = outer_fwd<float>(P, X, sums, O, ops);
                 bool keep = !((double)F.lo > gub_prev);
-                if (keep) keep = !block_mono<float>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr, ops);
+                if (keep) keep = !mono_any<float>(P, blk, X, X64, O, OA, R, RA, ops);
                 ch.flag32[ci] = keep ? 1 : 0;
             } else {
                 ch.flag32[ci] = 0;

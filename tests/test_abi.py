@@ -63,6 +63,13 @@ def test_invalid_problems_rejected_without_gpu():
     with pytest.raises(gb.GbError) as e:
         gb.gb_create_problem(p.nodes, p.root, p.tables, p.n, p.u, p.l, 1e-6)
     assert e.value.status == gb.GB_E_INVALID
+    with pytest.raises(gb.GbError) as e:   # diagonal samples run in the interpreter only
+        gb.gb_create_problem(p.nodes, p.root, p.tables, p.n, p.l, p.u, 1e-6,
+                             gb.gb_default_options(samples=10, eval_mode=2))
+    assert e.value.status == gb.GB_E_INVALID
+    with pytest.raises(gb.GbError) as e:
+        gb.gb_create_problem(p.nodes, p.root, p.tables, p.n, p.l, p.u, 1e-6, gb.gb_default_options(samples=65))
+    assert e.value.status == gb.GB_E_INVALID
     with pytest.raises(gb.GbError) as e:   # split_m must be 2 or 4
         gb.gb_create_problem(p.nodes, p.root, p.tables, p.n, p.l, p.u, 1e-6,
                              gb.gb_default_options(split_m=3))

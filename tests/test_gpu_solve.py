@@ -27,10 +27,11 @@ def _covers(lo, hi, x):
     return bool(np.any(np.all((lo <= x) & (x <= hi), axis=1)))
 
 
-def _run_both(p, B, m, d, K, fp32=False, tol_x=0.0, tol_f=None, max_gen=10**9, cap=None):
+def _run_both(p, B, m, d, K, fp32=False, tol_x=0.0, tol_f=None, max_gen=10**9, cap=None, samples=0,
+              mono_all=False):
     tol = p.tol_f if tol_f is None else tol_f
     opts = dict(block=B, split_m=m, split_d=d, max_children=K * m ** d, fp32_prefilter=int(fp32),
-                tol_x=tol_x, max_generations=max_gen)
+                tol_x=tol_x, max_generations=max_gen, samples=samples, mono_all=int(mono_all))
     if tol_f is not None:
         opts["tol_f"] = tol_f if tol_f > 0 else 0.0
     if cap is not None:
@@ -39,7 +40,8 @@ def _run_both(p, B, m, d, K, fp32=False, tol_x=0.0, tol_f=None, max_gen=10**9, c
     g = s.solve(raise_on_error=False)
     s.close()
     o = O.Oracle(p, block=B).solve(tol_f=tol, tol_x=tol_x, split_m=m, split_d=d, fp32=fp32,
-                                   max_parents=K, max_gen=max_gen, cap=cap if cap else 1 << 40)
+                                   max_parents=K, max_gen=max_gen, cap=cap if cap else 1 << 40,
+                                   samples=samples, mono_all=mono_all)
     return g, o
 
 
@@ -88,6 +90,29 @@ def test_paper_mode_rastrigin_iterations():
     assert g.generations == o.generations == 9 and g.n_boxes == 1
     assert g.fmin_lo <= 0.0 <= g.fmin_hi
     assert np.array_equal(g.trace["kept"], o.trace["kept"])
+
+
+@pytest.mark.parametrize("fam,per_block", [("paper_rastrigin", 9), ("paper_breiman", 8)])
+def test_full_paper_procedure_on_the_gpu(fam, per_block):
+    # 4-way split of a block, one region per generation, 10 diagonal samples,
+    # first-order test on every coordinate, tol_x = 1e-4 (sections 3.1, 4)
+    p = S.make(fam, n=10, block=5)
+    g, o = _run_both(p, 5, 4, 5, 1, tol_x=1e-4, tol_f=0.0, samples=10, mono_all=True)
+    assert g.status == o.status == 0
+    assert g.generations == o.generations == 2 * per_block and g.n_boxes == 1
+    fstar = 0.0 if fam == "paper_rastrigin" else -1.0
+    assert g.fmin_lo <= fstar <= g.fmin_hi
+    assert np.array_equal(g.trace["kept"], o.trace["kept"])
+    assert g.mid_evals == o.mids
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("samples,mono_all", [(10, True), (3, False), (0, True)])
+def test_paper_mode_chain_parity(fp32, samples, mono_all):
+    p = S.chain(n=12, seed=5)
+    g, o = _run_both(p, 6, 2, 3, 8, fp32=fp32, samples=samples, mono_all=mono_all)
+    _assert_identical(g, o)
+    assert g.mid_evals == o.mids
 
 
 @pytest.mark.parametrize("fam,kw,B,m,d,K", [
