@@ -234,4 +234,87 @@ def paper_breiman(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> 
                    block if block else min(n, 10), np.zeros(n), 0)
 
 
-FAMILIES.update(paper_rastrigin=paper_rastrigin, paper_breiman=paper_breiman)
+def paper_ackley(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S1-S2 as printed: -20 exp(-0.02 sqrt(mean x_i^2)) - exp(mean cos(2 pi x_i)) + 20 + e,
+    -35 <= x_i <= 40; min 0 at x = 0."""
+    g = Dag()
+    x = g.ivar(0)
+    s1 = g.isum(g.sqr(x), 0, n, 1)
+    s2 = g.isum(g.cos(g.mul(g.scale(g.pi(), 2.0), x)), 0, n, 1)
+    nn = g.const(float(n))
+    a_part = g.scale(g.exp(g.scale(g.sqrt(g.div(s1, nn)), -0.02)), -20.0)
+    c_part = g.neg(g.exp(g.div(s2, nn)))
+    f = g.add(g.add(a_part, c_part), g.add(g.const(20.0), g.euler()))
+    return Problem("paper_ackley", n, g.nodes(), f, g.tables, np.full(n, -35.0), np.full(n, 40.0), tol_f,
+                   block if block else min(n, 10), np.zeros(n), 0, meta=dict(fstar=0.0))
+
+
+def paper_belegundu(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S3-S4: 0.1 sum (x_i - 5)^2 - cos(5 sqrt(sum (x_i - 5)^2)), -10 <= x_i <= 11; min -1 at x = 5."""
+    g = Dag()
+    d = g.sub(g.ivar(0), g.const(5.0))
+    s1 = g.isum(g.sqr(d), 0, n, 1)
+    f = g.sub(g.scale(s1, 0.1), g.cos(g.scale(g.sqrt(s1), 5.0)))
+    return Problem("paper_belegundu", n, g.nodes(), f, g.tables, np.full(n, -10.0), np.full(n, 11.0), tol_f,
+                   block if block else min(n, 10), np.full(n, 5.0), 0, meta=dict(fstar=-1.0))
+
+
+def paper_fu(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S7-S8: 1 + sum [8 sin^2(7 (x_i - 0.9)^2) + 6 sin^2(14 (x_i - 0.9)^2) + (x_i - 0.9)^2],
+    -10 <= x_i <= 10; min 1 at x = 0.9."""
+    g = Dag()
+    q = g.sqr(g.sub(g.ivar(0), g.const(0.9)))
+    term = g.add(g.add(g.scale(g.sqr(g.sin(g.scale(q, 7.0))), 8.0), g.scale(g.sqr(g.sin(g.scale(q, 14.0))), 6.0)),
+                 q)
+    f = g.add(g.const(1.0), g.isum(term, 0, n, 1))
+    return Problem("paper_fu", n, g.nodes(), f, g.tables, np.full(n, -10.0), np.full(n, 10.0), tol_f,
+                   block if block else min(n, 10), np.full(n, 0.9), 0, meta=dict(fstar=1.0))
+
+
+def paper_levy(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S11-S13 with y_i = 1 + 0.25 (x_i - 1) (so y_i - 1 = 0.25 (x_i - 1)):
+    (pi / n) {10 sin^2(pi y_1) + (y_n - 1)^2 + sum_{i<n} (y_i - 1)^2 (1 + 10 sin^2(pi y_{i+1}))},
+    -10 <= x_i <= 10; min 0 at x = 1."""
+    if n < 2:
+        raise ValueError("paper_levy needs n >= 2")
+    g = Dag()
+
+    def y(node):          # y = 1 + 0.25 (x - 1)
+        return g.add(g.const(1.0), g.scale(g.sub(node, g.const(1.0)), 0.25))
+
+    def ym1_sq(node):     # (y - 1)^2 = (0.25 (x - 1))^2
+        return g.sqr(g.scale(g.sub(node, g.const(1.0)), 0.25))
+
+    def sin2_pi(node):    # sin^2(pi y)
+        return g.sqr(g.sin(g.mul(g.pi(), y(node))))
+
+    term = g.mul(ym1_sq(g.ivar(0)), g.add(g.const(1.0), g.scale(sin2_pi(g.ivar(1)), 10.0)))
+    inner = g.add(g.add(g.scale(sin2_pi(g.var(0)), 10.0), ym1_sq(g.var(n - 1))), g.isum(term, 0, n - 1, 1))
+    f = g.div(g.mul(g.pi(), inner), g.const(float(n)))
+    return Problem("paper_levy", n, g.nodes(), f, g.tables, np.full(n, -10.0), np.full(n, 10.0), tol_f,
+                   block if block else min(n, 10), np.ones(n), 0, meta=dict(fstar=0.0))
+
+
+def paper_salomon(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S16-S17: 1 - cos(2 pi sqrt(sum x_i^2)) + 0.1 sqrt(sum x_i^2), -100 <= x_i <= 110; min 0 at x = 0."""
+    g = Dag()
+    r = g.sqrt(g.isum(g.sqr(g.ivar(0)), 0, n, 1))
+    f = g.add(g.sub(g.const(1.0), g.cos(g.mul(g.scale(g.pi(), 2.0), r))), g.scale(r, 0.1))
+    return Problem("paper_salomon", n, g.nodes(), f, g.tables, np.full(n, -100.0), np.full(n, 110.0), tol_f,
+                   block if block else min(n, 10), np.zeros(n), 0, meta=dict(fstar=0.0))
+
+
+def paper_rosenbrock(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S22-S23: sum_{i<n} [100 (x_i^2 - x_{i+1})^2 + (x_i - 1)^2], -30 <= x_i <= 30; min 0 at x = 1."""
+    if n < 2:
+        raise ValueError("paper_rosenbrock needs n >= 2")
+    g = Dag()
+    term = g.add(g.scale(g.sqr(g.sub(g.sqr(g.ivar(0)), g.ivar(1))), 100.0), g.sqr(g.sub(g.ivar(0), g.const(1.0))))
+    f = g.isum(term, 0, n - 1, 1)
+    return Problem("paper_rosenbrock", n, g.nodes(), f, g.tables, np.full(n, -30.0), np.full(n, 30.0), tol_f,
+                   block if block else min(n, 10), np.ones(n), 0, meta=dict(fstar=0.0))
+
+
+FAMILIES.update(paper_rastrigin=paper_rastrigin, paper_breiman=paper_breiman, paper_ackley=paper_ackley,
+                paper_belegundu=paper_belegundu, paper_fu=paper_fu, paper_levy=paper_levy,
+                paper_salomon=paper_salomon, paper_rosenbrock=paper_rosenbrock)

@@ -92,7 +92,16 @@ def test_paper_mode_rastrigin_iterations():
     assert np.array_equal(g.trace["kept"], o.trace["kept"])
 
 
-@pytest.mark.parametrize("fam,per_block", [("paper_rastrigin", 9), ("paper_breiman", 8)])
+# per-block iteration counts printed by the paper (Tables 2, S2-S5, S7, S8)
+PAPER_PER_BLOCK = [("paper_rastrigin", 9), ("paper_breiman", 8), ("paper_ackley", 10), ("paper_belegundu", 9),
+                   ("paper_fu", 9), ("paper_levy", 9), ("paper_salomon", 11)]
+
+
+def _fstar(p):
+    return p.meta.get("fstar", -0.1 * p.n if p.family == "paper_breiman" else 0.0)
+
+
+@pytest.mark.parametrize("fam,per_block", PAPER_PER_BLOCK)
 def test_full_paper_procedure_on_the_gpu(fam, per_block):
     # 4-way split of a block, one region per generation, 10 diagonal samples,
     # first-order test on every coordinate, tol_x = 1e-4 (sections 3.1, 4)
@@ -100,10 +109,29 @@ def test_full_paper_procedure_on_the_gpu(fam, per_block):
     g, o = _run_both(p, 5, 4, 5, 1, tol_x=1e-4, tol_f=0.0, samples=10, mono_all=True)
     assert g.status == o.status == 0
     assert g.generations == o.generations == 2 * per_block and g.n_boxes == 1
-    fstar = 0.0 if fam == "paper_rastrigin" else -1.0
-    assert g.fmin_lo <= fstar <= g.fmin_hi
+    assert g.fmin_lo <= _fstar(p) <= g.fmin_hi
     assert np.array_equal(g.trace["kept"], o.trace["kept"])
     assert g.mid_evals == o.mids
+
+
+@pytest.mark.parametrize("fam,per_block", PAPER_PER_BLOCK)
+def test_paper_functions_table_path(fam, per_block):
+    # the default path (per-parent tables, midpoint sample, block test) on the
+    # paper's partition also takes the printed number of generations
+    p = S.make(fam, n=10, block=5)
+    s = gb.Solver(p, block=5, split_m=4, split_d=5, max_children=1024, tol_x=1e-4, tol_f=0.0)
+    g = s.solve()
+    s.close()
+    assert g.status == 0 and g.generations == 2 * per_block and g.n_boxes == 1
+    assert g.fmin_lo <= _fstar(p) <= g.fmin_hi
+    assert _covers(g.box_lo, g.box_hi, p.s)
+
+
+def test_paper_rosenbrock_parity():
+    p = S.paper_rosenbrock(n=6, block=3)
+    g, o = _run_both(p, 3, 2, 3, 8, tol_f=1e-6)
+    _assert_identical(g, o)
+    assert g.fmin_lo <= 0.0 <= g.fmin_hi
 
 
 @pytest.mark.parametrize("fp32", [False, True])

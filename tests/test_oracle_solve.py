@@ -36,7 +36,15 @@ def _covers(res, x):
     return bool(inside.any())
 
 
-@pytest.mark.parametrize("fam", ["paper_rastrigin", "paper_breiman"])
+PAPER_FAMILIES = ["paper_rastrigin", "paper_breiman", "paper_ackley", "paper_belegundu", "paper_fu",
+                  "paper_levy", "paper_salomon"]
+
+
+def _fstar(p):
+    return p.meta.get("fstar", -0.1 * p.n if p.family == "paper_breiman" else 0.0)   # SI Appendix A
+
+
+@pytest.mark.parametrize("fam", PAPER_FAMILIES)
 def test_paper_mode_iteration_counts(fam):
     rows = [r for r in _golden_rows() if r[0] == fam]
     per_block = {r[2] * 10 // r[1] for r in rows}
@@ -50,12 +58,11 @@ def test_paper_mode_iteration_counts(fam):
         assert res.generations == (n // B) * per_block
         assert len(res.box_flo) == 1 == rows[0][3]
         assert np.all(res.box_hi - res.box_lo < 1e-4)
-        fstar = 0.0 if fam == "paper_rastrigin" else -0.1 * n   # SI Appendix A
-        assert res.glb <= fstar <= res.gub
-        assert _covers(res, np.zeros(n))
+        assert res.glb <= _fstar(p) <= res.gub
+        assert _covers(res, p.s)
 
 
-@pytest.mark.parametrize("fam", ["paper_rastrigin", "paper_breiman"])
+@pytest.mark.parametrize("fam", PAPER_FAMILIES)
 def test_full_paper_procedure_iteration_counts(fam):
     # the paper's procedure in full: 10 diagonal samples per region and the
     # first-order test on every coordinate (section 3.1, section 4), besides
@@ -69,9 +76,19 @@ def test_full_paper_procedure_iteration_counts(fam):
         assert res.status == O.ST_OK
         assert res.generations == (n // B) * per_block
         assert len(res.box_flo) == 1 == rows[0][3]
-        fstar = 0.0 if fam == "paper_rastrigin" else -0.1 * n
-        assert res.glb <= fstar <= res.gub
-        assert _covers(res, np.zeros(n))
+        assert res.glb <= _fstar(p) <= res.gub
+        assert _covers(res, p.s)
+
+
+@pytest.mark.parametrize("fam", PAPER_FAMILIES + ["paper_rosenbrock"])
+@pytest.mark.parametrize("n", [2, 3])
+def test_paper_functions_enclose_their_printed_minimum(fam, n):
+    # SI Appendix A / D print each function's minimiser and minimum value
+    p = S.make(fam, n=n)
+    res = O.Oracle(p, block=n).solve(tol_f=1e-6, split_m=2, split_d=n, max_parents=16)
+    assert res.status == O.ST_OK
+    assert res.glb <= _fstar(p) <= res.gub and res.gub - res.glb <= 1e-6
+    assert _covers(res, p.s)
 
 
 def _diag_quadratic(n, s):
