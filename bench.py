@@ -18,6 +18,11 @@ mixed10k
   n = 10,000: separable cosine terms on even i, chain terms on odd i, box
   [-5.12, 5.12]^n, width 1e-6, FP32 prefilter + FP64, blocks of 100, 2^10
   children of one box per generation, block-record box pool.
+levy50_paper
+  the paper's own procedure on its Levy function (Eq. S11-S13), n = 50: 4^10
+  children of one region per iteration, 10 diagonal GUB samples, first-order
+  test on every coordinate, region width 1e-4; metric = solve time, compared
+  with the time the paper prints for it (Table 2).
 serving
   512 requests, Poisson arrivals (20/s), n log-uniform on [2, 2000], family
   uniform over sep_cos / chain / ackley, width 1e-6, 150 GB pool budget:
@@ -67,22 +72,28 @@ FP32_OPS_PER_SM_CLK = 128.0  # 128 FP32 lanes per SM (directed add / mul at full
 SMS = 152
 WORKLOADS = {
     "chain100": dict(family="chain", n=100, block=10, split_m=4, split_d=10, max_children=1 << 20, fp32=0,
-                     gens_per_sync=0, pool_gb=16.0, cpu_parents=4, cpu_split_d=10, cpu_gens=20,
+                     gens_per_sync=0, pool_gb=16.0, cpu_parents=4, cpu_split_m=2, cpu_split_d=10, cpu_gens=20,
                      # DRAM bytes (read + write) of one k_eval64_tab launch, ncu capture in
                      # profiles/k_eval64_tab_chain100.md
                      traffic=24.69e6,
                      name="chain n=100 (coupled quartic, planted min 0), FP64, B=10, 4-way split of the 10 "
                           "block coordinates (4^10 children) of 1 best box per generation, tol_f=1e-6"),
     "ackley1000": dict(family="ackley", n=1000, block=10, split_m=2, split_d=10, max_children=1 << 10, fp32=1,
-                       gens_per_sync=16, pool_gb=32.0, cpu_parents=1, cpu_split_d=10, cpu_gens=12,
+                       gens_per_sync=16, pool_gb=32.0, cpu_parents=1, cpu_split_m=2, cpu_split_d=10, cpu_gens=12,
                        name="ackley n=1000 (exp/sqrt/cos mean form + quadratic, planted min 0), FP32 "
                             "prefilter + FP64, B=10, 2-way split of 10 coordinates of 1 best box per generation, "
                             "tol_f=1e-6"),
     "mixed10k": dict(family="mixed", n=10000, block=100, split_m=2, split_d=10, max_children=1 << 10, fp32=1,
-                     gens_per_sync=16, pool_gb=64.0, cpu_parents=1, cpu_split_d=10, cpu_gens=2,
+                     gens_per_sync=16, pool_gb=64.0, cpu_parents=1, cpu_split_m=2, cpu_split_d=10, cpu_gens=2,
                      name="mixed n=10000 (separable cosine terms on even i, chain terms on odd i, planted min 0), "
                           "FP32 prefilter + FP64, B=100, 2-way split of 10 coordinates of 1 best box per "
                           "generation, block-record pool, tol_f=1e-6"),
+    "levy50_paper": dict(family="paper_levy", n=50, block=10, split_m=4, split_d=10, max_children=1 << 20, fp32=0,
+                         gens_per_sync=0, pool_gb=16.0, cpu_parents=1, cpu_split_m=4, cpu_split_d=5, cpu_gens=2,
+                         paper=True, baseline_s=15.0, paper_iters=45,
+                         name="the paper's procedure on Levy n=50 (Eq. S11-S13): 4-way split of the 10 block "
+                              "coordinates (4^10 children) of 1 best region per iteration, 10 diagonal samples, "
+                              "first-order test on every coordinate, region width tolerance 1e-4"),
 }
 
 
@@ -111,6 +122,8 @@ def _workload(a):
 
 
 def _problem(w, seed=0):
+    if w["family"].startswith("paper_"):   # the paper's functions are fixed (no seed)
+        return S.make(w["family"], n=w["n"])
     return S.make(w["family"], n=w["n"], seed=seed)
 
 
@@ -182,14 +195,15 @@ def cpu_baseline(w, gens):
     p = _problem(w, 0)
     o = oracle.Oracle(p, block=w["block"])
     t = time.perf_counter()
-    r = o.solve(split_m=2, split_d=w["cpu_split_d"], max_parents=w["cpu_parents"], max_gen=gens,
-                fp32=bool(w["fp32"]))
+    paper = dict(samples=10, mono_all=True, tol_x=1e-4) if w.get("paper") else {}
+    r = o.solve(split_m=w["cpu_split_m"], split_d=w["cpu_split_d"], max_parents=w["cpu_parents"], max_gen=gens,
+                fp32=bool(w["fp32"]), **paper)
     dt = time.perf_counter() - t
     evals = r.evals64 + r.evals32
     return {"value": evals / dt, "unit": "box-evals/s", "cores": 1, "kind": "oracle",
             "sample": f"first {r.generations} generations of the {w['family']} n={w['n']} solve, "
-                      f"{w['cpu_parents']} parents x {2 ** w['cpu_split_d']} children per generation "
-                      f"({evals} box evaluations, {dt:.1f} s, 1 thread)"}
+                      f"{w['cpu_parents']} parents x {w['cpu_split_m'] ** w['cpu_split_d']} children per "
+                      f"generation ({evals} box evaluations, {dt:.1f} s, 1 thread)"}
 
 
 def run_reference(a):
@@ -206,13 +220,20 @@ def run_reference(a):
     for i in range(a.steps):
         vals.append(cpu_baseline(w, max(1, gens // 2)))
     v = statistics.median([x["value"] for x in vals])
-    line = {"impl": "reference", "metric": "box-evals/s", "value": v, "unit": "box-evals/s",
+    metric, unit, hib, note = "box-evals/s", "box-evals/s", True, None
+    if w.get("paper"):
+        # the procedure fixes the work of a solve: iterations x 4^10 children
+        metric, unit, hib = "solve time", "s", False
+        v = w["paper_iters"] * w["split_m"] ** w["split_d"] / v
+        note = (f"extrapolated: {w['paper_iters']} iterations x {w['split_m'] ** w['split_d']} children "
+                "at the sampled oracle rate")
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": unit,
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": None,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": hib, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if w["fp32"] else "f64",
-            "data": "synthetic", "config": {"workload": w["name"]},
+            "data": "synthetic", "config": {"workload": w["name"], "note": note},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[0]["sample"], "value": v},
-            "e2e": {"value": v, "unit": "box-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -396,6 +417,8 @@ def main():
                 max_children=a.max_children or w["max_children"], fp32_prefilter=w["fp32"],
                 gens_per_sync=w["gens_per_sync"], device=local,
                 pool_bytes=int((a.pool_gb or w["pool_gb"]) * (1 << 30)))
+    if w.get("paper"):
+        opts.update(samples=10, mono_all=1, tol_x=1e-4)
     if a.max_gens > 0:
         opts["max_generations"] = a.max_gens
     solver = gb.Solver(p, **opts)
@@ -426,8 +449,9 @@ def main():
     evals = sum(r.box_evals_fp64 + r.box_evals_fp32 for r in results)
     mids = sum(r.mid_evals for r in results)
     launches = sum(r.kernel_launches for r in results)
-    ok = all(r.status == 0 and r.fmin_lo <= 0.0 <= r.fmin_hi and r.fmin_hi - r.fmin_lo <= p.tol_f
-             for r in results)
+    fstar = p.meta.get("fstar", 0.0)
+    ok = all(r.status == 0 and r.fmin_lo <= fstar <= r.fmin_hi and
+             (w.get("paper") or r.fmin_hi - r.fmin_lo <= p.tol_f) for r in results)
 
     # ---- per-kernel event times of the child evaluation ---------------------
     # (graph replays carry no per-kernel events: one extra solve with a host
@@ -445,7 +469,9 @@ def main():
     k_n = sum((r.eval32_launches if use32 else r.eval64_launches) for r in prof)
     k_evals = sum((r.box_evals_fp32 if use32 else r.box_evals_fp64 - 1) for r in prof)
     warp = opts["max_children"] < (1 << 16)
-    if w["fp32"] and warp:   # FP32 prefilter and FP64 evaluation in one warp-per-child kernel
+    if w.get("paper"):       # paper mode runs in the bytecode interpreter
+        kname = "k_eval32" if use32 else "k_eval64"
+    elif w["fp32"] and warp:   # FP32 prefilter and FP64 evaluation in one warp-per-child kernel
         kname = "k_eval3264_tabw (FP64 operations over the fused kernel's time)"
     else:
         kname = ("k_eval32_tab" if use32 else "k_eval64_tab") + ("w" if warp else "")
@@ -480,12 +506,19 @@ def main():
         probe_ops, _ = gb.gb_measure_peak(local, 1 if use32 else 0)
     except Exception:
         probe_ops = None
+    metric, unit, hib, vsb = "box-evals/s", "box-evals/s", True, None
+    if w.get("paper"):   # the paper prints solve times for its procedure
+        metric, unit, hib = "solve time", "s", False
+        value = dev_ms * 1e-3 / a.steps
+        vsb = value / w["baseline_s"]
     line = {
-        "metric": "box-evals/s", "value": value, "unit": "box-evals/s", "n_gpus": world,
+        "metric": metric, "value": value, "unit": unit, "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dev_ms / a.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": hib, "scaling": "weak", "vs_baseline": vsb,
         "dtype": "f32+f64" if w["fp32"] else "f64", "data": "synthetic",
         "config": {"workload": w["name"], "l2": "flushed between steps (512 MB write)",
+                   "box_evals_per_s": evals / (dev_ms * 1e-3),
+                   "paper_time_s": w.get("baseline_s"),
                    "solves_per_s": a.steps / (dev_ms * 1e-3), "generations_per_solve":
                    results[-1].generations, "mid_evals_per_s": mids / (dev_ms * 1e-3),
                    "fp32_evals_per_solve": results[-1].box_evals_fp32,
@@ -494,7 +527,8 @@ def main():
                    "peak_pool_boxes": int(results[-1].trace["pool"].max()) if len(results[-1].trace["pool"]) else 1,
                    "all_enclosures_valid": ok, "enclosure": [results[-1].fmin_lo, results[-1].fmin_hi],
                    "host_ms_per_step": 1e3 * host_t / a.steps, "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "e2e": ({"value": e2e_evals / e2e_t, "unit": "box-evals/s", "h2d_bytes_per_step": int(h2d),
+        "e2e": ({"value": (e2e_t / e2e_steps) if w.get("paper") else e2e_evals / e2e_t,
+                 "unit": unit, "h2d_bytes_per_step": int(h2d),
                  "d2h_bytes_per_step": int(d2h)} if e2e_t > 0 else None),
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

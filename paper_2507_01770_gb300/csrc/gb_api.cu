@@ -366,7 +366,7 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             return bad(e, "cudaMemset");
     } else {
         size_t per_slot = (size_t)n * 16 + (fp32 ? (size_t)n * 8 : 0) + (size_t)NG * 32 + (fp32 ? (size_t)NG * 8 : 0) +
-                          4 + 2 * 16;
+                          4 + 2 * 16 + (size_t)opt.samples * NG * 16;
         cap = opt.max_boxes > 0 ? opt.max_boxes : (long long)(opt.pool_bytes / per_slot);
         if (cap < 1) return bad(cudaErrorMemoryAllocation, "pool budget below one box");
         if (cap > (1LL << 31) - 1) cap = (1LL << 31) - 1;
@@ -378,6 +378,10 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             if ((e = alloc(&pl.lo32, (size_t)cap * n, A)) || (e = alloc(&pl.hi32, (size_t)cap * n, A)) ||
                 (e = alloc(&pl.gsum32, (size_t)cap * NG, A)))
                 return bad(e, "allocate box pool");
+        }
+        if (opt.samples > 0) {   // cached group sums at every diagonal sample
+            pl.S = opt.samples;
+            if ((e = alloc(&pl.gsamp, (size_t)cap * opt.samples * NG, A))) return bad(e, "allocate box pool");
         }
     }
     p->cap = cap;

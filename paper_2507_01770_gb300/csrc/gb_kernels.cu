@@ -102,6 +102,10 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
                 iv32 c = group_sum<float>(P, S, g, X32, R32, ops);
                 (pool.recs ? pool.rgsum32 : pool.gsum32)[at] = make_float2(c.lo, c.hi);
             }
+            for (int j = 1; pool.gsamp && j <= pool.S; j++) {
+                const iv64 v = group_sum<double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
+                pool.gsamp[(size_t)(j - 1) * pool.NG + gg] = make_double2(v.lo, v.hi);
+            }
         }
     }
     __syncthreads();
@@ -118,7 +122,8 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
         nsamp = P.samples;
         for (int j = 1; j <= P.samples; j++) {
             const SampleView SV{X, j, P.samples + 1};
-            sum_values<double>(P, -1, SV, (const CacheRef<double2>*)nullptr, R, sums, ops);
+            const CacheRef<double2> cs{pool.gsamp + (size_t)(j - 1) * pool.NG, nullptr, nullptr, 0};
+            sum_values<double>(P, -1, SV, pool.gsamp ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
             const iv64 Fs = outer_fwd<double>(P, SV, sums, O, ops);
             if (Fs.hi < gub) gub = Fs.hi;
         }
@@ -531,7 +536,10 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
     if (P.samples > 0) {   // diagonal samples, each evaluated in full
         for (int j = 1; j <= P.samples; j++) {
             const SampleView SV{X, j, P.samples + 1};
-            sum_values<double>(P, blk, SV, (const CacheRef<double2>*)nullptr, R, sums, ops);
+            // the child's sample j agrees with its parent's on every coordinate
+            // it did not split: the groups off the split block come from the cache
+            const CacheRef<double2> cs{pool.gsamp + ((size_t)c.slot * pool.S + (j - 1)) * pool.NG, nullptr, nullptr, 0};
+            sum_values<double>(P, blk, SV, pool.gsamp ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
             const iv64 Fs = outer_fwd<double>(P, SV, sums, O, ops);
             if (Fs.hi == Fs.hi) {
                 const unsigned long long k = gb_order_key(Fs.hi);
@@ -758,6 +766,9 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
             pool.gsum[dst] = pool.gsum[src];
             pool.gmid[dst] = pool.gmid[src];
             if (pool.fp32) pool.gsum32[dst] = pool.gsum32[src];
+            for (int j = 0; pool.gsamp && j < pool.S; j++)
+                pool.gsamp[((size_t)ns * pool.S + j) * pool.NG + S.group0 + g] =
+                    pool.gsamp[((size_t)c.slot * pool.S + j) * pool.NG + S.group0 + g];
         }
         for (int g = dr.x; g < dr.y; g++, slot_k++) {
             if ((slot_k & 31) != lane) continue;
@@ -778,6 +789,10 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
             }
             pool.gsum[dst] = make_double2(a.lo, a.hi);
             pool.gmid[dst] = make_double2(b.lo, b.hi);
+            for (int j = 1; pool.gsamp && j <= pool.S; j++) {
+                const iv64 v = group_sum<double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
+                pool.gsamp[((size_t)ns * pool.S + (j - 1)) * pool.NG + S.group0 + g] = make_double2(v.lo, v.hi);
+            }
         }
     }
     if (lane == 0) {

@@ -16,7 +16,8 @@ struct GbPool {
     double2* gmid;    // [cap][NG] cached group sums at the box midpoint (FP64)
     float2* gsum32;   // [cap][NG] cached group sums of F (FP32 prefilter only)
     unsigned* freel;  // [cap] free slots
-    int n, NG, fp32;
+    double2* gsamp;   // [cap][S][NG] cached group sums at the S diagonal samples (dense rows, samples > 0)
+    int n, NG, fp32, S;
     // block-record mode (recs = 1): a box is a row of nb record ids; record q
     // holds block coordinates [q*B, q*B + B) and the cached sums of the groups
     // its block owns [q*GPB, q*GPB + GPB).  lo64..gsum32 above are unused.
