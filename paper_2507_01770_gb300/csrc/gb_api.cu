@@ -335,7 +335,9 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     // replaces few of the blocks (a record holds B coordinates and the cached sums of the
     // groups its block owns; records per box budgeted at 4 * nrec)
     const int nrec = std::min(H.nb, H.span + 1);
-    const bool recs = opt.pool_mode == 2 || (opt.pool_mode == 0 && n >= 128 && 4 * nrec <= H.nb);
+    // paper mode caches per-box sample sums and coordinate partials in dense rows
+    const bool paper = opt.samples > 0 || opt.mono_all;
+    const bool recs = opt.pool_mode == 2 || (opt.pool_mode == 0 && !paper && n >= 128 && 4 * nrec <= H.nb);
     long long cap = 0;
     if (recs) {
         const size_t per_slot = (size_t)H.nb * 4 + 4 + 4 + 2 * 16;
@@ -366,7 +368,8 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             return bad(e, "cudaMemset");
     } else {
         size_t per_slot = (size_t)n * 16 + (fp32 ? (size_t)n * 8 : 0) + (size_t)NG * 32 + (fp32 ? (size_t)NG * 8 : 0) +
-                          4 + 2 * 16 + (size_t)opt.samples * NG * 16;
+                          4 + 2 * 16 + (size_t)opt.samples * NG * 16 +
+                          (opt.mono_all ? (size_t)P.n_sum * n * 16 : 0);
         cap = opt.max_boxes > 0 ? opt.max_boxes : (long long)(opt.pool_bytes / per_slot);
         if (cap < 1) return bad(cudaErrorMemoryAllocation, "pool budget below one box");
         if (cap > (1LL << 31) - 1) cap = (1LL << 31) - 1;
@@ -378,6 +381,9 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             if ((e = alloc(&pl.lo32, (size_t)cap * n, A)) || (e = alloc(&pl.hi32, (size_t)cap * n, A)) ||
                 (e = alloc(&pl.gsum32, (size_t)cap * NG, A)))
                 return bad(e, "allocate box pool");
+        }
+        if (opt.mono_all && P.n_sum > 0) {   // cached coordinate partials for the all-coordinate test
+            if ((e = alloc(&pl.gdp, (size_t)cap * P.n_sum * n, A))) return bad(e, "allocate box pool");
         }
         if (opt.samples > 0) {   // cached group sums at every diagonal sample
             pl.S = opt.samples;

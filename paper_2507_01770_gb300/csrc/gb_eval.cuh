@@ -440,4 +440,105 @@ __device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X,
     return mono;
 }
 
+// ---- cached coordinate partials (first-order test on every coordinate) ----
+// D_kj: the sum over the terms of sum k of their leaf adjoints for
+// coordinate j, accumulated from [0, 0] in ascending term and leaf order
+// (the value block_mono multiplies by the sum's outer adjoint); stored per
+// box as row[k * n + j], an untouched pair as (+inf, -inf).
+__device__ __forceinline__ bool d_touched(double2 d) {
+    return !(__double_as_longlong(d.x) == 0x7ff0000000000000LL &&
+             __double_as_longlong(d.y) == (long long)0xfff0000000000000ULL);
+}
+
+// D of the coordinates of block blk over box X into row (FP64).
+template <typename V>
+__device__ __noinline__ void block_D(const GbProg& P, int blk, const V& X, iv64* R, iv64* RA, double2* row,
+                                        int& ops) {
+    const int c0 = blk * P.B;
+    const int c1 = min(P.n, c0 + P.B);
+    iv64 W[GB_MAX_ISUM][GB_MAX_WIN];
+    unsigned touched[GB_MAX_ISUM];
+    int cur[GB_MAX_ISUM];
+    for (int k = 0; k < P.n_sum; k++) {
+        GbSum S = P.sums[k];
+        int need = c0 - S.off_max - S.first;
+        cur[k] = need <= 0 ? 0 : (need + S.step - 1) / S.step;
+        touched[k] = 0;
+        for (int w = 0; w < GB_MAX_WIN; w++) W[k][w] = iv64{0.0, 0.0};
+    }
+    for (int j = c0; j < c1; j++) {
+        for (int k = 0; k < P.n_sum; k++) {
+            GbSum S = P.sums[k];
+            double2 out = make_double2(__longlong_as_double(0x7ff0000000000000LL),
+                                       __longlong_as_double((long long)0xfff0000000000000ULL));
+            if (S.has_var) {
+                while (cur[k] < S.count && S.first + cur[k] * S.step + S.off_min <= j) {
+                    int i = S.first + cur[k] * S.step;
+                    term_fwd<double>(P, S, i, X, R, ops);
+                    for (int t = 0; t < S.nins; t++) RA[t] = iv64{0.0, 0.0};
+                    RA[S.nins - 1] = iv64{1.0, 1.0};
+                    const GbIns* ins = P.tins + S.ins0;
+                    reverse_sweep<double>(ins, S.nins, R, RA, ops);
+                    for (int t = 0; t < S.nins; t++) {
+                        GbIns in = ins[t];
+                        if (in.op != D_IVAR) continue;
+                        int cc = i + in.aux;
+                        if (cc < c0 || cc >= c1) continue;
+                        int w = cc & (GB_MAX_WIN - 1);
+                        W[k][w] = iadd(W[k][w], RA[t]);
+                        ops += 2;
+                        touched[k] |= 1u << w;
+                    }
+                    cur[k]++;
+                }
+                int w = j & (GB_MAX_WIN - 1);
+                if (touched[k] & (1u << w)) {
+                    out = make_double2(W[k][w].lo, W[k][w].hi);
+                    W[k][w] = iv64{0.0, 0.0};
+                    touched[k] &= ~(1u << w);
+                }
+            }
+            row[(size_t)k * P.n + j] = out;
+        }
+    }
+}
+
+// Blocks whose D a split of block blk changes: the blocks with a coordinate
+// within the widest term's reach (its IDX_VAR offset range) of the block.
+__device__ __forceinline__ int2 d_affected(const GbProg& P, int blk) {
+    int tw = 0;
+    for (int k = 0; k < P.n_sum; k++)
+        if (P.sums[k].has_var) tw = max(tw, P.sums[k].off_max - P.sums[k].off_min);
+    const int c0 = blk * P.B, c1 = min(P.n, c0 + P.B) - 1;
+    return make_int2(max(0, c0 - tw) / P.B, min(P.nb - 1, (c1 + tw) / P.B));
+}
+
+// First-order test of block blk from cached D and the box's own outer
+// adjoints OA (the operations of block_mono after its term sweeps).
+__device__ __forceinline__ bool cached_mono(const GbProg& P, int blk, const View<double>& X64, const iv64* OA,
+                                            const double2* row, int& ops) {
+    const int c0 = blk * P.B;
+    const int c1 = min(P.n, c0 + P.B);
+    for (int j = c0; j < c1; j++) {
+        iv64 g{0.0, 0.0};
+        for (int v = 0; v < P.n_var_leaves; v++) {
+            GbVarLeaf L = P.var_leaves[v];
+            if (L.coord == j) g = iadd(g, OA[L.reg]), ops += 2;
+        }
+        for (int k = 0; k < P.n_sum; k++) {
+            const GbSum S = P.sums[k];
+            if (!S.has_var) continue;
+            const double2 d = row[(size_t)k * P.n + j];
+            if (!d_touched(d)) continue;
+            g = iadd(g, imul(OA[S.outer_reg], iv64{d.x, d.y}));
+            ops += 4;
+        }
+        iv64 x = X64.get(j);
+        if ((gt_zero(g.lo) && !same_value(x.lo, __ldg(P.l + j))) ||
+            (lt_zero(g.hi) && !same_value(x.hi, __ldg(P.u + j))))
+            return true;
+    }
+    return false;
+}
+
 }  // namespace gb

@@ -108,6 +108,10 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
             }
         }
     }
+    if (pool.gdp) {   // coordinate partials of the domain, every block
+        iv64 RA[GB_MAX_TREGS];
+        for (int b = threadIdx.x; b < P.nb; b += blockDim.x) block_D(P, b, X, R, RA, pool.gdp, ops);
+    }
     __syncthreads();
     if (threadIdx.x != 0) return;
     // F and the midpoint sample from the group sums just cached (the same
@@ -518,6 +522,24 @@ __device__ __forceinline__ bool mono_any(const GbProg& P, int blk, const V& X, c
     return false;
 }
 
+// First-order test on every coordinate with the parent's cached D: the
+// blocks a split of blk changes are tested in full, every other block from
+// the cache with the child's own outer adjoints (the same operations in the
+// same order as the full test, so the same decision).
+template <typename V>
+__device__ __noinline__ bool mono_cached(const GbProg& P, const GbPool& pool, unsigned slot, int blk, const V& X,
+                                         const iv64* O, iv64* OA, iv64* R, iv64* RA, int& ops) {
+    const int2 ab = d_affected(P, blk);
+    const double2* row = pool.gdp + (size_t)slot * P.n_sum * P.n;
+    for (int b = ab.x; b <= ab.y; b++)   // also leaves the outer adjoints in OA
+        if (block_mono<double>(P, b, X, X, O, OA, R, RA, (double*)nullptr, ops)) return true;
+    for (int b = 0; b < P.nb; b++) {
+        if (b >= ab.x && b <= ab.y) continue;
+        if (cached_mono(P, b, X, OA, row, ops)) return true;
+    }
+    return false;
+}
+
 __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool, const GbParents& par,
                                              const GbChildren& ch, long long ci, const GbSplit& sp,
                                              double gub_prev, unsigned long long* gkey, bool* has_key,
@@ -558,7 +580,9 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
     sum_values<double>(P, blk, X, &cf, R, sums, ops);
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
     bool keep = !(F.lo > gub_prev);
-    if (keep) keep = !mono_any<double>(P, blk, X, X, O, OA, R, RA, ops);
+    if (keep)
+        keep = !(pool.gdp ? mono_cached(P, pool, c.slot, blk, X, O, OA, R, RA, ops)
+                          : mono_any<double>(P, blk, X, X, O, OA, R, RA, ops));
     ch.flo[ci] = canon_lo(F.lo);
     ch.flag[ci] = keep ? 1 : 0;
     return true;
@@ -794,6 +818,17 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
                 pool.gsamp[((size_t)ns * pool.S + (j - 1)) * pool.NG + S.group0 + g] = make_double2(v.lo, v.hi);
             }
         }
+    }
+    if (pool.gdp) {   // coordinate partials: the parent's, recomputed where the split reaches
+        const int2 ab = d_affected(P, blk);
+        const int a0 = ab.x * P.B, a1 = min(n, (ab.y + 1) * P.B);
+        const double2* src = pool.gdp + (size_t)c.slot * P.n_sum * n;
+        double2* dst = pool.gdp + (size_t)ns * P.n_sum * n;
+        for (int k = 0; k < P.n_sum; k++)
+            for (int j = lane; j < n; j += 32)
+                if (j < a0 || j >= a1) dst[(size_t)k * n + j] = src[(size_t)k * n + j];
+        iv64 RA[GB_MAX_TREGS];
+        for (int b = ab.x + lane; b <= ab.y; b += 32) block_D(P, b, X, R, RA, dst, ops);
     }
     if (lane == 0) {
         long long e = kept_old + s;

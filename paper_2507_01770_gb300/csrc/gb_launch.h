@@ -17,6 +17,7 @@ struct GbPool {
     float2* gsum32;   // [cap][NG] cached group sums of F (FP32 prefilter only)
     unsigned* freel;  // [cap] free slots
     double2* gsamp;   // [cap][S][NG] cached group sums at the S diagonal samples (dense rows, samples > 0)
+    double2* gdp;     // [cap][n_sum][n] cached coordinate partial sums D (dense rows, mono_all)
     int n, NG, fp32, S;
     // block-record mode (recs = 1): a box is a row of nb record ids; record q
     // holds block coordinates [q*B, q*B + B) and the cached sums of the groups
