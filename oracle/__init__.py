@@ -28,7 +28,7 @@ _lib = None
 # operator codes of the objective node format (see synthetic.dag)
 OP = dict(CONST=0, PI=1, EULER=2, VAR=3, IDX_VAR=4, IDX_COEF=5, ADD=6, SUB=7,
           MUL=8, DIV=9, NEG=10, SQR=11, SQRT=12, EXP=13, SIN=14, COS=15,
-          SCALE=16, ISUM=17)
+          SCALE=16, ISUM=17, IPROD=18)
 
 ST_OK, ST_INVALID, ST_CAPACITY, ST_LIMIT = 0, 1, 3, 4
 
@@ -86,6 +86,8 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int32)]
             L.oracle_iv_op.argtypes = [ip, dp, dp, ctypes.c_double, ip, dp]
             L.oracle_tree_sum.argtypes = [dp, dp, ip, ip, dp]
+            L.oracle_tree_prod.argtypes = [dp, dp, ip, ip, dp]
+            L.oracle_tree_prod_adjoint.argtypes = [dp, dp, ip, ctypes.c_double, ctypes.c_double, ip, dp]
             L.oracle_solve.argtypes = [vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Result)]
             L.oracle_solve.restype = ip
             L.oracle_free_result.argtypes = [ctypes.POINTER(_Result)]
@@ -114,6 +116,25 @@ def tree_sum(lo, hi, f32: bool = False):
     out = np.zeros(2)
     lib().oracle_tree_sum(_dp(lo), _dp(hi), len(lo), int(f32), _dp(out))
     return float(out[0]), float(out[1])
+
+
+def tree_prod(lo, hi, f32: bool = False):
+    """The IPROD reduction tree (the pairwise tree of tree_sum with products)."""
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    out = np.zeros(2)
+    lib().oracle_tree_prod(_dp(lo), _dp(hi), len(lo), int(f32), _dp(out))
+    return float(out[0]), float(out[1])
+
+
+def tree_prod_adjoint(lo, hi, seed=(1.0, 1.0), f32: bool = False):
+    """Adjoint of every item of the IPROD tree for a product adjoint seed; (m, 2)."""
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    out = np.zeros((len(lo), 2))
+    lib().oracle_tree_prod_adjoint(_dp(lo), _dp(hi), len(lo), float(seed[0]), float(seed[1]), int(f32),
+                                   _dp(out))
+    return out
 
 
 @dataclass

@@ -281,8 +281,12 @@ enum {
     O_CONST = 0, O_PI = 1, O_EULER = 2, O_VAR = 3, O_IDX_VAR = 4, O_IDX_COEF = 5,
     O_ADD = 6, O_SUB = 7, O_MUL = 8, O_DIV = 9, O_NEG = 10, O_SQR = 11,
     O_SQRT = 12, O_EXP = 13, O_SIN = 14, O_COS = 15, O_SCALE = 16, O_ISUM = 17,
-    O_COUNT = 18
+    O_IPROD = 18, O_COUNT = 19
 };
+
+/* ISUM and IPROD reduce a per-index template over an index set; they share
+ * the layout, the grouping and the tree, and differ in the operation. */
+static int is_red(int op) { return op == O_ISUM || op == O_IPROD; }
 
 typedef struct { int32_t op, a, b, c, d, pad; double v; } onode;
 
@@ -305,7 +309,7 @@ typedef struct {
     /* structure derived from the DAG */
     char* outer;          /* node reachable from root outside any template */
     char* in_tmpl;        /* scratch for template membership */
-    int n_isum;           /* ISUM nodes on the outer side, ascending */
+    int n_isum;           /* ISUM / IPROD nodes on the outer side, ascending */
     int* isum_node;
     int** tmpl_nodes;     /* per ISUM: template nodes ascending */
     int* tmpl_count;
@@ -313,7 +317,8 @@ typedef struct {
     int* off_max;
     int* has_var;         /* per ISUM: template contains IDX_VAR */
     /* scratch */
-    iv *val, *adj, *tval, *tadj, *terms, *groups, *gsum, *dacc;
+    iv *val, *adj, *tval, *tadj, *terms, *groups, *gsum, *dacc, *gadj, *tseed;
+    int* gstart;
     char* touched;
     int max_terms;
 } oprob;
@@ -328,7 +333,7 @@ static int mark_template(const oprob* P, int r, char* mark) {
     if (mark[r]) return 0;
     mark[r] = 1;
     const onode* q = &P->nd[r];
-    if (q->op == O_VAR || q->op == O_ISUM) return 1;
+    if (q->op == O_VAR || is_red(q->op)) return 1;
     int k = n_operands(q->op);
     if (k >= 1 && mark_template(P, q->a, mark)) return 1;
     if (k >= 2 && mark_template(P, q->b, mark)) return 1;
@@ -340,7 +345,7 @@ static int mark_outer(const oprob* P, int r) {
     P->outer[r] = 1;
     const onode* q = &P->nd[r];
     if (q->op == O_IDX_VAR || q->op == O_IDX_COEF) return 1;
-    if (q->op == O_ISUM) return 0;           /* template handled separately */
+    if (is_red(q->op)) return 0;             /* template handled separately */
     int k = n_operands(q->op);
     if (k >= 1 && mark_outer(P, q->a)) return 1;
     if (k >= 2 && mark_outer(P, q->b)) return 1;
@@ -357,6 +362,7 @@ static void free_prob(oprob* P) {
     free(P->has_var);
     free(P->val); free(P->adj); free(P->tval); free(P->tadj); free(P->terms);
     free(P->groups); free(P->gsum); free(P->dacc); free(P->touched);
+    free(P->gadj); free(P->tseed); free(P->gstart);
     free(P);
 }
 
@@ -399,12 +405,12 @@ static oprob* make_prob(const void* nodes, int nn, int root, const double* const
         if (k >= 2 && (q->b < 0 || q->b >= v)) { free_prob(P); return NULL; }
         if ((q->op == O_CONST || q->op == O_SCALE) && !isfinite(q->v)) { free_prob(P); return NULL; }
         if (q->op == O_VAR && (q->a < 0 || q->a >= n)) { free_prob(P); return NULL; }
-        if (q->op == O_ISUM && (q->a < 0 || q->a >= v || q->d < 1)) { free_prob(P); return NULL; }
+        if (is_red(q->op) && (q->a < 0 || q->a >= v || q->d < 1)) { free_prob(P); return NULL; }
     }
     P->outer = (char*)calloc(nn, 1);
     P->in_tmpl = (char*)calloc(nn, 1);
     if (mark_outer(P, root)) { free_prob(P); return NULL; }
-    /* ISUM nodes and their templates */
+    /* ISUM / IPROD nodes and their templates */
     P->isum_node = (int*)malloc(sizeof(int) * nn);
     P->tmpl_nodes = (int**)calloc(nn, sizeof(int*));
     P->tmpl_count = (int*)calloc(nn, sizeof(int));
@@ -413,7 +419,7 @@ static oprob* make_prob(const void* nodes, int nn, int root, const double* const
     P->has_var = (int*)calloc(nn, sizeof(int));
     int max_terms = 1;
     for (int v = 0; v < nn; v++) {
-        if (!P->outer[v] || P->nd[v].op != O_ISUM) continue;
+        if (!P->outer[v] || !is_red(P->nd[v].op)) continue;
         int k = P->n_isum++;
         P->isum_node[k] = v;
         const onode* s = &P->nd[v];
@@ -458,6 +464,9 @@ static oprob* make_prob(const void* nodes, int nn, int root, const double* const
     P->terms = (iv*)calloc(max_terms, sizeof(iv));
     P->groups = (iv*)calloc(max_terms, sizeof(iv));
     P->gsum = (iv*)calloc(max_terms, sizeof(iv));
+    P->gadj = (iv*)calloc(max_terms, sizeof(iv));
+    P->tseed = (iv*)calloc(max_terms, sizeof(iv));
+    P->gstart = (int*)calloc(max_terms + 1, sizeof(int));
     P->dacc = (iv*)calloc(B, sizeof(iv));
     P->touched = (char*)calloc(B, 1);
     return P;
@@ -560,6 +569,55 @@ static iv tree_sum(iv* a, int m, int p) {
     return a[0];
 }
 
+/* The same tree with products (IPROD); the empty product is [1, 1]. */
+static iv tree_prod(iv* a, int m, int p) {
+    if (m == 0) return mk(1.0, 1.0);
+    for (int s = 1; s < m; s *= 2)
+        for (int i = 0; i + s < m; i += 2 * s) a[i] = iv_mul(a[i], a[i + s], p);
+    return a[0];
+}
+
+/* Reverse sweep of tree_prod over a[0..m): adj[i] receives the adjoint of
+ * item i when the product has adjoint seed.  Every tree node feeds exactly
+ * one product, so a node's adjoint is its consumer's adjoint times the other
+ * operand's value (reverse mode over the tree's code list, top level first).
+ * Reading: the paper does not say how partials are formed (section 3.1);
+ * this is the reverse-mode rule of every other operation applied to the
+ * fixed reduction tree. */
+static void tree_prod_adjoint(const iv* a, int m, iv seed, iv* adj, int p) {
+    if (m == 0) return;
+    int L = 0;
+    while ((1 << L) < m) L++;
+    iv* V = (iv*)malloc(sizeof(iv) * (size_t)m * (L + 1));   /* values entering level l */
+    iv* A = (iv*)malloc(sizeof(iv) * (size_t)m * (L + 1));   /* their adjoints */
+    memcpy(V, a, sizeof(iv) * (size_t)m);
+    for (int l = 0; l < L; l++) {
+        const int s = 1 << l;
+        const iv* cur = V + (size_t)l * m;
+        iv* nxt = V + (size_t)(l + 1) * m;
+        memcpy(nxt, cur, sizeof(iv) * (size_t)m);
+        for (int i = 0; i + s < m; i += 2 * s) nxt[i] = iv_mul(cur[i], cur[i + s], p);
+    }
+    A[(size_t)L * m] = seed;
+    for (int l = L - 1; l >= 0; l--) {
+        const int s = 1 << l;
+        const iv* cur = V + (size_t)l * m;
+        const iv* up = A + (size_t)(l + 1) * m;
+        iv* dn = A + (size_t)l * m;
+        for (int i = 0; i < m; i += 2 * s) {
+            if (i + s < m) {
+                dn[i] = iv_mul(up[i], cur[i + s], p);
+                dn[i + s] = iv_mul(up[i], cur[i], p);
+            } else {
+                dn[i] = up[i];
+            }
+        }
+    }
+    memcpy(adj, A, sizeof(iv) * (size_t)m);
+    free(V);
+    free(A);
+}
+
 /* Evaluates template k (ISUM node index isum_node[k]) for index i; values
  * in P->tval, returns the root value. */
 static iv eval_term(oprob* P, int k, int i, obox X, int p) {
@@ -577,15 +635,14 @@ static void term_blocks(const oprob* P, int k, int i, int* bmin, int* bmax) {
     *bmax = (i + P->off_max[k]) / P->B;
 }
 
-/* ISUM value: terms in index order are grouped into maximal runs with the
- * same touched-block range; each group is reduced by tree_sum, then the
- * groups (in order) by tree_sum again. */
-static iv isum_value(oprob* P, int k, obox X, int p) {
+/* Groups of reduction k: terms in index order split into maximal runs with
+ * the same touched-block range; group g holds the term ordinals
+ * [gstart[g], gstart[g + 1]).  Returns the number of groups. */
+static int isum_groups(const oprob* P, int k, int* gstart) {
     const onode* s = &P->nd[P->isum_node[k]];
     int cnt = isum_count(s);
-    if (cnt == 0) return mk(0.0, 0.0);
-    for (int q = 0; q < cnt; q++) P->terms[q] = eval_term(P, k, s->b + q * s->d, X, p);
     int ng = 0, start = 0;
+    if (cnt == 0) return 0;
     for (int q = 1; q <= cnt; q++) {
         int b0, b1, c0, c1;
         term_blocks(P, k, s->b + start * s->d, &b0, &b1);
@@ -595,12 +652,31 @@ static iv isum_value(oprob* P, int k, obox X, int p) {
             boundary = (c0 != b0 || c1 != b1);
         }
         if (boundary) {
-            for (int r = start; r < q; r++) P->groups[r - start] = P->terms[r];
-            P->gsum[ng++] = tree_sum(P->groups, q - start, p);
+            gstart[ng++] = start;
             start = q;
         }
     }
-    return tree_sum(P->gsum, ng, p);
+    gstart[ng] = cnt;
+    return ng;
+}
+
+/* ISUM / IPROD value: each group reduced by the tree (sum or product),
+ * then the groups in order by the tree again.  Leaves the term values in
+ * P->terms and the group values in P->gsum. */
+static iv isum_value(oprob* P, int k, obox X, int p) {
+    const onode* s = &P->nd[P->isum_node[k]];
+    const int prod = s->op == O_IPROD;
+    int cnt = isum_count(s);
+    if (cnt == 0) return prod ? mk(1.0, 1.0) : mk(0.0, 0.0);
+    for (int q = 0; q < cnt; q++) P->terms[q] = eval_term(P, k, s->b + q * s->d, X, p);
+    int ng = isum_groups(P, k, P->gstart);
+    for (int g = 0; g < ng; g++) {
+        int a = P->gstart[g], e = P->gstart[g + 1];
+        for (int r = a; r < e; r++) P->groups[r - a] = P->terms[r];
+        P->gsum[g] = prod ? tree_prod(P->groups, e - a, p) : tree_sum(P->groups, e - a, p);
+    }
+    for (int g = 0; g < ng; g++) P->groups[g] = P->gsum[g];
+    return prod ? tree_prod(P->groups, ng, p) : tree_sum(P->groups, ng, p);
 }
 
 /* Forward pass of the outer expression; returns F(X). */
@@ -608,7 +684,7 @@ static iv eval_outer(oprob* P, obox X, int p) {
     int k = 0;
     for (int v = 0; v < P->nn; v++) {
         if (!P->outer[v]) continue;
-        if (P->nd[v].op == O_ISUM) {
+        if (is_red(P->nd[v].op)) {
             while (P->isum_node[k] != v) k++;
             P->val[v] = isum_value(P, k, X, p);
         } else {
@@ -621,10 +697,12 @@ static iv eval_outer(oprob* P, obox X, int p) {
 /* Interval partials of f for the coordinates of block blk (section 3.1's
  * first-order test needs [DLB_i, DUB_i]).  Reading: reverse-mode interval
  * adjoints; for coordinate j the sum runs over the outer VAR(j) leaves
- * (ascending node), then over the ISUM nodes (ascending) of
- * adj(ISUM) * D_j, where D_j sums the template adjoints (seeded with [1,1])
- * of the IDX_VAR leaves that hit x_j, in ascending term index and ascending
- * leaf node.  Requires eval_outer(X) to have run.  G has B entries. */
+ * (ascending node), then over the ISUM / IPROD nodes (ascending) of
+ * adj(node) * D_j, where D_j sums the template adjoints of the IDX_VAR leaves
+ * that hit x_j, in ascending term index and ascending leaf node.  A sum's
+ * templates are seeded with [1,1]; a product's with the term's adjoint in
+ * the product tree (tree_prod_adjoint, seed [1,1]).  Requires eval_outer(X)
+ * to have run.  G has B entries. */
 static void block_partials(oprob* P, obox X, int p, int blk, iv* G, int* width) {
     int c0 = blk * P->B, c1 = c0 + P->B;
     if (c1 > P->n) c1 = P->n;
@@ -632,7 +710,7 @@ static void block_partials(oprob* P, obox X, int p, int blk, iv* G, int* width) 
     for (int v = 0; v < P->nn; v++) P->adj[v] = mk(0.0, 0.0);
     P->adj[P->root] = mk(1.0, 1.0);
     for (int v = P->nn - 1; v >= 0; v--) {
-        if (!P->outer[v] || P->nd[v].op == O_ISUM) continue;
+        if (!P->outer[v] || is_red(P->nd[v].op)) continue;
         push_adjoint(P, v, p, P->val, P->adj);
     }
     for (int j = c0; j < c1; j++) G[j - c0] = mk(0.0, 0.0);
@@ -643,6 +721,17 @@ static void block_partials(oprob* P, obox X, int p, int blk, iv* G, int* width) 
         if (!P->has_var[k]) continue;
         const onode* s = &P->nd[P->isum_node[k]];
         int cnt = isum_count(s);
+        const int prod = s->op == O_IPROD;
+        if (prod) {
+            /* a term's adjoint within the product (seed [1, 1] at the
+             * product): the group tree's reverse sweep, then the group's */
+            isum_value(P, k, X, p);
+            int ng = isum_groups(P, k, P->gstart);
+            tree_prod_adjoint(P->gsum, ng, mk(1.0, 1.0), P->gadj, p);
+            for (int g = 0; g < ng; g++)
+                tree_prod_adjoint(P->terms + P->gstart[g], P->gstart[g + 1] - P->gstart[g], P->gadj[g],
+                                  P->tseed + P->gstart[g], p);
+        }
         for (int j = c0; j < c1; j++) { P->dacc[j - c0] = mk(0.0, 0.0); P->touched[j - c0] = 0; }
         for (int q = 0; q < cnt; q++) {
             int i = s->b + q * s->d;
@@ -650,7 +739,7 @@ static void block_partials(oprob* P, obox X, int p, int blk, iv* G, int* width) 
             eval_term(P, k, i, X, p);
             int troot = s->a;
             for (int t = 0; t < P->tmpl_count[k]; t++) P->tadj[P->tmpl_nodes[k][t]] = mk(0.0, 0.0);
-            P->tadj[troot] = mk(1.0, 1.0);
+            P->tadj[troot] = prod ? P->tseed[q] : mk(1.0, 1.0);
             for (int t = P->tmpl_count[k] - 1; t >= 0; t--)
                 push_adjoint(P, P->tmpl_nodes[k][t], p, P->tval, P->tadj);
             for (int t = 0; t < P->tmpl_count[k]; t++) {
@@ -765,6 +854,27 @@ int oracle_iv_op(int op, const double* x, const double* y, double c, int p, doub
     default: return 1;
     }
     out[0] = r.lo; out[1] = r.hi;
+    return 0;
+}
+
+int oracle_tree_prod(const double* lo, const double* hi, int m, int p, double* out) {
+    iv* a = (iv*)malloc(sizeof(iv) * (m > 0 ? m : 1));
+    for (int i = 0; i < m; i++) a[i] = mk(lo[i], hi[i]);
+    iv r = tree_prod(a, m, p);
+    out[0] = r.lo; out[1] = r.hi;
+    free(a);
+    return 0;
+}
+
+int oracle_tree_prod_adjoint(const double* lo, const double* hi, int m, double seed_lo, double seed_hi, int p,
+                             double* out) {
+    iv* a = (iv*)malloc(sizeof(iv) * (m > 0 ? m : 1));
+    iv* g = (iv*)malloc(sizeof(iv) * (m > 0 ? m : 1));
+    for (int i = 0; i < m; i++) a[i] = mk(lo[i], hi[i]);
+    tree_prod_adjoint(a, m, mk(seed_lo, seed_hi), g, p);
+    for (int i = 0; i < m; i++) { out[2 * i] = g[i].lo; out[2 * i + 1] = g[i].hi; }
+    free(a);
+    free(g);
     return 0;
 }
 

@@ -8,17 +8,18 @@ independently, in the CUDA library and in ``oracle/``).
 Node layout (32 bytes, little endian, matches ``gb_node`` in include/gb.h):
 
     int32 op   operator code (OP_* below)
-    int32 a    first operand node | VAR coordinate | IDX_COEF table | ISUM template root
-    int32 b    second operand node | IDX_VAR / IDX_COEF index offset | ISUM first index
-    int32 c    ISUM end index (exclusive)
-    int32 d    ISUM index step (> 0)
+    int32 a    first operand node | VAR coordinate | IDX_COEF table | ISUM / IPROD template root
+    int32 b    second operand node | IDX_VAR / IDX_COEF index offset | ISUM / IPROD first index
+    int32 c    ISUM / IPROD end index (exclusive)
+    int32 d    ISUM / IPROD index step (> 0)
     int32 pad  zero
     f64   v    CONST value | SCALE factor
 
 Nodes are topologically ordered: every operand index is smaller than the node's
 own index.  An ISUM node sums a *template* sub-DAG over an index set
 {b, b+d, ...} < c; inside the template IDX_VAR(off) stands for x[i+off] and
-IDX_COEF(t, off) for table t at i+off.  The objective of Eq. 1 is the node
+IDX_COEF(t, off) for table t at i+off.  An IPROD node is the product of its
+template over the index set, laid out like ISUM.  The objective of Eq. 1 is the node
 given as ``root``; the simple bounds of Eq. 2 are passed beside it.
 """
 from __future__ import annotations
@@ -43,12 +44,14 @@ OP_SIN = 14
 OP_COS = 15
 OP_SCALE = 16
 OP_ISUM = 17
+OP_IPROD = 18
 
 OP_NAMES = {
     OP_CONST: "CONST", OP_PI: "PI", OP_EULER: "EULER", OP_VAR: "VAR",
     OP_IDX_VAR: "IDX_VAR", OP_IDX_COEF: "IDX_COEF", OP_ADD: "ADD", OP_SUB: "SUB",
     OP_MUL: "MUL", OP_DIV: "DIV", OP_NEG: "NEG", OP_SQR: "SQR", OP_SQRT: "SQRT",
     OP_EXP: "EXP", OP_SIN: "SIN", OP_COS: "COS", OP_SCALE: "SCALE", OP_ISUM: "ISUM",
+    OP_IPROD: "IPROD",
 }
 
 NODE_DTYPE = np.dtype([
@@ -128,6 +131,9 @@ class Dag:
 
     def isum(self, template_root: int, first: int, end: int, step: int = 1):
         return self._push(OP_ISUM, a=template_root, b=first, c=end, d=step)
+
+    def iprod(self, template_root: int, first: int, end: int, step: int = 1):
+        return self._push(OP_IPROD, a=template_root, b=first, c=end, d=step)
 
     # -- output -----------------------------------------------------------
     def nodes(self) -> np.ndarray:

@@ -315,6 +315,43 @@ def paper_rosenbrock(n: int = 10, tol_f: float = 0.0, block: int | None = None) 
                    block if block else min(n, 10), np.ones(n), 0, meta=dict(fstar=0.0))
 
 
+def paper_griewank(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S9-S10: 1 + sum_i x_i^2 / 4000 - prod_i cos(x_i / sqrt(i)) (i = 1..n), -100 <= x_i <= 110;
+    min 0 at x = 0.  sqrt(i) is the interval square root of the exact integer i (table 0)."""
+    g = Dag()
+    x = g.ivar(0)
+    idx = g.table(np.arange(1, n + 1, dtype=np.float64))
+    s1 = g.isum(g.div(g.sqr(x), g.const(4000.0)), 0, n, 1)
+    p1 = g.iprod(g.cos(g.div(x, g.sqrt(g.icoef(idx)))), 0, n, 1)
+    f = g.sub(g.add(g.const(1.0), s1), p1)
+    return Problem("paper_griewank", n, g.nodes(), f, g.tables, np.full(n, -100.0), np.full(n, 110.0), tol_f,
+                   block if block else min(n, 10), np.zeros(n), 0, meta=dict(fstar=0.0))
+
+
+def paper_styblinski(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S18-S19: (1 / (2n)) sum_i x_i^2 - 4n prod_i cos(x_i), -10 <= x_i <= 11; min -4n at x = 0."""
+    g = Dag()
+    x = g.ivar(0)
+    s1 = g.div(g.isum(g.sqr(x), 0, n, 1), g.const(2.0 * n))
+    p1 = g.iprod(g.cos(x), 0, n, 1)
+    f = g.sub(s1, g.scale(p1, 4.0 * n))
+    return Problem("paper_styblinski", n, g.nodes(), f, g.tables, np.full(n, -10.0), np.full(n, 11.0), tol_f,
+                   block if block else min(n, 10), np.zeros(n), 0, meta=dict(fstar=-4.0 * n))
+
+
+def paper_zabinsky(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S20-S21: -2.5 prod_i sin(x_i - pi/6) - prod_i sin(5 (x_i - pi/6)), 0 <= x_i <= pi;
+    min -3.5 at x = 2 pi / 3.  The upper bound is the double nearest pi (just below it)."""
+    g = Dag()
+    d = g.sub(g.ivar(0), g.div(g.pi(), g.const(6.0)))
+    p1 = g.iprod(g.sin(d), 0, n, 1)
+    p2 = g.iprod(g.sin(g.scale(d, 5.0)), 0, n, 1)
+    f = g.sub(g.scale(p1, -2.5), p2)
+    return Problem("paper_zabinsky", n, g.nodes(), f, g.tables, np.zeros(n), np.full(n, np.pi), tol_f,
+                   block if block else min(n, 10), np.full(n, 2.0 * np.pi / 3.0), 0, meta=dict(fstar=-3.5))
+
+
+FAMILIES.update(paper_griewank=paper_griewank, paper_styblinski=paper_styblinski, paper_zabinsky=paper_zabinsky)
 FAMILIES.update(paper_rastrigin=paper_rastrigin, paper_breiman=paper_breiman, paper_ackley=paper_ackley,
                 paper_belegundu=paper_belegundu, paper_fu=paper_fu, paper_levy=paper_levy,
                 paper_salomon=paper_salomon, paper_rosenbrock=paper_rosenbrock)

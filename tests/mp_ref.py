@@ -88,6 +88,8 @@ def _point_value_mp(p, xs):
             r = ev(a, i) * mpmath.mpf(float(q["v"]))
         elif op == D.OP_ISUM:
             r = mpmath.fsum(ev(a, k) for k in _isum_indices(q))
+        elif op == D.OP_IPROD:
+            r = mpmath.fprod(ev(a, k) for k in _isum_indices(q))
         else:
             raise ValueError(op)
         memo[key] = r
@@ -97,16 +99,16 @@ def _point_value_mp(p, xs):
 
 
 # -------------------------------------------------------------------------
-def _tree(vals):
-    """Pairwise reduction in index order (level s: a[i] += a[i+s])."""
+def _tree(vals, prod: bool = False):
+    """Pairwise reduction in index order (level s: a[i] = a[i] op a[i+s])."""
     a = list(vals)
     m = len(a)
     if m == 0:
-        return iv.mpf(0)
+        return iv.mpf(1 if prod else 0)
     s = 1
     while s < m:
         for i in range(0, m - s, 2 * s):
-            a[i] = a[i] + a[i + s]
+            a[i] = a[i] * a[i + s] if prod else a[i] + a[i + s]
         s *= 2
     return a[0]
 
@@ -162,19 +164,20 @@ def iv53_value(p, lo, hi, B: int):
             r = ev(a, i, memo) ** 2
         elif op == D.OP_SCALE:
             r = ev(a, i, memo) * iv.mpf(float(q["v"]))
-        elif op == D.OP_ISUM:
+        elif op in (D.OP_ISUM, D.OP_IPROD):
+            prod = op == D.OP_IPROD
             offs = _template_offsets(p, a)
             idx = _isum_indices(q)
             terms = [ev(a, k, {}) for k in idx]
             if not offs:
-                return _tree(terms)
+                return _tree(terms, prod)
             keys = [((k + min(offs)) // B, (k + max(offs)) // B) for k in idx]
             groups, start = [], 0
             for t in range(1, len(idx) + 1):
                 if t == len(idx) or keys[t] != keys[start]:
-                    groups.append(_tree(terms[start:t]))
+                    groups.append(_tree(terms[start:t], prod))
                     start = t
-            r = _tree(groups)
+            r = _tree(groups, prod)
         else:
             raise ValueError(f"unsupported op {op} in iv53_value")
         memo[(v, i)] = r

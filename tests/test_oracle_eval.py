@@ -57,6 +57,72 @@ def test_tree_sum_matches_exact_rational_rounding():
         assert O.tree_sum(lo, hi) == _exact_tree(lo, hi)
 
 
+def _exact_mul(a, b):
+    ps = [Fraction(x) * Fraction(y) for x in a for y in b]
+    return (_rd(min(ps)), _ru(max(ps)))
+
+
+def _exact_prod_tree(lo, hi):
+    a = [(float(l), float(h)) for l, h in zip(lo, hi)]
+    m = len(a)
+    s = 1
+    while s < m:
+        for i in range(0, m - s, 2 * s):
+            a[i] = _exact_mul(a[i], a[i + s])
+        s *= 2
+    return a[0] if m else (1.0, 1.0)
+
+
+def _random_intervals(rng, m):
+    mag = 2.0 ** rng.integers(-20, 20, m)
+    lo = rng.uniform(-1, 1, m) * mag
+    hi = lo + np.abs(rng.uniform(0, 1, m)) * mag
+    return lo, hi
+
+
+def test_tree_prod_matches_exact_rational_rounding():
+    # the IPROD reduction: the pairwise tree of tree_sum with products, each
+    # node the optimal outward rounding of the exact interval product
+    rng = np.random.default_rng(4)
+    for m in list(range(0, 20)) + [31, 32, 33, 50]:
+        lo, hi = _random_intervals(rng, m)
+        assert O.tree_prod(lo, hi) == _exact_prod_tree(lo, hi)
+
+
+def test_tree_prod_adjoint_closed_form_on_exact_points():
+    # d/dx_i prod_j x_j = prod_{j != i} x_j: with signed powers of two every
+    # product is exact, so the reverse sweep must give it exactly (a wrong
+    # partner, a skipped level or the item's own value fails here)
+    rng = np.random.default_rng(5)
+    for m in (1, 2, 3, 5, 7, 8, 13, 16, 21):
+        x = rng.choice([-1.0, 1.0], m) * 2.0 ** rng.integers(-6, 6, m)
+        seed = (0.75, 0.75)
+        adj = O.tree_prod_adjoint(x, x, seed)
+        for i in range(m):
+            want = 0.75 * float(np.prod(np.delete(x, i)))
+            assert adj[i, 0] == want == adj[i, 1], (m, i)
+
+
+def test_tree_prod_adjoint_encloses_partial_products():
+    # for interval items the adjoint of item i must enclose prod_{j != i} x_j
+    # at every point of the box (exact rational check at sampled points)
+    rng = np.random.default_rng(6)
+    for m in (2, 3, 6, 9, 17):
+        lo, hi = _random_intervals(rng, m)
+        adj = O.tree_prod_adjoint(lo, hi)
+        for _ in range(20):
+            t = rng.uniform(0, 1, m)
+            t[rng.integers(0, m)] = rng.integers(0, 2)
+            x = [Fraction(float(a)) + (Fraction(float(b)) - Fraction(float(a))) * Fraction(float(u))
+                 for a, b, u in zip(lo, hi, t)]
+            for i in range(m):
+                pr = Fraction(1)
+                for j in range(m):
+                    if j != i:
+                        pr *= x[j]
+                assert Fraction(adj[i, 0]) <= pr <= Fraction(adj[i, 1])
+
+
 def test_tree_sum_is_not_sequential():
     # 1 + 3 * 2^-53: sequential rounding down keeps 1, the pairwise tree
     # first adds the two small terms exactly
@@ -67,6 +133,45 @@ def test_tree_sum_is_not_sequential():
         seq = _rd(Fraction(seq) + Fraction(v))
     assert got == _exact_tree(lo, lo)
     assert got[0] != seq
+
+
+def _poly_product_problem(n):
+    """1 + prod_i (1 + a_i (x_i - x_{i+1})^2) - prod_i (x_i - c_i): polynomial IPROD templates."""
+    rng = np.random.default_rng(n)
+    g = S.Dag()
+    ta = g.table(rng.uniform(0.5, 2.0, n))
+    tc = g.table(rng.uniform(-1.0, 1.0, n))
+    t1 = g.add(g.const(1.0), g.mul(g.icoef(ta), g.sqr(g.sub(g.ivar(0), g.ivar(1)))))
+    t2 = g.sub(g.ivar(0), g.icoef(tc))
+    f = g.sub(g.add(g.const(1.0), g.iprod(t1, 0, n - 1, 1)), g.iprod(t2, 0, n, 1))
+    return S.Problem("poly_prod", n, g.nodes(), f, g.tables, np.full(n, -2.0), np.full(n, 3.0),
+                     1e-6, 3, np.zeros(n), 0)
+
+
+@pytest.mark.parametrize("n,B", [(3, 3), (7, 3), (12, 5), (21, 4)])
+def test_polynomial_product_F_bit_exact_vs_mpmath(n, B):
+    p = _poly_product_problem(n)
+    o = O.Oracle(p, block=B)
+    lo, hi = S.random_boxes(p, 30, seed=n + 7)
+    for k in range(len(lo)):
+        F, _, _, _ = o.eval_box(lo[k], hi[k])
+        assert tuple(F) == mp_ref.iv53_value(p, lo[k], hi[k], B)
+
+
+def test_polynomial_product_partials_contain_derivative():
+    p = _poly_product_problem(8)
+    B = 3
+    o = O.Oracle(p, block=B)
+    rng = np.random.default_rng(9)
+    lo, hi = S.random_boxes(p, 10, seed=19, min_width=1e-4)
+    for k in range(len(lo)):
+        blk = k % 3
+        F, _, G, _ = o.eval_box(lo[k], hi[k], blk=blk)
+        for x in _sample_points(rng, lo[k], hi[k], 3):
+            assert F[0] <= mp_ref.point_value(p, x) <= F[1]
+            for t in range(min(B, p.n - blk * B)):
+                gx = mp_ref.point_grad(p, x, blk * B + t)
+                assert G[t, 0] <= gx + mpmath.mpf(1e-30) and gx - mpmath.mpf(1e-30) <= G[t, 1]
 
 
 @pytest.mark.parametrize("n,B", [(2, 2), (5, 3), (7, 3), (12, 5), (20, 10), (33, 10)])
@@ -103,7 +208,8 @@ def _sample_points(rng, lo, hi, count):
 
 
 CASES = [("sep_cos", dict(n=3)), ("chain", dict(n=6)), ("ackley", dict(n=4)),
-         ("mixed", dict(n=7)), ("paper_rastrigin", dict(n=3)), ("paper_breiman", dict(n=3))]
+         ("mixed", dict(n=7)), ("paper_rastrigin", dict(n=3)), ("paper_breiman", dict(n=3)),
+         ("paper_griewank", dict(n=5)), ("paper_styblinski", dict(n=4)), ("paper_zabinsky", dict(n=5))]
 
 
 @pytest.mark.parametrize("f32", [False, True])

@@ -1,7 +1,7 @@
 """Pins of the oracle's branch and bound (section 3.1, variable cycling of
 section 3.2) against what the paper and the mathematics fix:
 
-* the paper's own iteration and region counts (Tables S4, S7, Table 1),
+* the paper's own iteration and region counts (Table 2, Tables S2-S10),
   reproduced per cycling block in paper mode;
 * the planted minimum (closed form min f = 0 at s) and the enclosure width;
 * a separable problem against its 1-D sub-problems solved separately;
@@ -37,7 +37,7 @@ def _covers(res, x):
 
 
 PAPER_FAMILIES = ["paper_rastrigin", "paper_breiman", "paper_ackley", "paper_belegundu", "paper_fu",
-                  "paper_levy", "paper_salomon"]
+                  "paper_levy", "paper_salomon", "paper_griewank", "paper_styblinski", "paper_zabinsky"]
 
 
 def _fstar(p):
