@@ -52,26 +52,29 @@ typedef enum gb_status {
 /* ---------------------------------------------------------------------- */
 /* Node operators.  Nodes are topologically ordered (operand index < node
  * index).  ISUM(a = template root, b = first, c = end, d = step) is the sum
- * over i in {b, b+d, ...} < c of the template sub-DAG rooted at a, in which
+ * over i in {b, b+d, ...} < c of the template sub-DAG rooted at a, and
+ * IPROD (same fields) the product (the Griewank, Styblinski and Zabinsky
+ * functions of the paper's SI Appendix A; IPROD problems run on the
+ * interpreter kernels, eval_mode 0 or 1).  In a template
  * IDX_VAR(b = offset) stands for x[i+offset] and IDX_COEF(a = table,
  * b = offset) for coef_tables[a][i+offset].  CONST(v) is the exact double v;
  * PI and EULER are the constants pi and e, enclosed by adjacent doubles;
  * SCALE(a, v) multiplies node a by the exact double v.  Template nodes may
- * not use VAR or ISUM; outer nodes may not use IDX_VAR or IDX_COEF. */
+ * not use VAR, ISUM or IPROD; outer nodes may not use IDX_VAR or IDX_COEF. */
 enum {
     GB_OP_CONST = 0, GB_OP_PI = 1, GB_OP_EULER = 2, GB_OP_VAR = 3,
     GB_OP_IDX_VAR = 4, GB_OP_IDX_COEF = 5, GB_OP_ADD = 6, GB_OP_SUB = 7,
     GB_OP_MUL = 8, GB_OP_DIV = 9, GB_OP_NEG = 10, GB_OP_SQR = 11,
     GB_OP_SQRT = 12, GB_OP_EXP = 13, GB_OP_SIN = 14, GB_OP_COS = 15,
-    GB_OP_SCALE = 16, GB_OP_ISUM = 17
+    GB_OP_SCALE = 16, GB_OP_ISUM = 17, GB_OP_IPROD = 18
 };
 
 typedef struct gb_node {
     int32_t op;   /* GB_OP_* */
-    int32_t a;    /* operand 1 | VAR coordinate | IDX_COEF table | ISUM template root */
-    int32_t b;    /* operand 2 | IDX_VAR / IDX_COEF offset | ISUM first index */
-    int32_t c;    /* ISUM end index (exclusive) */
-    int32_t d;    /* ISUM step (>= 1) */
+    int32_t a;    /* operand 1 | VAR coordinate | IDX_COEF table | ISUM / IPROD template root */
+    int32_t b;    /* operand 2 | IDX_VAR / IDX_COEF offset | ISUM / IPROD first index */
+    int32_t c;    /* ISUM / IPROD end index (exclusive) */
+    int32_t d;    /* ISUM / IPROD step (>= 1) */
     int32_t pad;  /* must be 0 */
     double v;     /* CONST value | SCALE factor */
 } gb_node;

@@ -218,6 +218,13 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         delete p;
         return fail(GB_E_INVALID, err);
     }
+    if (p->hp.any_prod) {   // products run on the bytecode interpreter only
+        if (opt.eval_mode >= 2) {
+            delete p;
+            return fail(GB_E_INVALID, "IPROD problems need eval_mode 0 or 1");
+        }
+        p->opt.eval_mode = opt.eval_mode = 1;
+    }
     // term-table layouts also set each sum's tree offsets: build them before
     // the program is uploaded
     if (opt.eval_mode != 1) {
@@ -263,7 +270,8 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     P.n_outer = (int)H.outer.size();
     P.outer_root = H.outer_root;
     P.n_var_leaves = (int)H.var_leaves.size();
-    P.outer_sum = (H.outer.size() == 1 && H.outer[0].op == D_ISUMV && H.outer_root == 0) ? 1 : 0;
+    P.outer_sum = (H.outer.size() == 1 && H.outer[0].op == D_ISUMV && H.outer_root == 0 && !H.any_prod) ? 1 : 0;
+    P.any_prod = H.any_prod;
     P.samples = opt.samples;
     P.mono_all = opt.mono_all ? 1 : 0;
     GbIns *d_outer, *d_tins;
@@ -369,7 +377,7 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     } else {
         size_t per_slot = (size_t)n * 16 + (fp32 ? (size_t)n * 8 : 0) + (size_t)NG * 32 + (fp32 ? (size_t)NG * 8 : 0) +
                           4 + 2 * 16 + (size_t)opt.samples * NG * 16 +
-                          (opt.mono_all ? (size_t)P.n_sum * n * 16 : 0);
+                          (opt.mono_all && !H.any_prod ? (size_t)P.n_sum * n * 16 : 0);
         cap = opt.max_boxes > 0 ? opt.max_boxes : (long long)(opt.pool_bytes / per_slot);
         if (cap < 1) return bad(cudaErrorMemoryAllocation, "pool budget below one box");
         if (cap > (1LL << 31) - 1) cap = (1LL << 31) - 1;
@@ -382,7 +390,7 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
                 (e = alloc(&pl.gsum32, (size_t)cap * NG, A)))
                 return bad(e, "allocate box pool");
         }
-        if (opt.mono_all && P.n_sum > 0) {   // cached coordinate partials for the all-coordinate test
+        if (opt.mono_all && P.n_sum > 0 && !H.any_prod) {   // cached coordinate partials (sums only)
             if ((e = alloc(&pl.gdp, (size_t)cap * P.n_sum * n, A))) return bad(e, "allocate box pool");
         }
         if (opt.samples > 0) {   // cached group sums at every diagonal sample

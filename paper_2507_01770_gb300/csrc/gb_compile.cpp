@@ -98,7 +98,7 @@ bool mark_outer(Ctx& c, int v, std::string& err) {
         err = "IDX_VAR / IDX_COEF node " + std::to_string(v) + " used outside a sum template";
         return false;
     }
-    if (q.op == GB_OP_ISUM) return true;
+    if (q.op == GB_OP_ISUM || q.op == GB_OP_IPROD) return true;
     int k = n_operands(q.op);
     if (k >= 1 && !mark_outer(c, q.a, err)) return false;
     if (k >= 2 && !mark_outer(c, q.b, err)) return false;
@@ -109,8 +109,8 @@ bool mark_template(Ctx& c, int v, std::string& err) {
     if (c.mark[v]) return true;
     c.mark[v] = 1;
     const gb_node& q = c.nd[v];
-    if (q.op == GB_OP_VAR || q.op == GB_OP_ISUM) {
-        err = "VAR / ISUM node " + std::to_string(v) + " inside a sum template";
+    if (q.op == GB_OP_VAR || q.op == GB_OP_ISUM || q.op == GB_OP_IPROD) {
+        err = "VAR / ISUM / IPROD node " + std::to_string(v) + " inside a sum template";
         return false;
     }
     int k = n_operands(q.op);
@@ -129,7 +129,7 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
     if (ntab < 0) return "negative table count";
     for (int v = 0; v < nn; v++) {
         const gb_node& q = nd[v];
-        if (q.op < 0 || q.op > GB_OP_ISUM) return "unknown operator at node " + std::to_string(v);
+        if (q.op < 0 || q.op > GB_OP_IPROD) return "unknown operator at node " + std::to_string(v);
         if (q.pad != 0) return "nonzero pad at node " + std::to_string(v);
         int k = n_operands(q.op);
         if (k >= 1 && (q.a < 0 || q.a >= v)) return "operand not before node " + std::to_string(v);
@@ -137,8 +137,8 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
         if ((q.op == GB_OP_CONST || q.op == GB_OP_SCALE) && !std::isfinite(q.v))
             return "non-finite constant at node " + std::to_string(v);
         if (q.op == GB_OP_VAR && (q.a < 0 || q.a >= n)) return "VAR coordinate out of range";
-        if (q.op == GB_OP_ISUM && (q.a < 0 || q.a >= v || q.d < 1))
-            return "bad ISUM at node " + std::to_string(v);
+        if ((q.op == GB_OP_ISUM || q.op == GB_OP_IPROD) && (q.a < 0 || q.a >= v || q.d < 1))
+            return "bad ISUM / IPROD at node " + std::to_string(v);
     }
     Ctx c{nd, nn, std::vector<char>(nn, 0), std::vector<char>(nn, 0)};
     std::string err;
@@ -147,6 +147,7 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
     P->n = n;
     P->B = B;
     P->nb = (n + B - 1) / B;
+    P->any_prod = 0;
     P->outer.clear(); P->tins.clear(); P->sums.clear(); P->groups.clear();
     P->dirty.clear(); P->var_leaves.clear();
 
@@ -173,9 +174,9 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
             I.aux = q.a;
             P->var_leaves.push_back(GbVarLeaf{oreg[v], q.a});
         }
-        if (q.op != GB_OP_ISUM) continue;
+        if (q.op != GB_OP_ISUM && q.op != GB_OP_IPROD) continue;
 
-        // ---- an ISUM node: its template -----------------------------------
+        // ---- an ISUM / IPROD node: its template ---------------------------
         int ks = (int)P->sums.size();
         if (ks >= GB_MAX_ISUM) return "too many sums";
         I.aux = ks;
@@ -183,6 +184,8 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
         if (!mark_template(c, q.a, err)) return err;
         std::vector<int> treg(nn, -1);
         GbSum S{};
+        S.prod = q.op == GB_OP_IPROD ? 1 : 0;
+        if (S.prod) P->any_prod = 1;
         S.ins0 = (int)P->tins.size();
         int omin = 0, omax = 0, hv = 0, nleaf = 0;
         for (int t = 0; t <= q.a; t++) {
@@ -332,6 +335,7 @@ void gb_build_tables(GbHostProg* P, int m, int d, int sbits) {
     P->max_srows = 0;
     P->max_nseg = 0;
     P->max_rows = P->max_dterm = 0;
+    if (P->any_prod) return;   // the tables hold sums only: products run on the interpreter
     const int n = P->n, B = P->B, ns = (int)P->sums.size();
     int node = 0, max_leaves = 0;
     for (GbSum& S : P->sums) {

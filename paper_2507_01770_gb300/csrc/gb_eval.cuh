@@ -117,15 +117,20 @@ struct SampleView {
 };
 
 // Binary-counter pairwise tree.
-template <typename I> struct Tree {
+template <typename I, bool PROD = false> struct Tree {
     I lvl[20];
     unsigned cnt;
+    // the tree's operation: sums (ISUM) or products (IPROD)
+    __device__ __forceinline__ static I comb(I a, I b) {
+        if constexpr (PROD) return imul(a, b);
+        else return iadd(a, b);
+    }
     __device__ __forceinline__ void init() { cnt = 0; }
     __device__ __forceinline__ void push(I v) {
         unsigned c = cnt;
         int L = 0;
         while (c & 1u) {
-            v = iadd(lvl[L], v);
+            v = comb(lvl[L], v);
             c >>= 1;
             L++;
         }
@@ -139,7 +144,7 @@ template <typename I> struct Tree {
         unsigned c = cnt >> L;
         int lev = L;
         while (c & 1u) {
-            v = iadd(lvl[lev], v);
+            v = comb(lvl[lev], v);
             c >>= 1;
             lev++;
         }
@@ -148,11 +153,11 @@ template <typename I> struct Tree {
     }
     __device__ __forceinline__ I result() const {
         I r;
-        if (!cnt) { r.lo = 0; r.hi = 0; return r; }
+        if (!cnt) { r.lo = PROD ? 1 : 0; r.hi = PROD ? 1 : 0; return r; }
         // levels present in ascending order (the set bits of cnt)
         unsigned c = cnt;
         r = lvl[__ffs(c) - 1];
-        for (c &= c - 1; c; c &= c - 1) r = iadd(lvl[__ffs(c) - 1], r);
+        for (c &= c - 1; c; c &= c - 1) r = comb(lvl[__ffs(c) - 1], r);
         return r;
     }
 };
@@ -280,35 +285,78 @@ __device__ __forceinline__ void reverse_sweep(const GbIns* ins, int nins, const 
     }
 }
 
-// Sum of the terms of one group (local group g of sum S).
-template <typename T, typename V>
-__device__ __forceinline__ typename Prec<T>::I group_sum(const GbProg& P, const GbSum& S, int g, const V& X,
-                                                          typename Prec<T>::I* R, int& ops) {
+// Sum (IPROD: product) of the terms of one group (local group g of sum S).
+template <bool PROD, typename T, typename V>
+__device__ __forceinline__ typename Prec<T>::I group_reduce(const GbProg& P, const GbSum& S, int g, const V& X,
+                                                             typename Prec<T>::I* R, int& ops) {
     typedef typename Prec<T>::I I;
     GbGroup G = P.groups[S.group0 + g];
-    Tree<I> tr;
+    Tree<I, PROD> tr;
     tr.init();
     for (int t = 0; t < G.count; t++) tr.push(term_fwd<T>(P, S, S.first + (G.t0 + t) * S.step, X, R, ops));
-    ops += 2 * (G.count > 0 ? G.count - 1 : 0);
+    ops += (PROD ? 8 : 2) * (G.count > 0 ? G.count - 1 : 0);
+    return tr.result();
+}
+
+// PR: the program may hold IPROD reductions (kernels are instantiated for
+// both, so sum-only programs carry no product code).
+template <bool PR, typename T, typename V>
+__device__ __forceinline__ typename Prec<T>::I group_sum(const GbProg& P, const GbSum& S, int g, const V& X,
+                                                          typename Prec<T>::I* R, int& ops) {
+    if constexpr (PR) {
+        if (S.prod) return group_reduce<true, T>(P, S, g, X, R, ops);
+    }
+    return group_reduce<false, T>(P, S, g, X, R, ops);
+}
+
+// Value of product k: the groups dirty for block blk recomputed, the others
+// from `cache` (NULL: all recomputed), reduced by the product tree.
+template <typename T, typename V, typename C>
+__device__ __noinline__ typename Prec<T>::I prod_value(const GbProg& P, int k, int blk, const V& X,
+                                                        const CacheRef<C>* cache, typename Prec<T>::I* R,
+                                                        int& ops) {
+    typedef typename Prec<T>::I I;
+    const GbSum S = P.sums[k];
+    const int2 dr = cache ? (blk >= 0 ? P.dirty[blk * P.n_sum + k] : make_int2(0, 0)) : make_int2(0, S.ngroups);
+    Tree<I, true> tr;
+    tr.init();
+    for (int g = 0; g < S.ngroups; g++) {
+        I v;
+        if (g >= dr.x && g < dr.y) {
+            v = group_reduce<true, T>(P, S, g, X, R, ops);
+        } else {
+            C c = (*cache)[S.group0 + g];
+            v.lo = c.x;
+            v.hi = c.y;
+        }
+        tr.push(v);
+    }
+    ops += 8 * (S.ngroups > 0 ? S.ngroups - 1 : 0);
     return tr.result();
 }
 
 // Value of every sum: dirty groups recomputed, the others read from `cache`
 // (one interval per global group; NULL: recompute everything).
-template <typename T, typename V, typename C>
+template <bool PR, typename T, typename V, typename C>
 __device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X, const CacheRef<C>* cache,
                                            typename Prec<T>::I* R, typename Prec<T>::I* sums, int& ops) {
     typedef typename Prec<T>::I I;
     for (int k = 0; k < P.n_sum; k++) {
         GbSum S = P.sums[k];
         // with a cache: the dirty groups of block blk recomputed (blk < 0: none)
+        if constexpr (PR) {
+            if (S.prod) {
+                sums[k] = prod_value<T>(P, k, blk, X, cache, R, ops);
+                continue;
+            }
+        }
         int2 dr = cache ? (blk >= 0 ? P.dirty[blk * P.n_sum + k] : make_int2(0, 0)) : make_int2(0, S.ngroups);
         Tree<I> tr;
         tr.init();
         for (int g = 0; g < S.ngroups; g++) {
             I v;
             if (g >= dr.x && g < dr.y) {
-                v = group_sum<T>(P, S, g, X, R, ops);
+                v = group_reduce<false, T>(P, S, g, X, R, ops);
             } else {
                 C c = (*cache)[S.group0 + g];
                 v.lo = c.x;
@@ -319,6 +367,65 @@ __device__ __forceinline__ void sum_values(const GbProg& P, int blk, const V& X,
         ops += 2 * (S.ngroups > 0 ? S.ngroups - 1 : 0);
         sums[k] = tr.result();
     }
+}
+
+// ---- IPROD adjoints ----
+// Adjoint of item q of the pairwise product tree over m items (the tree of
+// Tree<I, true>) when the product has adjoint a: reverse mode over the
+// tree's products, where every node feeds one product, so each level
+// multiplies the adjoint by the value of the node's partner (the product of
+// a run of items), taken from the top level down.  get(i) gives item i.
+template <typename I, typename G>
+__device__ __forceinline__ I tree_item_adjoint(I a, int m, int q, const G& get, int& ops) {
+    int plo[20], phi[20], np = 0;
+    int h = q;   // q's node at level s starts at item h (a multiple of s)
+    for (int s = 1; s < m; s <<= 1) {
+        if ((h & (2 * s - 1)) == 0) {   // left operand: partner [h + s, h + 2s) if present
+            if (h + s < m) plo[np] = h + s, phi[np] = min(h + 2 * s, m), np++;
+        } else {                        // right operand of the node at h - s
+            plo[np] = h - s, phi[np] = h, np++;
+            h -= s;
+        }
+    }
+    for (int t = np - 1; t >= 0; t--) {
+        Tree<I, true> tr;
+        tr.init();
+        for (int i = plo[t]; i < phi[t]; i++) tr.push(get(i));
+        ops += 8 * (phi[t] - plo[t]);
+        a = imul(a, tr.result());
+    }
+    return a;
+}
+
+// The adjoint, within product S (seed [1, 1] at the product), of its term
+// with ordinal tt: through the tree over the groups, then through the
+// group's own tree.  Group values: from `cache` except the groups dirty for
+// block dblk (all recomputed without a cache).
+template <typename T, typename V, typename C>
+__device__ __noinline__ typename Prec<T>::I prod_term_seed(const GbProg& P, int ks, int tt, const V& X,
+                                                            const CacheRef<C>* cache, int dblk,
+                                                            typename Prec<T>::I* R, int& ops) {
+    typedef typename Prec<T>::I I;
+    const GbSum S = P.sums[ks];
+    int gl = 0;
+    while (gl + 1 < S.ngroups && P.groups[S.group0 + gl + 1].t0 <= tt) gl++;
+    const GbGroup G = P.groups[S.group0 + gl];
+    const int2 dr = cache ? (dblk >= 0 ? P.dirty[dblk * P.n_sum + ks] : make_int2(0, 0)) : make_int2(0, S.ngroups);
+    auto gval = [&](int g) {
+        I v;
+        if (g >= dr.x && g < dr.y) {
+            v = group_reduce<true, T>(P, S, g, X, R, ops);
+        } else {
+            C c = (*cache)[S.group0 + g];
+            v.lo = c.x;
+            v.hi = c.y;
+        }
+        return v;
+    };
+    auto tval = [&](int t) { return term_fwd<T>(P, S, S.first + (G.t0 + t) * S.step, X, R, ops); };
+    I a = mk<T>((T)1, (T)1);
+    a = tree_item_adjoint(a, S.ngroups, gl, gval, ops);
+    return tree_item_adjoint(a, G.count, tt - G.t0, tval, ops);
 }
 
 // Outer forward pass; O receives all outer registers, returns F.
@@ -364,12 +471,14 @@ __device__ __forceinline__ typename Prec<T>::I outer_fwd(const GbProg& P, const 
 // true if some partial excludes 0 with the corresponding face off the domain
 // edge.  X64 gives the FP64 box for the edge comparison.  G (optional)
 // receives the partials of the block.  Needs the outer registers O of the
-// forward pass.
-template <typename T, typename V>
+// forward pass.  A product's term templates are seeded with the term's
+// adjoint in the product (prod_term_seed; group values from gcache except
+// the groups dirty for block dblk, all recomputed when gcache is null).
+template <bool PR, typename T, typename V, typename C>
 __device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X, const View<double>& X64,
                                            const typename Prec<T>::I* O, typename Prec<T>::I* OA,
                                            typename Prec<T>::I* R, typename Prec<T>::I* RA,
-                                           double* Gout, int& ops) {
+                                           double* Gout, const CacheRef<C>* gcache, int dblk, int& ops) {
     typedef typename Prec<T>::I I;
     // outer adjoints
     for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
@@ -401,9 +510,13 @@ __device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X,
             if (!S.has_var) continue;
             while (cur[k] < S.count && S.first + cur[k] * S.step + S.off_min <= j) {
                 int i = S.first + cur[k] * S.step;
+                I seed = mk<T>((T)1, (T)1);
+                if constexpr (PR) {
+                    if (S.prod) seed = prod_term_seed<T>(P, k, cur[k], X, gcache, dblk, R, ops);
+                }
                 term_fwd<T>(P, S, i, X, R, ops);
                 for (int t = 0; t < S.nins; t++) RA[t] = mk<T>((T)0, (T)0);
-                RA[S.nins - 1] = mk<T>((T)1, (T)1);
+                RA[S.nins - 1] = seed;
                 const GbIns* ins = P.tins + S.ins0;
                 reverse_sweep<T>(ins, S.nins, R, RA, ops);
                 for (int t = 0; t < S.nins; t++) {

@@ -41,13 +41,14 @@ struct GbIns {
     double c;         // CONST value | SCALE factor
 };  // 32 bytes
 
-// One ISUM node: its template bytecode and the grouping of its terms.
+// One ISUM (or IPROD) node: its template bytecode and the grouping of its terms.
 // Terms are grouped into maximal runs with the same range of touched
 // cycling blocks; the cached partial sums of a box are kept per group.
 struct GbSum {
     int32_t ins0, nins;      // template instructions [ins0, ins0 + nins)
     int32_t first, step, count;  // index set {first + t * step : t < count}
     int32_t off_min, off_max, has_var;
+    int32_t prod;            // 1: IPROD (product of the terms; empty product [1, 1])
     int32_t group0, ngroups; // global group ids [group0, group0 + ngroups)
     int32_t outer_reg;       // outer register receiving the sum
     int32_t nvar_leaves;     // IVAR instructions in the template
@@ -158,6 +159,7 @@ struct GbProg {
     int32_t outer_sum;               // 1: the outer expression is one sum (F = that sum, adjoint [1, 1])
     int32_t samples;                 // GUB samples per box (0: midpoint; S: diagonal points j / (S + 1))
     int32_t mono_all;                // first-order test on every coordinate
+    int32_t any_prod;                // some reduction is an IPROD
 };
 
 // Host-side compiled program (arrays in host memory before upload).
@@ -167,6 +169,7 @@ struct GbProg {
 struct GbHostProg {
     int32_t n = 0, B = 0, nb = 0;
     int32_t outer_root = 0;
+    int32_t any_prod = 0;
     std::vector<GbIns> outer, tins;
     std::vector<GbSum> sums;
     std::vector<GbGroup> groups;

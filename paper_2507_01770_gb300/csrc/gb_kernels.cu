@@ -56,6 +56,7 @@ __device__ __forceinline__ int block_prefix(bool f, int* smem_warp, int* total) 
 
 // ---------------------------------------------------------------------------
 // Root box: the whole domain [l, u] (section 3.1 "initialization").
+template <bool PR>
 __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, GbState* st) {
     const int n = P.n;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -94,16 +95,16 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
         for (int g = threadIdx.x; g < S.ngroups; g += blockDim.x) {
             const int gg = S.group0 + g;
             const size_t at = pool.recs ? (size_t)P.gown[gg].x * pool.GPB + P.gown[gg].y : (size_t)gg;
-            iv64 a = group_sum<double>(P, S, g, X, R, ops);
-            iv64 b = group_sum<double>(P, S, g, MX, R, ops);
+            iv64 a = group_sum<PR, double>(P, S, g, X, R, ops);
+            iv64 b = group_sum<PR, double>(P, S, g, MX, R, ops);
             (pool.recs ? pool.rgsum : pool.gsum)[at] = make_double2(a.lo, a.hi);
             (pool.recs ? pool.rgmid : pool.gmid)[at] = make_double2(b.lo, b.hi);
             if (pool.fp32) {
-                iv32 c = group_sum<float>(P, S, g, X32, R32, ops);
+                iv32 c = group_sum<PR, float>(P, S, g, X32, R32, ops);
                 (pool.recs ? pool.rgsum32 : pool.gsum32)[at] = make_float2(c.lo, c.hi);
             }
             for (int j = 1; pool.gsamp && j <= pool.S; j++) {
-                const iv64 v = group_sum<double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
+                const iv64 v = group_sum<PR, double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
                 pool.gsamp[(size_t)(j - 1) * pool.NG + gg] = make_double2(v.lo, v.hi);
             }
         }
@@ -118,7 +119,7 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
     // group values and tree as a full evaluation)
     iv64 sums[GB_MAX_ISUM], O[GB_MAX_OREGS];
     const CacheRef<double2> cf = cache64(pool, P, 0, 0), cm = cache64(pool, P, 0, 1);
-    sum_values<double>(P, -1, X, &cf, R, sums, ops);
+    sum_values<PR, double>(P, -1, X, &cf, R, sums, ops);
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
     double gub = __longlong_as_double(0x7ff0000000000000LL);
     long long nsamp = 1;
@@ -127,12 +128,12 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
         for (int j = 1; j <= P.samples; j++) {
             const SampleView SV{X, j, P.samples + 1};
             const CacheRef<double2> cs{pool.gsamp + (size_t)(j - 1) * pool.NG, nullptr, nullptr, 0};
-            sum_values<double>(P, -1, SV, pool.gsamp ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
+            sum_values<PR, double>(P, -1, SV, pool.gsamp ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
             const iv64 Fs = outer_fwd<double>(P, SV, sums, O, ops);
             if (Fs.hi < gub) gub = Fs.hi;
         }
     } else {
-        sum_values<double>(P, -1, MX, &cm, R, sums, ops);
+        sum_values<PR, double>(P, -1, MX, &cm, R, sums, ops);
         const iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
         if (Fm.hi == Fm.hi) gub = Fm.hi;
     }
@@ -512,13 +513,15 @@ __global__ void k_prep(GbProg P, GbPool pool, GbParents par, GbSplit sp, GbState
 
 // FP64 child evaluation: midpoint sample, F(X), first-order test.
 // First-order test: the active block, or every block (mono_all).
-template <typename T, typename V>
+// gc: the parent's cached group values (groups dirty for blk recomputed).
+template <bool PR, typename T, typename V, typename C>
 __device__ __forceinline__ bool mono_any(const GbProg& P, int blk, const V& X, const View<double>& X64,
                                          const typename Prec<T>::I* O, typename Prec<T>::I* OA,
-                                         typename Prec<T>::I* R, typename Prec<T>::I* RA, int& ops) {
-    if (!P.mono_all) return block_mono<T>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr, ops);
+                                         typename Prec<T>::I* R, typename Prec<T>::I* RA,
+                                         const CacheRef<C>* gc, int& ops) {
+    if (!P.mono_all) return block_mono<PR, T>(P, blk, X, X64, O, OA, R, RA, (double*)nullptr, gc, blk, ops);
     for (int b = 0; b < P.nb; b++)
-        if (block_mono<T>(P, b, X, X64, O, OA, R, RA, (double*)nullptr, ops)) return true;
+        if (block_mono<PR, T>(P, b, X, X64, O, OA, R, RA, (double*)nullptr, gc, blk, ops)) return true;
     return false;
 }
 
@@ -532,7 +535,9 @@ __device__ __noinline__ bool mono_cached(const GbProg& P, const GbPool& pool, un
     const int2 ab = d_affected(P, blk);
     const double2* row = pool.gdp + (size_t)slot * P.n_sum * P.n;
     for (int b = ab.x; b <= ab.y; b++)   // also leaves the outer adjoints in OA
-        if (block_mono<double>(P, b, X, X, O, OA, R, RA, (double*)nullptr, ops)) return true;
+        if (block_mono<false, double>(P, b, X, X, O, OA, R, RA, (double*)nullptr, (const CacheRef<double2>*)nullptr, -1,
+                               ops))
+            return true;
     for (int b = 0; b < P.nb; b++) {
         if (b >= ab.x && b <= ab.y) continue;
         if (cached_mono(P, b, X, OA, row, ops)) return true;
@@ -540,6 +545,7 @@ __device__ __noinline__ bool mono_cached(const GbProg& P, const GbPool& pool, un
     return false;
 }
 
+template <bool PR>
 __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool, const GbParents& par,
                                              const GbChildren& ch, long long ci, const GbSplit& sp,
                                              double gub_prev, unsigned long long* gkey, bool* has_key,
@@ -561,7 +567,7 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
             // the child's sample j agrees with its parent's on every coordinate
             // it did not split: the groups off the split block come from the cache
             const CacheRef<double2> cs{pool.gsamp + ((size_t)c.slot * pool.S + (j - 1)) * pool.NG, nullptr, nullptr, 0};
-            sum_values<double>(P, blk, SV, pool.gsamp ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
+            sum_values<PR, double>(P, blk, SV, pool.gsamp ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
             const iv64 Fs = outer_fwd<double>(P, SV, sums, O, ops);
             if (Fs.hi == Fs.hi) {
                 const unsigned long long k = gb_order_key(Fs.hi);
@@ -570,24 +576,25 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
             }
         }
     } else {
-        sum_values<double>(P, blk, MX, &cm, R, sums, ops);
+        sum_values<PR, double>(P, blk, MX, &cm, R, sums, ops);
         iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
         if (Fm.hi == Fm.hi) {
             *gkey = gb_order_key(Fm.hi);
             *has_key = true;
         }
     }
-    sum_values<double>(P, blk, X, &cf, R, sums, ops);
+    sum_values<PR, double>(P, blk, X, &cf, R, sums, ops);
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
     bool keep = !(F.lo > gub_prev);
     if (keep)
         keep = !(pool.gdp ? mono_cached(P, pool, c.slot, blk, X, O, OA, R, RA, ops)
-                          : mono_any<double>(P, blk, X, X, O, OA, R, RA, ops));
+                          : mono_any<PR, double>(P, blk, X, X, O, OA, R, RA, &cf, ops));
     ch.flo[ci] = canon_lo(F.lo);
     ch.flag[ci] = keep ? 1 : 0;
     return true;
 }
 
+template <bool PR>
 __global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents par, GbChildren ch, GbSplit sp,
                                                 int from_list, GbState* st) {
     if (st->halt) return;
@@ -603,7 +610,7 @@ __global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents
         int ops = 0;
         if (idx < lim) {
             long long ci = from_list ? (long long)ch.list32[idx] : idx;
-            valid = eval64_child(P, pool, par, ch, ci, sp, gub_prev, &key, &has, ops);
+            valid = eval64_child<PR>(P, pool, par, ch, ci, sp, gub_prev, &key, &has, ops);
         }
         warp_min_gub(key, has, st);
         warp_add_ops(ops, &st->ops64);
@@ -618,6 +625,7 @@ __global__ void __launch_bounds__(128) k_eval64(GbProg P, GbPool pool, GbParents
 
 // FP32 prefilter: F(X) and the first-order test in FP32 directed rounding,
 // cut-off against the GUB of the previous generation.
+template <bool PR>
 __global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents par, GbChildren ch, GbSplit sp,
                                                 GbState* st) {
     if (st->halt) return;
@@ -639,10 +647,10 @@ __global__ void __launch_bounds__(128) k_eval32(GbProg P, GbPool pool, GbParents
                 iv32 R[GB_MAX_TREGS], RA[GB_MAX_TREGS], O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
                 const int blk = c.info.z;
                 const CacheRef<float2> c32 = cache32(pool, P, c.slot);
-                sum_values<float>(P, blk, X, &c32, R, sums, ops);
+                sum_values<PR, float>(P, blk, X, &c32, R, sums, ops);
                 iv32 F = outer_fwd<float>(P, X, sums, O, ops);
                 bool keep = !((double)F.lo > gub_prev);
-                if (keep) keep = !mono_any<float>(P, blk, X, X64, O, OA, R, RA, ops);
+                if (keep) keep = !mono_any<PR, float>(P, blk, X, X64, O, OA, R, RA, &c32, ops);
                 ch.flag32[ci] = keep ? 1 : 0;
             } else {
                 ch.flag32[ci] = 0;
@@ -749,6 +757,7 @@ __device__ __forceinline__ void tab_dirty_groups(const GbProg& P, const GbPool& 
 // ---------------------------------------------------------------------------
 // Survivors into free slots: coordinates, FP32 shadow, group caches (dirty
 // groups recomputed, the rest copied from the parent), pool entry.
+template <bool PR>
 __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                 const GbChildren& ch, const GbSplit& sp, const GbEntries& En,
                                                 double tol_x, const GbState* st, long long s, int lane,
@@ -804,17 +813,17 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
                 b = iv64{shM[at].x, shM[at].y};
                 if (pool.fp32) pool.gsum32[dst] = sh32[at];
             } else {
-                a = group_sum<double>(P, S, g, X, R, ops);
-                b = group_sum<double>(P, S, g, MX, R, ops);
+                a = group_sum<PR, double>(P, S, g, X, R, ops);
+                b = group_sum<PR, double>(P, S, g, MX, R, ops);
                 if (pool.fp32) {
-                    iv32 f = group_sum<float>(P, S, g, X32, R32, ops);
+                    iv32 f = group_sum<PR, float>(P, S, g, X32, R32, ops);
                     pool.gsum32[dst] = make_float2(f.lo, f.hi);
                 }
             }
             pool.gsum[dst] = make_double2(a.lo, a.hi);
             pool.gmid[dst] = make_double2(b.lo, b.hi);
             for (int j = 1; pool.gsamp && j <= pool.S; j++) {
-                const iv64 v = group_sum<double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
+                const iv64 v = group_sum<PR, double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
                 pool.gsamp[((size_t)ns * pool.S + (j - 1)) * pool.NG + S.group0 + g] = make_double2(v.lo, v.hi);
             }
         }
@@ -919,6 +928,7 @@ __global__ void k_gc_scatter(GbPool pool, const GbState* st, const int* tile_off
 // with those entries replaced.  A new record holds the child's coordinates of
 // its block and the cached sums of the groups it owns (groups of the dirty
 // ranges recomputed, the others copied from the parent's record).
+template <bool PR>
 __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                 const GbChildren& ch, const GbSplit& sp, const GbEntries& En,
                                                 double tol_x, const GbState* st, long long s, int lane,
@@ -997,10 +1007,10 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
             m = iv64{shM[at].x, shM[at].y};
             if (pool.fp32) pool.rgsum32[dst] = sh32[at];
         } else {
-            a = group_sum<double>(P, S, gl, X, R, ops);
-            m = group_sum<double>(P, S, gl, MX, R, ops);
+            a = group_sum<PR, double>(P, S, gl, X, R, ops);
+            m = group_sum<PR, double>(P, S, gl, MX, R, ops);
             if (pool.fp32) {
-                const iv32 f = group_sum<float>(P, S, gl, X32, R32, ops);
+                const iv32 f = group_sum<PR, float>(P, S, gl, X32, R32, ops);
                 pool.rgsum32[dst] = make_float2(f.lo, f.hi);
             }
         }
@@ -1018,6 +1028,7 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
     }
 }
 
+template <bool PR>
 __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbParents par, GbChildren ch,
                                                      GbSplit sp, GbEntries En, double tol_x, GbState* st,
                                                      GbTabs Tb, int tab) {
@@ -1029,9 +1040,9 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < kept; s += nwarps) {
         if (pool.recs)
-            materialize_rec(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0, shF[w], shM[w], sh32[w]);
+            materialize_rec<PR>(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0, shF[w], shM[w], sh32[w]);
         else
-            materialize_one(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0, shF[w], shM[w], sh32[w]);
+            materialize_one<PR>(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0, shF[w], shM[w], sh32[w]);
         __syncwarp();
     }
 }
@@ -1170,6 +1181,7 @@ __global__ void k_to_f32(const double* lo, const double* hi, float* lo32, float*
     hi32[i] = __double2float_ru(hi[i]);
 }
 
+template <bool PR>
 __global__ void __launch_bounds__(128) k_eval_boxes(GbProg P, const double* lo, const double* hi,
                                                     const float* lo32, const float* hi32, long long nbox,
                                                     int blk, int fp32, double* Fo, double* Fmo, double* Go,
@@ -1181,29 +1193,31 @@ __global__ void __launch_bounds__(128) k_eval_boxes(GbProg P, const double* lo, 
     MidView MX{X};
     iv64 R[GB_MAX_TREGS], O[GB_MAX_OREGS], sums[GB_MAX_ISUM];
     int ops = 0;
-    sum_values<double>(P, blk, MX, (const CacheRef<double2>*)nullptr, R, sums, ops);
+    sum_values<PR, double>(P, blk, MX, (const CacheRef<double2>*)nullptr, R, sums, ops);
     iv64 Fm = outer_fwd<double>(P, MX, sums, O, ops);
     Fmo[2 * b] = Fm.lo;
     Fmo[2 * b + 1] = Fm.hi;
     if (!fp32) {
         iv64 RA[GB_MAX_TREGS], OA[GB_MAX_OREGS];
-        sum_values<double>(P, blk, X, (const CacheRef<double2>*)nullptr, R, sums, ops);
+        sum_values<PR, double>(P, blk, X, (const CacheRef<double2>*)nullptr, R, sums, ops);
         iv64 F = outer_fwd<double>(P, X, sums, O, ops);
         Fo[2 * b] = F.lo;
         Fo[2 * b + 1] = F.hi;
         if (blk >= 0) {
-            bool m = block_mono<double>(P, blk, X, X, O, OA, R, RA, Go + (size_t)b * P.B * 2, ops);
+            bool m = block_mono<PR, double>(P, blk, X, X, O, OA, R, RA, Go + (size_t)b * P.B * 2,
+                                        (const CacheRef<double2>*)nullptr, -1, ops);
             mono[b] = m ? 1 : 0;
         }
     } else {
         View<float> X32{lo32 + (size_t)b * n, hi32 + (size_t)b * n, nullptr, nullptr, 0, 0, 1, 2, 0u};
         iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS], O32[GB_MAX_OREGS], OA32[GB_MAX_OREGS], s32[GB_MAX_ISUM];
-        sum_values<float>(P, blk, X32, (const CacheRef<float2>*)nullptr, R32, s32, ops);
+        sum_values<PR, float>(P, blk, X32, (const CacheRef<float2>*)nullptr, R32, s32, ops);
         iv32 F = outer_fwd<float>(P, X32, s32, O32, ops);
         Fo[2 * b] = F.lo;
         Fo[2 * b + 1] = F.hi;
         if (blk >= 0) {
-            bool m = block_mono<float>(P, blk, X32, X, O32, OA32, R32, RA32, Go + (size_t)b * P.B * 2, ops);
+            bool m = block_mono<PR, float>(P, blk, X32, X, O32, OA32, R32, RA32, Go + (size_t)b * P.B * 2,
+                                       (const CacheRef<float2>*)nullptr, -1, ops);
             mono[b] = m ? 1 : 0;
         }
     }
@@ -1240,7 +1254,8 @@ long long gb_launches_so_far() { return gb_launch_count; }
 cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, double tol_x,
                                 GbState* st, cudaStream_t s) {
     gb_launch_count++;
-    k_root_init<<<1, 256, 0, s>>>(P, pool, E, tol_x, st);
+    if (P.any_prod) k_root_init<true><<<1, 256, 0, s>>>(P, pool, E, tol_x, st);
+    else k_root_init<false><<<1, 256, 0, s>>>(P, pool, E, tol_x, st);
     return cudaGetLastError();
 }
 
@@ -1298,7 +1313,8 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
                 if ((e = gb_launch_eval32_tab(P, pool, par, *tabs, ch, Cmax, sp, st, s)) != cudaSuccess) return e;
             } else {
                 gb_launch_count++;
-                k_eval32<<<gch, 128, 0, s>>>(P, pool, par, ch, sp, st);
+                if (P.any_prod) k_eval32<true><<<gch, 128, 0, s>>>(P, pool, par, ch, sp, st);
+                else k_eval32<false><<<gch, 128, 0, s>>>(P, pool, par, ch, sp, st);
             }
             if (ev) cudaEventRecord(ev[3], s);
             gb_launch_count += 3;
@@ -1313,7 +1329,8 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
                 return e;
         } else {
             gb_launch_count++;
-            k_eval64<<<gch, 128, 0, s>>>(P, pool, par, ch, sp, G.fp32, st);
+            if (P.any_prod) k_eval64<true><<<gch, 128, 0, s>>>(P, pool, par, ch, sp, G.fp32, st);
+            else k_eval64<false><<<gch, 128, 0, s>>>(P, pool, par, ch, sp, G.fp32, st);
         }
         if (ev) cudaEventRecord(ev[1], s);
     }
@@ -1337,8 +1354,11 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     GbTabs Tb{};
     if (tabs) Tb = *tabs;
     gb_launch_count++;
-    k_materialize<<<(unsigned)std::min<long long>(grid_for(Cmax * 32, 128), 152 * 16), 128, 0, s>>>(
-        P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, tabs ? 1 : 0);
+    const unsigned gmat = (unsigned)std::min<long long>(grid_for(Cmax * 32, 128), 152 * 16);
+    if (P.any_prod)
+        k_materialize<true><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, tabs ? 1 : 0);
+    else
+        k_materialize<false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, tabs ? 1 : 0);
     if (G.K <= 4096) {   // few parents: freed by the finishing block itself
         gb_launch_count++;
         k_finish<<<1, 256, 0, s>>>(G, par, pool, E_new, 1, st);
@@ -1383,7 +1403,11 @@ cudaError_t gb_launch_eval_boxes(const GbProg& P, const double* lo, const double
         k_to_f32<<<grid_for(cnt, 256), 256, 0, s>>>(lo, hi, lo32, hi32, cnt);
     }
     gb_launch_count++;
-    k_eval_boxes<<<grid_for(nbox, 128), 128, 0, s>>>(P, lo, hi, lo32, hi32, nbox, blk, fp32, F, Fmid, G, mono);
+    if (P.any_prod)
+        k_eval_boxes<true><<<grid_for(nbox, 128), 128, 0, s>>>(P, lo, hi, lo32, hi32, nbox, blk, fp32, F, Fmid, G, mono);
+    else
+        k_eval_boxes<false><<<grid_for(nbox, 128), 128, 0, s>>>(P, lo, hi, lo32, hi32, nbox, blk, fp32, F, Fmid, G,
+                                                                mono);
     return cudaGetLastError();
 }
 

@@ -155,7 +155,29 @@ def mixed(n: int = 10000, seed: int = 0, tol_f: float = 1e-6, block: int | None 
                    block if block else min(n, 100), s, seed)
 
 
-FAMILIES = {"sep_cos": sep_cos, "chain": chain, "ackley": ackley, "mixed": mixed}
+def prod_poly(n: int = 8, seed: int = 0, tol_f: float = 1e-6, block: int | None = None) -> Problem:
+    """A polynomial objective with a coupled product (products over an index
+    set, no transcendentals, so every interval operation is exact up to its
+    directed rounding):
+    sum_i (x_i - c_i)^2 + prod_{i<n-1} (1 + a_i ((x_i - c_i) - (x_{i+1} - c_{i+1}))^2) - 1,
+    a_i ~ U[0.5, 2], c_i ~ U[-1, 1], box [-2, 3]^n; min 0 at x = c (every factor >= 1)."""
+    if n < 2:
+        raise ValueError("prod_poly needs n >= 2")
+    r = _rng(seed)
+    a = r.uniform(0.5, 2.0, n)
+    c = r.uniform(-1.0, 1.0, n)
+    g = Dag()
+    ta, tc = g.table(a), g.table(c)
+    d0 = g.sub(g.ivar(0), g.icoef(tc))
+    s1 = g.isum(g.sqr(d0), 0, n, 1)
+    d1 = g.sub(g.sub(g.ivar(0), g.icoef(tc)), g.sub(g.ivar(1), g.icoef(tc, 1)))
+    p1 = g.iprod(g.add(g.const(1.0), g.mul(g.icoef(ta), g.sqr(d1))), 0, n - 1, 1)
+    f = g.sub(g.add(s1, p1), g.const(1.0))
+    return Problem("prod_poly", n, g.nodes(), f, g.tables, np.full(n, -2.0), np.full(n, 3.0), tol_f,
+                   block if block else min(n, 10), c.copy(), seed)
+
+
+FAMILIES = {"sep_cos": sep_cos, "chain": chain, "ackley": ackley, "mixed": mixed, "prod_poly": prod_poly}
 
 
 def make(family: str, **kw) -> Problem:

@@ -74,6 +74,20 @@ def test_invalid_problems_rejected_without_gpu():
         gb.gb_create_problem(p.nodes, p.root, p.tables, p.n, p.l, p.u, 1e-6,
                              gb.gb_default_options(split_m=3))
     assert e.value.status == gb.GB_E_INVALID
+    q = S.paper_griewank(n=4)
+    with pytest.raises(gb.GbError) as e:   # products run on the interpreter only
+        gb.gb_create_problem(q.nodes, q.root, q.tables, q.n, q.l, q.u, 1e-6, gb.gb_default_options(eval_mode=3))
+    assert e.value.status == gb.GB_E_INVALID and "IPROD" in str(e.value)
+    g = S.Dag()
+    t = g.iprod(g.ivar(0), 0, 2, 1)
+    f = g.isum(g.mul(g.ivar(0), g.const(2.0)), 0, 2, 1)
+    g2 = S.Dag()
+    inner = g2.iprod(g2.ivar(0), 0, 2, 1)
+    bad_t = g2.isum(g2.add(g2.ivar(0), inner), 0, 2, 1)   # IPROD inside a sum template
+    with pytest.raises(gb.GbError) as e:
+        gb.gb_create_problem(g2.nodes(), bad_t, [], 2, [0.0, 0.0], [1.0, 1.0], 1e-6)
+    assert e.value.status == gb.GB_E_INVALID
+    del t, f
     g = S.Dag()
     f = g.add(g.ivar(0), g.const(1.0))      # IDX_VAR outside a sum
     with pytest.raises(gb.GbError) as e:

@@ -44,7 +44,8 @@ def _ulp(x):
 
 
 POLY = [("chain", dict(n=33, seed=3), 10), ("chain", dict(n=12, seed=4), 5),
-        ("chain", dict(n=2, seed=5), 2), ("chain", dict(n=100, seed=0), 10)]
+        ("chain", dict(n=2, seed=5), 2), ("chain", dict(n=100, seed=0), 10),
+        ("prod_poly", dict(n=12, seed=1), 5), ("prod_poly", dict(n=37, seed=2), 10)]
 
 
 @pytest.mark.parametrize("fp32", [False, True])
@@ -64,6 +65,32 @@ def test_polynomial_bit_exact(fam, kw, B, fp32):
         assert np.array_equal(gFm, oFm)
         assert np.array_equal(gG[:, :w], oG[:, :w]), (blk, np.argwhere(gG[:, :w] != oG[:, :w])[:5])
         assert np.array_equal(gM, oM)
+    solver.close()
+
+
+def test_signed_product_bit_exact():
+    # products whose factors straddle zero and change sign (every case of
+    # the interval product), two products and a sum, offsets 0 and 1
+    n = 11
+    rng = np.random.default_rng(8)
+    g = S.Dag()
+    tc = g.table(rng.uniform(-1.0, 1.0, n))
+    t1 = g.sub(g.ivar(0), g.icoef(tc))
+    t2 = g.add(g.const(0.5), g.mul(g.ivar(0), g.ivar(1)))
+    f = g.add(g.sub(g.iprod(t1, 0, n, 1), g.scale(g.iprod(t2, 0, n - 1, 2), 0.75)),
+              g.isum(g.sqr(g.ivar(0)), 0, n, 1))
+    p = S.Problem("signed_prod", n, g.nodes(), f, g.tables, np.full(n, -2.0), np.full(n, 2.0),
+                  1e-6, 4, np.zeros(n), 0)
+    solver = gb.Solver(p, block=4)
+    orc = O.Oracle(p, block=4)
+    lo, hi = S.random_boxes(p, 200, seed=6)
+    for fp32 in (False, True):
+        for blk in range(3):
+            gF, gFm, gG, gM = _gpu_eval(solver, lo, hi, blk, fp32)
+            oF, oFm, oG, oM = _oracle_eval(orc, lo, hi, blk, fp32)
+            w = min(4, n - blk * 4)
+            assert np.array_equal(gF, oF) and np.array_equal(gFm, oFm)
+            assert np.array_equal(gG[:, :w], oG[:, :w]) and np.array_equal(gM, oM)
     solver.close()
 
 
@@ -89,7 +116,8 @@ def test_custom_dag_bit_exact():
 TRANS = [("sep_cos", dict(n=2, seed=1), 2), ("sep_cos", dict(n=25, seed=2), 10),
          ("ackley", dict(n=10, seed=3), 5), ("ackley", dict(n=1000, seed=0), 10),
          ("mixed", dict(n=21, seed=4), 10), ("paper_rastrigin", dict(n=7), 7),
-         ("paper_breiman", dict(n=5), 5)]
+         ("paper_breiman", dict(n=5), 5), ("paper_griewank", dict(n=13), 5),
+         ("paper_styblinski", dict(n=6), 3), ("paper_zabinsky", dict(n=9), 9)]
 
 
 def _term_scale(p):
@@ -102,6 +130,12 @@ def _term_scale(p):
         return 20.0 + math.e + 1.0
     if p.family == "paper_rastrigin":
         return 10.0 * p.n
+    if p.family == "paper_griewank":      # products of cosines (<= 1) beside sum x^2 / 4000
+        return 1.0 + 110.0 ** 2 / 4000.0 * p.n
+    if p.family == "paper_styblinski":    # 4n times a product of cosines
+        return 4.0 * p.n
+    if p.family == "paper_zabinsky":      # 2.5 and 1 times products of sines
+        return 3.5
     return 0.1 * p.n
 
 

@@ -28,10 +28,10 @@ def _covers(lo, hi, x):
 
 
 def _run_both(p, B, m, d, K, fp32=False, tol_x=0.0, tol_f=None, max_gen=10**9, cap=None, samples=0,
-              mono_all=False):
+              mono_all=False, **extra):
     tol = p.tol_f if tol_f is None else tol_f
     opts = dict(block=B, split_m=m, split_d=d, max_children=K * m ** d, fp32_prefilter=int(fp32),
-                tol_x=tol_x, max_generations=max_gen, samples=samples, mono_all=int(mono_all))
+                tol_x=tol_x, max_generations=max_gen, samples=samples, mono_all=int(mono_all), **extra)
     if tol_f is not None:
         opts["tol_f"] = tol_f if tol_f > 0 else 0.0
     if cap is not None:
@@ -92,9 +92,10 @@ def test_paper_mode_rastrigin_iterations():
     assert np.array_equal(g.trace["kept"], o.trace["kept"])
 
 
-# per-block iteration counts printed by the paper (Tables 2, S2-S5, S7, S8)
+# per-block iteration counts printed by the paper (Tables 2, S2-S10)
 PAPER_PER_BLOCK = [("paper_rastrigin", 9), ("paper_breiman", 8), ("paper_ackley", 10), ("paper_belegundu", 9),
-                   ("paper_fu", 9), ("paper_levy", 9), ("paper_salomon", 11)]
+                   ("paper_fu", 9), ("paper_levy", 9), ("paper_salomon", 11), ("paper_griewank", 11),
+                   ("paper_styblinski", 9), ("paper_zabinsky", 8)]
 
 
 def _fstar(p):
@@ -132,6 +133,20 @@ def test_paper_rosenbrock_parity():
     g, o = _run_both(p, 3, 2, 3, 8, tol_f=1e-6)
     _assert_identical(g, o)
     assert g.fmin_lo <= 0.0 <= g.fmin_hi
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("samples,mono_all,extra", [(0, False, {}), (10, True, {}), (0, True, {}),
+                                                    (0, False, dict(pool_mode=2)), (0, False, dict(pool_mode=1))])
+def test_product_run_parity(fp32, samples, mono_all, extra):
+    # IPROD (product tree, its reverse sweep in the first-order test, cached
+    # group products of the dense rows and of block records): bit-identical
+    # runs on a polynomial objective
+    p = S.prod_poly(n=12, seed=5)
+    g, o = _run_both(p, 4, 2, 4, 8, fp32=fp32, samples=samples, mono_all=mono_all, **extra)
+    _assert_identical(g, o)
+    assert g.fmin_lo <= 0.0 <= g.fmin_hi and g.fmin_hi - g.fmin_lo <= p.tol_f
+    assert _covers(g.box_lo, g.box_hi, p.s)
 
 
 @pytest.mark.parametrize("fp32", [False, True])

@@ -209,7 +209,8 @@ def _sample_points(rng, lo, hi, count):
 
 CASES = [("sep_cos", dict(n=3)), ("chain", dict(n=6)), ("ackley", dict(n=4)),
          ("mixed", dict(n=7)), ("paper_rastrigin", dict(n=3)), ("paper_breiman", dict(n=3)),
-         ("paper_griewank", dict(n=5)), ("paper_styblinski", dict(n=4)), ("paper_zabinsky", dict(n=5))]
+         ("paper_griewank", dict(n=5)), ("paper_styblinski", dict(n=4)), ("paper_zabinsky", dict(n=5)),
+         ("prod_poly", dict(n=6))]
 
 
 @pytest.mark.parametrize("f32", [False, True])

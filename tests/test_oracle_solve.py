@@ -137,7 +137,8 @@ CASES = [("sep_cos", dict(n=2), dict(split_m=2, split_d=1)),
          ("chain", dict(n=6, block=3), dict(split_m=2, split_d=3)),
          ("chain", dict(n=10, block=5), dict(split_m=2, split_d=5, max_parents=8)),
          ("ackley", dict(n=3), dict(split_m=2, split_d=3)),
-         ("mixed", dict(n=6, block=3), dict(split_m=2, split_d=3))]
+         ("mixed", dict(n=6, block=3), dict(split_m=2, split_d=3)),
+         ("prod_poly", dict(n=6, block=3), dict(split_m=2, split_d=3, max_parents=16))]
 
 
 @pytest.mark.parametrize("fp32", [False, True])
@@ -175,7 +176,9 @@ def test_separable_reduction():
 
 
 @pytest.mark.parametrize("fam,kw", [("sep_cos", dict(n=2)), ("chain", dict(n=3, block=3)),
-                                     ("ackley", dict(n=2)), ("paper_breiman", dict(n=2))])
+                                     ("ackley", dict(n=2)), ("paper_breiman", dict(n=2)),
+                                     ("paper_griewank", dict(n=2)), ("paper_styblinski", dict(n=2)),
+                                     ("paper_zabinsky", dict(n=2)), ("prod_poly", dict(n=3, block=3))])
 def test_brute_force_grid(fam, kw):
     import itertools
     import mp_ref
@@ -187,7 +190,7 @@ def test_brute_force_grid(fam, kw):
     vals = [float(mp_ref.point_value(p, x, dps=30)) for x in pts]
     k = int(np.argmin(vals))
     assert min(vals) >= res.glb                 # GLB is a lower bound of f
-    fstar = 0.0 if not fam.startswith("paper") else -0.1 * p.n
+    fstar = p.meta.get("fstar", -0.1 * p.n) if fam.startswith("paper") else 0.0
     assert res.glb <= fstar <= res.gub
     # every point with f below the final GUB lies in some output region
     for x, v in zip(pts, vals):
