@@ -28,7 +28,7 @@ _lib = None
 # operator codes of the objective node format (see synthetic.dag)
 OP = dict(CONST=0, PI=1, EULER=2, VAR=3, IDX_VAR=4, IDX_COEF=5, ADD=6, SUB=7,
           MUL=8, DIV=9, NEG=10, SQR=11, SQRT=12, EXP=13, SIN=14, COS=15,
-          SCALE=16, ISUM=17, IPROD=18)
+          SCALE=16, ISUM=17, IPROD=18, STEP=19)
 
 ST_OK, ST_INVALID, ST_CAPACITY, ST_LIMIT = 0, 1, 3, 4
 

@@ -153,6 +153,19 @@ typedef struct { double lo, hi; } iv;
 static iv mk(double lo, double hi) { iv r = {lo, hi}; return r; }
 static iv entire(void) { return mk(-INFINITY, INFINITY); }
 
+/* Unit step H(y) = 1 for y >= 0, 0 for y < 0 (the indicator that builds the
+ * discontinuous test function of SI Appendix F, Eq. S24): exact on an
+ * interval wholly on one side of 0, [0, 1] on one that holds the jump. */
+static iv iv_step(iv x) {
+    if (x.lo >= 0.0) return mk(1.0, 1.0);
+    if (x.hi < 0.0) return mk(0.0, 0.0);
+    return mk(0.0, 1.0);
+}
+
+/* Whether the box of x holds the jump of H (its derivative is then not
+ * bounded there). */
+static int step_jump(iv x) { return !(x.lo >= 0.0) && !(x.hi < 0.0); }
+
 /* Eq. 3 */
 static iv iv_add(iv x, iv y, int p) {
     return mk(R_add(x.lo, y.lo, p, 0), R_add(x.hi, y.hi, p, 1));
@@ -281,7 +294,7 @@ enum {
     O_CONST = 0, O_PI = 1, O_EULER = 2, O_VAR = 3, O_IDX_VAR = 4, O_IDX_COEF = 5,
     O_ADD = 6, O_SUB = 7, O_MUL = 8, O_DIV = 9, O_NEG = 10, O_SQR = 11,
     O_SQRT = 12, O_EXP = 13, O_SIN = 14, O_COS = 15, O_SCALE = 16, O_ISUM = 17,
-    O_IPROD = 18, O_COUNT = 19
+    O_IPROD = 18, O_STEP = 19, O_COUNT = 20
 };
 
 /* ISUM and IPROD reduce a per-index template over an index set; they share
@@ -294,7 +307,7 @@ static int n_operands(int op) {
     switch (op) {
     case O_ADD: case O_SUB: case O_MUL: case O_DIV: return 2;
     case O_NEG: case O_SQR: case O_SQRT: case O_EXP: case O_SIN: case O_COS:
-    case O_SCALE: return 1;
+    case O_SCALE: case O_STEP: return 1;
     default: return 0;
     }
 }
@@ -501,6 +514,7 @@ static iv node_value(const oprob* P, int v, int i, obox X, int p, const iv* vals
     case O_SIN: return iv_trig(vals[q->a], p, 0);
     case O_COS: return iv_trig(vals[q->a], p, 1);
     case O_SCALE: return iv_scale(vals[q->a], q->v, p);
+    case O_STEP: return iv_step(vals[q->a]);
     default: return entire();
     }
 }
@@ -552,6 +566,13 @@ static void push_adjoint(const oprob* P, int v, int p, const iv* vals, iv* adj) 
         break;
     case O_SCALE:
         adj[q->a] = iv_add(adj[q->a], iv_scale(g, q->v, p), p);
+        break;
+    case O_STEP:
+        /* H' = 0 off the jump; a box that holds the jump (with a nonzero
+         * adjoint) gets an unbounded partial, so the first-order test keeps it.
+         * Reading: the paper gives no rule for partials of a discontinuous f. */
+        if (step_jump(vals[q->a]) && !(g.lo == 0.0 && g.hi == 0.0))
+            adj[q->a] = iv_add(adj[q->a], entire(), p);
         break;
     default:
         break;
@@ -849,6 +870,7 @@ int oracle_iv_op(int op, const double* x, const double* y, double c, int p, doub
     case O_SIN: r = iv_trig(a, p, 0); break;
     case O_COS: r = iv_trig(a, p, 1); break;
     case O_SCALE: r = iv_scale(a, c, p); break;
+    case O_STEP: r = iv_step(a); break;
     case O_PI: r = const_pi(p); break;
     case O_EULER: r = const_e(p); break;
     default: return 1;

@@ -9,4 +9,5 @@ from . import dag  # noqa: F401
 from .families import (Problem, make, sep_cos, chain, ackley, mixed, prod_poly,  # noqa: F401
                        paper_rastrigin, paper_breiman, paper_ackley, paper_belegundu, paper_fu, paper_levy,
                        paper_salomon, paper_rosenbrock, paper_griewank, paper_styblinski, paper_zabinsky,
+                       paper_discontinuous,
                        random_boxes, serving_stream, FAMILIES)

@@ -45,13 +45,14 @@ OP_COS = 15
 OP_SCALE = 16
 OP_ISUM = 17
 OP_IPROD = 18
+OP_STEP = 19
 
 OP_NAMES = {
     OP_CONST: "CONST", OP_PI: "PI", OP_EULER: "EULER", OP_VAR: "VAR",
     OP_IDX_VAR: "IDX_VAR", OP_IDX_COEF: "IDX_COEF", OP_ADD: "ADD", OP_SUB: "SUB",
     OP_MUL: "MUL", OP_DIV: "DIV", OP_NEG: "NEG", OP_SQR: "SQR", OP_SQRT: "SQRT",
     OP_EXP: "EXP", OP_SIN: "SIN", OP_COS: "COS", OP_SCALE: "SCALE", OP_ISUM: "ISUM",
-    OP_IPROD: "IPROD",
+    OP_IPROD: "IPROD", OP_STEP: "STEP",
 }
 
 NODE_DTYPE = np.dtype([
@@ -125,6 +126,10 @@ class Dag:
 
     def cos(self, x):
         return self._push(OP_COS, a=x)
+
+    def step(self, x):
+        """Unit step: 1 where x >= 0, else 0."""
+        return self._push(OP_STEP, a=x)
 
     def scale(self, x, v: float):
         return self._push(OP_SCALE, a=x, v=v)

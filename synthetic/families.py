@@ -373,6 +373,25 @@ def paper_zabinsky(n: int = 10, tol_f: float = 0.0, block: int | None = None) ->
                    block if block else min(n, 10), np.full(n, 2.0 * np.pi / 3.0), 0, meta=dict(fstar=-3.5))
 
 
+def paper_discontinuous(n: int = 10, tol_f: float = 0.0, block: int | None = None) -> Problem:
+    """Eq. S24-S27: -1 on the small cube D = [1.5 - eps/2, 1.5 + eps/2]^n (eps = 1e-6; S24 prints
+    1.5 - eps/2 on both sides, read as the cube centred on 1.5), the Levy function L elsewhere,
+    -10 <= x_i <= 10; min -1 on D.  Written as (1 - I) L - I with the indicator
+    I = prod_i H(x_i - a) H(b - x_i) of D (H the unit step; a, b the doubles nearest 1.5 -/+ eps/2)."""
+    lev = paper_levy(n=n, tol_f=tol_f, block=block)
+    g = Dag()
+    g._nodes = [tuple(r) for r in lev.nodes.tolist()]
+    g.tables = list(lev.tables)
+    eps = 1e-6
+    a, b = 1.5 - eps / 2, 1.5 + eps / 2
+    x = g.ivar(0)
+    ind = g.iprod(g.mul(g.step(g.sub(x, g.const(a))), g.step(g.sub(g.const(b), x))), 0, n, 1)
+    f = g.sub(g.mul(g.sub(g.const(1.0), ind), int(lev.root)), ind)
+    return Problem("paper_discontinuous", n, g.nodes(), f, g.tables, lev.l, lev.u, tol_f,
+                   lev.block, np.full(n, 1.5), 0, meta=dict(fstar=-1.0, cube=(a, b)))
+
+
+FAMILIES.update(paper_discontinuous=paper_discontinuous)
 FAMILIES.update(paper_griewank=paper_griewank, paper_styblinski=paper_styblinski, paper_zabinsky=paper_zabinsky)
 FAMILIES.update(paper_rastrigin=paper_rastrigin, paper_breiman=paper_breiman, paper_ackley=paper_ackley,
                 paper_belegundu=paper_belegundu, paper_fu=paper_fu, paper_levy=paper_levy,

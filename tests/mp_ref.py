@@ -86,6 +86,8 @@ def _point_value_mp(p, xs):
             r = mpmath.cos(ev(a, i))
         elif op == D.OP_SCALE:
             r = ev(a, i) * mpmath.mpf(float(q["v"]))
+        elif op == D.OP_STEP:
+            r = mpmath.mpf(1) if ev(a, i) >= 0 else mpmath.mpf(0)
         elif op == D.OP_ISUM:
             r = mpmath.fsum(ev(a, k) for k in _isum_indices(q))
         elif op == D.OP_IPROD:
@@ -127,7 +129,7 @@ def _template_offsets(p, root):
             offs.append(int(q["b"]))
         if op in _BIN:
             stack += [int(q["a"]), int(q["b"])]
-        elif op in (D.OP_NEG, D.OP_SQR, D.OP_SQRT, D.OP_EXP, D.OP_SIN, D.OP_COS, D.OP_SCALE):
+        elif op in (D.OP_NEG, D.OP_SQR, D.OP_SQRT, D.OP_EXP, D.OP_SIN, D.OP_COS, D.OP_SCALE, D.OP_STEP):
             stack.append(int(q["a"]))
     return offs
 

@@ -210,7 +210,7 @@ def _sample_points(rng, lo, hi, count):
 CASES = [("sep_cos", dict(n=3)), ("chain", dict(n=6)), ("ackley", dict(n=4)),
          ("mixed", dict(n=7)), ("paper_rastrigin", dict(n=3)), ("paper_breiman", dict(n=3)),
          ("paper_griewank", dict(n=5)), ("paper_styblinski", dict(n=4)), ("paper_zabinsky", dict(n=5)),
-         ("prod_poly", dict(n=6))]
+         ("prod_poly", dict(n=6)), ("paper_discontinuous", dict(n=4))]
 
 
 @pytest.mark.parametrize("f32", [False, True])
@@ -241,6 +241,61 @@ def test_containment_of_f_and_partials(fam, kw, f32):
         mid = 0.5 * lo[k] + 0.5 * hi[k]
         fm = mp_ref.point_value(p, mid)
         assert Fm[0] <= fm <= Fm[1]
+
+
+def _disc_and_levy(n, B):
+    return S.paper_discontinuous(n=n, block=B), S.paper_levy(n=n, block=B)
+
+
+def test_discontinuous_equals_levy_off_the_cube():
+    # Eq. S24: f = L away from the cube D.  Boxes that miss D in some
+    # coordinate give the Levy F and the Levy partials bit for bit (the
+    # indicator is exactly [0, 0] there and its adjoints vanish)
+    n, B = 7, 3
+    p, lev = _disc_and_levy(n, B)
+    a, b = p.meta["cube"]
+    od, ol = O.Oracle(p, block=B), O.Oracle(lev, block=B)
+    lo, hi = S.random_boxes(p, 60, seed=31, around_s=0.2)
+    k = 0
+    for j in range(len(lo)):
+        x0, x1 = lo[j].copy(), hi[j].copy()
+        q = j % n                         # make coordinate q miss D
+        if j % 2:
+            x0[q], x1[q] = b + 1e-3, b + 0.5
+        else:
+            x0[q], x1[q] = a - 0.5, a - 1e-9
+        for blk in range((n + B - 1) // B):
+            F, Fm, G, M = od.eval_box(x0, x1, blk=blk)
+            F2, Fm2, G2, M2 = ol.eval_box(x0, x1, blk=blk)
+            assert tuple(F) == tuple(F2) and tuple(Fm) == tuple(Fm2)
+            assert np.array_equal(G, G2) and M == M2
+            k += 1
+    assert k > 0
+
+
+def test_discontinuous_on_and_across_the_cube():
+    n, B = 4, 4
+    p, lev = _disc_and_levy(n, B)
+    a, b = p.meta["cube"]
+    o = O.Oracle(p, block=B)
+    # a box inside D: the constant -1, and every partial holds 0
+    inner_lo = np.full(n, a + (b - a) / 4)
+    inner_hi = np.full(n, b - (b - a) / 4)
+    F, _, G, M = o.eval_box(inner_lo, inner_hi, blk=0)
+    assert tuple(F) == (-1.0, -1.0)
+    assert np.all(G[:, 0] <= 0.0) and np.all(G[:, 1] >= 0.0) and M == 0
+    # a box across the boundary of D in every coordinate: F holds -1 and the
+    # Levy values of its points off D; the partials are unbounded (no
+    # first-order discard of a box that may hold the minimum)
+    lo, hi = np.full(n, 1.4), np.full(n, 1.5)
+    F, _, G, M = o.eval_box(lo, hi, blk=0)
+    FL, _, _, _ = O.Oracle(lev, block=B).eval_box(lo, hi, blk=0)
+    assert F[0] <= -1.0 <= F[1] and F[1] >= FL[1] and F[0] <= FL[0]
+    assert np.all(np.isinf(G)) and M == 0
+    # the GUB sample at a point of D is -1, off D the Levy value
+    import mp_ref
+    assert mp_ref.point_value(p, np.full(n, 1.5)) == -1
+    assert abs(mp_ref.point_value(p, np.full(n, 1.0))) < 1e-50    # Levy's minimum 0 (sin(pi) at 60 digits)
 
 
 @pytest.mark.parametrize("fam,kw", CASES[:4])

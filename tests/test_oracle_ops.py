@@ -89,6 +89,22 @@ def test_div_is_eq6_product_with_reciprocal(f32):
         assert got[0] <= min(q) and got[1] >= max(q)
 
 
+@pytest.mark.parametrize("f32", [False, True])
+def test_unit_step_is_the_image_of_the_interval(f32):
+    # H(y) = 1 for y >= 0 and 0 for y < 0; the interval image of [a, b] is
+    # {H(y) : a <= y <= b}, enclosed by [0, 1] exactly when it holds both values
+    cases = {(0.0, 0.0): (1.0, 1.0), (-0.0, 2.0): (1.0, 1.0), (1e-300, 1.0): (1.0, 1.0),
+             (-1e-300, -1e-300): (0.0, 0.0), (-3.0, -1.0): (0.0, 0.0), (-1.0, 0.0): (0.0, 1.0),
+             (-1e-300, 1e-300): (0.0, 1.0), (-math.inf, math.inf): (0.0, 1.0)}
+    for x, want in cases.items():
+        assert O.iv_op("STEP", x, f32=f32) == want, x
+    rng = np.random.default_rng(12)
+    lo, hi = _rand_intervals(rng, 2000, f32)
+    for a, b in zip(lo, hi):
+        img = {1.0 if y >= 0 else 0.0 for y in (a, b, 0.0) if a <= y <= b}
+        assert O.iv_op("STEP", (a, b), f32=f32) == (min(img), max(img))
+
+
 def test_closed_interval_zero_times_infinity():
     assert O.iv_op("MUL", (0.0, 0.0), (-math.inf, math.inf)) == (0.0, 0.0)
     assert O.iv_op("MUL", (0.0, 2.0), (1.0, math.inf)) == (0.0, math.inf)

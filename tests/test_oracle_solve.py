@@ -101,6 +101,22 @@ def _diag_quadratic(n, s):
                      np.asarray(s, dtype=np.float64), 0)
 
 
+def test_discontinuous_paper_procedure():
+    # SI Appendix F: the minimum -1 sits on the cube D of side 1e-6 around
+    # 1.5.  Under the paper's procedure the region holding D is kept (its
+    # F_lo is -1) and narrowed to tol_x; no diagonal sample lands in D, so
+    # the GUB stays at the Levy minimum 0 and Levy's minimiser keeps a second
+    # region (Table S14 prints one region: the reading differs there)
+    p = S.paper_discontinuous(n=5, block=5)
+    res = O.Oracle(p, block=5).solve(tol_f=0.0, tol_x=1e-4, split_m=4, split_d=5, max_parents=1,
+                                     samples=10, mono_all=True)
+    assert res.status == O.ST_OK
+    assert res.glb == -1.0 and res.glb <= -1.0 <= res.gub
+    assert _covers(res, np.full(5, 1.5)) and _covers(res, np.ones(5))
+    assert len(res.box_flo) == 2
+    assert np.all(res.box_hi - res.box_lo < 1e-4)
+
+
 def test_diagonal_samples_hit_a_minimiser_on_the_diagonal():
     # the interior diagonal points of [0, 11]^n at j / 11 are (j, ..., j)
     # exactly; with the minimiser at (5, ..., 5) the root's samples already
