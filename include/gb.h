@@ -59,14 +59,17 @@ typedef enum gb_status {
  * IDX_VAR(b = offset) stands for x[i+offset] and IDX_COEF(a = table,
  * b = offset) for coef_tables[a][i+offset].  CONST(v) is the exact double v;
  * PI and EULER are the constants pi and e, enclosed by adjacent doubles;
- * SCALE(a, v) multiplies node a by the exact double v.  Template nodes may
+ * SCALE(a, v) multiplies node a by the exact double v.  STEP(a) is the unit
+ * step H(a) = 1 for a >= 0, 0 for a < 0, for discontinuous objectives (SI
+ * Appendix F); a box that holds the jump gets an unbounded partial through
+ * it, so the first-order test never rules it out.  Template nodes may
  * not use VAR, ISUM or IPROD; outer nodes may not use IDX_VAR or IDX_COEF. */
 enum {
     GB_OP_CONST = 0, GB_OP_PI = 1, GB_OP_EULER = 2, GB_OP_VAR = 3,
     GB_OP_IDX_VAR = 4, GB_OP_IDX_COEF = 5, GB_OP_ADD = 6, GB_OP_SUB = 7,
     GB_OP_MUL = 8, GB_OP_DIV = 9, GB_OP_NEG = 10, GB_OP_SQR = 11,
     GB_OP_SQRT = 12, GB_OP_EXP = 13, GB_OP_SIN = 14, GB_OP_COS = 15,
-    GB_OP_SCALE = 16, GB_OP_ISUM = 17, GB_OP_IPROD = 18
+    GB_OP_SCALE = 16, GB_OP_ISUM = 17, GB_OP_IPROD = 18, GB_OP_STEP = 19
 };
 
 typedef struct gb_node {

@@ -33,7 +33,7 @@ int n_operands(int op) {
     switch (op) {
     case GB_OP_ADD: case GB_OP_SUB: case GB_OP_MUL: case GB_OP_DIV: return 2;
     case GB_OP_NEG: case GB_OP_SQR: case GB_OP_SQRT: case GB_OP_EXP: case GB_OP_SIN:
-    case GB_OP_COS: case GB_OP_SCALE: return 1;
+    case GB_OP_COS: case GB_OP_SCALE: case GB_OP_STEP: return 1;
     default: return 0;
     }
 }
@@ -57,6 +57,7 @@ uint8_t dev_op(int op) {
     case GB_OP_SIN: return D_SIN;
     case GB_OP_COS: return D_COS;
     case GB_OP_SCALE: return D_SCALE;
+    case GB_OP_STEP: return D_STEP;
     default: return D_ISUMV;
     }
 }
@@ -129,7 +130,7 @@ std::string gb_compile(const gb_node* nd, int32_t nn, int32_t root, const int64_
     if (ntab < 0) return "negative table count";
     for (int v = 0; v < nn; v++) {
         const gb_node& q = nd[v];
-        if (q.op < 0 || q.op > GB_OP_IPROD) return "unknown operator at node " + std::to_string(v);
+        if (q.op < 0 || q.op > GB_OP_STEP) return "unknown operator at node " + std::to_string(v);
         if (q.pad != 0) return "nonzero pad at node " + std::to_string(v);
         int k = n_operands(q.op);
         if (k >= 1 && (q.a < 0 || q.a >= v)) return "operand not before node " + std::to_string(v);

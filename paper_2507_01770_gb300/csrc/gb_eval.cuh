@@ -171,6 +171,7 @@ template <typename I> __device__ __noinline__ I slow_fwd(int op, I a, I b) {
     case D_SQRT: return isqrt(a);
     case D_EXP: return iexp(a);
     case D_SIN: return itrig(a, false);
+    case D_STEP: return istep(a);
     default: return itrig(a, true);   // D_COS
     }
 }
@@ -187,6 +188,14 @@ template <typename I> __device__ __noinline__ void slow_rev(int op, I g, I va, I
     }
     case D_SQRT: *da = imul(g, iscale(ircp(vt), (T)0.5)); break;
     case D_SIN: *da = imul(g, itrig(va, true)); break;
+    case D_STEP: {   // H' = 0 off the jump; unbounded on a box that holds it (nonzero adjoint)
+        const bool jump = !(va.lo >= (T)0) && !(va.hi < (T)0);
+        const bool live = !(g.lo == (T)0 && g.hi == (T)0);
+        const T inf = (T)INFINITY;
+        da->lo = jump && live ? -inf : (T)0;
+        da->hi = jump && live ? inf : (T)0;
+        break;
+    }
     default: *da = imul(g, ineg(itrig(va, false))); break;   // D_COS
     }
 }
@@ -216,6 +225,7 @@ __device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const G
         case D_SQRT:
         case D_EXP:
         case D_SIN:
+        case D_STEP:
         case D_COS: v = slow_fwd(in.op, R[in.a], R[in.a]); break;
         case D_SCALE:
             if (in.clo32 == in.chi32 || sizeof(T) == 8)
@@ -268,6 +278,7 @@ __device__ __forceinline__ void reverse_sweep(const GbIns* ins, int nins, const 
         case D_EXP: A[in.a] = iadd(A[in.a], imul(g, V[t])); break;
         case D_SQRT:
         case D_SIN:
+        case D_STEP:
         case D_COS: {
             I da, db;
             slow_rev(in.op, g, V[in.a], V[in.a], V[t], &da, &db);
@@ -453,6 +464,7 @@ __device__ __forceinline__ typename Prec<T>::I outer_fwd(const GbProg& P, const 
         case D_SQRT:
         case D_EXP:
         case D_SIN:
+        case D_STEP:
         case D_COS: v = slow_fwd(in.op, O[in.a], O[in.b]); break;
         case D_SCALE:
             if (in.clo32 == in.chi32 || sizeof(T) == 8)

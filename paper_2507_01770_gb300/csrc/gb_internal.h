@@ -26,7 +26,7 @@
 // Device opcodes of one instruction (registers are node slots).
 enum GbDevOp : uint8_t {
     D_CONST = 0, D_PI, D_EULER, D_VAR, D_IVAR, D_COEF, D_ISUMV,
-    D_ADD, D_SUB, D_MUL, D_DIV, D_NEG, D_SQR, D_SQRT, D_EXP, D_SIN, D_COS, D_SCALE
+    D_ADD, D_SUB, D_MUL, D_DIV, D_NEG, D_SQR, D_SQRT, D_EXP, D_SIN, D_COS, D_SCALE, D_STEP
 };
 
 struct GbIns {

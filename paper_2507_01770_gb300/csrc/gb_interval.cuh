@@ -195,6 +195,17 @@ template <typename I> __device__ __forceinline__ I imul(I x, I y) {
     return r;
 }
 
+// Unit step H(y) = 1 for y >= 0, else 0: exact on an interval wholly on one
+// side of the jump, [0, 1] on one that holds it.
+template <typename I> __device__ __forceinline__ I istep(I x) {
+    typedef decltype(x.lo) T;
+    I r;
+    if (x.lo >= (T)0) r.lo = r.hi = (T)1;
+    else if (x.hi < (T)0) r.lo = r.hi = (T)0;
+    else r.lo = (T)0, r.hi = (T)1;
+    return r;
+}
+
 // square without the dependence widening of x*x
 template <typename I> __device__ __forceinline__ I isqr(I x) {
     typedef decltype(x.lo) T;

@@ -94,6 +94,38 @@ def test_signed_product_bit_exact():
     solver.close()
 
 
+def _step_poly(n, seed):
+    """sum_i (x_i - c_i)^2 + 0.5 H(x_i - c_i)(x_i - c_i) - 0.25 prod_i H(x_i - c_i + 0.3) H(c_i + 0.3 - x_i):
+    unit steps in a sum template, a product of steps and a kink at c."""
+    rng = np.random.default_rng(seed)
+    g = S.Dag()
+    tc = g.table(rng.uniform(-1.0, 1.0, n))
+    d = g.sub(g.ivar(0), g.icoef(tc))
+    s1 = g.isum(g.add(g.sqr(d), g.scale(g.mul(g.step(d), d), 0.5)), 0, n, 1)
+    ind = g.iprod(g.mul(g.step(g.add(d, g.const(0.3))), g.step(g.sub(g.const(0.3), d))), 0, n, 1)
+    f = g.sub(s1, g.scale(ind, 0.25))
+    return S.Problem("step_poly", n, g.nodes(), f, g.tables, np.full(n, -2.0), np.full(n, 2.0),
+                     1e-6, 4, np.zeros(n), 0)
+
+
+def test_step_bit_exact():
+    # the unit step forward (exact, or [0, 1] across the jump) and its
+    # reverse step (0, or unbounded across the jump) bit for bit
+    p = _step_poly(10, 3)
+    solver = gb.Solver(p, block=4)
+    orc = O.Oracle(p, block=4)
+    lo, hi = S.random_boxes(p, 300, seed=4)
+    for fp32 in (False, True):
+        for blk in range(3):
+            gF, gFm, gG, gM = _gpu_eval(solver, lo, hi, blk, fp32)
+            oF, oFm, oG, oM = _oracle_eval(orc, lo, hi, blk, fp32)
+            w = min(4, 10 - blk * 4)
+            assert np.array_equal(gF, oF) and np.array_equal(gFm, oFm)
+            assert np.array_equal(gG[:, :w], oG[:, :w]) and np.array_equal(gM, oM)
+            assert np.isinf(oG[:, :w]).any()          # some boxes hold a jump
+    solver.close()
+
+
 def test_custom_dag_bit_exact():
     g = S.Dag()
     y = g.sub(g.ivar(0), g.ivar(1))
@@ -117,7 +149,8 @@ TRANS = [("sep_cos", dict(n=2, seed=1), 2), ("sep_cos", dict(n=25, seed=2), 10),
          ("ackley", dict(n=10, seed=3), 5), ("ackley", dict(n=1000, seed=0), 10),
          ("mixed", dict(n=21, seed=4), 10), ("paper_rastrigin", dict(n=7), 7),
          ("paper_breiman", dict(n=5), 5), ("paper_griewank", dict(n=13), 5),
-         ("paper_styblinski", dict(n=6), 3), ("paper_zabinsky", dict(n=9), 9)]
+         ("paper_styblinski", dict(n=6), 3), ("paper_zabinsky", dict(n=9), 9),
+         ("paper_discontinuous", dict(n=6), 3)]
 
 
 def _term_scale(p):

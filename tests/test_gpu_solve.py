@@ -149,6 +149,39 @@ def test_product_run_parity(fp32, samples, mono_all, extra):
     assert _covers(g.box_lo, g.box_hi, p.s)
 
 
+def test_discontinuous_paper_procedure_on_the_gpu():
+    # SI Appendix F under the paper's procedure: the region of the cube is
+    # kept with F_lo = -1, no sample lands in the cube, and the run ends with
+    # the cube's region and Levy's minimiser, as in the oracle
+    p = S.paper_discontinuous(n=10, block=5)
+    g, o = _run_both(p, 5, 4, 5, 1, tol_x=1e-4, tol_f=0.0, samples=10, mono_all=True)
+    assert g.status == o.status == 0
+    assert g.generations == o.generations and g.n_boxes == len(o.box_flo) == 2
+    assert np.array_equal(g.trace["kept"], o.trace["kept"])
+    assert g.fmin_lo == o.glb == -1.0
+    assert _covers(g.box_lo, g.box_hi, np.full(10, 1.5)) and _covers(g.box_lo, g.box_hi, np.ones(10))
+
+
+def _step_sum(n, seed):
+    rng = np.random.default_rng(seed)
+    g = S.Dag()
+    tc = g.table(rng.uniform(-1.0, 1.0, n))
+    d = g.sub(g.ivar(0), g.icoef(tc))
+    f = g.isum(g.add(g.sqr(d), g.scale(g.mul(g.step(d), d), 0.5)), 0, n, 1)
+    return S.Problem("step_sum", n, g.nodes(), f, g.tables, np.full(n, -2.0), np.full(n, 2.0),
+                     1e-6, 5, g.tables[tc].copy(), 0)
+
+
+@pytest.mark.parametrize("eval_mode", [1, 3, 4])
+def test_step_run_parity_all_kernels(eval_mode):
+    # a unit step inside a sum template runs on the interpreter and on both
+    # term-table kernels with the oracle's exact results
+    p = _step_sum(10, 7)
+    g, o = _run_both(p, 5, 2, 5, 8, eval_mode=eval_mode)
+    _assert_identical(g, o)
+    assert g.fmin_lo <= 0.0 <= g.fmin_hi
+
+
 @pytest.mark.parametrize("fp32", [False, True])
 @pytest.mark.parametrize("samples,mono_all", [(10, True), (3, False), (0, True)])
 def test_paper_mode_chain_parity(fp32, samples, mono_all):
