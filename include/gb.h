@@ -193,6 +193,47 @@ gb_status gb_solve_device(gb_problem* prob, gb_result* out);
 /* Releases the host arrays of a result (safe on a zeroed result). */
 void gb_free_result(gb_result* res);
 
+/* ---------------------------------------------------------------------- */
+/* Checkpoint and resume of the region list (section 3.1's list L)          */
+/* ---------------------------------------------------------------------- */
+/* The pool a solve left behind: every region, active or final, in pool
+ * order (the order the best-first selection breaks ties by), with its lower
+ * bound, its cycling word and the incumbent GUB.  Host arrays, owned by the
+ * library until gb_free_snapshot. */
+typedef struct gb_snapshot {
+    int32_t n;                /* problem dimension */
+    int32_t block;            /* cycling block size of the problem it was taken from */
+    int64_t count;            /* regions */
+    double* lo;               /* count x n, row-major */
+    double* hi;
+    double* flo;              /* lower bound of f on each region (as the pool holds it) */
+    int32_t* cyc;             /* next coordinate to split; bit 31 marks a final region (all widths < tol_x) */
+    double gub;               /* incumbent upper bound of the minimum */
+    int64_t generations;      /* generations run to reach this pool, over every call */
+} gb_snapshot;
+
+/* Takes the pool left by the last gb_solve / gb_solve_device /
+ * gb_solve_resume on prob (whatever its status: a solve stopped by
+ * max_generations or by GB_E_CAPACITY leaves a valid pool).
+ * GB_E_INVALID if no solve has run, GB_E_BUSY while one runs. */
+gb_status gb_snapshot_take(gb_problem* prob, gb_snapshot* out);
+
+/* Continues the branch and bound from a snapshot instead of the domain:
+ * the regions enter the pool in snapshot order with their lower bounds and
+ * cycling words, the incumbent is the snapshot's GUB, and the per-region
+ * cached sums are recomputed.  prob must have the snapshot's n; its other
+ * options may differ (a larger pool, another generation limit or device).
+ * With the same block, split and selection options the run continues
+ * exactly as the uninterrupted solve would: the generations of the resumed
+ * call follow those of the snapshot.  out->generations counts this call.
+ * Needs dense rows (pool_mode 1).  GB_E_INVALID on a mismatched or
+ * malformed snapshot (regions outside the bounds, lo > hi, a cycling word
+ * out of range, a NaN bound), GB_E_CAPACITY if the regions do not fit. */
+gb_status gb_solve_resume(gb_problem* prob, const gb_snapshot* snap, gb_result* out);
+
+/* Releases the host arrays of a snapshot (safe on a zeroed one). */
+void gb_free_snapshot(gb_snapshot* snap);
+
 /* Releases the problem and all its device memory. */
 void gb_destroy_problem(gb_problem* prob);
 

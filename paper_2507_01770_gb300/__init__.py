@@ -51,6 +51,13 @@ class gb_gen_stat(ctypes.Structure):
 _PD = ctypes.POINTER(ctypes.c_double)
 
 
+class gb_snapshot(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("block", ctypes.c_int32), ("count", ctypes.c_int64),
+                ("lo", ctypes.POINTER(ctypes.c_double)), ("hi", ctypes.POINTER(ctypes.c_double)),
+                ("flo", ctypes.POINTER(ctypes.c_double)), ("cyc", ctypes.POINTER(ctypes.c_int32)),
+                ("gub", ctypes.c_double), ("generations", ctypes.c_int64)]
+
+
 class gb_result(ctypes.Structure):
     _fields_ = [("fmin_lo", ctypes.c_double), ("fmin_hi", ctypes.c_double),
                 ("n_boxes", ctypes.c_int64), ("n", ctypes.c_int32), ("status", ctypes.c_int32),
@@ -70,7 +77,8 @@ class gb_result(ctypes.Structure):
 EXPORTS = ["gb_default_options", "gb_create_problem", "gb_solve", "gb_solve_device",
            "gb_free_result", "gb_destroy_problem", "gb_status_str", "gb_last_error",
            "gb_eval_boxes", "gb_eval_boxes_noalloc", "gb_problem_info", "gb_measure_peak",
-           "gb_server_create", "gb_submit", "gb_poll", "gb_server_destroy", "gb_autotune"]
+           "gb_server_create", "gb_submit", "gb_poll", "gb_server_destroy", "gb_autotune",
+           "gb_snapshot_take", "gb_solve_resume", "gb_free_snapshot"]
 
 
 def library_path() -> str:
@@ -104,6 +112,12 @@ def load(build_if_missing: bool = True):
         getattr(L, fn).restype = ctypes.c_int
     L.gb_free_result.argtypes = [ctypes.POINTER(gb_result)]
     L.gb_free_result.restype = None
+    L.gb_snapshot_take.argtypes = [vp, ctypes.POINTER(gb_snapshot)]
+    L.gb_snapshot_take.restype = ctypes.c_int
+    L.gb_solve_resume.argtypes = [vp, ctypes.POINTER(gb_snapshot), ctypes.POINTER(gb_result)]
+    L.gb_solve_resume.restype = ctypes.c_int
+    L.gb_free_snapshot.argtypes = [ctypes.POINTER(gb_snapshot)]
+    L.gb_free_snapshot.restype = None
     L.gb_destroy_problem.argtypes = [vp]
     L.gb_destroy_problem.restype = None
     L.gb_status_str.argtypes = [ctypes.c_int]
@@ -322,6 +336,62 @@ def gb_measure_peak(device: int = 0, which: int = 0) -> tuple[float, float]:
     return ops.value, ms.value
 
 
+@dataclass
+class Snapshot:
+    """The region list a solve left (gb_snapshot): boxes in pool order, their
+    lower bounds, cycling words (bit 31: final), the incumbent and the
+    generations run so far."""
+    n: int
+    block: int
+    lo: np.ndarray
+    hi: np.ndarray
+    flo: np.ndarray
+    cyc: np.ndarray
+    gub: float
+    generations: int
+
+
+def gb_snapshot_take(prob: "_Problem") -> Snapshot:
+    L = load()
+    s = gb_snapshot()
+    rc = L.gb_snapshot_take(prob.handle, ctypes.byref(s))
+    try:
+        if rc != GB_OK:
+            raise GbError(rc, gb_last_error())
+        c, n = int(s.count), int(s.n)
+
+        def arr(ptr, count, dt):
+            if count == 0:
+                return np.zeros(0, dtype=dt)
+            return np.ctypeslib.as_array(ptr, shape=(count,)).astype(dt, copy=True)
+
+        return Snapshot(n, int(s.block), arr(s.lo, c * n, np.float64).reshape(c, n),
+                        arr(s.hi, c * n, np.float64).reshape(c, n), arr(s.flo, c, np.float64),
+                        arr(s.cyc, c, np.int32), float(s.gub), int(s.generations))
+    finally:
+        L.gb_free_snapshot(ctypes.byref(s))
+
+
+def gb_solve_resume(prob: "_Problem", snap: Snapshot, raise_on_error: bool = True) -> Result:
+    L = load()
+    lo = np.ascontiguousarray(snap.lo, dtype=np.float64).reshape(-1)
+    hi = np.ascontiguousarray(snap.hi, dtype=np.float64).reshape(-1)
+    flo = np.ascontiguousarray(snap.flo, dtype=np.float64)
+    cyc = np.ascontiguousarray(snap.cyc, dtype=np.int32)
+    s = gb_snapshot(int(snap.n), int(snap.block), len(flo), lo.ctypes.data_as(_PD), hi.ctypes.data_as(_PD),
+                    flo.ctypes.data_as(_PD), cyc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                    float(snap.gub), int(snap.generations))
+    r = gb_result()
+    rc = L.gb_solve_resume(prob.handle, ctypes.byref(s), ctypes.byref(r))
+    try:
+        res = _result(r, prob.n)
+    finally:
+        L.gb_free_result(ctypes.byref(r))
+    if rc not in (GB_OK, GB_E_CAPACITY, GB_E_LIMIT) and raise_on_error:
+        raise GbError(rc, gb_last_error())
+    return res
+
+
 class Solver:
     """Convenience wrapper: a problem description (nodes, root, tables, n,
     l, u, tol_f) plus options -> a device-resident problem."""
@@ -341,6 +411,12 @@ class Solver:
 
     def eval_boxes(self, lo, hi, block_index: int = -1, fp32: bool = False):
         return gb_eval_boxes(self.h, lo, hi, block_index, fp32)
+
+    def snapshot(self) -> "Snapshot":
+        return gb_snapshot_take(self.h)
+
+    def resume(self, snap: "Snapshot", raise_on_error: bool = True) -> Result:
+        return gb_solve_resume(self.h, snap, raise_on_error=raise_on_error)
 
     def info(self) -> dict:
         return gb_problem_info(self.h)

@@ -116,6 +116,9 @@ struct gb_problem {
     long long graph_kernels = 0;
     size_t device_bytes = 0;       // device memory held by the problem
     bool marks_used = false;       // a solve stamped record marks (cleared before the next one)
+    bool have_pool = false;        // a solve has left a pool to snapshot
+    std::vector<double> lo_host, hi_host;   // the bounds l, u (snapshot checks)
+    long long gen_base = 0;        // generations before this solve (resumed solves)
 };
 
 extern "C" {
@@ -210,6 +213,8 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
 
     gb_problem* p = new gb_problem();
     p->n = n;
+    p->lo_host.assign(l, l + n);
+    p->hi_host.assign(u, u + n);
     p->opt = opt;
     p->tol_f = tol_f;
     p->device = opt.device;
@@ -528,7 +533,7 @@ void gb_free_result(gb_result* r) {
 // its asynchronous copy has landed) and enqueues the next generation,
 // solve_finish gathers the output.  gb_solve runs the three blocking; the
 // serving loop interleaves many problems without blocking on any of them.
-__attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
+static gb_status solve_begin_from(gb_problem* p, const gb_snapshot* snap) {
     SolveRun& R = p->run;
     R = SolveRun{};
     R.t0 = std::chrono::steady_clock::now();
@@ -543,7 +548,41 @@ __attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
         GB_CU(cudaMemsetAsync(p->pool.rmark, 0, sizeof(unsigned) * (size_t)p->pool.R, s));
         p->marks_used = false;
     }
-    GB_CU(gb_launch_root_init(p->P, p->pool, p->E[0], p->G.tol_x, p->st, s));
+    p->have_pool = true;
+    if (!snap) {
+        p->gen_base = 0;
+        GB_CU(gb_launch_root_init(p->P, p->pool, p->E[0], p->G.tol_x, p->st, s));
+    } else {   // regions of a snapshot: upload, enter the pool, recompute their caches
+        p->gen_base = snap->generations;
+        const long long c = snap->count;
+        const size_t nb = (size_t)c * p->n;
+        double *d_lo = nullptr, *d_hi = nullptr, *d_flo = nullptr;
+        int* d_cyc = nullptr;
+        if (c > 0) {
+            cudaError_t e1 = cudaMallocAsync((void**)&d_lo, nb * sizeof(double), s);
+            cudaError_t e2 = cudaMallocAsync((void**)&d_hi, nb * sizeof(double), s);
+            cudaError_t e3 = cudaMallocAsync((void**)&d_flo, (size_t)c * sizeof(double), s);
+            cudaError_t e4 = cudaMallocAsync((void**)&d_cyc, (size_t)c * sizeof(int), s);
+            if (e1 || e2 || e3 || e4) {
+                if (d_lo) cudaFreeAsync(d_lo, s);
+                if (d_hi) cudaFreeAsync(d_hi, s);
+                if (d_flo) cudaFreeAsync(d_flo, s);
+                if (d_cyc) cudaFreeAsync(d_cyc, s);
+                return fail(GB_E_OOM, "device allocation for the snapshot");
+            }
+            GB_CU(cudaMemcpyAsync(d_lo, snap->lo, nb * sizeof(double), cudaMemcpyHostToDevice, s));
+            GB_CU(cudaMemcpyAsync(d_hi, snap->hi, nb * sizeof(double), cudaMemcpyHostToDevice, s));
+            GB_CU(cudaMemcpyAsync(d_flo, snap->flo, (size_t)c * sizeof(double), cudaMemcpyHostToDevice, s));
+            GB_CU(cudaMemcpyAsync(d_cyc, snap->cyc, (size_t)c * sizeof(int), cudaMemcpyHostToDevice, s));
+        }
+        GB_CU(gb_launch_resume(p->P, p->pool, p->E[0], c, d_lo, d_hi, d_flo, d_cyc, snap->gub, p->st, s));
+        if (c > 0) {
+            cudaFreeAsync(d_lo, s);
+            cudaFreeAsync(d_hi, s);
+            cudaFreeAsync(d_flo, s);
+            cudaFreeAsync(d_cyc, s);
+        }
+    }
     GB_CU(gb_launch_stats(p->E[0], p->G, 1, p->st, s));
     GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
     GB_CU(cudaEventRecord(p->ev_state, s));
@@ -551,6 +590,8 @@ __attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) {
     R.active = true;
     return GB_OK;
 }
+
+__attribute__((visibility("hidden"))) gb_status solve_begin(gb_problem* p) { return solve_begin_from(p, nullptr); }
 
 // Captures gens_per_sync consecutive generations as one CUDA graph per
 // starting pool buffer (once per problem; every argument of a generation is
@@ -714,10 +755,11 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
     return R.status;
 }
 
-static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
+static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes, const gb_snapshot* snap = nullptr) {
     if (!p || !out) return fail(GB_E_INVALID, "NULL argument");
     std::memset(out, 0, sizeof(*out));
-    gb_status st = solve_begin(p);
+    if (p->run.active) return fail(GB_E_BUSY, "a solve of this problem is in progress");
+    gb_status st = solve_begin_from(p, snap);
     if (st != GB_OK) return st;
     while (!solve_advance(p, true)) {
     }
@@ -728,6 +770,89 @@ static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes) {
 gb_status gb_solve(gb_problem* p, gb_result* out) { return solve_impl(p, out, true); }
 
 gb_status gb_solve_device(gb_problem* p, gb_result* out) { return solve_impl(p, out, false); }
+
+gb_status gb_snapshot_take(gb_problem* p, gb_snapshot* out) {
+    if (!p || !out) return fail(GB_E_INVALID, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    if (p->run.active) return fail(GB_E_BUSY, "a solve of this problem is in progress");
+    if (!p->have_pool) return fail(GB_E_INVALID, "no solve has run on this problem");
+    GB_CU(cudaSetDevice(p->device));
+    cudaStream_t s = p->stream;
+    GB_CU(cudaStreamSynchronize(s));
+    const GbState h = *p->st_host;   // state after the last solve's output pass (pool and gen unchanged)
+    const long long c = h.pool;
+    const int cur = (int)(h.gen & 1);
+    out->n = p->n;
+    out->block = p->hp.B;
+    out->count = c;
+    out->gub = gb_key_value(h.gub_key);
+    out->generations = p->gen_base + h.gen;
+    if (c == 0) return GB_OK;
+    const size_t nb = (size_t)c * p->n;
+    double *d_lo = nullptr, *d_hi = nullptr, *d_flo = nullptr;
+    int* d_cyc = nullptr;
+    cudaError_t e1 = cudaMallocAsync((void**)&d_lo, nb * sizeof(double), s);
+    cudaError_t e2 = cudaMallocAsync((void**)&d_hi, nb * sizeof(double), s);
+    cudaError_t e3 = cudaMallocAsync((void**)&d_flo, (size_t)c * sizeof(double), s);
+    cudaError_t e4 = cudaMallocAsync((void**)&d_cyc, (size_t)c * sizeof(int), s);
+    out->lo = (double*)std::malloc(nb * sizeof(double));
+    out->hi = (double*)std::malloc(nb * sizeof(double));
+    out->flo = (double*)std::malloc((size_t)c * sizeof(double));
+    out->cyc = (int32_t*)std::malloc((size_t)c * sizeof(int32_t));
+    gb_status rc = GB_OK;
+    if (e1 || e2 || e3 || e4) rc = fail(GB_E_OOM, "device allocation for the snapshot");
+    else if (!out->lo || !out->hi || !out->flo || !out->cyc) rc = fail(GB_E_OOM, "host allocation");
+    cudaError_t e = cudaSuccess;
+    if (rc == GB_OK) {
+        if ((e = gb_launch_snapshot(p->E[cur], c, p->pool, d_lo, d_hi, d_flo, d_cyc, s)) == cudaSuccess &&
+            (e = cudaMemcpyAsync(out->lo, d_lo, nb * sizeof(double), cudaMemcpyDeviceToHost, s)) == cudaSuccess &&
+            (e = cudaMemcpyAsync(out->hi, d_hi, nb * sizeof(double), cudaMemcpyDeviceToHost, s)) == cudaSuccess &&
+            (e = cudaMemcpyAsync(out->flo, d_flo, (size_t)c * sizeof(double), cudaMemcpyDeviceToHost, s)) ==
+                cudaSuccess &&
+            (e = cudaMemcpyAsync(out->cyc, d_cyc, (size_t)c * sizeof(int), cudaMemcpyDeviceToHost, s)) == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "snapshot");
+    }
+    if (d_lo) cudaFreeAsync(d_lo, s);
+    if (d_hi) cudaFreeAsync(d_hi, s);
+    if (d_flo) cudaFreeAsync(d_flo, s);
+    if (d_cyc) cudaFreeAsync(d_cyc, s);
+    if (rc != GB_OK) gb_free_snapshot(out);
+    return rc;
+}
+
+gb_status gb_solve_resume(gb_problem* p, const gb_snapshot* snap, gb_result* out) {
+    if (!p || !snap || !out) return fail(GB_E_INVALID, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    if (snap->n != p->n) return fail(GB_E_INVALID, "snapshot dimension differs from the problem's");
+    if (snap->count < 0 || (snap->count > 0 && (!snap->lo || !snap->hi || !snap->flo || !snap->cyc)))
+        return fail(GB_E_INVALID, "malformed snapshot");
+    if (snap->gub != snap->gub) return fail(GB_E_INVALID, "snapshot GUB is NaN");
+    if (p->pool.recs) return fail(GB_E_INVALID, "resume needs dense rows (pool_mode 1)");
+    if (snap->count > p->cap) return fail(GB_E_CAPACITY, "snapshot regions exceed the pool capacity");
+    const int n = p->n;
+    for (long long q = 0; q < snap->count; q++) {
+        const int c = snap->cyc[q] & 0x7fffffff;
+        if (c < 0 || c >= n) return fail(GB_E_INVALID, "snapshot cycling word out of range");
+        if (snap->flo[q] != snap->flo[q]) return fail(GB_E_INVALID, "snapshot lower bound is NaN");
+        const double* lo = snap->lo + (size_t)q * n;
+        const double* hi = snap->hi + (size_t)q * n;
+        for (int j = 0; j < n; j++)
+            if (!(lo[j] <= hi[j]) || !(lo[j] >= p->lo_host[j]) || !(hi[j] <= p->hi_host[j]))
+                return fail(GB_E_INVALID, "snapshot region outside the bounds (or lo > hi) at region " +
+                                              std::to_string(q));
+    }
+    return solve_impl(p, out, true, snap);
+}
+
+void gb_free_snapshot(gb_snapshot* snap) {
+    if (!snap) return;
+    std::free(snap->lo);
+    std::free(snap->hi);
+    std::free(snap->flo);
+    std::free(snap->cyc);
+    std::memset(snap, 0, sizeof(*snap));
+}
 
 gb_status gb_eval_boxes(gb_problem* p, const double* d_lo, const double* d_hi, int64_t nbox, int32_t blk,
                         int32_t fp32, double* d_F, double* d_Fmid, double* d_G, int32_t* d_mono, void* stream) {

@@ -1174,6 +1174,102 @@ __global__ void k_out_gather(GbEntries E, const unsigned* list, const GbState* s
 
 // ---------------------------------------------------------------------------
 // Parity hook: full evaluation of given boxes.
+// ---------------------------------------------------------------------------
+// Checkpoint and resume of the pool (the list L of section 3.1).
+// Every pool entry in pool order: its box, lower bound and cycling word.
+__global__ void k_snap_gather(GbEntries E, long long count, GbPool pool, double* out_lo, double* out_hi,
+                              double* out_flo, int* out_cyc) {
+    const int lane = threadIdx.x & 31;
+    const long long q = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (q >= count) return;
+    const unsigned slot = E.slot[q];
+    const int n = pool.n;
+    const View<double> X = box_view64(pool, slot);
+    for (int j = lane; j < n; j += 32) {
+        const iv64 x = X.get(j);
+        out_lo[(size_t)q * n + j] = x.lo;
+        out_hi[(size_t)q * n + j] = x.hi;
+    }
+    if (lane == 0) {
+        out_flo[q] = E.flo[q];
+        out_cyc[q] = E.cyc[q];
+    }
+}
+
+// Resume (dense rows): box q goes to slot q and entry q; its FP32 shadow is
+// the outward float of its bounds (as the root's and every split boundary's
+// are), its group caches (F, midpoint, FP32, samples) and coordinate
+// partials are recomputed in full, so a child of it reads the same cached
+// values as a child of the original box.  One warp per box.
+template <bool PR>
+__global__ void __launch_bounds__(128) k_resume_boxes(GbProg P, GbPool pool, GbEntries E, long long count,
+                                                      const double* lo, const double* hi, const double* flo,
+                                                      const int* cyc) {
+    const int lane = threadIdx.x & 31;
+    const long long q = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (q >= count) return;
+    const int n = P.n;
+    const unsigned slot = (unsigned)q;
+    for (int j = lane; j < n; j += 32) {
+        const double a = lo[(size_t)q * n + j], b = hi[(size_t)q * n + j];
+        pool.lo64[(size_t)slot * n + j] = a;
+        pool.hi64[(size_t)slot * n + j] = b;
+        if (pool.fp32) {
+            pool.lo32[(size_t)slot * n + j] = __double2float_rd(a);
+            pool.hi32[(size_t)slot * n + j] = __double2float_ru(b);
+        }
+    }
+    __syncwarp();
+    const View<double> X = box_view64(pool, slot);
+    const MidView MX{X};
+    View<float> X32;
+    if (pool.fp32) X32 = box_view32(pool, slot);
+    iv64 R[GB_MAX_TREGS];
+    iv32 R32[GB_MAX_TREGS];
+    int ops = 0;
+    for (int k = 0; k < P.n_sum; k++) {
+        const GbSum S = P.sums[k];
+        for (int g = lane; g < S.ngroups; g += 32) {
+            const size_t at = (size_t)slot * pool.NG + S.group0 + g;
+            const iv64 a = group_sum<PR, double>(P, S, g, X, R, ops);
+            const iv64 b = group_sum<PR, double>(P, S, g, MX, R, ops);
+            pool.gsum[at] = make_double2(a.lo, a.hi);
+            pool.gmid[at] = make_double2(b.lo, b.hi);
+            if (pool.fp32) {
+                const iv32 c = group_sum<PR, float>(P, S, g, X32, R32, ops);
+                pool.gsum32[at] = make_float2(c.lo, c.hi);
+            }
+            for (int j = 1; pool.gsamp && j <= pool.S; j++) {
+                const iv64 v = group_sum<PR, double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
+                pool.gsamp[((size_t)slot * pool.S + (j - 1)) * pool.NG + S.group0 + g] = make_double2(v.lo, v.hi);
+            }
+        }
+    }
+    if (pool.gdp) {
+        iv64 RA[GB_MAX_TREGS];
+        for (int b = lane; b < P.nb; b += 32) block_D(P, b, X, R, RA, pool.gdp + (size_t)slot * P.n_sum * n, ops);
+    }
+    if (lane == 0) {
+        E.flo[q] = flo[q];
+        E.slot[q] = slot;
+        E.cyc[q] = cyc[q];
+    }
+}
+
+// The device state of a resumed solve: `count` entries, incumbent gub.
+__global__ void k_resume_state(long long count, double gub, GbState* st) {
+    GbState s0 = {};
+    s0.pool = count;
+    s0.nfree = 0;
+    s0.bump = count;
+    s0.cap = st->cap;
+    s0.gub_key = gb_order_key(gub);
+    s0.gub_new_key = s0.gub_key;
+    s0.sel_T = ~0ull;
+    s0.min_key = ~0ull;
+    *st = s0;
+}
+
 __global__ void k_to_f32(const double* lo, const double* hi, float* lo32, float* hi32, long long count) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -1256,6 +1352,29 @@ cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEnt
     gb_launch_count++;
     if (P.any_prod) k_root_init<true><<<1, 256, 0, s>>>(P, pool, E, tol_x, st);
     else k_root_init<false><<<1, 256, 0, s>>>(P, pool, E, tol_x, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_snapshot(const GbEntries& E, long long count, const GbPool& pool, double* lo, double* hi,
+                               double* flo, int* cyc, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    gb_launch_count++;
+    k_snap_gather<<<grid_for(count * 32, 128), 128, 0, s>>>(E, count, pool, lo, hi, flo, cyc);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_resume(const GbProg& P, const GbPool& pool, const GbEntries& E, long long count,
+                             const double* lo, const double* hi, const double* flo, const int* cyc, double gub,
+                             GbState* st, cudaStream_t s) {
+    if (count > 0) {
+        gb_launch_count++;
+        if (P.any_prod)
+            k_resume_boxes<true><<<grid_for(count * 32, 128), 128, 0, s>>>(P, pool, E, count, lo, hi, flo, cyc);
+        else
+            k_resume_boxes<false><<<grid_for(count * 32, 128), 128, 0, s>>>(P, pool, E, count, lo, hi, flo, cyc);
+    }
+    gb_launch_count++;
+    k_resume_state<<<1, 1, 0, s>>>(count, gub, st);
     return cudaGetLastError();
 }
 

@@ -123,6 +123,14 @@ cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEnt
 // max_count bounds the grid.
 // Active count of the pool (read from the device state) for the next generation.
 cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, GbState* st, cudaStream_t s);
+// Checkpoint: every entry of E[0, count) with its box (lo, hi: count x n), LB and cycling word.
+cudaError_t gb_launch_snapshot(const GbEntries& E, long long count, const GbPool& pool, double* lo, double* hi,
+                               double* flo, int* cyc, cudaStream_t s);
+// Resume (dense rows): boxes to slots 0 .. count-1 with recomputed caches, entries in the given order, and
+// the device state of a pool of `count` entries with incumbent gub.
+cudaError_t gb_launch_resume(const GbProg& P, const GbPool& pool, const GbEntries& E, long long count,
+                             const double* lo, const double* hi, const double* flo, const int* cyc, double gub,
+                             GbState* st, cudaStream_t s);
 // One generation: select, partition, prepare parents, (term tables), evaluate
 // children (FP32 pass, compaction, FP64 pass), compact survivors,
 // materialise, free parents, finish, and the active count of the new pool.

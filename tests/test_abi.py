@@ -44,13 +44,15 @@ def test_struct_layouts_match_header(tmp_path):
     import subprocess
     src = tmp_path / "sizes.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gb.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(gb_node), sizeof(gb_options),'
-                   ' sizeof(gb_gen_stat), sizeof(gb_result), offsetof(gb_result, trace)); return 0;}\n')
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gb_node), sizeof(gb_options),'
+                   ' sizeof(gb_gen_stat), sizeof(gb_result), offsetof(gb_result, trace), sizeof(gb_snapshot),'
+                   ' offsetof(gb_snapshot, generations)); return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [D.NODE_DTYPE.itemsize, ctypes.sizeof(gb.gb_options), ctypes.sizeof(gb.gb_gen_stat),
-                   ctypes.sizeof(gb.gb_result), gb.gb_result.trace.offset]
+                   ctypes.sizeof(gb.gb_result), gb.gb_result.trace.offset, ctypes.sizeof(gb.gb_snapshot),
+                   gb.gb_snapshot.generations.offset]
 
 
 def test_invalid_problems_rejected_without_gpu():
