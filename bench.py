@@ -304,8 +304,8 @@ def run_serving(a):
             o.eval_mode = t["eval_mode"]
         return o
 
-    def serve(times):
-        srv = gb.Server(pool_budget_bytes=150 << 30, device=0, max_active=32)
+    def serve(times, fused=False):
+        srv = gb.Server(pool_budget_bytes=150 << 30, device=0, max_active=32, fused=fused)
         for _, p in stream[:3]:                       # warm-up
             rid = srv.submit(p, _serving_opts(gb, p, True))
             while srv.poll(rid) is None:
@@ -347,9 +347,14 @@ def run_serving(a):
         finish = max(finish, t) + sv
         fifo_lat.append(1e3 * (finish - t))
     fifo_lat = np.array(fifo_lat)
-    # saturation
+    # saturation, every request advancing on its own (the default), and with
+    # the fused child evaluation over the requests of a step
     sat = serve(np.zeros(len(stream)))
     sat_t = max(t for _, t in sat.values())
+    sat_u = serve(np.zeros(len(stream)), fused=True)
+    sat_ut = max(t for _, t in sat_u.values())
+    ok = ok and all(sat[i][0].status == 0 and sat[i][0].fmin_lo == sat_u[i][0].fmin_lo
+                    and sat[i][0].fmin_hi == sat_u[i][0].fmin_hi for i in range(len(stream)))
     fams = {}
     for _, p in stream:
         fams[p.family] = fams.get(p.family, 0) + 1
@@ -362,6 +367,9 @@ def run_serving(a):
                                    "150 GB budget, 32 slots, 4 GB per request, one best box "
                                    "per generation",
                        "value_is": "capacity: all requests submitted at once, solves per second",
+                       "fused_solves_per_s": len(stream) / sat_ut,
+                       "fused_is": "the same stream with the children of the requests of a step evaluated in "
+                                   "one persistent launch per generation (gb_server_set_fused)",
                        "sequential_fp64_solves_per_s": len(stream) / sum(service),
                        "speedup_vs_sequential_fp64": (len(stream) / sat_t) / (len(stream) / sum(service)),
                        "poisson_20_per_s": {

@@ -251,7 +251,15 @@ const char* gb_last_error(void);
  * runs its generations on its own stream, and the server advances whichever
  * request's previous generation has finished, so the requests' kernels
  * overlap on the device.  Finished requests free their memory and slot for
- * the queued ones.  A request's result does not depend on the others. */
+ * the queued ones.  A request's result does not depend on the others.
+ * Fused mode (gb_server_set_fused): the requests whose children are
+ * evaluated by the term-table FP32-then-FP64 kernel advance in steps of 4
+ * generations: every such request whose previous step has finished joins
+ * the next one, and each generation of a step evaluates the children of all
+ * its requests in one persistent launch (each warp takes a few children of
+ * one request, with that request's program, tables and incumbent); the
+ * other requests advance on their own as above.  Results are the same in
+ * both modes. */
 typedef struct gb_server gb_server;
 
 /* Starts a server (and its worker thread) on `device`.  pool_budget_bytes
@@ -259,6 +267,12 @@ typedef struct gb_server gb_server;
  * GB_E_INVALID for a zero budget or max_active < 1, GB_E_CUDA without the
  * device. */
 gb_status gb_server_create(size_t pool_budget_bytes, int32_t device, int32_t max_active, gb_server** out);
+
+/* fused = 1: one fused child-evaluation launch per generation over the
+ * eligible requests of a step; 0 (default): every request advances on its
+ * own, 4 generations per CUDA-graph replay.  May be changed at any time; it
+ * applies from the next step.  GB_E_INVALID for a NULL server. */
+gb_status gb_server_set_fused(gb_server* srv, int32_t fused);
 
 /* Queues a request (same arguments as gb_create_problem; everything is
  * copied) and returns at once with its id.  Never blocks on the GPU.

@@ -78,7 +78,7 @@ EXPORTS = ["gb_default_options", "gb_create_problem", "gb_solve", "gb_solve_devi
            "gb_free_result", "gb_destroy_problem", "gb_status_str", "gb_last_error",
            "gb_eval_boxes", "gb_eval_boxes_noalloc", "gb_problem_info", "gb_measure_peak",
            "gb_server_create", "gb_submit", "gb_poll", "gb_server_destroy", "gb_autotune",
-           "gb_snapshot_take", "gb_solve_resume", "gb_free_snapshot"]
+           "gb_snapshot_take", "gb_solve_resume", "gb_free_snapshot", "gb_server_set_fused"]
 
 
 def library_path() -> str:
@@ -134,6 +134,8 @@ def load(build_if_missing: bool = True):
     L.gb_measure_peak.restype = ctypes.c_int
     L.gb_server_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)]
     L.gb_server_create.restype = ctypes.c_int
+    L.gb_server_set_fused.argtypes = [vp, i32]
+    L.gb_server_set_fused.restype = ctypes.c_int
     L.gb_submit.argtypes = [vp, vp, i32, i32, ctypes.POINTER(_PD), ctypes.POINTER(i64), i32, i32, _PD, _PD,
                             ctypes.c_double, ctypes.POINTER(gb_options), ctypes.POINTER(ctypes.c_uint64)]
     L.gb_submit.restype = ctypes.c_int
@@ -428,12 +430,18 @@ class Solver:
 class Server:
     """Binding of the gb_server_* calls (continuous batching on one GPU)."""
 
-    def __init__(self, pool_budget_bytes: int, device: int = 0, max_active: int = 16):
+    def __init__(self, pool_budget_bytes: int, device: int = 0, max_active: int = 16, fused: bool = False):
         h = ctypes.c_void_p()
         rc = load().gb_server_create(int(pool_budget_bytes), int(device), int(max_active), ctypes.byref(h))
         if rc != GB_OK:
             raise GbError(rc, gb_last_error())
         self.h = h
+        self.set_fused(fused)
+
+    def set_fused(self, fused: bool):
+        rc = load().gb_server_set_fused(self.h, int(bool(fused)))
+        if rc != GB_OK:
+            raise GbError(rc, gb_last_error())
         self._n = {}
 
     def submit(self, problem, options: gb_options | None = None) -> int:

@@ -113,6 +113,8 @@ struct gb_problem {
     GbGenConst G{};
     gb_gen_stat* trace_dev = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // gens_per_sync generations starting on pool buffer 0 / 1
+    cudaGraphExec_t gpart[2][2] = {};  // fused serving: [pool buffer][before / after the child evaluation]
+    long long part_kernels[2][2] = {};
     long long graph_kernels = 0;
     size_t device_bytes = 0;       // device memory held by the problem
     bool marks_used = false;       // a solve stamped record marks (cleared before the next one)
@@ -163,6 +165,9 @@ void gb_destroy_problem(gb_problem* p) {
     if (p->ev_state) cudaEventDestroy(p->ev_state);
     for (cudaGraphExec_t g : p->gexec)
         if (g) cudaGraphExecDestroy(g);
+    for (auto& pp : p->gpart)
+        for (cudaGraphExec_t g : pp)
+            if (g) cudaGraphExecDestroy(g);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -632,7 +637,11 @@ static cudaError_t capture_graphs(gb_problem* p) {
 // Returns 1 when the generation loop has ended (R.status holds the outcome),
 // 0 when more generations were enqueued or (non-blocking) the previous ones
 // have not finished yet.
-__attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool block) {
+// 1: the loop has ended (R.status holds the outcome); 0: the previous
+// generation has finished and the next may be enqueued; -1: it has not
+// finished yet (non-blocking).  Reading the same state again gives the same
+// answer.
+__attribute__((visibility("hidden"))) int solve_check(gb_problem* p, bool block) {
     SolveRun& R = p->run;
     if (R.loop_done) return 1;
     auto stop = [&](gb_status st) {
@@ -641,10 +650,9 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
         return 1;
     };
     cudaError_t q = block ? cudaEventSynchronize(p->ev_state) : cudaEventQuery(p->ev_state);
-    if (q == cudaErrorNotReady) return 0;
+    if (q == cudaErrorNotReady) return -1;
     if (q != cudaSuccess) return stop(cuda_fail(q, "generation"));
     cudaSetDevice(p->device);
-    cudaStream_t s = p->stream;
     const GbState h = *p->st_host;
     float ms = 0.f;
     if (R.timed64 && cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) R.t64 += ms, R.n64++;
@@ -656,6 +664,20 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
                                                       : "box pool capacity reached"));
     if (h.active == 0) return stop(GB_OK);
     if (h.halt || h.gen >= p->opt.max_generations) return stop(fail(GB_E_LIMIT, "generation limit reached"));
+    return 0;
+}
+
+__attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool block) {
+    SolveRun& R = p->run;
+    const int c = solve_check(p, block);
+    if (c != 0) return c > 0 ? 1 : 0;
+    auto stop = [&](gb_status st) {
+        R.status = st;
+        R.loop_done = true;
+        return 1;
+    };
+    cudaStream_t s = p->stream;
+    const GbState h = *p->st_host;
     const long long l0 = gb_launches_so_far();
     const int cur = (int)(h.gen & 1);   // every completed generation swaps the pool buffers
     cudaError_t e = cudaSuccess;
@@ -753,6 +775,148 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
     out->status = R.status;
     R.active = false;
     return R.status;
+}
+
+// ---------------------------------------------------------------------------
+// Fused evaluation over several problems (serving): one generation of every
+// problem in lockstep -- its selection, partition and term tables on its own
+// stream, then one persistent launch evaluating the children of all of them,
+// then its compaction, materialisation and statistics on its own stream.
+#define GB_BATCH_RING 8   // descriptor buffers in flight (steps overlap)
+struct GbBatchCtx {
+    cudaStream_t ss[GB_BATCH_RING] = {};   // step i launches on ss[i % ring]: steps overlap
+    cudaEvent_t ev_ev[GB_BATCH_RING] = {};
+    std::vector<cudaEvent_t> ev_pre;
+    GbEvalDesc* h = nullptr;   // pinned [GB_BATCH_RING][GB_BATCH_MAX]
+    GbEvalDesc* d = nullptr;   // device, same shape
+    cudaEvent_t ev_slot[GB_BATCH_RING] = {};   // the fused launch that last read each buffer
+    int next = 0;
+};
+
+__attribute__((visibility("hidden"))) GbBatchCtx* batch_create(int device) {
+    if (cudaSetDevice(device) != cudaSuccess) return nullptr;
+    GbBatchCtx* B = new GbBatchCtx();
+    bool ok = true;
+    for (int i = 0; ok && i < GB_BATCH_RING; i++)
+        ok = cudaStreamCreateWithFlags(&B->ss[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&B->ev_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok &&
+              cudaMallocHost((void**)&B->h, sizeof(GbEvalDesc) * GB_BATCH_MAX * GB_BATCH_RING) == cudaSuccess &&
+              cudaMalloc((void**)&B->d, sizeof(GbEvalDesc) * GB_BATCH_MAX * GB_BATCH_RING) == cudaSuccess;
+    B->ev_pre.assign(GB_BATCH_MAX, nullptr);
+    for (int i = 0; ok && i < GB_BATCH_MAX; i++)
+        ok = cudaEventCreateWithFlags(&B->ev_pre[i], cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < GB_BATCH_RING; i++)
+        ok = cudaEventCreateWithFlags(&B->ev_slot[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        batch_destroy(B);
+        return nullptr;
+    }
+    return B;
+}
+
+__attribute__((visibility("hidden"))) void batch_destroy(GbBatchCtx* B) {
+    if (!B) return;
+    for (cudaStream_t s : B->ss)
+        if (s) cudaStreamSynchronize(s);
+    for (cudaEvent_t e : B->ev_pre)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : B->ev_ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : B->ev_slot)
+        if (e) cudaEventDestroy(e);
+    if (B->h) cudaFreeHost(B->h);
+    if (B->d) cudaFree(B->d);
+    for (cudaStream_t s : B->ss)
+        if (s) cudaStreamDestroy(s);
+    delete B;
+}
+
+__attribute__((visibility("hidden"))) void solve_abort(gb_problem* p, gb_status st) {
+    p->run.status = st;
+    p->run.loop_done = true;
+}
+
+// Problems whose child evaluation is the FP32-then-FP64 warp-per-child table
+// kernel can join a fused launch.
+__attribute__((visibility("hidden"))) bool solve_fusable(const gb_problem* p) {
+    return p->use_tabs && p->tabs.warp && p->G.fp32 && p->opt.fp32_prefilter;
+}
+
+// The part (1: before, 2: after the child evaluation) of a generation that
+// starts on pool buffer cur, captured once per problem as a CUDA graph
+// (every size comes from the device state) and launched on its stream.
+static cudaError_t launch_part(gb_problem* p, int cur, int part, long long* nl) {
+    cudaGraphExec_t& gx = p->gpart[cur][part - 1];
+    if (!gx) {
+        cudaStream_t s = p->stream;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        long long n1 = 0;
+        e = gb_launch_generation(p->P, p->pool, p->E[cur], p->E[1 - cur], p->par, p->ch, p->sp, p->sc, &p->tabs,
+                                 p->G, p->cap, p->Cmax, p->st, s, nullptr, &n1, part);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        p->part_kernels[cur][part - 1] = n1;
+    }
+    *nl = p->part_kernels[cur][part - 1];
+    return cudaGraphLaunch(gx, p->stream);
+}
+
+// G consecutive generations of every problem in probs (each fusable, its
+// previous generation finished: solve_check returned 0), one fused
+// child-evaluation launch per generation; a problem whose search ends inside
+// the run skips its remaining generations (every kernel checks st->halt),
+// as in a graph of G generations.  The state is read back after the last.
+__attribute__((visibility("hidden"))) gb_status batch_generation(gb_problem* const* probs, int k, GbBatchCtx* B,
+                                                                int G) {
+    if (k <= 0) return GB_OK;
+    if (k > GB_BATCH_MAX) return fail(GB_E_INVALID, "too many problems for one fused launch");
+    if (G < 1) G = 1;
+    for (int g = 0; g < G; g++) {
+        // a descriptor buffer whose last fused launch has finished
+        const int slot = B->next;
+        B->next = (B->next + 1) % GB_BATCH_RING;
+        GB_CU(cudaEventSynchronize(B->ev_slot[slot]));
+        GbEvalDesc* hd = B->h + (size_t)slot * GB_BATCH_MAX;
+        GbEvalDesc* dd = B->d + (size_t)slot * GB_BATCH_MAX;
+        cudaStream_t bs = B->ss[slot];
+        cudaEvent_t ev_eval = B->ev_ev[slot];
+        long long units = 0;   // work units the step can hold (children per generation at most)
+        for (int i = 0; i < k; i++) {
+            gb_problem* p = probs[i];
+            const int cur = (int)((p->st_host->gen + g) & 1);
+            long long nl = 0;
+            GB_CU(launch_part(p, cur, 1, &nl));
+            GB_CU(cudaEventRecord(B->ev_pre[i], p->stream));
+            hd[i] = GbEvalDesc{p->P, p->pool, p->par, p->tabs, p->ch, p->sp, p->st};
+            p->run.launches += nl + 1;   // + its share of the fused launch
+            units += (p->Cmax + 3) / 4;
+        }
+        GB_CU(cudaMemcpyAsync(dd, hd, sizeof(GbEvalDesc) * (size_t)k, cudaMemcpyHostToDevice, bs));
+        for (int i = 0; i < k; i++) GB_CU(cudaStreamWaitEvent(bs, B->ev_pre[i], 0));
+        GB_CU(gb_launch_eval3264_batch(dd, k, units, bs));
+        GB_CU(cudaEventRecord(ev_eval, bs));
+        GB_CU(cudaEventRecord(B->ev_slot[slot], bs));
+        for (int i = 0; i < k; i++) {
+            gb_problem* p = probs[i];
+            const int cur = (int)((p->st_host->gen + g) & 1);
+            long long nl = 0;
+            GB_CU(cudaStreamWaitEvent(p->stream, ev_eval, 0));
+            GB_CU(launch_part(p, cur, 2, &nl));
+            p->run.launches += nl;
+        }
+    }
+    for (int i = 0; i < k; i++) {
+        gb_problem* p = probs[i];
+        GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, p->stream));
+        GB_CU(cudaEventRecord(p->ev_state, p->stream));
+    }
+    return GB_OK;
 }
 
 static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes, const gb_snapshot* snap = nullptr) {

@@ -1389,13 +1389,16 @@ cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long c
 cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEntries& E, const GbEntries& E_new,
                                  const GbParents& par, const GbChildren& ch, const GbSplit& sp, const GbScan& sc,
                                  const GbTabs* tabs, const GbGenConst& G, long long cap, long long Cmax,
-                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch) {
+                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch, int part) {
     long long n0 = gb_launch_count;
     cudaError_t e;
     const unsigned gpool = (unsigned)std::min<long long>(grid_for(cap, 256), 152 * 8);
     const unsigned gtile_pool = (unsigned)std::min<long long>(grid_for(cap, GB_TILE), 152 * 8);
     const unsigned gtile_ch = (unsigned)std::min<long long>(grid_for(Cmax, GB_TILE), 152 * 8);
     const unsigned gch = (unsigned)std::min<long long>(grid_for(Cmax, 128), 152 * 32);
+    // part 0: the whole generation; 1: up to the child evaluation; 2: after it
+    if (part == 2) goto after_eval;
+    {
     // (the selection mode and the K = 1 threshold were set by the last k_stats)
     if (G.K > 1) {
         for (int pass = 0; pass < 4; pass++) {
@@ -1416,6 +1419,10 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
         if ((e = gb_launch_ptab(P, pool, par, *tabs, G.K, sp, st, s)) != cudaSuccess) return e;
         gb_launch_count++;
         if ((e = gb_launch_ptab_d(P, pool, par, *tabs, G.K, P.B, st, s)) != cudaSuccess) return e;
+    }
+    if (part == 1) {   // up to the child evaluation (a fused launch over many problems follows)
+        if (nlaunch) *nlaunch = gb_launch_count - n0;
+        return cudaGetLastError();
     }
     const bool fused = G.fp32 && tabs && tabs->warp;
     if (fused) {
@@ -1453,6 +1460,8 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
         }
         if (ev) cudaEventRecord(ev[1], s);
     }
+    }
+after_eval:
     if (Cmax <= (1LL << 16)) {
         gb_launch_count++;
         k_cc_small<<<1, 1024, 0, s>>>(ch, G, st);

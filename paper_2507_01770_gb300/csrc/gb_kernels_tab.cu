@@ -816,12 +816,88 @@ __global__ void __launch_bounds__(128) k_eval3264_tabw(GbProg P, GbPool pool, Gb
     }
 }
 
+// The same FP32-then-FP64 warp-per-child evaluation over the children of
+// many problems in one persistent launch (continuous batching): the work is
+// the concatenation of every live problem's children in units of
+// GB_BATCH_UNIT; a warp evaluates a unit's children with that problem's
+// arguments and then adds its counters and GUB samples to that problem's
+// state, exactly as the per-problem kernel does.
+#define GB_BATCH_UNIT 4
+__global__ void __launch_bounds__(128) k_eval3264_batch(const GbEvalDesc* __restrict__ D, int nreq) {
+    __shared__ long long off[GB_BATCH_MAX + 1];
+    if (threadIdx.x == 0) {
+        long long o = 0;
+        for (int q = 0; q < nreq; q++) {
+            off[q] = o;
+            const GbState* st = D[q].st;
+            if (!st->halt) o += (st->nch + GB_BATCH_UNIT - 1) / GB_BATCH_UNIT;
+        }
+        off[nreq] = o;
+    }
+    __syncthreads();
+    const long long total = off[nreq];
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; u < total; u += nw) {
+        int lo = 0, hi = nreq - 1;   // the problem q with off[q] <= u < off[q + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const GbEvalDesc& d = D[lo];
+        GbState* st = d.st;
+        const long long lim = st->nch;
+        const double gub_prev = gb_key_value(st->gub_key);
+        const long long c0 = (u - off[lo]) * GB_BATCH_UNIT;
+        const long long c1 = min(lim, c0 + GB_BATCH_UNIT);
+        int red32 = 0, pops32 = 0, red64 = 0, pops64 = 0;
+        unsigned long long nv = 0, n32 = 0, key = ~0ull;
+        bool has = false;
+        for (long long ci = c0; ci < c1; ci++) {
+            const int v = eval32_tab_child_w(d.P, d.pool, d.par, d.Tb, d.ch, ci, d.sp, gub_prev, red32, pops32, lane);
+            if (v < 0) continue;
+            nv++;
+            if (v == 0) continue;
+            n32++;
+            unsigned long long k2 = ~0ull;
+            bool h2 = false;
+            eval64_tab_child_w(d.P, d.pool, d.par, d.Tb, d.ch, ci, d.sp, gub_prev, &k2, &h2, red64, pops64, lane);
+            if (h2 && k2 < key) key = k2, has = true;
+        }
+        warp_min_gub(key, has, st);
+        warp_add_ops((lane == 0 ? red32 : 0) + pops32, &st->ops32);
+        warp_add_ops((lane == 0 ? red64 : 0) + pops64, &st->ops64);
+        if (lane == 0 && nv) {
+            atomicAdd((unsigned long long*)&st->evals32, nv);
+            atomicAdd((unsigned long long*)&st->children, nv);
+        }
+        if (lane == 0 && n32) {
+            atomicAdd((unsigned long long*)&st->evals64, n32);
+            atomicAdd((unsigned long long*)&st->mids, n32);
+            atomicAdd((unsigned long long*)&st->kept32, n32);
+            atomicAdd((unsigned long long*)&st->n32, n32);
+        }
+    }
+}
+
 unsigned grid_for(long long items, int per_block) {
     long long g = (items + per_block - 1) / per_block;
     return (unsigned)(g < 1 ? 1 : g);
 }
 
 }  // namespace
+
+extern thread_local long long gb_launch_count;   // kernels launched by this thread (gb_kernels.cu)
+
+cudaError_t gb_launch_eval3264_batch(const GbEvalDesc* d_desc, int nreq, long long max_units, cudaStream_t s) {
+    if (nreq <= 0) return cudaSuccess;
+    if (nreq > GB_BATCH_MAX) return cudaErrorInvalidValue;
+    gb_launch_count++;
+    const unsigned grid = (unsigned)std::min<long long>(grid_for(max_units * 32, 128), 152 * 8);
+    k_eval3264_batch<<<grid, 128, 0, s>>>(d_desc, nreq);
+    return cudaGetLastError();
+}
 
 cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                            long long K, const GbSplit& sp, GbState* st, cudaStream_t s) {

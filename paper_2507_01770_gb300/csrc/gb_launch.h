@@ -136,11 +136,30 @@ cudaError_t gb_launch_resume(const GbProg& P, const GbPool& pool, const GbEntrie
 // materialise, free parents, finish, and the active count of the new pool.
 // Every size is read from the device state.  ev (4 events or null) brackets
 // the FP64 and FP32 evaluation kernels.  Returns the kernels launched in
-// *nlaunch.
+// *nlaunch.  part 1 stops before the child evaluation and part 2 starts
+// after it (a fused evaluation over several problems goes between them).
 cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEntries& E, const GbEntries& E_new,
                                  const GbParents& par, const GbChildren& ch, const GbSplit& sp, const GbScan& sc,
                                  const GbTabs* tabs, const GbGenConst& G, long long cap, long long Cmax,
-                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch);
+                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch, int part = 0);
+
+// One problem of a fused child evaluation: the arguments of its
+// k_eval3264_tabw launch (term tables, one child per warp, FP32 then FP64).
+struct GbEvalDesc {
+    GbProg P;
+    GbPool pool;
+    GbParents par;
+    GbTabs Tb;
+    GbChildren ch;
+    GbSplit sp;
+    GbState* st;
+};
+#define GB_BATCH_MAX 256   // problems per fused launch
+// The children of every problem of D[0, nreq) in one persistent launch on s:
+// each warp takes units of a few children of one problem in turn, with that
+// problem's program, tables, incumbent and counters.  max_units (the units
+// the step can hold at most) sizes the grid.
+cudaError_t gb_launch_eval3264_batch(const GbEvalDesc* d_desc, int nreq, long long max_units, cudaStream_t s);
 // Final output: entries with flo <= GUB, in pool order, gathered into rows.
 cudaError_t gb_launch_output(const GbEntries& E, long long count, const GbPool& pool, double gub,
                              unsigned* list, double* out_lo, double* out_hi, double* out_flo,
@@ -155,6 +174,14 @@ extern "C" gb_status gb_internal_fail(gb_status s, const char* msg);
 // resumable solve (gb_api.cu), used by the serving loop (gb_server.cpp)
 extern "C" gb_status solve_begin(gb_problem* p);
 extern "C" int solve_advance(gb_problem* p, bool block);
+extern "C" int solve_check(gb_problem* p, bool block);
+extern "C" void solve_abort(gb_problem* p, gb_status st);   // ends the loop with st (solve_finish still runs)
+// fused evaluation over several problems (gb_api.cu), used by the serving loop
+struct GbBatchCtx;
+extern "C" GbBatchCtx* batch_create(int device);
+extern "C" void batch_destroy(GbBatchCtx* B);
+extern "C" bool solve_fusable(const gb_problem* p);
+extern "C" gb_status batch_generation(gb_problem* const* probs, int k, GbBatchCtx* B, int G);
 extern "C" gb_status solve_finish(gb_problem* p, gb_result* out, bool copy_boxes);
 extern "C" size_t gb_internal_device_bytes(const gb_problem* p);
 // per-parent term tables (gb_kernels_tab.cu); sizes read from the device state

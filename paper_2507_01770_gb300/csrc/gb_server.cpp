@@ -1,5 +1,12 @@
 // Serving: continuous batching of minimisation requests on one GPU.
 //
+// Fused mode: the running requests whose children go through the term-table
+// FP32-then-FP64 kernel are advanced in steps: every such request whose
+// previous generation has finished joins the next step, which enqueues a
+// generation of each of them with a single fused child-evaluation launch
+// over all their children (batch_generation); the other requests advance as
+// below.
+//
 // gb_submit copies a request (objective, bounds, options) and returns at once.
 // A worker thread admits queued requests in arrival order while the device
 // memory they need fits the server's budget and a slot is free, runs every
@@ -8,6 +15,7 @@
 // kernels overlap on the device -- and retires finished requests, which frees
 // their memory and slots for the next ones.  Each request's search depends
 // only on its own state, so its result is the same alone and in a mix.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
@@ -57,6 +65,8 @@ struct gb_server {
     std::map<uint64_t, std::shared_ptr<Request>> all;
     uint64_t next_id = 1;
     bool stop = false;
+    int fused = 0;
+    GbBatchCtx* batch = nullptr;   // worker thread only
     std::thread worker;
 };
 
@@ -119,9 +129,23 @@ void worker_loop(gb_server* S) {
         }
         // ---- advance every request whose previous generation has finished ----
         bool progressed = false;
+        int fused;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            fused = S->fused;
+        }
+        if (fused && !S->batch) S->batch = batch_create(S->device);
+        std::vector<gb_problem*> step;   // fusable requests ready for their next generation
         for (size_t k = 0; k < S->running.size();) {
             auto r = S->running[k];
-            int done = solve_advance(r->prob, false);
+            int done;
+            if (fused && S->batch && solve_fusable(r->prob)) {
+                const int c = solve_check(r->prob, false);   // launched by the fused step below
+                if (c == 0) step.push_back(r->prob);
+                done = c > 0;
+            } else {
+                done = solve_advance(r->prob, false);
+            }
             if (!done) {
                 k++;
                 continue;
@@ -133,6 +157,16 @@ void worker_loop(gb_server* S) {
             r->prob = nullptr;
             S->running.erase(S->running.begin() + k);
             finish_request(S, r, st);
+        }
+        if (!step.empty()) {   // every ready request joins this step; the others are still running theirs
+            for (size_t b = 0; b < step.size(); b += GB_BATCH_MAX) {
+                const int k = (int)std::min<size_t>(GB_BATCH_MAX, step.size() - b);
+                if (batch_generation(step.data() + b, k, S->batch, 4) != GB_OK) {
+                    // a failed enqueue ends those requests with the error
+                    for (int i = 0; i < k; i++) solve_abort(step[b + i], GB_E_CUDA);
+                }
+            }
+            progressed = true;
         }
         if (!progressed && !S->running.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
@@ -201,6 +235,13 @@ gb_status gb_submit(gb_server* S, const gb_node* dag, int32_t n_nodes, int32_t r
     return GB_OK;
 }
 
+gb_status gb_server_set_fused(gb_server* S, int32_t fused) {
+    if (!S) return gb_internal_fail(GB_E_INVALID, "NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->fused = fused ? 1 : 0;
+    return GB_OK;
+}
+
 gb_status gb_poll(gb_server* S, uint64_t id, gb_result* out) {
     if (!S || !out) return gb_internal_fail(GB_E_INVALID, "bad gb_poll arguments");
     std::shared_ptr<Request> r;
@@ -227,6 +268,7 @@ gb_status gb_server_destroy(gb_server* S) {
     S->cv.notify_all();
     if (S->worker.joinable()) S->worker.join();
     cudaSetDevice(S->device);
+    batch_destroy(S->batch);
     for (auto& r : S->running)
         if (r->prob) gb_destroy_problem(r->prob);
     for (auto& kv : S->all) gb_free_result(&kv.second->result);

@@ -1,7 +1,8 @@
 """Serving (continuous batching) on the GPU: a mix of requests of different
 families and dimensions submitted together runs concurrently, and every
 request's result is the same as when it is solved alone (enclosure, boxes and
-per-generation trace bit for bit: each search depends only on its own state)."""
+per-generation trace bit for bit: each search depends only on its own state),
+with and without the fused child evaluation over the requests."""
 import time
 
 import numpy as np
@@ -44,14 +45,29 @@ def _wait(srv, ids, timeout=300.0):
     return out
 
 
-def test_results_identical_alone_and_in_the_mix():
-    reqs = _mix()
+def _fusable_mix():
+    # every request on the term-table FP32-then-FP64 kernel: all in one fused launch per step
+    reqs = []
+    for k in range(6):
+        reqs.append((S.chain(n=10 + 5 * k, seed=40 + k),
+                     dict(block=5, split_m=2, split_d=5, max_children=4 * 32, fp32_prefilter=1)))
+        reqs.append((S.ackley(n=8 + 4 * k, seed=50 + k),
+                     dict(block=8, split_m=2, split_d=8, max_children=2 << 8, fp32_prefilter=1)))
+        reqs.append((S.sep_cos(n=4 + k, seed=60 + k),
+                     dict(block=4, split_m=4, split_d=2, max_children=4 * 16, fp32_prefilter=1)))
+    return reqs
+
+
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("mix", ["mixed", "fusable"])
+def test_results_identical_alone_and_in_the_mix(fused, mix):
+    reqs = _mix() if mix == "mixed" else _fusable_mix()
     alone = []
     for p, o in reqs:
         s = gb.Solver(p, pool_bytes=1 << 28, **o)
         alone.append(s.solve())
         s.close()
-    srv = gb.Server(pool_budget_bytes=8 << 30, device=0, max_active=6)
+    srv = gb.Server(pool_budget_bytes=8 << 30, device=0, max_active=6 if mix == "mixed" else 12, fused=fused)
     ids = []
     for p, o in reqs:
         opts = gb.gb_default_options(pool_bytes=1 << 28, **o)
