@@ -471,10 +471,13 @@ __global__ void k_part_scatter(GbEntries E, GbGenConst G, const GbState* st, con
 // Per parent: split coordinates and piece boundaries (Eqs. 10-11 with the
 // rounding reading: boundary t = RN(lo + RN(RN(RN(hi - lo) / m) * t)),
 // boundary 0 = lo, boundary m = hi).
+// One thread per (parent, split coordinate): the split position of the
+// parent and the piece boundaries of one coordinate (the divisions of the
+// coordinates run in parallel).
 __global__ void k_prep(GbProg P, GbPool pool, GbParents par, GbSplit sp, GbState* st) {
     if (st->halt) return;
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p == 0) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx == 0) {
         st->gub_new_key = st->gub_key;
         st->nfree = st->nfree_after_drop;
         st->kept = 0;
@@ -484,6 +487,8 @@ __global__ void k_prep(GbProg P, GbPool pool, GbParents par, GbSplit sp, GbState
         st->overflow = 0;
     }
     const long long npar = st->parents;
+    const long long p = idx / sp.dmax;
+    const int k = (int)(idx - p * sp.dmax);
     if (p >= npar) return;
     const int n = P.n, B = P.B;
     int c = par.cyc[p] & 0x7fffffff;
@@ -491,11 +496,11 @@ __global__ void k_prep(GbProg P, GbPool pool, GbParents par, GbSplit sp, GbState
     int e = min((b + 1) * B, n);
     int dd = min(sp.d, e - c);
     int nxt = (c + dd == n) ? 0 : c + dd;
-    par.info[p] = make_int4(c, dd, b, nxt);
+    if (k == 0) par.info[p] = make_int4(c, dd, b, nxt);
     unsigned slot = par.slot[p];
     const int ms = sp.m + 1;
     const View<double> PX = box_view64(pool, slot);
-    for (int k = 0; k < dd; k++) {
+    if (k < dd) {
         int j = c + k;
         const iv64 pj = PX.get(j);
         double lo = pj.lo, hi = pj.hi;
@@ -1412,7 +1417,7 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     k_scan_tiles<<<1, 1024, 0, s>>>(3, sc.tile_cnt, sc.tile_off, sc.max_tiles, 0, 0, G, st);
     k_part_scatter<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_off, sc.max_tiles, E_new, par, pool.freel);
     gb_launch_count++;
-    k_prep<<<grid_for(G.K, 128), 128, 0, s>>>(P, pool, par, sp, st);
+    k_prep<<<grid_for(G.K * (long long)sp.dmax, 128), 128, 0, s>>>(P, pool, par, sp, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (tabs) {
         gb_launch_count++;
