@@ -128,3 +128,29 @@ def test_malformed_snapshots_are_refused():
             s.resume(b)
         assert e.value.status == gb.GB_E_INVALID, change
     s.close()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_regions_solved_one_after_another(world):
+    # the sharded solve of paper_2507_01770_gb300.shard with its ranks run in
+    # turn on this GPU: the merged enclosure is rigorous and within tol_f,
+    # and the merged regions cover the planted minimiser
+    from paper_2507_01770_gb300 import shard
+    p = S.chain(n=12, seed=3, block=6)
+    opts = dict(block=6, split_m=2, split_d=3, max_children=8 * 8)
+    s0, first = _solve(p, max_generations=6, **opts)
+    snap = s0.snapshot()
+    s0.close()
+    parts = []
+    for sh in shard.split_snapshot(snap, world):
+        s = gb.Solver(p, **opts)
+        r = s.resume(sh)
+        s.close()
+        assert r.status == gb.GB_OK
+        parts.append((r.fmin_lo, r.fmin_hi, r.box_lo, r.box_hi, r.box_flo, r.generations, r.status))
+    m = shard.merge_results(parts, p.n)
+    assert m.fmin_lo <= 0.0 <= m.fmin_hi and m.fmin_hi - m.fmin_lo <= p.tol_f
+    assert np.any(np.all((m.box_lo <= p.s) & (p.s <= m.box_hi), axis=1))
+    full_s, full = _solve(p, **opts)
+    full_s.close()
+    assert max(full.fmin_lo, m.fmin_lo) <= min(full.fmin_hi, m.fmin_hi)

@@ -1,0 +1,98 @@
+"""One problem over several ranks (paper_2507_01770_gb300.shard), host logic
+with two gloo ranks on the CPU: the snapshot of the first phase is dealt out
+round-robin, every rank resumes its share, and the merged enclosure is
+[min GLB, min GUB] with the regions whose LB is not above the global GUB.
+The solver is a stand-in (no GPU): it returns its shard's regions with a
+rank-dependent incumbent, so the test checks the plumbing and the merge."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+class _FakeResult:
+    def __init__(self, lo, hi, flo, gub, gens):
+        self.box_lo, self.box_hi, self.box_flo = lo, hi, flo
+        self.fmin_lo = float(flo.min()) if len(flo) else np.inf
+        self.fmin_hi, self.generations, self.status = gub, gens, 0
+
+
+class _FakeSolver:
+    """First phase: 10 regions of a 3-D box with LB = q / 10, GUB 0.55.
+    Resume: keeps the shard's regions with LB <= a rank-dependent GUB."""
+
+    def __init__(self, rank, max_gen):
+        self.rank, self.max_gen = rank, max_gen
+
+    def solve(self, raise_on_error=True):
+        return _FakeResult(None, None, np.zeros(0), 0.55, self.max_gen)
+
+    def snapshot(self):
+        import paper_2507_01770_gb300 as gb
+        q = np.arange(10, dtype=np.float64)
+        lo = np.stack([q, q, q], axis=1)
+        return gb.Snapshot(3, 3, lo, lo + 0.5, q / 10, np.zeros(10, np.int32), 0.55, self.max_gen)
+
+    def resume(self, snap, raise_on_error=True):
+        gub = [0.5, 0.25][self.rank]
+        keep = snap.flo <= gub
+        return _FakeResult(snap.lo[keep], snap.hi[keep], snap.flo[keep], gub, 7 + self.rank)
+
+    def close(self):
+        pass
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    from paper_2507_01770_gb300 import shard
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    res = shard.sharded_solve(lambda g: _FakeSolver(rank, g), 5, dist, rank, world)
+    out.put((rank, res.fmin_lo, res.fmin_hi, res.box_flo.tolist(), res.generations))
+    dist.destroy_process_group()
+
+
+def test_sharded_solve_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, glb, gub, flo, gens in got:
+        # rank 0 keeps LB <= 0.5 of regions 0, 2, 4 (0, .2, .4); rank 1 LB <= .25 of 1, 3, ... (.1)
+        # global GUB = 0.25: the kept regions are those with LB <= 0.25
+        assert gub == 0.25
+        assert sorted(flo) == [0.0, 0.1, 0.2]
+        assert glb == 0.0
+        assert gens == [7, 8]
+
+
+def test_split_and_merge_without_ranks():
+    import paper_2507_01770_gb300 as gb
+    from paper_2507_01770_gb300 import shard
+    q = np.arange(7, dtype=np.float64)
+    lo = np.stack([q, -q], axis=1)
+    snap = gb.Snapshot(2, 2, lo, lo + 1, q, np.arange(7, dtype=np.int32) % 2, 3.5, 4)
+    parts = shard.split_snapshot(snap, 3)
+    assert [list(p.flo) for p in parts] == [[0, 3, 6], [1, 4], [2, 5]]
+    assert all(p.gub == 3.5 and p.generations == 4 and p.n == 2 for p in parts)
+    assert np.array_equal(np.concatenate([p.lo for p in parts])[np.argsort(np.concatenate([p.flo for p in parts]))],
+                          lo)
+    m = shard.merge_results([(0.0, 2.0, lo[:3], lo[:3] + 1, q[:3], 1, 0), (1.0, 1.5, lo[3:], lo[3:] + 1, q[3:], 2, 0)],
+                            2)
+    assert m.fmin_hi == 1.5 and m.fmin_lo == 0.0 and list(m.box_flo) == [0.0, 1.0]
