@@ -3,12 +3,13 @@
 The branch and bound of section 3.1 keeps a list of regions; regions are
 independent, so after a first phase on one rank the list can be dealt out
 (the paper's outlook to GPU clusters, sections 3.2 and 5).  Each rank
-continues its share with ``gb_solve_resume`` on its own GPU, starting from
-the incumbent of the split; the global enclosure is [min GLB, min GUB] over
-the ranks (every rank's regions end with LB >= its GUB - tol_f >= the
-global GUB - tol_f, so the width stays within tol_f), and the output
-regions are those with LB <= the global GUB.  Ranks do not exchange the
-incumbent during their phase (no collective on the data path).
+continues its share with ``gb_solve_resume`` on its own GPU in rounds of a
+fixed number of generations; between rounds the ranks exchange their
+incumbents (a min over the ranks' GUBs, 8 bytes each: the one exchange of
+the path).  The global enclosure is [min GLB, min GUB] over the ranks
+(every rank's regions end with LB >= its GUB - tol_f >= the global GUB -
+tol_f, so the width stays within tol_f), and the output regions are those
+with LB <= the global GUB.
 
 Only host-side logic lives here: splitting a snapshot, merging results and
 the collectives that carry them (any ``torch.distributed`` backend).  The
@@ -76,15 +77,22 @@ def _pack(snap: Snapshot):
                 generations=snap.generations)
 
 
-def sharded_solve(make_solver, first_generations: int, dist, rank: int, world: int) -> ShardedResult:
+def sharded_solve(make_solver, first_generations: int, dist, rank: int, world: int,
+                  round_generations: int = 64) -> ShardedResult:
     """Solve one problem on `world` ranks (one GPU each).
 
     make_solver(max_generations) -> an object with ``solve(raise_on_error)``,
-    ``snapshot()``, ``resume(snapshot)`` and ``close()`` (``Solver`` of this
-    package).  Rank 0 runs the first `first_generations` generations and
-    snapshots the pool; the shards go to the ranks (broadcast), each resumes
-    its own; the results are gathered on every rank and merged.  `dist` is
-    ``torch.distributed`` with an initialised process group."""
+    ``snapshot()``, ``resume(snapshot, raise_on_error)`` and ``close()``
+    (``Solver`` of this package).  Rank 0 runs the first `first_generations`
+    generations and snapshots the pool; the shards go to the ranks
+    (broadcast).  Then, in rounds, every rank resumes its own region list for
+    up to `round_generations` generations and snapshots it again, and the
+    ranks exchange their incumbents (the minimum over the ranks becomes every
+    rank's incumbent: any upper bound of the global minimum is a valid
+    cut-off for every region); the rounds end when no rank has an active
+    region.  The results are gathered on every rank and merged.  `dist` is
+    ``torch.distributed`` (or any object with ``broadcast_object_list`` and
+    ``all_gather_object``) with an initialised process group."""
     payload = [None]
     if rank == 0:
         s = make_solver(first_generations)
@@ -93,15 +101,34 @@ def sharded_solve(make_solver, first_generations: int, dist, rank: int, world: i
         s.close()
         payload = [dict(shards=[_pack(x) for x in split_snapshot(snap, world)])]
     dist.broadcast_object_list(payload, src=0)
-    mine = payload[0]["shards"][rank]
-    snap = Snapshot(**mine)
-    if len(snap.flo) == 0:
-        part = (np.inf, snap.gub, None, None, np.zeros(0), 0, 0)
-    else:
-        s = make_solver(0)
-        r = s.resume(snap, raise_on_error=False)
-        s.close()
-        part = (r.fmin_lo, r.fmin_hi, r.box_lo, r.box_hi, r.box_flo, r.generations, r.status)
+    snap = Snapshot(**payload[0]["shards"][rank])
+    n = snap.n
+    solver = make_solver(round_generations) if len(snap.flo) else None
+    part = (np.inf, snap.gub, None, None, np.zeros(0), 0, 0)
+    gens = 0
+    while True:
+        done = True
+        if solver is not None:
+            r = solver.resume(snap, raise_on_error=False)
+            gens += r.generations
+            part = (r.fmin_lo, r.fmin_hi, r.box_lo, r.box_hi, r.box_flo, gens, r.status)
+            done = r.status != _LIMIT
+            if not done:
+                snap = solver.snapshot()
+        # the incumbent exchange: a min over the ranks' GUBs (and whether all are done)
+        views = [None] * world
+        dist.all_gather_object(views, (float(part[1]) if solver is not None else float(snap.gub), done))
+        gub = min(v[0] for v in views)
+        if all(v[1] for v in views):
+            break
+        if not done:
+            snap = Snapshot(snap.n, snap.block, snap.lo, snap.hi, snap.flo, snap.cyc, min(snap.gub, gub),
+                            snap.generations)
+    if solver is not None:
+        solver.close()
     parts = [None] * world
     dist.all_gather_object(parts, part)
-    return merge_results(parts, snap.n)
+    return merge_results(parts, n)
+
+
+_LIMIT = 4   # GB_E_LIMIT: the round's generation limit, regions still active

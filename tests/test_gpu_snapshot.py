@@ -130,25 +130,60 @@ def test_malformed_snapshots_are_refused():
     s.close()
 
 
+class _ThreadDist:
+    """broadcast_object_list / all_gather_object between threads (one per
+    rank, all on this GPU: the ranks share nothing but these host calls)."""
+
+    def __init__(self, world):
+        import threading
+        self.world, self.bar, self.local = world, threading.Barrier(world), threading.local()
+        self.slots, self.shared = [None] * world, None
+
+    def broadcast_object_list(self, lst, src=0):
+        if self.local.rank == src:
+            self.shared = lst[0]
+        self.bar.wait()
+        lst[0] = self.shared
+        self.bar.wait()
+
+    def all_gather_object(self, out, obj):
+        self.slots[self.local.rank] = obj
+        self.bar.wait()
+        out[:] = list(self.slots)
+        self.bar.wait()
+
+
 @pytest.mark.parametrize("world", [2, 3])
-def test_sharded_regions_solved_one_after_another(world):
-    # the sharded solve of paper_2507_01770_gb300.shard with its ranks run in
-    # turn on this GPU: the merged enclosure is rigorous and within tol_f,
-    # and the merged regions cover the planted minimiser
+def test_sharded_solve_ranks_as_threads(world):
+    # shard.sharded_solve with its ranks as threads on this GPU: rounds of
+    # generations with the incumbent exchanged between them; the merged
+    # enclosure is rigorous and within tol_f, covers the planted minimiser
+    # and overlaps the single-rank solve's
+    import threading
     from paper_2507_01770_gb300 import shard
     p = S.chain(n=12, seed=3, block=6)
     opts = dict(block=6, split_m=2, split_d=3, max_children=8 * 8)
-    s0, first = _solve(p, max_generations=6, **opts)
-    snap = s0.snapshot()
-    s0.close()
-    parts = []
-    for sh in shard.split_snapshot(snap, world):
-        s = gb.Solver(p, **opts)
-        r = s.resume(sh)
-        s.close()
-        assert r.status == gb.GB_OK
-        parts.append((r.fmin_lo, r.fmin_hi, r.box_lo, r.box_hi, r.box_flo, r.generations, r.status))
-    m = shard.merge_results(parts, p.n)
+    D = _ThreadDist(world)
+    res, errs = [None] * world, []
+
+    def run(rank):
+        try:
+            D.local.rank = rank
+            res[rank] = shard.sharded_solve(lambda g: gb.Solver(p, max_generations=g, **opts), 6, D, rank, world,
+                                            round_generations=16)
+        except Exception as e:   # noqa: BLE001 - reported below
+            errs.append(e)
+            D.bar.abort()
+
+    th = [threading.Thread(target=run, args=(r,)) for r in range(world)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=300)
+    assert not errs, errs
+    m = res[0]
+    assert all(r.fmin_lo == m.fmin_lo and r.fmin_hi == m.fmin_hi for r in res)
+    assert all(st == gb.GB_OK for st in m.statuses)
     assert m.fmin_lo <= 0.0 <= m.fmin_hi and m.fmin_hi - m.fmin_lo <= p.tol_f
     assert np.any(np.all((m.box_lo <= p.s) & (p.s <= m.box_hi), axis=1))
     full_s, full = _solve(p, **opts)

@@ -1,9 +1,10 @@
 """One problem over several ranks (paper_2507_01770_gb300.shard), host logic
 with two gloo ranks on the CPU: the snapshot of the first phase is dealt out
-round-robin, every rank resumes its share, and the merged enclosure is
-[min GLB, min GUB] with the regions whose LB is not above the global GUB.
-The solver is a stand-in (no GPU): it returns its shard's regions with a
-rank-dependent incumbent, so the test checks the plumbing and the merge."""
+round-robin, every rank resumes its share in rounds with the incumbent
+exchanged between rounds, and the merged enclosure is [min GLB, min GUB]
+with the regions whose LB is not above the global GUB.  The solver is a
+stand-in (no GPU), so the test checks the plumbing, the exchange and the
+merge."""
 import os
 import socket
 
@@ -30,24 +31,36 @@ class _FakeResult:
 
 class _FakeSolver:
     """First phase: 10 regions of a 3-D box with LB = q / 10, GUB 0.55.
-    Resume: keeps the shard's regions with LB <= a rank-dependent GUB."""
+    Resume: the first round stops on its generation limit with a
+    rank-dependent incumbent (0.5, 0.25); the second records the incumbent
+    it was given and keeps the regions with LB not above it."""
 
     def __init__(self, rank, max_gen):
-        self.rank, self.max_gen = rank, max_gen
+        self.rank, self.max_gen, self.calls, self.given = rank, max_gen, 0, []
+        self.regions = None
 
     def solve(self, raise_on_error=True):
         return _FakeResult(None, None, np.zeros(0), 0.55, self.max_gen)
 
     def snapshot(self):
         import paper_2507_01770_gb300 as gb
+        if self.regions is not None:     # after a round: the shard's regions, its own incumbent
+            lo, hi, flo = self.regions
+            return gb.Snapshot(3, 3, lo, hi, flo, np.zeros(len(flo), np.int32), [0.5, 0.25][self.rank], 9)
         q = np.arange(10, dtype=np.float64)
         lo = np.stack([q, q, q], axis=1)
         return gb.Snapshot(3, 3, lo, lo + 0.5, q / 10, np.zeros(10, np.int32), 0.55, self.max_gen)
 
     def resume(self, snap, raise_on_error=True):
-        gub = [0.5, 0.25][self.rank]
-        keep = snap.flo <= gub
-        return _FakeResult(snap.lo[keep], snap.hi[keep], snap.flo[keep], gub, 7 + self.rank)
+        self.calls += 1
+        self.given.append(snap.gub)
+        self.regions = (snap.lo, snap.hi, snap.flo)
+        if self.calls == 1:
+            r = _FakeResult(snap.lo, snap.hi, snap.flo, [0.5, 0.25][self.rank], 3)
+            r.status = 4                  # generation limit of the round
+            return r
+        keep = ~(snap.flo > snap.gub)
+        return _FakeResult(snap.lo[keep], snap.hi[keep], snap.flo[keep], snap.gub, 4 + self.rank)
 
     def close(self):
         pass
@@ -57,8 +70,14 @@ def _rank(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     from paper_2507_01770_gb300 import shard
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    res = shard.sharded_solve(lambda g: _FakeSolver(rank, g), 5, dist, rank, world)
-    out.put((rank, res.fmin_lo, res.fmin_hi, res.box_flo.tolist(), res.generations))
+    made = []
+
+    def make(g):
+        made.append(_FakeSolver(rank, g))
+        return made[-1]
+
+    res = shard.sharded_solve(make, 5, dist, rank, world, round_generations=3)
+    out.put((rank, res.fmin_lo, res.fmin_hi, res.box_flo.tolist(), res.generations, made[-1].given))
     dist.destroy_process_group()
 
 
@@ -73,13 +92,15 @@ def test_sharded_solve_two_gloo_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, glb, gub, flo, gens in got:
-        # rank 0 keeps LB <= 0.5 of regions 0, 2, 4 (0, .2, .4); rank 1 LB <= .25 of 1, 3, ... (.1)
-        # global GUB = 0.25: the kept regions are those with LB <= 0.25
+    for rank, glb, gub, flo, gens, given in got:
+        # round 1 starts from the split's incumbent 0.55; after it the ranks
+        # exchange 0.5 and 0.25, so round 2 of every rank runs with 0.25 and
+        # keeps its regions with LB <= 0.25: rank 0 {0, 0.2}, rank 1 {0.1}
+        assert given == [0.55, 0.25]
         assert gub == 0.25
         assert sorted(flo) == [0.0, 0.1, 0.2]
         assert glb == 0.0
-        assert gens == [7, 8]
+        assert gens == [3 + 4, 3 + 5]
 
 
 def test_split_and_merge_without_ranks():
