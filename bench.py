@@ -57,6 +57,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -137,7 +138,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples: BENCH_CLOCKS_DIR if set, else a temporary directory
+        d = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.mkdtemp(prefix="gb_clocks_")
+        self.path = os.path.join(d, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
