@@ -553,7 +553,7 @@ static gb_status solve_begin_from(gb_problem* p, const gb_snapshot* snap) {
         GB_CU(cudaMemsetAsync(p->pool.rmark, 0, sizeof(unsigned) * (size_t)p->pool.R, s));
         p->marks_used = false;
     }
-    p->have_pool = true;
+    p->have_pool = false;
     if (!snap) {
         p->gen_base = 0;
         GB_CU(gb_launch_root_init(p->P, p->pool, p->E[0], p->G.tol_x, p->st, s));
@@ -563,36 +563,34 @@ static gb_status solve_begin_from(gb_problem* p, const gb_snapshot* snap) {
         const size_t nb = (size_t)c * p->n;
         double *d_lo = nullptr, *d_hi = nullptr, *d_flo = nullptr;
         int* d_cyc = nullptr;
+        cudaError_t e = cudaSuccess;
         if (c > 0) {
             cudaError_t e1 = cudaMallocAsync((void**)&d_lo, nb * sizeof(double), s);
             cudaError_t e2 = cudaMallocAsync((void**)&d_hi, nb * sizeof(double), s);
             cudaError_t e3 = cudaMallocAsync((void**)&d_flo, (size_t)c * sizeof(double), s);
             cudaError_t e4 = cudaMallocAsync((void**)&d_cyc, (size_t)c * sizeof(int), s);
-            if (e1 || e2 || e3 || e4) {
-                if (d_lo) cudaFreeAsync(d_lo, s);
-                if (d_hi) cudaFreeAsync(d_hi, s);
-                if (d_flo) cudaFreeAsync(d_flo, s);
-                if (d_cyc) cudaFreeAsync(d_cyc, s);
-                return fail(GB_E_OOM, "device allocation for the snapshot");
-            }
-            GB_CU(cudaMemcpyAsync(d_lo, snap->lo, nb * sizeof(double), cudaMemcpyHostToDevice, s));
-            GB_CU(cudaMemcpyAsync(d_hi, snap->hi, nb * sizeof(double), cudaMemcpyHostToDevice, s));
-            GB_CU(cudaMemcpyAsync(d_flo, snap->flo, (size_t)c * sizeof(double), cudaMemcpyHostToDevice, s));
-            GB_CU(cudaMemcpyAsync(d_cyc, snap->cyc, (size_t)c * sizeof(int), cudaMemcpyHostToDevice, s));
+            e = e1 ? e1 : e2 ? e2 : e3 ? e3 : e4;
+            if (e == cudaSuccess &&
+                (e = cudaMemcpyAsync(d_lo, snap->lo, nb * sizeof(double), cudaMemcpyHostToDevice, s)) == cudaSuccess &&
+                (e = cudaMemcpyAsync(d_hi, snap->hi, nb * sizeof(double), cudaMemcpyHostToDevice, s)) == cudaSuccess &&
+                (e = cudaMemcpyAsync(d_flo, snap->flo, (size_t)c * sizeof(double), cudaMemcpyHostToDevice, s)) ==
+                    cudaSuccess)
+                e = cudaMemcpyAsync(d_cyc, snap->cyc, (size_t)c * sizeof(int), cudaMemcpyHostToDevice, s);
         }
-        GB_CU(gb_launch_resume(p->P, p->pool, p->E[0], c, d_lo, d_hi, d_flo, d_cyc, snap->gub, p->st, s));
-        if (c > 0) {
-            cudaFreeAsync(d_lo, s);
-            cudaFreeAsync(d_hi, s);
-            cudaFreeAsync(d_flo, s);
-            cudaFreeAsync(d_cyc, s);
-        }
+        if (e == cudaSuccess)
+            e = gb_launch_resume(p->P, p->pool, p->E[0], c, d_lo, d_hi, d_flo, d_cyc, snap->gub, p->st, s);
+        if (d_lo) cudaFreeAsync(d_lo, s);
+        if (d_hi) cudaFreeAsync(d_hi, s);
+        if (d_flo) cudaFreeAsync(d_flo, s);
+        if (d_cyc) cudaFreeAsync(d_cyc, s);
+        if (e != cudaSuccess) return cuda_fail(e, "resume from a snapshot");
     }
     GB_CU(gb_launch_stats(p->E[0], p->G, 1, p->st, s));
     GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
     GB_CU(cudaEventRecord(p->ev_state, s));
     R.launches += gb_launches_so_far() - l0;
     R.active = true;
+    p->have_pool = true;
     return GB_OK;
 }
 
