@@ -357,9 +357,18 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     const bool paper = opt.samples > 0 || opt.mono_all;
     const bool recs = opt.pool_mode == 2 || (opt.pool_mode == 0 && !paper && n >= 128 && 4 * nrec <= H.nb);
     long long cap = 0;
+    // widest IDX_VAR offset range of a template: 0 when every term reads one coordinate
+    int tw = 0;
+    for (const GbSum& S : H.sums)
+        if (S.has_var) tw = std::max(tw, S.off_max - S.off_min);
     if (recs) {
+        // paper mode on records: sample sums per owned group; the coordinate
+        // partials of a record's block only when no template reaches across
+        // coordinates (then they depend on the record's coordinates alone)
+        const bool rdp = opt.mono_all && P.n_sum > 0 && !H.any_prod && tw == 0;
         const size_t per_slot = (size_t)H.nb * 4 + 4 + 4 + 2 * 16;
-        const size_t per_rec = (size_t)opt.block * (16 + (fp32 ? 8 : 0)) + (size_t)H.GPB * (32 + (fp32 ? 8 : 0)) + 4 + 1 + 4;
+        const size_t per_rec = (size_t)opt.block * (16 + (fp32 ? 8 : 0)) + (size_t)H.GPB * (32 + (fp32 ? 8 : 0)) + 4 + 1 + 4 +
+                               (size_t)opt.samples * H.GPB * 16 + (rdp ? (size_t)P.n_sum * opt.block * 16 : 0);
         const long long rho = 4LL * nrec;
         cap = opt.max_boxes > 0 ? opt.max_boxes : (long long)(opt.pool_bytes / (per_slot + rho * per_rec));
         if (cap < 1) return bad(cudaErrorMemoryAllocation, "pool budget below one box");
@@ -382,6 +391,11 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         if (fp32 && ((e = alloc(&pl.rlo32, RB, A)) || (e = alloc(&pl.rhi32, RB, A)) ||
                      (e = alloc(&pl.rgsum32, RG, A))))
             return bad(e, "allocate block records");
+        if (opt.samples > 0) {
+            pl.S = opt.samples;
+            if ((e = alloc(&pl.rgsamp, RG * (size_t)opt.samples, A))) return bad(e, "allocate block records");
+        }
+        if (rdp && (e = alloc(&pl.rgdp, (size_t)R * P.n_sum * opt.block, A))) return bad(e, "allocate block records");
         if ((e = cudaMemsetAsync(pl.rmark, 0, sizeof(unsigned) * (size_t)R, p->stream)))
             return bad(e, "cudaMemset");
     } else {

@@ -100,6 +100,15 @@ __device__ __forceinline__ CacheRef<double2> cache64(const GbPool& pool, const G
                                  pool.GPB};
     return CacheRef<double2>{(which ? pool.gmid : pool.gsum) + (size_t)slot * pool.NG, nullptr, nullptr, 0};
 }
+// The box's group sums at diagonal sample j (1 .. S).
+__device__ __forceinline__ CacheRef<double2> samp64(const GbPool& pool, const GbProg& P, unsigned slot, int j) {
+    if (pool.recs)
+        return CacheRef<double2>{pool.rgsamp + (size_t)(j - 1) * pool.R * pool.GPB, pool.rid + (size_t)slot * pool.nb,
+                                 P.gown, pool.GPB};
+    return CacheRef<double2>{pool.gsamp + ((size_t)slot * pool.S + (j - 1)) * pool.NG, nullptr, nullptr, 0};
+}
+__device__ __forceinline__ bool has_samp(const GbPool& pool) { return pool.recs ? pool.rgsamp != nullptr : pool.gsamp != nullptr; }
+
 __device__ __forceinline__ CacheRef<float2> cache32(const GbPool& pool, const GbProg& P, unsigned slot) {
     if (pool.recs)
         return CacheRef<float2>{pool.rgsum32, pool.rid + (size_t)slot * pool.nb, P.gown, pool.GPB};

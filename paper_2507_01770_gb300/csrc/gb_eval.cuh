@@ -568,8 +568,9 @@ __device__ __forceinline__ bool block_mono(const GbProg& P, int blk, const V& X,
 // ---- cached coordinate partials (first-order test on every coordinate) ----
 // D_kj: the sum over the terms of sum k of their leaf adjoints for
 // coordinate j, accumulated from [0, 0] in ascending term and leaf order
-// (the value block_mono multiplies by the sum's outer adjoint); stored per
-// box as row[k * n + j], an untouched pair as (+inf, -inf).
+// (the value block_mono multiplies by the sum's outer adjoint); stored as
+// row[k * stride + (j - j0)] (a dense row: stride n, j0 0; a block record:
+// stride B, j0 its first coordinate), an untouched pair as (+inf, -inf).
 __device__ __forceinline__ bool d_touched(double2 d) {
     return !(__double_as_longlong(d.x) == 0x7ff0000000000000LL &&
              __double_as_longlong(d.y) == (long long)0xfff0000000000000ULL);
@@ -578,7 +579,7 @@ __device__ __forceinline__ bool d_touched(double2 d) {
 // D of the coordinates of block blk over box X into row (FP64).
 template <typename V>
 __device__ __noinline__ void block_D(const GbProg& P, int blk, const V& X, iv64* R, iv64* RA, double2* row,
-                                        int& ops) {
+                                        int stride, int j0, int& ops) {
     const int c0 = blk * P.B;
     const int c1 = min(P.n, c0 + P.B);
     iv64 W[GB_MAX_ISUM][GB_MAX_WIN];
@@ -623,7 +624,7 @@ __device__ __noinline__ void block_D(const GbProg& P, int blk, const V& X, iv64*
                     touched[k] &= ~(1u << w);
                 }
             }
-            row[(size_t)k * P.n + j] = out;
+            row[(size_t)k * stride + (j - j0)] = out;
         }
     }
 }
@@ -641,7 +642,7 @@ __device__ __forceinline__ int2 d_affected(const GbProg& P, int blk) {
 // First-order test of block blk from cached D and the box's own outer
 // adjoints OA (the operations of block_mono after its term sweeps).
 __device__ __forceinline__ bool cached_mono(const GbProg& P, int blk, const View<double>& X64, const iv64* OA,
-                                            const double2* row, int& ops) {
+                                            const double2* row, int stride, int j0, int& ops) {
     const int c0 = blk * P.B;
     const int c1 = min(P.n, c0 + P.B);
     for (int j = c0; j < c1; j++) {
@@ -653,7 +654,7 @@ __device__ __forceinline__ bool cached_mono(const GbProg& P, int blk, const View
         for (int k = 0; k < P.n_sum; k++) {
             const GbSum S = P.sums[k];
             if (!S.has_var) continue;
-            const double2 d = row[(size_t)k * P.n + j];
+            const double2 d = row[(size_t)k * stride + (j - j0)];
             if (!d_touched(d)) continue;
             g = iadd(g, imul(OA[S.outer_reg], iv64{d.x, d.y}));
             ops += 4;

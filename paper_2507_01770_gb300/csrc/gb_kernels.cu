@@ -103,15 +103,21 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
                 iv32 c = group_sum<PR, float>(P, S, g, X32, R32, ops);
                 (pool.recs ? pool.rgsum32 : pool.gsum32)[at] = make_float2(c.lo, c.hi);
             }
-            for (int j = 1; pool.gsamp && j <= pool.S; j++) {
+            for (int j = 1; has_samp(pool) && j <= pool.S; j++) {
                 const iv64 v = group_sum<PR, double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
-                pool.gsamp[(size_t)(j - 1) * pool.NG + gg] = make_double2(v.lo, v.hi);
+                if (pool.recs) pool.rgsamp[(size_t)(j - 1) * pool.R * pool.GPB + at] = make_double2(v.lo, v.hi);
+                else pool.gsamp[(size_t)(j - 1) * pool.NG + gg] = make_double2(v.lo, v.hi);
             }
         }
     }
     if (pool.gdp) {   // coordinate partials of the domain, every block
         iv64 RA[GB_MAX_TREGS];
-        for (int b = threadIdx.x; b < P.nb; b += blockDim.x) block_D(P, b, X, R, RA, pool.gdp, ops);
+        for (int b = threadIdx.x; b < P.nb; b += blockDim.x) block_D(P, b, X, R, RA, pool.gdp, n, 0, ops);
+    }
+    if (pool.rgdp) {   // the same per block record (the root's record of block b is b)
+        iv64 RA[GB_MAX_TREGS];
+        for (int b = threadIdx.x; b < P.nb; b += blockDim.x)
+            block_D(P, b, X, R, RA, pool.rgdp + (size_t)b * P.n_sum * pool.B, pool.B, b * pool.B, ops);
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -127,8 +133,8 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
         nsamp = P.samples;
         for (int j = 1; j <= P.samples; j++) {
             const SampleView SV{X, j, P.samples + 1};
-            const CacheRef<double2> cs{pool.gsamp + (size_t)(j - 1) * pool.NG, nullptr, nullptr, 0};
-            sum_values<PR, double>(P, -1, SV, pool.gsamp ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
+            const CacheRef<double2> cs = samp64(pool, P, 0, j);
+            sum_values<PR, double>(P, -1, SV, has_samp(pool) ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
             const iv64 Fs = outer_fwd<double>(P, SV, sums, O, ops);
             if (Fs.hi < gub) gub = Fs.hi;
         }
@@ -538,14 +544,19 @@ template <typename V>
 __device__ __noinline__ bool mono_cached(const GbProg& P, const GbPool& pool, unsigned slot, int blk, const V& X,
                                          const iv64* O, iv64* OA, iv64* R, iv64* RA, int& ops) {
     const int2 ab = d_affected(P, blk);
-    const double2* row = pool.gdp + (size_t)slot * P.n_sum * P.n;
     for (int b = ab.x; b <= ab.y; b++)   // also leaves the outer adjoints in OA
         if (block_mono<false, double>(P, b, X, X, O, OA, R, RA, (double*)nullptr, (const CacheRef<double2>*)nullptr, -1,
                                ops))
             return true;
     for (int b = 0; b < P.nb; b++) {
         if (b >= ab.x && b <= ab.y) continue;
-        if (cached_mono(P, b, X, OA, row, ops)) return true;
+        // dense: the box's row; records: the parent's record of block b
+        const bool hit = pool.recs
+            ? cached_mono(P, b, X, OA,
+                          pool.rgdp + (size_t)pool.rid[(size_t)slot * pool.nb + b] * P.n_sum * pool.B, pool.B,
+                          b * pool.B, ops)
+            : cached_mono(P, b, X, OA, pool.gdp + (size_t)slot * P.n_sum * P.n, P.n, 0, ops);
+        if (hit) return true;
     }
     return false;
 }
@@ -571,8 +582,8 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
             const SampleView SV{X, j, P.samples + 1};
             // the child's sample j agrees with its parent's on every coordinate
             // it did not split: the groups off the split block come from the cache
-            const CacheRef<double2> cs{pool.gsamp + ((size_t)c.slot * pool.S + (j - 1)) * pool.NG, nullptr, nullptr, 0};
-            sum_values<PR, double>(P, blk, SV, pool.gsamp ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
+            const CacheRef<double2> cs = samp64(pool, P, c.slot, j);
+            sum_values<PR, double>(P, blk, SV, has_samp(pool) ? &cs : (const CacheRef<double2>*)nullptr, R, sums, ops);
             const iv64 Fs = outer_fwd<double>(P, SV, sums, O, ops);
             if (Fs.hi == Fs.hi) {
                 const unsigned long long k = gb_order_key(Fs.hi);
@@ -592,7 +603,7 @@ __device__ __forceinline__ bool eval64_child(const GbProg& P, const GbPool& pool
     iv64 F = outer_fwd<double>(P, X, sums, O, ops);
     bool keep = !(F.lo > gub_prev);
     if (keep)
-        keep = !(pool.gdp ? mono_cached(P, pool, c.slot, blk, X, O, OA, R, RA, ops)
+        keep = !(pool.gdp || pool.rgdp ? mono_cached(P, pool, c.slot, blk, X, O, OA, R, RA, ops)
                           : mono_any<PR, double>(P, blk, X, X, O, OA, R, RA, &cf, ops));
     ch.flo[ci] = canon_lo(F.lo);
     ch.flag[ci] = keep ? 1 : 0;
@@ -842,7 +853,7 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
             for (int j = lane; j < n; j += 32)
                 if (j < a0 || j >= a1) dst[(size_t)k * n + j] = src[(size_t)k * n + j];
         iv64 RA[GB_MAX_TREGS];
-        for (int b = ab.x + lane; b <= ab.y; b += 32) block_D(P, b, X, R, RA, dst, ops);
+        for (int b = ab.x + lane; b <= ab.y; b += 32) block_D(P, b, X, R, RA, dst, n, 0, ops);
     }
     if (lane == 0) {
         long long e = kept_old + s;
@@ -999,11 +1010,17 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
         const int gl = g - S.group0;
         const int2 dr = P.dirty[blk * P.n_sum + k];
         const size_t dst = (size_t)crow[b] * GPB + o, src = (size_t)prow[b] * GPB + o;
+        const size_t sstep = (size_t)pool.R * GPB;   // sample j's sums: rgsamp + (j - 1) * sstep
         if (gl < dr.x || gl >= dr.y) {
             pool.rgsum[dst] = pool.rgsum[src];
             pool.rgmid[dst] = pool.rgmid[src];
             if (pool.fp32) pool.rgsum32[dst] = pool.rgsum32[src];
+            for (int j = 0; pool.rgsamp && j < pool.S; j++) pool.rgsamp[j * sstep + dst] = pool.rgsamp[j * sstep + src];
             continue;
+        }
+        for (int j = 1; pool.rgsamp && j <= pool.S; j++) {
+            const iv64 v = group_sum<PR, double>(P, S, gl, SampleView{X, j, pool.S + 1}, R, ops);
+            pool.rgsamp[(j - 1) * sstep + dst] = make_double2(v.lo, v.hi);
         }
         iv64 a, m;
         if (tab) {
@@ -1021,6 +1038,13 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
         }
         pool.rgsum[dst] = make_double2(a.lo, a.hi);
         pool.rgmid[dst] = make_double2(m.lo, m.hi);
+    }
+    if (pool.rgdp) {   // coordinate partials of each new record's block (templates within one coordinate)
+        iv64 RA[GB_MAX_TREGS];
+        for (int t = lane; t < nrec && blk - t >= 0; t += 32) {
+            const int b = blk - t;
+            block_D(P, b, X, R, RA, pool.rgdp + (size_t)crow[b] * P.n_sum * B, B, b * B, ops);
+        }
     }
     if (lane == 0) {
         const int w = pool.swide[c.slot] + wide_delta;
@@ -1252,7 +1276,8 @@ __global__ void __launch_bounds__(128) k_resume_boxes(GbProg P, GbPool pool, GbE
     }
     if (pool.gdp) {
         iv64 RA[GB_MAX_TREGS];
-        for (int b = lane; b < P.nb; b += 32) block_D(P, b, X, R, RA, pool.gdp + (size_t)slot * P.n_sum * n, ops);
+        for (int b = lane; b < P.nb; b += 32)
+            block_D(P, b, X, R, RA, pool.gdp + (size_t)slot * P.n_sum * n, n, 0, ops);
     }
     if (lane == 0) {
         E.flo[q] = flo[q];

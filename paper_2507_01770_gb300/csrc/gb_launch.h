@@ -18,6 +18,9 @@ struct GbPool {
     unsigned* freel;  // [cap] free slots
     double2* gsamp;   // [cap][S][NG] cached group sums at the S diagonal samples (dense rows, samples > 0)
     double2* gdp;     // [cap][n_sum][n] cached coordinate partial sums D (dense rows, mono_all)
+    double2* rgsamp;  // [S][R][GPB] the owned groups' sums at the S diagonal samples (records, samples > 0)
+    double2* rgdp;    // [R][n_sum][B] coordinate partial sums D of the record's block (records, mono_all,
+                      // templates confined to one coordinate)
     int n, NG, fp32, S;
     // block-record mode (recs = 1): a box is a row of nb record ids; record q
     // holds block coordinates [q*B, q*B + B) and the cached sums of the groups
