@@ -105,10 +105,12 @@ typedef struct gb_options {
     int32_t gens_per_sync;    /* <= 1: the host reads the state after every generation (per-kernel timing);
                                  G > 1: generations run as replays of a captured CUDA graph, G between
                                  state reads (the search is the same) */
-    int32_t pool_mode;        /* box storage (section 3.3): 0 auto (block records when n >= 128 and a
-                                 child replaces at most a quarter of the blocks), 1 one dense row of n
-                                 coordinates per box, 2 block records shared between a box and its
-                                 children; results are identical */
+    int32_t pool_mode;        /* box storage (the list L of section 3.2): 0 auto (block records when
+                                 n >= 128, a child replaces at most a quarter of the blocks and neither
+                                 samples nor mono_all is set), 1 one dense row of n coordinates per box,
+                                 2 block records shared between a box and its children (also with
+                                 samples / mono_all: the way to hold the paper's procedure's 10^7-region
+                                 lists); results are identical */
     int32_t samples;          /* GUB samples per box: 0 the midpoint; S in 1..64 the S interior points
                                  j / (S + 1) of its diagonal (the paper takes 10, section 4); S > 0 needs
                                  eval_mode 0 or 1 (bytecode interpreter) */
