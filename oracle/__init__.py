@@ -86,6 +86,7 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int32)]
             L.oracle_iv_op.argtypes = [ip, dp, dp, ctypes.c_double, ip, dp]
             L.oracle_tree_sum.argtypes = [dp, dp, ip, ip, dp]
+            L.oracle_iv_op_batch.argtypes = [ip, dp, dp, dp, dp, dp, ctypes.c_int64, ip, dp]
             L.oracle_tree_prod.argtypes = [dp, dp, ip, ip, dp]
             L.oracle_tree_prod_adjoint.argtypes = [dp, dp, ip, ctypes.c_double, ctypes.c_double, ip, dp]
             L.oracle_solve.argtypes = [vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Result)]
@@ -108,6 +109,20 @@ def iv_op(op: str, x, y=(0.0, 0.0), c: float = 0.0, f32: bool = False):
     if rc:
         raise ValueError(op)
     return float(out[0]), float(out[1])
+
+
+def iv_op_batch(op: str, xlo, xhi, ylo=None, yhi=None, c=None, f32: bool = False) -> np.ndarray:
+    """iv_op over arrays of operands; returns (count, 2) [lo, hi]."""
+    xlo = np.ascontiguousarray(xlo, dtype=np.float64)
+    xhi = np.ascontiguousarray(xhi, dtype=np.float64)
+    ylo = np.ascontiguousarray(ylo if ylo is not None else np.zeros_like(xlo), dtype=np.float64)
+    yhi = np.ascontiguousarray(yhi if yhi is not None else np.zeros_like(xlo), dtype=np.float64)
+    cc = np.ascontiguousarray(c if c is not None else np.zeros_like(xlo), dtype=np.float64)
+    out = np.zeros((len(xlo), 2))
+    if lib().oracle_iv_op_batch(OP[op], _dp(xlo), _dp(xhi), _dp(ylo), _dp(yhi), _dp(cc), len(xlo), int(f32),
+                                _dp(out)):
+        raise ValueError(op)
+    return out
 
 
 def tree_sum(lo, hi, f32: bool = False):

@@ -879,6 +879,18 @@ int oracle_iv_op(int op, const double* x, const double* y, double c, int p, doub
     return 0;
 }
 
+/* oracle_iv_op over count operand pairs (x: xlo/xhi, y: ylo/yhi, scale
+ * factors c, may be NULL); out: count x 2.  Returns 1 for an unknown op. */
+int oracle_iv_op_batch(int op, const double* xlo, const double* xhi, const double* ylo, const double* yhi,
+                       const double* c, int64_t count, int p, double* out) {
+    for (int64_t k = 0; k < count; k++) {
+        const double x[2] = {xlo[k], xhi[k]};
+        const double y[2] = {ylo ? ylo[k] : 0.0, yhi ? yhi[k] : 0.0};
+        if (oracle_iv_op(op, x, y, c ? c[k] : 0.0, p, out + 2 * k)) return 1;
+    }
+    return 0;
+}
+
 int oracle_tree_prod(const double* lo, const double* hi, int m, int p, double* out) {
     iv* a = (iv*)malloc(sizeof(iv) * (m > 0 ? m : 1));
     for (int i = 0; i < m; i++) a[i] = mk(lo[i], hi[i]);

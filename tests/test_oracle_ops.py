@@ -179,3 +179,84 @@ def test_trig_wide_argument_is_full_range():
     assert lo == -1.0 and hi < -0.98
     lo, hi = O.iv_op("SIN", (1.5, 1.6))      # contains pi/2: maximum 1 reached
     assert hi == 1.0 and lo > 0.99
+
+
+# ---------------------------------------------------------------------------
+# A million operand pairs against exact arithmetic by error-free
+# transformations (independent of mpmath and of the oracle): for a + b,
+# Knuth's TwoSum gives s = RN(a + b) and the exact error e = a + b - s; for
+# a * b, Dekker's splitting gives p = RN(a * b) and e = a * b - p (exact while
+# nothing overflows or underflows).  The value rounded down is s when e >= 0,
+# else the double below s; rounded up, s when e <= 0, else the double above.
+_SPLIT = 134217729.0   # 2^27 + 1
+
+
+def _two_sum(a, b):
+    s = a + b
+    bp = s - a
+    ap = s - bp
+    return s, (a - ap) + (b - bp)
+
+
+def _split(a):
+    c = _SPLIT * a
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def _two_prod(a, b):
+    p = a * b
+    ah, al = _split(a)
+    bh, bl = _split(b)
+    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
+
+
+def _rd(v, e):
+    return np.where(e < 0, np.nextafter(v, -np.inf), v)
+
+
+def _ru(v, e):
+    return np.where(e > 0, np.nextafter(v, np.inf), v)
+
+
+def _million(rng):
+    count = 1_000_000
+    mag = 2.0 ** rng.uniform(-20, 20, (count, 2))
+    v = mag * rng.choice([-1.0, 1.0], (count, 2))
+    kind = rng.integers(0, 4, count)
+    v[kind == 1, 0] = 0.0
+    v[kind == 2, 1] = v[kind == 2, 0] * (1 + 2.0 ** -40)
+    return np.minimum(v[:, 0], v[:, 1]), np.maximum(v[:, 0], v[:, 1])
+
+
+@pytest.mark.parametrize("op", ["ADD", "SUB", "MUL", "SQR", "NEG", "SCALE"])
+def test_a_million_operations_exact_by_error_free_transformations(op):
+    rng = np.random.default_rng(zlib.crc32(op.encode()) + 1)
+    a, b = _million(rng)
+    c, d = _million(rng)
+    k = rng.uniform(-50, 50, len(a))
+    got = O.iv_op_batch(op, a, b, c, d, k)
+    if op in ("ADD", "SUB"):
+        y_lo, y_hi = (c, d) if op == "ADD" else (-d, -c)
+        s1, e1 = _two_sum(a, y_lo)
+        s2, e2 = _two_sum(b, y_hi)
+        want = np.stack([_rd(s1, e1), _ru(s2, e2)], axis=1)
+    elif op == "NEG":
+        want = np.stack([-b, -a], axis=1)
+    elif op in ("MUL", "SCALE"):
+        ys = [c, d] if op == "MUL" else [k, k]
+        los, his = [], []
+        for x in (a, b):
+            for y in ys:
+                p, e = _two_prod(x, y)
+                los.append(_rd(p, e))
+                his.append(_ru(p, e))
+        want = np.stack([np.min(los, axis=0), np.max(his, axis=0)], axis=1)
+    else:   # SQR: [0, max] across zero, else the ordered squares
+        pa, ea = _two_prod(a, a)
+        pb, eb = _two_prod(b, b)
+        lo = np.where(a >= 0, _rd(pa, ea), np.where(b <= 0, _rd(pb, eb), 0.0))
+        hi = np.where(a >= 0, _ru(pb, eb), np.where(b <= 0, _ru(pa, ea), np.maximum(_ru(pa, ea), _ru(pb, eb))))
+        want = np.stack([lo, hi], axis=1)
+    bad = np.nonzero(got != want)
+    assert bad[0].size == 0, (op, bad[0][:3], got[bad[0][:3]], want[bad[0][:3]])
