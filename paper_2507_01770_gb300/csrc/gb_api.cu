@@ -790,10 +790,11 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
 }
 
 // ---------------------------------------------------------------------------
-// Fused evaluation over several problems (serving): one generation of every
-// problem in lockstep -- its selection, partition and term tables on its own
-// stream, then one persistent launch evaluating the children of all of them,
-// then its compaction, materialisation and statistics on its own stream.
+// Fused evaluation over several problems (serving): a step runs G
+// generations of every problem it holds together -- per generation, each
+// problem's selection, partition and term tables on its own stream, then one
+// persistent launch evaluating the children of all of them, then each
+// problem's compaction, materialisation and statistics on its own stream.
 #define GB_BATCH_RING 8   // descriptor buffers in flight (steps overlap)
 struct GbBatchCtx {
     cudaStream_t ss[GB_BATCH_RING] = {};   // step i launches on ss[i % ring]: steps overlap
