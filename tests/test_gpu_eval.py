@@ -126,6 +126,30 @@ def test_step_bit_exact():
     solver.close()
 
 
+def test_product_special_cases_bit_exact():
+    # an empty product (1), a one-term product and products of points
+    g = S.Dag()
+    x = g.ivar(0)
+    empty = g.iprod(g.add(x, g.const(1.0)), 2, 2, 1)
+    one = g.iprod(g.sqr(x), 1, 2, 1)
+    allp = g.iprod(g.scale(x, 2.0), 0, 5, 1)
+    f = g.add(g.add(g.scale(empty, 3.0), one), allp)
+    p = S.Problem("prod_special", 5, g.nodes(), f, g.tables, np.full(5, -2.0), np.full(5, 2.0), 1e-6, 3,
+                  np.zeros(5), 0)
+    solver = gb.Solver(p, block=3)
+    orc = O.Oracle(p, block=3)
+    lo, hi = S.random_boxes(p, 100, seed=9)
+    lo[:10] = hi[:10]                      # point boxes
+    for fp32 in (False, True):
+        for blk in range(2):
+            gF, gFm, gG, gM = _gpu_eval(solver, lo, hi, blk, fp32)
+            oF, oFm, oG, oM = _oracle_eval(orc, lo, hi, blk, fp32)
+            w = min(3, 5 - blk * 3)
+            assert np.array_equal(gF, oF) and np.array_equal(gFm, oFm)
+            assert np.array_equal(gG[:, :w], oG[:, :w]) and np.array_equal(gM, oM)
+    solver.close()
+
+
 def test_custom_dag_bit_exact():
     g = S.Dag()
     y = g.sub(g.ivar(0), g.ivar(1))

@@ -355,3 +355,38 @@ def test_invalid_problems_are_rejected():
     q2 = S.Problem("bad", 4, p.nodes, p.root, p.tables, p.l, p.l, 1e-6, 2, p.s, 0)
     with pytest.raises(ValueError):
         O.Oracle(q2)                         # l < u violated
+
+
+def test_product_special_cases():
+    # the empty product is 1; a one-term product is the term; a product of
+    # point factors is their exact product when it is representable
+    g = S.Dag()
+    x = g.ivar(0)
+    empty = g.iprod(g.add(x, g.const(1.0)), 2, 2, 1)
+    one = g.iprod(g.sqr(x), 1, 2, 1)
+    f = g.add(g.scale(empty, 3.0), one)
+    p = S.Problem("prod_special", 3, g.nodes(), f, g.tables, np.full(3, -2.0), np.full(3, 2.0), 1e-6, 3,
+                  np.zeros(3), 0)
+    o = O.Oracle(p, block=3)
+    F, _, G, _ = o.eval_box(np.array([0.0, 0.5, 0.0]), np.array([0.0, 0.5, 0.0]), blk=0)
+    assert tuple(F) == (3.25, 3.25)
+    assert tuple(G[1]) == (1.0, 1.0) and tuple(G[0]) == (0.0, 0.0)
+    g2 = S.Dag()
+    t = g2.iprod(g2.scale(g2.ivar(0), 2.0), 0, 4, 1)
+    p2 = S.Problem("prod_points", 4, g2.nodes(), t, g2.tables, np.full(4, -4.0), np.full(4, 4.0), 1e-6, 4,
+                   np.zeros(4), 0)
+    pts = np.array([0.5, -1.5, 3.0, 0.25])
+    F2, _, G2, _ = O.Oracle(p2, block=4).eval_box(pts, pts, blk=0)
+    assert tuple(F2) == (float(np.prod(2 * pts)),) * 2
+    for j in range(4):   # d/dx_j prod_i 2 x_i = 2 prod_{i != j} 2 x_i, exact here
+        want = 2.0 * float(np.prod(np.delete(2 * pts, j)))
+        assert tuple(G2[j]) == (want, want)
+
+
+def test_nested_reductions_rejected():
+    g = S.Dag()
+    inner = g.iprod(g.ivar(0), 0, 2, 1)
+    f = g.isum(g.add(g.ivar(0), inner), 0, 2, 1)
+    p = S.Problem("nested", 2, g.nodes(), f, g.tables, np.zeros(2), np.ones(2), 1e-6, 2, np.zeros(2), 0)
+    with pytest.raises(Exception):
+        O.Oracle(p, block=2)
