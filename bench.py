@@ -187,6 +187,22 @@ def flush_l2(torch, dev, buf):
     torch.cuda.synchronize(dev)
 
 
+def host_cpu():
+    """The host's processor (model or part, architecture, logical cores)."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{model or platform.processor() or 'unknown'} ({platform.machine()}, {os.cpu_count()} logical cores)"
+
+
 def cpu_baseline(w, gens):
     """Oracle, one thread, on the workload's problem: the first `gens`
     generations with 2^d children per parent (d = the workload's split
@@ -203,7 +219,7 @@ def cpu_baseline(w, gens):
                 fp32=bool(w["fp32"]), **paper)
     dt = time.perf_counter() - t
     evals = r.evals64 + r.evals32
-    return {"value": evals / dt, "unit": "box-evals/s", "cores": 1, "kind": "oracle",
+    return {"value": evals / dt, "unit": "box-evals/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"first {r.generations} generations of the {w['family']} n={w['n']} solve, "
                       f"{w['cpu_parents']} parents x {w['cpu_split_m'] ** w['cpu_split_d']} children per "
                       f"generation ({evals} box evaluations, {dt:.1f} s, 1 thread)"}
