@@ -77,8 +77,18 @@ def _pack(snap: Snapshot):
                 generations=snap.generations)
 
 
+def _concat(snaps: list[Snapshot]) -> Snapshot:
+    """The regions of several snapshots in rank order (incumbent: the lowest)."""
+    n, blk = snaps[0].n, snaps[0].block
+    lo = np.concatenate([x.lo.reshape(-1, n) for x in snaps])
+    hi = np.concatenate([x.hi.reshape(-1, n) for x in snaps])
+    flo = np.concatenate([x.flo for x in snaps])
+    cyc = np.concatenate([x.cyc for x in snaps]).astype(np.int32)
+    return Snapshot(n, blk, lo, hi, flo, cyc, min(x.gub for x in snaps), max(x.generations for x in snaps))
+
+
 def sharded_solve(make_solver, first_generations: int, dist, rank: int, world: int,
-                  round_generations: int = 64) -> ShardedResult:
+                  round_generations: int = 64, rebalance: bool = False) -> ShardedResult:
     """Solve one problem on `world` ranks (one GPU each).
 
     make_solver(max_generations) -> an object with ``solve(raise_on_error)``,
@@ -89,10 +99,12 @@ def sharded_solve(make_solver, first_generations: int, dist, rank: int, world: i
     up to `round_generations` generations and snapshots it again, and the
     ranks exchange their incumbents (the minimum over the ranks becomes every
     rank's incumbent: any upper bound of the global minimum is a valid
-    cut-off for every region); the rounds end when no rank has an active
-    region.  The results are gathered on every rank and merged.  `dist` is
-    ``torch.distributed`` (or any object with ``broadcast_object_list`` and
-    ``all_gather_object``) with an initialised process group."""
+    cut-off for every region); with `rebalance` the ranks' region lists are
+    also pooled and dealt out again after every round.  The rounds end when
+    no rank has an active region.  The results are gathered on every rank
+    and merged.  `dist` is ``torch.distributed`` (or any object with
+    ``broadcast_object_list`` and ``all_gather_object``) with an initialised
+    process group."""
     payload = [None]
     if rank == 0:
         s = make_solver(first_generations)
@@ -103,32 +115,39 @@ def sharded_solve(make_solver, first_generations: int, dist, rank: int, world: i
     dist.broadcast_object_list(payload, src=0)
     snap = Snapshot(**payload[0]["shards"][rank])
     n = snap.n
-    solver = make_solver(round_generations) if len(snap.flo) else None
-    part = (np.inf, snap.gub, None, None, np.zeros(0), 0, 0)
+    solver = make_solver(round_generations)
+    finished = []   # results of the region lists this rank has run to the end
     gens = 0
     while True:
         done = True
-        if solver is not None:
+        if len(snap.flo):
             r = solver.resume(snap, raise_on_error=False)
             gens += r.generations
-            part = (r.fmin_lo, r.fmin_hi, r.box_lo, r.box_hi, r.box_flo, gens, r.status)
             done = r.status != _LIMIT
-            if not done:
+            if done:
+                finished.append((r.fmin_lo, r.fmin_hi, r.box_lo, r.box_hi, r.box_flo, gens, r.status))
+                snap = Snapshot(n, snap.block, np.zeros((0, n)), np.zeros((0, n)), np.zeros(0),
+                                np.zeros(0, np.int32), float(r.fmin_hi), snap.generations)
+            else:
                 snap = solver.snapshot()
         # the incumbent exchange: a min over the ranks' GUBs (and whether all are done)
         views = [None] * world
-        dist.all_gather_object(views, (float(part[1]) if solver is not None else float(snap.gub), done))
+        dist.all_gather_object(views, (float(snap.gub), done))
         gub = min(v[0] for v in views)
         if all(v[1] for v in views):
             break
-        if not done:
-            snap = Snapshot(snap.n, snap.block, snap.lo, snap.hi, snap.flo, snap.cyc, min(snap.gub, gub),
-                            snap.generations)
-    if solver is not None:
-        solver.close()
+        if rebalance:   # pool the unfinished lists and deal them out again
+            lists = [None] * world
+            dist.all_gather_object(lists, None if done else _pack(snap))
+            live = [Snapshot(**x) for x in lists if x is not None]
+            snap = split_snapshot(_concat(live), world)[rank]
+        snap = Snapshot(snap.n, snap.block, snap.lo, snap.hi, snap.flo, snap.cyc, min(snap.gub, gub),
+                        snap.generations)
+    solver.close()
+    mine = finished or [(np.inf, snap.gub, None, None, np.zeros(0), gens, 0)]
     parts = [None] * world
-    dist.all_gather_object(parts, part)
-    return merge_results(parts, n)
+    dist.all_gather_object(parts, mine)
+    return merge_results([q for p in parts for q in p], n)
 
 
 _LIMIT = 4   # GB_E_LIMIT: the round's generation limit, regions still active

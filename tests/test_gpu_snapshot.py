@@ -153,8 +153,9 @@ class _ThreadDist:
         self.bar.wait()
 
 
+@pytest.mark.parametrize("rebalance", [False, True])
 @pytest.mark.parametrize("world", [2, 3])
-def test_sharded_solve_ranks_as_threads(world):
+def test_sharded_solve_ranks_as_threads(world, rebalance):
     # shard.sharded_solve with its ranks as threads on this GPU: rounds of
     # generations with the incumbent exchanged between them; the merged
     # enclosure is rigorous and within tol_f, covers the planted minimiser
@@ -170,7 +171,7 @@ def test_sharded_solve_ranks_as_threads(world):
         try:
             D.local.rank = rank
             res[rank] = shard.sharded_solve(lambda g: gb.Solver(p, max_generations=g, **opts), 6, D, rank, world,
-                                            round_generations=16)
+                                            round_generations=16, rebalance=rebalance)
         except Exception as e:   # noqa: BLE001 - reported below
             errs.append(e)
             D.bar.abort()

@@ -36,7 +36,7 @@ class _FakeSolver:
     it was given and keeps the regions with LB not above it."""
 
     def __init__(self, rank, max_gen):
-        self.rank, self.max_gen, self.calls, self.given = rank, max_gen, 0, []
+        self.rank, self.max_gen, self.calls, self.given, self.seen = rank, max_gen, 0, [], []
         self.regions = None
 
     def solve(self, raise_on_error=True):
@@ -54,6 +54,7 @@ class _FakeSolver:
     def resume(self, snap, raise_on_error=True):
         self.calls += 1
         self.given.append(snap.gub)
+        self.seen.append([round(float(v), 6) for v in snap.flo])
         self.regions = (snap.lo, snap.hi, snap.flo)
         if self.calls == 1:
             r = _FakeResult(snap.lo, snap.hi, snap.flo, [0.5, 0.25][self.rank], 3)
@@ -66,7 +67,7 @@ class _FakeSolver:
         pass
 
 
-def _rank(rank, world, port, out):
+def _rank(rank, world, port, out, rebalance=False):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     from paper_2507_01770_gb300 import shard
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -76,23 +77,30 @@ def _rank(rank, world, port, out):
         made.append(_FakeSolver(rank, g))
         return made[-1]
 
-    res = shard.sharded_solve(make, 5, dist, rank, world, round_generations=3)
-    out.put((rank, res.fmin_lo, res.fmin_hi, res.box_flo.tolist(), res.generations, made[-1].given))
+    res = shard.sharded_solve(make, 5, dist, rank, world, round_generations=3, rebalance=rebalance)
+    out.put((rank, res.fmin_lo, res.fmin_hi, res.box_flo.tolist(), res.generations, made[-1].given,
+             made[-1].seen))
     dist.destroy_process_group()
 
 
-def test_sharded_solve_two_gloo_ranks():
+@pytest.mark.parametrize("rebalance", [False, True])
+def test_sharded_solve_two_gloo_ranks(rebalance):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q, rebalance)) for r in range(2)]
     for p in procs:
         p.start()
     got = [q.get(timeout=120) for _ in procs]
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, glb, gub, flo, gens, given in got:
+    for rank, glb, gub, flo, gens, given, seen in got:
+        # round 2 regions: the rank's own, or (rebalanced) the pooled lists
+        # [0 .2 .4 .6 .8 | .1 .3 .5 .7 .9] dealt out again
+        own = [[0.0, 0.2, 0.4, 0.6, 0.8], [0.1, 0.3, 0.5, 0.7, 0.9]][rank]
+        dealt = [[0.0, 0.4, 0.8, 0.3, 0.7], [0.2, 0.6, 0.1, 0.5, 0.9]][rank]
+        assert seen == [own, dealt if rebalance else own]
         # round 1 starts from the split's incumbent 0.55; after it the ranks
         # exchange 0.5 and 0.25, so round 2 of every rank runs with 0.25 and
         # keeps its regions with LB <= 0.25: rank 0 {0, 0.2}, rank 1 {0.1}
@@ -100,7 +108,7 @@ def test_sharded_solve_two_gloo_ranks():
         assert gub == 0.25
         assert sorted(flo) == [0.0, 0.1, 0.2]
         assert glb == 0.0
-        assert gens == [3 + 4, 3 + 5]
+        assert sorted(gens) == [3 + 4, 3 + 5]
 
 
 def test_split_and_merge_without_ranks():
