@@ -106,6 +106,18 @@ def test_autotune_rejects_invalid_problems_without_gpu():
     assert e.value.status == gb.GB_E_INVALID
 
 
+def test_checkpoint_and_server_calls_reject_null_without_gpu():
+    import ctypes
+    L = gb.load()
+    snap = gb.gb_snapshot()
+    res = gb.gb_result()
+    assert L.gb_snapshot_take(None, ctypes.byref(snap)) == gb.GB_E_INVALID
+    assert L.gb_solve_resume(None, ctypes.byref(snap), ctypes.byref(res)) == gb.GB_E_INVALID
+    assert L.gb_server_set_fused(None, 1) == gb.GB_E_INVALID
+    L.gb_free_snapshot(ctypes.byref(snap))          # a zeroed snapshot is released safely
+    L.gb_free_result(ctypes.byref(res))
+
+
 def test_status_strings():
     assert gb.gb_status_str(gb.GB_OK) == "ok"
     assert gb.gb_status_str(gb.GB_E_CAPACITY) == "box pool capacity reached"
