@@ -125,3 +125,20 @@ def test_split_and_merge_without_ranks():
     m = shard.merge_results([(0.0, 2.0, lo[:3], lo[:3] + 1, q[:3], 1, 0), (1.0, 1.5, lo[3:], lo[3:] + 1, q[3:], 2, 0)],
                             2)
     assert m.fmin_hi == 1.5 and m.fmin_lo == 0.0 and list(m.box_flo) == [0.0, 1.0]
+
+
+def test_split_with_more_ranks_than_regions_and_merge_of_empty_parts():
+    import paper_2507_01770_gb300 as gb
+    from paper_2507_01770_gb300 import shard
+    lo = np.array([[0.0, 1.0], [2.0, 3.0]])
+    snap = gb.Snapshot(2, 2, lo, lo + 1, np.array([0.5, 0.25]), np.array([0, 1], np.int32), 1.0, 2)
+    parts = shard.split_snapshot(snap, 4)
+    assert [len(p.flo) for p in parts] == [1, 1, 0, 0]
+    assert parts[2].lo.shape == (0, 2) and parts[3].gub == 1.0
+    m = shard.merge_results([(np.inf, 1.0, None, None, np.zeros(0), 0, 0),
+                             (0.25, 0.75, lo[1:], lo[1:] + 1, np.array([0.25]), 3, 0)], 2)
+    assert m.fmin_hi == 0.75 and m.fmin_lo == 0.25 and len(m.box_flo) == 1
+    c = shard._concat([parts[0], parts[1], parts[2]])
+    assert list(c.flo) == [0.5, 0.25] and c.gub == 1.0
+    with pytest.raises(ValueError):
+        shard.split_snapshot(snap, 0)
