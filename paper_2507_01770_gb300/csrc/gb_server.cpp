@@ -67,6 +67,7 @@ struct gb_server {
     bool stop = false;
     int fused = 0;
     GbBatchCtx* batch = nullptr;   // worker thread only
+    bool batch_failed = false;     // could not set up the fused step: requests advance on their own
     std::thread worker;
 };
 
@@ -134,7 +135,10 @@ void worker_loop(gb_server* S) {
             std::lock_guard<std::mutex> lk(S->mu);
             fused = S->fused;
         }
-        if (fused && !S->batch) S->batch = batch_create(S->device);
+        if (fused && !S->batch && !S->batch_failed) {
+            S->batch = batch_create(S->device);
+            S->batch_failed = S->batch == nullptr;
+        }
         std::vector<gb_problem*> step;   // fusable requests ready for their next generation
         for (size_t k = 0; k < S->running.size();) {
             auto r = S->running[k];
