@@ -23,6 +23,10 @@ levy50_paper
   children of one region per iteration, 10 diagonal GUB samples, first-order
   test on every coordinate, region width 1e-4; metric = solve time, compared
   with the time the paper prints for it (Table 2).
+paper (--family F --n N [--pool-mode 2])
+  the same procedure on any of the paper's functions (SI Appendix A, F) at
+  any n; compared with the cloud-server time the paper prints for (F, N)
+  when it prints one (Table 2, Tables S2-S10, S14).
 serving
   512 requests, Poisson arrivals (20/s), n log-uniform on [2, 2000], family
   uniform over sep_cos / chain / ackley, width 1e-6, 150 GB pool budget:
@@ -98,13 +102,46 @@ WORKLOADS = {
 }
 
 
+# The paper's procedure: iterations per block of 10 coordinates and the
+# cloud-server (GH200) solve times it prints, by function and n (Table 2,
+# Tables S2-S10, S14).
+PAPER_PRINTED = {
+    "paper_levy": (9, {50: 15, 100: 42, 500: 909, 1000: 3582, 2000: 14543, 5000: 93447, 10000: 376589}),
+    "paper_ackley": (10, {50: 11, 100: 29, 500: 565, 1000: 2288}),
+    "paper_belegundu": (9, {50: 6, 100: 15, 500: 426, 1000: 1896}),
+    "paper_breiman": (8, {50: 5, 100: 13, 500: 301, 1000: 1218}),
+    "paper_fu": (9, {50: 13, 100: 41, 500: 892, 1000: 3538}),
+    "paper_griewank": (11, {50: 9, 100: 28, 500: 605, 1000: 2523}),
+    "paper_rastrigin": (9, {50: 6, 100: 18, 500: 400, 1000: 1727}),
+    "paper_salomon": (11, {50: 5, 100: 12, 500: 328, 1000: 1435}),
+    "paper_styblinski": (9, {50: 7, 100: 21, 500: 419, 1000: 1791}),
+    "paper_zabinsky": (8, {50: 9, 100: 26, 500: 619, 1000: 2635}),
+    "paper_discontinuous": (9, {50: 35, 100: 114, 500: 2527, 1000: 9928}),
+}
+
+
+def _paper_workload(family, n, pool_mode, pool_gb):
+    per_block, times = PAPER_PRINTED[family]
+    return dict(family=family, n=n, block=10, split_m=4, split_d=10, max_children=1 << 20, fp32=0,
+                gens_per_sync=0, pool_gb=pool_gb or 32.0, pool_mode=pool_mode, cpu_parents=1, cpu_split_m=4,
+                cpu_split_d=5, cpu_gens=2, paper=True, baseline_s=times.get(n), paper_iters=per_block * n // 10,
+                name=f"the paper's procedure on {family[6:]} n={n}: 4-way split of the 10 block coordinates "
+                     "(4^10 children) of 1 best region per iteration, 10 diagonal samples, first-order test "
+                     "on every coordinate, region width tolerance 1e-4"
+                     + (", block-record pool" if pool_mode == 2 else ""))
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb", choices=["gb", "reference"])
-    ap.add_argument("--workload", default="chain100", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--workload", default="chain100", choices=sorted(WORKLOADS) + ["serving", "paper"])
+    ap.add_argument("--family", default="paper_levy", choices=sorted(PAPER_PRINTED),
+                    help="paper workload: the function")
+    ap.add_argument("--n", type=int, default=50, help="paper workload: the dimension")
+    ap.add_argument("--pool-mode", type=int, default=0, help="paper workload: 2 for block records")
     ap.add_argument("--max-children", type=int, default=0, help="children per generation (0: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-gens", type=int, default=0, help="generations in the oracle sample (0: the workload's)")
@@ -119,6 +156,8 @@ def _args():
 
 
 def _workload(a):
+    if a.workload == "paper":
+        return _paper_workload(a.family, a.n, a.pool_mode, a.pool_gb)
     return WORKLOADS[a.workload if a.workload in WORKLOADS else "chain100"]
 
 
@@ -446,6 +485,8 @@ def main():
                 pool_bytes=int((a.pool_gb or w["pool_gb"]) * (1 << 30)))
     if w.get("paper"):
         opts.update(samples=10, mono_all=1, tol_x=1e-4)
+        if w.get("pool_mode"):
+            opts["pool_mode"] = w["pool_mode"]
     if a.max_gens > 0:
         opts["max_generations"] = a.max_gens
     solver = gb.Solver(p, **opts)
@@ -537,7 +578,7 @@ def main():
     if w.get("paper"):   # the paper prints solve times for its procedure
         metric, unit, hib = "solve time", "s", False
         value = dev_ms * 1e-3 / a.steps
-        vsb = value / w["baseline_s"]
+        vsb = value / w["baseline_s"] if w.get("baseline_s") else None
     line = {
         "metric": metric, "value": value, "unit": unit, "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dev_ms / a.steps,
