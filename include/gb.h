@@ -316,11 +316,14 @@ gb_status gb_eval_boxes(gb_problem* prob, const double* d_lo, const double* d_hi
  * of this entry point.
  *  - The FP32 copy of the boxes that fp32 = 1 needs is kept in a fixed array
  *    inside the library instead of a per-call buffer: at most 2^20
- *    coordinates (nbox * n <= 1048576) per call; larger calls return
- *    GB_E_INVALID with a message.  The array (8 MiB) is held on every GPU
- *    that loads the library until the process exits.
- *  - The first call on a device looks up the array's device address with
- *    that device current; make that first call before any stream capture.
+ *    coordinates (nbox * n <= 1048576) per FP32 call; larger FP32 calls
+ *    return GB_E_INVALID with a message.  fp32 = 0 needs no scratch and has
+ *    no size limit.  The array (8 MiB) is held on every GPU that loads the
+ *    library until the process exits.
+ *  - The first FP32 call on a device looks up the array's device address
+ *    with that device current (a failed lookup is retried by the next call);
+ *    make that first call before any stream capture.  The caller's current
+ *    device is left as it was.
  *  - Every call shares the one array; each call writes the part it uses
  *    before reading it, so no clearing is needed, but calls whose work
  *    overlaps on the GPU (unordered streams or threads) race. */

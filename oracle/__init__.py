@@ -21,7 +21,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _CFLAGS = ["-O1", "-frounding-math", "-ffp-contract=off", "-fno-fast-math",
-           "-fno-math-errno", "-shared", "-fPIC"]
+           "-fno-math-errno", "-pthread", "-shared", "-fPIC"]
 _lock = threading.Lock()
 _lib = None
 
@@ -50,7 +50,7 @@ class _Opts(ctypes.Structure):
                 ("split_m", ctypes.c_int32), ("split_d", ctypes.c_int32),
                 ("fp32", ctypes.c_int32), ("samples", ctypes.c_int32),
                 ("max_gen", ctypes.c_int64), ("max_parents", ctypes.c_int64),
-                ("cap", ctypes.c_int64), ("mono_all", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("cap", ctypes.c_int64), ("mono_all", ctypes.c_int32), ("threads", ctypes.c_int32)]
 
 
 _P64 = ctypes.POINTER(ctypes.c_int64)
@@ -209,13 +209,16 @@ class Oracle:
     def solve(self, tol_f: float | None = None, tol_x: float = 0.0, split_m: int = 2,
               split_d: int = 1, fp32: bool = False, max_gen: int = 10**9,
               max_parents: int = 1 << 20, cap: int = 1 << 40, samples: int = 0,
-              mono_all: bool = False) -> SolveResult:
+              mono_all: bool = False, threads: int = 1) -> SolveResult:
         """samples: 0 one midpoint sample per box, S > 0 the S interior diagonal
         points j / (S + 1); mono_all: first-order test on every coordinate
-        (the paper's rule) instead of the active block."""
+        (the paper's rule) instead of the active block; threads: threads for
+        the per-child loops of a generation (the result does not depend on
+        it)."""
         o = _Opts(tol_f=float(self.p.tol_f if tol_f is None else tol_f), tol_x=float(tol_x),
                   split_m=split_m, split_d=split_d, fp32=int(fp32), samples=int(samples),
-                  max_gen=max_gen, max_parents=max_parents, cap=cap, mono_all=int(mono_all), pad=0)
+                  max_gen=max_gen, max_parents=max_parents, cap=cap, mono_all=int(mono_all),
+                  threads=int(threads))
         r = _Result()
         lib().oracle_solve(self.h, ctypes.byref(o), ctypes.byref(r))
         try:

@@ -25,10 +25,14 @@
  * takes the readings written beside each function.
  *
  * Build: gcc -O1 -frounding-math -ffp-contract=off -fno-fast-math
- *        -fno-math-errno -shared -fPIC oracle.c -lm
- * No claim of speed is made; every directed operation is its own call.
+ *        -fno-math-errno -pthread -shared -fPIC oracle.c -lm
+ * No claim of speed is made; every directed operation is its own call.  The
+ * per-child loops of a generation may run on several threads (each with its
+ * own scratch and its own rounding mode, results in per-child slots), which
+ * changes nothing in what is computed.
  */
 #include <fenv.h>
+#include <pthread.h>
 #include <float.h>
 #include <math.h>
 #include <stdint.h>
@@ -485,6 +489,34 @@ static oprob* make_prob(const void* nodes, int nn, int root, const double* const
     return P;
 }
 
+/* A copy of P that shares its structure (read only) and owns fresh scratch
+ * arrays, so that several threads can evaluate boxes of one problem. */
+static oprob* clone_scratch(const oprob* P) {
+    oprob* Q = (oprob*)malloc(sizeof(oprob));
+    *Q = *P;
+    Q->val = (iv*)calloc(P->nn, sizeof(iv));
+    Q->adj = (iv*)calloc(P->nn, sizeof(iv));
+    Q->tval = (iv*)calloc(P->nn, sizeof(iv));
+    Q->tadj = (iv*)calloc(P->nn, sizeof(iv));
+    Q->terms = (iv*)calloc(P->max_terms, sizeof(iv));
+    Q->groups = (iv*)calloc(P->max_terms, sizeof(iv));
+    Q->gsum = (iv*)calloc(P->max_terms, sizeof(iv));
+    Q->gadj = (iv*)calloc(P->max_terms, sizeof(iv));
+    Q->tseed = (iv*)calloc(P->max_terms, sizeof(iv));
+    Q->gstart = (int*)calloc(P->max_terms + 1, sizeof(int));
+    Q->dacc = (iv*)calloc(P->B, sizeof(iv));
+    Q->touched = (char*)calloc(P->B, 1);
+    return Q;
+}
+
+static void free_clone(oprob* Q) {
+    if (!Q) return;
+    free(Q->val); free(Q->adj); free(Q->tval); free(Q->tadj); free(Q->terms);
+    free(Q->groups); free(Q->gsum); free(Q->gadj); free(Q->tseed); free(Q->gstart);
+    free(Q->dacc); free(Q->touched);
+    free(Q);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Evaluation                                                                */
 /* ------------------------------------------------------------------------ */
@@ -928,7 +960,8 @@ typedef struct {
     double tol_f, tol_x;
     int32_t split_m, split_d, fp32, samples;   /* samples: 0 midpoint, S > 0 diagonal points */
     int64_t max_gen, max_parents, cap;
-    int32_t mono_all, pad;                     /* mono_all: first-order test on every coordinate */
+    int32_t mono_all;                          /* mono_all: first-order test on every coordinate */
+    int32_t threads;                           /* threads for the per-child loops (<= 1: one) */
 } oopts;
 
 typedef struct {
@@ -1041,6 +1074,67 @@ static int mono_box(oprob* P, obox X, int p, int blk, iv* G, int mono_all) {
     return 0;
 }
 
+/* The per-child passes of a generation: 0 the FP32 test (cut-off against
+ * the previous GUB and the first-order test), 1 the GUB samples of the
+ * children the FP32 test kept, 2 the FP64 test of those children against
+ * the new GUB.  Each job takes the children [q0, q1) with its own copy of
+ * the problem's scratch; every result goes to the child's own slot. */
+typedef struct {
+    oprob* P;
+    const oopts* opt;
+    entry* kids;
+    int64_t q0, q1;
+    char *cand, *ok;
+    double* fm;
+    double gub_prev, gub_new;
+    int64_t mids;
+    int pass;
+    iv* G;
+    double* mid;
+} cjob;
+
+static void* child_pass(void* arg) {
+    cjob* J = (cjob*)arg;
+    for (int64_t q = J->q0; q < J->q1; q++) {
+        entry* ch = &J->kids[q];
+        obox X = {ch->lo, ch->hi};
+        if (J->pass == 0) {
+            iv f = eval_outer(J->P, X, 1);
+            int mono = mono_box(J->P, X, 1, ch->blk, J->G, J->opt->mono_all);
+            J->cand[q] = !(f.lo > J->gub_prev) && !mono;
+        } else if (J->pass == 1) {
+            J->fm[q] = J->cand[q] ? sample_gub(J->P, ch->lo, ch->hi, J->opt->samples, J->mid, &J->mids) : INFINITY;
+        } else {
+            J->ok[q] = 0;
+            if (!J->cand[q]) continue;
+            iv f = eval_outer(J->P, X, 0);
+            int mono = mono_box(J->P, X, 0, ch->blk, J->G, J->opt->mono_all);
+            J->ok[q] = !(f.lo > J->gub_new) && !mono;
+            ch->flo = canon_lo(f.lo);
+        }
+    }
+    return NULL;
+}
+
+/* Runs pass `pass` over children [0, count) on T jobs (contiguous chunks);
+ * job 0 runs on the calling thread. */
+static void run_pass(cjob* jobs, int T, int pass, int64_t count) {
+    pthread_t tid[256];
+    int started[256] = {0};
+    for (int t = 0; t < T; t++) {
+        jobs[t].pass = pass;
+        jobs[t].q0 = count * t / T;
+        jobs[t].q1 = count * (t + 1) / T;
+    }
+    for (int t = 1; t < T; t++)
+        started[t] = pthread_create(&tid[t], NULL, child_pass, &jobs[t]) == 0;
+    child_pass(&jobs[0]);
+    for (int t = 1; t < T; t++) {
+        if (started[t]) pthread_join(tid[t], NULL);
+        else child_pass(&jobs[t]);   /* no thread: run it here */
+    }
+}
+
 int oracle_solve(void* h, const oopts* opt, oresult* R) {
     oprob* P = (oprob*)h;
     memset(R, 0, sizeof(*R));
@@ -1053,6 +1147,14 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
     int64_t tcap = 0;
     iv* G = (iv*)malloc(sizeof(iv) * B);
     double* mid = (double*)malloc(sizeof(double) * n);
+    const int T = opt->threads < 1 ? 1 : (opt->threads > 256 ? 256 : opt->threads);
+    cjob* jobs = (cjob*)calloc(T, sizeof(cjob));
+    for (int t = 0; t < T; t++) {
+        jobs[t].P = t == 0 ? P : clone_scratch(P);
+        jobs[t].opt = opt;
+        jobs[t].G = (iv*)malloc(sizeof(iv) * B);
+        jobs[t].mid = (double*)malloc(sizeof(double) * n);
+    }
 
     /* initialisation: the whole domain (section 3.1) */
     elist pool = {0}, par = {0}, kids = {0}, keep = {0};
@@ -1156,41 +1258,39 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
 
         /* sample (GUB update) and rule out (cut-off and first-order test) */
         double gub_prev = gub, gub_new = gub;
-        char* cand = (char*)malloc(kids.len ? kids.len : 1);
+        const int64_t nk = kids.len ? kids.len : 1;
+        char* cand = (char*)malloc(nk);
+        char* okv = (char*)malloc(nk);
+        double* fmv = (double*)malloc(sizeof(double) * nk);
+        for (int t = 0; t < T; t++) {
+            jobs[t].kids = kids.e;
+            jobs[t].cand = cand;
+            jobs[t].ok = okv;
+            jobs[t].fm = fmv;
+            jobs[t].gub_prev = gub_prev;
+            jobs[t].mids = 0;
+        }
         int64_t kept32 = kids.len;
         if (f32) {
+            run_pass(jobs, T, 0, kids.len);
             kept32 = 0;
-            for (int64_t q = 0; q < kids.len; q++) {
-                entry* ch = &kids.e[q];
-                obox X = {ch->lo, ch->hi};
-                iv f = eval_outer(P, X, 1);
-                int mono = mono_box(P, X, 1, ch->blk, G, opt->mono_all);
-                cand[q] = !(f.lo > gub_prev) && !mono;
-                kept32 += cand[q];
-            }
+            for (int64_t q = 0; q < kids.len; q++) kept32 += cand[q];
             R->evals32 += kids.len;
         } else {
             memset(cand, 1, kids.len);
         }
-        for (int64_t q = 0; q < kids.len; q++) {
-            if (!cand[q]) continue;
-            entry* ch = &kids.e[q];
-            double fm = sample_gub(P, ch->lo, ch->hi, opt->samples, mid, &R->mids);
-            if (fm < gub_new) gub_new = fm;
-        }
+        run_pass(jobs, T, 1, kids.len);
+        for (int t = 0; t < T; t++) R->mids += jobs[t].mids;
+        for (int64_t q = 0; q < kids.len; q++)   /* the minimum is exact: any order gives it */
+            if (cand[q] && fmv[q] < gub_new) gub_new = fmv[q];
+        for (int t = 0; t < T; t++) jobs[t].gub_new = gub_new;
+        run_pass(jobs, T, 2, kids.len);
         keep.len = 0;
         int64_t kept = 0;
         for (int64_t q = 0; q < kids.len; q++) {
             entry* ch = &kids.e[q];
-            int ok = 0;
-            if (cand[q]) {
-                obox X = {ch->lo, ch->hi};
-                iv f = eval_outer(P, X, 0);
-                R->evals64++;
-                int mono = mono_box(P, X, 0, ch->blk, G, opt->mono_all);
-                ok = !(f.lo > gub_new) && !mono;
-                ch->flo = canon_lo(f.lo);
-            }
+            const int ok = okv[q];
+            if (cand[q]) R->evals64++;
             if (ok) {
                 int fin = 0;
                 if (opt->tol_x > 0.0) {
@@ -1205,7 +1305,7 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
                 ent_free(ch);
             }
         }
-        free(cand);
+        free(cand); free(okv); free(fmv);
         /* capacity: boxes alive during the generation.  On overflow the
            generation is abandoned: its children are dropped, its parents go
            back to the end of the list, the samples' GUB is kept, and the
@@ -1254,6 +1354,12 @@ int oracle_solve(void* h, const oopts* opt, oresult* R) {
     }
     free(out.e); free(par.e); free(kids.e); free(keep.e);
     free(G); free(mid);
+    for (int t = 0; t < T; t++) {
+        free(jobs[t].G);
+        free(jobs[t].mid);
+        if (t > 0) free_clone(jobs[t].P);
+    }
+    free(jobs);
     R->generations = gen;
     R->status = status;
     return status;

@@ -252,7 +252,9 @@ class Result:
     trace: dict
 
 
-def _result(r: gb_result, n: int) -> Result:
+def _result(r: gb_result, n: int, rc: int | None = None) -> Result:
+    """The host copy of a result; `rc` (the call's return code) is the
+    status whenever it is given, so a failed call never reads as OK."""
     nb = r.n_boxes
 
     def arr(ptr, count):
@@ -268,7 +270,7 @@ def _result(r: gb_result, n: int) -> Result:
         for k in tr:
             tr[k].append(getattr(g, k))
     tr = {k: np.array(v) for k, v in tr.items()}
-    return Result(r.fmin_lo, r.fmin_hi, r.status, nb,
+    return Result(r.fmin_lo, r.fmin_hi, r.status if rc is None else int(rc), nb,
                   lo.reshape(nb, n) if lo is not None else None,
                   hi.reshape(nb, n) if hi is not None else None,
                   arr(r.box_flo, nb), r.generations, r.box_evals_fp32, r.box_evals_fp64,
@@ -282,7 +284,7 @@ def gb_solve(prob: _Problem, device_only: bool = False, raise_on_error: bool = T
     r = gb_result()
     rc = (L.gb_solve_device if device_only else L.gb_solve)(prob.handle, ctypes.byref(r))
     try:
-        res = _result(r, prob.n)
+        res = _result(r, prob.n, rc)
     finally:
         L.gb_free_result(ctypes.byref(r))
     if rc not in (GB_OK, GB_E_CAPACITY, GB_E_LIMIT) and raise_on_error:
@@ -386,7 +388,7 @@ def gb_solve_resume(prob: "_Problem", snap: Snapshot, raise_on_error: bool = Tru
     r = gb_result()
     rc = L.gb_solve_resume(prob.handle, ctypes.byref(s), ctypes.byref(r))
     try:
-        res = _result(r, prob.n)
+        res = _result(r, prob.n, rc)
     finally:
         L.gb_free_result(ctypes.byref(r))
     if rc not in (GB_OK, GB_E_CAPACITY, GB_E_LIMIT) and raise_on_error:

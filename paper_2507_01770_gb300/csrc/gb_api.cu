@@ -944,9 +944,17 @@ static gb_status solve_impl(gb_problem* p, gb_result* out, bool copy_boxes, cons
     return fin;
 }
 
-gb_status gb_solve(gb_problem* p, gb_result* out) { return solve_impl(p, out, true); }
+// The status of a solve goes into the result on every return path, so a
+// caller that reads out->status sees a failure (whose result holds no
+// enclosure) as well as the return code does.
+static gb_status with_status(gb_result* out, gb_status rc) {
+    if (out) out->status = rc;
+    return rc;
+}
 
-gb_status gb_solve_device(gb_problem* p, gb_result* out) { return solve_impl(p, out, false); }
+gb_status gb_solve(gb_problem* p, gb_result* out) { return with_status(out, solve_impl(p, out, true)); }
+
+gb_status gb_solve_device(gb_problem* p, gb_result* out) { return with_status(out, solve_impl(p, out, false)); }
 
 gb_status gb_snapshot_take(gb_problem* p, gb_snapshot* out) {
     if (!p || !out) return fail(GB_E_INVALID, "NULL argument");
@@ -998,7 +1006,7 @@ gb_status gb_snapshot_take(gb_problem* p, gb_snapshot* out) {
     return rc;
 }
 
-gb_status gb_solve_resume(gb_problem* p, const gb_snapshot* snap, gb_result* out) {
+static gb_status solve_resume_impl(gb_problem* p, const gb_snapshot* snap, gb_result* out) {
     if (!p || !snap || !out) return fail(GB_E_INVALID, "NULL argument");
     std::memset(out, 0, sizeof(*out));
     if (snap->n != p->n) return fail(GB_E_INVALID, "snapshot dimension differs from the problem's");
@@ -1020,6 +1028,10 @@ gb_status gb_solve_resume(gb_problem* p, const gb_snapshot* snap, gb_result* out
                                               std::to_string(q));
     }
     return solve_impl(p, out, true, snap);
+}
+
+gb_status gb_solve_resume(gb_problem* p, const gb_snapshot* snap, gb_result* out) {
+    return with_status(out, solve_resume_impl(p, snap, out));
 }
 
 void gb_free_snapshot(gb_snapshot* snap) {

@@ -1377,6 +1377,18 @@ inline unsigned grid_for(long long items, int per_block) {
 thread_local long long gb_launch_count = 0;
 
 long long gb_launches_so_far() { return gb_launch_count; }
+
+int gb_sm_count() {
+    static int sms[64];   // per device ordinal, 0 until queried
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int v = __atomic_load_n(&sms[dev], __ATOMIC_RELAXED);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 152;
+        __atomic_store_n(&sms[dev], v, __ATOMIC_RELAXED);
+    }
+    return v;
+}
 cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, double tol_x,
                                 GbState* st, cudaStream_t s) {
     gb_launch_count++;
@@ -1410,7 +1422,7 @@ cudaError_t gb_launch_resume(const GbProg& P, const GbPool& pool, const GbEntrie
 
 cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, GbState* st, cudaStream_t s) {
     unsigned g = grid_for(cap, 256);
-    if (g > 152 * 8) g = 152 * 8;
+    if (g > gb_sm_count() * 8) g = gb_sm_count() * 8;
     gb_launch_count++;
     k_stats<<<g, 256, 0, s>>>(E, G, st);
     return cudaGetLastError();
@@ -1422,10 +1434,10 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
                                  GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch, int part) {
     long long n0 = gb_launch_count;
     cudaError_t e;
-    const unsigned gpool = (unsigned)std::min<long long>(grid_for(cap, 256), 152 * 8);
-    const unsigned gtile_pool = (unsigned)std::min<long long>(grid_for(cap, GB_TILE), 152 * 8);
-    const unsigned gtile_ch = (unsigned)std::min<long long>(grid_for(Cmax, GB_TILE), 152 * 8);
-    const unsigned gch = (unsigned)std::min<long long>(grid_for(Cmax, 128), 152 * 32);
+    const unsigned gpool = (unsigned)std::min<long long>(grid_for(cap, 256), gb_sm_count() * 8);
+    const unsigned gtile_pool = (unsigned)std::min<long long>(grid_for(cap, GB_TILE), gb_sm_count() * 8);
+    const unsigned gtile_ch = (unsigned)std::min<long long>(grid_for(Cmax, GB_TILE), gb_sm_count() * 8);
+    const unsigned gch = (unsigned)std::min<long long>(grid_for(Cmax, 128), gb_sm_count() * 32);
     // part 0: the whole generation; 1: up to the child evaluation; 2: after it
     if (part == 2) goto after_eval;
     {
@@ -1502,9 +1514,9 @@ after_eval:
         k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_off, ch.surv);
     }
     if (pool.recs) {
-        const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), 152 * 8);
+        const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), gb_sm_count() * 8);
         gb_launch_count += 4;
-        k_gc_mark<<<152 * 8, 256, 0, s>>>(pool, E_new, par, st);
+        k_gc_mark<<<gb_sm_count() * 8, 256, 0, s>>>(pool, E_new, par, st);
         k_gc_count<<<grec, PT, 0, s>>>(pool, st, sc.tile_cnt);
         k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0, G, st);
         k_gc_scatter<<<grec, PT, 0, s>>>(pool, st, sc.tile_off);
@@ -1512,7 +1524,7 @@ after_eval:
     GbTabs Tb{};
     if (tabs) Tb = *tabs;
     gb_launch_count++;
-    const unsigned gmat = (unsigned)std::min<long long>(grid_for(Cmax * 32, 128), 152 * 16);
+    const unsigned gmat = (unsigned)std::min<long long>(grid_for(Cmax * 32, 128), gb_sm_count() * 16);
     if (P.any_prod)
         k_materialize<true><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, tabs ? 1 : 0);
     else

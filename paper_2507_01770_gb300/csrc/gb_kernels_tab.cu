@@ -894,7 +894,7 @@ cudaError_t gb_launch_eval3264_batch(const GbEvalDesc* d_desc, int nreq, long lo
     if (nreq <= 0) return cudaSuccess;
     if (nreq > GB_BATCH_MAX) return cudaErrorInvalidValue;
     gb_launch_count++;
-    const unsigned grid = (unsigned)std::min<long long>(grid_for(max_units * 32, 128), 152 * 8);
+    const unsigned grid = (unsigned)std::min<long long>(grid_for(max_units * 32, 128), gb_sm_count() * 8);
     k_eval3264_batch<<<grid, 128, 0, s>>>(d_desc, nreq);
     return cudaGetLastError();
 }
@@ -916,12 +916,12 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
                                  GbState* st, cudaStream_t s) {
     if (T.warp) {
         unsigned g = grid_for(Cmax * 32, 128);
-        if (g > 152 * 32) g = 152 * 32;
+        if (g > gb_sm_count() * 32) g = gb_sm_count() * 32;
         k_eval64_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
         return cudaGetLastError();
     }
     unsigned g = grid_for(Cmax, 128);
-    if (g > 152 * GB_TAB_GRID) g = 152 * GB_TAB_GRID;
+    if (g > gb_sm_count() * GB_TAB_GRID) g = gb_sm_count() * GB_TAB_GRID;
     k_eval64_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
     return cudaGetLastError();
 }
@@ -937,7 +937,7 @@ cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const G
                                     const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
                                     cudaStream_t s) {
     unsigned g = grid_for(Cmax * 32, 128);
-    if (g > 152 * 32) g = 152 * 32;
+    if (g > gb_sm_count() * 32) g = gb_sm_count() * 32;
     k_eval3264_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);
     return cudaGetLastError();
 }
@@ -947,12 +947,12 @@ cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbPa
                                  cudaStream_t s) {
     if (T.warp) {
         unsigned g = grid_for(Cmax * 32, 128);
-        if (g > 152 * 32) g = 152 * 32;
+        if (g > gb_sm_count() * 32) g = gb_sm_count() * 32;
         k_eval32_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);
         return cudaGetLastError();
     }
     unsigned g = grid_for(Cmax, 128);
-    if (g > 152 * GB_TAB_GRID) g = 152 * GB_TAB_GRID;
+    if (g > gb_sm_count() * GB_TAB_GRID) g = gb_sm_count() * GB_TAB_GRID;
     k_eval32_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);
     return cudaGetLastError();
 }

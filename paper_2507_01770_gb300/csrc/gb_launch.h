@@ -116,8 +116,8 @@ struct GbGenConst {
 };
 
 // Child kernels run one child per warp when a generation has few children
-// (fewer than 2^16: one child per thread would leave most of the 152 SMs
-// idle), else one child per thread (eval_mode 3 / 4 force either).
+// (fewer than 2^16: one child per thread would leave most of the SMs idle),
+// else one child per thread (eval_mode 3 / 4 force either).
 inline bool gb_warp_per_child(long long Cmax) { return Cmax < (1LL << 16); }
 
 cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEntries& E, double tol_x,
@@ -172,6 +172,8 @@ cudaError_t gb_launch_eval_boxes(const GbProg& P, const double* lo, const double
                                  int* mono, cudaStream_t s);
 cudaError_t gb_launch_peak(int which, int iters, int blocks, void* sink, cudaStream_t s);
 long long gb_launches_so_far();
+// Streaming multiprocessors of the current device (queried once per device).
+int gb_sm_count();
 extern "C" const GbProg* gb_internal_prog(const gb_problem* p, int* device, int* n, int* nb);
 extern "C" gb_status gb_internal_fail(gb_status s, const char* msg);
 // resumable solve (gb_api.cu), used by the serving loop (gb_server.cpp)

@@ -238,3 +238,18 @@ def test_bad_options_rejected():
     p = S.chain(n=4)
     assert O.Oracle(p).solve(split_m=3).status == O.ST_INVALID
     assert O.Oracle(p).solve(split_d=0).status == O.ST_INVALID
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_threaded_oracle_equals_single_thread(oracle_mod, fp32):
+    # the per-child passes on several threads write per-child slots and take
+    # an exact minimum: the run must be the same as on one thread
+    p = S.ackley(n=12, seed=3, block=6) if fp32 else S.chain(n=12, seed=5, block=6)
+    o = oracle_mod.Oracle(p, block=6)
+    a = o.solve(split_m=2, split_d=3, max_parents=8, fp32=fp32, threads=1)
+    b = o.solve(split_m=2, split_d=3, max_parents=8, fp32=fp32, threads=5)
+    assert a.status == b.status and a.generations == b.generations
+    for k in a.trace:
+        assert np.array_equal(a.trace[k], b.trace[k]), k
+    assert a.glb == b.glb and a.gub == b.gub and a.mids == b.mids and a.evals64 == b.evals64
+    assert np.array_equal(a.box_lo, b.box_lo) and np.array_equal(a.box_flo, b.box_flo)

@@ -142,3 +142,52 @@ def test_split_with_more_ranks_than_regions_and_merge_of_empty_parts():
     assert list(c.flo) == [0.5, 0.25] and c.gub == 1.0
     with pytest.raises(ValueError):
         shard.split_snapshot(snap, 0)
+
+
+class _FailingSolver(_FakeSolver):
+    """As _FakeSolver, but rank 1's first resume fails (GB_E_CUDA): its
+    result holds no regions and reads status 6."""
+
+    def resume(self, snap, raise_on_error=True):
+        if self.rank == 1:
+            self.calls += 1
+            self.given.append(snap.gub)
+            self.seen.append([round(float(v), 6) for v in snap.flo])
+            r = _FakeResult(None, None, np.zeros(0), 0.0, 0)
+            r.fmin_lo = r.fmin_hi = 0.0     # what a zeroed result holds: not a bound of anything
+            r.status = 6
+            return r
+        return super().resume(snap, raise_on_error)
+
+
+def _rank_failing(rank, world, port, out, rebalance):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    from paper_2507_01770_gb300 import shard
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    res = shard.sharded_solve(lambda g: _FailingSolver(rank, g), 5, dist, rank, world, round_generations=3,
+                              rebalance=rebalance)
+    out.put((rank, res.fmin_lo, res.fmin_hi, sorted(res.box_flo.tolist()), res.statuses))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("rebalance", [False, True])
+def test_failed_resume_keeps_its_regions_in_the_merge(rebalance):
+    # rank 1's resume fails: its zeroed result (GUB 0, no regions) must not
+    # enter the merge.  It keeps the regions it was given (LB .1 .3 .5 .7 .9)
+    # with the split's incumbent 0.55; rank 0 runs round 1 (GUB 0.5) and
+    # round 2 with the exchanged 0.5 (regions 0 .2 .4).  Merge: GUB 0.5, the
+    # regions with LB <= 0.5 from both ranks, GLB 0, statuses report 6.
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_failing, args=(r, 2, port, q, rebalance)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, glb, gub, flo, statuses in got:
+        assert gub == 0.5 and glb == 0.0
+        assert flo == [0.0, 0.1, 0.2, 0.3, 0.4, 0.5]
+        assert 6 in statuses and 0 in statuses
