@@ -84,6 +84,8 @@ def lib():
             L.oracle_n_blocks.restype = ip
             L.oracle_eval_box.argtypes = [vp, dp, dp, ip, ip, dp, dp, dp,
                                           ctypes.POINTER(ctypes.c_int32)]
+            L.oracle_eval_box_dev.argtypes = [vp, dp, dp, ip, ip, dp, dp, dp, dp, dp, dp]
+            L.oracle_set_extra_widening.argtypes = [ip]
             L.oracle_iv_op.argtypes = [ip, dp, dp, ctypes.c_double, ip, dp]
             L.oracle_tree_sum.argtypes = [dp, dp, ip, ip, dp]
             L.oracle_iv_op_batch.argtypes = [ip, dp, dp, dp, dp, dp, ctypes.c_int64, ip, dp]
@@ -123,6 +125,13 @@ def iv_op_batch(op: str, xlo, xhi, ylo=None, yhi=None, c=None, f32: bool = False
                                 _dp(out)):
         raise ValueError(op)
     return out
+
+
+def set_extra_widening(k: int) -> None:
+    """Test hook: widen every transcendental endpoint by k more ulps (0: the
+    oracle's own rule).  Used only to perturb library values when pinning
+    the deviation bound."""
+    lib().oracle_set_extra_widening(int(k))
 
 
 def tree_sum(lo, hi, f32: bool = False):
@@ -205,6 +214,21 @@ class Oracle:
         lib().oracle_eval_box(self.h, _dp(lo), _dp(hi), int(f32), int(blk), _dp(F), _dp(Fm),
                               _dp(G), ctypes.byref(mono))
         return F, Fm, G.reshape(self.B, 2), int(mono.value)
+
+    def eval_box_dev(self, lo, hi, blk: int = -1, f32: bool = False):
+        """eval_box's F, Fmid and G with their deviation bounds: (F, dF,
+        Fmid, dFmid, G[width], dG[width]).  An implementation running the
+        same operations whose exp / sin / cos endpoints are within a few ulps
+        of the oracle's gives endpoints within these bounds (0 for
+        objectives without transcendentals)."""
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        F, dF, Fm, dFm = np.zeros(2), np.zeros(1), np.zeros(2), np.zeros(1)
+        G = np.zeros(2 * self.B)
+        dG = np.zeros(self.B)
+        lib().oracle_eval_box_dev(self.h, _dp(lo), _dp(hi), int(f32), int(blk), _dp(F), _dp(dF), _dp(Fm),
+                                  _dp(dFm), _dp(G), _dp(dG))
+        return F, float(dF[0]), Fm, float(dFm[0]), G.reshape(self.B, 2), dG
 
     def solve(self, tol_f: float | None = None, tol_x: float = 0.0, split_m: int = 2,
               split_d: int = 1, fp32: bool = False, max_gen: int = 10**9,

@@ -228,7 +228,12 @@ static iv iv_scale(iv x, double c, int p) {
  * documents at most 1 ulp of error for exp, sin and cos in both precisions,
  * and one more ulp is added as margin.  The paper is silent on how it rounds
  * transcendental functions (section 2.1 only defines outward rounding). */
-#define K_WIDEN 2
+#define K_WIDEN (2 + g_extra_widen)
+
+/* Extra widening of every transcendental endpoint, in ulps (0 in every use
+ * but one test, which perturbs the library values this way to check the
+ * deviation bound further down against an actual deviation). */
+static int g_extra_widen = 0;
 
 static double PI_LO, PI_HI, E_LO, E_HI;      /* adjacent doubles around pi, e */
 
@@ -845,6 +850,414 @@ static uint64_t order_key(double x) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Deviation bound (the tolerance of transcendental parity)                  */
+/* ------------------------------------------------------------------------ */
+/* Two implementations that run the same directed operations in the same
+ * order produce the same bits; they can differ only where a library
+ * transcendental (exp, sin, cos) is called, because each library is only
+ * within its documented error of the true value and each side widens by its
+ * own count of ulps.  Beside every interval the oracle computes, the
+ * functions below carry a number d >= 0 such that an implementation whose
+ * transcendental endpoints lie within DEV_KT ulps of the oracle's produces
+ * endpoints (both ends) within d of the oracle's.  Rules (first order plus
+ * the second-order terms, all rounded upward; mag = larger endpoint
+ * magnitude):
+ *   constants, coordinates, coefficients     d = 0
+ *   a + b, a - b                             da + db
+ *   a * b (min / max of products)            mag(b) da + mag(a) db + da db
+ *   1 / b                                    db / (mig(b) (mig(b) - db)); infinite when db >= mig(b)
+ *   a^2                                      (2 mag(a) + da) da
+ *   sqrt(a)                                  min(sqrt(da), da / (2 sqrt(lo(a) - da)))
+ *   exp(a)                                   KT ulp(mag) + exp(hi(a) + da) da
+ *   sin(a), cos(a)                           KT ulp(mag) + da + (2 ulp(mag a) + 2 da)^2
+ *                                            (the last term covers an extremum that one side
+ *                                            includes and the other does not); 2 when the width
+ *                                            test may decide differently
+ *   unit step                                1 when a lies within da of the jump, else 0
+ * and every rounded result whose operands deviate gains one ulp (directed
+ * rounding of two different exact values differs by at most their distance
+ * plus one ulp).  Reading of the "width within 4 ulp n" requirement for
+ * transcendental families: the GPU result must lie within d of the oracle's;
+ * for objectives without transcendentals d = 0 (bit-exact parity). */
+#define DEV_KT 8.0
+
+static double up_add(double a, double b) { return d_add(a, b, 1); }
+static double umul(double a, double b) { return (a == 0.0 || b == 0.0) ? 0.0 : d_mul(a, b, 1); }
+static double magv(iv x) {
+    double m = fmax(fabs(x.lo), fabs(x.hi));
+    return isnan(x.lo) || isnan(x.hi) ? INFINITY : m;
+}
+/* Twice the spacing of precision p at magnitude m: one ulp of any value up
+ * to just past the next power of two. */
+static double ulp_at(double m, int p) {
+    m = fabs(m);
+    if (!(m < INFINITY)) return INFINITY;
+    if (p) {
+        float f = (float)m;
+        if ((double)f < m) f = nextafterf(f, INFINITY);
+        return 2.0 * ((double)nextafterf(f, INFINITY) - (double)f);
+    }
+    return 2.0 * (nextafter(m, INFINITY) - m);
+}
+static double dflip(double d, iv r, int p) { return d > 0.0 ? up_add(d, ulp_at(magv(r), p)) : 0.0; }
+
+static double dev_mul(iv a, double da, iv b, double db) {
+    return up_add(up_add(umul(magv(b), da), umul(magv(a), db)), umul(da, db));
+}
+static double mig(iv y) { return y.lo > 0.0 ? y.lo : (y.hi < 0.0 ? -y.hi : 0.0); }
+static double dev_recip(iv y, double dy, iv r, int p) {
+    if (dy == 0.0) return 0.0;
+    double m = mig(y);
+    if (!(m > dy)) return INFINITY;
+    return dflip(d_div(dy, d_mul(m, d_sub(m, dy, 0), 0), 1), r, p);
+}
+static double dev_sqrt(iv a, double da, iv r, int p) {
+    if (da == 0.0) return 0.0;
+    double d = d_sqrt(da, 1);
+    double m = d_sub(a.lo, da, 0);
+    if (m > 0.0) d = fmin(d, d_div(da, d_mul(2.0, d_sqrt(m, 0), 0), 1));
+    return dflip(d, r, p);
+}
+static double dev_exp(iv a, double da, iv r, int p) {
+    double d = DEV_KT * ulp_at(magv(r), p);
+    if (da > 0.0) {
+        double e = nextafter(nextafter(exp(up_add(a.hi, da)), INFINITY), INFINITY);
+        d = up_add(d, dflip(umul(e, da), r, p));
+    }
+    return d;
+}
+static double dev_trig(iv a, double da, iv r, int p) {
+    double d = DEV_KT * ulp_at(magv(r), p);
+    if (da == 0.0) return d;
+    double big = p ? 1048576.0 : 1099511627776.0;
+    double w = up_add(up_add(d_sub(a.hi, a.lo, 1), da), da);
+    if (!(w < 2.0 * PI_LO) || !(up_add(magv(a), da) <= big)) return 2.0;
+    double e = up_add(ulp_at(magv(a), p), up_add(da, da));
+    return dflip(up_add(up_add(d, da), umul(e, e)), r, p);
+}
+static double scale_mag(double c, int p) {
+    return p ? fmax(fabs(R_in(c, 1, 0)), fabs(R_in(c, 1, 1))) : fabs(c);
+}
+
+/* Deviation of node v's value r from its operands' values and deviations. */
+static double node_dev(const oprob* P, int v, int p, const iv* vals, const double* devs, iv r) {
+    const onode* q = &P->nd[v];
+    const int k = n_operands(q->op);
+    iv a = mk(0.0, 0.0), b = mk(0.0, 0.0);
+    double da = 0.0, db = 0.0;
+    if (k >= 1) { a = vals[q->a]; da = devs[q->a]; }
+    if (k >= 2) { b = vals[q->b]; db = devs[q->b]; }
+    switch (q->op) {
+    case O_ADD: case O_SUB: return dflip(up_add(da, db), r, p);
+    case O_MUL: return dflip(dev_mul(a, da, b, db), r, p);
+    case O_DIV: {
+        iv rb = iv_recip(b, p);
+        return dflip(dev_mul(a, da, rb, dev_recip(b, db, rb, p)), r, p);
+    }
+    case O_NEG: return da;
+    case O_SQR: return dflip(umul(up_add(umul(2.0, magv(a)), da), da), r, p);
+    case O_SQRT: return dev_sqrt(a, da, r, p);
+    case O_EXP: return dev_exp(a, da, r, p);
+    case O_SIN: case O_COS: return dev_trig(a, da, r, p);
+    case O_SCALE: return dflip(umul(scale_mag(q->v, p), da), r, p);
+    case O_STEP: return (da > 0.0 && (fabs(a.lo) <= da || fabs(a.hi) <= da)) ? 1.0 : 0.0;
+    default: return 0.0;
+    }
+}
+
+/* The reduction trees with deviations carried beside the values. */
+static void tree_dev(iv* a, double* d, int m, int p, int prod) {
+    for (int s = 1; s < m; s *= 2)
+        for (int i = 0; i + s < m; i += 2 * s) {
+            iv r = prod ? iv_mul(a[i], a[i + s], p) : iv_add(a[i], a[i + s], p);
+            d[i] = dflip(prod ? dev_mul(a[i], d[i], a[i + s], d[i + s]) : up_add(d[i], d[i + s]), r, p);
+            a[i] = r;
+        }
+}
+
+/* tree_prod_adjoint with deviations: adj / dadj receive each item's adjoint. */
+static void tree_prod_adjoint_dev(const iv* a, const double* da, int m, iv seed, double dseed, iv* adj,
+                                  double* dadj, int p) {
+    if (m == 0) return;
+    int L = 0;
+    while ((1 << L) < m) L++;
+    const size_t sz = (size_t)m * (L + 1);
+    iv* V = (iv*)malloc(sizeof(iv) * sz);
+    iv* A = (iv*)malloc(sizeof(iv) * sz);
+    double* DV = (double*)malloc(sizeof(double) * sz);
+    double* DA = (double*)malloc(sizeof(double) * sz);
+    memcpy(V, a, sizeof(iv) * (size_t)m);
+    memcpy(DV, da, sizeof(double) * (size_t)m);
+    for (int l = 0; l < L; l++) {
+        const int s = 1 << l;
+        const size_t c = (size_t)l * m, nx = (size_t)(l + 1) * m;
+        memcpy(V + nx, V + c, sizeof(iv) * (size_t)m);
+        memcpy(DV + nx, DV + c, sizeof(double) * (size_t)m);
+        for (int i = 0; i + s < m; i += 2 * s) {
+            V[nx + i] = iv_mul(V[c + i], V[c + i + s], p);
+            DV[nx + i] = dflip(dev_mul(V[c + i], DV[c + i], V[c + i + s], DV[c + i + s]), V[nx + i], p);
+        }
+    }
+    A[(size_t)L * m] = seed;
+    DA[(size_t)L * m] = dseed;
+    for (int l = L - 1; l >= 0; l--) {
+        const int s = 1 << l;
+        const size_t c = (size_t)l * m, up = (size_t)(l + 1) * m;
+        for (int i = 0; i < m; i += 2 * s) {
+            if (i + s < m) {
+                A[c + i] = iv_mul(A[up + i], V[c + i + s], p);
+                DA[c + i] = dflip(dev_mul(A[up + i], DA[up + i], V[c + i + s], DV[c + i + s]), A[c + i], p);
+                A[c + i + s] = iv_mul(A[up + i], V[c + i], p);
+                DA[c + i + s] = dflip(dev_mul(A[up + i], DA[up + i], V[c + i], DV[c + i]), A[c + i + s], p);
+            } else {
+                A[c + i] = A[up + i];
+                DA[c + i] = DA[up + i];
+            }
+        }
+    }
+    memcpy(adj, A, sizeof(iv) * (size_t)m);
+    memcpy(dadj, DA, sizeof(double) * (size_t)m);
+    free(V); free(A); free(DV); free(DA);
+}
+
+/* Scratch of one deviation evaluation (values beside their deviations). */
+typedef struct {
+    iv *val, *adj, *tval, *tadj, *terms, *grp, *gsum, *gadj, *tseed, *dacc, *G;
+    double *dval, *dadj, *dtval, *dtadj, *dterms, *dgrp, *dgsum, *dgadj, *dtseed, *ddacc, *dG;
+    int* gstart;
+    char* touched;
+} dscr;
+
+static void dscr_alloc(const oprob* P, dscr* S) {
+    const size_t nn = (size_t)P->nn, mt = (size_t)P->max_terms, B = (size_t)P->B;
+    S->val = (iv*)calloc(nn, sizeof(iv)); S->dval = (double*)calloc(nn, sizeof(double));
+    S->adj = (iv*)calloc(nn, sizeof(iv)); S->dadj = (double*)calloc(nn, sizeof(double));
+    S->tval = (iv*)calloc(nn, sizeof(iv)); S->dtval = (double*)calloc(nn, sizeof(double));
+    S->tadj = (iv*)calloc(nn, sizeof(iv)); S->dtadj = (double*)calloc(nn, sizeof(double));
+    S->terms = (iv*)calloc(mt, sizeof(iv)); S->dterms = (double*)calloc(mt, sizeof(double));
+    S->grp = (iv*)calloc(mt, sizeof(iv)); S->dgrp = (double*)calloc(mt, sizeof(double));
+    S->gsum = (iv*)calloc(mt, sizeof(iv)); S->dgsum = (double*)calloc(mt, sizeof(double));
+    S->gadj = (iv*)calloc(mt, sizeof(iv)); S->dgadj = (double*)calloc(mt, sizeof(double));
+    S->tseed = (iv*)calloc(mt, sizeof(iv)); S->dtseed = (double*)calloc(mt, sizeof(double));
+    S->dacc = (iv*)calloc(B, sizeof(iv)); S->ddacc = (double*)calloc(B, sizeof(double));
+    S->G = (iv*)calloc(B, sizeof(iv)); S->dG = (double*)calloc(B, sizeof(double));
+    S->gstart = (int*)calloc(mt + 1, sizeof(int));
+    S->touched = (char*)calloc(B, 1);
+}
+
+static void dscr_free(dscr* S) {
+    free(S->val); free(S->dval); free(S->adj); free(S->dadj); free(S->tval); free(S->dtval);
+    free(S->tadj); free(S->dtadj); free(S->terms); free(S->dterms); free(S->grp); free(S->dgrp);
+    free(S->gsum); free(S->dgsum); free(S->gadj); free(S->dgadj); free(S->tseed); free(S->dtseed);
+    free(S->dacc); free(S->ddacc); free(S->G); free(S->dG); free(S->gstart); free(S->touched);
+}
+
+/* Template k at index i: values in S->tval, deviations in S->dtval. */
+static void dev_term(const oprob* P, int k, int i, obox X, int p, dscr* S) {
+    for (int t = 0; t < P->tmpl_count[k]; t++) {
+        int v = P->tmpl_nodes[k][t];
+        S->tval[v] = node_value(P, v, i, X, p, S->tval);
+        S->dtval[v] = node_dev(P, v, p, S->tval, S->dtval, S->tval[v]);
+    }
+}
+
+/* Reduction k with deviations (isum_value's groups and trees); leaves the
+ * term values in S->terms and the group values in S->gsum. */
+static iv dev_reduction(const oprob* P, int k, obox X, int p, dscr* S, double* d) {
+    const onode* s = &P->nd[P->isum_node[k]];
+    const int prod = s->op == O_IPROD;
+    int cnt = isum_count(s);
+    if (cnt == 0) { *d = 0.0; return prod ? mk(1.0, 1.0) : mk(0.0, 0.0); }
+    for (int q = 0; q < cnt; q++) {
+        dev_term(P, k, s->b + q * s->d, X, p, S);
+        S->terms[q] = S->tval[s->a];
+        S->dterms[q] = S->dtval[s->a];
+    }
+    int ng = isum_groups(P, k, S->gstart);
+    for (int g = 0; g < ng; g++) {
+        int a = S->gstart[g], e = S->gstart[g + 1];
+        for (int r = a; r < e; r++) { S->grp[r - a] = S->terms[r]; S->dgrp[r - a] = S->dterms[r]; }
+        tree_dev(S->grp, S->dgrp, e - a, p, prod);
+        S->gsum[g] = S->grp[0];
+        S->dgsum[g] = S->dgrp[0];
+    }
+    for (int g = 0; g < ng; g++) { S->grp[g] = S->gsum[g]; S->dgrp[g] = S->dgsum[g]; }
+    tree_dev(S->grp, S->dgrp, ng, p, prod);
+    *d = S->dgrp[0];
+    return S->grp[0];
+}
+
+/* Forward pass of the outer expression with deviations. */
+static iv dev_outer(const oprob* P, obox X, int p, dscr* S, double* d) {
+    int k = 0;
+    for (int v = 0; v < P->nn; v++) {
+        if (!P->outer[v]) continue;
+        if (is_red(P->nd[v].op)) {
+            while (P->isum_node[k] != v) k++;
+            S->val[v] = dev_reduction(P, k, X, p, S, &S->dval[v]);
+        } else {
+            S->val[v] = node_value(P, v, -1, X, p, S->val);
+            S->dval[v] = node_dev(P, v, p, S->val, S->dval, S->val[v]);
+        }
+    }
+    *d = S->dval[P->root];
+    return S->val[P->root];
+}
+
+/* adj[t] += x with deviations. */
+static void acc_dev(iv* adj, double* dadj, int t, iv x, double dx, int p) {
+    iv r = iv_add(adj[t], x, p);
+    dadj[t] = dflip(up_add(dadj[t], dx), r, p);
+    adj[t] = r;
+}
+
+/* push_adjoint with deviations. */
+static void push_adjoint_dev(const oprob* P, int v, int p, const iv* vals, const double* dv, iv* adj,
+                             double* dadj) {
+    const onode* q = &P->nd[v];
+    const iv g = adj[v];
+    const double dg = dadj[v];
+    iv x;
+    switch (q->op) {
+    case O_ADD:
+        acc_dev(adj, dadj, q->a, g, dg, p);
+        acc_dev(adj, dadj, q->b, g, dg, p);
+        break;
+    case O_SUB:
+        acc_dev(adj, dadj, q->a, g, dg, p);
+        acc_dev(adj, dadj, q->b, iv_neg(g), dg, p);
+        break;
+    case O_MUL:
+        x = iv_mul(g, vals[q->b], p);
+        acc_dev(adj, dadj, q->a, x, dflip(dev_mul(g, dg, vals[q->b], dv[q->b]), x, p), p);
+        x = iv_mul(g, vals[q->a], p);
+        acc_dev(adj, dadj, q->b, x, dflip(dev_mul(g, dg, vals[q->a], dv[q->a]), x, p), p);
+        break;
+    case O_DIV: {
+        iv rb = iv_recip(vals[q->b], p);
+        double drb = dev_recip(vals[q->b], dv[q->b], rb, p);
+        x = iv_mul(g, rb, p);
+        acc_dev(adj, dadj, q->a, x, dflip(dev_mul(g, dg, rb, drb), x, p), p);
+        iv y = iv_mul(vals[v], rb, p);
+        double dy = dflip(dev_mul(vals[v], dv[v], rb, drb), y, p);
+        x = iv_mul(g, iv_neg(y), p);
+        acc_dev(adj, dadj, q->b, x, dflip(dev_mul(g, dg, y, dy), x, p), p);
+        break;
+    }
+    case O_NEG:
+        acc_dev(adj, dadj, q->a, iv_neg(g), dg, p);
+        break;
+    case O_SQR: {
+        iv s2 = iv_scale(vals[q->a], 2.0, p);
+        double ds2 = dflip(umul(2.0, dv[q->a]), s2, p);
+        x = iv_mul(g, s2, p);
+        acc_dev(adj, dadj, q->a, x, dflip(dev_mul(g, dg, s2, ds2), x, p), p);
+        break;
+    }
+    case O_SQRT: {
+        iv rv = iv_recip(vals[v], p);
+        double drv = dev_recip(vals[v], dv[v], rv, p);
+        iv h = iv_scale(rv, 0.5, p);
+        double dh = dflip(umul(0.5, drv), h, p);
+        x = iv_mul(g, h, p);
+        acc_dev(adj, dadj, q->a, x, dflip(dev_mul(g, dg, h, dh), x, p), p);
+        break;
+    }
+    case O_EXP:
+        x = iv_mul(g, vals[v], p);
+        acc_dev(adj, dadj, q->a, x, dflip(dev_mul(g, dg, vals[v], dv[v]), x, p), p);
+        break;
+    case O_SIN: case O_COS: {
+        iv c = iv_trig(vals[q->a], p, q->op == O_SIN);
+        double dc = dev_trig(vals[q->a], dv[q->a], c, p);
+        if (q->op == O_COS) c = iv_neg(c);
+        x = iv_mul(g, c, p);
+        acc_dev(adj, dadj, q->a, x, dflip(dev_mul(g, dg, c, dc), x, p), p);
+        break;
+    }
+    case O_SCALE:
+        x = iv_scale(g, q->v, p);
+        acc_dev(adj, dadj, q->a, x, dflip(umul(scale_mag(q->v, p), dg), x, p), p);
+        break;
+    case O_STEP: {
+        const iv a = vals[q->a];
+        const double da = dv[q->a];
+        const int unsure = (da > 0.0 && (fabs(a.lo) <= da || fabs(a.hi) <= da)) ||
+                           (dg > 0.0 && fabs(g.lo) <= dg && fabs(g.hi) <= dg);
+        if (step_jump(a) && !(g.lo == 0.0 && g.hi == 0.0)) acc_dev(adj, dadj, q->a, entire(), 0.0, p);
+        if (unsure) dadj[q->a] = INFINITY;
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+/* block_partials with deviations: S->G[0..width) and S->dG.  Needs
+ * dev_outer(X) to have run on S. */
+static void dev_block_partials(const oprob* P, obox X, int p, int blk, dscr* S, int* width) {
+    int c0 = blk * P->B, c1 = c0 + P->B;
+    if (c1 > P->n) c1 = P->n;
+    *width = c1 - c0;
+    for (int v = 0; v < P->nn; v++) { S->adj[v] = mk(0.0, 0.0); S->dadj[v] = 0.0; }
+    S->adj[P->root] = mk(1.0, 1.0);
+    for (int v = P->nn - 1; v >= 0; v--) {
+        if (!P->outer[v] || is_red(P->nd[v].op)) continue;
+        push_adjoint_dev(P, v, p, S->val, S->dval, S->adj, S->dadj);
+    }
+    for (int j = c0; j < c1; j++) { S->G[j - c0] = mk(0.0, 0.0); S->dG[j - c0] = 0.0; }
+    for (int v = 0; v < P->nn; v++)
+        if (P->outer[v] && P->nd[v].op == O_VAR && P->nd[v].a >= c0 && P->nd[v].a < c1)
+            acc_dev(S->G, S->dG, P->nd[v].a - c0, S->adj[v], S->dadj[v], p);
+    for (int k = 0; k < P->n_isum; k++) {
+        if (!P->has_var[k]) continue;
+        const onode* s = &P->nd[P->isum_node[k]];
+        int cnt = isum_count(s);
+        const int prod = s->op == O_IPROD;
+        if (prod) {
+            double dd;
+            dev_reduction(P, k, X, p, S, &dd);
+            int ng = isum_groups(P, k, S->gstart);
+            tree_prod_adjoint_dev(S->gsum, S->dgsum, ng, mk(1.0, 1.0), 0.0, S->gadj, S->dgadj, p);
+            for (int g = 0; g < ng; g++)
+                tree_prod_adjoint_dev(S->terms + S->gstart[g], S->dterms + S->gstart[g],
+                                      S->gstart[g + 1] - S->gstart[g], S->gadj[g], S->dgadj[g],
+                                      S->tseed + S->gstart[g], S->dtseed + S->gstart[g], p);
+        }
+        for (int j = c0; j < c1; j++) { S->dacc[j - c0] = mk(0.0, 0.0); S->ddacc[j - c0] = 0.0; S->touched[j - c0] = 0; }
+        for (int q = 0; q < cnt; q++) {
+            int i = s->b + q * s->d;
+            if (i + P->off_max[k] < c0 || i + P->off_min[k] >= c1) continue;
+            dev_term(P, k, i, X, p, S);
+            int troot = s->a;
+            for (int t = 0; t < P->tmpl_count[k]; t++) {
+                S->tadj[P->tmpl_nodes[k][t]] = mk(0.0, 0.0);
+                S->dtadj[P->tmpl_nodes[k][t]] = 0.0;
+            }
+            S->tadj[troot] = prod ? S->tseed[q] : mk(1.0, 1.0);
+            S->dtadj[troot] = prod ? S->dtseed[q] : 0.0;
+            for (int t = P->tmpl_count[k] - 1; t >= 0; t--)
+                push_adjoint_dev(P, P->tmpl_nodes[k][t], p, S->tval, S->dtval, S->tadj, S->dtadj);
+            for (int t = 0; t < P->tmpl_count[k]; t++) {
+                const int leafv = P->tmpl_nodes[k][t];
+                if (P->nd[leafv].op != O_IDX_VAR) continue;
+                int j = i + P->nd[leafv].b;
+                if (j < c0 || j >= c1) continue;
+                acc_dev(S->dacc, S->ddacc, j - c0, S->tadj[leafv], S->dtadj[leafv], p);
+                S->touched[j - c0] = 1;
+            }
+        }
+        const int sv = P->isum_node[k];
+        for (int j = c0; j < c1; j++)
+            if (S->touched[j - c0]) {
+                iv x = iv_mul(S->adj[sv], S->dacc[j - c0], p);
+                double dx = dflip(dev_mul(S->adj[sv], S->dadj[sv], S->dacc[j - c0], S->ddacc[j - c0]), x, p);
+                acc_dev(S->G, S->dG, j - c0, x, dx, p);
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exported: problem handle, single-box evaluation, reduction-tree hook      */
 /* ------------------------------------------------------------------------ */
 void* oracle_create(const void* nodes, int nn, int root, const double* const* tables,
@@ -883,6 +1296,41 @@ int oracle_eval_box(void* h, const double* lo, const double* hi, int p, int blk,
     free(m);
     return 0;
 }
+
+/* oracle_eval_box with the deviation bound of each result: F and its bound
+ * dF (1 double, both ends), Fmid and dFmid, the partials of block blk (2 B
+ * doubles) and their bounds dG (B doubles).  The values equal
+ * oracle_eval_box's. */
+int oracle_eval_box_dev(void* h, const double* lo, const double* hi, int p, int blk, double* F, double* dF,
+                        double* Fmid, double* dFmid, double* G, double* dG) {
+    oprob* P = (oprob*)h;
+    dscr S;
+    dscr_alloc(P, &S);
+    obox X = {lo, hi};
+    iv f = dev_outer(P, X, p, &S, dF);
+    F[0] = f.lo; F[1] = f.hi;
+    if (blk >= 0) {
+        int width = 0;
+        dev_block_partials(P, X, p, blk, &S, &width);
+        for (int t = 0; t < width; t++) {
+            G[2 * t] = S.G[t].lo; G[2 * t + 1] = S.G[t].hi;
+            dG[t] = S.dG[t];
+        }
+    }
+    double* m = (double*)malloc(sizeof(double) * P->n);
+    for (int j = 0; j < P->n; j++) m[j] = midpoint(lo[j], hi[j]);
+    obox M = {m, m};
+    iv fm = dev_outer(P, M, 0, &S, dFmid);
+    Fmid[0] = fm.lo; Fmid[1] = fm.hi;
+    free(m);
+    dscr_free(&S);
+    return 0;
+}
+
+/* Test hook: widen every transcendental endpoint by k more ulps (k = 0
+ * restores the oracle's rule).  Not thread-safe; used only to perturb the
+ * library values when checking the deviation bound. */
+void oracle_set_extra_widening(int k) { g_extra_widen = k < 0 ? 0 : k; }
 
 /* Single interval operation, for pinning the arithmetic against an
  * independent multiprecision library.  op uses the node codes; c is the
