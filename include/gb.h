@@ -166,13 +166,14 @@ typedef struct gb_result {
     int64_t mid_evals;        /* FP64 midpoint samples */
     double solve_ms;          /* wall time of the solve on the host clock */
     double device_ms;         /* CUDA-event time from the first to the last launch */
-    double eval64_ms;         /* CUDA-event time inside the FP64 evaluation kernels */
-    double eval32_ms;         /* CUDA-event time inside the FP32 evaluation kernels */
+    double eval64_ms;         /* CUDA-event time of the child evaluation: per-parent term tables, FP32 pass
+                                 and FP64 kernels (with gens_per_sync <= 1) */
+    double eval32_ms;         /* CUDA-event time inside the FP32 evaluation kernels (part of eval64_ms) */
     int64_t eval64_launches;
     int64_t eval32_launches;
     int64_t kernel_launches;  /* kernels the library launched for this solve */
-    int64_t ops64;            /* directed-rounding FP64 operations executed by the FP64 evaluation kernels */
-    int64_t ops32;            /* directed-rounding FP32 operations executed by the FP32 evaluation kernels */
+    int64_t ops64;            /* directed-rounding FP64 operations executed by the evaluation (tables, children) */
+    int64_t ops32;            /* directed-rounding FP32 operations executed by the evaluation (tables, children) */
     double queue_ms;          /* serving: submit -> admission (host clock); 0 for gb_solve */
     double latency_ms;        /* serving: submit -> result ready (host clock); 0 for gb_solve */
     int32_t pool_mode;        /* box storage used: 1 dense rows, 2 block records */

@@ -1456,6 +1456,8 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     gb_launch_count++;
     k_prep<<<grid_for(G.K * (long long)sp.dmax, 128), 128, 0, s>>>(P, pool, par, sp, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the evaluation window (ev[0] .. ev[1]): per-parent tables and every child kernel
+    if (ev && part == 0) cudaEventRecord(ev[0], s);
     if (tabs) {
         gb_launch_count++;
         if ((e = gb_launch_ptab(P, pool, par, *tabs, G.K, sp, st, s)) != cudaSuccess) return e;
@@ -1469,7 +1471,7 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     const bool fused = G.fp32 && tabs && tabs->warp;
     if (fused) {
         // FP32 prefilter and FP64 evaluation in one warp-per-child kernel
-        if (ev) cudaEventRecord(ev[2], s), cudaEventRecord(ev[3], s), cudaEventRecord(ev[0], s);
+        if (ev) cudaEventRecord(ev[2], s), cudaEventRecord(ev[3], s);
         gb_launch_count++;
         if ((e = gb_launch_eval3264_tabw(P, pool, par, *tabs, ch, Cmax, sp, st, s)) != cudaSuccess) return e;
         if (ev) cudaEventRecord(ev[1], s);
@@ -1490,7 +1492,6 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
             k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 1, 0, G, st);
             k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 0, st, sc.tile_off, ch.list32);
         }
-        if (ev) cudaEventRecord(ev[0], s);
         if (tabs) {
             gb_launch_count++;
             if ((e = gb_launch_eval64_tab(P, pool, par, *tabs, ch, Cmax, sp, G.fp32 != 0, st, s)) != cudaSuccess)

@@ -58,7 +58,7 @@ constexpr int PTAB_T = 64;
 __device__ __forceinline__ int ptab_parts(const GbPool& pool) { return pool.fp32 ? 4 : 3; }
 
 __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp,
-                                                 int row_blocks, const GbState* st) {
+                                                 int row_blocks, GbState* st) {
     if (st->halt) return;
     const long long p = blockIdx.y;
     if (p >= st->parents) return;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             else T.nf32[nb + g] = c32[S.group0 + g];
         }
         __syncthreads();
-        int off = 0;
+        int off = 0, tops = 0;
         for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
             const int mN = (mL + 1) / 2;
             for (int q = threadIdx.x; q < mN; q += blockDim.x) {
@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
                     if (2 * q + 1 < mL) {
                         float2 y = T.nf32[a + 1];
                         v = iadd(v, iv32{y.x, y.y});
+                        tops += 2;
                     }
                     T.nf32[c] = make_float2(v.lo, v.hi);
                 } else {
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
                     if (2 * q + 1 < mL) {
                         double2 y = arr[a + 1];
                         v = iadd(v, iv64{y.x, y.y});
+                        tops += 2;
                     }
                     arr[c] = make_double2(v.lo, v.hi);
                 }
@@ -109,12 +111,13 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             __syncthreads();
             off += mL;
         }
+        if (tops) atomicAdd(kind == 2 ? &st->ops32 : &st->ops64, (unsigned long long)tops);
         return;
     }
     const GbSplitPos SP = P.sps[spi];
     const size_t o = (size_t)p * sp.dmax * (sp.m + 1);
     const int parts = ptab_parts(pool);
-    int ops = 0;
+    int ops = 0, ops32 = 0;
     for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < SP.tab_entries * parts;
          item += row_blocks * blockDim.x) {
         const int row = item / parts, part = item - row * parts;
@@ -168,11 +171,11 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             X32.mshift = sp.mshift;
             X32.mstride = sp.m + 1;
             X32.r = r;
-            const iv32 f = term_fwd<float>(P, S, i, X32, R32, ops);
+            const iv32 f = term_fwd<float>(P, S, i, X32, R32, ops32);
             T.tv32[orow] = make_float2(f.lo, f.hi);
             for (int t = 0; t < S.nins; t++) RA32[t] = iv32{0.f, 0.f};
             RA32[S.nins - 1] = iv32{1.f, 1.f};
-            reverse_sweep<float>(P.tins + S.ins0, S.nins, R32, RA32, ops);
+            reverse_sweep<float>(P.tins + S.ins0, S.nins, R32, RA32, ops32);
             int leaf = 0;
             for (int t = 0; t < S.nins; t++) {
                 if (P.tins[S.ins0 + t].op != D_IVAR) continue;
@@ -181,6 +184,8 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             }
         }
     }
+    if (ops) atomicAdd(&st->ops64, (unsigned long long)ops);
+    if (ops32) atomicAdd(&st->ops32, (unsigned long long)ops32);
 }
 
 // ---------------------------------------------------------------------------
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
 // combination of its digit bits, the in-place pairwise sum of its terms (F,
 // midpoint, FP32).
 __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents par, GbTabs T,
-                                                const GbState* st) {
+                                                GbState* st) {
     if (st->halt) return;
     const long long p = blockIdx.y;
     if (p >= st->parents) return;
@@ -205,6 +210,7 @@ __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents
     const double2* tl = T.tl64 + (size_t)p * T.max_rows * T.max_leaves;
     const float2* tl32 = pool.fp32 ? T.tl32 + (size_t)p * T.max_rows * T.max_leaves : nullptr;
     const int nd_items = nent << GB_TAB_DBITS;
+    int ops = 0, ops32 = 0;
     for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nd_items + (SP.nseg << GB_TAB_SBITS);
          item += gridDim.x * blockDim.x) {
         if (item >= nd_items) {   // segment table entry
@@ -229,6 +235,8 @@ __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents
                     t32.push(iv32{f.x, f.y});
                 }
             }
+            ops += 4 * ((1 << G.level) - 1);   // F and midpoint trees
+            if (tl32) ops32 += 2 * ((1 << G.level) - 1);
             const size_t o = (size_t)p * T.max_srows + G.base + c;
             const iv64 vf = tf.result(), vm = tm.result();
             T.ts64[o] = make_double2(vf.lo, vf.hi);
@@ -256,10 +264,16 @@ __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents
                 D32 = q > rg.x ? iadd(D32, iv32{v32.x, v32.y}) : iv32{v32.x, v32.y};
             }
         }
+        if (rg.y - rg.x > 1) {
+            ops += 2 * (rg.y - rg.x - 1);
+            if (tl32) ops32 += 2 * (rg.y - rg.x - 1);
+        }
         const size_t o = (size_t)p * T.max_drows + J.base + c;
         T.td64[o] = make_double2(D.lo, D.hi);
         if (tl32) T.td32[o] = make_float2(D32.lo, D32.hi);
     }
+    if (ops) atomicAdd(&st->ops64, (unsigned long long)ops);
+    if (ops32) atomicAdd(&st->ops32, (unsigned long long)ops32);
 }
 
 // ---------------------------------------------------------------------------
