@@ -131,8 +131,9 @@ def test_malformed_snapshots_are_refused():
 
 
 class _ThreadDist:
-    """broadcast_object_list / all_gather_object between threads (one per
-    rank, all on this GPU: the ranks share nothing but these host calls)."""
+    """broadcast_object_list / all_gather_object / all_reduce (MIN) /
+    all_gather between threads (one per rank, all on this GPU: the ranks
+    share nothing but these host calls)."""
 
     def __init__(self, world):
         import threading
@@ -150,6 +151,25 @@ class _ThreadDist:
         self.slots[self.local.rank] = obj
         self.bar.wait()
         out[:] = list(self.slots)
+        self.bar.wait()
+
+    class ReduceOp:
+        MIN = "min"
+
+    def all_reduce(self, t, op=None):
+        self.slots[self.local.rank] = t.clone()
+        self.bar.wait()
+        r = self.slots[0].clone()
+        for x in self.slots[1:]:
+            r = torch.minimum(r, x)
+        self.bar.wait()
+        t.copy_(r)
+
+    def all_gather(self, out, t):
+        self.slots[self.local.rank] = t.clone()
+        self.bar.wait()
+        for o, x in zip(out, self.slots):
+            o.copy_(x)
         self.bar.wait()
 
 
