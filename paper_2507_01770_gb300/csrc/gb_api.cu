@@ -515,6 +515,9 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     if ((e = alloc(&p->sc.tile_cnt, (size_t)3 * p->sc.max_tiles, A)) ||
         (e = alloc(&p->sc.tile_off, (size_t)3 * p->sc.max_tiles, A)) ||
         (e = alloc(&p->sc.hist, (size_t)65536, A)) || (e = alloc(&p->out_list, (size_t)cap, A)) ||
+        (e = alloc(&p->sc.tile_flag, (size_t)p->sc.max_tiles, A)) ||
+        (e = alloc(&p->sc.stat_key, (size_t)GB_STAT_BLOCKS, A)) ||
+        (e = alloc(&p->sc.stat_pos, (size_t)GB_STAT_BLOCKS, A)) ||
         (e = alloc(&p->st, 1, A)))
         return bad(e, "allocate scan buffers");
     if ((e = cudaMemsetAsync(p->sc.hist, 0, 65536 * sizeof(unsigned), p->stream))) return bad(e, "cudaMemset");
@@ -563,6 +566,8 @@ static gb_status solve_begin_from(gb_problem* p, const gb_snapshot* snap) {
     init.cap = p->cap;
     GB_CU(cudaEventRecord(p->ev[0], s));
     GB_CU(cudaMemcpyAsync(p->st, &init, sizeof(GbState), cudaMemcpyHostToDevice, s));
+    // the pool partitions' tile flags carry an epoch that restarts with every solve
+    GB_CU(cudaMemsetAsync(p->sc.tile_flag, 0, sizeof(unsigned long long) * (size_t)p->sc.max_tiles, s));
     if (p->pool.recs && p->marks_used) {   // collection numbers restart at 1 in every solve
         GB_CU(cudaMemsetAsync(p->pool.rmark, 0, sizeof(unsigned) * (size_t)p->pool.R, s));
         p->marks_used = false;
@@ -599,7 +604,7 @@ static gb_status solve_begin_from(gb_problem* p, const gb_snapshot* snap) {
         if (d_cyc) cudaFreeAsync(d_cyc, s);
         if (e != cudaSuccess) return cuda_fail(e, "resume from a snapshot");
     }
-    GB_CU(gb_launch_stats(p->E[0], p->G, 1, p->st, s));
+    GB_CU(gb_launch_stats(p->E[0], p->G, 1, p->sc, p->st, s));
     GB_CU(cudaMemcpyAsync(p->st_host, p->st, sizeof(GbState), cudaMemcpyDeviceToHost, s));
     GB_CU(cudaEventRecord(p->ev_state, s));
     R.launches += gb_launches_so_far() - l0;

@@ -145,8 +145,9 @@ template <typename I> __device__ __forceinline__ I shfl_iv(I v, int src) {
 // (load(G, row, v) fills v[0..NV) from the term row or the segment row);
 // the values are then pushed in order into the binary counter at each
 // segment's level, which forms the group's pairwise tree (Tree::push_level).
-// sg advances past the run; nseg = its length.  Every lane returns the same
-// values.
+// sg advances past the run; nseg = its length.  The counter is kept by lane 0
+// alone (its levels are thread-local memory: one copy per warp instead of 32
+// identical ones), so `out` is defined in lane 0 only.
 template <typename I, int NV, typename L>
 __device__ __forceinline__ void warp_group(const GbProg& P, const GbSplitPos& SP, int k, int g, unsigned r,
                                            int& sg, int lane, L load, I* out, int& nseg) {
@@ -172,13 +173,17 @@ __device__ __forceinline__ void warp_group(const GbProg& P, const GbSplitPos& SP
         if (rr == 0) break;
         for (int j = 0; j < rr; j++) {
             const int lj = __shfl_sync(0xffffffffu, lev, j);
-            for (int t = 0; t < NV; t++) tr[t].push_level(shfl_iv(v[t], j), lj);
+            for (int t = 0; t < NV; t++) {
+                const I x = shfl_iv(v[t], j);
+                if (lane == 0) tr[t].push_level(x, lj);   // the counter lives in lane 0 only
+            }
         }
         nseg += rr;
         sg += rr;
         if (rr < 32) break;
     }
-    for (int t = 0; t < NV; t++) out[t] = tr[t].result();
+    if (lane == 0)
+        for (int t = 0; t < NV; t++) out[t] = tr[t].result();
 }
 
 }  // namespace gb

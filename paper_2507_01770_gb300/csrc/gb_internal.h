@@ -252,4 +252,7 @@ struct GbState {
     unsigned long long min_key;        // smallest active key (K = 1 selection)
     long long evals32, evals64, mids;  // running counters
     unsigned long long ops64, ops32;   // directed-rounding operations executed by the eval kernels
+    long long sel_pos;                 // K = 1: pool position of the selected entry (last with the smallest key)
+    unsigned long long part_epoch;     // pool partitions started in this solve (their tile flags carry it)
+    unsigned long long part_ticket;    // pool partition: next tile to hand out
 };

@@ -256,11 +256,15 @@ __device__ __forceinline__ float lib_sin(float x) { return sinf(x); }
 template <typename T> __device__ __forceinline__ int k_exp() { return sizeof(T) == 8 ? K_EXP64 : K_EXP32; }
 template <typename T> __device__ __forceinline__ int k_trig() { return sizeof(T) == 8 ? K_TRIG64 : K_TRIG32; }
 
+// A point interval (lo == hi, the sample points) calls the library once:
+// the same value either way, half the dependent FP64 chain.
 template <typename I> __device__ __forceinline__ I iexp(I x) {
     typedef decltype(x.lo) T;
     I r;
-    r.lo = step_dn(lib_exp(x.lo), k_exp<T>());
-    r.hi = step_up(lib_exp(x.hi), k_exp<T>());
+    const T a = lib_exp(x.lo);
+    const T b = x.hi == x.lo ? a : lib_exp(x.hi);
+    r.lo = step_dn(a, k_exp<T>());
+    r.hi = step_up(b, k_exp<T>());
     if (r.lo < (T)0) r.lo = (T)0;
     return r;
 }
@@ -306,8 +310,8 @@ template <typename I> __device__ __forceinline__ I itrig(I x, bool is_cos) {
     r.lo = (T)-1;
     r.hi = (T)1;
     if (!(w < pi.lo * (T)2) || !(fabs(x.lo) <= big) || !(fabs(x.hi) <= big)) return r;
-    T va = is_cos ? lib_cos(x.lo) : lib_sin(x.lo);
-    T vb = is_cos ? lib_cos(x.hi) : lib_sin(x.hi);
+    const T va = is_cos ? lib_cos(x.lo) : lib_sin(x.lo);
+    const T vb = x.hi == x.lo ? va : (is_cos ? lib_cos(x.hi) : lib_sin(x.hi));
     int k = k_trig<T>();
     T lo = fmin(step_dn(va, k), step_dn(vb, k));
     T hi = fmax(step_up(va, k), step_up(vb, k));

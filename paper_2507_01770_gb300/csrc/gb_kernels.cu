@@ -171,51 +171,77 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
 __device__ __forceinline__ double gub_of(const GbState* st) { return gb_key_value(st->gub_key); }
 
 // Pool statistics at the end of a generation (and after the root): the
-// number of active entries and, for K = 1, the smallest active key.  The last
-// block to finish then starts the next generation: it stops the solve if
-// nothing is active or a limit was reached, otherwise it chooses the
-// selection (all active boxes if at most K; the minimum key when K = 1; else
-// a radix select of the K-th smallest key).
-__global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbState* st) {
+// number of active entries and, for K = 1, the smallest active key and the
+// last pool position holding it (the entry the selection takes: ties go to
+// the most recently inserted).  Each block leaves its (key, position) pair;
+// the last block to finish combines them and starts the next generation: it
+// stops the solve if nothing is active or a limit was reached, otherwise it
+// chooses the selection (all active boxes if at most K; the entry above when
+// K = 1; else a radix select of the K-th smallest key) and opens the next
+// pool partition (ticket 0, a new epoch).
+__device__ __forceinline__ void better_key(unsigned long long& k, long long& q, unsigned long long k2, long long q2) {
+    if (k2 < k || (k2 == k && q2 > q)) k = k2, q = q2;
+}
+
+__global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbState* st, unsigned long long* bkey,
+                                               long long* bpos) {
     if (st->halt) return;
     __shared__ unsigned long long s_c[8], s_k[8];
+    __shared__ long long s_q[8];
     __shared__ bool s_last;
     const long long count = st->pool;
     const double thr = thr_of(gub_of(st), G.tol_f);
-    long long c = 0;
+    long long c = 0, kq = -1;
     unsigned long long kmin = ~0ull;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
          q += (long long)gridDim.x * blockDim.x) {
         const double f = E.flo[q];
         if (f < thr && !((unsigned)E.cyc[q] & GB_FINAL_BIT)) {
             c++;
-            const unsigned long long k = gb_order_key(f);
-            kmin = k < kmin ? k : kmin;
+            better_key(kmin, kq, gb_order_key(f), q);
         }
     }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int o = 16; o; o >>= 1) {
         c += __shfl_down_sync(0xffffffffu, c, o);
-        const unsigned long long other = __shfl_down_sync(0xffffffffu, kmin, o);
-        kmin = other < kmin ? other : kmin;
+        const unsigned long long k2 = __shfl_down_sync(0xffffffffu, kmin, o);
+        const long long q2 = __shfl_down_sync(0xffffffffu, kq, o);
+        better_key(kmin, kq, k2, q2);
     }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) s_c[w] = (unsigned long long)c, s_k[w] = kmin;
+    if (lane == 0) s_c[w] = (unsigned long long)c, s_k[w] = kmin, s_q[w] = kq;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long tc = 0, tk = ~0ull;
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) tc += s_c[i], tk = s_k[i] < tk ? s_k[i] : tk;
+        long long tq = -1;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) tc += s_c[i], better_key(tk, tq, s_k[i], s_q[i]);
         if (tc) atomicAdd((unsigned long long*)&st->active, tc);
-        if (tk != ~0ull) atomicMin(&st->min_key, tk);
+        bkey[blockIdx.x] = tk;
+        bpos[blockIdx.x] = tq;
         __threadfence();
         s_last = atomicAdd(&st->stats_done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    // last block: start of the next generation
+    if (!s_last) return;
+    // last block: combine every block's pair, then start the next generation
     __threadfence();
+    kmin = ~0ull;
+    kq = -1;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) better_key(kmin, kq, __ldcg(bkey + b), __ldcg(bpos + b));
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long k2 = __shfl_down_sync(0xffffffffu, kmin, o);
+        const long long q2 = __shfl_down_sync(0xffffffffu, kq, o);
+        better_key(kmin, kq, k2, q2);
+    }
+    if (lane == 0) s_k[w] = kmin, s_q[w] = kq;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    unsigned long long mk = ~0ull;
+    long long mq = -1;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) better_key(mk, mq, s_k[i], s_q[i]);
     st->stats_done = 0;
+    st->part_ticket = 0;
+    st->part_epoch += 1;
     const long long active = (long long)atomicAdd((unsigned long long*)&st->active, 0ull);
-    const unsigned long long mk = atomicMin(&st->min_key, ~0ull);
     if (active == 0 || st->gen >= G.max_gen || st->overflow || st->error) {
         st->halt = 1;
         return;
@@ -226,10 +252,10 @@ __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbStat
         st->sel_below = active;
         st->sel_need = 0;
     } else if (G.K == 1) {
-        // the smallest active key (the partition then takes the most recently
-        // inserted box among those with that key)
+        // the smallest active key, the most recently inserted entry holding it
         st->sel_mode = 1;
         st->sel_T = mk;
+        st->sel_pos = mq;
         st->sel_below = 0;
         st->sel_need = 1;
     } else {
@@ -297,6 +323,7 @@ __global__ void __launch_bounds__(1024) k_radix_pick(int pass, GbState* st, unsi
                 st->radix_prefix = (st->radix_prefix << 16) | (unsigned long long)(w * 2048 + k * 32 + lane);
                 st->radix_rank = rank - before;
                 st->sel_below += before;
+                if (pass == 3) st->sel_ties = c;   // entries whose whole key equals the threshold
             }
             if (b) break;
             acc += __shfl_sync(0xffffffffu, inc, 31);
@@ -312,52 +339,13 @@ __global__ void __launch_bounds__(1024) k_radix_pick(int pass, GbState* st, unsi
 }
 
 // ---------------------------------------------------------------------------
-// Pool partition: class of entry q.
+// Pool partition: class of an entry (cut off, selected below the threshold,
+// tie at the threshold).
 struct PartFlags { bool drop, below, tie; };
-
-__device__ __forceinline__ PartFlags part_flags(const GbEntries& E, long long q, long long count, double gub,
-                                                double thr, unsigned long long T) {
-    PartFlags f{false, false, false};
-    if (q >= count) return f;
-    double v = E.flo[q];
-    if (v > gub) { f.drop = true; return f; }
-    bool act = v < thr && !((unsigned)E.cyc[q] & GB_FINAL_BIT);
-    if (!act) return f;
-    if (T == ~0ull) { f.below = true; return f; }
-    unsigned long long key = gb_order_key(v);
-    f.below = key < T;
-    f.tie = key == T;
-    return f;
-}
 
 constexpr int PT = 256;  // threads per partition / compaction block; tile = 4 rounds
 
 __device__ __forceinline__ long long ntiles_of(long long items) { return (items + GB_TILE - 1) / GB_TILE; }
-
-__global__ void k_part_count(GbEntries E, GbGenConst G, const GbState* st, int* tile_cnt, int max_tiles) {
-    if (st->halt) return;
-    __shared__ int sw[PT / 32 + 1];
-    const long long count = st->pool;
-    const double gub = gub_of(st);
-    const double thr = thr_of(gub, G.tol_f);
-    const unsigned long long T = st->sel_T;
-    const long long nt = ntiles_of(count);
-    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-        const long long base = tile * GB_TILE;
-        int cd = 0, cb = 0, ct = 0, tot;
-        for (int r = 0; r < GB_TILE / PT; r++) {
-            PartFlags f = part_flags(E, base + r * PT + threadIdx.x, count, gub, thr, T);
-            block_prefix<PT>(f.drop, sw, &tot); cd += tot;
-            block_prefix<PT>(f.below, sw, &tot); cb += tot;
-            block_prefix<PT>(f.tie, sw, &tot); ct += tot;
-        }
-        if (threadIdx.x == 0) {
-            tile_cnt[tile] = cd;
-            tile_cnt[max_tiles + tile] = cb;
-            tile_cnt[2 * max_tiles + tile] = ct;
-        }
-    }
-}
 
 // Survivor count S of the generation: overflow if the slots cannot take
 // them; with block records, a collection first if their new records do not fit.
@@ -368,18 +356,18 @@ __device__ __forceinline__ void set_survivors(const GbGenConst& G, GbState* st, 
     st->gc = (!st->overflow && G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
 }
 
-// Exclusive scan of up to 3 arrays of tile counts (one block of 1024
-// threads, each owning a contiguous run of tiles).
-// what: 0 = partition (3 arrays, items = pool), 1 = FP32 list and 2 =
-// survivors (items = children of the generation), 3 = output (items = count),
-// 4 = free block records (items = records ever used).
+// Exclusive scan of an array of tile counts (one block of 1024 threads,
+// each owning a contiguous run of tiles).
+// what: 1 = FP32 list and 2 = survivors (items = children of the
+// generation), 3 = output (items = count), 4 = free block records (items =
+// records ever used).
 __global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_cnt, int* tile_off, int max_tiles,
                                                      int what, long long out_count, GbGenConst G, GbState* st) {
     if (what != 3 && st->halt) return;
     if (what == 4 && !st->gc) return;
     __shared__ long long part[1024];
     __shared__ long long tot[3];
-    const long long items = what == 0 ? st->pool : what == 3 ? out_count : what == 4 ? st->rec_bump : st->nch;
+    const long long items = what == 3 ? out_count : what == 4 ? st->rec_bump : st->nch;
     const int ntiles = (int)ntiles_of(items);
     const int t = threadIdx.x;
     const int per = (ntiles + 1023) / 1024;
@@ -406,17 +394,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_c
         __syncthreads();
     }
     if (t != 0) return;
-    if (what == 0) {
-        long long D = tot[0], Bl = tot[1], Ti = tot[2];
-        long long need = st->sel_T == ~0ull ? 0 : st->sel_need;
-        st->drops = D;
-        st->parents = Bl + need;
-        st->nch = (Bl + need) << G.flog2;
-        st->kept_old = items - D - (Bl + need);
-        st->nfree_after_drop = st->nfree + D;
-        st->sel_below = Bl;
-        st->sel_ties = Ti;
-    } else if (what == 1) {
+    if (what == 1) {
         st->n32 = tot[0];
         st->kept32 = tot[0];
     } else if (what == 2) {
@@ -429,42 +407,144 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_c
     }
 }
 
-__global__ void k_part_scatter(GbEntries E, GbGenConst G, const GbState* st, const int* tile_off, int max_tiles,
-                               GbEntries En, GbParents par, unsigned* freel) {
+// Pool partition in one launch.  Tiles of GB_TILE entries are handed out in
+// order (a ticket); each tile classifies its entries (cut off, selected --
+// below the threshold, or the K = 1 entry --, tie), publishes its three
+// counts, finds the counts of every tile before it by looking back at their
+// published values (decoupled look-back: a predecessor's inclusive prefix
+// ends the walk, its aggregate is added and the walk goes on), publishes its
+// own inclusive prefix and scatters its entries stably: cut-off slots to the
+// free list, parents to the parent buffers (the last `need` ties in pool
+// order), the rest to the new pool.  A tile only waits for tiles whose
+// tickets were taken before its own, by blocks already running, so every
+// wait ends; each is bounded all the same (on running out it sets an error
+// bit and publishes, so no block waits on it).  The tile that finishes last
+// in order writes the totals of the partition.
+constexpr unsigned long long GB_FLAG_AGG = 1, GB_FLAG_INC = 2;
+constexpr long long GB_SPIN_LIMIT = 1LL << 26;
+
+__device__ __forceinline__ PartFlags part_flags1(const GbEntries& E, long long q, long long count, double gub,
+                                                 double thr, unsigned long long T, int mode, long long spos) {
+    PartFlags f{false, false, false};
+    if (q >= count) return f;
+    const double v = E.flo[q];
+    if (v > gub) { f.drop = true; return f; }
+    const bool act = v < thr && !((unsigned)E.cyc[q] & GB_FINAL_BIT);
+    if (!act) return f;
+    if (mode == 1) { f.below = q == spos; return f; }
+    if (T == ~0ull) { f.below = true; return f; }
+    const unsigned long long key = gb_order_key(v);
+    f.below = key < T;
+    f.tie = key == T;
+    return f;
+}
+
+__global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbState* st, int* agg, int* inc,
+                                                int max_tiles, unsigned long long* flag, GbEntries En,
+                                                GbParents par, unsigned* freel) {
     if (st->halt) return;
     __shared__ int sw[PT / 32 + 1];
+    __shared__ long long s_tile;
+    __shared__ long long s_ex[3];
     const long long count = st->pool;
     const double gub = gub_of(st);
     const double thr = thr_of(gub, G.tol_f);
+    const int mode = st->sel_mode;
     const unsigned long long T = st->sel_T;
-    const long long need = (T == ~0ull) ? 0 : st->sel_need;
-    const long long Ti = st->sel_ties;
+    const long long spos = st->sel_pos;
+    // ties (key == T) exist only for the radix threshold; the last `need` of them are taken
+    const long long need = (mode == 2 && T != ~0ull) ? st->sel_need : 0;
+    const long long Ti = (mode == 2 && T != ~0ull) ? st->sel_ties : 0;
     const long long nfree = st->nfree;
+    const unsigned long long epoch = st->part_epoch;
     const long long nt = ntiles_of(count);
-    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-        long long od = tile_off[tile];
-        long long ob = tile_off[max_tiles + tile];
-        long long ot = tile_off[2 * max_tiles + tile];
+    auto totals = [&](long long D, long long Bl, long long Tt) {
+        const long long npar = Bl + need;
+        st->drops = D;
+        st->parents = npar;
+        st->nch = npar << G.flog2;
+        st->kept_old = count - D - npar;
+        st->nfree_after_drop = nfree + D;
+        st->sel_below = Bl;
+        st->sel_ties = Tt;
+    };
+    if (nt == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) totals(0, 0, 0);
+        return;
+    }
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&st->part_ticket, 1ull);
+        __syncthreads();
+        const long long tile = s_tile;
+        if (tile >= nt) break;
         const long long base = tile * GB_TILE;
+        PartFlags f[GB_TILE / PT];
+        int rd[GB_TILE / PT], rb[GB_TILE / PT], rt[GB_TILE / PT];
+        int cd = 0, cb = 0, ct = 0, t;
+#pragma unroll
         for (int r = 0; r < GB_TILE / PT; r++) {
-            long long q = base + r * PT + threadIdx.x;
-            PartFlags f = part_flags(E, q, count, gub, thr, T);
-            int td, tb, tt;
-            long long rd = od + block_prefix<PT>(f.drop, sw, &td);
-            long long rb = ob + block_prefix<PT>(f.below, sw, &tb);
-            long long rt = ot + block_prefix<PT>(f.tie, sw, &tt);
-            od += td; ob += tb; ot += tt;
+            f[r] = part_flags1(E, base + r * PT + threadIdx.x, count, gub, thr, T, mode, spos);
+            rd[r] = cd + block_prefix<PT>(f[r].drop, sw, &t);
+            cd += t;
+            rb[r] = cb + block_prefix<PT>(f[r].below, sw, &t);
+            cb += t;
+            rt[r] = ct + block_prefix<PT>(f[r].tie, sw, &t);
+            ct += t;
+        }
+        if (threadIdx.x == 0) {
+            long long ed = 0, eb = 0, et = 0;
+            volatile unsigned long long* vf = flag;
+            if (tile > 0) {
+                agg[tile] = cd;
+                agg[max_tiles + tile] = cb;
+                agg[2 * max_tiles + tile] = ct;
+                __threadfence();
+                vf[tile] = (epoch << 2) | GB_FLAG_AGG;
+                bool bad = false;
+                for (long long j = tile - 1; j >= 0;) {
+                    unsigned long long fl;
+                    long long spins = 0;
+                    while (((fl = vf[j]) >> 2) != epoch)
+                        if (++spins > GB_SPIN_LIMIT) { bad = true; break; }
+                    if (bad) break;
+                    __threadfence();
+                    const volatile int* vs = (fl & 3) == GB_FLAG_INC ? inc : agg;
+                    ed += vs[j];
+                    eb += vs[max_tiles + j];
+                    et += vs[2 * max_tiles + j];
+                    if ((fl & 3) == GB_FLAG_INC) break;
+                    j--;
+                }
+                if (bad) atomicOr(&st->error, 4);
+            }
+            inc[tile] = (int)(ed + cd);
+            inc[max_tiles + tile] = (int)(eb + cb);
+            inc[2 * max_tiles + tile] = (int)(et + ct);
+            __threadfence();
+            vf[tile] = (epoch << 2) | GB_FLAG_INC;
+            s_ex[0] = ed;
+            s_ex[1] = eb;
+            s_ex[2] = et;
+            if (tile == nt - 1) totals(ed + cd, eb + cb, et + ct);
+        }
+        __syncthreads();
+        const long long od = s_ex[0], ob = s_ex[1], ot = s_ex[2];
+#pragma unroll
+        for (int r = 0; r < GB_TILE / PT; r++) {
+            const long long q = base + r * PT + threadIdx.x;
             if (q >= count) continue;
-            long long sel_before = rb + max(0LL, rt - (Ti - need));
-            bool sel = f.below || (f.tie && rt >= Ti - need);
-            if (f.drop) {
-                freel[nfree + rd] = E.slot[q];
+            const long long gd = od + rd[r], gb = ob + rb[r], gt = ot + rt[r];
+            const long long sel_before = gb + max(0LL, gt - (Ti - need));
+            const bool sel = f[r].below || (f[r].tie && gt >= Ti - need);
+            if (f[r].drop) {
+                freel[nfree + gd] = E.slot[q];
             } else if (sel) {
                 par.slot[sel_before] = E.slot[q];
                 par.cyc[sel_before] = E.cyc[q];
                 par.flo[sel_before] = E.flo[q];
             } else {
-                long long kr = q - rd - sel_before;
+                const long long kr = q - gd - sel_before;
                 En.flo[kr] = E.flo[q];
                 En.slot[kr] = E.slot[q];
                 En.cyc[kr] = E.cyc[q];
@@ -773,12 +853,12 @@ __device__ __forceinline__ void tab_dirty_groups(const GbProg& P, const GbPool& 
 // ---------------------------------------------------------------------------
 // Survivors into free slots: coordinates, FP32 shadow, group caches (dirty
 // groups recomputed, the rest copied from the parent), pool entry.
-template <bool PR>
+template <bool PR, bool TAB>
 __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                 const GbChildren& ch, const GbSplit& sp, const GbEntries& En,
                                                 double tol_x, const GbState* st, long long s, int lane,
-                                                const GbTabs& Tb, bool tab, double2* shF, double2* shM,
-                                                float2* sh32) {
+                                                const GbTabs& Tb, double2* shF, double2* shM, float2* sh32) {
+    constexpr bool tab = TAB;
     const long long nfree = st->nfree, bump = st->bump, kept_old = st->kept_old;
     const long long ci = ch.surv[s];
     ChildCtx c = child_ctx(par, ci, sp);
@@ -803,8 +883,8 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
     narrow = __all_sync(0xffffffffu, narrow) && tol_x > 0.0;
     const int blk = c.info.z;
     MidView MX{X};
-    iv64 R[GB_MAX_TREGS];
-    iv32 R32[GB_MAX_TREGS];
+    iv64 R[TAB ? 1 : GB_MAX_TREGS];
+    iv32 R32[TAB ? 1 : GB_MAX_TREGS];
     int slot_k = 0, ops = 0;
     for (int k = 0; k < P.n_sum; k++) {
         GbSum S = P.sums[k];
@@ -823,7 +903,7 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
             if ((slot_k & 31) != lane) continue;
             size_t dst = (size_t)ns * pool.NG + S.group0 + g;
             iv64 a, b;
-            if (tab) {
+            if constexpr (TAB) {
                 const int at = k * GB_TAB_MAX_DIRTY + (g - dr.x);
                 a = iv64{shF[at].x, shF[at].y};
                 b = iv64{shM[at].x, shM[at].y};
@@ -838,13 +918,14 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
             }
             pool.gsum[dst] = make_double2(a.lo, a.hi);
             pool.gmid[dst] = make_double2(b.lo, b.hi);
-            for (int j = 1; pool.gsamp && j <= pool.S; j++) {
-                const iv64 v = group_sum<PR, double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
-                pool.gsamp[((size_t)ns * pool.S + (j - 1)) * pool.NG + S.group0 + g] = make_double2(v.lo, v.hi);
-            }
+            if constexpr (!TAB)   // diagonal samples: paper mode runs on the interpreter only
+                for (int j = 1; pool.gsamp && j <= pool.S; j++) {
+                    const iv64 v = group_sum<PR, double>(P, S, g, SampleView{X, j, pool.S + 1}, R, ops);
+                    pool.gsamp[((size_t)ns * pool.S + (j - 1)) * pool.NG + S.group0 + g] = make_double2(v.lo, v.hi);
+                }
         }
     }
-    if (pool.gdp) {   // coordinate partials: the parent's, recomputed where the split reaches
+    if (!TAB && pool.gdp) {   // coordinate partials: the parent's, recomputed where the split reaches
         const int2 ab = d_affected(P, blk);
         const int a0 = ab.x * P.B, a1 = min(n, (ab.y + 1) * P.B);
         const double2* src = pool.gdp + (size_t)c.slot * P.n_sum * n;
@@ -944,12 +1025,12 @@ __global__ void k_gc_scatter(GbPool pool, const GbState* st, const int* tile_off
 // with those entries replaced.  A new record holds the child's coordinates of
 // its block and the cached sums of the groups it owns (groups of the dirty
 // ranges recomputed, the others copied from the parent's record).
-template <bool PR>
+template <bool PR, bool TAB>
 __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                 const GbChildren& ch, const GbSplit& sp, const GbEntries& En,
                                                 double tol_x, const GbState* st, long long s, int lane,
-                                                const GbTabs& Tb, bool tab, double2* shF, double2* shM,
-                                                float2* sh32) {
+                                                const GbTabs& Tb, double2* shF, double2* shM, float2* sh32) {
+    constexpr bool tab = TAB;
     const long long nfree = st->nfree, bump = st->bump, kept_old = st->kept_old;
     const long long rnf = st->rec_nfree, rbump = st->rec_bump;
     const long long ci = ch.surv[s];
@@ -974,20 +1055,54 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
     View<float> X32;
     if (pool.fp32) X32 = view32(pool, par, c, sp);
     int wide_delta = 0;
+    // the child's coordinates of each new record: the parent's record of that
+    // block, with the split coordinates' pieces; each lane loads its batch of
+    // coordinates before storing any (the stores go to the arrays the loads
+    // read, so they would otherwise wait one memory round trip each)
+    constexpr int BATCH = 4;
+    const size_t bo = (size_t)c.p * sp.dmax * (sp.m + 1);
     for (int t = 0; t < nrec && blk - t >= 0; t++) {
         const int b = blk - t, j0 = b * B, j1 = min(n, j0 + B);
-        const size_t o = (size_t)crow[b] * B;
+        const size_t o = (size_t)crow[b] * B, src = (size_t)prow[b] * B;
         bool wide = false;
-        for (int j = j0 + lane; j < j1; j += 32) {
-            const iv64 x = X.get(j);
-            pool.rlo[o + (j - j0)] = x.lo;
-            pool.rhi[o + (j - j0)] = x.hi;
-            if (pool.fp32) {
-                const iv32 y = X32.get(j);
-                pool.rlo32[o + (j - j0)] = y.lo;
-                pool.rhi32[o + (j - j0)] = y.hi;
+        for (int jb = j0; jb < j1; jb += 32 * BATCH) {
+            double xl[BATCH], xh[BATCH];
+            float yl[BATCH], yh[BATCH];
+#pragma unroll
+            for (int u = 0; u < BATCH; u++) {
+                const int j = jb + u * 32 + lane;
+                if (j >= j1) continue;
+                const unsigned k = (unsigned)(j - c.info.x);
+                if (k < (unsigned)c.info.y) {   // a split coordinate: its piece's boundaries
+                    const int dig = (c.r >> (k * sp.mshift)) & ((1 << sp.mshift) - 1);
+                    const size_t at = bo + (size_t)k * (sp.m + 1) + dig;
+                    xl[u] = par.bnd[at];
+                    xh[u] = par.bnd[at + 1];
+                    if (pool.fp32) {
+                        yl[u] = par.bnd_rd[at];
+                        yh[u] = par.bnd_ru[at + 1];
+                    }
+                } else {
+                    xl[u] = pool.rlo[src + (j - j0)];
+                    xh[u] = pool.rhi[src + (j - j0)];
+                    if (pool.fp32) {
+                        yl[u] = pool.rlo32[src + (j - j0)];
+                        yh[u] = pool.rhi32[src + (j - j0)];
+                    }
+                }
             }
-            if (!(__dsub_rn(x.hi, x.lo) < tol_x)) wide = true;
+#pragma unroll
+            for (int u = 0; u < BATCH; u++) {
+                const int j = jb + u * 32 + lane;
+                if (j >= j1) continue;
+                pool.rlo[o + (j - j0)] = xl[u];
+                pool.rhi[o + (j - j0)] = xh[u];
+                if (pool.fp32) {
+                    pool.rlo32[o + (j - j0)] = yl[u];
+                    pool.rhi32[o + (j - j0)] = yh[u];
+                }
+                if (!(__dsub_rn(xh[u], xl[u]) < tol_x)) wide = true;
+            }
         }
         wide = __any_sync(0xffffffffu, wide);
         if (lane == 0) {
@@ -996,8 +1111,8 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
         }
     }
     const MidView MX{X};
-    iv64 R[GB_MAX_TREGS];
-    iv32 R32[GB_MAX_TREGS];
+    iv64 R[TAB ? 1 : GB_MAX_TREGS];
+    iv32 R32[TAB ? 1 : GB_MAX_TREGS];
     int ops = 0;
     for (int it = lane; it < nrec * GPB; it += 32) {
         const int t = it / GPB, o = it - t * GPB, b = blk - t;
@@ -1018,12 +1133,13 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
             for (int j = 0; pool.rgsamp && j < pool.S; j++) pool.rgsamp[j * sstep + dst] = pool.rgsamp[j * sstep + src];
             continue;
         }
-        for (int j = 1; pool.rgsamp && j <= pool.S; j++) {
-            const iv64 v = group_sum<PR, double>(P, S, gl, SampleView{X, j, pool.S + 1}, R, ops);
-            pool.rgsamp[(j - 1) * sstep + dst] = make_double2(v.lo, v.hi);
-        }
+        if constexpr (!TAB)   // diagonal samples: paper mode runs on the interpreter only
+            for (int j = 1; pool.rgsamp && j <= pool.S; j++) {
+                const iv64 v = group_sum<PR, double>(P, S, gl, SampleView{X, j, pool.S + 1}, R, ops);
+                pool.rgsamp[(j - 1) * sstep + dst] = make_double2(v.lo, v.hi);
+            }
         iv64 a, m;
-        if (tab) {
+        if constexpr (TAB) {
             const int at = k * GB_TAB_MAX_DIRTY + (gl - dr.x);
             a = iv64{shF[at].x, shF[at].y};
             m = iv64{shM[at].x, shM[at].y};
@@ -1039,7 +1155,7 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
         pool.rgsum[dst] = make_double2(a.lo, a.hi);
         pool.rgmid[dst] = make_double2(m.lo, m.hi);
     }
-    if (pool.rgdp) {   // coordinate partials of each new record's block (templates within one coordinate)
+    if (!TAB && pool.rgdp) {   // coordinate partials of each new record's block (templates within one coordinate)
         iv64 RA[GB_MAX_TREGS];
         for (int t = lane; t < nrec && blk - t >= 0; t += 32) {
             const int b = blk - t;
@@ -1057,10 +1173,10 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
     }
 }
 
-template <bool PR>
+template <bool PR, bool RECS, bool TAB>
 __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbParents par, GbChildren ch,
                                                      GbSplit sp, GbEntries En, double tol_x, GbState* st,
-                                                     GbTabs Tb, int tab) {
+                                                     GbTabs Tb) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __shared__ double2 shF[4][GB_SHG], shM[4][GB_SHG];
     __shared__ float2 sh32[4][GB_SHG];
@@ -1068,10 +1184,10 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
     const long long kept = st->kept;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < kept; s += nwarps) {
-        if (pool.recs)
-            materialize_rec<PR>(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0, shF[w], shM[w], sh32[w]);
+        if constexpr (RECS)
+            materialize_rec<PR, TAB>(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, shF[w], shM[w], sh32[w]);
         else
-            materialize_one<PR>(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, tab != 0, shF[w], shM[w], sh32[w]);
+            materialize_one<PR, TAB>(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, shF[w], shM[w], sh32[w]);
         __syncwarp();
     }
 }
@@ -1420,11 +1536,13 @@ cudaError_t gb_launch_resume(const GbProg& P, const GbPool& pool, const GbEntrie
     return cudaGetLastError();
 }
 
-cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, GbState* st, cudaStream_t s) {
+cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, const GbScan& sc, GbState* st,
+                            cudaStream_t s) {
     unsigned g = grid_for(cap, 256);
     if (g > gb_sm_count() * 8) g = gb_sm_count() * 8;
+    if (g > (unsigned)GB_STAT_BLOCKS) g = GB_STAT_BLOCKS;
     gb_launch_count++;
-    k_stats<<<g, 256, 0, s>>>(E, G, st);
+    k_stats<<<g, 256, 0, s>>>(E, G, st, sc.stat_key, sc.stat_pos);
     return cudaGetLastError();
 }
 
@@ -1449,10 +1567,9 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
             k_radix_pick<<<1, 1024, 0, s>>>(pass, st, sc.hist);
         }
     }
-    gb_launch_count += 3;
-    k_part_count<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_cnt, sc.max_tiles);
-    k_scan_tiles<<<1, 1024, 0, s>>>(3, sc.tile_cnt, sc.tile_off, sc.max_tiles, 0, 0, G, st);
-    k_part_scatter<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_off, sc.max_tiles, E_new, par, pool.freel);
+    gb_launch_count++;
+    k_part_1p<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_cnt, sc.tile_off, sc.max_tiles, sc.tile_flag, E_new, par,
+                                        pool.freel);
     gb_launch_count++;
     k_prep<<<grid_for(G.K * (long long)sp.dmax, 128), 128, 0, s>>>(P, pool, par, sp, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1526,10 +1643,17 @@ after_eval:
     if (tabs) Tb = *tabs;
     gb_launch_count++;
     const unsigned gmat = (unsigned)std::min<long long>(grid_for(Cmax * 32, 128), gb_sm_count() * 16);
-    if (P.any_prod)
-        k_materialize<true><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, tabs ? 1 : 0);
-    else
-        k_materialize<false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, tabs ? 1 : 0);
+    // products never use term tables
+    if (P.any_prod) {
+        if (pool.recs) k_materialize<true, true, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
+        else k_materialize<true, false, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
+    } else if (tabs) {
+        if (pool.recs) k_materialize<false, true, true><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
+        else k_materialize<false, false, true><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
+    } else {
+        if (pool.recs) k_materialize<false, true, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
+        else k_materialize<false, false, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
+    }
     if (G.K <= 4096) {   // few parents: freed by the finishing block itself
         gb_launch_count++;
         k_finish<<<1, 256, 0, s>>>(G, par, pool, E_new, 1, st);
@@ -1538,7 +1662,7 @@ after_eval:
         k_free_parents<<<grid_for(G.K, 256), 256, 0, s>>>(par, pool, E_new, st);
         k_finish<<<1, 1, 0, s>>>(G, par, pool, E_new, 0, st);
     }
-    if ((e = gb_launch_stats(E_new, G, cap, st, s)) != cudaSuccess) return e;
+    if ((e = gb_launch_stats(E_new, G, cap, sc, st, s)) != cudaSuccess) return e;
     if (nlaunch) *nlaunch = gb_launch_count - n0;
     return cudaGetLastError();
 }

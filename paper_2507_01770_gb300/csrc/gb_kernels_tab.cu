@@ -47,15 +47,23 @@ template <> struct TabPrec<float> {
 __device__ __forceinline__ iv64 mid_node(const GbTabs& T, size_t i) { double2 v = T.nm64[i]; return iv64{v.x, v.y}; }
 
 // ---------------------------------------------------------------------------
-// k_ptab: per parent (blockIdx.y).  Blocks x < row_blocks: one table row part
-// per thread -- rows are (dirty term, digit combination) and each row has up
-// to four independent parts: 0 the FP64 value, 1 the midpoint value, 2 the
-// FP64 leaf adjoints, 3 the FP32 value and leaf adjoints.  Blocks x >=
-// row_blocks: one group tree of the parent's cached sums each (sum k, kind:
-// F, midpoint, FP32), level by level.
-constexpr int PTAB_T = 64;
+// k_ptab: per parent (blockIdx.y).  Blocks x < row_blocks: table row parts,
+// PTAB_ITEMS per block (one warp) -- rows are (dirty term, digit
+// combination) and each row has up to three independent parts: 0 the FP64
+// value and leaf adjoints (one forward pass, then the reverse sweep), 1 the
+// midpoint value, 2 the FP32 value and leaf adjoints.  A part is one serial
+// chain of FP64 work (a template's interval operations, transcendentals
+// included).  On GB300 a dependent FP64 operation takes ~30 ns and a warp's
+// FP64 instruction holds the SM's FP64 pipe for ~16 clocks whatever its
+// active lanes, so each part gets a warp of its own (parts in one warp would
+// diverge and run one after the other), spread over the SMs.
+// Blocks x >= row_blocks: one group tree of the parent's cached sums each
+// (sum k, kind: F, midpoint, FP32), level by level.
+constexpr int PTAB_T = 32;
+constexpr int PTAB_ITEMS = 1;
+constexpr int PTAB_SMEM_DT = 256;   // dirty terms staged in shared memory for the row lookup
 
-__device__ __forceinline__ int ptab_parts(const GbPool& pool) { return pool.fp32 ? 4 : 3; }
+__host__ __device__ __forceinline__ int ptab_parts(const GbPool& pool) { return pool.fp32 ? 3 : 2; }
 
 __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp,
                                                  int row_blocks, GbState* st) {
@@ -111,28 +119,35 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             __syncthreads();
             off += mL;
         }
-        if (tops) atomicAdd(kind == 2 ? &st->ops32 : &st->ops64, (unsigned long long)tops);
+        warp_add_ops(tops, kind == 2 ? &st->ops32 : &st->ops64);
         return;
     }
     const GbSplitPos SP = P.sps[spi];
+    // the split position's dirty terms, staged for the row -> term lookup
+    __shared__ int s_row[PTAB_SMEM_DT];
+    const bool staged = SP.ndterm <= PTAB_SMEM_DT;
+    if (staged)
+        for (int t = threadIdx.x; t < SP.ndterm; t += blockDim.x) s_row[t] = P.dterms[SP.dterm0 + t].row;
+    __syncthreads();
     const size_t o = (size_t)p * sp.dmax * (sp.m + 1);
     const int parts = ptab_parts(pool);
     int ops = 0, ops32 = 0;
-    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < SP.tab_entries * parts;
-         item += row_blocks * blockDim.x) {
+    for (int item = blockIdx.x * PTAB_ITEMS + threadIdx.x; threadIdx.x < PTAB_ITEMS && item < SP.tab_entries * parts;
+         item += row_blocks * PTAB_ITEMS) {
         const int row = item / parts, part = item - row * parts;
         // the dirty term owning this row (rows are contiguous per term)
         int lo = 0, hi = SP.ndterm - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (P.dterms[SP.dterm0 + mid].row <= row) lo = mid; else hi = mid - 1;
+            const int r0 = staged ? s_row[mid] : P.dterms[SP.dterm0 + mid].row;
+            if (r0 <= row) lo = mid; else hi = mid - 1;
         }
         const GbDTerm D = P.dterms[SP.dterm0 + lo];
         const unsigned r = (unsigned)(row - D.row) << D.dshift;   // a child index with these digits
         const GbSum S = P.sums[D.sum];
         const int i = S.first + D.term * S.step;
         const size_t orow = (size_t)p * T.max_rows + row;
-        if (part < 3) {
+        if (part < 2) {
             iv64 R[GB_MAX_TREGS];
             View<double> X = box_view64(pool, slot);
             X.blo = par.bnd + o;
@@ -142,15 +157,13 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             X.mshift = sp.mshift;
             X.mstride = sp.m + 1;
             X.r = r;
-            if (part == 0) {
-                const iv64 v = term_fwd<double>(P, S, i, X, R, ops);
-                T.tv64[orow] = make_double2(v.lo, v.hi);
-            } else if (part == 1) {
+            if (part == 1) {
                 const iv64 v = term_fwd<double>(P, S, i, MidView{X}, R, ops);
                 T.tm64[orow] = make_double2(v.lo, v.hi);
             } else {
                 iv64 RA[GB_MAX_TREGS];
-                term_fwd<double>(P, S, i, X, R, ops);
+                const iv64 v = term_fwd<double>(P, S, i, X, R, ops);
+                T.tv64[orow] = make_double2(v.lo, v.hi);
                 for (int t = 0; t < S.nins; t++) RA[t] = iv64{0.0, 0.0};
                 RA[S.nins - 1] = iv64{1.0, 1.0};
                 reverse_sweep<double>(P.tins + S.ins0, S.nins, R, RA, ops);
@@ -184,8 +197,8 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             }
         }
     }
-    if (ops) atomicAdd(&st->ops64, (unsigned long long)ops);
-    if (ops32) atomicAdd(&st->ops32, (unsigned long long)ops32);
+    warp_add_ops(ops, &st->ops64);   // one atomic per warp (every lane reaches here)
+    warp_add_ops(ops32, &st->ops32);
 }
 
 // ---------------------------------------------------------------------------
@@ -272,8 +285,8 @@ __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents
         T.td64[o] = make_double2(D.lo, D.hi);
         if (tl32) T.td32[o] = make_float2(D32.lo, D32.hi);
     }
-    if (ops) atomicAdd(&st->ops64, (unsigned long long)ops);
-    if (ops32) atomicAdd(&st->ops32, (unsigned long long)ops32);
+    warp_add_ops(ops, &st->ops64);   // one atomic per warp (every lane reaches here)
+    warp_add_ops(ops32, &st->ops32);
 }
 
 // ---------------------------------------------------------------------------
@@ -310,6 +323,77 @@ __device__ __forceinline__ I tab_path(const GbSum& S, int2 dr, I* cur, N node, i
         off += mL;
     }
     return cur[0];
+}
+
+// tab_path for a warp whose lanes all walk the same path (one child per
+// warp): the clean sibling nodes the walk reads depend only on the tree's
+// shape and the dirty range, so they are listed first (lane t takes the t-th
+// one the walk will read) and loaded by all lanes at once, one round of
+// memory latency instead of one per level; the walk then takes each from its
+// lane.  Same operations in the same order as tab_path, so the same sum,
+// returned in lane 0 (cur is read in lane 0 only).
+template <typename I, typename N>
+__device__ __forceinline__ I tab_path_w(const GbSum& S, int2 dr, I* cur, N node, int lane, int& ops) {
+    if (S.ngroups == 0 || S.nnodes <= 0) {
+        I z;
+        z.lo = 0;
+        z.hi = 0;
+        return z;
+    }
+    if (dr.x >= dr.y) return node(S.nnodes - 1);   // no dirty group: the parent's root
+    int mine = -1, cnt = 0;
+    {
+        int lo = dr.x, hi = dr.y, off = 0;
+        for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
+            const int nlo = lo >> 1, nhi = ((hi - 1) >> 1) + 1;
+            for (int q = nlo; q < nhi; q++) {
+                const int a = 2 * q;
+                if (!(a >= lo && a < hi)) mine = cnt++ == lane ? off + a : mine;
+                if (a + 1 < mL && !(a + 1 >= lo && a + 1 < hi)) mine = cnt++ == lane ? off + a + 1 : mine;
+            }
+            lo = nlo;
+            hi = nhi;
+            off += mL;
+        }
+    }
+    I pre;
+    pre.lo = 0;
+    pre.hi = 0;
+    if (mine >= 0) pre = node(mine);
+    I tmp[GB_TAB_MAX_DIRTY];
+    int lo = dr.x, hi = dr.y, off = 0, used = 0;
+    // every lane follows the walk (the shuffles), lane 0 alone computes it:
+    // cur and tmp are touched by one thread per warp
+    auto take = [&](int idx) {
+        const I v = shfl_iv(pre, used & 31);
+        return used++ < 32 ? v : node(idx);
+    };
+    for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
+        const int nlo = lo >> 1, nhi = ((hi - 1) >> 1) + 1;
+        for (int q = nlo; q < nhi; q++) {
+            const int a = 2 * q;
+            const bool la = a >= lo && a < hi, lb = a + 1 >= lo && a + 1 < hi;
+            I left = la ? pre : take(off + a);
+            I right = left;
+            if (a + 1 < mL) right = lb ? pre : take(off + a + 1);
+            if (lane == 0) {
+                if (la) left = cur[a - lo];
+                I v = left;
+                if (a + 1 < mL) {
+                    if (lb) right = cur[a + 1 - lo];
+                    v = iadd(left, right);
+                }
+                tmp[q - nlo] = v;
+            }
+            if (a + 1 < mL) ops += 2;
+        }
+        if (lane == 0)
+            for (int q = 0; q < nhi - nlo; q++) cur[q] = tmp[q];
+        lo = nlo;
+        hi = nhi;
+        off += mL;
+    }
+    return cur[0];   // defined in lane 0
 }
 
 // Sum k of a child (FP32 tables): dirty group values from the term-tree
@@ -508,13 +592,19 @@ __device__ __forceinline__ void tab_sums64(const GbProg& P, const GbTabs& Tb, lo
     }
 }
 
-// FP64 child: midpoint sample, F(X), first-order test.
+// FP64 child: midpoint sample, F(X), cut-off.  SUM1: the outer expression
+// is one sum (F is that sum; the first-order test is left to
+// eval64_tab_mono and *need_mono tells whether the child passed the
+// cut-off).  Otherwise the first-order test follows at once and the flag is
+// set here.  Returns false for an invalid child.
+template <bool SUM1>
 __device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                  const GbTabs& Tb, const GbChildren& ch, long long ci,
                                                  const GbSplit& sp, double gub_prev, unsigned long long* gkey,
-                                                 bool* has_key, int& ops) {
+                                                 bool* has_key, int& ops, bool* need_mono) {
     ChildCtx c = child_ctx(par, ci, sp);
     const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
+    *need_mono = false;
     if (spi < 0) {   // invalid child (or, defensively, a split position without a layout)
         ch.flag[ci] = 0;
         ch.flo[ci] = __longlong_as_double(0x7ff0000000000000LL);
@@ -523,45 +613,98 @@ __device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& 
     const GbSplitPos SP = P.sps[spi];
     const int blk = c.info.z;
     View<double> X = view64(pool, par, c, sp);
-    MidView MX{X};
-    iv64 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];
+    iv64 sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];
     tab_sums64(P, Tb, c.p, SP, blk, c.r, sums, msums, ops);
-    iv64 Fm = outer_value<double>(P, MX, msums, O, ops);
-    if (Fm.hi == Fm.hi) {
-        *gkey = gb_order_key(Fm.hi);
-        *has_key = true;
+    if constexpr (SUM1) {
+        const iv64 Fm = msums[0], F = sums[0];
+        if (Fm.hi == Fm.hi) {
+            *gkey = gb_order_key(Fm.hi);
+            *has_key = true;
+        }
+        const bool keep = !(F.lo > gub_prev);
+        ch.flo[ci] = canon_lo(F.lo);
+        if (keep) *need_mono = true;
+        else ch.flag[ci] = 0;
+    } else {
+        MidView MX{X};
+        iv64 O[GB_MAX_OREGS], OA[GB_MAX_OREGS];
+        iv64 Fm = outer_value<double>(P, MX, msums, O, ops);
+        if (Fm.hi == Fm.hi) {
+            *gkey = gb_order_key(Fm.hi);
+            *has_key = true;
+        }
+        iv64 F = outer_value<double>(P, X, sums, O, ops);
+        bool keep = !(F.lo > gub_prev);
+        ch.flo[ci] = canon_lo(F.lo);
+        if (keep) keep = !tab_mono<double>(P, Tb, c.p, SP, blk, c.r, X, O, OA, ops);
+        ch.flag[ci] = keep ? 1 : 0;
     }
-    iv64 F = outer_value<double>(P, X, sums, O, ops);
-    bool keep = !(F.lo > gub_prev);
-    if (keep) keep = !tab_mono<double>(P, Tb, c.p, SP, blk, c.r, X, O, OA, ops);
-    ch.flo[ci] = canon_lo(F.lo);
-    ch.flag[ci] = keep ? 1 : 0;
     return true;
 }
 
+// First-order test of a child that passed the cut-off, for objectives whose
+// outer expression is one sum (its adjoint is [1, 1], so the test needs no
+// outer values); sets the child's flag.
+__device__ __forceinline__ void eval64_tab_mono(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                                const GbTabs& Tb, const GbChildren& ch, long long ci,
+                                                const GbSplit& sp, int& ops) {
+    const ChildCtx c = child_ctx(par, ci, sp);
+    const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
+    const View<double> X = view64(pool, par, c, sp);
+    iv64 O[1], OA[1];
+    const bool mono = tab_mono<double>(P, Tb, c.p, SP, c.info.z, c.r, X, O, OA, ops);
+    ch.flag[ci] = mono ? 0 : 1;
+}
+
+// One child per thread.  When the outer expression is one sum, the children
+// of a warp that pass the cut-off are queued in shared memory and their
+// first-order tests run 32 at a time, every lane busy, instead of inside the
+// branch of the lanes that passed (the same tests, so the same flags).
+template <bool QUEUE>
 __global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval64_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
                                                     GbChildren ch, GbSplit sp, int from_list, GbState* st) {
     if (st->halt) return;
+    __shared__ unsigned s_queue[4][QUEUE ? 64 : 1];   // per warp: at most 31 left over + 32 new
     const long long lim = from_list ? st->n32 : st->nch;
     const double gub_prev = gb_key_value(st->gub_key);
     const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    unsigned* q = s_queue[threadIdx.x >> 5];
+    constexpr bool queue = QUEUE;
+    int qn = 0;   // warp-uniform queue length
+    int ops = 0;
+    unsigned long long key = ~0ull, nvalid = 0;
+    bool has = false;
     for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < lim; base += stride) {
-        long long idx = base + (threadIdx.x & 31);
-        unsigned long long key = ~0ull;
-        bool has = false, valid = false;
-        int ops = 0;
+        const long long idx = base + lane;
+        bool valid = false, need = false;
+        long long ci = 0;
         if (idx < lim) {
-            long long ci = from_list ? (long long)ch.list32[idx] : idx;
-            valid = eval64_tab_child(P, pool, par, Tb, ch, ci, sp, gub_prev, &key, &has, ops);
+            ci = from_list ? (long long)ch.list32[idx] : idx;
+            unsigned long long k2 = ~0ull;
+            bool h2 = false;
+            valid = eval64_tab_child<QUEUE>(P, pool, par, Tb, ch, ci, sp, gub_prev, &k2, &h2, ops, &need);
+            if (h2 && k2 < key) key = k2, has = true;
         }
-        warp_min_gub(key, has, st);
-        warp_add_ops(ops, &st->ops64);
-        unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
-        if ((threadIdx.x & 31) == 0 && nv) {
-            atomicAdd((unsigned long long*)&st->evals64, (unsigned long long)nv);
-            atomicAdd((unsigned long long*)&st->mids, (unsigned long long)nv);
-            if (!from_list) atomicAdd((unsigned long long*)&st->children, (unsigned long long)nv);
+        nvalid += __popc(__ballot_sync(0xffffffffu, valid));
+        if constexpr (!queue) continue;
+        const unsigned bal = __ballot_sync(0xffffffffu, need);
+        if (need) q[qn + __popc(bal & ((1u << lane) - 1u))] = (unsigned)ci;
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+            eval64_tab_mono(P, pool, par, Tb, ch, q[qn - 32 + lane], sp, ops);
+            qn -= 32;
+            __syncwarp();
         }
+    }
+    if (queue && lane < qn) eval64_tab_mono(P, pool, par, Tb, ch, q[lane], sp, ops);   // the rest of the queue
+    warp_min_gub(key, has, st);
+    warp_add_ops(ops, &st->ops64);
+    if (lane == 0 && nvalid) {
+        atomicAdd((unsigned long long*)&st->evals64, nvalid);
+        atomicAdd((unsigned long long*)&st->mids, nvalid);
+        if (!from_list) atomicAdd((unsigned long long*)&st->children, nvalid);
     }
 }
 
@@ -615,35 +758,167 @@ __global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval32_tab(GbProg P, GbPoo
 // per-thread kernels, so the results are identical.  Operation counts: the
 // work every lane repeats is counted once (lane 0), the shared work per lane.
 
-// First-order test, coordinates of the block spread over the lanes.
+// The partial-table entries of a split position's block, (coordinate,
+// sum)-major, staged in shared memory by the warp that evaluates a child:
+// jk range, partial-table base and digit field (shift | mask << 16).
+constexpr int GB_WMETA = 384;
+struct WMeta { int x, y, base, sm; };
+
+// Per-warp shared scratch of the one-child-per-warp kernels: the outer
+// expression's values and adjoints (written by lane 0, read by every lane
+// in the first-order test) and the staged partial-table entries.
+struct WScratch {
+    iv64* O64;
+    iv64* OA64;
+    iv32* O32;
+    iv32* OA32;
+    WMeta* meta;
+};
+template <typename T> __device__ __forceinline__ typename TabPrec<T>::I* ws_O(const WScratch& w);
+template <> __device__ __forceinline__ iv64* ws_O<double>(const WScratch& w) { return w.O64; }
+template <> __device__ __forceinline__ iv32* ws_O<float>(const WScratch& w) { return w.O32; }
+template <typename T> __device__ __forceinline__ typename TabPrec<T>::I* ws_OA(const WScratch& w);
+template <> __device__ __forceinline__ iv64* ws_OA<double>(const WScratch& w) { return w.OA64; }
+template <> __device__ __forceinline__ iv32* ws_OA<float>(const WScratch& w) { return w.OA32; }
+
+// The kernels' shared declarations: 4 warps per block.
+#define GB_WSCRATCH_DECL                                                   \
+    __shared__ WMeta s_meta[4][GB_WMETA];                                  \
+    __shared__ iv64 s_o64[4][GB_MAX_OREGS], s_oa64[4][GB_MAX_OREGS];       \
+    __shared__ iv32 s_o32[4][GB_MAX_OREGS], s_oa32[4][GB_MAX_OREGS];       \
+    const int wib_ = threadIdx.x >> 5;                                     \
+    const WScratch ws{s_o64[wib_], s_oa64[wib_], s_o32[wib_], s_oa32[wib_], s_meta[wib_]};
+
+__device__ __forceinline__ bool stage_meta(const GbProg& P, const GbSplitPos& SP, int cnt, WMeta* m, int lane) {
+    if (cnt > GB_WMETA) return false;
+    for (int e = lane; e < cnt; e += 32) {
+        const int2 rg = P.jk[SP.jk0 + e];
+        const GbJkD J = P.jkd[SP.jk0 + e];
+        m[e] = WMeta{rg.x, rg.y, J.base, (int)(unsigned short)J.shift | ((int)J.mask << 16)};
+    }
+    __syncwarp();
+    return true;
+}
+
+// tab_partial from the staged entries: the tabulated sums of every sum are
+// loaded together (one round of memory latency), then combined in the same
+// order as tab_partial.
+template <typename T>
+__device__ __forceinline__ typename TabPrec<T>::I tab_partial_m(const GbProg& P, const GbTabs& Tb,
+                                                                const typename TabPrec<T>::P2* tl,
+                                                                const typename TabPrec<T>::P2* td, const WMeta* M,
+                                                                int j, int c0, unsigned r,
+                                                                const typename TabPrec<T>::I* OA, unsigned unit,
+                                                                int& ops) {
+    typedef typename TabPrec<T>::I I;
+    typedef typename TabPrec<T>::P2 P2;
+    const WMeta* mj = M + (j - c0) * P.n_sum;
+    P2 e[GB_MAX_ISUM];
+#pragma unroll
+    for (int k = 0; k < GB_MAX_ISUM; k++) {
+        if (k < P.n_sum) {
+            const WMeta m = mj[k];
+            const int shift = (short)(m.sm & 0xffff);
+            if (m.x != m.y && shift >= 0) e[k] = td[m.base + (int)((r >> shift) & ((unsigned)m.sm >> 16))];
+        }
+    }
+    I g;
+    bool have = false;
+    for (int v = 0; v < P.n_var_leaves; v++) {
+        GbVarLeaf L = P.var_leaves[v];
+        if (L.coord != j) continue;
+        if (have) g = iadd(g, OA[L.reg]), ops += 2;
+        else g = OA[L.reg], have = true;
+    }
+#pragma unroll
+    for (int k = 0; k < GB_MAX_ISUM; k++) {
+        if (k >= P.n_sum) break;
+        const WMeta m = mj[k];
+        if (m.x == m.y) continue;
+        const int shift = (short)(m.sm & 0xffff);
+        I Dk;
+        if (shift >= 0) {
+            Dk = mk<T>(e[k].x, e[k].y);
+        } else {
+            for (int q = m.x; q < m.y; q++) {
+                const GbContrib C = P.contribs[q];
+                const unsigned combo = (r >> C.dshift) & C.mask;
+                const P2 t = tl[C.base + (int)combo * Tb.max_leaves];
+                const I v = mk<T>(t.x, t.y);
+                if (q > m.x) Dk = iadd(Dk, v), ops += 2;
+                else Dk = v;
+            }
+        }
+        I term;
+        if ((unit >> k) & 1u) term = Dk;
+        else term = imul(OA[P.sums[k].outer_reg], Dk), ops += 2;
+        if (have) g = iadd(g, term), ops += 2;
+        else g = term, have = true;
+    }
+    if (!have) g = mk<T>((T)0, (T)0);
+    return g;
+}
+
+// First-order test, coordinates of the block spread over the lanes (the
+// block's partial-table entries staged in shared memory when they fit).
+// The outer adjoints are computed by lane 0 from the outer values in the
+// warp's scratch and shared through it.
 template <typename T>
 __device__ __forceinline__ bool tab_mono_w(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
-                                           int blk, unsigned r, const View<double>& X64,
-                                           const typename TabPrec<T>::I* O, typename TabPrec<T>::I* OA,
+                                           int blk, unsigned r, const View<double>& X64, const WScratch& ws,
                                            int& red, int& par, int lane) {
     typedef typename TabPrec<T>::I I;
+    I* O = ws_O<T>(ws);
+    I* OA = ws_OA<T>(ws);
     unsigned unit = 1u;   // a single outer sum: its adjoint is [1, 1]
     if (!P.outer_sum) {
-        for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
-        OA[P.outer_root] = mk<T>((T)1, (T)1);
-        reverse_sweep<T>(P.outer, P.n_outer, O, OA, red);
-        unit = unit_sums(P, OA);
+        if (lane == 0) {
+            for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
+            OA[P.outer_root] = mk<T>((T)1, (T)1);
+            reverse_sweep<T>(P.outer, P.n_outer, O, OA, red);
+            unit = unit_sums(P, OA);
+        }
+        __syncwarp();
+        unit = __shfl_sync(0xffffffffu, unit, 0);
     }
     const int c0 = blk * P.B, c1 = min(P.n, c0 + P.B);
     const typename TabPrec<T>::P2* tl = leaf_tab<T>(Tb, p);
     const typename TabPrec<T>::P2* td = part_tab<T>(Tb, p);
     bool hit = false;
-    for (int j = c0 + lane; j < c1 && !hit; j += 32) {
-        const I g = tab_partial<T>(P, Tb, tl, td, SP, j, c0, r, OA, unit, par);
-        hit = mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi));
+    if (stage_meta(P, SP, (c1 - c0) * P.n_sum, ws.meta, lane)) {
+        for (int j = c0 + lane; j < c1; j += 32) {
+            const I g = tab_partial_m<T>(P, Tb, tl, td, ws.meta, j, c0, r, OA, unit, par);
+            hit |= mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi));
+        }
+    } else {
+        for (int j = c0 + lane; j < c1 && !hit; j += 32) {
+            const I g = tab_partial<T>(P, Tb, tl, td, SP, j, c0, r, OA, unit, par);
+            hit = mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi));
+        }
     }
+    __syncwarp();   // the scratch is reused by the warp's next child
     return __any_sync(0xffffffffu, hit);
+}
+
+// F from lane 0's sums (the outer expression evaluated by lane 0 into the
+// warp's scratch), broadcast to every lane.
+template <typename T, typename V>
+__device__ __forceinline__ typename TabPrec<T>::I outer_w(const GbProg& P, const V& X,
+                                                          const typename TabPrec<T>::I* sums, const WScratch& ws,
+                                                          int lane, int& red) {
+    typedef typename TabPrec<T>::I I;
+    I F{};
+    if (lane == 0) F = outer_value<T>(P, X, sums, ws_O<T>(ws), red);
+    __syncwarp();
+    F.lo = __shfl_sync(0xffffffffu, F.lo, 0);
+    F.hi = __shfl_sync(0xffffffffu, F.hi, 0);
+    return F;
 }
 
 __device__ __forceinline__ bool eval64_tab_child_w(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                    const GbTabs& Tb, const GbChildren& ch, long long ci,
                                                    const GbSplit& sp, double gub_prev, unsigned long long* gkey,
-                                                   bool* has_key, int& red, int& pops, int lane) {
+                                                   bool* has_key, int& red, int& pops, int lane, const WScratch& ws) {
     const ChildCtx c = child_ctx(par, ci, sp);
     const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
     if (spi < 0) {
@@ -659,7 +934,7 @@ __device__ __forceinline__ bool eval64_tab_child_w(const GbProg& P, const GbPool
     const MidView MX{X};
     const size_t rowbase = (size_t)c.p * Tb.max_rows, nbase = (size_t)c.p * Tb.tree_nodes;
     const size_t sbase = (size_t)c.p * Tb.max_srows;
-    iv64 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];
+    iv64 sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];   // lane 0's
     int dt = SP.seg0;
     for (int k = 0; k < P.n_sum; k++) {
         const GbSum S = P.sums[k];
@@ -675,22 +950,25 @@ __device__ __forceinline__ bool eval64_tab_child_w(const GbProg& P, const GbPool
                                     v[0] = iv64{a.x, a.y};
                                     v[1] = iv64{b.x, b.y};
                                 }, v2, cnt);
-            curF[g - dr.x] = v2[0];
-            curM[g - dr.x] = v2[1];
+            if (lane == 0) {
+                curF[g - dr.x] = v2[0];
+                curM[g - dr.x] = v2[1];
+            }
             red += 4 * (cnt > 0 ? cnt - 1 : 0);
         }
         const size_t nb = nbase + S.node0;
-        sums[k] = tab_path(S, dr, curF, [&](int i) { return TabPrec<double>::node(Tb, nb + i); }, red);
-        msums[k] = tab_path(S, dr, curM, [&](int i) { return mid_node(Tb, nb + i); }, red);
+        const iv64 a = tab_path_w(S, dr, curF, [&](int i) { return TabPrec<double>::node(Tb, nb + i); }, lane, red);
+        const iv64 b = tab_path_w(S, dr, curM, [&](int i) { return mid_node(Tb, nb + i); }, lane, red);
+        if (lane == 0) sums[k] = a, msums[k] = b;
     }
-    const iv64 Fm = outer_value<double>(P, MX, msums, O, red);
-    if (Fm.hi == Fm.hi) {
+    const iv64 Fm = outer_w<double>(P, MX, msums, ws, lane, red);
+    if (lane == 0 && Fm.hi == Fm.hi) {
         *gkey = gb_order_key(Fm.hi);
         *has_key = true;
     }
-    const iv64 F = outer_value<double>(P, X, sums, O, red);
-    bool keep = !(F.lo > gub_prev);
-    if (keep) keep = !tab_mono_w<double>(P, Tb, c.p, SP, blk, c.r, X, O, OA, red, pops, lane);
+    const iv64 F = outer_w<double>(P, X, sums, ws, lane, red);   // leaves the outer values of X in the scratch
+    bool keep = !(F.lo > gub_prev);   // the same in every lane
+    if (keep) keep = !tab_mono_w<double>(P, Tb, c.p, SP, blk, c.r, X, ws, red, pops, lane);
     if (lane == 0) {
         ch.flo[ci] = canon_lo(F.lo);
         ch.flag[ci] = keep ? 1 : 0;
@@ -704,6 +982,7 @@ __global__ void __launch_bounds__(128) k_eval64_tabw(GbProg P, GbPool pool, GbPa
     const long long lim = from_list ? st->n32 : st->nch;
     const double gub_prev = gb_key_value(st->gub_key);
     const int lane = threadIdx.x & 31;
+    GB_WSCRATCH_DECL
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     unsigned long long key = ~0ull;
     bool has = false;
@@ -713,7 +992,7 @@ __global__ void __launch_bounds__(128) k_eval64_tabw(GbProg P, GbPool pool, GbPa
         const long long ci = from_list ? (long long)ch.list32[w] : w;
         unsigned long long k2 = ~0ull;
         bool h2 = false;
-        if (eval64_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, &k2, &h2, red, pops, lane)) nv++;
+        if (eval64_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, &k2, &h2, red, pops, lane, ws)) nv++;
         if (h2 && k2 < key) key = k2, has = true;
     }
     warp_min_gub(key, has, st);
@@ -730,7 +1009,7 @@ __global__ void __launch_bounds__(128) k_eval64_tabw(GbProg P, GbPool pool, GbPa
 __device__ __forceinline__ int eval32_tab_child_w(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                   const GbTabs& Tb, const GbChildren& ch, long long ci,
                                                   const GbSplit& sp, double gub_prev, int& red, int& pops,
-                                                  int lane) {
+                                                  int lane, const WScratch& ws) {
     const ChildCtx c = child_ctx(par, ci, sp);
     const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
     if (lane == 0) {
@@ -747,7 +1026,7 @@ __device__ __forceinline__ int eval32_tab_child_w(const GbProg& P, const GbPool&
     const View<double> X64 = view64(pool, par, c, sp);
     const size_t rowbase = (size_t)c.p * Tb.max_rows, nbase = (size_t)c.p * Tb.tree_nodes;
     const size_t sbase = (size_t)c.p * Tb.max_srows;
-    iv32 O[GB_MAX_OREGS], OA[GB_MAX_OREGS], sums[GB_MAX_ISUM];
+    iv32 sums[GB_MAX_ISUM];   // lane 0's
     int dt = SP.seg0;
     for (int k = 0; k < P.n_sum; k++) {
         const GbSum S = P.sums[k];
@@ -755,19 +1034,22 @@ __device__ __forceinline__ int eval32_tab_child_w(const GbProg& P, const GbPool&
         iv32 cur[GB_TAB_MAX_DIRTY];
         for (int g = dr.x; g < dr.y; g++) {
             int cnt;
+            iv32 v;
             warp_group<iv32, 1>(P, SP, k, g, c.r, dt, lane,
                                 [&](const GbSeg& G, int at, iv32* v) {
                                     const float2 a = G.level ? Tb.ts32[sbase + at] : Tb.tv32[rowbase + at];
                                     v[0] = iv32{a.x, a.y};
-                                }, cur + (g - dr.x), cnt);
+                                }, &v, cnt);
+            if (lane == 0) cur[g - dr.x] = v;
             red += 2 * (cnt > 0 ? cnt - 1 : 0);
         }
         const size_t nb = nbase + S.node0;
-        sums[k] = tab_path(S, dr, cur, [&](int i) { return TabPrec<float>::node(Tb, nb + i); }, red);
+        const iv32 a = tab_path_w(S, dr, cur, [&](int i) { return TabPrec<float>::node(Tb, nb + i); }, lane, red);
+        if (lane == 0) sums[k] = a;
     }
-    const iv32 F = outer_value<float>(P, X, sums, O, red);
-    bool keep = !((double)F.lo > gub_prev);
-    if (keep) keep = !tab_mono_w<float>(P, Tb, c.p, SP, blk, c.r, X64, O, OA, red, pops, lane);
+    const iv32 F = outer_w<float>(P, X, sums, ws, lane, red);
+    bool keep = !((double)F.lo > gub_prev);   // the same in every lane
+    if (keep) keep = !tab_mono_w<float>(P, Tb, c.p, SP, blk, c.r, X64, ws, red, pops, lane);
     if (lane == 0) ch.flag32[ci] = keep ? 1 : 0;
     return keep ? 1 : 0;
 }
@@ -778,11 +1060,12 @@ __global__ void __launch_bounds__(128) k_eval32_tabw(GbProg P, GbPool pool, GbPa
     const long long lim = st->nch;
     const double gub_prev = gb_key_value(st->gub_key);
     const int lane = threadIdx.x & 31;
+    GB_WSCRATCH_DECL
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     int red = 0, pops = 0;
     unsigned long long nv = 0;
     for (long long ci = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; ci < lim; ci += nw)
-        if (eval32_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, red, pops, lane) >= 0) nv++;
+        if (eval32_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, red, pops, lane, ws) >= 0) nv++;
     warp_add_ops((lane == 0 ? red : 0) + pops, &st->ops32);
     if (lane == 0 && nv) {
         atomicAdd((unsigned long long*)&st->evals32, nv);
@@ -800,19 +1083,20 @@ __global__ void __launch_bounds__(128) k_eval3264_tabw(GbProg P, GbPool pool, Gb
     const long long lim = st->nch;
     const double gub_prev = gb_key_value(st->gub_key);
     const int lane = threadIdx.x & 31;
+    GB_WSCRATCH_DECL
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     int red32 = 0, pops32 = 0, red64 = 0, pops64 = 0;
     unsigned long long nv = 0, n32 = 0, key = ~0ull;
     bool has = false;
     for (long long ci = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; ci < lim; ci += nw) {
-        const int v = eval32_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, red32, pops32, lane);
+        const int v = eval32_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, red32, pops32, lane, ws);
         if (v < 0) continue;
         nv++;
         if (v == 0) continue;
         n32++;
         unsigned long long k2 = ~0ull;
         bool h2 = false;
-        eval64_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, &k2, &h2, red64, pops64, lane);
+        eval64_tab_child_w(P, pool, par, Tb, ch, ci, sp, gub_prev, &k2, &h2, red64, pops64, lane, ws);
         if (h2 && k2 < key) key = k2, has = true;
     }
     warp_min_gub(key, has, st);
@@ -851,6 +1135,7 @@ __global__ void __launch_bounds__(128) k_eval3264_batch(const GbEvalDesc* __rest
     __syncthreads();
     const long long total = off[nreq];
     const int lane = threadIdx.x & 31;
+    GB_WSCRATCH_DECL
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long u = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; u < total; u += nw) {
         int lo = 0, hi = nreq - 1;   // the problem q with off[q] <= u < off[q + 1]
@@ -869,14 +1154,15 @@ __global__ void __launch_bounds__(128) k_eval3264_batch(const GbEvalDesc* __rest
         unsigned long long nv = 0, n32 = 0, key = ~0ull;
         bool has = false;
         for (long long ci = c0; ci < c1; ci++) {
-            const int v = eval32_tab_child_w(d.P, d.pool, d.par, d.Tb, d.ch, ci, d.sp, gub_prev, red32, pops32, lane);
+            const int v = eval32_tab_child_w(d.P, d.pool, d.par, d.Tb, d.ch, ci, d.sp, gub_prev, red32, pops32, lane,
+                                             ws);
             if (v < 0) continue;
             nv++;
             if (v == 0) continue;
             n32++;
             unsigned long long k2 = ~0ull;
             bool h2 = false;
-            eval64_tab_child_w(d.P, d.pool, d.par, d.Tb, d.ch, ci, d.sp, gub_prev, &k2, &h2, red64, pops64, lane);
+            eval64_tab_child_w(d.P, d.pool, d.par, d.Tb, d.ch, ci, d.sp, gub_prev, &k2, &h2, red64, pops64, lane, ws);
             if (h2 && k2 < key) key = k2, has = true;
         }
         warp_min_gub(key, has, st);
@@ -915,10 +1201,10 @@ cudaError_t gb_launch_eval3264_batch(const GbEvalDesc* d_desc, int nreq, long lo
 
 cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                            long long K, const GbSplit& sp, GbState* st, cudaStream_t s) {
-    // row parts of a parent spread over blocks of PTAB_T threads, then one
-    // block per group tree
-    const int parts = pool.fp32 ? 4 : 3, kinds = pool.fp32 ? 3 : 2;
-    int row_blocks = (P.max_rows * parts + PTAB_T - 1) / PTAB_T;
+    // row parts of a parent, PTAB_ITEMS per one-warp block, then one block
+    // per group tree
+    const int parts = ptab_parts(pool), kinds = pool.fp32 ? 3 : 2;
+    int row_blocks = (P.max_rows * parts + PTAB_ITEMS - 1) / PTAB_ITEMS;
     if (row_blocks < 1) row_blocks = 1;
     k_ptab<<<dim3((unsigned)(row_blocks + P.n_sum * kinds), (unsigned)K), PTAB_T, 0, s>>>(P, pool, par, T, sp,
                                                                                           row_blocks, st);
@@ -936,7 +1222,8 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
     }
     unsigned g = grid_for(Cmax, 128);
     if (g > gb_sm_count() * GB_TAB_GRID) g = gb_sm_count() * GB_TAB_GRID;
-    k_eval64_tab<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
+    if (P.outer_sum) k_eval64_tab<true><<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
+    else k_eval64_tab<false><<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
     return cudaGetLastError();
 }
 

@@ -91,13 +91,17 @@ struct GbTabs {
     int warp;         // child kernels: 1 one child per warp, 0 one child per thread
 };
 
-// scratch for the three-phase scans
+// scratch for the scans
 struct GbScan {
-    int* tile_cnt;     // [3][max_tiles]
-    int* tile_off;     // [3][max_tiles]
+    int* tile_cnt;     // [3][max_tiles] tile counts (pool partition: aggregates)
+    int* tile_off;     // [3][max_tiles] tile offsets (pool partition: inclusive prefixes)
     unsigned* hist;    // [65536] radix-select histogram
+    unsigned long long* tile_flag;   // [max_tiles] pool partition: epoch << 2 | 1 aggregate / 2 prefix published
+    unsigned long long* stat_key;    // [GB_STAT_BLOCKS] per-block smallest active key (k_stats)
+    long long* stat_pos;             // [GB_STAT_BLOCKS] its last pool position in that block
     int max_tiles;
 };
+constexpr int GB_STAT_BLOCKS = 4096;   // grid cap of k_stats
 
 constexpr int GB_TILE = 1024;
 
@@ -125,7 +129,8 @@ cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEnt
 // Active count of the pool; count and GUB are read from the device state,
 // max_count bounds the grid.
 // Active count of the pool (read from the device state) for the next generation.
-cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, GbState* st, cudaStream_t s);
+cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, const GbScan& sc, GbState* st,
+                            cudaStream_t s);
 // Checkpoint: every entry of E[0, count) with its box (lo, hi: count x n), LB and cycling word.
 cudaError_t gb_launch_snapshot(const GbEntries& E, long long count, const GbPool& pool, double* lo, double* hi,
                                double* flo, int* cyc, cudaStream_t s);
