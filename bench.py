@@ -149,6 +149,8 @@ def _args():
     ap.add_argument("--n", type=int, default=50, help="paper workload: the dimension")
     ap.add_argument("--pool-mode", type=int, default=0, help="paper workload: 2 for block records")
     ap.add_argument("--max-children", type=int, default=0, help="children per generation (0: the workload's)")
+    ap.add_argument("--eval-mode", type=int, default=-1, help="child evaluation kernels (gb_options.eval_mode; "
+                    "-1: the workload's)")
     ap.add_argument("--split-m", type=int, default=0, help="pieces per split coordinate (0: the workload's)")
     ap.add_argument("--split-d", type=int, default=0, help="coordinates split per generation (0: the workload's)")
     ap.add_argument("--no-nested", action="store_true",
@@ -520,6 +522,10 @@ def _options(a, w, local, override=True):
             opts["pool_mode"] = w["pool_mode"]
     if override and a.max_gens > 0:
         opts["max_generations"] = a.max_gens
+    if override and a.eval_mode >= 0:
+        opts["eval_mode"] = a.eval_mode
+    elif w.get("eval_mode") is not None:
+        opts["eval_mode"] = w["eval_mode"]
     return opts
 
 

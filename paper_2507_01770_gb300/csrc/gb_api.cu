@@ -496,6 +496,15 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
                          (e = alloc(&T.nf32, nodes, A))))
                 return bad(e, "allocate term tables");
             T.warp = opt.eval_mode == 4 ? 1 : opt.eval_mode == 3 ? 0 : (gb_warp_per_child(p->Cmax) ? 1 : 0);
+            T.max_sum_nodes = 1;
+            for (const GbSum& S : Hh.sums) T.max_sum_nodes = std::max(T.max_sum_nodes, (int)S.nnodes);
+            T.tree_smem = (size_t)T.max_sum_nodes * sizeof(double2) <= 48 * 1024 ? 1 : 0;   // no opt-in needed
+            if (T.warp) {   // per-child sums and dirty group values (k_child_sums)
+                const size_t cs = (size_t)p->Cmax * (P.n_sum > 0 ? P.n_sum : 1), cg = (size_t)p->Cmax * GB_CG;
+                if ((e = alloc(&T.cs64, cs, A)) || (e = alloc(&T.csm64, cs, A)) || (e = alloc(&T.cg64, cg, A)) ||
+                    (e = alloc(&T.cgm64, cg, A)) || (fp32 && ((e = alloc(&T.cs32, cs, A)) || (e = alloc(&T.cg32, cg, A)))))
+                    return bad(e, "allocate child sums");
+            }
             p->use_tabs = true;
         }
     }

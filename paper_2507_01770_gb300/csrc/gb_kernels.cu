@@ -439,11 +439,36 @@ __device__ __forceinline__ PartFlags part_flags1(const GbEntries& E, long long q
     return f;
 }
 
+// Exclusive block scan of one 64-bit value per thread (PT threads; packed
+// counters add field by field as long as no field overflows); the block's
+// total is left in sh[PT / 32].
+__device__ __forceinline__ unsigned long long block_scan_packed(unsigned long long v, unsigned long long* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) sh[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long x = lane < PT / 32 ? sh[lane] : 0, xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        if (lane < PT / 32) sh[lane] = xi - x;   // exclusive warp offsets
+        if (lane == PT / 32 - 1) sh[PT / 32] = xi;
+    }
+    __syncthreads();
+    return sh[w] + inc - v;
+}
+
 __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbState* st, int* agg, int* inc,
                                                 int max_tiles, unsigned long long* flag, GbEntries En,
                                                 GbParents par, unsigned* freel) {
     if (st->halt) return;
-    __shared__ int sw[PT / 32 + 1];
+    __shared__ unsigned long long s_scan[PT / 32 + 1];
     __shared__ long long s_tile;
     __shared__ long long s_ex[3];
     const long long count = st->pool;
@@ -479,60 +504,101 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
         const long long tile = s_tile;
         if (tile >= nt) break;
         const long long base = tile * GB_TILE;
-        PartFlags f[GB_TILE / PT];
-        int rd[GB_TILE / PT], rb[GB_TILE / PT], rt[GB_TILE / PT];
-        int cd = 0, cb = 0, ct = 0, t;
+        // thread t classifies entries base + 4t .. base + 4t + 3; the three
+        // counts travel packed (21 bits each) through one block scan
+        constexpr int PER = GB_TILE / PT;
+        const long long q0 = base + (long long)PER * threadIdx.x;
+        PartFlags f[PER];
 #pragma unroll
-        for (int r = 0; r < GB_TILE / PT; r++) {
-            f[r] = part_flags1(E, base + r * PT + threadIdx.x, count, gub, thr, T, mode, spos);
-            rd[r] = cd + block_prefix<PT>(f[r].drop, sw, &t);
-            cd += t;
-            rb[r] = cb + block_prefix<PT>(f[r].below, sw, &t);
-            cb += t;
-            rt[r] = ct + block_prefix<PT>(f[r].tie, sw, &t);
-            ct += t;
-        }
-        if (threadIdx.x == 0) {
-            long long ed = 0, eb = 0, et = 0;
-            volatile unsigned long long* vf = flag;
-            if (tile > 0) {
-                agg[tile] = cd;
-                agg[max_tiles + tile] = cb;
-                agg[2 * max_tiles + tile] = ct;
-                __threadfence();
-                vf[tile] = (epoch << 2) | GB_FLAG_AGG;
-                bool bad = false;
-                for (long long j = tile - 1; j >= 0;) {
-                    unsigned long long fl;
-                    long long spins = 0;
-                    while (((fl = vf[j]) >> 2) != epoch)
-                        if (++spins > GB_SPIN_LIMIT) { bad = true; break; }
-                    if (bad) break;
-                    __threadfence();
-                    const volatile int* vs = (fl & 3) == GB_FLAG_INC ? inc : agg;
-                    ed += vs[j];
-                    eb += vs[max_tiles + j];
-                    et += vs[2 * max_tiles + j];
-                    if ((fl & 3) == GB_FLAG_INC) break;
-                    j--;
-                }
-                if (bad) atomicOr(&st->error, 4);
+        for (int u = 0; u < PER; u++) f[u] = part_flags1(E, q0 + u, count, gub, thr, T, mode, spos);
+        unsigned long long mine = 0;
+#pragma unroll
+        for (int u = 0; u < PER; u++)
+            mine += (unsigned long long)f[u].drop | ((unsigned long long)f[u].below << 21) |
+                    ((unsigned long long)f[u].tie << 42);
+        const unsigned long long before = block_scan_packed(mine, s_scan);   // exclusive
+        const unsigned long long total = s_scan[PT / 32];
+        int rd[PER], rb[PER], rt[PER];
+        {
+            unsigned long long run = before;
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                rd[u] = (int)(run & 0x1fffff);
+                rb[u] = (int)((run >> 21) & 0x1fffff);
+                rt[u] = (int)(run >> 42);
+                run += (unsigned long long)f[u].drop | ((unsigned long long)f[u].below << 21) |
+                       ((unsigned long long)f[u].tie << 42);
             }
-            inc[tile] = (int)(ed + cd);
-            inc[max_tiles + tile] = (int)(eb + cb);
-            inc[2 * max_tiles + tile] = (int)(et + ct);
-            __threadfence();
-            vf[tile] = (epoch << 2) | GB_FLAG_INC;
-            s_ex[0] = ed;
-            s_ex[1] = eb;
-            s_ex[2] = et;
-            if (tile == nt - 1) totals(ed + cd, eb + cb, et + ct);
+        }
+        const int cd = (int)(total & 0x1fffff), cb = (int)((total >> 21) & 0x1fffff), ct = (int)(total >> 42);
+        // publication and look-back by warp 0: its lanes inspect 32
+        // predecessors at a time (the nearest inclusive prefix ends the walk,
+        // the aggregates after it are summed)
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            volatile unsigned long long* vf = flag;
+            volatile int* va = agg;
+            volatile int* vi = inc;
+            long long ed = 0, eb = 0, et = 0;
+            if (tile > 0) {
+                if (lane == 0) {
+                    agg[tile] = cd;
+                    agg[max_tiles + tile] = cb;
+                    agg[2 * max_tiles + tile] = ct;
+                    __threadfence();
+                    vf[tile] = (epoch << 2) | GB_FLAG_AGG;
+                }
+                bool bad = false, done = false;
+                long long top = tile - 1;   // the window is [top - 31, top]
+                while (!done) {
+                    const long long j = top - lane;
+                    unsigned long long fl = epoch << 2 | GB_FLAG_INC;   // lanes before tile 0: an empty prefix
+                    long long spins = 0;
+                    if (j >= 0)
+                        while (((fl = vf[j]) >> 2) != epoch)
+                            if (++spins > GB_SPIN_LIMIT) { bad = true; break; }
+                    if (__any_sync(0xffffffffu, bad)) { bad = true; break; }
+                    __threadfence();
+                    const unsigned incm = __ballot_sync(0xffffffffu, (fl & 3) == GB_FLAG_INC);
+                    const int stop = incm ? __ffs(incm) - 1 : 31;   // the nearest inclusive prefix (or the window end)
+                    long long xd = 0, xb = 0, xt = 0;
+                    if (j >= 0 && lane <= stop) {
+                        const bool isinc = (fl & 3) == GB_FLAG_INC;
+                        const volatile int* vs = isinc ? vi : va;
+                        xd = vs[j];
+                        xb = vs[max_tiles + j];
+                        xt = vs[2 * max_tiles + j];
+                    }
+                    for (int o = 16; o; o >>= 1) {
+                        xd += __shfl_down_sync(0xffffffffu, xd, o);
+                        xb += __shfl_down_sync(0xffffffffu, xb, o);
+                        xt += __shfl_down_sync(0xffffffffu, xt, o);
+                    }
+                    ed += __shfl_sync(0xffffffffu, xd, 0);
+                    eb += __shfl_sync(0xffffffffu, xb, 0);
+                    et += __shfl_sync(0xffffffffu, xt, 0);
+                    done = incm != 0 || top - 31 < 0;
+                    top -= 32;
+                }
+                if (bad && lane == 0) atomicOr(&st->error, 4);
+            }
+            if (lane == 0) {
+                inc[tile] = (int)(ed + cd);
+                inc[max_tiles + tile] = (int)(eb + cb);
+                inc[2 * max_tiles + tile] = (int)(et + ct);
+                __threadfence();
+                vf[tile] = (epoch << 2) | GB_FLAG_INC;
+                s_ex[0] = ed;
+                s_ex[1] = eb;
+                s_ex[2] = et;
+                if (tile == nt - 1) totals(ed + cd, eb + cb, et + ct);
+            }
         }
         __syncthreads();
         const long long od = s_ex[0], ob = s_ex[1], ot = s_ex[2];
 #pragma unroll
-        for (int r = 0; r < GB_TILE / PT; r++) {
-            const long long q = base + r * PT + threadIdx.x;
+        for (int r = 0; r < PER; r++) {
+            const long long q = q0 + r;
             if (q >= count) continue;
             const long long gd = od + rd[r], gb = ob + rb[r], gt = ot + rt[r];
             const long long sel_before = gb + max(0LL, gt - (Ti - need));
@@ -813,8 +879,18 @@ __global__ void k_cc_scatter(GbChildren ch, int mode, const GbState* st, const i
 // g - dr.x].
 constexpr int GB_SHG = GB_MAX_ISUM * GB_TAB_MAX_DIRTY;
 __device__ __forceinline__ void tab_dirty_groups(const GbProg& P, const GbPool& pool, const GbTabs& Tb,
-                                                 const ChildCtx& c, int lane, double2* shF, double2* shM,
-                                                 float2* sh32) {
+                                                 const ChildCtx& c, long long ci, int lane, double2* shF,
+                                                 double2* shM, float2* sh32) {
+    if (Tb.cg64) {   // computed by k_child_sums: copy the slots
+        for (int q = lane; q < GB_SHG; q += 32) {
+            const size_t at = (size_t)ci * GB_CG + q;
+            shF[q] = Tb.cg64[at];
+            shM[q] = Tb.cgm64[at];
+            if (pool.fp32) sh32[q] = Tb.cg32[at];
+        }
+        __syncwarp();
+        return;
+    }
     const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
     const int blk = c.info.z;
     const size_t rowbase = (size_t)c.p * Tb.max_rows, sbase = (size_t)c.p * Tb.max_srows;
@@ -862,7 +938,7 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
     const long long nfree = st->nfree, bump = st->bump, kept_old = st->kept_old;
     const long long ci = ch.surv[s];
     ChildCtx c = child_ctx(par, ci, sp);
-    if (tab) tab_dirty_groups(P, pool, Tb, c, lane, shF, shM, sh32);
+    if (tab) tab_dirty_groups(P, pool, Tb, c, ci, lane, shF, shM, sh32);
     const unsigned ns = (s < nfree) ? pool.freel[nfree - 1 - s] : (unsigned)(bump + (s - nfree));
     const int n = pool.n;
     View<double> X = view64(pool, par, c, sp);
@@ -1035,7 +1111,7 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
     const long long rnf = st->rec_nfree, rbump = st->rec_bump;
     const long long ci = ch.surv[s];
     const ChildCtx c = child_ctx(par, ci, sp);
-    if (tab) tab_dirty_groups(P, pool, Tb, c, lane, shF, shM, sh32);
+    if (tab) tab_dirty_groups(P, pool, Tb, c, ci, lane, shF, shM, sh32);
     const unsigned ns = (s < nfree) ? pool.freel[nfree - 1 - s] : (unsigned)(bump + (s - nfree));
     const int n = pool.n, nb = pool.nb, B = pool.B, GPB = pool.GPB, nrec = pool.nrec;
     const int blk = c.info.z;
@@ -1580,6 +1656,10 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
         if ((e = gb_launch_ptab(P, pool, par, *tabs, G.K, sp, st, s)) != cudaSuccess) return e;
         gb_launch_count++;
         if ((e = gb_launch_ptab_d(P, pool, par, *tabs, G.K, P.B, st, s)) != cudaSuccess) return e;
+        if (tabs->cs64) {
+            gb_launch_count++;
+            if ((e = gb_launch_child_sums(P, par, *tabs, sp, Cmax, G.fp32, st, s)) != cudaSuccess) return e;
+        }
     }
     if (part == 1) {   // up to the child evaluation (a fused launch over many problems follows)
         if (nlaunch) *nlaunch = gb_launch_count - n0;

@@ -59,15 +59,53 @@ __device__ __forceinline__ iv64 mid_node(const GbTabs& T, size_t i) { double2 v 
 // diverge and run one after the other), spread over the SMs.
 // Blocks x >= row_blocks: one group tree of the parent's cached sums each
 // (sum k, kind: F, midpoint, FP32), level by level.
-constexpr int PTAB_T = 32;
-constexpr int PTAB_ITEMS = 1;
+constexpr int PTAB_T = 128;
+constexpr int PTAB_ITEMS = 4;        // row parts per block: one per warp, in its lane 0
 constexpr int PTAB_SMEM_DT = 256;   // dirty terms staged in shared memory for the row lookup
 
 __host__ __device__ __forceinline__ int ptab_parts(const GbPool& pool) { return pool.fp32 ? 3 : 2; }
 
+// One level-major pairwise group tree: the level-0 nodes (the parent's
+// cached group sums) are in a[0, ngroups); every level is formed from the one
+// below it.  `a` is shared memory when the tree fits (one memory round trip
+// for the whole tree), else the output itself.
+template <typename I, typename P2>
+__device__ __forceinline__ void build_tree(P2* a, int ngroups, int& tops) {
+    int off = 0;
+    for (int mL = ngroups; mL > 1; mL = (mL + 1) / 2) {
+        const int mN = (mL + 1) / 2;
+        for (int q = threadIdx.x; q < mN; q += blockDim.x) {
+            const P2 x = a[off + 2 * q];
+            I v = mk<decltype(x.x)>(x.x, x.y);
+            if (2 * q + 1 < mL) {
+                const P2 y = a[off + 2 * q + 1];
+                v = iadd(v, mk<decltype(y.x)>(y.x, y.y));
+                tops += 2;
+            }
+            P2 o;
+            o.x = v.lo;
+            o.y = v.hi;
+            a[off + mL + q] = o;
+        }
+        __syncthreads();
+        off += mL;
+    }
+}
+
+template <typename I, typename P2, typename C>
+__device__ __forceinline__ void tree_job(const GbSum& S, const C& cache, P2* out, P2* sm, bool in_smem, int& tops) {
+    P2* a = in_smem ? sm : out;
+    for (int g = threadIdx.x; g < S.ngroups; g += blockDim.x) a[g] = cache[S.group0 + g];
+    __syncthreads();
+    build_tree<I>(a, S.ngroups, tops);
+    if (in_smem)
+        for (int i = threadIdx.x; i < S.nnodes; i += blockDim.x) out[i] = sm[i];
+}
+
 __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp,
                                                  int row_blocks, GbState* st) {
     if (st->halt) return;
+    extern __shared__ double2 s_tree[];   // T.max_sum_nodes entries when the trees fit
     const long long p = blockIdx.y;
     if (p >= st->parents) return;
     const int4 info = par.info[p];
@@ -82,43 +120,11 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
         const int k = job % P.n_sum, kind = job / P.n_sum;
         const GbSum S = P.sums[k];
         const size_t nb = (size_t)p * T.tree_nodes + S.node0;
-        const CacheRef<double2> cf = cache64(pool, P, slot, 0), cm = cache64(pool, P, slot, 1);
-        const CacheRef<float2> c32 = cache32(pool, P, slot);
-        for (int g = threadIdx.x; g < S.ngroups; g += blockDim.x) {
-            if (kind == 0) T.nf64[nb + g] = cf[S.group0 + g];
-            else if (kind == 1) T.nm64[nb + g] = cm[S.group0 + g];
-            else T.nf32[nb + g] = c32[S.group0 + g];
-        }
-        __syncthreads();
-        int off = 0, tops = 0;
-        for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
-            const int mN = (mL + 1) / 2;
-            for (int q = threadIdx.x; q < mN; q += blockDim.x) {
-                const size_t a = nb + off + 2 * q, c = nb + off + mL + q;
-                if (kind == 2) {
-                    float2 x = T.nf32[a];
-                    iv32 v{x.x, x.y};
-                    if (2 * q + 1 < mL) {
-                        float2 y = T.nf32[a + 1];
-                        v = iadd(v, iv32{y.x, y.y});
-                        tops += 2;
-                    }
-                    T.nf32[c] = make_float2(v.lo, v.hi);
-                } else {
-                    double2* arr = kind == 0 ? T.nf64 : T.nm64;
-                    double2 x = arr[a];
-                    iv64 v{x.x, x.y};
-                    if (2 * q + 1 < mL) {
-                        double2 y = arr[a + 1];
-                        v = iadd(v, iv64{y.x, y.y});
-                        tops += 2;
-                    }
-                    arr[c] = make_double2(v.lo, v.hi);
-                }
-            }
-            __syncthreads();
-            off += mL;
-        }
+        const bool in_smem = T.tree_smem != 0;
+        int tops = 0;
+        if (kind == 0) tree_job<iv64>(S, cache64(pool, P, slot, 0), T.nf64 + nb, s_tree, in_smem, tops);
+        else if (kind == 1) tree_job<iv64>(S, cache64(pool, P, slot, 1), T.nm64 + nb, s_tree, in_smem, tops);
+        else tree_job<iv32>(S, cache32(pool, P, slot), T.nf32 + nb, (float2*)s_tree, in_smem, tops);
         warp_add_ops(tops, kind == 2 ? &st->ops32 : &st->ops64);
         return;
     }
@@ -132,7 +138,8 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
     const size_t o = (size_t)p * sp.dmax * (sp.m + 1);
     const int parts = ptab_parts(pool);
     int ops = 0, ops32 = 0;
-    for (int item = blockIdx.x * PTAB_ITEMS + threadIdx.x; threadIdx.x < PTAB_ITEMS && item < SP.tab_entries * parts;
+    const int wib = threadIdx.x >> 5;
+    for (int item = blockIdx.x * PTAB_ITEMS + wib; (threadIdx.x & 31) == 0 && item < SP.tab_entries * parts;
          item += row_blocks * PTAB_ITEMS) {
         const int row = item / parts, part = item - row * parts;
         // the dirty term owning this row (rows are contiguous per term)
@@ -205,10 +212,21 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
 // k_ptab_d: per parent (blockIdx.y), from the term rows of k_ptab (runs
 // after it): (1) the partial tables: for each (coordinate of the block, sum)
 // tabulated by the layout and each digit combination of its bits, the serial
-// sum of the leaf adjoints of its contributions (the order tab_partial uses);
-// (2) the segment tables: for each term-tree segment of level >= 1 and each
-// combination of its digit bits, the in-place pairwise sum of its terms (F,
-// midpoint, FP32).
+// sum of the leaf adjoints of its contributions (the order tab_partial uses),
+// one thread per entry; (2) the segment tables: for each term-tree segment
+// of level >= 1 and each combination of its digit bits, the in-place
+// pairwise sum of its 2^level terms (F, midpoint, FP32), one warp per entry.
+// A segment is an aligned power-of-two block, so its pairwise tree is a
+// perfect binary tree: lane i holds term i (or, above 32 terms, the pairwise
+// sum of its aligned run of terms) and at level s lane i adds lane i + s --
+// the left node plus the right node, as the serial tree does, in log2 steps
+// instead of 2^level dependent ones.
+template <typename I> __device__ __forceinline__ I shfl_down_iv(I v, int d) {
+    v.lo = __shfl_down_sync(0xffffffffu, v.lo, d);
+    v.hi = __shfl_down_sync(0xffffffffu, v.hi, d);
+    return v;
+}
+
 __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents par, GbTabs T,
                                                 GbState* st) {
     if (st->halt) return;
@@ -223,43 +241,10 @@ __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents
     const double2* tl = T.tl64 + (size_t)p * T.max_rows * T.max_leaves;
     const float2* tl32 = pool.fp32 ? T.tl32 + (size_t)p * T.max_rows * T.max_leaves : nullptr;
     const int nd_items = nent << GB_TAB_DBITS;
+    const int lane = threadIdx.x & 31;
     int ops = 0, ops32 = 0;
-    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nd_items + (SP.nseg << GB_TAB_SBITS);
-         item += gridDim.x * blockDim.x) {
-        if (item >= nd_items) {   // segment table entry
-            const int si = (item - nd_items) >> GB_TAB_SBITS, c = (item - nd_items) & ((1 << GB_TAB_SBITS) - 1);
-            const GbSeg G = P.segs[SP.seg0 + si];
-            if (G.level == 0 || c > (int)G.mask) continue;
-            const unsigned r = (unsigned)c << G.shift;
-            const size_t rb = (size_t)p * T.max_rows;
-            Tree<iv64> tf, tm;
-            Tree<iv32> t32;
-            tf.init();
-            tm.init();
-            t32.init();
-            for (int t = 0; t < (1 << G.level); t++) {
-                const GbDTerm D = P.dterms[SP.dterm0 + G.dterm + t];
-                const size_t at = rb + D.row + ((r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u));
-                const double2 a = T.tv64[at], b = T.tm64[at];
-                tf.push(iv64{a.x, a.y});
-                tm.push(iv64{b.x, b.y});
-                if (tl32) {
-                    const float2 f = T.tv32[at];
-                    t32.push(iv32{f.x, f.y});
-                }
-            }
-            ops += 4 * ((1 << G.level) - 1);   // F and midpoint trees
-            if (tl32) ops32 += 2 * ((1 << G.level) - 1);
-            const size_t o = (size_t)p * T.max_srows + G.base + c;
-            const iv64 vf = tf.result(), vm = tm.result();
-            T.ts64[o] = make_double2(vf.lo, vf.hi);
-            T.tsm64[o] = make_double2(vm.lo, vm.hi);
-            if (tl32) {
-                const iv32 v32 = t32.result();
-                T.ts32[o] = make_float2(v32.lo, v32.hi);
-            }
-            continue;
-        }
+    // (1) partial tables
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < nd_items; item += gridDim.x * blockDim.x) {
         const int e = item >> GB_TAB_DBITS, c = item & ((1 << GB_TAB_DBITS) - 1);
         const GbJkD J = P.jkd[SP.jk0 + e];
         if (J.shift < 0 || c > (int)J.mask) continue;
@@ -284,6 +269,57 @@ __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents
         const size_t o = (size_t)p * T.max_drows + J.base + c;
         T.td64[o] = make_double2(D.lo, D.hi);
         if (tl32) T.td32[o] = make_float2(D32.lo, D32.hi);
+    }
+    // (2) segment tables
+    const int nw_items = SP.nseg << GB_TAB_SBITS;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const size_t rb = (size_t)p * T.max_rows;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw_items; w += nwarps) {
+        const int si = w >> GB_TAB_SBITS, c = w & ((1 << GB_TAB_SBITS) - 1);
+        const GbSeg G = P.segs[SP.seg0 + si];
+        if (G.level == 0 || c > (int)G.mask) continue;   // the same for the whole warp
+        const unsigned r = (unsigned)c << G.shift;
+        const int L = G.level, sub = L > 5 ? L - 5 : 0, width = 1 << (L - sub);
+        iv64 f{0.0, 0.0}, m{0.0, 0.0};
+        iv32 f32{0.f, 0.f};
+        if (lane < width) {
+            Tree<iv64> tf, tm;
+            Tree<iv32> t32;
+            tf.init();
+            tm.init();
+            t32.init();
+            for (int t = lane << sub; t < (lane + 1) << sub; t++) {
+                const GbDTerm D = P.dterms[SP.dterm0 + G.dterm + t];
+                const size_t at = rb + D.row + ((r >> D.dshift) & ((1u << (D.w * P.mshift)) - 1u));
+                const double2 a = T.tv64[at], b = T.tm64[at];
+                tf.push(iv64{a.x, a.y});
+                tm.push(iv64{b.x, b.y});
+                if (tl32) {
+                    const float2 x = T.tv32[at];
+                    t32.push(iv32{x.x, x.y});
+                }
+            }
+            f = tf.result();
+            m = tm.result();
+            if (tl32) f32 = t32.result();
+        }
+        for (int d = 1; d < width; d <<= 1) {
+            const iv64 of = shfl_down_iv(f, d), om = shfl_down_iv(m, d);
+            const iv32 o32 = shfl_down_iv(f32, d);
+            if ((lane & (2 * d - 1)) == 0) {
+                f = iadd(f, of);
+                m = iadd(m, om);
+                if (tl32) f32 = iadd(f32, o32);
+            }
+        }
+        if (lane == 0) {
+            ops += 4 * ((1 << L) - 1);   // F and midpoint trees
+            if (tl32) ops32 += 2 * ((1 << L) - 1);
+            const size_t o = (size_t)p * T.max_srows + G.base + c;
+            T.ts64[o] = make_double2(f.lo, f.hi);
+            T.tsm64[o] = make_double2(m.lo, m.hi);
+            if (tl32) T.ts32[o] = make_float2(f32.lo, f32.hi);
+        }
     }
     warp_add_ops(ops, &st->ops64);   // one atomic per warp (every lane reaches here)
     warp_add_ops(ops32, &st->ops32);
@@ -394,6 +430,82 @@ __device__ __forceinline__ I tab_path_w(const GbSum& S, int2 dr, I* cur, N node,
         off += mL;
     }
     return cur[0];   // defined in lane 0
+}
+
+// ---------------------------------------------------------------------------
+// k_child_sums (one child per warp): every child's sums before the child
+// kernel, one thread per (child, sum, kind) -- kind 0 F, 1 midpoint, 2 FP32.
+// A thread takes its sum's dirty groups from the term-tree segments (the
+// binary counter over the segments in order) and the path of the group tree
+// above them (tab_path), the same operations in the same order as the child
+// kernels' own assembly, so the same values; it stores the dirty group
+// values too, for the materialisation of the survivors.  Consecutive threads
+// are consecutive children of the same (sum, kind), so a warp follows one
+// control path; the ~10^4 short chains run side by side instead of one
+// child's chains one after another in a warp.
+template <typename I, typename P2>
+__device__ __forceinline__ void child_sum(const GbProg& P, const GbSplitPos& SP, int k, int blk, unsigned r,
+                                          const P2* trow, const P2* tseg, const P2* nodes, I* gout, I* sout,
+                                          int& ops) {
+    const GbSum S = P.sums[k];
+    const int2 dr = P.dirty[blk * P.n_sum + k];
+    int sg = SP.seg0;
+    const int send = SP.seg0 + SP.nseg;
+    while (sg < send) {   // the run of (k, first dirty group): segments are ordered by sum, group, term
+        const GbSeg G = P.segs[sg];
+        if (G.sum > k || (G.sum == k && G.group >= dr.x)) break;
+        sg++;
+    }
+    I cur[GB_TAB_MAX_DIRTY];
+    for (int g = dr.x; g < dr.y; g++) {
+        Tree<I> tr;
+        tr.init();
+        int ns = 0;
+        while (sg < send) {
+            const GbSeg G = P.segs[sg];
+            if (G.sum != k || G.group != g) break;
+            const int at = G.base + (int)((r >> G.shift) & G.mask);
+            const P2 v = G.level ? tseg[at] : trow[at];
+            tr.push_level(mk<decltype(v.x)>(v.x, v.y), G.level);
+            ns++;
+            sg++;
+        }
+        ops += 2 * (ns > 0 ? ns - 1 : 0);
+        cur[g - dr.x] = tr.result();
+        gout[k * GB_TAB_MAX_DIRTY + (g - dr.x)] = cur[g - dr.x];
+    }
+    *sout = tab_path(S, dr, cur, [&](int i) { const P2 v = nodes[S.node0 + i]; return mk<decltype(v.x)>(v.x, v.y); },
+                     ops);
+}
+
+__global__ void __launch_bounds__(128) k_child_sums(GbProg P, GbParents par, GbTabs Tb, GbSplit sp, long long Cmax,
+                                                    int kinds, GbState* st) {
+    if (st->halt) return;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long ci = t % Cmax, rest = t / Cmax;
+    const int k = (int)(rest % (P.n_sum > 0 ? P.n_sum : 1)), kind = (int)(rest / (P.n_sum > 0 ? P.n_sum : 1));
+    int ops = 0;
+    if (P.n_sum > 0 && kind < kinds && ci < st->nch) {
+        const ChildCtx c = child_ctx(par, ci, sp);
+        const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
+        if (spi >= 0) {
+            const GbSplitPos SP = P.sps[spi];
+            const size_t rowb = (size_t)c.p * Tb.max_rows, segb = (size_t)c.p * Tb.max_srows,
+                         nodeb = (size_t)c.p * Tb.tree_nodes;
+            const size_t so = (size_t)ci * P.n_sum + k, go = (size_t)ci * GB_CG;
+            if (kind == 0)
+                child_sum<iv64>(P, SP, k, c.info.z, c.r, Tb.tv64 + rowb, Tb.ts64 + segb, Tb.nf64 + nodeb,
+                                (iv64*)(Tb.cg64 + go), (iv64*)(Tb.cs64 + so), ops);
+            else if (kind == 1)
+                child_sum<iv64>(P, SP, k, c.info.z, c.r, Tb.tm64 + rowb, Tb.tsm64 + segb, Tb.nm64 + nodeb,
+                                (iv64*)(Tb.cgm64 + go), (iv64*)(Tb.csm64 + so), ops);
+            else
+                child_sum<iv32>(P, SP, k, c.info.z, c.r, Tb.tv32 + rowb, Tb.ts32 + segb, Tb.nf32 + nodeb,
+                                (iv32*)(Tb.cg32 + go), (iv32*)(Tb.cs32 + so), ops);
+        }
+    }
+    warp_add_ops(kind < 2 ? ops : 0, &st->ops64);
+    warp_add_ops(kind == 2 ? ops : 0, &st->ops32);
 }
 
 // Sum k of a child (FP32 tables): dirty group values from the term-tree
@@ -936,6 +1048,14 @@ __device__ __forceinline__ bool eval64_tab_child_w(const GbProg& P, const GbPool
     const size_t sbase = (size_t)c.p * Tb.max_srows;
     iv64 sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];   // lane 0's
     int dt = SP.seg0;
+    if (Tb.cs64) {   // computed by k_child_sums
+        if (lane == 0)
+            for (int k = 0; k < P.n_sum; k++) {
+                const double2 a = Tb.cs64[(size_t)ci * P.n_sum + k], b = Tb.csm64[(size_t)ci * P.n_sum + k];
+                sums[k] = iv64{a.x, a.y};
+                msums[k] = iv64{b.x, b.y};
+            }
+    } else
     for (int k = 0; k < P.n_sum; k++) {
         const GbSum S = P.sums[k];
         const int2 dr = P.dirty[blk * P.n_sum + k];
@@ -1028,6 +1148,13 @@ __device__ __forceinline__ int eval32_tab_child_w(const GbProg& P, const GbPool&
     const size_t sbase = (size_t)c.p * Tb.max_srows;
     iv32 sums[GB_MAX_ISUM];   // lane 0's
     int dt = SP.seg0;
+    if (Tb.cs32) {   // computed by k_child_sums
+        if (lane == 0)
+            for (int k = 0; k < P.n_sum; k++) {
+                const float2 a = Tb.cs32[(size_t)ci * P.n_sum + k];
+                sums[k] = iv32{a.x, a.y};
+            }
+    } else
     for (int k = 0; k < P.n_sum; k++) {
         const GbSum S = P.sums[k];
         const int2 dr = P.dirty[blk * P.n_sum + k];
@@ -1201,13 +1328,13 @@ cudaError_t gb_launch_eval3264_batch(const GbEvalDesc* d_desc, int nreq, long lo
 
 cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                            long long K, const GbSplit& sp, GbState* st, cudaStream_t s) {
-    // row parts of a parent, PTAB_ITEMS per one-warp block, then one block
-    // per group tree
+    // row parts of a parent, one per warp, then one block per group tree
     const int parts = ptab_parts(pool), kinds = pool.fp32 ? 3 : 2;
     int row_blocks = (P.max_rows * parts + PTAB_ITEMS - 1) / PTAB_ITEMS;
     if (row_blocks < 1) row_blocks = 1;
-    k_ptab<<<dim3((unsigned)(row_blocks + P.n_sum * kinds), (unsigned)K), PTAB_T, 0, s>>>(P, pool, par, T, sp,
-                                                                                          row_blocks, st);
+    const size_t smem = T.tree_smem ? (size_t)T.max_sum_nodes * sizeof(double2) : 0;
+    k_ptab<<<dim3((unsigned)(row_blocks + P.n_sum * kinds), (unsigned)K), PTAB_T, smem, s>>>(P, pool, par, T, sp,
+                                                                                             row_blocks, st);
     return cudaGetLastError();
 }
 
@@ -1229,8 +1356,20 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
 
 cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                              long long K, int B, GbState* st, cudaStream_t s) {
-    const int items = (B * P.n_sum << GB_TAB_DBITS) + (P.max_nseg << GB_TAB_SBITS);
-    k_ptab_d<<<dim3((unsigned)grid_for(items, 128), (unsigned)K), 128, 0, s>>>(P, pool, par, T, st);
+    // threads for the partial-table entries, warps for the segment entries
+    const long long items = std::max<long long>((long long)B * P.n_sum << GB_TAB_DBITS,
+                                                (long long)P.max_nseg << (GB_TAB_SBITS + 5));
+    unsigned g = grid_for(items, 128);
+    if (g > (unsigned)gb_sm_count() * 16) g = gb_sm_count() * 16;
+    k_ptab_d<<<dim3(g, (unsigned)K), 128, 0, s>>>(P, pool, par, T, st);
+    return cudaGetLastError();
+}
+
+cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const GbTabs& T, const GbSplit& sp,
+                                 long long Cmax, int fp32, GbState* st, cudaStream_t s) {
+    if (!T.cs64 || P.n_sum <= 0) return cudaSuccess;
+    const int kinds = fp32 ? 3 : 2;
+    k_child_sums<<<grid_for(Cmax * P.n_sum * kinds, 128), 128, 0, s>>>(P, par, T, sp, Cmax, kinds, st);
     return cudaGetLastError();
 }
 

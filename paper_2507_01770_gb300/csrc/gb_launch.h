@@ -89,7 +89,18 @@ struct GbTabs {
     float2* ts32;     // FP32
     int max_rows, max_leaves, tree_nodes, max_drows, max_srows;
     int warp;         // child kernels: 1 one child per warp, 0 one child per thread
+    int max_sum_nodes;   // nodes of the largest sum's group tree
+    int tree_smem;       // 1: k_ptab builds the group trees in shared memory (they fit)
+    // one child per warp: every child's sums and dirty group values, computed
+    // before the child kernel by k_child_sums (null otherwise)
+    double2* cs64;    // [Cmax][n_sum] F
+    double2* csm64;   // [Cmax][n_sum] midpoint
+    float2* cs32;     // [Cmax][n_sum] FP32
+    double2* cg64;    // [Cmax][GB_CG] dirty group values, slot k * GB_TAB_MAX_DIRTY + (g - first dirty group)
+    double2* cgm64;
+    float2* cg32;
 };
+constexpr int GB_CG = GB_MAX_ISUM * GB_TAB_MAX_DIRTY;
 
 // scratch for the scans
 struct GbScan {
@@ -204,6 +215,9 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
 // Partial tables of every parent (after gb_launch_ptab).
 cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                              long long K, int B, GbState* st, cudaStream_t s);
+// One child per warp: every child's sums and dirty group values (tables first).
+cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const GbTabs& T, const GbSplit& sp,
+                                 long long Cmax, int fp32, GbState* st, cudaStream_t s);
 cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                     const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
                                     cudaStream_t s);
