@@ -281,6 +281,35 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     P.outer_root = H.outer_root;
     P.n_var_leaves = (int)H.var_leaves.size();
     P.outer_sum = (H.outer.size() == 1 && H.outer[0].op == D_ISUMV && H.outer_root == 0 && !H.any_prod) ? 1 : 0;
+    {
+        // the outer adjoints that are exact constants: the root's is [1, 1];
+        // an addition passes its adjoint to both operands, a subtraction to
+        // the left one (the right one gets its negation), a negation its
+        // negation; anything else makes its operands' adjoints data-dependent
+        const int no = (int)H.outer.size();
+        std::vector<double> adj(no, 0.0);
+        std::vector<char> known(no, 1);
+        if (no > 0) adj[H.outer_root] = 1.0;
+        auto pass = [&](int r, double v, bool k) {
+            if (r < 0 || r >= no) return;
+            if (!k) known[r] = 0;
+            else adj[r] += v;
+        };
+        for (int t = no - 1; t >= 0; t--) {
+            const GbIns& I = H.outer[t];
+            const bool k = known[t] != 0;
+            switch (I.op) {
+            case D_ADD: pass(I.a, adj[t], k); pass(I.b, adj[t], k); break;
+            case D_SUB: pass(I.a, adj[t], k); pass(I.b, -adj[t], k); break;
+            case D_NEG: pass(I.a, -adj[t], k); break;
+            case D_CONST: case D_PI: case D_EULER: case D_VAR: case D_ISUMV: break;
+            default: pass(I.a, 0.0, false); pass(I.b, 0.0, false); break;
+            }
+        }
+        bool unit = !H.any_prod && H.var_leaves.empty() && !H.sums.empty();
+        for (const GbSum& S : H.sums) unit = unit && known[S.outer_reg] && adj[S.outer_reg] == 1.0;
+        P.outer_unit = unit ? 1 : 0;
+    }
     P.any_prod = H.any_prod;
     P.samples = opt.samples;
     P.mono_all = opt.mono_all ? 1 : 0;

@@ -157,6 +157,8 @@ struct GbProg {
     const GbSeg* segs;               // term-tree segments of every split position
     int32_t max_srows, max_nseg;
     int32_t outer_sum;               // 1: the outer expression is one sum (F = that sum, adjoint [1, 1])
+    int32_t outer_unit;              // 1: every sum's outer adjoint is exactly [1, 1] and no outer VAR
+                                     //    leaf: the first-order test needs no reverse sweep of the outer
     int32_t samples;                 // GUB samples per box (0: midpoint; S: diagonal points j / (S + 1))
     int32_t mono_all;                // first-order test on every coordinate
     int32_t any_prod;                // some reduction is an IPROD
@@ -253,6 +255,7 @@ struct GbState {
     long long evals32, evals64, mids;  // running counters
     unsigned long long ops64, ops32;   // directed-rounding operations executed by the eval kernels
     long long sel_pos;                 // K = 1: pool position of the selected entry (last with the smallest key)
+    long long active_acc;              // k_stats: active entries counted so far by its blocks
     unsigned long long part_epoch;     // pool partitions started in this solve (their tile flags carry it)
     unsigned long long part_ticket;    // pool partition: next tile to hand out
 };

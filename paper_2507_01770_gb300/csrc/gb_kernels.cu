@@ -170,6 +170,62 @@ __global__ void k_root_init(GbProg P, GbPool pool, GbEntries E, double tol_x, Gb
 
 __device__ __forceinline__ double gub_of(const GbState* st) { return gb_key_value(st->gub_key); }
 
+// Parents' slots back to the free list, or (on overflow) the parents back
+// into the pool after the carried-over entries.
+__device__ __forceinline__ void free_parents(const GbParents& par, const GbPool& pool, const GbEntries& En,
+                                             const GbState* st, long long p0, long long step) {
+    const long long npar = st->parents;
+    for (long long p = p0; p < npar; p += step) {
+        if (st->overflow) {
+            long long e = st->kept_old + p;
+            En.flo[e] = par.flo[p];
+            En.slot[e] = par.slot[p];
+            En.cyc[e] = par.cyc[p];
+            continue;
+        }
+        long long kept = st->kept, nfree = st->nfree;
+        long long base = kept < nfree ? nfree - kept : 0;
+        pool.freel[base + p] = par.slot[p];
+    }
+}
+
+// End of a generation, by the last block of k_stats: pool size, free list,
+// record counters, GUB, trace row, generation number.
+__device__ __forceinline__ void finish_counters(const GbGenConst& G, GbState* st) {
+    const long long npar = st->parents;
+    long long kept = st->kept, nfree = st->nfree;
+    if (st->overflow) {
+        st->pool = st->kept_old + npar;
+        st->kept = 0;
+    } else {
+        long long from_free = kept < nfree ? kept : nfree;
+        st->bump += kept - from_free;
+        if (G.nrec) {
+            const long long used = kept * G.nrec, rf = st->rec_nfree;
+            const long long r_from_free = used < rf ? used : rf;
+            st->rec_nfree = rf - r_from_free;
+            st->rec_bump += used - r_from_free;
+        }
+        st->nfree = nfree - from_free + npar;
+        st->pool = st->kept_old + kept;
+    }
+    st->gub_key = st->gub_new_key;
+    if (G.trace && st->gen < G.trace_cap) {
+        gb_gen_stat row;
+        row.parents = npar;
+        row.children = st->children;
+        row.kept32 = G.fp32 ? st->kept32 : st->children;
+        row.kept = st->overflow ? 0 : st->kept;
+        row.pool = st->pool;
+        row.gub = gb_key_value(st->gub_key);
+        G.trace[st->gen] = row;
+    }
+    st->gen += 1;
+    st->min_key = ~0ull;
+    if (st->gc) st->rec_gc += 1;
+    st->gc = 0;
+}
+
 // Pool statistics at the end of a generation (and after the root): the
 // number of active entries and, for K = 1, the smallest active key and the
 // last pool position holding it (the entry the selection takes: ties go to
@@ -184,13 +240,20 @@ __device__ __forceinline__ void better_key(unsigned long long& k, long long& q, 
 }
 
 __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbState* st, unsigned long long* bkey,
-                                               long long* bpos) {
+                                               long long* bpos, GbParents par, GbPool pool, int finish) {
     if (st->halt) return;
     __shared__ unsigned long long s_c[8], s_k[8];
     __shared__ long long s_q[8];
     __shared__ bool s_last;
-    const long long count = st->pool;
-    const double thr = thr_of(gub_of(st), G.tol_f);
+    // at the end of a generation (finish): the parents' slots go back to the
+    // free list (on overflow the parents go back into the pool), and the new
+    // pool and incumbent are read from the generation's counters; the last
+    // block rolls the counters forward
+    if (finish) free_parents(par, pool, E, st, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                             (long long)gridDim.x * blockDim.x);
+    const long long count = !finish ? st->pool
+                                    : st->kept_old + (st->overflow ? st->parents : st->kept);
+    const double thr = thr_of(gb_key_value(finish ? st->gub_new_key : st->gub_key), G.tol_f);
     long long c = 0, kq = -1;
     unsigned long long kmin = ~0ull;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
@@ -214,7 +277,7 @@ __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbStat
         unsigned long long tc = 0, tk = ~0ull;
         long long tq = -1;
         for (int i = 0; i < (int)(blockDim.x >> 5); i++) tc += s_c[i], better_key(tk, tq, s_k[i], s_q[i]);
-        if (tc) atomicAdd((unsigned long long*)&st->active, tc);
+        if (tc) atomicAdd((unsigned long long*)&st->active_acc, tc);
         bkey[blockIdx.x] = tk;
         bpos[blockIdx.x] = tq;
         __threadfence();
@@ -238,10 +301,12 @@ __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbStat
     unsigned long long mk = ~0ull;
     long long mq = -1;
     for (int i = 0; i < (int)(blockDim.x >> 5); i++) better_key(mk, mq, s_k[i], s_q[i]);
+    if (finish) finish_counters(G, st);
     st->stats_done = 0;
     st->part_ticket = 0;
     st->part_epoch += 1;
-    const long long active = (long long)atomicAdd((unsigned long long*)&st->active, 0ull);
+    const long long active = (long long)atomicExch((unsigned long long*)&st->active_acc, 0ull);
+    st->active = active;
     if (active == 0 || st->gen >= G.max_gen || st->overflow || st->error) {
         st->halt = 1;
         return;
@@ -1268,75 +1333,6 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
     }
 }
 
-// Parents' slots back to the free list, or (on overflow) the parents back
-// into the pool after the carried-over entries.
-__device__ __forceinline__ void free_parents(const GbParents& par, const GbPool& pool, const GbEntries& En,
-                                             const GbState* st, long long p0, long long step) {
-    const long long npar = st->parents;
-    for (long long p = p0; p < npar; p += step) {
-        if (st->overflow) {
-            long long e = st->kept_old + p;
-            En.flo[e] = par.flo[p];
-            En.slot[e] = par.slot[p];
-            En.cyc[e] = par.cyc[p];
-            continue;
-        }
-        long long kept = st->kept, nfree = st->nfree;
-        long long base = kept < nfree ? nfree - kept : 0;
-        pool.freel[base + p] = par.slot[p];
-    }
-}
-
-__global__ void k_free_parents(GbParents par, GbPool pool, GbEntries En, GbState* st) {
-    if (st->halt) return;
-    free_parents(par, pool, En, st, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                 (long long)gridDim.x * blockDim.x);
-}
-
-// End of a generation: pool size, free list, record counters, GUB, trace row.
-// With fused = 1 (one block) the block first frees the parents itself.
-__global__ void k_finish(GbGenConst G, GbParents par, GbPool pool, GbEntries En, int fused, GbState* st) {
-    if (st->halt) return;
-    if (fused) {
-        free_parents(par, pool, En, st, threadIdx.x, blockDim.x);
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    const long long npar = st->parents;
-    long long kept = st->kept, nfree = st->nfree;
-    if (st->overflow) {
-        st->pool = st->kept_old + npar;
-        st->kept = 0;
-    } else {
-        long long from_free = kept < nfree ? kept : nfree;
-        st->bump += kept - from_free;
-        if (G.nrec) {
-            const long long used = kept * G.nrec, rf = st->rec_nfree;
-            const long long r_from_free = used < rf ? used : rf;
-            st->rec_nfree = rf - r_from_free;
-            st->rec_bump += used - r_from_free;
-        }
-        st->nfree = nfree - from_free + npar;
-        st->pool = st->kept_old + kept;
-    }
-    st->gub_key = st->gub_new_key;
-    if (G.trace && st->gen < G.trace_cap) {
-        gb_gen_stat row;
-        row.parents = npar;
-        row.children = st->children;
-        row.kept32 = G.fp32 ? st->kept32 : st->children;
-        row.kept = st->overflow ? 0 : st->kept;
-        row.pool = st->pool;
-        row.gub = gb_key_value(st->gub_key);
-        G.trace[st->gen] = row;
-    }
-    st->gen += 1;
-    st->active = 0;
-    st->min_key = ~0ull;
-    if (st->gc) st->rec_gc += 1;
-    st->gc = 0;
-}
-
 // ---------------------------------------------------------------------------
 // Output: entries with LB <= GUB (stable), gathered into rows; GLB = min LB.
 __global__ void k_out_count(GbEntries E, long long count, double gub, int* tile_cnt, GbState* st) {
@@ -1613,12 +1609,13 @@ cudaError_t gb_launch_resume(const GbProg& P, const GbPool& pool, const GbEntrie
 }
 
 cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, const GbScan& sc, GbState* st,
-                            cudaStream_t s) {
+                            cudaStream_t s, const GbParents* par, const GbPool* pool) {
     unsigned g = grid_for(cap, 256);
     if (g > gb_sm_count() * 8) g = gb_sm_count() * 8;
     if (g > (unsigned)GB_STAT_BLOCKS) g = GB_STAT_BLOCKS;
     gb_launch_count++;
-    k_stats<<<g, 256, 0, s>>>(E, G, st, sc.stat_key, sc.stat_pos);
+    k_stats<<<g, 256, 0, s>>>(E, G, st, sc.stat_key, sc.stat_pos, par ? *par : GbParents{}, pool ? *pool : GbPool{},
+                              par ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1646,9 +1643,11 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     gb_launch_count++;
     k_part_1p<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_cnt, sc.tile_off, sc.max_tiles, sc.tile_flag, E_new, par,
                                         pool.freel);
-    gb_launch_count++;
-    k_prep<<<grid_for(G.K * (long long)sp.dmax, 128), 128, 0, s>>>(P, pool, par, sp, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!tabs) {   // with term tables k_ptab splits the parents itself
+        gb_launch_count++;
+        k_prep<<<grid_for(G.K * (long long)sp.dmax, 128), 128, 0, s>>>(P, pool, par, sp, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     // the evaluation window (ev[0] .. ev[1]): per-parent tables and every child kernel
     if (ev && part == 0) cudaEventRecord(ev[0], s);
     if (tabs) {
@@ -1734,15 +1733,9 @@ after_eval:
         if (pool.recs) k_materialize<false, true, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
         else k_materialize<false, false, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
     }
-    if (G.K <= 4096) {   // few parents: freed by the finishing block itself
-        gb_launch_count++;
-        k_finish<<<1, 256, 0, s>>>(G, par, pool, E_new, 1, st);
-    } else {
-        gb_launch_count += 2;
-        k_free_parents<<<grid_for(G.K, 256), 256, 0, s>>>(par, pool, E_new, st);
-        k_finish<<<1, 1, 0, s>>>(G, par, pool, E_new, 0, st);
-    }
-    if ((e = gb_launch_stats(E_new, G, cap, sc, st, s)) != cudaSuccess) return e;
+    // the end of the generation (parents freed, counters) and the statistics
+    // of the new pool, which start the next generation
+    if ((e = gb_launch_stats(E_new, G, cap, sc, st, s, &par, &pool)) != cudaSuccess) return e;
     if (nlaunch) *nlaunch = gb_launch_count - n0;
     return cudaGetLastError();
 }

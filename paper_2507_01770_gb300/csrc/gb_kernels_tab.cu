@@ -102,14 +102,62 @@ __device__ __forceinline__ void tree_job(const GbSum& S, const C& cache, P2* out
         for (int i = threadIdx.x; i < S.nnodes; i += blockDim.x) out[i] = sm[i];
 }
 
+// The split of parent p (Eqs. 10-11 with the rounding reading: boundary t of
+// [lo, hi] is RN(lo + RN(RN(RN(hi - lo) / m) * t)), boundary 0 = lo, boundary
+// m = hi; the division by m = 2 or 4 is the exact product by 1 / m): its
+// split position (first coordinate, coordinates split, block, next cycling
+// position) and the m + 1 boundaries of each split coordinate with their
+// outward floats, computed by threads 0 .. dmax-1 into the block's shared
+// memory (and, when `publish`, into the parent buffers for the later kernels).
+__device__ __forceinline__ int4 parent_split(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                             const GbSplit& sp, long long p, unsigned slot, double* bnd, float* brd,
+                                             float* bru, bool publish) {
+    const int n = P.n, B = P.B;
+    const int c = par.cyc[p] & 0x7fffffff, b = c / B, e = min((b + 1) * B, n);
+    const int dd = min(sp.d, e - c), nxt = (c + dd == n) ? 0 : c + dd;
+    const int4 info = make_int4(c, dd, b, nxt);
+    const int k = threadIdx.x, ms = sp.m + 1;
+    if (k < dd) {
+        const iv64 pj = box_view64(pool, slot).get(c + k);
+        const double lo = pj.lo, hi = pj.hi;
+        const double q = __dmul_rn(__dsub_rn(hi, lo), sp.m == 2 ? 0.5 : 0.25);
+        for (int t = 0; t <= sp.m; t++) {
+            const double v = (t == 0) ? lo : (t == sp.m ? hi : __dadd_rn(lo, __dmul_rn(q, (double)t)));
+            bnd[k * ms + t] = v;
+            brd[k * ms + t] = __double2float_rd(v);
+            bru[k * ms + t] = __double2float_ru(v);
+            if (publish) {
+                const size_t o = ((size_t)p * sp.dmax + k) * ms + t;
+                par.bnd[o] = v;
+                par.bnd_rd[o] = __double2float_rd(v);
+                par.bnd_ru[o] = __double2float_ru(v);
+            }
+        }
+    }
+    if (publish && k == 0) par.info[p] = info;
+    return info;
+}
+
 __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp,
                                                  int row_blocks, GbState* st) {
     if (st->halt) return;
     extern __shared__ double2 s_tree[];   // T.max_sum_nodes entries when the trees fit
+    __shared__ double s_bnd[GB_MAX_SPLIT_D * 5];
+    __shared__ float s_brd[GB_MAX_SPLIT_D * 5], s_bru[GB_MAX_SPLIT_D * 5];
     const long long p = blockIdx.y;
     if (p >= st->parents) return;
-    const int4 info = par.info[p];
+    if (blockIdx.x == 0 && p == 0 && threadIdx.x == 0) {   // the generation's counters (k_prep's part)
+        st->gub_new_key = st->gub_key;
+        st->nfree = st->nfree_after_drop;
+        st->kept = 0;
+        st->kept32 = 0;
+        st->n32 = 0;
+        st->children = 0;
+        st->overflow = 0;
+    }
     const unsigned slot = par.slot[p];
+    const int4 info = parent_split(P, pool, par, sp, p, slot, s_bnd, s_brd, s_bru, blockIdx.x == 0);
+    __syncthreads();
     const int spi = P.sp_of_cyc[info.x];
     if (spi < 0) return;
     if ((int)blockIdx.x >= row_blocks) {
@@ -135,7 +183,6 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
     if (staged)
         for (int t = threadIdx.x; t < SP.ndterm; t += blockDim.x) s_row[t] = P.dterms[SP.dterm0 + t].row;
     __syncthreads();
-    const size_t o = (size_t)p * sp.dmax * (sp.m + 1);
     const int parts = ptab_parts(pool);
     int ops = 0, ops32 = 0;
     const int wib = threadIdx.x >> 5;
@@ -157,8 +204,8 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
         if (part < 2) {
             iv64 R[GB_MAX_TREGS];
             View<double> X = box_view64(pool, slot);
-            X.blo = par.bnd + o;
-            X.bhi = par.bnd + o;
+            X.blo = s_bnd;
+            X.bhi = s_bnd;
             X.c0 = info.x;
             X.dd = info.y;
             X.mshift = sp.mshift;
@@ -184,8 +231,8 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
         } else {
             iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS];
             View<float> X32 = box_view32(pool, slot);
-            X32.blo = par.bnd_rd + o;
-            X32.bhi = par.bnd_ru + o;
+            X32.blo = s_brd;
+            X32.bhi = s_bru;
             X32.c0 = info.x;
             X32.dd = info.y;
             X32.mshift = sp.mshift;
@@ -432,6 +479,67 @@ __device__ __forceinline__ I tab_path_w(const GbSum& S, int2 dr, I* cur, N node,
     return cur[0];   // defined in lane 0
 }
 
+// tab_path for 32 lanes that walk the same path (same tree and dirty range)
+// over their own dirty values: the sibling nodes are loaded once across the
+// lanes (lane t the t-th one the walk reads) and handed out by shuffles;
+// every lane computes its own walk.  Same operations in the same order as
+// tab_path.
+template <typename I, typename N>
+__device__ __forceinline__ I tab_path_lanes(const GbSum& S, int2 dr, I* cur, N node, int lane, int& ops) {
+    if (S.ngroups == 0 || S.nnodes <= 0) {
+        I z;
+        z.lo = 0;
+        z.hi = 0;
+        return z;
+    }
+    if (dr.x >= dr.y) return node(S.nnodes - 1);
+    int mine = -1, cnt = 0;
+    {
+        int lo = dr.x, hi = dr.y, off = 0;
+        for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
+            const int nlo = lo >> 1, nhi = ((hi - 1) >> 1) + 1;
+            for (int q = nlo; q < nhi; q++) {
+                const int a = 2 * q;
+                if (!(a >= lo && a < hi)) mine = cnt++ == lane ? off + a : mine;
+                if (a + 1 < mL && !(a + 1 >= lo && a + 1 < hi)) mine = cnt++ == lane ? off + a + 1 : mine;
+            }
+            lo = nlo;
+            hi = nhi;
+            off += mL;
+        }
+    }
+    I pre;
+    pre.lo = 0;
+    pre.hi = 0;
+    if (mine >= 0) pre = node(mine);
+    I tmp[GB_TAB_MAX_DIRTY];
+    int lo = dr.x, hi = dr.y, off = 0, used = 0;
+    auto take = [&](int idx) {
+        const I v = shfl_iv(pre, used & 31);
+        return used++ < 32 ? v : node(idx);
+    };
+    for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
+        const int nlo = lo >> 1, nhi = ((hi - 1) >> 1) + 1;
+        for (int q = nlo; q < nhi; q++) {
+            const int a = 2 * q;
+            const bool la = a >= lo && a < hi, lb = a + 1 >= lo && a + 1 < hi;
+            I left = la ? cur[a - lo] : take(off + a);
+            I v = left;
+            if (a + 1 < mL) {
+                const I right = lb ? cur[a + 1 - lo] : take(off + a + 1);
+                v = iadd(left, right);
+                ops += 2;
+            }
+            tmp[q - nlo] = v;
+        }
+        for (int q = 0; q < nhi - nlo; q++) cur[q] = tmp[q];
+        lo = nlo;
+        hi = nhi;
+        off += mL;
+    }
+    return cur[0];
+}
+
 // ---------------------------------------------------------------------------
 // k_child_sums (one child per warp): every child's sums before the child
 // kernel, one thread per (child, sum, kind) -- kind 0 F, 1 midpoint, 2 FP32.
@@ -446,7 +554,7 @@ __device__ __forceinline__ I tab_path_w(const GbSum& S, int2 dr, I* cur, N node,
 template <typename I, typename P2>
 __device__ __forceinline__ void child_sum(const GbProg& P, const GbSplitPos& SP, int k, int blk, unsigned r,
                                           const P2* trow, const P2* tseg, const P2* nodes, I* gout, I* sout,
-                                          int& ops) {
+                                          bool lanes, int& ops) {
     const GbSum S = P.sums[k];
     const int2 dr = P.dirty[blk * P.n_sum + k];
     int sg = SP.seg0;
@@ -474,8 +582,8 @@ __device__ __forceinline__ void child_sum(const GbProg& P, const GbSplitPos& SP,
         cur[g - dr.x] = tr.result();
         gout[k * GB_TAB_MAX_DIRTY + (g - dr.x)] = cur[g - dr.x];
     }
-    *sout = tab_path(S, dr, cur, [&](int i) { const P2 v = nodes[S.node0 + i]; return mk<decltype(v.x)>(v.x, v.y); },
-                     ops);
+    auto node = [&](int i) { const P2 v = nodes[S.node0 + i]; return mk<decltype(v.x)>(v.x, v.y); };
+    *sout = lanes ? tab_path_lanes(S, dr, cur, node, threadIdx.x & 31, ops) : tab_path(S, dr, cur, node, ops);
 }
 
 __global__ void __launch_bounds__(128) k_child_sums(GbProg P, GbParents par, GbTabs Tb, GbSplit sp, long long Cmax,
@@ -485,23 +593,34 @@ __global__ void __launch_bounds__(128) k_child_sums(GbProg P, GbParents par, GbT
     const long long ci = t % Cmax, rest = t / Cmax;
     const int k = (int)(rest % (P.n_sum > 0 ? P.n_sum : 1)), kind = (int)(rest / (P.n_sum > 0 ? P.n_sum : 1));
     int ops = 0;
-    if (P.n_sum > 0 && kind < kinds && ci < st->nch) {
-        const ChildCtx c = child_ctx(par, ci, sp);
-        const int spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
-        if (spi >= 0) {
+    // the warp's 32 children share one path when they share a parent and a
+    // (sum, kind) and all of them are evaluated (the decision is the warp's)
+    const long long t0 = t - (threadIdx.x & 31);
+    bool lanes = t0 % Cmax + 31 < Cmax && (t0 % Cmax) >> sp.flog2 == (t0 % Cmax + 31) >> sp.flog2 &&
+                 t0 + 31 < (long long)gridDim.x * blockDim.x;
+    const bool live0 = P.n_sum > 0 && kind < kinds && ci < st->nch;
+    ChildCtx c{};
+    int spi = -1;
+    if (live0) {
+        c = child_ctx(par, ci, sp);
+        spi = c.valid ? P.sp_of_cyc[c.info.x] : -1;
+    }
+    if (lanes) lanes = __all_sync(0xffffffffu, live0 && spi >= 0);
+    {
+        if (live0 && spi >= 0) {
             const GbSplitPos SP = P.sps[spi];
             const size_t rowb = (size_t)c.p * Tb.max_rows, segb = (size_t)c.p * Tb.max_srows,
                          nodeb = (size_t)c.p * Tb.tree_nodes;
             const size_t so = (size_t)ci * P.n_sum + k, go = (size_t)ci * GB_CG;
             if (kind == 0)
                 child_sum<iv64>(P, SP, k, c.info.z, c.r, Tb.tv64 + rowb, Tb.ts64 + segb, Tb.nf64 + nodeb,
-                                (iv64*)(Tb.cg64 + go), (iv64*)(Tb.cs64 + so), ops);
+                                (iv64*)(Tb.cg64 + go), (iv64*)(Tb.cs64 + so), lanes, ops);
             else if (kind == 1)
                 child_sum<iv64>(P, SP, k, c.info.z, c.r, Tb.tm64 + rowb, Tb.tsm64 + segb, Tb.nm64 + nodeb,
-                                (iv64*)(Tb.cgm64 + go), (iv64*)(Tb.csm64 + so), ops);
+                                (iv64*)(Tb.cgm64 + go), (iv64*)(Tb.csm64 + so), lanes, ops);
             else
                 child_sum<iv32>(P, SP, k, c.info.z, c.r, Tb.tv32 + rowb, Tb.ts32 + segb, Tb.nf32 + nodeb,
-                                (iv32*)(Tb.cg32 + go), (iv32*)(Tb.cs32 + so), ops);
+                                (iv32*)(Tb.cg32 + go), (iv32*)(Tb.cs32 + so), lanes, ops);
         }
     }
     warp_add_ops(kind < 2 ? ops : 0, &st->ops64);
@@ -903,10 +1022,23 @@ template <> __device__ __forceinline__ iv32* ws_OA<float>(const WScratch& w) { r
 
 __device__ __forceinline__ bool stage_meta(const GbProg& P, const GbSplitPos& SP, int cnt, WMeta* m, int lane) {
     if (cnt > GB_WMETA) return false;
-    for (int e = lane; e < cnt; e += 32) {
-        const int2 rg = P.jk[SP.jk0 + e];
-        const GbJkD J = P.jkd[SP.jk0 + e];
-        m[e] = WMeta{rg.x, rg.y, J.base, (int)(unsigned short)J.shift | ((int)J.mask << 16)};
+    // up to 4 entries per lane in flight at once (one memory round trip per 128 entries)
+    for (int e0 = 0; e0 < cnt; e0 += 128) {
+        int2 rg[4];
+        GbJkD J[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int e = e0 + u * 32 + lane;
+            if (e < cnt) {
+                rg[u] = P.jk[SP.jk0 + e];
+                J[u] = P.jkd[SP.jk0 + e];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int e = e0 + u * 32 + lane;
+            if (e < cnt) m[e] = WMeta{rg[u].x, rg[u].y, J[u].base, (int)(unsigned short)J[u].shift | ((int)J[u].mask << 16)};
+        }
     }
     __syncwarp();
     return true;
@@ -982,8 +1114,8 @@ __device__ __forceinline__ bool tab_mono_w(const GbProg& P, const GbTabs& Tb, lo
     typedef typename TabPrec<T>::I I;
     I* O = ws_O<T>(ws);
     I* OA = ws_OA<T>(ws);
-    unsigned unit = 1u;   // a single outer sum: its adjoint is [1, 1]
-    if (!P.outer_sum) {
+    unsigned unit = P.outer_unit ? 0xffffffffu : 1u;   // a single outer sum: its adjoint is [1, 1]
+    if (!P.outer_sum && !P.outer_unit) {
         if (lane == 0) {
             for (int t = 0; t < P.n_outer; t++) OA[t] = mk<T>((T)0, (T)0);
             OA[P.outer_root] = mk<T>((T)1, (T)1);
@@ -1096,7 +1228,7 @@ __device__ __forceinline__ bool eval64_tab_child_w(const GbProg& P, const GbPool
     return true;
 }
 
-__global__ void __launch_bounds__(128) k_eval64_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+__global__ void __launch_bounds__(128, 1) k_eval64_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
                                                      GbChildren ch, GbSplit sp, int from_list, GbState* st) {
     if (st->halt) return;
     const long long lim = from_list ? st->n32 : st->nch;
@@ -1204,7 +1336,7 @@ __global__ void __launch_bounds__(128) k_eval32_tabw(GbProg P, GbPool pool, GbPa
 // whose child passes the FP32 test evaluates it in FP64 at once (the same
 // children, the same previous GUB and the same operations as the FP32 kernel,
 // the survivor list and the FP64 kernel in sequence, without the list).
-__global__ void __launch_bounds__(128) k_eval3264_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+__global__ void __launch_bounds__(128, 1) k_eval3264_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
                                                        GbChildren ch, GbSplit sp, GbState* st) {
     if (st->halt) return;
     const long long lim = st->nch;

@@ -140,8 +140,10 @@ cudaError_t gb_launch_root_init(const GbProg& P, const GbPool& pool, const GbEnt
 // Active count of the pool; count and GUB are read from the device state,
 // max_count bounds the grid.
 // Active count of the pool (read from the device state) for the next generation.
+// par / pool non-null: at the end of a generation (free the parents, roll
+// the counters forward first).
 cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long cap, const GbScan& sc, GbState* st,
-                            cudaStream_t s);
+                            cudaStream_t s, const GbParents* par = nullptr, const GbPool* pool = nullptr);
 // Checkpoint: every entry of E[0, count) with its box (lo, hi: count x n), LB and cycling word.
 cudaError_t gb_launch_snapshot(const GbEntries& E, long long count, const GbPool& pool, double* lo, double* hi,
                                double* flo, int* cyc, cudaStream_t s);
