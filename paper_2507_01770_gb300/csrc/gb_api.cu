@@ -95,6 +95,7 @@ struct gb_problem {
     GbProg P{};
     std::vector<void*> owned;      // device allocations
     cudaStream_t stream = nullptr;
+    GbFork fork{};                 // second stream and events for the single parent's tables
     GbPool pool{};
     GbEntries E[2]{};
     GbParents par{};
@@ -168,6 +169,9 @@ void gb_destroy_problem(gb_problem* p) {
     for (auto& pp : p->gpart)
         for (cudaGraphExec_t g : pp)
             if (g) cudaGraphExecDestroy(g);
+    if (p->fork.fork) cudaEventDestroy(p->fork.fork);
+    if (p->fork.join) cudaEventDestroy(p->fork.join);
+    if (p->fork.s2) cudaStreamDestroy(p->fork.s2);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -267,6 +271,10 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
         return rc;
     };
     if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking))) return bad(e, "cudaStreamCreate");
+    if ((e = cudaStreamCreateWithFlags(&p->fork.s2, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&p->fork.fork, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&p->fork.join, cudaEventDisableTiming)))
+        return bad(e, "cudaStreamCreate");
     DevAlloc A{&p->owned, &p->device_bytes, p->stream};
 
     // ---- program and tables ----------------------------------------------
@@ -672,7 +680,7 @@ static cudaError_t capture_graphs(gb_problem* p) {
             long long n1 = 0;
             e = gb_launch_generation(p->P, p->pool, p->E[b], p->E[1 - b], p->par, p->ch, p->sp, p->sc,
                                      p->use_tabs ? &p->tabs : nullptr, p->G, p->cap, p->Cmax, p->st, s, nullptr,
-                                     &n1);
+                                     &n1, 0, &p->fork);
             nl += n1;
         }
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
@@ -744,7 +752,8 @@ __attribute__((visibility("hidden"))) int solve_advance(gb_problem* p, bool bloc
     } else {
         long long nl = 0;
         e = gb_launch_generation(p->P, p->pool, p->E[cur], p->E[1 - cur], p->par, p->ch, p->sp, p->sc,
-                                 p->use_tabs ? &p->tabs : nullptr, p->G, p->cap, p->Cmax, p->st, s, &p->ev[2], &nl);
+                                 p->use_tabs ? &p->tabs : nullptr, p->G, p->cap, p->Cmax, p->st, s, &p->ev[2], &nl, 0,
+                                 &p->fork);
         if (e != cudaSuccess) return stop(cuda_fail(e, "generation launch"));
         R.timed64 = true;
         R.timed32 = p->opt.fp32_prefilter != 0;
@@ -911,7 +920,7 @@ static cudaError_t launch_part(gb_problem* p, int cur, int part, long long* nl) 
         if (e != cudaSuccess) return e;
         long long n1 = 0;
         e = gb_launch_generation(p->P, p->pool, p->E[cur], p->E[1 - cur], p->par, p->ch, p->sp, p->sc, &p->tabs,
-                                 p->G, p->cap, p->Cmax, p->st, s, nullptr, &n1, part);
+                                 p->G, p->cap, p->Cmax, p->st, s, nullptr, &n1, part, &p->fork);
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);

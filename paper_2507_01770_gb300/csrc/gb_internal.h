@@ -236,7 +236,7 @@ struct GbState {
     long long sel_ties;         // active entries with key == sel_T
     long long radix_rank;       // radix select: remaining rank
     long long n32;              // length of the FP32-survivor list
-    long long nfree_after_drop; // free-list size after the cut-off's frees
+    long long nfree_base;       // free-list size when the pool partition starts (set by k_stats)
     unsigned long long gub_key;     // incumbent upper bound (order key)
     unsigned long long gub_new_key; // min over this generation's samples
     unsigned long long sel_T;       // selection threshold key (~0: take all active)

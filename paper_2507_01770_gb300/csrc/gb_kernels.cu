@@ -302,6 +302,8 @@ __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbStat
     long long mq = -1;
     for (int i = 0; i < (int)(blockDim.x >> 5); i++) better_key(mk, mq, s_k[i], s_q[i]);
     if (finish) finish_counters(G, st);
+    st->nfree_base = st->nfree;
+    if (G.K == 1) st->sel_pos = mq;   // the one parent (also when it is the only active entry)
     st->stats_done = 0;
     st->part_ticket = 0;
     st->part_epoch += 1;
@@ -320,7 +322,6 @@ __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbStat
         // the smallest active key, the most recently inserted entry holding it
         st->sel_mode = 1;
         st->sel_T = mk;
-        st->sel_pos = mq;
         st->sel_below = 0;
         st->sel_need = 1;
     } else {
@@ -484,7 +485,9 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_c
 // tickets were taken before its own, by blocks already running, so every
 // wait ends; each is bounded all the same (on running out it sets an error
 // bit and publishes, so no block waits on it).  The tile that finishes last
-// in order writes the totals of the partition.
+// in order writes the totals of the partition.  With par_by_tab (K = 1 and
+// term tables) the single parent is written by k_ptab, which reads it from
+// the pool position k_stats found and may run at the same time.
 constexpr unsigned long long GB_FLAG_AGG = 1, GB_FLAG_INC = 2;
 constexpr long long GB_SPIN_LIMIT = 1LL << 26;
 
@@ -531,7 +534,7 @@ __device__ __forceinline__ unsigned long long block_scan_packed(unsigned long lo
 
 __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbState* st, int* agg, int* inc,
                                                 int max_tiles, unsigned long long* flag, GbEntries En,
-                                                GbParents par, unsigned* freel) {
+                                                GbParents par, unsigned* freel, int par_by_tab) {
     if (st->halt) return;
     __shared__ unsigned long long s_scan[PT / 32 + 1];
     __shared__ long long s_tile;
@@ -545,7 +548,8 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
     // ties (key == T) exist only for the radix threshold; the last `need` of them are taken
     const long long need = (mode == 2 && T != ~0ull) ? st->sel_need : 0;
     const long long Ti = (mode == 2 && T != ~0ull) ? st->sel_ties : 0;
-    const long long nfree = st->nfree;
+    // (st->nfree itself is rewritten by the last tile while late blocks start)
+    const long long nfree = st->nfree_base;
     const unsigned long long epoch = st->part_epoch;
     const long long nt = ntiles_of(count);
     auto totals = [&](long long D, long long Bl, long long Tt) {
@@ -554,7 +558,7 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
         st->parents = npar;
         st->nch = npar << G.flog2;
         st->kept_old = count - D - npar;
-        st->nfree_after_drop = nfree + D;
+        st->nfree = nfree + D;
         st->sel_below = Bl;
         st->sel_ties = Tt;
     };
@@ -671,6 +675,7 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
             if (f[r].drop) {
                 freel[nfree + gd] = E.slot[q];
             } else if (sel) {
+                if (par_by_tab) continue;   // the table kernel writes the single parent
                 par.slot[sel_before] = E.slot[q];
                 par.cyc[sel_before] = E.cyc[q];
                 par.flo[sel_before] = E.flo[q];
@@ -696,7 +701,6 @@ __global__ void k_prep(GbProg P, GbPool pool, GbParents par, GbSplit sp, GbState
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx == 0) {
         st->gub_new_key = st->gub_key;
-        st->nfree = st->nfree_after_drop;
         st->kept = 0;
         st->kept32 = 0;
         st->n32 = 0;
@@ -1622,7 +1626,8 @@ cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long c
 cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEntries& E, const GbEntries& E_new,
                                  const GbParents& par, const GbChildren& ch, const GbSplit& sp, const GbScan& sc,
                                  const GbTabs* tabs, const GbGenConst& G, long long cap, long long Cmax,
-                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch, int part) {
+                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch, int part,
+                                 const GbFork* fork) {
     long long n0 = gb_launch_count;
     cudaError_t e;
     const unsigned gpool = (unsigned)std::min<long long>(grid_for(cap, 256), gb_sm_count() * 8);
@@ -1640,25 +1645,47 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
             k_radix_pick<<<1, 1024, 0, s>>>(pass, st, sc.hist);
         }
     }
+    // K = 1 with term tables: the parent is the pool entry the last k_stats
+    // found, so its tables need nothing from the partition and run beside it
+    // (on the fork stream when there is one), joined before the children
+    const bool sel_tabs = tabs && G.K == 1;
+    cudaStream_t ts = s;
+    if (sel_tabs && fork) {
+        if ((e = cudaEventRecord(fork->fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(fork->s2, fork->fork, 0)) != cudaSuccess) return e;
+        ts = fork->s2;
+    }
+    auto tables = [&]() -> cudaError_t {
+        cudaError_t et;
+        // the evaluation window (ev[0] .. ev[1]): per-parent tables and every child kernel
+        if (ev && part == 0) cudaEventRecord(ev[0], ts);
+        gb_launch_count++;
+        if ((et = gb_launch_ptab(P, pool, par, *tabs, G.K, sp, st, ts, sel_tabs ? &E : nullptr)) != cudaSuccess)
+            return et;
+        gb_launch_count++;
+        if ((et = gb_launch_ptab_d(P, pool, par, *tabs, G.K, P.B, st, ts, sel_tabs)) != cudaSuccess) return et;
+        if (tabs->cs64) {
+            gb_launch_count++;
+            if ((et = gb_launch_child_sums(P, par, *tabs, sp, Cmax, G.fp32, st, ts, sel_tabs)) != cudaSuccess)
+                return et;
+        }
+        return cudaSuccess;
+    };
+    if (sel_tabs && (e = tables()) != cudaSuccess) return e;
     gb_launch_count++;
     k_part_1p<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_cnt, sc.tile_off, sc.max_tiles, sc.tile_flag, E_new, par,
-                                        pool.freel);
+                                        pool.freel, sel_tabs ? 1 : 0);
     if (!tabs) {   // with term tables k_ptab splits the parents itself
         gb_launch_count++;
         k_prep<<<grid_for(G.K * (long long)sp.dmax, 128), 128, 0, s>>>(P, pool, par, sp, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (ev && part == 0) cudaEventRecord(ev[0], s);
+    } else if (!sel_tabs) {
+        if ((e = tables()) != cudaSuccess) return e;
     }
-    // the evaluation window (ev[0] .. ev[1]): per-parent tables and every child kernel
-    if (ev && part == 0) cudaEventRecord(ev[0], s);
-    if (tabs) {
-        gb_launch_count++;
-        if ((e = gb_launch_ptab(P, pool, par, *tabs, G.K, sp, st, s)) != cudaSuccess) return e;
-        gb_launch_count++;
-        if ((e = gb_launch_ptab_d(P, pool, par, *tabs, G.K, P.B, st, s)) != cudaSuccess) return e;
-        if (tabs->cs64) {
-            gb_launch_count++;
-            if ((e = gb_launch_child_sums(P, par, *tabs, sp, Cmax, G.fp32, st, s)) != cudaSuccess) return e;
-        }
+    if (ts != s) {
+        if ((e = cudaEventRecord(fork->join, ts)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, fork->join, 0)) != cudaSuccess) return e;
     }
     if (part == 1) {   // up to the child evaluation (a fused launch over many problems follows)
         if (nlaunch) *nlaunch = gb_launch_count - n0;

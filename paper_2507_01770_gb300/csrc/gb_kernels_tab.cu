@@ -110,10 +110,10 @@ __device__ __forceinline__ void tree_job(const GbSum& S, const C& cache, P2* out
 // outward floats, computed by threads 0 .. dmax-1 into the block's shared
 // memory (and, when `publish`, into the parent buffers for the later kernels).
 __device__ __forceinline__ int4 parent_split(const GbProg& P, const GbPool& pool, const GbParents& par,
-                                             const GbSplit& sp, long long p, unsigned slot, double* bnd, float* brd,
-                                             float* bru, bool publish) {
+                                             const GbSplit& sp, long long p, unsigned slot, int cyc, double* bnd,
+                                             float* brd, float* bru, bool publish) {
     const int n = P.n, B = P.B;
-    const int c = par.cyc[p] & 0x7fffffff, b = c / B, e = min((b + 1) * B, n);
+    const int c = cyc & 0x7fffffff, b = c / B, e = min((b + 1) * B, n);
     const int dd = min(sp.d, e - c), nxt = (c + dd == n) ? 0 : c + dd;
     const int4 info = make_int4(c, dd, b, nxt);
     const int k = threadIdx.x, ms = sp.m + 1;
@@ -139,24 +139,32 @@ __device__ __forceinline__ int4 parent_split(const GbProg& P, const GbPool& pool
 }
 
 __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp,
-                                                 int row_blocks, GbState* st) {
+                                                 int row_blocks, GbState* st, GbEntries E, int from_sel) {
     if (st->halt) return;
     extern __shared__ double2 s_tree[];   // T.max_sum_nodes entries when the trees fit
     __shared__ double s_bnd[GB_MAX_SPLIT_D * 5];
     __shared__ float s_brd[GB_MAX_SPLIT_D * 5], s_bru[GB_MAX_SPLIT_D * 5];
     const long long p = blockIdx.y;
-    if (p >= st->parents) return;
+    // from_sel: the one parent is pool entry sel_pos (the partition, which
+    // writes the parent count, may be running)
+    if (!from_sel && p >= st->parents) return;
+    const long long q = from_sel ? st->sel_pos : 0;
+    const unsigned slot = from_sel ? E.slot[q] : par.slot[p];
+    const int cyc = from_sel ? E.cyc[q] : par.cyc[p];
     if (blockIdx.x == 0 && p == 0 && threadIdx.x == 0) {   // the generation's counters (k_prep's part)
+        if (from_sel) {
+            par.slot[0] = slot;
+            par.cyc[0] = cyc;
+            par.flo[0] = E.flo[q];
+        }
         st->gub_new_key = st->gub_key;
-        st->nfree = st->nfree_after_drop;
         st->kept = 0;
         st->kept32 = 0;
         st->n32 = 0;
         st->children = 0;
         st->overflow = 0;
     }
-    const unsigned slot = par.slot[p];
-    const int4 info = parent_split(P, pool, par, sp, p, slot, s_bnd, s_brd, s_bru, blockIdx.x == 0);
+    const int4 info = parent_split(P, pool, par, sp, p, slot, cyc, s_bnd, s_brd, s_bru, blockIdx.x == 0);
     __syncthreads();
     const int spi = P.sp_of_cyc[info.x];
     if (spi < 0) return;
@@ -275,10 +283,10 @@ template <typename I> __device__ __forceinline__ I shfl_down_iv(I v, int d) {
 }
 
 __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents par, GbTabs T,
-                                                GbState* st) {
+                                                GbState* st, int fixed) {
     if (st->halt) return;
     const long long p = blockIdx.y;
-    if (p >= st->parents) return;
+    if (!fixed && p >= st->parents) return;
     const int4 info = par.info[p];
     const int spi = P.sp_of_cyc[info.x];
     if (spi < 0) return;
@@ -587,7 +595,7 @@ __device__ __forceinline__ void child_sum(const GbProg& P, const GbSplitPos& SP,
 }
 
 __global__ void __launch_bounds__(128) k_child_sums(GbProg P, GbParents par, GbTabs Tb, GbSplit sp, long long Cmax,
-                                                    int kinds, GbState* st) {
+                                                    int kinds, GbState* st, long long nch_fixed) {
     if (st->halt) return;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long ci = t % Cmax, rest = t / Cmax;
@@ -598,7 +606,7 @@ __global__ void __launch_bounds__(128) k_child_sums(GbProg P, GbParents par, GbT
     const long long t0 = t - (threadIdx.x & 31);
     bool lanes = t0 % Cmax + 31 < Cmax && (t0 % Cmax) >> sp.flog2 == (t0 % Cmax + 31) >> sp.flog2 &&
                  t0 + 31 < (long long)gridDim.x * blockDim.x;
-    const bool live0 = P.n_sum > 0 && kind < kinds && ci < st->nch;
+    const bool live0 = P.n_sum > 0 && kind < kinds && ci < (nch_fixed >= 0 ? nch_fixed : st->nch);
     ChildCtx c{};
     int spi = -1;
     if (live0) {
@@ -1459,14 +1467,16 @@ cudaError_t gb_launch_eval3264_batch(const GbEvalDesc* d_desc, int nreq, long lo
 }
 
 cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                           long long K, const GbSplit& sp, GbState* st, cudaStream_t s) {
+                           long long K, const GbSplit& sp, GbState* st, cudaStream_t s, const GbEntries* Esel) {
     // row parts of a parent, one per warp, then one block per group tree
     const int parts = ptab_parts(pool), kinds = pool.fp32 ? 3 : 2;
     int row_blocks = (P.max_rows * parts + PTAB_ITEMS - 1) / PTAB_ITEMS;
     if (row_blocks < 1) row_blocks = 1;
     const size_t smem = T.tree_smem ? (size_t)T.max_sum_nodes * sizeof(double2) : 0;
     k_ptab<<<dim3((unsigned)(row_blocks + P.n_sum * kinds), (unsigned)K), PTAB_T, smem, s>>>(P, pool, par, T, sp,
-                                                                                             row_blocks, st);
+                                                                                             row_blocks, st,
+                                                                                             Esel ? *Esel : GbEntries{},
+                                                                                             Esel ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1487,21 +1497,23 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
 }
 
 cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                             long long K, int B, GbState* st, cudaStream_t s) {
+                             long long K, int B, GbState* st, cudaStream_t s, bool fixed) {
     // threads for the partial-table entries, warps for the segment entries
     const long long items = std::max<long long>((long long)B * P.n_sum << GB_TAB_DBITS,
                                                 (long long)P.max_nseg << (GB_TAB_SBITS + 5));
     unsigned g = grid_for(items, 128);
     if (g > (unsigned)gb_sm_count() * 16) g = gb_sm_count() * 16;
-    k_ptab_d<<<dim3(g, (unsigned)K), 128, 0, s>>>(P, pool, par, T, st);
+    k_ptab_d<<<dim3(g, (unsigned)K), 128, 0, s>>>(P, pool, par, T, st, fixed ? 1 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const GbTabs& T, const GbSplit& sp,
-                                 long long Cmax, int fp32, GbState* st, cudaStream_t s) {
+                                 long long Cmax, int fp32, GbState* st, cudaStream_t s, bool fixed) {
     if (!T.cs64 || P.n_sum <= 0) return cudaSuccess;
     const int kinds = fp32 ? 3 : 2;
-    k_child_sums<<<grid_for(Cmax * P.n_sum * kinds, 128), 128, 0, s>>>(P, par, T, sp, Cmax, kinds, st);
+    // fixed: one parent, its 2^flog2 children (the count is not read from the state)
+    const long long nch = fixed ? (1LL << sp.flog2) : -1;
+    k_child_sums<<<grid_for(Cmax * P.n_sum * kinds, 128), 128, 0, s>>>(P, par, T, sp, Cmax, kinds, st, nch);
     return cudaGetLastError();
 }
 

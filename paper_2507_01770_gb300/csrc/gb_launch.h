@@ -159,10 +159,19 @@ cudaError_t gb_launch_resume(const GbProg& P, const GbPool& pool, const GbEntrie
 // the FP64 and FP32 evaluation kernels.  Returns the kernels launched in
 // *nlaunch.  part 1 stops before the child evaluation and part 2 starts
 // after it (a fused evaluation over several problems goes between them).
+// A second stream and two events of a problem: with one parent per
+// generation and term tables, the parent's tables (k_ptab, k_ptab_d,
+// k_child_sums) run on s2 beside the pool partition on the main stream (the
+// parent is the pool entry k_stats found), joined before the child kernel.
+struct GbFork {
+    cudaStream_t s2;
+    cudaEvent_t fork, join;
+};
 cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEntries& E, const GbEntries& E_new,
                                  const GbParents& par, const GbChildren& ch, const GbSplit& sp, const GbScan& sc,
                                  const GbTabs* tabs, const GbGenConst& G, long long cap, long long Cmax,
-                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch, int part = 0);
+                                 GbState* st, cudaStream_t s, cudaEvent_t* ev, long long* nlaunch, int part = 0,
+                                 const GbFork* fork = nullptr);
 
 // One problem of a fused child evaluation: the arguments of its
 // k_eval3264_tabw launch (term tables, one child per warp, FP32 then FP64).
@@ -208,18 +217,22 @@ extern "C" gb_status batch_generation(gb_problem* const* probs, int k, GbBatchCt
 extern "C" gb_status solve_finish(gb_problem* p, gb_result* out, bool copy_boxes);
 extern "C" size_t gb_internal_device_bytes(const gb_problem* p);
 // per-parent term tables (gb_kernels_tab.cu); sizes read from the device state
+// Esel non-null: the single parent is pool entry st->sel_pos of *Esel (the
+// partition may still be running).
 cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                           long long K, const GbSplit& sp, GbState* st, cudaStream_t s);
+                           long long K, const GbSplit& sp, GbState* st, cudaStream_t s,
+                           const GbEntries* Esel = nullptr);
 cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                  const GbChildren& ch, long long Cmax, const GbSplit& sp, bool from_list,
                                  GbState* st, cudaStream_t s);
 // FP32 prefilter + FP64 evaluation fused, one child per warp (tables).
 // Partial tables of every parent (after gb_launch_ptab).
+// fixed: the generation has K parents for certain (do not read the count the partition writes).
 cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
-                             long long K, int B, GbState* st, cudaStream_t s);
+                             long long K, int B, GbState* st, cudaStream_t s, bool fixed = false);
 // One child per warp: every child's sums and dirty group values (tables first).
 cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const GbTabs& T, const GbSplit& sp,
-                                 long long Cmax, int fp32, GbState* st, cudaStream_t s);
+                                 long long Cmax, int fp32, GbState* st, cudaStream_t s, bool fixed = false);
 cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                     const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
                                     cudaStream_t s);
