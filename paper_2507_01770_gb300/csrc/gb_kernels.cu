@@ -230,13 +230,76 @@ __device__ __forceinline__ void finish_counters(const GbGenConst& G, GbState* st
 // number of active entries and, for K = 1, the smallest active key and the
 // last pool position holding it (the entry the selection takes: ties go to
 // the most recently inserted).  Each block leaves its (key, position) pair;
-// the last block to finish combines them and starts the next generation: it
-// stops the solve if nothing is active or a limit was reached, otherwise it
-// chooses the selection (all active boxes if at most K; the entry above when
-// K = 1; else a radix select of the K-th smallest key) and opens the next
-// pool partition (ticket 0, a new epoch).
+// the last block to finish combines them and starts the next generation
+// (open_generation).  With K = 1 the end of a generation does not need this
+// pass over the pool: the partition and k_materialize leave the pairs of the
+// entries they write, and k_materialize's last block does the rest.
 __device__ __forceinline__ void better_key(unsigned long long& k, long long& q, unsigned long long k2, long long q2) {
     if (k2 < k || (k2 == k && q2 > q)) k = k2, q = q2;
+}
+
+// The best (key, position) pair of a block; every thread calls it, thread 0
+// gets the result (sk, sq: one entry per warp in shared memory).
+__device__ __forceinline__ void block_best(unsigned long long& k, long long& q, unsigned long long* sk, long long* sq) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long k2 = __shfl_down_sync(0xffffffffu, k, o);
+        const long long q2 = __shfl_down_sync(0xffffffffu, q, o);
+        better_key(k, q, k2, q2);
+    }
+    __syncthreads();
+    if (lane == 0) sk[w] = k, sq[w] = q;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 1; i < (int)(blockDim.x >> 5); i++) better_key(k, q, sk[i], sq[i]);
+}
+
+// The best pair over n per-block pairs (every thread of one block calls it;
+// thread 0 gets the result).
+__device__ __forceinline__ void combine_pairs(const unsigned long long* bkey, const long long* bpos, int n,
+                                              unsigned long long& k, long long& q, unsigned long long* sk,
+                                              long long* sq) {
+    k = ~0ull;
+    q = -1;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) better_key(k, q, __ldcg(bkey + b), __ldcg(bpos + b));
+    block_best(k, q, sk, sq);
+}
+
+// By one thread, once the new pool's active count and (for K = 1) its
+// smallest active key mk and that key's last position mq are known: stop
+// the solve if nothing is active or a limit was reached, else choose the
+// next selection (K = 1: the entry at mq; all active entries if at most K;
+// else a radix select of the K-th smallest key) and open the next pool
+// partition (ticket 0, a new epoch).
+__device__ __forceinline__ void open_generation(const GbGenConst& G, GbState* st, long long active,
+                                                unsigned long long mk, long long mq) {
+    st->nfree_base = st->nfree;
+    st->stats_done = 0;
+    st->part_ticket = 0;
+    st->part_epoch += 1;
+    st->active = active;
+    if (active == 0 || st->gen >= G.max_gen || st->overflow || st->error) {
+        st->halt = 1;
+        return;
+    }
+    if (G.K == 1) {
+        // the smallest active key, the most recently inserted entry holding it
+        st->sel_mode = 1;
+        st->sel_T = mk;
+        st->sel_pos = mq;
+        st->sel_below = 0;
+        st->sel_need = 1;
+    } else if (active <= G.K) {
+        st->sel_mode = 0;
+        st->sel_T = ~0ull;
+        st->sel_below = active;
+        st->sel_need = 0;
+    } else {
+        st->sel_mode = 2;
+        st->radix_prefix = 0;
+        st->radix_rank = G.K;
+        st->sel_below = 0;
+    }
 }
 
 __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbState* st, unsigned long long* bkey,
@@ -302,34 +365,8 @@ __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbStat
     long long mq = -1;
     for (int i = 0; i < (int)(blockDim.x >> 5); i++) better_key(mk, mq, s_k[i], s_q[i]);
     if (finish) finish_counters(G, st);
-    st->nfree_base = st->nfree;
-    if (G.K == 1) st->sel_pos = mq;   // the one parent (also when it is the only active entry)
-    st->stats_done = 0;
-    st->part_ticket = 0;
-    st->part_epoch += 1;
     const long long active = (long long)atomicExch((unsigned long long*)&st->active_acc, 0ull);
-    st->active = active;
-    if (active == 0 || st->gen >= G.max_gen || st->overflow || st->error) {
-        st->halt = 1;
-        return;
-    }
-    if (active <= G.K) {
-        st->sel_mode = 0;
-        st->sel_T = ~0ull;
-        st->sel_below = active;
-        st->sel_need = 0;
-    } else if (G.K == 1) {
-        // the smallest active key, the most recently inserted entry holding it
-        st->sel_mode = 1;
-        st->sel_T = mk;
-        st->sel_below = 0;
-        st->sel_need = 1;
-    } else {
-        st->sel_mode = 2;
-        st->radix_prefix = 0;
-        st->radix_rank = G.K;
-        st->sel_below = 0;
-    }
+    open_generation(G, st, active, mk, mq);
 }
 
 // Radix select (16-bit digits, 4 passes) of the K-th smallest active key.
@@ -534,9 +571,11 @@ __device__ __forceinline__ unsigned long long block_scan_packed(unsigned long lo
 
 __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbState* st, int* agg, int* inc,
                                                 int max_tiles, unsigned long long* flag, GbEntries En,
-                                                GbParents par, unsigned* freel, int par_by_tab) {
+                                                GbParents par, unsigned* freel, int par_by_tab,
+                                                unsigned long long* pkey, long long* ppos) {
     if (st->halt) return;
-    __shared__ unsigned long long s_scan[PT / 32 + 1];
+    __shared__ unsigned long long s_scan[PT / 32 + 1], s_bk[PT / 32];
+    __shared__ long long s_bq[PT / 32];
     __shared__ long long s_tile;
     __shared__ long long s_ex[3];
     const long long count = st->pool;
@@ -564,8 +603,13 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
     };
     if (nt == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) totals(0, 0, 0);
+        if (pkey && threadIdx.x == 0) pkey[blockIdx.x] = ~0ull, ppos[blockIdx.x] = -1;
         return;
     }
+    // pkey: the smallest key of the kept entries that can be selected (not
+    // final) and its last new position, one pair per block
+    unsigned long long bk = ~0ull;
+    long long bq = -1;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&st->part_ticket, 1ull);
@@ -681,11 +725,18 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
                 par.flo[sel_before] = E.flo[q];
             } else {
                 const long long kr = q - gd - sel_before;
-                En.flo[kr] = E.flo[q];
+                const double v = E.flo[q];
+                const int cy = E.cyc[q];
+                En.flo[kr] = v;
                 En.slot[kr] = E.slot[q];
-                En.cyc[kr] = E.cyc[q];
+                En.cyc[kr] = cy;
+                if (!((unsigned)cy & GB_FINAL_BIT)) better_key(bk, bq, gb_order_key(v), kr);
             }
         }
+    }
+    if (pkey) {
+        block_best(bk, bq, s_bk, s_bq);
+        if (threadIdx.x == 0) pkey[blockIdx.x] = bk, ppos[blockIdx.x] = bq;
     }
 }
 
@@ -1318,23 +1369,63 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
     }
 }
 
+// The survivors into the pool, one warp per survivor.  With the end of the
+// generation fused (K = 1; `pkey` non-null): each block also leaves the
+// smallest key of its new entries that can be selected (not final) and its
+// last position after the npart pairs the partition left, and the last block
+// to finish ends the generation: the parent's slot back to the free list (on
+// overflow the parent back into the pool), the counters rolled forward, and
+// the next selection.  For K = 1 the smallest selectable key of the new pool
+// is all the selection needs: its entry is the next parent when it is below
+// the new incumbent's cut-off threshold, and if it is not, no entry is.
 template <bool PR, bool RECS, bool TAB>
 __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbParents par, GbChildren ch,
                                                      GbSplit sp, GbEntries En, double tol_x, GbState* st,
-                                                     GbTabs Tb) {
+                                                     GbTabs Tb, GbGenConst G, int npart, unsigned long long* pkey,
+                                                     long long* ppos) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __shared__ double2 shF[4][GB_SHG], shM[4][GB_SHG];
     __shared__ float2 sh32[4][GB_SHG];
-    if (st->halt || st->overflow) return;
-    const long long kept = st->kept;
+    __shared__ unsigned long long s_bk[4];
+    __shared__ long long s_bq[4];
+    __shared__ bool s_last;
+    if (st->halt) return;
+    const long long kept = st->overflow ? 0 : st->kept;
+    const long long kept_old = st->kept_old;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long bk = ~0ull;
+    long long bq = -1;
     for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < kept; s += nwarps) {
         if constexpr (RECS)
             materialize_rec<PR, TAB>(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, shF[w], shM[w], sh32[w]);
         else
             materialize_one<PR, TAB>(P, pool, par, ch, sp, En, tol_x, st, s, lane, Tb, shF[w], shM[w], sh32[w]);
         __syncwarp();
+        if (pkey && lane == 0) {   // the entry lane 0 has just written
+            const long long e = kept_old + s;
+            const int cy = En.cyc[e];
+            if (!((unsigned)cy & GB_FINAL_BIT)) better_key(bk, bq, gb_order_key(En.flo[e]), e);
+        }
     }
+    if (!pkey) return;
+    block_best(bk, bq, s_bk, s_bq);
+    if (threadIdx.x == 0) {
+        pkey[npart + blockIdx.x] = bk;
+        ppos[npart + blockIdx.x] = bq;
+        __threadfence();
+        s_last = atomicAdd(&st->stats_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    free_parents(par, pool, En, st, threadIdx.x, blockDim.x);
+    unsigned long long mk;
+    long long mq;
+    combine_pairs(pkey, ppos, npart + (int)gridDim.x, mk, mq, s_bk, s_bq);   // (synchronises the block)
+    if (threadIdx.x != 0) return;
+    finish_counters(G, st);
+    const bool active = mq >= 0 && gb_key_value(mk) < thr_of(gb_key_value(st->gub_key), G.tol_f);
+    open_generation(G, st, active ? 1 : 0, mk, mq);
 }
 
 // ---------------------------------------------------------------------------
@@ -1634,10 +1725,14 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     const unsigned gtile_pool = (unsigned)std::min<long long>(grid_for(cap, GB_TILE), gb_sm_count() * 8);
     const unsigned gtile_ch = (unsigned)std::min<long long>(grid_for(Cmax, GB_TILE), gb_sm_count() * 8);
     const unsigned gch = (unsigned)std::min<long long>(grid_for(Cmax, 128), gb_sm_count() * 32);
+    const unsigned gmat_max = (unsigned)std::min<long long>(grid_for(Cmax * 32, 128), gb_sm_count() * 16);
+    // K = 1: the partition and k_materialize leave per-block (key, position)
+    // pairs and k_materialize's last block ends the generation
+    const bool fuse_end = G.K == 1 && gtile_pool + gmat_max <= (unsigned)GB_STAT_BLOCKS;
     // part 0: the whole generation; 1: up to the child evaluation; 2: after it
     if (part == 2) goto after_eval;
     {
-    // (the selection mode and the K = 1 threshold were set by the last k_stats)
+    // (the selection was chosen at the end of the last generation)
     if (G.K > 1) {
         for (int pass = 0; pass < 4; pass++) {
             gb_launch_count += 2;
@@ -1674,7 +1769,8 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     if (sel_tabs && (e = tables()) != cudaSuccess) return e;
     gb_launch_count++;
     k_part_1p<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_cnt, sc.tile_off, sc.max_tiles, sc.tile_flag, E_new, par,
-                                        pool.freel, sel_tabs ? 1 : 0);
+                                        pool.freel, sel_tabs ? 1 : 0, fuse_end ? sc.stat_key : nullptr,
+                                        fuse_end ? sc.stat_pos : nullptr);
     if (!tabs) {   // with term tables k_ptab splits the parents itself
         gb_launch_count++;
         k_prep<<<grid_for(G.K * (long long)sp.dmax, 128), 128, 0, s>>>(P, pool, par, sp, st);
@@ -1748,21 +1844,28 @@ after_eval:
     GbTabs Tb{};
     if (tabs) Tb = *tabs;
     gb_launch_count++;
-    const unsigned gmat = (unsigned)std::min<long long>(grid_for(Cmax * 32, 128), gb_sm_count() * 16);
+    const unsigned gmat = gmat_max;
+    // K = 1: the generation ends in k_materialize's last block (no k_stats pass)
+    unsigned long long* pk = fuse_end ? sc.stat_key : nullptr;
+    long long* pq = fuse_end ? sc.stat_pos : nullptr;
+    const int np = (int)gtile_pool;
+#define GB_MAT(PR, RECS, TAB)                                                                                      \
+    k_materialize<PR, RECS, TAB><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, G, np, pk, pq)
     // products never use term tables
     if (P.any_prod) {
-        if (pool.recs) k_materialize<true, true, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
-        else k_materialize<true, false, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
+        if (pool.recs) GB_MAT(true, true, false);
+        else GB_MAT(true, false, false);
     } else if (tabs) {
-        if (pool.recs) k_materialize<false, true, true><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
-        else k_materialize<false, false, true><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
+        if (pool.recs) GB_MAT(false, true, true);
+        else GB_MAT(false, false, true);
     } else {
-        if (pool.recs) k_materialize<false, true, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
-        else k_materialize<false, false, false><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb);
+        if (pool.recs) GB_MAT(false, true, false);
+        else GB_MAT(false, false, false);
     }
-    // the end of the generation (parents freed, counters) and the statistics
-    // of the new pool, which start the next generation
-    if ((e = gb_launch_stats(E_new, G, cap, sc, st, s, &par, &pool)) != cudaSuccess) return e;
+#undef GB_MAT
+    // otherwise the end of the generation (parents freed, counters) and the
+    // statistics of the new pool, which start the next generation
+    if (!fuse_end && (e = gb_launch_stats(E_new, G, cap, sc, st, s, &par, &pool)) != cudaSuccess) return e;
     if (nlaunch) *nlaunch = gb_launch_count - n0;
     return cudaGetLastError();
 }
