@@ -186,4 +186,60 @@ __device__ __forceinline__ void warp_group(const GbProg& P, const GbSplitPos& SP
         for (int t = 0; t < NV; t++) out[t] = tr[t].result();
 }
 
+// Exclusive scan of one int per thread over a block (any multiple of 32
+// threads up to 1024; sw: 32 ints of shared memory); *total gets the sum.
+__device__ __forceinline__ int block_excl_scan(int v, int* sw, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) sw[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < nw ? sw[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) sw[lane] = t;
+    }
+    __syncthreads();
+    *total = sw[nw - 1];
+    return x - v + (w ? sw[w - 1] : 0);
+}
+
+// The survivors of a generation (children kept by the FP64 tests whose lower
+// bound is not above the new incumbent), in ascending order, listed by one
+// block: each thread counts a contiguous run of children and one block scan
+// places the runs.  `cg`: the flags were written by other blocks of the
+// running kernel and are read through L2.  Returns the count (every thread).
+__device__ __forceinline__ long long survivor_list_block(const GbChildren& ch, long long n, double gub_new, bool cg,
+                                                         int* sw) {
+    const long long per = (n + blockDim.x - 1) / blockDim.x;
+    const long long i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+    auto pred = [&](long long i) {
+        const unsigned char f = cg ? __ldcg(ch.flag + i) : ch.flag[i];
+        return f != 0 && !((cg ? __ldcg(ch.flo + i) : ch.flo[i]) > gub_new);
+    };
+    int c = 0;
+    for (long long i = i0; i < i1; i++) c += pred(i) ? 1 : 0;
+    int tot;
+    long long o = block_excl_scan(c, sw, &tot);
+    for (long long i = i0; i < i1; i++)
+        if (pred(i)) ch.surv[o++] = (unsigned)i;
+    return tot;
+}
+
+// The generation's survivor count and what it implies: overflow when the
+// pool cannot take them, a record collection when their records do not fit.
+__device__ __forceinline__ void set_survivors(const GbGenConst& G, GbState* st, long long S) {
+    st->kept = S;
+    const long long room = st->nfree + (st->cap - st->bump);
+    st->overflow = S > room ? 1 : 0;
+    st->gc = (!st->overflow && G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
+}
+
 }  // namespace gb

@@ -251,6 +251,8 @@ struct GbState {
     long long rec_gc;                  // block records: collections run
     int gc;                            // block records: collect before this generation's inserts
     unsigned stats_done;               // blocks of k_stats finished (the last one starts the generation)
+    unsigned cc_done;                  // blocks of the child kernel finished (the last one lists the survivors)
+    unsigned part_done;                // blocks of the partition finished (the last one combines their keys)
     unsigned long long min_key;        // smallest active key (K = 1 selection)
     long long evals32, evals64, mids;  // running counters
     unsigned long long ops64, ops32;   // directed-rounding operations executed by the eval kernels

@@ -452,12 +452,6 @@ __device__ __forceinline__ long long ntiles_of(long long items) { return (items 
 
 // Survivor count S of the generation: overflow if the slots cannot take
 // them; with block records, a collection first if their new records do not fit.
-__device__ __forceinline__ void set_survivors(const GbGenConst& G, GbState* st, long long S) {
-    st->kept = S;
-    const long long room = st->nfree + (st->cap - st->bump);
-    st->overflow = S > room ? 1 : 0;
-    st->gc = (!st->overflow && G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
-}
 
 // Exclusive scan of an array of tile counts (one block of 1024 threads,
 // each owning a contiguous run of tiles).
@@ -603,11 +597,12 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
     };
     if (nt == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) totals(0, 0, 0);
-        if (pkey && threadIdx.x == 0) pkey[blockIdx.x] = ~0ull, ppos[blockIdx.x] = -1;
+        if (pkey && blockIdx.x == 0 && threadIdx.x == 0) pkey[0] = ~0ull, ppos[0] = -1;
         return;
     }
     // pkey: the smallest key of the kept entries that can be selected (not
-    // final) and its last new position, one pair per block
+    // final) and its last new position: one pair per block, combined into
+    // pkey[0] by the last block to finish
     unsigned long long bk = ~0ull;
     long long bq = -1;
     for (;;) {
@@ -734,9 +729,23 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
             }
         }
     }
-    if (pkey) {
-        block_best(bk, bq, s_bk, s_bq);
-        if (threadIdx.x == 0) pkey[blockIdx.x] = bk, ppos[blockIdx.x] = bq;
+    if (!pkey) return;
+    __shared__ bool s_last;
+    block_best(bk, bq, s_bk, s_bq);
+    if (threadIdx.x == 0) {
+        pkey[blockIdx.x] = bk;
+        ppos[blockIdx.x] = bq;
+        __threadfence();
+        s_last = atomicAdd(&st->part_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    combine_pairs(pkey, ppos, (int)gridDim.x, bk, bq, s_bk, s_bq);
+    if (threadIdx.x == 0) {
+        pkey[0] = bk;
+        ppos[0] = bq;
+        st->part_done = 0;
     }
 }
 
@@ -1144,19 +1153,9 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
 // does the count, the scan and the scatter.
 __global__ void __launch_bounds__(1024) k_cc_small(GbChildren ch, GbGenConst G, GbState* st) {
     if (st->halt) return;
-    __shared__ int sw[1024 / 32 + 1];
-    const long long n = st->nch;
-    const double gub_new = gb_key_value(st->gub_new_key);
-    long long o = 0;
-    for (long long base = 0; base < n; base += 1024) {
-        const long long i = base + threadIdx.x;
-        const bool f = child_pred(ch, i, n, 1, gub_new);
-        int tot;
-        const int rk = block_prefix<1024>(f, sw, &tot);
-        if (f) ch.surv[o + rk] = (unsigned)i;
-        o += tot;
-    }
-    if (threadIdx.x == 0) set_survivors(G, st, o);
+    __shared__ int sw[32];
+    const long long S = survivor_list_block(ch, st->nch, gb_key_value(st->gub_new_key), false, sw);
+    if (threadIdx.x == 0) set_survivors(G, st, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -1372,7 +1371,7 @@ __device__ __forceinline__ void materialize_rec(const GbProg& P, const GbPool& p
 // The survivors into the pool, one warp per survivor.  With the end of the
 // generation fused (K = 1; `pkey` non-null): each block also leaves the
 // smallest key of its new entries that can be selected (not final) and its
-// last position after the npart pairs the partition left, and the last block
+// last position after the npart pairs of the partition, and the last block
 // to finish ends the generation: the parent's slot back to the free list (on
 // overflow the parent back into the pool), the counters rolled forward, and
 // the next selection.  For K = 1 the smallest selectable key of the new pool
@@ -1728,7 +1727,8 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     const unsigned gmat_max = (unsigned)std::min<long long>(grid_for(Cmax * 32, 128), gb_sm_count() * 16);
     // K = 1: the partition and k_materialize leave per-block (key, position)
     // pairs and k_materialize's last block ends the generation
-    const bool fuse_end = G.K == 1 && gtile_pool + gmat_max <= (unsigned)GB_STAT_BLOCKS;
+    const bool fuse_end = G.K == 1 && gtile_pool <= (unsigned)GB_STAT_BLOCKS && 1 + gmat_max <= (unsigned)GB_STAT_BLOCKS;
+    bool cc_done = false;   // the survivor list came with the child kernel
     // part 0: the whole generation; 1: up to the child evaluation; 2: after it
     if (part == 2) goto after_eval;
     {
@@ -1792,7 +1792,10 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
         // FP32 prefilter and FP64 evaluation in one warp-per-child kernel
         if (ev) cudaEventRecord(ev[2], s), cudaEventRecord(ev[3], s);
         gb_launch_count++;
-        if ((e = gb_launch_eval3264_tabw(P, pool, par, *tabs, ch, Cmax, sp, st, s)) != cudaSuccess) return e;
+        cc_done = Cmax <= (1LL << 16);
+        if ((e = gb_launch_eval3264_tabw(P, pool, par, *tabs, ch, Cmax, sp, st, s, cc_done ? &G : nullptr)) !=
+            cudaSuccess)
+            return e;
         if (ev) cudaEventRecord(ev[1], s);
     } else {
         if (G.fp32) {
@@ -1824,7 +1827,9 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     }
     }
 after_eval:
-    if (Cmax <= (1LL << 16)) {
+    if (cc_done) {
+        // (listed by the child kernel's last block)
+    } else if (Cmax <= (1LL << 16)) {
         gb_launch_count++;
         k_cc_small<<<1, 1024, 0, s>>>(ch, G, st);
     } else {
@@ -1848,7 +1853,7 @@ after_eval:
     // K = 1: the generation ends in k_materialize's last block (no k_stats pass)
     unsigned long long* pk = fuse_end ? sc.stat_key : nullptr;
     long long* pq = fuse_end ? sc.stat_pos : nullptr;
-    const int np = (int)gtile_pool;
+    const int np = 1;   // the partition's combined pair
 #define GB_MAT(PR, RECS, TAB)                                                                                      \
     k_materialize<PR, RECS, TAB><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, G, np, pk, pq)
     // products never use term tables

@@ -1344,8 +1344,11 @@ __global__ void __launch_bounds__(128) k_eval32_tabw(GbProg P, GbPool pool, GbPa
 // whose child passes the FP32 test evaluates it in FP64 at once (the same
 // children, the same previous GUB and the same operations as the FP32 kernel,
 // the survivor list and the FP64 kernel in sequence, without the list).
+// With `cc` (at most 2^16 children) the last block to finish lists the
+// generation's survivors against the final incumbent (k_cc_small's work).
 __global__ void __launch_bounds__(128, 1) k_eval3264_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
-                                                       GbChildren ch, GbSplit sp, GbState* st) {
+                                                       GbChildren ch, GbSplit sp, GbState* st, GbGenConst G,
+                                                       int cc) {
     if (st->halt) return;
     const long long lim = st->nch;
     const double gub_prev = gb_key_value(st->gub_key);
@@ -1378,6 +1381,21 @@ __global__ void __launch_bounds__(128, 1) k_eval3264_tabw(GbProg P, GbPool pool,
         atomicAdd((unsigned long long*)&st->mids, n32);
         atomicAdd((unsigned long long*)&st->kept32, n32);
         atomicAdd((unsigned long long*)&st->n32, n32);
+    }
+    if (!cc) return;
+    __shared__ int s_sw[32];
+    __shared__ bool s_last;
+    __threadfence();   // this thread's flags and bounds, before the block's arrival
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->cc_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double gub_new = gb_key_value(__ldcg((const unsigned long long*)&st->gub_new_key));
+    const long long S = survivor_list_block(ch, lim, gub_new, true, s_sw);
+    if (threadIdx.x == 0) {
+        st->cc_done = 0;
+        set_survivors(G, st, S);
     }
 }
 
@@ -1519,10 +1537,10 @@ cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const Gb
 
 cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                     const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, const GbGenConst* cc) {
     unsigned g = grid_for(Cmax * 32, 128);
     if (g > gb_sm_count() * 32) g = gb_sm_count() * 32;
-    k_eval3264_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st);
+    k_eval3264_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st, cc ? *cc : GbGenConst{}, cc ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -233,9 +233,10 @@ cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParent
 // One child per warp: every child's sums and dirty group values (tables first).
 cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const GbTabs& T, const GbSplit& sp,
                                  long long Cmax, int fp32, GbState* st, cudaStream_t s, bool fixed = false);
+// cc non-null (at most 2^16 children): the kernel's last block also lists the survivors.
 cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                     const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
-                                    cudaStream_t s);
+                                    cudaStream_t s, const GbGenConst* cc = nullptr);
 cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                  const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,
                                  cudaStream_t s);
