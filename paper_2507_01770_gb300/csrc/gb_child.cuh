@@ -213,23 +213,37 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sw, int* total) {
 
 // The survivors of a generation (children kept by the FP64 tests whose lower
 // bound is not above the new incumbent), in ascending order, listed by one
-// block: each thread counts a contiguous run of children and one block scan
-// places the runs.  `cg`: the flags were written by other blocks of the
-// running kernel and are read through L2.  Returns the count (every thread).
+// block: each thread takes a contiguous run of at most 64 children (n <= 64
+// blockDim.x), loads its flags and bounds eight at a time (independent
+// loads), keeps the verdicts as a bit mask, and one block scan places the
+// runs.  `cg`: the flags were written by other blocks of the running kernel
+// and are read through L2.  Returns the count (every thread).
 __device__ __forceinline__ long long survivor_list_block(const GbChildren& ch, long long n, double gub_new, bool cg,
                                                          int* sw) {
-    const long long per = (n + blockDim.x - 1) / blockDim.x;
-    const long long i0 = threadIdx.x * per, i1 = min(n, i0 + per);
-    auto pred = [&](long long i) {
-        const unsigned char f = cg ? __ldcg(ch.flag + i) : ch.flag[i];
-        return f != 0 && !((cg ? __ldcg(ch.flo + i) : ch.flo[i]) > gub_new);
-    };
-    int c = 0;
-    for (long long i = i0; i < i1; i++) c += pred(i) ? 1 : 0;
+    const int per = (int)((n + blockDim.x - 1) / blockDim.x);
+    const long long i0 = (long long)threadIdx.x * per;
+    unsigned long long m = 0;
+    for (int c0 = 0; c0 < per; c0 += 8) {
+        unsigned char f[8];
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const long long i = i0 + c0 + u;
+            const bool in = c0 + u < per && i < n;
+            f[u] = in ? (cg ? __ldcg(ch.flag + i) : ch.flag[i]) : (unsigned char)0;
+            v[u] = in ? (cg ? __ldcg(ch.flo + i) : ch.flo[i]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (f[u] != 0 && !(v[u] > gub_new)) m |= 1ull << (c0 + u);
+    }
     int tot;
-    long long o = block_excl_scan(c, sw, &tot);
-    for (long long i = i0; i < i1; i++)
-        if (pred(i)) ch.surv[o++] = (unsigned)i;
+    long long o = block_excl_scan(__popcll(m), sw, &tot);
+    while (m) {
+        const int b = __ffsll((long long)m) - 1;
+        ch.surv[o++] = (unsigned)(i0 + b);
+        m &= m - 1;
+    }
     return tot;
 }
 
@@ -240,6 +254,7 @@ __device__ __forceinline__ void set_survivors(const GbGenConst& G, GbState* st, 
     const long long room = st->nfree + (st->cap - st->bump);
     st->overflow = S > room ? 1 : 0;
     st->gc = (!st->overflow && G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
+    if (G.gc_cond_on) cudaGraphSetConditional((cudaGraphConditionalHandle)G.gc_cond, st->gc ? 1u : 0u);
 }
 
 }  // namespace gb

@@ -1729,6 +1729,22 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     // pairs and k_materialize's last block ends the generation
     const bool fuse_end = G.K == 1 && gtile_pool <= (unsigned)GB_STAT_BLOCKS && 1 + gmat_max <= (unsigned)GB_STAT_BLOCKS;
     bool cc_done = false;   // the survivor list came with the child kernel
+    // Inside a captured graph with block records, the record collection is a
+    // conditional node: it runs only in the generations whose new records do
+    // not fit (the kernel that lists the survivors sets its condition).
+    GbGenConst Gc = G;
+    if (pool.recs && fork && part != 1) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaGraph_t cg = nullptr;
+        if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr) == cudaSuccess &&
+            cs == cudaStreamCaptureStatusActive) {
+            cudaGraphConditionalHandle h;
+            if ((e = cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+                return e;
+            Gc.gc_cond = (unsigned long long)h;
+            Gc.gc_cond_on = 1;
+        }
+    }
     // part 0: the whole generation; 1: up to the child evaluation; 2: after it
     if (part == 2) goto after_eval;
     {
@@ -1792,8 +1808,8 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
         // FP32 prefilter and FP64 evaluation in one warp-per-child kernel
         if (ev) cudaEventRecord(ev[2], s), cudaEventRecord(ev[3], s);
         gb_launch_count++;
-        cc_done = Cmax <= (1LL << 16);
-        if ((e = gb_launch_eval3264_tabw(P, pool, par, *tabs, ch, Cmax, sp, st, s, cc_done ? &G : nullptr)) !=
+        cc_done = Cmax <= 64LL * 128;   // (at most 64 children per thread of the last block)
+        if ((e = gb_launch_eval3264_tabw(P, pool, par, *tabs, ch, Cmax, sp, st, s, cc_done ? &Gc : nullptr)) !=
             cudaSuccess)
             return e;
         if (ev) cudaEventRecord(ev[1], s);
@@ -1831,20 +1847,50 @@ after_eval:
         // (listed by the child kernel's last block)
     } else if (Cmax <= (1LL << 16)) {
         gb_launch_count++;
-        k_cc_small<<<1, 1024, 0, s>>>(ch, G, st);
+        k_cc_small<<<1, 1024, 0, s>>>(ch, Gc, st);
     } else {
         gb_launch_count += 3;
         k_cc_count<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_cnt);
-        k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 2, 0, G, st);
+        k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 2, 0, Gc, st);
         k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_off, ch.surv);
     }
     if (pool.recs) {
         const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), gb_sm_count() * 8);
-        gb_launch_count += 4;
-        k_gc_mark<<<gb_sm_count() * 8, 256, 0, s>>>(pool, E_new, par, st);
-        k_gc_count<<<grec, PT, 0, s>>>(pool, st, sc.tile_cnt);
-        k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0, G, st);
-        k_gc_scatter<<<grec, PT, 0, s>>>(pool, st, sc.tile_off);
+        cudaStream_t gs = s;
+        if (Gc.gc_cond_on) {
+            // the collection as the body of a conditional node (run when the
+            // survivor listing set its flag), captured on the third stream
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t cg;
+            const cudaGraphNode_t* deps = nullptr;
+            const cudaGraphEdgeData* ed = nullptr;
+            size_t nd = 0;
+            if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &ed, &nd)) != cudaSuccess) return e;
+            cudaGraphNodeParams np{};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = (cudaGraphConditionalHandle)Gc.gc_cond;
+            np.conditional.type = cudaGraphCondTypeIf;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            if ((e = cudaGraphAddNode(&node, cg, deps, ed, nd, &np)) != cudaSuccess) return e;
+            if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+                cudaSuccess)
+                return e;
+            if ((e = cudaStreamBeginCaptureToGraph(fork->s3, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return e;
+            gs = fork->s3;
+        } else {
+            gb_launch_count += 4;
+        }
+        k_gc_mark<<<gb_sm_count() * 8, 256, 0, gs>>>(pool, E_new, par, st);
+        k_gc_count<<<grec, PT, 0, gs>>>(pool, st, sc.tile_cnt);
+        k_scan_tiles<<<1, 1024, 0, gs>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0, G, st);
+        k_gc_scatter<<<grec, PT, 0, gs>>>(pool, st, sc.tile_off);
+        if (gs != s) {
+            cudaGraph_t body = nullptr;
+            if ((e = cudaStreamEndCapture(gs, &body)) != cudaSuccess) return e;
+        }
     }
     GbTabs Tb{};
     if (tabs) Tb = *tabs;

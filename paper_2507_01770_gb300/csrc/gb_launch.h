@@ -128,6 +128,10 @@ struct GbGenConst {
     long long trace_cap;
     int nrec;               // block records: new records per child (0: dense rows)
     long long R;            // block records: capacity
+    // record collection as a conditional node of a captured graph: the
+    // handle the kernel that lists the survivors sets to the collection flag
+    unsigned long long gc_cond;
+    int gc_cond_on;
 };
 
 // Child kernels run one child per warp when a generation has few children
@@ -163,8 +167,10 @@ cudaError_t gb_launch_resume(const GbProg& P, const GbPool& pool, const GbEntrie
 // generation and term tables, the parent's tables (k_ptab, k_ptab_d,
 // k_child_sums) run on s2 beside the pool partition on the main stream (the
 // parent is the pool entry k_stats found), joined before the child kernel.
+// s3: the stream that captures the body of the record collection's
+// conditional node.
 struct GbFork {
-    cudaStream_t s2;
+    cudaStream_t s2, s3;
     cudaEvent_t fork, join;
 };
 cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEntries& E, const GbEntries& E_new,
