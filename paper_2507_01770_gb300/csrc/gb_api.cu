@@ -114,7 +114,6 @@ struct gb_problem {
     GbGenConst G{};
     gb_gen_stat* trace_dev = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // gens_per_sync generations starting on pool buffer 0 / 1
-    bool gc_cond = false;          // graphs hold the record collection as a conditional node (4 kernels per run)
     cudaGraphExec_t gpart[2][2] = {};  // fused serving: [pool buffer][before / after the child evaluation]
     long long part_kernels[2][2] = {};
     long long graph_kernels = 0;
@@ -173,7 +172,6 @@ void gb_destroy_problem(gb_problem* p) {
     if (p->fork.fork) cudaEventDestroy(p->fork.fork);
     if (p->fork.join) cudaEventDestroy(p->fork.join);
     if (p->fork.s2) cudaStreamDestroy(p->fork.s2);
-    if (p->fork.s3) cudaStreamDestroy(p->fork.s3);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -274,7 +272,6 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
     };
     if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking))) return bad(e, "cudaStreamCreate");
     if ((e = cudaStreamCreateWithFlags(&p->fork.s2, cudaStreamNonBlocking)) ||
-        (e = cudaStreamCreateWithFlags(&p->fork.s3, cudaStreamNonBlocking)) ||
         (e = cudaEventCreateWithFlags(&p->fork.fork, cudaEventDisableTiming)) ||
         (e = cudaEventCreateWithFlags(&p->fork.join, cudaEventDisableTiming)))
         return bad(e, "cudaStreamCreate");
@@ -686,7 +683,6 @@ static cudaError_t capture_graphs(gb_problem* p) {
                                      &n1, 0, &p->fork);
             nl += n1;
         }
-        p->gc_cond = p->gc_cond || p->pool.recs;
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -826,7 +822,6 @@ __attribute__((visibility("hidden"))) gb_status solve_finish(gb_problem* p, gb_r
         out->device_ms = ms;
     }
     R.launches += gb_launches_so_far() - l0;
-    if (p->gc_cond) R.launches += 4 * hf.rec_gc;   // the collections' conditional kernels
     out->kernel_launches = R.launches;
     out->ops64 = (int64_t)hf.ops64;
     out->ops32 = (int64_t)hf.ops32;
@@ -926,7 +921,6 @@ static cudaError_t launch_part(gb_problem* p, int cur, int part, long long* nl) 
         long long n1 = 0;
         e = gb_launch_generation(p->P, p->pool, p->E[cur], p->E[1 - cur], p->par, p->ch, p->sp, p->sc, &p->tabs,
                                  p->G, p->cap, p->Cmax, p->st, s, nullptr, &n1, part, &p->fork);
-        p->gc_cond = p->gc_cond || p->pool.recs;
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);

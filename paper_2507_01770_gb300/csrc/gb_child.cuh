@@ -186,6 +186,25 @@ __device__ __forceinline__ void warp_group(const GbProg& P, const GbSplitPos& SP
         for (int t = 0; t < NV; t++) out[t] = tr[t].result();
 }
 
+// A block's arrival at a grid-wide counter of n blocks; every thread calls
+// it and gets true in the last block to arrive.  The block's writes before
+// the call (any thread's: the barrier orders them before thread 0's release
+// fence, which is cumulative) are visible to that last block after it (its
+// thread 0 acquires before the second barrier).  Fences at GPU scope with
+// acquire-release strength: the ordering this needs, without the cost of a
+// sequentially consistent fence in every thread.
+__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned n, bool* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        const bool last = atomicAdd(counter, 1u) == n - 1;
+        if (last) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        *s_flag = last;
+    }
+    __syncthreads();
+    return *s_flag;
+}
+
 // Exclusive scan of one int per thread over a block (any multiple of 32
 // threads up to 1024; sw: 32 ints of shared memory); *total gets the sum.
 __device__ __forceinline__ int block_excl_scan(int v, int* sw, int* total) {
@@ -254,7 +273,6 @@ __device__ __forceinline__ void set_survivors(const GbGenConst& G, GbState* st, 
     const long long room = st->nfree + (st->cap - st->bump);
     st->overflow = S > room ? 1 : 0;
     st->gc = (!st->overflow && G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
-    if (G.gc_cond_on) cudaGraphSetConditional((cudaGraphConditionalHandle)G.gc_cond, st->gc ? 1u : 0u);
 }
 
 }  // namespace gb

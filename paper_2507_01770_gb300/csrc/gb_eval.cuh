@@ -201,11 +201,15 @@ template <typename I> __device__ __noinline__ void slow_rev(int op, I g, I va, I
 }
 
 // Forward interpretation of one template for term index i; returns the root.
+// `sins` / `pre` (both or neither): the template's instructions and the
+// values of its coordinate and coefficient loads, staged by stage_term.
 template <typename T, typename V>
 __device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const GbSum& S, int i,
-                                                         const V& X, typename Prec<T>::I* R, int& ops) {
+                                                         const V& X, typename Prec<T>::I* R, int& ops,
+                                                         const GbIns* sins = nullptr,
+                                                         const typename Prec<T>::I* pre = nullptr) {
     typedef typename Prec<T>::I I;
-    const GbIns* ins = P.tins + S.ins0;
+    const GbIns* ins = sins ? sins : P.tins + S.ins0;
     for (int t = 0; t < S.nins; t++) {
         GbIns in = ins[t];
         ops += in.pad & 0xff;
@@ -214,8 +218,8 @@ __device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const G
         case D_CONST: v = Prec<T>::cst(in); break;
         case D_PI: v = pi_iv((T)0); break;
         case D_EULER: v = e_iv((T)0); break;
-        case D_IVAR: v = X.get(i + in.aux); break;
-        case D_COEF: v = Prec<T>::coef(P, in.aux, i + in.aux2); break;
+        case D_IVAR: v = pre ? pre[t] : X.get(i + in.aux); break;
+        case D_COEF: v = pre ? pre[t] : Prec<T>::coef(P, in.aux, i + in.aux2); break;
         case D_ADD: v = iadd(R[in.a], R[in.b]); break;
         case D_SUB: v = isub(R[in.a], R[in.b]); break;
         case D_MUL: v = imul(R[in.a], R[in.b]); break;
@@ -238,6 +242,23 @@ __device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const G
         R[t] = v;
     }
     return R[S.nins - 1];
+}
+
+// Warp-cooperative staging for term_fwd: lane t (t < nins) loads instruction
+// t of the template into `sins` and, for a coordinate or coefficient load,
+// its value into `pre` -- the loads of all instructions in flight at once,
+// instead of one after the other in the interpreter loop.  Every lane of the
+// warp calls it (the views are the same in every lane).
+template <typename T, typename V>
+__device__ __forceinline__ void stage_term(const GbProg& P, const GbSum& S, int i, const V& X, GbIns* sins,
+                                           typename Prec<T>::I* pre, int lane) {
+    if (lane < S.nins) {
+        const GbIns in = P.tins[S.ins0 + lane];
+        sins[lane] = in;
+        if (in.op == D_IVAR) pre[lane] = X.get(i + in.aux);
+        else if (in.op == D_COEF) pre[lane] = Prec<T>::coef(P, in.aux, i + in.aux2);
+    }
+    __syncwarp();
 }
 
 // Reverse sweep over a bytecode list (forward values V, adjoints A already

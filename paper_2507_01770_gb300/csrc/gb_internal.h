@@ -13,6 +13,14 @@
 #define GB_HD
 #endif
 
+#ifdef __CUDACC__
+// Programmatic dependent launch (see gb_launch_ex): let the stream's next
+// kernel launch once every block of this one has started, and wait for the
+// kernels this one depends on to complete before touching their results.
+__device__ __forceinline__ void gb_grid_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void gb_grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
 // Limits of the bytecode interpreter (registers live in thread-local arrays).
 #define GB_MAX_TREGS 24   // nodes of one ISUM template
 #define GB_MAX_OREGS 32   // nodes of the outer expression

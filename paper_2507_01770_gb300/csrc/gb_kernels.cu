@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "gb_child.cuh"
 #include "gb_eval.cuh"
@@ -304,6 +305,8 @@ __device__ __forceinline__ void open_generation(const GbGenConst& G, GbState* st
 
 __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbState* st, unsigned long long* bkey,
                                                long long* bpos, GbParents par, GbPool pool, int finish) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     __shared__ unsigned long long s_c[8], s_k[8];
     __shared__ long long s_q[8];
@@ -343,13 +346,9 @@ __global__ void __launch_bounds__(256) k_stats(GbEntries E, GbGenConst G, GbStat
         if (tc) atomicAdd((unsigned long long*)&st->active_acc, tc);
         bkey[blockIdx.x] = tk;
         bpos[blockIdx.x] = tq;
-        __threadfence();
-        s_last = atomicAdd(&st->stats_done, 1u) == gridDim.x - 1;
     }
-    __syncthreads();
-    if (!s_last) return;
+    if (!arrive_last(&st->stats_done, gridDim.x, &s_last)) return;
     // last block: combine every block's pair, then start the next generation
-    __threadfence();
     kmin = ~0ull;
     kq = -1;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) better_key(kmin, kq, __ldcg(bkey + b), __ldcg(bpos + b));
@@ -460,6 +459,8 @@ __device__ __forceinline__ long long ntiles_of(long long items) { return (items 
 // records ever used).
 __global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_cnt, int* tile_off, int max_tiles,
                                                      int what, long long out_count, GbGenConst G, GbState* st) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (what != 3 && st->halt) return;
     if (what == 4 && !st->gc) return;
     __shared__ long long part[1024];
@@ -567,6 +568,8 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
                                                 int max_tiles, unsigned long long* flag, GbEntries En,
                                                 GbParents par, unsigned* freel, int par_by_tab,
                                                 unsigned long long* pkey, long long* ppos) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     __shared__ unsigned long long s_scan[PT / 32 + 1], s_bk[PT / 32];
     __shared__ long long s_bq[PT / 32];
@@ -735,12 +738,8 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
     if (threadIdx.x == 0) {
         pkey[blockIdx.x] = bk;
         ppos[blockIdx.x] = bq;
-        __threadfence();
-        s_last = atomicAdd(&st->part_done, 1u) == gridDim.x - 1;
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    if (!arrive_last(&st->part_done, gridDim.x, &s_last)) return;
     combine_pairs(pkey, ppos, (int)gridDim.x, bk, bq, s_bk, s_bq);
     if (threadIdx.x == 0) {
         pkey[0] = bk;
@@ -966,6 +965,8 @@ __device__ __forceinline__ bool child_pred(const GbChildren& ch, long long i, lo
 }
 
 __global__ void k_cc_count(GbChildren ch, int mode, const GbState* st, int* tile_cnt) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     __shared__ int sw[PT / 32 + 1];
     const long long n = st->nch;
@@ -983,6 +984,8 @@ __global__ void k_cc_count(GbChildren ch, int mode, const GbState* st, int* tile
 }
 
 __global__ void k_cc_scatter(GbChildren ch, int mode, const GbState* st, const int* tile_off, unsigned* out) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     __shared__ int sw[PT / 32 + 1];
     const long long n = st->nch;
@@ -1152,6 +1155,8 @@ __device__ __forceinline__ void materialize_one(const GbProg& P, const GbPool& p
 // Survivor list of a generation with at most 2^16 children: one block
 // does the count, the scan and the scatter.
 __global__ void __launch_bounds__(1024) k_cc_small(GbChildren ch, GbGenConst G, GbState* st) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     __shared__ int sw[32];
     const long long S = survivor_list_block(ch, st->nch, gb_key_value(st->gub_new_key), false, sw);
@@ -1167,6 +1172,8 @@ __global__ void __launch_bounds__(1024) k_cc_small(GbChildren ch, GbGenConst G, 
 // parents) with the collection's number, then list the unstamped ones in
 // ascending order as the free list.
 __global__ void k_gc_mark(GbPool pool, GbEntries En, GbParents par, const GbState* st) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt || !st->gc) return;
     const long long nbox = st->kept_old + st->parents, nb = pool.nb;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nbox * nb;
@@ -1182,6 +1189,8 @@ __device__ __forceinline__ bool rec_free(const GbPool& pool, long long id, long 
 }
 
 __global__ void k_gc_count(GbPool pool, const GbState* st, int* tile_cnt) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt || !st->gc) return;
     __shared__ int sw[PT / 32 + 1];
     const long long used = st->rec_bump, nt = ntiles_of(used);
@@ -1197,6 +1206,8 @@ __global__ void k_gc_count(GbPool pool, const GbState* st, int* tile_cnt) {
 }
 
 __global__ void k_gc_scatter(GbPool pool, const GbState* st, const int* tile_off) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt || !st->gc) return;
     __shared__ int sw[PT / 32 + 1];
     const long long used = st->rec_bump, nt = ntiles_of(used);
@@ -1382,6 +1393,8 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
                                                      GbSplit sp, GbEntries En, double tol_x, GbState* st,
                                                      GbTabs Tb, GbGenConst G, int npart, unsigned long long* pkey,
                                                      long long* ppos) {
+    gb_grid_trigger();
+    gb_grid_wait();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __shared__ double2 shF[4][GB_SHG], shM[4][GB_SHG];
     __shared__ float2 sh32[4][GB_SHG];
@@ -1411,12 +1424,8 @@ __global__ void __launch_bounds__(128) k_materialize(GbProg P, GbPool pool, GbPa
     if (threadIdx.x == 0) {
         pkey[npart + blockIdx.x] = bk;
         ppos[npart + blockIdx.x] = bq;
-        __threadfence();
-        s_last = atomicAdd(&st->stats_done, 1u) == gridDim.x - 1;
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    if (!arrive_last(&st->stats_done, gridDim.x, &s_last)) return;
     free_parents(par, pool, En, st, threadIdx.x, blockDim.x);
     unsigned long long mk;
     long long mq;
@@ -1660,6 +1669,17 @@ thread_local long long gb_launch_count = 0;
 
 long long gb_launches_so_far() { return gb_launch_count; }
 
+bool gb_pdl_enabled() {
+    static int on = -1;   // read once
+    int v = __atomic_load_n(&on, __ATOMIC_RELAXED);
+    if (v < 0) {
+        const char* e = std::getenv("GB_NO_PDL");
+        v = (e && e[0] == '1') ? 0 : 1;
+        __atomic_store_n(&on, v, __ATOMIC_RELAXED);
+    }
+    return v != 0;
+}
+
 int gb_sm_count() {
     static int sms[64];   // per device ordinal, 0 until queried
     int dev = 0;
@@ -1708,9 +1728,8 @@ cudaError_t gb_launch_stats(const GbEntries& E, const GbGenConst& G, long long c
     if (g > gb_sm_count() * 8) g = gb_sm_count() * 8;
     if (g > (unsigned)GB_STAT_BLOCKS) g = GB_STAT_BLOCKS;
     gb_launch_count++;
-    k_stats<<<g, 256, 0, s>>>(E, G, st, sc.stat_key, sc.stat_pos, par ? *par : GbParents{}, pool ? *pool : GbPool{},
-                              par ? 1 : 0);
-    return cudaGetLastError();
+    return gb_launch_ex(k_stats, g, 256, 0, s, par != nullptr, E, G, st, sc.stat_key, sc.stat_pos,
+                        par ? *par : GbParents{}, pool ? *pool : GbPool{}, par ? 1 : 0);
 }
 
 cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEntries& E, const GbEntries& E_new,
@@ -1729,22 +1748,6 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     // pairs and k_materialize's last block ends the generation
     const bool fuse_end = G.K == 1 && gtile_pool <= (unsigned)GB_STAT_BLOCKS && 1 + gmat_max <= (unsigned)GB_STAT_BLOCKS;
     bool cc_done = false;   // the survivor list came with the child kernel
-    // Inside a captured graph with block records, the record collection is a
-    // conditional node: it runs only in the generations whose new records do
-    // not fit (the kernel that lists the survivors sets its condition).
-    GbGenConst Gc = G;
-    if (pool.recs && fork && part != 1) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        cudaGraph_t cg = nullptr;
-        if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr) == cudaSuccess &&
-            cs == cudaStreamCaptureStatusActive) {
-            cudaGraphConditionalHandle h;
-            if ((e = cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
-                return e;
-            Gc.gc_cond = (unsigned long long)h;
-            Gc.gc_cond_on = 1;
-        }
-    }
     // part 0: the whole generation; 1: up to the child evaluation; 2: after it
     if (part == 2) goto after_eval;
     {
@@ -1784,9 +1787,14 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
     };
     if (sel_tabs && (e = tables()) != cudaSuccess) return e;
     gb_launch_count++;
-    k_part_1p<<<gtile_pool, PT, 0, s>>>(E, G, st, sc.tile_cnt, sc.tile_off, sc.max_tiles, sc.tile_flag, E_new, par,
-                                        pool.freel, sel_tabs ? 1 : 0, fuse_end ? sc.stat_key : nullptr,
-                                        fuse_end ? sc.stat_pos : nullptr);
+    // beside the tables the partition keeps to two blocks per SM (its blocks
+    // take tiles by ticket, so fewer blocks only take more tiles each) and
+    // leaves room for the table kernels' blocks
+    const unsigned gpart = ts != s ? std::min<unsigned>(gtile_pool, (unsigned)gb_sm_count() * 2) : gtile_pool;
+    if ((e = gb_launch_ex(k_part_1p, gpart, PT, 0, s, true, E, G, st, sc.tile_cnt, sc.tile_off, sc.max_tiles,
+                          sc.tile_flag, E_new, par, pool.freel, sel_tabs ? 1 : 0, fuse_end ? sc.stat_key : nullptr,
+                          fuse_end ? sc.stat_pos : nullptr)) != cudaSuccess)
+        return e;
     if (!tabs) {   // with term tables k_ptab splits the parents itself
         gb_launch_count++;
         k_prep<<<grid_for(G.K * (long long)sp.dmax, 128), 128, 0, s>>>(P, pool, par, sp, st);
@@ -1809,7 +1817,7 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
         if (ev) cudaEventRecord(ev[2], s), cudaEventRecord(ev[3], s);
         gb_launch_count++;
         cc_done = Cmax <= 64LL * 128;   // (at most 64 children per thread of the last block)
-        if ((e = gb_launch_eval3264_tabw(P, pool, par, *tabs, ch, Cmax, sp, st, s, cc_done ? &Gc : nullptr)) !=
+        if ((e = gb_launch_eval3264_tabw(P, pool, par, *tabs, ch, Cmax, sp, st, s, cc_done ? &G : nullptr)) !=
             cudaSuccess)
             return e;
         if (ev) cudaEventRecord(ev[1], s);
@@ -1847,50 +1855,24 @@ after_eval:
         // (listed by the child kernel's last block)
     } else if (Cmax <= (1LL << 16)) {
         gb_launch_count++;
-        k_cc_small<<<1, 1024, 0, s>>>(ch, Gc, st);
+        if ((e = gb_launch_ex(k_cc_small, 1, 1024, 0, s, true, ch, G, st)) != cudaSuccess) return e;
     } else {
         gb_launch_count += 3;
-        k_cc_count<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_cnt);
-        k_scan_tiles<<<1, 1024, 0, s>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 2, 0, Gc, st);
-        k_cc_scatter<<<gtile_ch, PT, 0, s>>>(ch, 1, st, sc.tile_off, ch.surv);
+        if ((e = gb_launch_ex(k_cc_count, gtile_ch, PT, 0, s, true, ch, 1, st, sc.tile_cnt)) != cudaSuccess ||
+            (e = gb_launch_ex(k_scan_tiles, 1, 1024, 0, s, true, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 2, 0LL,
+                              G, st)) != cudaSuccess ||
+            (e = gb_launch_ex(k_cc_scatter, gtile_ch, PT, 0, s, true, ch, 1, st, sc.tile_off, ch.surv)) != cudaSuccess)
+            return e;
     }
     if (pool.recs) {
         const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), gb_sm_count() * 8);
-        cudaStream_t gs = s;
-        if (Gc.gc_cond_on) {
-            // the collection as the body of a conditional node (run when the
-            // survivor listing set its flag), captured on the third stream
-            cudaStreamCaptureStatus cs;
-            cudaGraph_t cg;
-            const cudaGraphNode_t* deps = nullptr;
-            const cudaGraphEdgeData* ed = nullptr;
-            size_t nd = 0;
-            if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &ed, &nd)) != cudaSuccess) return e;
-            cudaGraphNodeParams np{};
-            np.type = cudaGraphNodeTypeConditional;
-            np.conditional.handle = (cudaGraphConditionalHandle)Gc.gc_cond;
-            np.conditional.type = cudaGraphCondTypeIf;
-            np.conditional.size = 1;
-            cudaGraphNode_t node;
-            if ((e = cudaGraphAddNode(&node, cg, deps, ed, nd, &np)) != cudaSuccess) return e;
-            if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
-                cudaSuccess)
-                return e;
-            if ((e = cudaStreamBeginCaptureToGraph(fork->s3, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                                   cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-                return e;
-            gs = fork->s3;
-        } else {
-            gb_launch_count += 4;
-        }
-        k_gc_mark<<<gb_sm_count() * 8, 256, 0, gs>>>(pool, E_new, par, st);
-        k_gc_count<<<grec, PT, 0, gs>>>(pool, st, sc.tile_cnt);
-        k_scan_tiles<<<1, 1024, 0, gs>>>(1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0, G, st);
-        k_gc_scatter<<<grec, PT, 0, gs>>>(pool, st, sc.tile_off);
-        if (gs != s) {
-            cudaGraph_t body = nullptr;
-            if ((e = cudaStreamEndCapture(gs, &body)) != cudaSuccess) return e;
-        }
+        gb_launch_count += 4;
+        if ((e = gb_launch_ex(k_gc_mark, gb_sm_count() * 8, 256, 0, s, true, pool, E_new, par, st)) != cudaSuccess ||
+            (e = gb_launch_ex(k_gc_count, grec, PT, 0, s, true, pool, st, sc.tile_cnt)) != cudaSuccess ||
+            (e = gb_launch_ex(k_scan_tiles, 1, 1024, 0, s, true, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0LL, G,
+                              st)) != cudaSuccess ||
+            (e = gb_launch_ex(k_gc_scatter, grec, PT, 0, s, true, pool, st, sc.tile_off)) != cudaSuccess)
+            return e;
     }
     GbTabs Tb{};
     if (tabs) Tb = *tabs;
@@ -1901,7 +1883,8 @@ after_eval:
     long long* pq = fuse_end ? sc.stat_pos : nullptr;
     const int np = 1;   // the partition's combined pair
 #define GB_MAT(PR, RECS, TAB)                                                                                      \
-    k_materialize<PR, RECS, TAB><<<gmat, 128, 0, s>>>(P, pool, par, ch, sp, E_new, G.tol_x, st, Tb, G, np, pk, pq)
+    e = gb_launch_ex(k_materialize<PR, RECS, TAB>, gmat, 128, 0, s, true, P, pool, par, ch, sp, E_new, G.tol_x,   \
+                     st, Tb, G, np, pk, pq)
     // products never use term tables
     if (P.any_prod) {
         if (pool.recs) GB_MAT(true, true, false);
@@ -1914,6 +1897,7 @@ after_eval:
         else GB_MAT(false, false, false);
     }
 #undef GB_MAT
+    if (e != cudaSuccess) return e;
     // otherwise the end of the generation (parents freed, counters) and the
     // statistics of the new pool, which start the next generation
     if (!fuse_end && (e = gb_launch_stats(E_new, G, cap, sc, st, s, &par, &pool)) != cudaSuccess) return e;

@@ -140,6 +140,8 @@ __device__ __forceinline__ int4 parent_split(const GbProg& P, const GbPool& pool
 
 __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParents par, GbTabs T, GbSplit sp,
                                                  int row_blocks, GbState* st, GbEntries E, int from_sel) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     extern __shared__ double2 s_tree[];   // T.max_sum_nodes entries when the trees fit
     __shared__ double s_bnd[GB_MAX_SPLIT_D * 5];
@@ -164,11 +166,24 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
         st->children = 0;
         st->overflow = 0;
     }
-    const int4 info = parent_split(P, pool, par, sp, p, slot, cyc, s_bnd, s_brd, s_bru, blockIdx.x == 0);
+    // the split position's tables (they depend on the cycling position only:
+    // its dirty terms are staged while the split's box loads are in flight)
+    const int spi = P.sp_of_cyc[cyc & 0x7fffffff];
+    const bool rows = (int)blockIdx.x < row_blocks;
+    __shared__ int s_row[PTAB_SMEM_DT];
+    GbSplitPos SP{};
+    bool staged = false;
+    if (rows && spi >= 0) {
+        SP = P.sps[spi];
+        staged = SP.ndterm <= PTAB_SMEM_DT;
+        if (staged)
+            for (int t = threadIdx.x; t < SP.ndterm; t += blockDim.x) s_row[t] = P.dterms[SP.dterm0 + t].row;
+    }
+    int4 info = make_int4(0, 0, 0, 0);
+    if (rows) info = parent_split(P, pool, par, sp, p, slot, cyc, s_bnd, s_brd, s_bru, blockIdx.x == 0);
     __syncthreads();
-    const int spi = P.sp_of_cyc[info.x];
     if (spi < 0) return;
-    if ((int)blockIdx.x >= row_blocks) {
+    if (!rows) {
         // group tree job (k, kind)
         const int kinds = pool.fp32 ? 3 : 2;
         const int job = blockIdx.x - row_blocks;
@@ -184,18 +199,13 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
         warp_add_ops(tops, kind == 2 ? &st->ops32 : &st->ops64);
         return;
     }
-    const GbSplitPos SP = P.sps[spi];
-    // the split position's dirty terms, staged for the row -> term lookup
-    __shared__ int s_row[PTAB_SMEM_DT];
-    const bool staged = SP.ndterm <= PTAB_SMEM_DT;
-    if (staged)
-        for (int t = threadIdx.x; t < SP.ndterm; t += blockDim.x) s_row[t] = P.dterms[SP.dterm0 + t].row;
-    __syncthreads();
     const int parts = ptab_parts(pool);
     int ops = 0, ops32 = 0;
-    const int wib = threadIdx.x >> 5;
-    for (int item = blockIdx.x * PTAB_ITEMS + wib; (threadIdx.x & 31) == 0 && item < SP.tab_entries * parts;
-         item += row_blocks * PTAB_ITEMS) {
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // per warp: the template's instructions and load values (stage_term)
+    __shared__ GbIns s_ins[PTAB_ITEMS][GB_MAX_TREGS];
+    __shared__ double2 s_pre[PTAB_ITEMS][GB_MAX_TREGS];
+    for (int item = blockIdx.x * PTAB_ITEMS + wib; item < SP.tab_entries * parts; item += row_blocks * PTAB_ITEMS) {
         const int row = item / parts, part = item - row * parts;
         // the dirty term owning this row (rows are contiguous per term)
         int lo = 0, hi = SP.ndterm - 1;
@@ -209,8 +219,9 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
         const GbSum S = P.sums[D.sum];
         const int i = S.first + D.term * S.step;
         const size_t orow = (size_t)p * T.max_rows + row;
+        const GbIns* ins = s_ins[wib];
         if (part < 2) {
-            iv64 R[GB_MAX_TREGS];
+            iv64* pre = reinterpret_cast<iv64*>(s_pre[wib]);
             View<double> X = box_view64(pool, slot);
             X.blo = s_bnd;
             X.bhi = s_bnd;
@@ -220,24 +231,31 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             X.mstride = sp.m + 1;
             X.r = r;
             if (part == 1) {
-                const iv64 v = term_fwd<double>(P, S, i, MidView{X}, R, ops);
-                T.tm64[orow] = make_double2(v.lo, v.hi);
+                stage_term<double>(P, S, i, MidView{X}, s_ins[wib], pre, lane);
+                if (lane == 0) {
+                    iv64 R[GB_MAX_TREGS];
+                    const iv64 v = term_fwd<double>(P, S, i, MidView{X}, R, ops, ins, pre);
+                    T.tm64[orow] = make_double2(v.lo, v.hi);
+                }
             } else {
-                iv64 RA[GB_MAX_TREGS];
-                const iv64 v = term_fwd<double>(P, S, i, X, R, ops);
-                T.tv64[orow] = make_double2(v.lo, v.hi);
-                for (int t = 0; t < S.nins; t++) RA[t] = iv64{0.0, 0.0};
-                RA[S.nins - 1] = iv64{1.0, 1.0};
-                reverse_sweep<double>(P.tins + S.ins0, S.nins, R, RA, ops);
-                int leaf = 0;
-                for (int t = 0; t < S.nins; t++) {
-                    if (P.tins[S.ins0 + t].op != D_IVAR) continue;
-                    T.tl64[orow * T.max_leaves + leaf] = make_double2(RA[t].lo, RA[t].hi);
-                    leaf++;
+                stage_term<double>(P, S, i, X, s_ins[wib], pre, lane);
+                if (lane == 0) {
+                    iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS];
+                    const iv64 v = term_fwd<double>(P, S, i, X, R, ops, ins, pre);
+                    T.tv64[orow] = make_double2(v.lo, v.hi);
+                    for (int t = 0; t < S.nins; t++) RA[t] = iv64{0.0, 0.0};
+                    RA[S.nins - 1] = iv64{1.0, 1.0};
+                    reverse_sweep<double>(ins, S.nins, R, RA, ops);
+                    int leaf = 0;
+                    for (int t = 0; t < S.nins; t++) {
+                        if (ins[t].op != D_IVAR) continue;
+                        T.tl64[orow * T.max_leaves + leaf] = make_double2(RA[t].lo, RA[t].hi);
+                        leaf++;
+                    }
                 }
             }
         } else {
-            iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS];
+            iv32* pre = reinterpret_cast<iv32*>(s_pre[wib]);
             View<float> X32 = box_view32(pool, slot);
             X32.blo = s_brd;
             X32.bhi = s_bru;
@@ -246,18 +264,23 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             X32.mshift = sp.mshift;
             X32.mstride = sp.m + 1;
             X32.r = r;
-            const iv32 f = term_fwd<float>(P, S, i, X32, R32, ops32);
-            T.tv32[orow] = make_float2(f.lo, f.hi);
-            for (int t = 0; t < S.nins; t++) RA32[t] = iv32{0.f, 0.f};
-            RA32[S.nins - 1] = iv32{1.f, 1.f};
-            reverse_sweep<float>(P.tins + S.ins0, S.nins, R32, RA32, ops32);
-            int leaf = 0;
-            for (int t = 0; t < S.nins; t++) {
-                if (P.tins[S.ins0 + t].op != D_IVAR) continue;
-                T.tl32[orow * T.max_leaves + leaf] = make_float2(RA32[t].lo, RA32[t].hi);
-                leaf++;
+            stage_term<float>(P, S, i, X32, s_ins[wib], pre, lane);
+            if (lane == 0) {
+                iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS];
+                const iv32 f = term_fwd<float>(P, S, i, X32, R32, ops32, ins, pre);
+                T.tv32[orow] = make_float2(f.lo, f.hi);
+                for (int t = 0; t < S.nins; t++) RA32[t] = iv32{0.f, 0.f};
+                RA32[S.nins - 1] = iv32{1.f, 1.f};
+                reverse_sweep<float>(ins, S.nins, R32, RA32, ops32);
+                int leaf = 0;
+                for (int t = 0; t < S.nins; t++) {
+                    if (ins[t].op != D_IVAR) continue;
+                    T.tl32[orow * T.max_leaves + leaf] = make_float2(RA32[t].lo, RA32[t].hi);
+                    leaf++;
+                }
             }
         }
+        __syncwarp();   // the staging is reused by the warp's next item
     }
     warp_add_ops(ops, &st->ops64);   // one atomic per warp (every lane reaches here)
     warp_add_ops(ops32, &st->ops32);
@@ -284,6 +307,8 @@ template <typename I> __device__ __forceinline__ I shfl_down_iv(I v, int d) {
 
 __global__ void __launch_bounds__(128) k_ptab_d(GbProg P, GbPool pool, GbParents par, GbTabs T,
                                                 GbState* st, int fixed) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     const long long p = blockIdx.y;
     if (!fixed && p >= st->parents) return;
@@ -596,6 +621,8 @@ __device__ __forceinline__ void child_sum(const GbProg& P, const GbSplitPos& SP,
 
 __global__ void __launch_bounds__(128) k_child_sums(GbProg P, GbParents par, GbTabs Tb, GbSplit sp, long long Cmax,
                                                     int kinds, GbState* st, long long nch_fixed) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long ci = t % Cmax, rest = t / Cmax;
@@ -902,6 +929,8 @@ __device__ __forceinline__ void eval64_tab_mono(const GbProg& P, const GbPool& p
 template <bool QUEUE>
 __global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval64_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
                                                     GbChildren ch, GbSplit sp, int from_list, GbState* st) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     __shared__ unsigned s_queue[4][QUEUE ? 64 : 1];   // per warp: at most 31 left over + 32 new
     const long long lim = from_list ? st->n32 : st->nch;
@@ -1349,6 +1378,8 @@ __global__ void __launch_bounds__(128) k_eval32_tabw(GbProg P, GbPool pool, GbPa
 __global__ void __launch_bounds__(128, 1) k_eval3264_tabw(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
                                                        GbChildren ch, GbSplit sp, GbState* st, GbGenConst G,
                                                        int cc) {
+    gb_grid_trigger();
+    gb_grid_wait();
     if (st->halt) return;
     const long long lim = st->nch;
     const double gub_prev = gb_key_value(st->gub_key);
@@ -1385,12 +1416,7 @@ __global__ void __launch_bounds__(128, 1) k_eval3264_tabw(GbProg P, GbPool pool,
     if (!cc) return;
     __shared__ int s_sw[32];
     __shared__ bool s_last;
-    __threadfence();   // this thread's flags and bounds, before the block's arrival
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->cc_done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    if (!arrive_last(&st->cc_done, gridDim.x, &s_last)) return;
     const double gub_new = gb_key_value(__ldcg((const unsigned long long*)&st->gub_new_key));
     const long long S = survivor_list_block(ch, lim, gub_new, true, s_sw);
     if (threadIdx.x == 0) {
@@ -1491,11 +1517,8 @@ cudaError_t gb_launch_ptab(const GbProg& P, const GbPool& pool, const GbParents&
     int row_blocks = (P.max_rows * parts + PTAB_ITEMS - 1) / PTAB_ITEMS;
     if (row_blocks < 1) row_blocks = 1;
     const size_t smem = T.tree_smem ? (size_t)T.max_sum_nodes * sizeof(double2) : 0;
-    k_ptab<<<dim3((unsigned)(row_blocks + P.n_sum * kinds), (unsigned)K), PTAB_T, smem, s>>>(P, pool, par, T, sp,
-                                                                                             row_blocks, st,
-                                                                                             Esel ? *Esel : GbEntries{},
-                                                                                             Esel ? 1 : 0);
-    return cudaGetLastError();
+    return gb_launch_ex(k_ptab, dim3((unsigned)(row_blocks + P.n_sum * kinds), (unsigned)K), PTAB_T, smem, s, true, P,
+                        pool, par, T, sp, row_blocks, st, Esel ? *Esel : GbEntries{}, Esel ? 1 : 0);
 }
 
 cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
@@ -1509,9 +1532,8 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
     }
     unsigned g = grid_for(Cmax, 128);
     if (g > gb_sm_count() * GB_TAB_GRID) g = gb_sm_count() * GB_TAB_GRID;
-    if (P.outer_sum) k_eval64_tab<true><<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
-    else k_eval64_tab<false><<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
-    return cudaGetLastError();
+    return gb_launch_ex(P.outer_sum ? k_eval64_tab<true> : k_eval64_tab<false>, g, 128, 0, s, true, P, pool, par, T,
+                        ch, sp, from_list ? 1 : 0, st);
 }
 
 cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
@@ -1521,8 +1543,7 @@ cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParent
                                                 (long long)P.max_nseg << (GB_TAB_SBITS + 5));
     unsigned g = grid_for(items, 128);
     if (g > (unsigned)gb_sm_count() * 16) g = gb_sm_count() * 16;
-    k_ptab_d<<<dim3(g, (unsigned)K), 128, 0, s>>>(P, pool, par, T, st, fixed ? 1 : 0);
-    return cudaGetLastError();
+    return gb_launch_ex(k_ptab_d, dim3(g, (unsigned)K), 128, 0, s, true, P, pool, par, T, st, fixed ? 1 : 0);
 }
 
 cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const GbTabs& T, const GbSplit& sp,
@@ -1531,8 +1552,8 @@ cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const Gb
     const int kinds = fp32 ? 3 : 2;
     // fixed: one parent, its 2^flog2 children (the count is not read from the state)
     const long long nch = fixed ? (1LL << sp.flog2) : -1;
-    k_child_sums<<<grid_for(Cmax * P.n_sum * kinds, 128), 128, 0, s>>>(P, par, T, sp, Cmax, kinds, st, nch);
-    return cudaGetLastError();
+    return gb_launch_ex(k_child_sums, grid_for(Cmax * P.n_sum * kinds, 128), 128, 0, s, true, P, par, T, sp, Cmax,
+                        kinds, st, nch);
 }
 
 cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
@@ -1540,8 +1561,8 @@ cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const G
                                     cudaStream_t s, const GbGenConst* cc) {
     unsigned g = grid_for(Cmax * 32, 128);
     if (g > gb_sm_count() * 32) g = gb_sm_count() * 32;
-    k_eval3264_tabw<<<g, 128, 0, s>>>(P, pool, par, T, ch, sp, st, cc ? *cc : GbGenConst{}, cc ? 1 : 0);
-    return cudaGetLastError();
+    return gb_launch_ex(k_eval3264_tabw, g, 128, 0, s, true, P, pool, par, T, ch, sp, st, cc ? *cc : GbGenConst{},
+                        cc ? 1 : 0);
 }
 
 cudaError_t gb_launch_eval32_tab(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,

@@ -128,10 +128,6 @@ struct GbGenConst {
     long long trace_cap;
     int nrec;               // block records: new records per child (0: dense rows)
     long long R;            // block records: capacity
-    // record collection as a conditional node of a captured graph: the
-    // handle the kernel that lists the survivors sets to the collection flag
-    unsigned long long gc_cond;
-    int gc_cond_on;
 };
 
 // Child kernels run one child per warp when a generation has few children
@@ -167,10 +163,8 @@ cudaError_t gb_launch_resume(const GbProg& P, const GbPool& pool, const GbEntrie
 // generation and term tables, the parent's tables (k_ptab, k_ptab_d,
 // k_child_sums) run on s2 beside the pool partition on the main stream (the
 // parent is the pool entry k_stats found), joined before the child kernel.
-// s3: the stream that captures the body of the record collection's
-// conditional node.
 struct GbFork {
-    cudaStream_t s2, s3;
+    cudaStream_t s2;
     cudaEvent_t fork, join;
 };
 cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEntries& E, const GbEntries& E_new,
@@ -207,6 +201,31 @@ cudaError_t gb_launch_peak(int which, int iters, int blocks, void* sink, cudaStr
 long long gb_launches_so_far();
 // Streaming multiprocessors of the current device (queried once per device).
 int gb_sm_count();
+
+// Programmatic dependent launch.  A kernel of the generation path starts with
+// gb_grid_trigger() (its own dependent may be launched once all of its blocks
+// have started) and gb_grid_wait() (it touches nothing before the kernels it
+// depends on have completed and their writes are visible), so a launch with
+// `pdl` overlaps its launch and block scheduling with the end of its
+// predecessor in the stream.  A kernel launched without `pdl` waits as
+// usual and the two calls return at once.  The environment variable
+// GB_NO_PDL=1 turns the overlap off.
+bool gb_pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t gb_launch_ex(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                                Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = (pdl && gb_pdl_enabled()) ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
+}
 extern "C" const GbProg* gb_internal_prog(const gb_problem* p, int* device, int* n, int* nb);
 extern "C" gb_status gb_internal_fail(gb_status s, const char* msg);
 // resumable solve (gb_api.cu), used by the serving loop (gb_server.cpp)
