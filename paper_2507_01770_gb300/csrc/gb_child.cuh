@@ -267,12 +267,12 @@ __device__ __forceinline__ long long survivor_list_block(const GbChildren& ch, l
 }
 
 // The generation's survivor count and what it implies: overflow when the
-// pool cannot take them, a record collection when their records do not fit.
+// pool cannot take them or their block records do not fit (after the
+// generation's record collection, if it ran).
 __device__ __forceinline__ void set_survivors(const GbGenConst& G, GbState* st, long long S) {
     st->kept = S;
     const long long room = st->nfree + (st->cap - st->bump);
-    st->overflow = S > room ? 1 : 0;
-    st->gc = (!st->overflow && G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
+    st->overflow = (S > room || (G.nrec && S * G.nrec > st->rec_nfree + (G.R - st->rec_bump))) ? 1 : 0;
 }
 
 }  // namespace gb

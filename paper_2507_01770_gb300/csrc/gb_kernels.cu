@@ -499,7 +499,6 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int narr, const int* tile_c
         set_survivors(G, st, tot[0]);
     } else if (what == 4) {
         st->rec_nfree = tot[0];
-        if (st->kept * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) st->overflow = 1;
     } else {
         st->kept = tot[0];
     }
@@ -597,6 +596,8 @@ __global__ void __launch_bounds__(PT) k_part_1p(GbEntries E, GbGenConst G, GbSta
         st->nfree = nfree + D;
         st->sel_below = Bl;
         st->sel_ties = Tt;
+        // a record collection when the generation's children might not fit
+        st->gc = (G.nrec && (npar << G.flog2) * G.nrec > st->rec_nfree + (G.R - st->rec_bump)) ? 1 : 0;
     };
     if (nt == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) totals(0, 0, 0);
@@ -1166,20 +1167,25 @@ __global__ void __launch_bounds__(1024) k_cc_small(GbChildren ch, GbGenConst G, 
 // ---------------------------------------------------------------------------
 // Block records: a box's row names one record per block, and a child shares
 // all but the records of the blocks it changes with its parent, so a record
-// is referenced by many boxes and is freed by a mark-and-sweep collection,
-// run only when the new records of a generation do not fit: stamp the records
-// named by the boxes still alive (entries carried over and this generation's
-// parents) with the collection's number, then list the unstamped ones in
-// ascending order as the free list.
-__global__ void k_gc_mark(GbPool pool, GbEntries En, GbParents par, const GbState* st) {
+// is referenced by many boxes and is freed by a mark-and-sweep collection.
+// It runs right after the pool partition, when the generation's new records
+// might not fit (the partition's verdict: the most children a generation can
+// keep, times the records a child writes, against the free and never-used
+// records): stamp the records named by the boxes still alive (entries carried
+// over and this generation's parents) with the collection's number, then
+// list the unstamped ones in ascending order as the free list.  With one
+// parent taken from its pool position (sel), the parent's slot is read there
+// (the parent buffer is written by the table kernel, which may be running).
+__global__ void k_gc_mark(GbPool pool, GbEntries En, GbParents par, const GbState* st, GbEntries E, int sel) {
     gb_grid_trigger();
     gb_grid_wait();
     if (st->halt || !st->gc) return;
     const long long nbox = st->kept_old + st->parents, nb = pool.nb;
+    const unsigned sel_slot = sel ? E.slot[st->sel_pos] : 0u;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nbox * nb;
          i += (long long)gridDim.x * blockDim.x) {
         const long long q = i / nb, b = i - q * nb;
-        const unsigned slot = q < st->kept_old ? En.slot[q] : par.slot[q - st->kept_old];
+        const unsigned slot = q < st->kept_old ? En.slot[q] : (sel ? sel_slot : par.slot[q - st->kept_old]);
         pool.rmark[pool.rid[(size_t)slot * nb + b]] = (unsigned)(st->rec_gc + 1);
     }
 }
@@ -1795,6 +1801,17 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
                           sc.tile_flag, E_new, par, pool.freel, sel_tabs ? 1 : 0, fuse_end ? sc.stat_key : nullptr,
                           fuse_end ? sc.stat_pos : nullptr)) != cudaSuccess)
         return e;
+    if (pool.recs) {   // the record collection, when the partition asked for it
+        const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), gb_sm_count() * 8);
+        gb_launch_count += 4;
+        if ((e = gb_launch_ex(k_gc_mark, gb_sm_count() * 8, 256, 0, s, true, pool, E_new, par, st, E,
+                              sel_tabs ? 1 : 0)) != cudaSuccess ||
+            (e = gb_launch_ex(k_gc_count, grec, PT, 0, s, true, pool, st, sc.tile_cnt)) != cudaSuccess ||
+            (e = gb_launch_ex(k_scan_tiles, 1, 1024, 0, s, true, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0LL, G,
+                              st)) != cudaSuccess ||
+            (e = gb_launch_ex(k_gc_scatter, grec, PT, 0, s, true, pool, st, sc.tile_off)) != cudaSuccess)
+            return e;
+    }
     if (!tabs) {   // with term tables k_ptab splits the parents itself
         gb_launch_count++;
         k_prep<<<grid_for(G.K * (long long)sp.dmax, 128), 128, 0, s>>>(P, pool, par, sp, st);
@@ -1862,16 +1879,6 @@ after_eval:
             (e = gb_launch_ex(k_scan_tiles, 1, 1024, 0, s, true, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 2, 0LL,
                               G, st)) != cudaSuccess ||
             (e = gb_launch_ex(k_cc_scatter, gtile_ch, PT, 0, s, true, ch, 1, st, sc.tile_off, ch.surv)) != cudaSuccess)
-            return e;
-    }
-    if (pool.recs) {
-        const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), gb_sm_count() * 8);
-        gb_launch_count += 4;
-        if ((e = gb_launch_ex(k_gc_mark, gb_sm_count() * 8, 256, 0, s, true, pool, E_new, par, st)) != cudaSuccess ||
-            (e = gb_launch_ex(k_gc_count, grec, PT, 0, s, true, pool, st, sc.tile_cnt)) != cudaSuccess ||
-            (e = gb_launch_ex(k_scan_tiles, 1, 1024, 0, s, true, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0LL, G,
-                              st)) != cudaSuccess ||
-            (e = gb_launch_ex(k_gc_scatter, grec, PT, 0, s, true, pool, st, sc.tile_off)) != cudaSuccess)
             return e;
     }
     GbTabs Tb{};
