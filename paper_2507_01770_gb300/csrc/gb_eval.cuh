@@ -200,10 +200,31 @@ template <typename I> __device__ __noinline__ void slow_rev(int op, I g, I va, I
     }
 }
 
+// The same, for lanes 0 and 1 of a warp interpreting the same template
+// together (PAIR interpreters): exp, sin and cos evaluate their two
+// endpoints in the two lanes (iexp_pair, itrig_pair); the other operations
+// run in both lanes alike.
+template <typename I> __device__ __noinline__ I slow_fwd_pair(int op, I a, I b) {
+    switch (op) {
+    case D_EXP: return iexp_pair(a);
+    case D_SIN: return itrig_pair(a, false);
+    case D_COS: return itrig_pair(a, true);
+    default: return slow_fwd(op, a, b);
+    }
+}
+template <typename I> __device__ __noinline__ void slow_rev_pair(int op, I g, I va, I vb, I vt, I* da, I* db) {
+    switch (op) {
+    case D_SIN: *da = imul(g, itrig_pair(va, true)); break;
+    case D_COS: *da = imul(g, ineg(itrig_pair(va, false))); break;
+    default: slow_rev(op, g, va, vb, vt, da, db); break;
+    }
+}
+
 // Forward interpretation of one template for term index i; returns the root.
 // `sins` / `pre` (both or neither): the template's instructions and the
 // values of its coordinate and coefficient loads, staged by stage_term.
-template <typename T, typename V>
+// PAIR: run by lanes 0 and 1 of a warp together (slow_fwd_pair).
+template <typename T, typename V, bool PAIR = false>
 __device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const GbSum& S, int i,
                                                          const V& X, typename Prec<T>::I* R, int& ops,
                                                          const GbIns* sins = nullptr,
@@ -227,10 +248,10 @@ __device__ __forceinline__ typename Prec<T>::I term_fwd(const GbProg& P, const G
         case D_SQR: v = isqr(R[in.a]); break;
         case D_DIV: v = slow_fwd(in.op, R[in.a], R[in.b]); break;
         case D_SQRT:
+        case D_STEP: v = slow_fwd(in.op, R[in.a], R[in.a]); break;
         case D_EXP:
         case D_SIN:
-        case D_STEP:
-        case D_COS: v = slow_fwd(in.op, R[in.a], R[in.a]); break;
+        case D_COS: v = PAIR ? slow_fwd_pair(in.op, R[in.a], R[in.a]) : slow_fwd(in.op, R[in.a], R[in.a]); break;
         case D_SCALE:
             if (in.clo32 == in.chi32 || sizeof(T) == 8)
                 v = iscale(R[in.a], sizeof(T) == 8 ? (T)in.c : (T)in.clo32);
@@ -264,7 +285,7 @@ __device__ __forceinline__ void stage_term(const GbProg& P, const GbSum& S, int 
 // Reverse sweep over a bytecode list (forward values V, adjoints A already
 // seeded).  Node t pushes into its first, then its second operand; a node's
 // adjoint thus receives its consumers' contributions in descending order.
-template <typename T>
+template <typename T, bool PAIR = false>
 __device__ __forceinline__ void reverse_sweep(const GbIns* ins, int nins, const typename Prec<T>::I* V,
                                               typename Prec<T>::I* A, int& ops) {
     typedef typename Prec<T>::I I;
@@ -302,7 +323,8 @@ __device__ __forceinline__ void reverse_sweep(const GbIns* ins, int nins, const 
         case D_STEP:
         case D_COS: {
             I da, db;
-            slow_rev(in.op, g, V[in.a], V[in.a], V[t], &da, &db);
+            if (PAIR) slow_rev_pair(in.op, g, V[in.a], V[in.a], V[t], &da, &db);
+            else slow_rev(in.op, g, V[in.a], V[in.a], V[t], &da, &db);
             A[in.a] = iadd(A[in.a], da);
             break;
         }

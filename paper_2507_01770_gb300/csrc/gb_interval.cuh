@@ -334,4 +334,64 @@ template <typename I> __device__ __forceinline__ I itrig(I x, bool is_cos) {
     return r;
 }
 
+// Two-lane forms of iexp and itrig for lanes 0 and 1 of a warp that hold the
+// same argument (both run the same interpreter; the table kernel does): lane
+// h evaluates the library function at endpoint h, and for itrig the
+// directed division of endpoint h by pi, and the two lanes exchange them --
+// the values of iexp / itrig, with the two endpoint evaluations side by side
+// instead of one after the other.  RU(a / b) is taken as -RD(-a / b), the
+// same number under IEEE directed rounding.
+template <typename T> __device__ __forceinline__ T pair_get(T v, int src) { return __shfl_sync(0x3u, v, src); }
+
+template <typename I> __device__ __forceinline__ I iexp_pair(I x) {
+    typedef decltype(x.lo) T;
+    const int h = threadIdx.x & 1;
+    const T v = lib_exp(h ? x.hi : x.lo);
+    const T a = pair_get(v, 0), vb = pair_get(v, 1);
+    const T b = x.hi == x.lo ? a : vb;
+    I r;
+    r.lo = step_dn(a, k_exp<T>());
+    r.hi = step_up(b, k_exp<T>());
+    if (r.lo < (T)0) r.lo = (T)0;
+    return r;
+}
+
+template <typename I> __device__ __forceinline__ I itrig_pair(I x, bool is_cos) {
+    typedef decltype(x.lo) T;
+    const int h = threadIdx.x & 1;
+    I pi = pi_iv(x.lo);
+    const T big = sizeof(T) == 8 ? (T)1099511627776.0 : (T)1048576.0;
+    T w = sub_ru(x.hi, x.lo);
+    I r;
+    r.lo = (T)-1;
+    r.hi = (T)1;
+    if (!(w < pi.lo * (T)2) || !(fabs(x.lo) <= big) || !(fabs(x.hi) <= big)) return r;
+    const T e = h ? x.hi : x.lo;
+    const T v = is_cos ? lib_cos(e) : lib_sin(e);
+    const T num = h ? -x.hi : x.lo;
+    const T den = h ? (x.hi >= (T)0 ? pi.lo : pi.hi) : (x.lo >= (T)0 ? pi.hi : pi.lo);
+    const T q = div_rd(num, den);
+    const T va = pair_get(v, 0), v1 = pair_get(v, 1);
+    const T vb = x.hi == x.lo ? va : v1;
+    int k = k_trig<T>();
+    T lo = fmin(step_dn(va, k), step_dn(vb, k));
+    T hi = fmax(step_up(va, k), step_up(vb, k));
+    T qlo = pair_get(q, 0), qhi = -pair_get(q, 1);
+    if (!is_cos) {
+        qlo = sub_rd(qlo, (T)0.5);
+        qhi = sub_ru(qhi, (T)0.5);
+    }
+    T k0 = ceil(qlo), k1 = floor(qhi);
+    if (k0 <= k1) {
+        long long i0 = (long long)k0;
+        bool two = k0 + (T)1 <= k1;
+        bool even0 = (i0 & 1LL) == 0;
+        if (even0 || two) hi = (T)1;
+        if (!even0 || two) lo = (T)-1;
+    }
+    r.lo = fmax(lo, (T)-1);
+    r.hi = fmin(hi, (T)1);
+    return r;
+}
+
 }  // namespace gb

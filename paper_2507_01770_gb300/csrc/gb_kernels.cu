@@ -1802,14 +1802,18 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
                           fuse_end ? sc.stat_pos : nullptr)) != cudaSuccess)
         return e;
     if (pool.recs) {   // the record collection, when the partition asked for it
-        const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), gb_sm_count() * 8);
+        // Launched without the early start: their blocks would otherwise sit
+        // on the SMs, waiting for the partition, in the way of the tables'
+        // blocks; two blocks per SM, as they mostly return at once.
+        const unsigned ggc = (unsigned)gb_sm_count() * 2;
+        const unsigned grec = (unsigned)std::min<long long>(grid_for(pool.R, GB_TILE), ggc);
         gb_launch_count += 4;
-        if ((e = gb_launch_ex(k_gc_mark, gb_sm_count() * 8, 256, 0, s, true, pool, E_new, par, st, E,
-                              sel_tabs ? 1 : 0)) != cudaSuccess ||
-            (e = gb_launch_ex(k_gc_count, grec, PT, 0, s, true, pool, st, sc.tile_cnt)) != cudaSuccess ||
-            (e = gb_launch_ex(k_scan_tiles, 1, 1024, 0, s, true, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0LL, G,
-                              st)) != cudaSuccess ||
-            (e = gb_launch_ex(k_gc_scatter, grec, PT, 0, s, true, pool, st, sc.tile_off)) != cudaSuccess)
+        if ((e = gb_launch_ex(k_gc_mark, ggc, 256, 0, s, false, pool, E_new, par, st, E, sel_tabs ? 1 : 0)) !=
+                cudaSuccess ||
+            (e = gb_launch_ex(k_gc_count, grec, PT, 0, s, false, pool, st, sc.tile_cnt)) != cudaSuccess ||
+            (e = gb_launch_ex(k_scan_tiles, 1, 1024, 0, s, false, 1, sc.tile_cnt, sc.tile_off, sc.max_tiles, 4, 0LL,
+                              G, st)) != cudaSuccess ||
+            (e = gb_launch_ex(k_gc_scatter, grec, PT, 0, s, false, pool, st, sc.tile_off)) != cudaSuccess)
             return e;
     }
     if (!tabs) {   // with term tables k_ptab splits the parents itself

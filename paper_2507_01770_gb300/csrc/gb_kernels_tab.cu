@@ -56,7 +56,11 @@ __device__ __forceinline__ iv64 mid_node(const GbTabs& T, size_t i) { double2 v 
 // included).  On GB300 a dependent FP64 operation takes ~30 ns and a warp's
 // FP64 instruction holds the SM's FP64 pipe for ~16 clocks whatever its
 // active lanes, so each part gets a warp of its own (parts in one warp would
-// diverge and run one after the other), spread over the SMs.
+// diverge and run one after the other), spread over the SMs.  The warp's
+// lanes first stage the template's instructions and its coordinate and
+// coefficient values in shared memory (all loads in flight at once), then
+// lanes 0 and 1 interpret it together: both run every operation, and exp,
+// sin and cos evaluate their two endpoints one per lane (itrig_pair).
 // Blocks x >= row_blocks: one group tree of the parent's cached sums each
 // (sum k, kind: F, midpoint, FP32), level by level.
 constexpr int PTAB_T = 128;
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
         return;
     }
     const int parts = ptab_parts(pool);
-    int ops = 0, ops32 = 0;
+    int ops = 0, ops32 = 0, spare = 0;   // (lane 1's interpreter counts go to `spare`)
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // per warp: the template's instructions and load values (stage_term)
     __shared__ GbIns s_ins[PTAB_ITEMS][GB_MAX_TREGS];
@@ -232,25 +236,28 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             X.r = r;
             if (part == 1) {
                 stage_term<double>(P, S, i, MidView{X}, s_ins[wib], pre, lane);
-                if (lane == 0) {
+                if (lane < 2) {
                     iv64 R[GB_MAX_TREGS];
-                    const iv64 v = term_fwd<double>(P, S, i, MidView{X}, R, ops, ins, pre);
-                    T.tm64[orow] = make_double2(v.lo, v.hi);
+                    const iv64 v = term_fwd<double, MidView, true>(P, S, i, MidView{X}, R, lane ? spare : ops, ins, pre);
+                    if (lane == 0) T.tm64[orow] = make_double2(v.lo, v.hi);
                 }
             } else {
                 stage_term<double>(P, S, i, X, s_ins[wib], pre, lane);
-                if (lane == 0) {
+                if (lane < 2) {
+                    int& o = lane ? spare : ops;
                     iv64 R[GB_MAX_TREGS], RA[GB_MAX_TREGS];
-                    const iv64 v = term_fwd<double>(P, S, i, X, R, ops, ins, pre);
-                    T.tv64[orow] = make_double2(v.lo, v.hi);
+                    const iv64 v = term_fwd<double, View<double>, true>(P, S, i, X, R, o, ins, pre);
                     for (int t = 0; t < S.nins; t++) RA[t] = iv64{0.0, 0.0};
                     RA[S.nins - 1] = iv64{1.0, 1.0};
-                    reverse_sweep<double>(ins, S.nins, R, RA, ops);
-                    int leaf = 0;
-                    for (int t = 0; t < S.nins; t++) {
-                        if (ins[t].op != D_IVAR) continue;
-                        T.tl64[orow * T.max_leaves + leaf] = make_double2(RA[t].lo, RA[t].hi);
-                        leaf++;
+                    reverse_sweep<double, true>(ins, S.nins, R, RA, o);
+                    if (lane == 0) {
+                        T.tv64[orow] = make_double2(v.lo, v.hi);
+                        int leaf = 0;
+                        for (int t = 0; t < S.nins; t++) {
+                            if (ins[t].op != D_IVAR) continue;
+                            T.tl64[orow * T.max_leaves + leaf] = make_double2(RA[t].lo, RA[t].hi);
+                            leaf++;
+                        }
                     }
                 }
             }
@@ -265,18 +272,21 @@ __global__ void __launch_bounds__(PTAB_T) k_ptab(GbProg P, GbPool pool, GbParent
             X32.mstride = sp.m + 1;
             X32.r = r;
             stage_term<float>(P, S, i, X32, s_ins[wib], pre, lane);
-            if (lane == 0) {
+            if (lane < 2) {
+                int& o = lane ? spare : ops32;
                 iv32 R32[GB_MAX_TREGS], RA32[GB_MAX_TREGS];
-                const iv32 f = term_fwd<float>(P, S, i, X32, R32, ops32, ins, pre);
-                T.tv32[orow] = make_float2(f.lo, f.hi);
+                const iv32 f = term_fwd<float, View<float>, true>(P, S, i, X32, R32, o, ins, pre);
                 for (int t = 0; t < S.nins; t++) RA32[t] = iv32{0.f, 0.f};
                 RA32[S.nins - 1] = iv32{1.f, 1.f};
-                reverse_sweep<float>(ins, S.nins, R32, RA32, ops32);
-                int leaf = 0;
-                for (int t = 0; t < S.nins; t++) {
-                    if (ins[t].op != D_IVAR) continue;
-                    T.tl32[orow * T.max_leaves + leaf] = make_float2(RA32[t].lo, RA32[t].hi);
-                    leaf++;
+                reverse_sweep<float, true>(ins, S.nins, R32, RA32, o);
+                if (lane == 0) {
+                    T.tv32[orow] = make_float2(f.lo, f.hi);
+                    int leaf = 0;
+                    for (int t = 0; t < S.nins; t++) {
+                        if (ins[t].op != D_IVAR) continue;
+                        T.tl32[orow * T.max_leaves + leaf] = make_float2(RA32[t].lo, RA32[t].hi);
+                        leaf++;
+                    }
                 }
             }
         }
