@@ -1675,6 +1675,10 @@ thread_local long long gb_launch_count = 0;
 
 long long gb_launches_so_far() { return gb_launch_count; }
 
+static thread_local bool t_pdl_off = false;
+
+void gb_pdl_thread(bool on) { t_pdl_off = !on; }
+
 bool gb_pdl_enabled() {
     static int on = -1;   // read once
     int v = __atomic_load_n(&on, __ATOMIC_RELAXED);
@@ -1683,7 +1687,7 @@ bool gb_pdl_enabled() {
         v = (e && e[0] == '1') ? 0 : 1;
         __atomic_store_n(&on, v, __ATOMIC_RELAXED);
     }
-    return v != 0;
+    return v != 0 && !t_pdl_off;
 }
 
 int gb_sm_count() {

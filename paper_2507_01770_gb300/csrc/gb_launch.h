@@ -209,8 +209,12 @@ int gb_sm_count();
 // `pdl` overlaps its launch and block scheduling with the end of its
 // predecessor in the stream.  A kernel launched without `pdl` waits as
 // usual and the two calls return at once.  The environment variable
-// GB_NO_PDL=1 turns the overlap off.
+// GB_NO_PDL=1 turns the overlap off, and so does gb_pdl_thread(false) for
+// the launches (and graph captures) of the calling thread: the serving
+// worker, where many problems share the SMs and blocks waiting early would
+// only hold resources another request could use.
 bool gb_pdl_enabled();
+void gb_pdl_thread(bool on);
 template <typename... KArgs, typename... Args>
 inline cudaError_t gb_launch_ex(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
                                 Args... args) {

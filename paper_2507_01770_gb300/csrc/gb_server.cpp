@@ -199,6 +199,7 @@ gb_status gb_server_create(size_t pool_budget_bytes, int32_t device, int32_t max
     S->max_active = max_active;
     S->worker = std::thread([S] {
         cudaSetDevice(S->device);
+        gb_pdl_thread(false);   // many requests share the SMs: no early-started blocks waiting on them
         worker_loop(S);
     });
     *out = S;
