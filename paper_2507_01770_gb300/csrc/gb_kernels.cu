@@ -1683,8 +1683,8 @@ bool gb_pdl_enabled() {
     static int on = -1;   // read once
     int v = __atomic_load_n(&on, __ATOMIC_RELAXED);
     if (v < 0) {
-        const char* e = std::getenv("GB_NO_PDL");
-        v = (e && e[0] == '1') ? 0 : 1;
+        const char* e = std::getenv("GB_PDL");
+        v = (e && e[0] == '1') ? 1 : 0;
         __atomic_store_n(&on, v, __ATOMIC_RELAXED);
     }
     return v != 0 && !t_pdl_off;
@@ -1790,7 +1790,7 @@ cudaError_t gb_launch_generation(const GbProg& P, const GbPool& pool, const GbEn
         if ((et = gb_launch_ptab_d(P, pool, par, *tabs, G.K, P.B, st, ts, sel_tabs)) != cudaSuccess) return et;
         if (tabs->cs64) {
             gb_launch_count++;
-            if ((et = gb_launch_child_sums(P, par, *tabs, sp, Cmax, G.fp32, st, ts, sel_tabs)) != cudaSuccess)
+            if ((et = gb_launch_child_sums(P, pool, par, *tabs, sp, Cmax, G.fp32, st, ts, sel_tabs)) != cudaSuccess)
                 return et;
         }
         return cudaSuccess;

@@ -629,12 +629,26 @@ __device__ __forceinline__ void child_sum(const GbProg& P, const GbSplitPos& SP,
     *sout = lanes ? tab_path_lanes(S, dr, cur, node, threadIdx.x & 31, ops) : tab_path(S, dr, cur, node, ops);
 }
 
-__global__ void __launch_bounds__(128) k_child_sums(GbProg P, GbParents par, GbTabs Tb, GbSplit sp, long long Cmax,
-                                                    int kinds, GbState* st, long long nch_fixed) {
+// The first-order verdict of one (parent, kind, block coordinate, digit
+// combination): defined after tab_partial and mono_hit below.
+__device__ void mono_fill(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& Tb,
+                          const GbSplit& sp, long long u, long long npar, int& ops64, int& ops32);
+
+__global__ void __launch_bounds__(128) k_child_sums(GbProg P, GbPool pool, GbParents par, GbTabs Tb, GbSplit sp,
+                                                    long long Cmax, int kinds, GbState* st, long long nch_fixed,
+                                                    long long mv_base) {
     gb_grid_trigger();
     gb_grid_wait();
     if (st->halt) return;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= mv_base) {   // whole blocks past the child sums: the verdict tables
+        int o64 = 0, o32 = 0;
+        const long long nch = nch_fixed >= 0 ? nch_fixed : st->nch;
+        mono_fill(P, pool, par, Tb, sp, t - mv_base, nch >> sp.flog2, o64, o32);
+        warp_add_ops(o64, &st->ops64);
+        warp_add_ops(o32, &st->ops32);
+        return;
+    }
     const long long ci = t % Cmax, rest = t / Cmax;
     const int k = (int)(rest % (P.n_sum > 0 ? P.n_sum : 1)), kind = (int)(rest / (P.n_sum > 0 ? P.n_sum : 1));
     int ops = 0;
@@ -801,6 +815,93 @@ __device__ __forceinline__ bool mono_hit(const GbProg& P, const View<double>& X6
     if (!pos && !neg) return false;
     const iv64 x = X64.get(j);
     return (pos && !same_value(x.lo, __ldg(P.l + j))) || (neg && !same_value(x.hi, __ldg(P.u + j)));
+}
+
+// The digit bits of a child index that block coordinate j's first-order
+// verdict depends on, when its objective has unit outer adjoints and no
+// coordinate in the outer expression: the tabulated partial-table field of
+// each sum with contributions to j (shift, mask) and, for a split
+// coordinate, its own digit (its bounds decide the boundary condition).
+// Returns false when a sum's partial is not tabulated (it is summed per
+// child from its contributions) or the bits span more than GB_MV_BITS; else
+// [lo, lo + nb).  `meta(k, x, y, shift, mask)` gives sum k's entry.
+template <typename M>
+__device__ __forceinline__ bool mv_bits(int n_sum, M meta, int jrel, int dd, int mshift, int& lo, int& nb) {
+    int a = 32, b = 0;
+    for (int k = 0; k < n_sum; k++) {
+        int x, y, shift;
+        unsigned mask;
+        meta(k, x, y, shift, mask);
+        if (x == y) continue;
+        if (shift < 0) return false;
+        if (mask == 0) continue;
+        a = min(a, shift);
+        b = max(b, shift + 32 - __clz(mask));
+    }
+    if (jrel >= 0 && jrel < dd) {
+        a = min(a, jrel * mshift);
+        b = max(b, (jrel + 1) * mshift);
+    }
+    if (b <= a) {
+        lo = 0;
+        nb = 0;
+        return true;
+    }
+    if (b - a > GB_MV_BITS) return false;
+    lo = a;
+    nb = b - a;
+    return true;
+}
+
+// Verdict table entry u (parent, kind, block coordinate, digit combination):
+// the partial of the coordinate and the first-order test for a child whose
+// digits are that combination (zero elsewhere: nothing else is read), with
+// the operations tab_mono_w performs for every child, so its lookup gives
+// the same verdict.
+__device__ void mono_fill(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& Tb,
+                          const GbSplit& sp, long long u, long long npar, int& ops64, int& ops32) {
+    const int kinds = Tb.mv32 ? 2 : 1;
+    const long long per_p = (long long)P.B * kinds << GB_MV_BITS;
+    const long long p = u / per_p;
+    const long long rem = u - p * per_p;
+    const int kind = (int)(rem / ((long long)P.B << GB_MV_BITS));
+    const int jl = (int)((rem >> GB_MV_BITS) % P.B), combo = (int)(rem & ((1 << GB_MV_BITS) - 1));
+    if (!Tb.mv64 || p >= npar) return;
+    const int4 info = par.info[p];
+    const int spi = P.sp_of_cyc[info.x];
+    if (spi < 0) return;
+    const GbSplitPos SP = P.sps[spi];
+    const int c0 = info.z * P.B, c1 = min(P.n, c0 + P.B), j = c0 + jl;
+    if (j >= c1) return;
+    auto meta = [&](int k, int& x, int& y, int& shift, unsigned& mask) {
+        const int at = SP.jk0 + jl * P.n_sum + k;
+        const int2 rg = P.jk[at];
+        const GbJkD J = P.jkd[at];
+        x = rg.x;
+        y = rg.y;
+        shift = J.shift;
+        mask = J.mask;
+    };
+    int lo, nb;
+    if (!mv_bits(P.n_sum, meta, j - info.x, info.y, sp.mshift, lo, nb) || combo >= (1 << nb)) return;
+    ChildCtx c;
+    c.p = p;
+    c.r = (unsigned)combo << lo;
+    c.info = info;
+    c.slot = par.slot[p];
+    c.valid = true;
+    const View<double> X64 = view64(pool, par, c, sp);
+    const unsigned unit = P.outer_unit ? 0xffffffffu : 1u;
+    const size_t at = (((size_t)p * P.B + jl) << GB_MV_BITS) + combo;
+    if (kind == 0) {
+        const iv64 g = tab_partial<double>(P, Tb, leaf_tab<double>(Tb, p), part_tab<double>(Tb, p), SP, j, c0, c.r,
+                                           (const iv64*)nullptr, unit, ops64);
+        Tb.mv64[at] = mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi)) ? 1 : 0;
+    } else {
+        const iv32 g = tab_partial<float>(P, Tb, leaf_tab<float>(Tb, p), part_tab<float>(Tb, p), SP, j, c0, c.r,
+                                          (const iv32*)nullptr, unit, ops32);
+        Tb.mv32[at] = mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi)) ? 1 : 0;
+    }
 }
 
 template <typename T>
@@ -1177,7 +1278,22 @@ __device__ __forceinline__ bool tab_mono_w(const GbProg& P, const GbTabs& Tb, lo
     const typename TabPrec<T>::P2* td = part_tab<T>(Tb, p);
     bool hit = false;
     if (stage_meta(P, SP, (c1 - c0) * P.n_sum, ws.meta, lane)) {
+        // the parent's verdict table where the coordinate has one (mono_fill)
+        const unsigned char* mv = sizeof(T) == 8 ? Tb.mv64 : Tb.mv32;
         for (int j = c0 + lane; j < c1; j += 32) {
+            int lo, nb;
+            const WMeta* mj = ws.meta + (j - c0) * P.n_sum;
+            auto meta = [&](int k, int& x, int& y, int& shift, unsigned& mask) {
+                const WMeta m = mj[k];
+                x = m.x;
+                y = m.y;
+                shift = (short)(m.sm & 0xffff);
+                mask = (unsigned)m.sm >> 16;
+            };
+            if (mv && mv_bits(P.n_sum, meta, j - X64.c0, X64.dd, X64.mshift, lo, nb)) {
+                hit |= mv[(((size_t)p * P.B + (j - c0)) << GB_MV_BITS) + ((r >> lo) & ((1u << nb) - 1u))] != 0;
+                continue;
+            }
             const I g = tab_partial_m<T>(P, Tb, tl, td, ws.meta, j, c0, r, OA, unit, par);
             hit |= mono_hit(P, X64, j, gt_zero(g.lo), lt_zero(g.hi));
         }
@@ -1556,14 +1672,18 @@ cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParent
     return gb_launch_ex(k_ptab_d, dim3(g, (unsigned)K), 128, 0, s, true, P, pool, par, T, st, fixed ? 1 : 0);
 }
 
-cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const GbTabs& T, const GbSplit& sp,
-                                 long long Cmax, int fp32, GbState* st, cudaStream_t s, bool fixed) {
+cudaError_t gb_launch_child_sums(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                                 const GbSplit& sp, long long Cmax, int fp32, GbState* st, cudaStream_t s,
+                                 bool fixed) {
     if (!T.cs64 || P.n_sum <= 0) return cudaSuccess;
     const int kinds = fp32 ? 3 : 2;
     // fixed: one parent, its 2^flog2 children (the count is not read from the state)
     const long long nch = fixed ? (1LL << sp.flog2) : -1;
-    return gb_launch_ex(k_child_sums, grid_for(Cmax * P.n_sum * kinds, 128), 128, 0, s, true, P, par, T, sp, Cmax,
-                        kinds, st, nch);
+    // then, in whole blocks of their own, the first-order verdict tables
+    const long long base = (Cmax * P.n_sum * kinds + 127) / 128 * 128;
+    const long long mv = T.mv64 ? (Cmax >> sp.flog2) * P.B * (T.mv32 ? 2 : 1) << GB_MV_BITS : 0;
+    return gb_launch_ex(k_child_sums, grid_for(base + mv, 128), 128, 0, s, true, P, pool, par, T, sp, Cmax,
+                        kinds, st, nch, base);
 }
 
 cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,

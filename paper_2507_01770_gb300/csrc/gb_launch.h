@@ -99,8 +99,16 @@ struct GbTabs {
     double2* cg64;    // [Cmax][GB_CG] dirty group values, slot k * GB_TAB_MAX_DIRTY + (g - first dirty group)
     double2* cgm64;
     float2* cg32;
+    // one child per warp, objectives whose sums all enter F with adjoint
+    // [1, 1] and no coordinate of their own in the outer expression: the
+    // first-order verdict of each block coordinate for every combination of
+    // the digit bits its partial depends on (at most GB_MV_BITS of them), per
+    // parent, written by k_child_sums (null otherwise)
+    unsigned char* mv64;   // [K][B][1 << GB_MV_BITS]
+    unsigned char* mv32;
 };
 constexpr int GB_CG = GB_MAX_ISUM * GB_TAB_MAX_DIRTY;
+constexpr int GB_MV_BITS = 6;
 
 // scratch for the scans
 struct GbScan {
@@ -206,13 +214,15 @@ int gb_sm_count();
 // gb_grid_trigger() (its own dependent may be launched once all of its blocks
 // have started) and gb_grid_wait() (it touches nothing before the kernels it
 // depends on have completed and their writes are visible), so a launch with
-// `pdl` overlaps its launch and block scheduling with the end of its
-// predecessor in the stream.  A kernel launched without `pdl` waits as
-// usual and the two calls return at once.  The environment variable
-// GB_NO_PDL=1 turns the overlap off, and so does gb_pdl_thread(false) for
-// the launches (and graph captures) of the calling thread: the serving
-// worker, where many problems share the SMs and blocks waiting early would
-// only hold resources another request could use.
+// `pdl` can overlap its launch and block scheduling with the end of its
+// predecessor in the stream.  A kernel launched without `pdl` waits as usual
+// and the two calls return at once.  The overlap is off unless the
+// environment sets GB_PDL=1: measured on GB300 it loses slightly (a C3
+// generation 80.8 us with it, 79.1 us without; served solves 50.7/s with
+// it, 53.4/s without), as the early blocks hold SM resources that the
+// kernels of the other stream, or of other requests, could use.
+// gb_pdl_thread(false) keeps it off for the calling thread's launches and
+// graph captures whatever the environment (the serving worker).
 bool gb_pdl_enabled();
 void gb_pdl_thread(bool on);
 template <typename... KArgs, typename... Args>
@@ -260,8 +270,9 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
 cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                              long long K, int B, GbState* st, cudaStream_t s, bool fixed = false);
 // One child per warp: every child's sums and dirty group values (tables first).
-cudaError_t gb_launch_child_sums(const GbProg& P, const GbParents& par, const GbTabs& T, const GbSplit& sp,
-                                 long long Cmax, int fp32, GbState* st, cudaStream_t s, bool fixed = false);
+cudaError_t gb_launch_child_sums(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
+                                 const GbSplit& sp, long long Cmax, int fp32, GbState* st, cudaStream_t s,
+                                 bool fixed = false);
 // cc non-null (at most 2^16 children): the kernel's last block also lists the survivors.
 cudaError_t gb_launch_eval3264_tabw(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,
                                     const GbChildren& ch, long long Cmax, const GbSplit& sp, GbState* st,

@@ -1,14 +1,14 @@
 """The launch mechanics do not change a solve (GPU).
 
-A generation's kernels are launched with programmatic dependent launch (a
-kernel may start while its predecessor finishes, and waits for it before
-touching its results), a single-parent generation runs the parent's tables
-on a second stream beside the pool partition, and a solve replays several
-generations from one CUDA graph.  None of this may change what the search
-computes (section 3.1 loop): the same solve with the early start turned off
-(GB_NO_PDL=1, in a child process, as the switch is read once per process),
-and with one generation per host synchronisation (no graphs), must give the
-same trace, enclosure and output boxes bit for bit.
+A generation's kernels can be launched with programmatic dependent launch
+(GB_PDL=1: a kernel may start while its predecessor finishes, and waits for
+it before touching its results), a single-parent generation runs the
+parent's tables on a second stream beside the pool partition, and a solve
+replays several generations from one CUDA graph.  None of this may change
+what the search computes (section 3.1 loop): the same solve with the early
+start turned on (in a child process, as the switch is read once per
+process) and off, and with one generation per host synchronisation (no
+graphs), must give the same trace, enclosure and output boxes bit for bit.
 """
 import json
 import os
@@ -57,19 +57,19 @@ print(json.dumps(out))
 """
 
 
-def _run(no_pdl):
+def _run(pdl):
     env = dict(os.environ)
-    env.pop("GB_NO_PDL", None)
-    if no_pdl:
-        env["GB_NO_PDL"] = "1"
+    env.pop("GB_PDL", None)
+    if pdl:
+        env["GB_PDL"] = "1"
     r = subprocess.run([sys.executable, "-c", CHILD, ROOT], capture_output=True, text=True, env=env, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def test_early_start_streams_and_graphs_do_not_change_the_solve():
-    a = _run(no_pdl=False)
-    b = _run(no_pdl=True)
+    a = _run(pdl=False)
+    b = _run(pdl=True)
     assert a.keys() == b.keys()
     for k in a:
         assert a[k] == b[k], k
