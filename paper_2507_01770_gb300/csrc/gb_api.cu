@@ -533,6 +533,18 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
                          (e = alloc(&T.nf32, nodes, A))))
                 return bad(e, "allocate term tables");
             T.warp = opt.eval_mode == 4 ? 1 : opt.eval_mode == 3 ? 0 : (gb_warp_per_child(p->Cmax) ? 1 : 0);
+            T.reg = 0;
+            if (P.outer_sum && P.n_sum == 1 && P.n_var_leaves == 0) {   // the register-resident walk of the one sum
+                const GbSum& S0 = Hh.sums[0];
+                bool fits = true;
+                for (int b = 0; b < Hh.nb && fits; b++) {
+                    const int2 dr = Hh.dirty[b];
+                    fits = dr.y - dr.x <= GB_REG_DIRTY;
+                    for (int g = dr.x; g < dr.y && fits; g++)
+                        fits = Hh.groups[S0.group0 + g].count < (1 << GB_REG_LEVELS);
+                }
+                T.reg = fits ? 1 : 0;
+            }
             T.max_sum_nodes = 1;
             for (const GbSum& S : Hh.sums) T.max_sum_nodes = std::max(T.max_sum_nodes, (int)S.nnodes);
             T.tree_smem = (size_t)T.max_sum_nodes * sizeof(double2) <= 48 * 1024 ? 1 : 0;   // no opt-in needed

@@ -21,6 +21,12 @@ using namespace gb;
 #ifndef GB_TAB_MINB
 #define GB_TAB_MINB 7
 #endif
+// The same for the register-resident single-sum kernel (80 registers, no
+// local memory to speak of; measured on the n = 100 chain, 4^10 children a
+// launch: 27.1 ms per solve at 6 blocks, 27.7 at 5 and at 7).
+#ifndef GB_TAB_MINB_REG
+#define GB_TAB_MINB_REG 6
+#endif
 // Blocks per SM of their grid (each thread loops over children).
 #ifndef GB_TAB_GRID
 #define GB_TAB_GRID 32
@@ -969,12 +975,173 @@ __device__ __forceinline__ void tab_sums64(const GbProg& P, const GbTabs& Tb, lo
     }
 }
 
+// Register-resident forms of the single-sum walk, for objectives whose outer
+// expression is one sum and whose blocks have at most GB_REG_DIRTY dirty
+// groups of fewer than 2^GB_REG_LEVELS terms (checked on the host).  The
+// level, count and range tests depend only on the parent's split position,
+// so they are the same for every lane.  Every case of them (carries of a
+// push, levels present, a path level's width) is its own straight-line
+// code reached through a switch: array indices are constants, so nothing
+// goes to thread-local memory, and no FP64 operation is issued under a
+// false predicate (a warp's FP64 instruction holds the pipe whatever its
+// active lanes).  Same operations in the same order as Tree, tab_path and
+// tab_sums64, so the same sums.
+static_assert(GB_REG_LEVELS == 5, "the switch cases below cover 5 levels");
+static_assert(GB_REG_DIRTY == 4, "the switch cases below cover 4 dirty groups");
+struct RegTree64 {
+    iv64 lvl[GB_REG_LEVELS];
+    unsigned cnt;
+    __device__ __forceinline__ void init() { cnt = 0; }
+    // v combined with the stored levels L .. L + K - 1 (lowest first), the
+    // result stored at level L + K
+    template <int L, int K>
+    __device__ __forceinline__ void put(iv64 v) {
+#pragma unroll
+        for (int i = 0; i < K; i++) v = iadd(lvl[L + i], v);
+        lvl[L + K] = v;
+    }
+    // Tree::push_level: the carries are the set bits of cnt from L up
+    __device__ __forceinline__ void push_level(iv64 v, int L) {
+        const int k = __ffs(~(cnt >> L)) - 1;
+        switch (L * 8 + k) {
+#define GB_PUT(a, b) \
+    case (a) * 8 + (b): put<a, b>(v); break;
+            GB_PUT(0, 0) GB_PUT(0, 1) GB_PUT(0, 2) GB_PUT(0, 3) GB_PUT(0, 4)
+            GB_PUT(1, 0) GB_PUT(1, 1) GB_PUT(1, 2) GB_PUT(1, 3)
+            GB_PUT(2, 0) GB_PUT(2, 1) GB_PUT(2, 2)
+            GB_PUT(3, 0) GB_PUT(3, 1)
+            GB_PUT(4, 0)
+#undef GB_PUT
+            default: break;   // beyond the levels the host check allows
+        }
+        cnt += 1u << L;
+    }
+    // Tree::result for the levels present M (ascending order)
+    template <unsigned M>
+    __device__ __forceinline__ iv64 res() const {
+        iv64 r{0.0, 0.0};
+        bool have = false;
+#pragma unroll
+        for (int i = 0; i < GB_REG_LEVELS; i++) {
+            if ((M >> i) & 1u) {
+                r = have ? iadd(lvl[i], r) : lvl[i];
+                have = true;
+            }
+        }
+        return r;
+    }
+    __device__ __forceinline__ iv64 result() const {
+        switch (cnt) {
+#define GB_RES(m) \
+    case m: return res<m>();
+            GB_RES(1) GB_RES(2) GB_RES(3) GB_RES(4) GB_RES(5) GB_RES(6) GB_RES(7) GB_RES(8)
+            GB_RES(9) GB_RES(10) GB_RES(11) GB_RES(12) GB_RES(13) GB_RES(14) GB_RES(15) GB_RES(16)
+            GB_RES(17) GB_RES(18) GB_RES(19) GB_RES(20) GB_RES(21) GB_RES(22) GB_RES(23) GB_RES(24)
+            GB_RES(25) GB_RES(26) GB_RES(27) GB_RES(28) GB_RES(29) GB_RES(30) GB_RES(31)
+#undef GB_RES
+            default: return iv64{0.0, 0.0};   // empty
+        }
+    }
+};
+
+// One level of tab_path over NT parents (SINGLE: the last one has no right
+// child).  Node a of the level below sits at cur[a - lo]; the t-th parent's
+// children a = 2(nlo + t), a + 1 sit at 2t - (lo & 1) and 2t + 1 - (lo & 1),
+// both at or after t, so the level is rebuilt in place in ascending t.
+template <int NT, bool SINGLE, typename N>
+__device__ __forceinline__ void path_level(iv64 (&cur)[GB_REG_DIRTY], int lo, int hi, int nlo, int off, N node,
+                                           int& ops) {
+    const bool odd = lo & 1;
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        const int a = 2 * (nlo + t);
+        constexpr int D = GB_REG_DIRTY - 1;
+        const int e0 = 2 * t, e1 = 2 * t + 1;   // even lo: cur indices of a, a + 1
+        const iv64 ca = odd ? cur[e0 - 1 < 0 ? 0 : (e0 - 1 > D ? D : e0 - 1)] : cur[e0 > D ? D : e0];
+        const iv64 left = (a >= lo && a < hi) ? ca : node(off + a);
+        if (SINGLE && t == NT - 1) {
+            cur[t] = left;
+        } else {
+            const iv64 cb = odd ? cur[e1 - 1 > D ? D : e1 - 1] : cur[e1 > D ? D : e1];
+            const iv64 right = (a + 1 >= lo && a + 1 < hi) ? cb : node(off + a + 1);
+            cur[t] = iadd(left, right);
+            ops += 2;
+        }
+    }
+}
+
+// tab_path over at most GB_REG_DIRTY dirty nodes per level.
+template <typename N>
+__device__ __forceinline__ iv64 tab_path_reg(const GbSum& S, int2 dr, iv64 (&cur)[GB_REG_DIRTY], N node, int& ops) {
+    if (S.ngroups == 0 || S.nnodes <= 0) return iv64{0.0, 0.0};
+    int lo = dr.x, hi = dr.y, off = 0;
+    if (lo >= hi) return node(S.nnodes - 1);   // no dirty group: the parent's root
+    for (int mL = S.ngroups; mL > 1; mL = (mL + 1) / 2) {
+        const int nlo = lo >> 1, nhi = ((hi - 1) >> 1) + 1;
+        const bool single = 2 * (nhi - 1) + 1 >= mL;
+        switch ((nhi - nlo) * 2 + (single ? 1 : 0)) {
+            case 2: path_level<1, false>(cur, lo, hi, nlo, off, node, ops); break;
+            case 3: path_level<1, true>(cur, lo, hi, nlo, off, node, ops); break;
+            case 4: path_level<2, false>(cur, lo, hi, nlo, off, node, ops); break;
+            case 5: path_level<2, true>(cur, lo, hi, nlo, off, node, ops); break;
+            case 6: path_level<3, false>(cur, lo, hi, nlo, off, node, ops); break;
+            case 7: path_level<3, true>(cur, lo, hi, nlo, off, node, ops); break;
+            case 8: path_level<4, false>(cur, lo, hi, nlo, off, node, ops); break;
+            case 9: path_level<4, true>(cur, lo, hi, nlo, off, node, ops); break;
+            default: break;   // wider than the host check allows
+        }
+        lo = nlo;
+        hi = nhi;
+        off += mL;
+    }
+    return cur[0];
+}
+
+// The one sum of a child over the box (MID false) or at its midpoint (MID
+// true): its dirty groups from the term-tree segments, then the group-tree
+// path (tab_sums64 for n_sum = 1, one of its two walks).
+template <bool MID>
+__device__ __forceinline__ iv64 tab_sum1_reg(const GbProg& P, const GbTabs& Tb, long long p, const GbSplitPos& SP,
+                                             int blk, unsigned r, int& ops) {
+    const double2* tv = (MID ? Tb.tm64 : Tb.tv64) + (size_t)p * Tb.max_rows;
+    const double2* ts = (MID ? Tb.tsm64 : Tb.ts64) + (size_t)p * Tb.max_srows;
+    const double2* nd = (MID ? Tb.nm64 : Tb.nf64) + (size_t)p * Tb.tree_nodes;
+    const GbSum S = P.sums[0];
+    const int2 dr = P.dirty[blk];
+    iv64 cur[GB_REG_DIRTY];
+    int sg = SP.seg0;
+    const int send = SP.seg0 + SP.nseg;
+#pragma unroll
+    for (int t = 0; t < GB_REG_DIRTY; t++) {
+        cur[t] = iv64{0.0, 0.0};
+        const int g = dr.x + t;
+        if (g < dr.y) {
+            RegTree64 tr;
+            tr.init();
+            int ns = 0;
+            while (sg < send) {
+                const GbSeg G = P.segs[sg];
+                if (G.sum != 0 || G.group != g) break;
+                const int at = G.base + (int)((r >> G.shift) & G.mask);
+                const double2 a = G.level ? ts[at] : tv[at];
+                tr.push_level(iv64{a.x, a.y}, G.level);
+                ns++;
+                sg++;
+            }
+            ops += 2 * (ns > 0 ? ns - 1 : 0);
+            cur[t] = tr.result();
+        }
+    }
+    const double2* ndk = nd + S.node0;
+    return tab_path_reg(S, dr, cur, [&](int i) { const double2 v = ndk[i]; return iv64{v.x, v.y}; }, ops);
+}
+
 // FP64 child: midpoint sample, F(X), cut-off.  SUM1: the outer expression
 // is one sum (F is that sum; the first-order test is left to
 // eval64_tab_mono and *need_mono tells whether the child passed the
 // cut-off).  Otherwise the first-order test follows at once and the flag is
 // set here.  Returns false for an invalid child.
-template <bool SUM1>
+template <bool SUM1, bool REG = false>
 __device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& pool, const GbParents& par,
                                                  const GbTabs& Tb, const GbChildren& ch, long long ci,
                                                  const GbSplit& sp, double gub_prev, unsigned long long* gkey,
@@ -989,6 +1156,19 @@ __device__ __forceinline__ bool eval64_tab_child(const GbProg& P, const GbPool& 
     }
     const GbSplitPos SP = P.sps[spi];
     const int blk = c.info.z;
+    if constexpr (SUM1 && REG) {
+        const iv64 F = tab_sum1_reg<false>(P, Tb, c.p, SP, blk, c.r, ops);
+        const iv64 Fm = tab_sum1_reg<true>(P, Tb, c.p, SP, blk, c.r, ops);
+        if (Fm.hi == Fm.hi) {
+            *gkey = gb_order_key(Fm.hi);
+            *has_key = true;
+        }
+        const bool keep = !(F.lo > gub_prev);
+        ch.flo[ci] = canon_lo(F.lo);
+        if (keep) *need_mono = true;
+        else ch.flag[ci] = 0;
+        return true;
+    }
     View<double> X = view64(pool, par, c, sp);
     iv64 sums[GB_MAX_ISUM], msums[GB_MAX_ISUM];
     tab_sums64(P, Tb, c.p, SP, blk, c.r, sums, msums, ops);
@@ -1033,12 +1213,31 @@ __device__ __forceinline__ void eval64_tab_mono(const GbProg& P, const GbPool& p
     ch.flag[ci] = mono ? 0 : 1;
 }
 
+// eval64_tab_mono for one sum (n_sum = 1, no outer VAR leaves): its
+// adjoint is [1, 1], so each partial is the tabulated sum alone.
+__device__ __forceinline__ void eval64_tab_mono1(const GbProg& P, const GbPool& pool, const GbParents& par,
+                                                 const GbTabs& Tb, const GbChildren& ch, long long ci,
+                                                 const GbSplit& sp, int& ops) {
+    const ChildCtx c = child_ctx(par, ci, sp);
+    const GbSplitPos SP = P.sps[P.sp_of_cyc[c.info.x]];
+    const View<double> X = view64(pool, par, c, sp);
+    const int c0 = c.info.z * P.B, c1 = min(P.n, c0 + P.B);
+    const double2* tl = leaf_tab<double>(Tb, c.p);
+    const double2* td = part_tab<double>(Tb, c.p);
+    bool mono = false;
+    for (int j = c0; j < c1 && !mono; j++) {
+        const iv64 g = tab_partial<double>(P, Tb, tl, td, SP, j, c0, c.r, (const iv64*)nullptr, 1u, ops);
+        mono = mono_hit(P, X, j, gt_zero(g.lo), lt_zero(g.hi));
+    }
+    ch.flag[ci] = mono ? 0 : 1;
+}
+
 // One child per thread.  When the outer expression is one sum, the children
 // of a warp that pass the cut-off are queued in shared memory and their
 // first-order tests run 32 at a time, every lane busy, instead of inside the
 // branch of the lanes that passed (the same tests, so the same flags).
-template <bool QUEUE>
-__global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval64_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
+template <bool QUEUE, bool REG>
+__global__ void __launch_bounds__(128, REG ? GB_TAB_MINB_REG : GB_TAB_MINB) k_eval64_tab(GbProg P, GbPool pool, GbParents par, GbTabs Tb,
                                                     GbChildren ch, GbSplit sp, int from_list, GbState* st) {
     gb_grid_trigger();
     gb_grid_wait();
@@ -1062,7 +1261,7 @@ __global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval64_tab(GbProg P, GbPoo
             ci = from_list ? (long long)ch.list32[idx] : idx;
             unsigned long long k2 = ~0ull;
             bool h2 = false;
-            valid = eval64_tab_child<QUEUE>(P, pool, par, Tb, ch, ci, sp, gub_prev, &k2, &h2, ops, &need);
+            valid = eval64_tab_child<QUEUE, REG>(P, pool, par, Tb, ch, ci, sp, gub_prev, &k2, &h2, ops, &need);
             if (h2 && k2 < key) key = k2, has = true;
         }
         nvalid += __popc(__ballot_sync(0xffffffffu, valid));
@@ -1072,12 +1271,16 @@ __global__ void __launch_bounds__(128, GB_TAB_MINB) k_eval64_tab(GbProg P, GbPoo
         qn += __popc(bal);
         __syncwarp();
         if (qn >= 32) {
-            eval64_tab_mono(P, pool, par, Tb, ch, q[qn - 32 + lane], sp, ops);
+            if constexpr (REG) eval64_tab_mono1(P, pool, par, Tb, ch, q[qn - 32 + lane], sp, ops);
+            else eval64_tab_mono(P, pool, par, Tb, ch, q[qn - 32 + lane], sp, ops);
             qn -= 32;
             __syncwarp();
         }
     }
-    if (queue && lane < qn) eval64_tab_mono(P, pool, par, Tb, ch, q[lane], sp, ops);   // the rest of the queue
+    if (queue && lane < qn) {   // the rest of the queue
+        if constexpr (REG) eval64_tab_mono1(P, pool, par, Tb, ch, q[lane], sp, ops);
+        else eval64_tab_mono(P, pool, par, Tb, ch, q[lane], sp, ops);
+    }
     warp_min_gub(key, has, st);
     warp_add_ops(ops, &st->ops64);
     if (lane == 0 && nvalid) {
@@ -1658,8 +1861,9 @@ cudaError_t gb_launch_eval64_tab(const GbProg& P, const GbPool& pool, const GbPa
     }
     unsigned g = grid_for(Cmax, 128);
     if (g > gb_sm_count() * GB_TAB_GRID) g = gb_sm_count() * GB_TAB_GRID;
-    return gb_launch_ex(P.outer_sum ? k_eval64_tab<true> : k_eval64_tab<false>, g, 128, 0, s, true, P, pool, par, T,
-                        ch, sp, from_list ? 1 : 0, st);
+    return gb_launch_ex(P.outer_sum ? (T.reg ? k_eval64_tab<true, true> : k_eval64_tab<true, false>)
+                                    : k_eval64_tab<false, false>,
+                        g, 128, 0, s, true, P, pool, par, T, ch, sp, from_list ? 1 : 0, st);
 }
 
 cudaError_t gb_launch_ptab_d(const GbProg& P, const GbPool& pool, const GbParents& par, const GbTabs& T,

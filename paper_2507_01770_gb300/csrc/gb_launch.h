@@ -106,9 +106,15 @@ struct GbTabs {
     // parent, written by k_child_sums (null otherwise)
     unsigned char* mv64;   // [K][B][1 << GB_MV_BITS]
     unsigned char* mv32;
+    // one child per thread, objectives whose outer expression is one sum:
+    // 1 when every block's dirty groups fit the register-resident walk (at
+    // most GB_REG_DIRTY groups of fewer than 2^GB_REG_LEVELS terms each)
+    int reg;
 };
 constexpr int GB_CG = GB_MAX_ISUM * GB_TAB_MAX_DIRTY;
 constexpr int GB_MV_BITS = 6;
+constexpr int GB_REG_DIRTY = 4;
+constexpr int GB_REG_LEVELS = 5;
 
 // scratch for the scans
 struct GbScan {
