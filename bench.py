@@ -84,9 +84,9 @@ FP32_OPS_PER_SM_CLK = 128.0  # 128 FP32 lanes per SM (directed add / mul at full
 WORKLOADS = {
     "chain100": dict(family="chain", n=100, block=10, split_m=4, split_d=10, max_children=1 << 20, fp32=0,
                      gens_per_sync=0, pool_gb=16.0, cpu_parents=4, cpu_split_m=2, cpu_split_d=10, cpu_gens=20,
-                     # DRAM bytes (read + write) of one k_eval64_tab launch: none until the
-                     # register-resident kernel's counters are taken
-                     traffic=None,
+                     # DRAM bytes (read + write) of one k_eval64_tab launch, ncu capture in
+                     # profiles/k_eval64_tab_chain100.md
+                     traffic=0.645e6,
                      name="chain n=100 (coupled quartic, planted min 0), FP64, B=10, 4-way split of the 10 "
                           "block coordinates (4^10 children) of 1 best box per generation, tol_f=1e-6"),
     "ackley1000": dict(family="ackley", n=1000, block=10, split_m=2, split_d=10, max_children=1 << 10, fp32=1,
