@@ -555,7 +555,8 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
                     return bad(e, "allocate child sums");
                 if ((P.outer_unit || (P.outer_sum && P.n_sum == 1)) && P.n_var_leaves == 0) {   // verdict tables
                     const size_t mv = (size_t)p->K * P.B << GB_MV_BITS;
-                    if ((e = alloc(&T.mv64, mv, A)) || (fp32 && (e = alloc(&T.mv32, mv, A))))
+                    if ((e = alloc(&T.mv64, mv, A)) || (fp32 && (e = alloc(&T.mv32, mv, A))) ||
+                        (e = alloc(&T.mvb, (size_t)p->K * P.B, A)))
                         return bad(e, "allocate first-order verdicts");
                 }
             }

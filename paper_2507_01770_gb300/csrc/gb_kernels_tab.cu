@@ -889,7 +889,10 @@ __device__ void mono_fill(const GbProg& P, const GbPool& pool, const GbParents& 
         mask = J.mask;
     };
     int lo, nb;
-    if (!mv_bits(P.n_sum, meta, j - info.x, info.y, sp.mshift, lo, nb) || combo >= (1 << nb)) return;
+    const bool fits = mv_bits(P.n_sum, meta, j - info.x, info.y, sp.mshift, lo, nb);
+    if (kind == 0 && combo == 0 && Tb.mvb)
+        Tb.mvb[(size_t)p * P.B + jl] = fits ? (unsigned short)(lo | nb << 8) : (unsigned short)0xffff;
+    if (!fits || combo >= (1 << nb)) return;
     ChildCtx c;
     c.p = p;
     c.r = (unsigned)combo << lo;
@@ -1480,6 +1483,21 @@ __device__ __forceinline__ bool tab_mono_w(const GbProg& P, const GbTabs& Tb, lo
     const typename TabPrec<T>::P2* tl = leaf_tab<T>(Tb, p);
     const typename TabPrec<T>::P2* td = part_tab<T>(Tb, p);
     bool hit = false;
+    const unsigned char* mvt = sizeof(T) == 8 ? Tb.mv64 : Tb.mv32;
+    if (mvt && Tb.mvb) {   // the parent's digit fields: one lookup per coordinate when all have a table
+        bool all = true;
+        for (int j = c0 + lane; j < c1; j += 32) {
+            const unsigned e = Tb.mvb[(size_t)p * P.B + (j - c0)];
+            if (e == 0xffffu) {
+                all = false;
+                continue;
+            }
+            const unsigned lo = e & 0xffu, nb = e >> 8;
+            hit |= mvt[(((size_t)p * P.B + (j - c0)) << GB_MV_BITS) + ((r >> lo) & ((1u << nb) - 1u))] != 0;
+        }
+        if (__all_sync(0xffffffffu, all)) return __any_sync(0xffffffffu, hit);
+        hit = false;   // some coordinate has no table: the test below covers every coordinate
+    }
     if (stage_meta(P, SP, (c1 - c0) * P.n_sum, ws.meta, lane)) {
         // the parent's verdict table where the coordinate has one (mono_fill)
         const unsigned char* mv = sizeof(T) == 8 ? Tb.mv64 : Tb.mv32;

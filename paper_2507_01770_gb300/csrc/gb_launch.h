@@ -106,6 +106,10 @@ struct GbTabs {
     // parent, written by k_child_sums (null otherwise)
     unsigned char* mv64;   // [K][B][1 << GB_MV_BITS]
     unsigned char* mv32;
+    // with the verdict tables: each block coordinate's digit field in them
+    // (first bit | bit count << 8; 0xffff: the coordinate has none), per
+    // parent -- it depends on the parent's split alone
+    unsigned short* mvb;   // [K][B]
     // one child per thread, objectives whose outer expression is one sum:
     // 1 when every block's dirty groups fit the register-resident walk (at
     // most GB_REG_DIRTY groups of fewer than 2^GB_REG_LEVELS terms each)
