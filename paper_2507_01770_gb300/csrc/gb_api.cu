@@ -547,7 +547,9 @@ gb_status gb_create_problem(const gb_node* dag, int32_t n_nodes, int32_t root, c
             }
             T.max_sum_nodes = 1;
             for (const GbSum& S : Hh.sums) T.max_sum_nodes = std::max(T.max_sum_nodes, (int)S.nnodes);
-            T.tree_smem = (size_t)T.max_sum_nodes * sizeof(double2) <= 48 * 1024 ? 1 : 0;   // no opt-in needed
+            // no opt-in needed: the table kernel's static shared memory (about 7 KB) and the
+            // trees stay within the 48 KB a launch gets by default
+            T.tree_smem = (size_t)T.max_sum_nodes * sizeof(double2) <= 32 * 1024 ? 1 : 0;
             if (T.warp) {   // per-child sums and dirty group values (k_child_sums)
                 const size_t cs = (size_t)p->Cmax * (P.n_sum > 0 ? P.n_sum : 1), cg = (size_t)p->Cmax * GB_CG;
                 if ((e = alloc(&T.cs64, cs, A)) || (e = alloc(&T.csm64, cs, A)) || (e = alloc(&T.cg64, cg, A)) ||
